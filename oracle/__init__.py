@@ -1,0 +1,355 @@
+"""FP64 CPU oracle of the particle PHD filter (TEST INFRASTRUCTURE ONLY).
+
+Only tests/, the package smoke check and the benchmark's CPU-baseline leg may
+import this module.  It shares no code with the CUDA path: the arithmetic is
+in `phd_oracle.c` (plain C, IEEE double, built with FMA contraction off so the
+results do not depend on the host's instruction set), driven from here with
+numpy arrays.  `OracleFilter` strings the stages together in the order of the
+paper's Algorithm 1 (predict, update, local estimation and fusion, resample,
+exchange); OSPA (the metric of Sec. 4.1) is computed with an optimal
+assignment.
+
+Readings of the paper taken here (each also stated in the C source):
+ * Eq. 7 is <psi_z, D> (the trailing "* x" is a typo); nu = 1 - p_D.
+ * Births: p_k(.|Z) = U(region) x N(0, s_b^2 I), weight nu_b / J.
+ * Distributed form: each PE is a full local filter over its slice (births
+   split J/K per PE with weight nu_b / J_j), uses its local C^j ("local"
+   mode) or the mean of the PEs' C^j ("global" mode), resamples to
+   round((rho / K) * max(1, N^j)) particles and sends floor(frac * min_j n_j)
+   random particles to the next PE on the ring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "phd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile phd_oracle.c into liboracle.so beside it (gcc, no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [
+        ("meas_model", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("dt", ctypes.c_double), ("sigma_a", ctypes.c_double),
+        ("sigma_z", ctypes.c_double * 2), ("sensor", ctypes.c_double * 2),
+        ("region", ctypes.c_double * 4), ("r_max", ctypes.c_double),
+        ("p_s", ctypes.c_double), ("p_d", ctypes.c_double),
+        ("clutter_rate", ctypes.c_double), ("birth_mass", ctypes.c_double),
+        ("birth_vel_sigma", ctypes.c_double),
+    ]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_U = ctypes.POINTER(ctypes.c_uint32)
+_M = ctypes.POINTER(_Model)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_kappa.restype = ctypes.c_double
+            L.orc_kappa.argtypes = [_M]
+            L.orc_measure.argtypes = [_M, _D, _D]
+            L.orc_likelihood.restype = ctypes.c_double
+            L.orc_likelihood.argtypes = [_M, _D, _D]
+            L.orc_predict.argtypes = [_M, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+            L.orc_colsum.argtypes = [_M, _D, _D, ctypes.c_int, _D, ctypes.c_int, _D]
+            L.orc_weight_update.argtypes = [_M, _D, _D, ctypes.c_int, _D, ctypes.c_int, _D, _D]
+            L.orc_extract.restype = ctypes.c_int
+            L.orc_extract.argtypes = [_M, _D, _D, ctypes.c_int, _D, ctypes.c_int, _D,
+                                      ctypes.c_double, _I, _D, _D, _D]
+            L.orc_resample.restype = ctypes.c_int
+            L.orc_resample.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_uint32, _D, _D, _I]
+            L.orc_exchange_slots.argtypes = [ctypes.c_int, ctypes.c_int, _U, _I]
+            L.orc_exchange.argtypes = [ctypes.c_int, _D, _D, _I, ctypes.c_int, ctypes.c_double,
+                                       _U, _I]
+            L.orc_fuse.restype = ctypes.c_int
+            L.orc_fuse.argtypes = [ctypes.c_int, _I, _I, _D, ctypes.c_int, ctypes.c_int, _I, _D]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _u(a):
+    return a.ctypes.data_as(_U)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def model(w) -> _Model:
+    """Oracle model struct from a scenario.Workload (or any object with its fields)."""
+    m = _Model()
+    m.meas_model = 0 if w.meas_model == "linear" else 1
+    m.dt, m.sigma_a = float(w.dt), float(w.sigma_a)
+    m.sigma_z[0], m.sigma_z[1] = float(w.sigma_z[0]), float(w.sigma_z[1])
+    m.sensor[0], m.sensor[1] = float(w.sensor[0]), float(w.sensor[1])
+    for k in range(4):
+        m.region[k] = float(w.region[k])
+    m.r_max = float(w.r_max)
+    m.p_s, m.p_d = float(w.p_s), float(w.p_d)
+    m.clutter_rate, m.birth_mass = float(w.clutter_rate), float(w.birth_mass)
+    m.birth_vel_sigma = float(w.birth_vel_sigma)
+    return m
+
+
+# ----------------------------------------------------------------------------
+# Stage wrappers (numpy in, numpy out)
+# ----------------------------------------------------------------------------
+
+def kappa(m: _Model) -> float:
+    return lib().orc_kappa(ctypes.byref(m))
+
+
+def measure(m: _Model, x) -> np.ndarray:
+    x = _f64(x, (-1, 4))
+    out = np.empty((len(x), 2))
+    for i in range(len(x)):
+        lib().orc_measure(ctypes.byref(m), _d(x[i]), _d(out[i]))
+    return out
+
+
+def likelihood(m: _Model, z, x) -> float:
+    z, x = _f64(z, (2,)), _f64(x, (4,))
+    return lib().orc_likelihood(ctypes.byref(m), _d(z), _d(x))
+
+
+def predict(m: _Model, x, w, J: int, noise):
+    """Eq. 5-6: survivors (len(x)) then J births; noise rows (n1, n2, u1, u2)."""
+    x, w = _f64(x, (-1, 4)), _f64(w, (-1,))
+    L = len(x)
+    noise = _f64(noise, (-1, 4))
+    assert len(noise) >= L + J
+    xo, wo = np.empty((L + J, 4)), np.empty(L + J)
+    lib().orc_predict(ctypes.byref(m), _d(x), _d(w), L, J, _d(noise), _d(xo), _d(wo))
+    return xo, wo
+
+
+def colsum(m: _Model, x, w, Z) -> np.ndarray:
+    """Eq. 7: C(z_p) = sum_j p_D g(z_p|x_j) w_j."""
+    x, w, Z = _f64(x, (-1, 4)), _f64(w, (-1,)), _f64(Z, (-1, 2))
+    C = np.empty(len(Z))
+    lib().orc_colsum(ctypes.byref(m), _d(x), _d(w), len(x), _d(Z), len(Z), _d(C))
+    return C
+
+
+def weight_update(m: _Model, x, w, Z, C_used) -> np.ndarray:
+    """Eq. 8 with nu = 1 - p_D."""
+    x, w, Z, C_used = _f64(x, (-1, 4)), _f64(w, (-1,)), _f64(Z, (-1, 2)), _f64(C_used, (-1,))
+    out = np.empty(len(x))
+    lib().orc_weight_update(ctypes.byref(m), _d(x), _d(w), len(x), _d(Z), len(Z),
+                            _d(C_used), _d(out))
+    return out
+
+
+@dataclass
+class Extraction:
+    labels: np.ndarray     # selection order: descending dW, ties by label
+    zeta: np.ndarray       # (n, 4)
+    dW: np.ndarray         # (M,) sub-weight mass per measurement (Eq. 16)
+    dW0: float             # missed-detection sub-weight mass (Eq. 17)
+    LT: int                # round(N_k) before the caps
+
+
+def extract(m: _Model, x, w_pred, Z, C_used, Nk: float) -> Extraction:
+    """Eq. 10-18 and Step 3: LT = round(N_k), top-LT dW^p, zeta_p (Eq. 18)."""
+    x, w_pred, Z, C_used = (_f64(x, (-1, 4)), _f64(w_pred, (-1,)), _f64(Z, (-1, 2)),
+                            _f64(C_used, (-1,)))
+    M = len(Z)
+    labels = np.empty(max(M, 1), dtype=np.int32)
+    zeta = np.empty((max(M, 1), 4))
+    dW = np.empty(max(M, 1))
+    dW0 = np.empty(1)
+    n = lib().orc_extract(ctypes.byref(m), _d(x), _d(w_pred), len(x), _d(Z), M, _d(C_used),
+                          float(Nk), _i(labels), _d(zeta), _d(dW), _d(dW0))
+    return Extraction(labels[:n].copy(), zeta[:n].copy(), dW[:M].copy(), float(dW0[0]),
+                      int(np.floor(Nk + 0.5)))
+
+
+def resample(x, w, rho: float, l_max: int, U: int):
+    """Systematic resampling with the exact integer-valued CDF; returns (x, w, parent)."""
+    x, w = _f64(x, (-1, 4)), _f64(w, (-1,))
+    N = len(x)
+    Nk = float(w.sum()) if N else 0.0
+    cap = int(min(l_max, max(0, np.floor(rho * max(1.0, Nk) + 0.5) + 1)))
+    cap = max(cap, 1)
+    xo, wo = np.empty((cap, 4)), np.empty(cap)
+    par = np.empty(cap, dtype=np.int32)
+    L = lib().orc_resample(_d(x), _d(w), N, float(rho), int(l_max), int(U) & 0xFFFFFFFF,
+                           _d(xo), _d(wo), _i(par))
+    assert L <= cap
+    return xo[:L].copy(), wo[:L].copy(), par[:L].copy()
+
+
+def exchange_slots(n: int, count: int, u) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.uint32))
+    slots = np.empty(max(count, 1), dtype=np.int32)
+    lib().orc_exchange_slots(int(n), int(count), _u(u), _i(slots))
+    return slots[:count].copy()
+
+
+def exchange(xs: List[np.ndarray], ws: List[np.ndarray], frac: float, u) -> tuple:
+    """Step 6 ring exchange over K slices; returns new (xs, ws, slots)."""
+    K = len(xs)
+    counts = np.asarray([len(a) for a in xs], dtype=np.int32)
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.uint32))
+    stride = u.shape[1]
+    assert counts.max(initial=0) <= stride
+    X = np.zeros((K, stride, 4))
+    W = np.zeros((K, stride))
+    for j in range(K):
+        X[j, :counts[j]] = xs[j]
+        W[j, :counts[j]] = ws[j]
+    nmin = int(counts.min()) if K else 0
+    Lx = int(np.floor(frac * nmin)) if K > 1 else 0
+    slots = np.zeros((K, max(Lx, 1)), dtype=np.int32)
+    lib().orc_exchange(K, _d(X), _d(W), _i(counts), stride, float(frac), _u(u), _i(slots))
+    return ([X[j, :counts[j]].copy() for j in range(K)],
+            [W[j, :counts[j]].copy() for j in range(K)], slots[:, :Lx].copy())
+
+
+def fuse(per_pe: Sequence[Extraction], M: int) -> tuple:
+    """Step 4 CU fusion: labels reported by more than K/2 PEs, mean state."""
+    K = len(per_pe)
+    stride = max([len(e.labels) for e in per_pe] + [1])
+    n = np.asarray([len(e.labels) for e in per_pe], dtype=np.int32)
+    lab = np.full((K, stride), -1, dtype=np.int32)
+    zet = np.zeros((K, stride, 4))
+    for j, e in enumerate(per_pe):
+        lab[j, :len(e.labels)] = e.labels
+        zet[j, :len(e.labels)] = e.zeta
+    out_l = np.empty(max(M, 1), dtype=np.int32)
+    out_z = np.empty((max(M, 1), 4))
+    c = lib().orc_fuse(K, _i(n), _i(lab), _d(zet), stride, M, _i(out_l), _d(out_z))
+    return out_l[:c].copy(), out_z[:c].copy()
+
+
+# ----------------------------------------------------------------------------
+# OSPA (Schuhmacher, Vo & Vo), on positions
+# ----------------------------------------------------------------------------
+
+def ospa(X, Y, c: float = 100.0, p: float = 2.0) -> float:
+    """OSPA distance between two point sets (rows are points)."""
+    from scipy.optimize import linear_sum_assignment
+    X = np.asarray(X, dtype=np.float64).reshape(-1, np.shape(X)[-1] if np.size(X) else 2)
+    Y = np.asarray(Y, dtype=np.float64).reshape(-1, np.shape(Y)[-1] if np.size(Y) else 2)
+    m, n = len(X), len(Y)
+    if m == 0 and n == 0:
+        return 0.0
+    if m == 0 or n == 0:
+        return float(c)
+    if m > n:
+        X, Y, m, n = Y, X, n, m
+    D = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    Dc = np.minimum(D, c) ** p
+    r, col = linear_sum_assignment(Dc)
+    cost = Dc[r, col].sum() + (c ** p) * (n - m)
+    return float((cost / n) ** (1.0 / p))
+
+
+# ----------------------------------------------------------------------------
+# The filter: global (K = 1) and distributed (K > 1) forms
+# ----------------------------------------------------------------------------
+
+class OracleFilter:
+    """The particle PHD filter (Sec. 2.2) and its DCPFPHD form (Algorithm 1).
+
+    Random numbers are injected: `noise` rows (n1, n2, u1, u2) per particle
+    slot laid out [K][pe_cap], one uint32 per PE for resampling, and uint32
+    exchange draws [K][pe_cap].
+    """
+
+    def __init__(self, w, init_x: Optional[List[np.ndarray]] = None,
+                 init_w: Optional[List[np.ndarray]] = None):
+        self.w = w
+        self.m = model(w)
+        self.K = int(w.num_pe)
+        self.pe_cap = int(w.pe_cap)
+        J = int(w.birth_count)
+        self.J = [J // self.K + (1 if j < J % self.K else 0) for j in range(self.K)]
+        self.rho_pe = float(w.particles_per_target) / self.K
+        self.l_max = [self.pe_cap - self.J[j] for j in range(self.K)]
+        self.x = init_x if init_x is not None else [np.zeros((0, 4)) for _ in range(self.K)]
+        self.wt = init_w if init_w is not None else [np.zeros(0) for _ in range(self.K)]
+        self.last = {}
+
+    def step(self, Z, noise, U, xu=None):
+        m, K = self.m, self.K
+        Z = _f64(Z, (-1, 2))
+        M = len(Z)
+        noise = _f64(noise, (K, self.pe_cap, 4))
+        # Step 1: predict (survivors + births per PE)
+        xp, wp = [], []
+        for j in range(K):
+            a, b = predict(m, self.x[j], self.wt[j], self.J[j], noise[j])
+            xp.append(a)
+            wp.append(b)
+        # Step 2: update with local C^j (paper) or the PE mean ("global")
+        C_loc = [colsum(m, xp[j], wp[j], Z) for j in range(K)]
+        if getattr(self.w, "ck_mode", "local") == "global":
+            C_mean = np.mean(np.stack(C_loc), axis=0) if M else np.zeros(0)
+            C_used = [C_mean] * K
+        else:
+            C_used = C_loc
+        wu = [weight_update(m, xp[j], wp[j], Z, C_used[j]) for j in range(K)]
+        Nk = [float(a.sum()) for a in wu]
+        # Step 3: local estimation; Step 4: CU fusion (identity for K = 1)
+        ex = [extract(m, xp[j], wp[j], Z, C_used[j], Nk[j]) for j in range(K)]
+        lab, zet = fuse(ex, M)
+        # Step 5: local resampling
+        xr, wr, par = [], [], []
+        for j in range(K):
+            a, b, c = resample(xp[j], wu[j], self.rho_pe, self.l_max[j], int(U[j]))
+            xr.append(a)
+            wr.append(b)
+            par.append(c)
+        # Step 6: ring exchange
+        slots = None
+        if K > 1 and self.w.exchange_frac > 0:
+            xr, wr, slots = exchange(xr, wr, self.w.exchange_frac, xu)
+        self.x, self.wt = xr, wr
+        self.last = dict(x_pred=xp, w_pred=wp, C_local=C_loc, C_used=C_used, w_upd=wu,
+                         Nk=Nk, extract=ex, parents=par, slots=slots)
+        return lab, zet
+
+
+__all__ = [
+    "build", "lib", "model", "kappa", "measure", "likelihood", "predict", "colsum",
+    "weight_update", "extract", "Extraction", "resample", "exchange_slots", "exchange",
+    "fuse", "ospa", "OracleFilter",
+]

@@ -1,0 +1,271 @@
+"""Seeded synthetic inputs for the particle PHD filter: workloads, truth, sensor, noise.
+
+This module is the one piece shared by the CUDA path's tests/benchmarks and the
+CPU oracle.  It simulates the *world* (target truth tracks and the sensor's
+measurement sets) and draws the random numbers the filter consumes, and it
+computes no filter quantity: no likelihood, weight, normaliser, sum or estimate
+lives here.
+
+Scenario (paper Sec. 4): targets move by the constant-velocity model with
+sampling period T = 1 and zero-mean Gaussian acceleration noise; each live
+target is detected with probability p_D; clutter is a Poisson number of points
+uniform over the measurement space.  Two sensors: linear position (x, y) with
+Gaussian noise, and range-bearing from a sensor position (paper Sec. 4,
+measurement model).  Numbers of the five workloads follow the published
+workload list; the truth-birth schedule of the larger workloads is not in the
+paper and is a reading (births at seeded steps in the first 40 % of the run,
+no deaths other than leaving the region).
+
+Noise layout consumed by both implementations (one row of four per particle
+slot, survivors first then births, per processing element (PE) slot range):
+  row = (n1, n2, u1, u2); survivors use n1, n2 as the standard normal
+  acceleration draws; births use n1, n2 as standard normal velocity draws and
+  u1, u2 in [0, 1) as the position fractions across the region.
+Resampling takes one uint32 per PE per step; the ring exchange takes one
+uint32 per selected slot (a partial Fisher-Yates draw), up to pe_cap per PE.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict, replace
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+DEG = math.pi / 180.0
+
+LINEAR = "linear"
+RANGE_BEARING = "range_bearing"
+
+
+@dataclass(frozen=True)
+class Workload:
+    """Parameters of one filter workload (model, sizes and run length)."""
+    name: str
+    meas_model: str = LINEAR
+    dt: float = 1.0
+    sigma_a: float = 5.0                    # process (acceleration) noise std, m/s^2
+    sigma_z: tuple = (10.0, 10.0)           # linear: (m, m); range-bearing: (m, rad)
+    sensor: tuple = (0.0, 0.0)
+    region: tuple = (-1000.0, 1000.0, -1000.0, 1000.0)   # x_min, x_max, y_min, y_max
+    r_max: float = 1000.0 * math.sqrt(2.0)  # range-bearing clutter range extent
+    p_s: float = 0.99
+    p_d: float = 0.95
+    clutter_rate: float = 10.0              # lambda: expected clutter points per scan
+    birth_mass: float = 0.1                 # expected births per step (nu_b)
+    birth_count: int = 500                  # J birth particles per step (all PEs)
+    birth_vel_sigma: float = 20.0
+    particles_per_target: int = 500         # rho
+    num_pe: int = 1                         # K processing elements (1 = global filter)
+    exchange_frac: float = 0.0
+    ck_mode: str = "local"                  # "local" (paper) or "global" (exact mean)
+    precision: str = "fp32"
+    n_targets: int = 4
+    birth_steps: Optional[tuple] = None     # explicit truth birth steps (1-based)
+    steps: int = 50
+    truth_vel_sigma: float = 20.0
+    pe_cap: int = 0                         # particle slots per PE (0: derived)
+    m_max: int = 0                          # measurement capacity (0: derived)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+    def as_dict(self) -> dict:
+        return asdict(self)
+
+
+def _derive_caps(w: Workload) -> Workload:
+    """Fill pe_cap / m_max with generous capacities for the workload's sizes."""
+    K = w.num_pe
+    j_pe = -(-w.birth_count // K)
+    # expected mass <= targets + births; keep 3x headroom on the survivor count
+    n_t = max(w.n_targets, 1)
+    rho_pe = w.particles_per_target / K
+    surv = int(math.ceil(rho_pe * (3 * n_t + 8)))
+    pe_cap = w.pe_cap or int(-(-(surv + j_pe) // 256) * 256)
+    m_exp = w.clutter_rate + w.n_targets
+    m_max = w.m_max or int(-(-int(m_exp + 8 * math.sqrt(m_exp) + 32) // 64) * 64)
+    return replace(w, pe_cap=pe_cap, m_max=m_max)
+
+
+def workload(name: str, **overrides) -> Workload:
+    """Named workloads: the five published configurations plus small test cases."""
+    base = {
+        # Plain global particle PHD, linear position sensor, FP64.
+        "linear4_fp64": Workload(
+            name="linear4_fp64", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+            clutter_rate=10.0, n_targets=4, birth_steps=(1, 10, 20, 30),
+            particles_per_target=500, birth_count=500, steps=50, precision="fp64"),
+        # Paper's distributed scheme: 16 PEs, 10 % ring exchange, CU fusion.
+        "dist16_10t": Workload(
+            name="dist16_10t", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+            clutter_rate=50.0, n_targets=10, particles_per_target=1000,
+            birth_count=1000, steps=100, num_pe=16, exchange_frac=0.1,
+            precision="fp32"),
+        # Dense scale, range-bearing sensor at the origin.
+        "dense_rb_100t": Workload(
+            name="dense_rb_100t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
+            clutter_rate=500.0, n_targets=100, particles_per_target=2000,
+            birth_count=20000, steps=100, precision="fp32"),
+        # Learned-birth evaluation scenario (range-bearing, 50 targets).
+        "rb_50t": Workload(
+            name="rb_50t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
+            clutter_rate=100.0, n_targets=50, particles_per_target=1000,
+            birth_count=5000, steps=100, precision="fp32"),
+    }
+    if name not in base:
+        raise KeyError(f"unknown workload {name!r}; known: {sorted(base)}")
+    return _derive_caps(base[name].with_(**overrides))
+
+
+# ----------------------------------------------------------------------------
+# Truth and sensor simulation
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Scenario:
+    workload: Workload
+    truth: List[np.ndarray] = field(default_factory=list)   # per step: (n_k, 4) float64
+    truth_ids: List[np.ndarray] = field(default_factory=list)
+    meas: List[np.ndarray] = field(default_factory=list)    # per step: (M_k, 2) float32
+    meas_is_target: List[np.ndarray] = field(default_factory=list)
+
+
+def _cv_move(x: np.ndarray, dt: float, acc: np.ndarray) -> np.ndarray:
+    """World motion of the truth tracks (constant velocity + acceleration noise)."""
+    out = x.copy()
+    out[:, 0] = x[:, 0] + dt * x[:, 1] + 0.5 * dt * dt * acc[:, 0]
+    out[:, 1] = x[:, 1] + dt * acc[:, 0]
+    out[:, 2] = x[:, 2] + dt * x[:, 3] + 0.5 * dt * dt * acc[:, 1]
+    out[:, 3] = x[:, 3] + dt * acc[:, 1]
+    return out
+
+
+def _sense(w: Workload, x: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Sensor output for true states x with noise draws v (world side)."""
+    if w.meas_model == LINEAR:
+        return np.stack([x[:, 0] + w.sigma_z[0] * v[:, 0],
+                         x[:, 2] + w.sigma_z[1] * v[:, 1]], axis=1)
+    px, py = x[:, 0] - w.sensor[0], x[:, 2] - w.sensor[1]
+    r = np.sqrt(px * px + py * py) + w.sigma_z[0] * v[:, 0]
+    th = np.arctan2(py, px) + w.sigma_z[1] * v[:, 1]
+    th = np.where(th > math.pi, th - 2 * math.pi, th)
+    th = np.where(th <= -math.pi, th + 2 * math.pi, th)
+    return np.stack([r, th], axis=1)
+
+
+def _clutter(w: Workload, rng: np.random.Generator, n: int) -> np.ndarray:
+    u = rng.random((n, 2))
+    if w.meas_model == LINEAR:
+        x0, x1, y0, y1 = w.region
+        return np.stack([x0 + u[:, 0] * (x1 - x0), y0 + u[:, 1] * (y1 - y0)], axis=1)
+    return np.stack([u[:, 0] * w.r_max, math.pi - u[:, 1] * 2 * math.pi], axis=1)
+
+
+def simulate(w: Workload, seed: int, steps: Optional[int] = None) -> Scenario:
+    """Truth tracks and measurement sets for `steps` scans (default: w.steps)."""
+    steps = w.steps if steps is None else steps
+    rng = np.random.default_rng(np.random.SeedSequence([0x5CE4, seed]))
+    x0, x1, y0, y1 = w.region
+    if w.birth_steps is not None:
+        bsteps = list(w.birth_steps)[: w.n_targets]
+        bsteps += [1] * (w.n_targets - len(bsteps))
+    else:
+        hi = max(1, int(0.4 * w.steps))
+        bsteps = sorted(int(s) for s in rng.integers(1, hi + 1, size=w.n_targets))
+    # initial states: positions in the inner 80 % of the region
+    cx, cy, hx, hy = 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.4 * (x1 - x0), 0.4 * (y1 - y0)
+    init = np.stack([cx + hx * (2 * rng.random(w.n_targets) - 1),
+                     w.truth_vel_sigma * rng.standard_normal(w.n_targets),
+                     cy + hy * (2 * rng.random(w.n_targets) - 1),
+                     w.truth_vel_sigma * rng.standard_normal(w.n_targets)], axis=1)
+    sc = Scenario(workload=w)
+    live = np.zeros((0, 4))
+    ids = np.zeros((0,), dtype=np.int64)
+    for k in range(1, steps + 1):
+        if len(live):
+            live = _cv_move(live, w.dt, w.sigma_a * rng.standard_normal((len(live), 2)))
+            inside = ((live[:, 0] >= x0) & (live[:, 0] <= x1) &
+                      (live[:, 2] >= y0) & (live[:, 2] <= y1))
+            live, ids = live[inside], ids[inside]
+        born = [t for t in range(w.n_targets) if bsteps[t] == k]
+        if born:
+            live = np.concatenate([live, init[born]], axis=0)
+            ids = np.concatenate([ids, np.asarray(born, dtype=np.int64)])
+        det = rng.random(len(live)) < w.p_d
+        zt = _sense(w, live[det], rng.standard_normal((int(det.sum()), 2)))
+        nc = int(rng.poisson(w.clutter_rate))
+        zc = _clutter(w, rng, nc)
+        z = np.concatenate([zt, zc], axis=0)
+        is_t = np.concatenate([np.ones(len(zt), bool), np.zeros(nc, bool)])
+        perm = rng.permutation(len(z))
+        sc.truth.append(live.copy())
+        sc.truth_ids.append(ids.copy())
+        sc.meas.append(np.ascontiguousarray(z[perm], dtype=np.float32))
+        sc.meas_is_target.append(is_t[perm])
+    return sc
+
+
+# ----------------------------------------------------------------------------
+# Random numbers consumed by the filter (injected into both implementations)
+# ----------------------------------------------------------------------------
+
+def births_per_pe(w: Workload) -> List[int]:
+    """Births per PE: J split as evenly as possible, lower PEs take the remainder."""
+    K, J = w.num_pe, w.birth_count
+    return [J // K + (1 if j < J % K else 0) for j in range(K)]
+
+
+def step_noise(seed: int, step: int, K: int, pe_cap: int, dtype=np.float64) -> np.ndarray:
+    """Per-slot predict/birth draws, shape (K * pe_cap, 4): (n1, n2, u1, u2).
+
+    Values are rounded to `dtype` here so both implementations read identical
+    numbers whatever precision they compute in.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([0xA11CE, seed, step]))
+    n = K * pe_cap
+    out = np.empty((n, 4), dtype=np.float64)
+    out[:, 0:2] = rng.standard_normal((n, 2))
+    out[:, 2:4] = rng.random((n, 2))
+    if dtype == np.float32:
+        out = out.astype(np.float32)
+        # a float32 rounding of u < 1 may round up to 1.0; keep u in [0, 1)
+        out[:, 2:4] = np.minimum(out[:, 2:4], np.float32(1.0 - 2.0 ** -24))
+    return np.ascontiguousarray(out)
+
+
+def resample_u32(seed: int, step: int, K: int) -> np.ndarray:
+    rng = np.random.default_rng(np.random.SeedSequence([0x5E5A, seed, step]))
+    return rng.integers(0, 2 ** 32, size=K, dtype=np.uint64).astype(np.uint32)
+
+
+def exchange_u32(seed: int, step: int, K: int, pe_cap: int) -> np.ndarray:
+    rng = np.random.default_rng(np.random.SeedSequence([0xE8C4, seed, step]))
+    return rng.integers(0, 2 ** 32, size=(K, pe_cap), dtype=np.uint64).astype(np.uint32)
+
+
+def random_particles(rng: np.random.Generator, w: Workload, n: int,
+                     centres: Optional[np.ndarray] = None, spread: float = 30.0,
+                     mass: float = 1.0) -> tuple:
+    """A synthetic particle cloud (states, weights) for stage-level tests.
+
+    Positions cluster around `centres` (or spread over the region), velocities
+    N(0, 20^2), weights positive with total `mass`.
+    """
+    x0, x1, y0, y1 = w.region
+    if centres is None or len(centres) == 0:
+        pos = np.stack([x0 + rng.random(n) * (x1 - x0), y0 + rng.random(n) * (y1 - y0)], 1)
+    else:
+        c = centres[rng.integers(0, len(centres), size=n)]
+        pos = c + spread * rng.standard_normal((n, 2))
+    vel = 20.0 * rng.standard_normal((n, 2))
+    x = np.stack([pos[:, 0], vel[:, 0], pos[:, 1], vel[:, 1]], axis=1)
+    wgt = rng.random(n) + 0.05
+    wgt *= mass / wgt.sum()
+    return x, wgt
+
+
+__all__ = [
+    "Workload", "workload", "Scenario", "simulate", "births_per_pe", "step_noise",
+    "resample_u32", "exchange_u32", "random_particles", "LINEAR", "RANGE_BEARING", "DEG",
+]
