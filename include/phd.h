@@ -1,0 +1,199 @@
+/*
+ * phd.h -- C ABI of libphd.so: the particle PHD filter step on one GB300 GPU.
+ *
+ * The library implements one step of the particle PHD filter of
+ * "Distributed Computation Particle PHD filter" (arXiv 1503.03769) in two
+ * forms: the exact global filter (Sec. 2.2) and the paper's distributed
+ * DCPFPHD scheme (Sec. 3, Algorithm 1), where K processing elements (PEs) each
+ * own a slice of the particles against the full measurement set, exchange
+ * particles on a ring and report measurement-labelled estimates to a central
+ * unit (CU) that fuses them.  Every stage runs in hand-written CUDA kernels on
+ * the caller's stream; there is no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a phd_status; no exception or longjmp crosses the ABI.
+ *  - "d_" pointers are device memory, "h_" pointers host memory.  Device
+ *    buffers are borrowed for the duration of the call (asynchronous calls:
+ *    until the stream reaches the enqueued work).
+ *  - Real-typed buffers hold float when cfg.precision == PHD_FP32 and double
+ *    when cfg.precision == PHD_FP64 ("real" below).
+ *  - A particle state is 4 reals [x, vx, y, vy] (Sec. 4 state vector); a
+ *    measurement is 2 reals: (x, y) for PHD_MEAS_LINEAR, (range, bearing in
+ *    (-pi, pi]) for PHD_MEAS_RANGE_BEARING.  The measurement's row index in
+ *    Z_k is its label p (Sec. 3, Step 3).
+ *  - Particle slices are laid out [K][pe_cap]: PE j owns slots
+ *    j*pe_cap .. j*pe_cap + n_j - 1.
+ *  - Calls are asynchronous on the stream given to phd_init unless marked
+ *    "synchronises"; those wait for the stream before returning.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef PHD_H
+#define PHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PHD_OK = 0,
+    PHD_ERR_INVALID_ARG = 1,  /* bad pointer, size, config value, or non-finite input */
+    PHD_ERR_CAPACITY = 2,     /* a count exceeds pe_cap / m_max / the caller's capacity */
+    PHD_ERR_CUDA = 3,         /* a CUDA runtime call failed; see phd_last_error_string */
+    PHD_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    PHD_ERR_STATE = 5         /* call out of order (e.g. extract before update) */
+} phd_status;
+
+enum { PHD_MEAS_LINEAR = 0, PHD_MEAS_RANGE_BEARING = 1 };
+enum { PHD_FP32 = 0, PHD_FP64 = 1 };
+enum { PHD_CK_LOCAL = 0, PHD_CK_GLOBAL = 1 };
+
+/* Filter configuration (plain data, copied by phd_init). */
+typedef struct phd_config {
+    int32_t meas_model;     /* PHD_MEAS_LINEAR | PHD_MEAS_RANGE_BEARING (Sec. 4) */
+    int32_t precision;      /* PHD_FP32: FP32 bulk, FP64 normalisers and CDF; PHD_FP64: all FP64 */
+    int32_t num_pe;         /* K >= 1 processing elements (1 = global filter), <= 256 */
+    int32_t ck_mode;        /* PHD_CK_LOCAL: each PE uses its own C^j (Step 2);
+                               PHD_CK_GLOBAL: every PE uses the mean of the C^j */
+    int32_t pe_cap;         /* particle slots per PE (survivors + births), <= 2^24 */
+    int32_t m_max;          /* largest |Z_k| accepted, 1..4096 */
+    int32_t birth_count;    /* J birth particles per step, split J/K per PE (Step 1) */
+    int32_t reserved0;      /* must be 0 */
+    double dt;              /* sampling period T */
+    double sigma_a;         /* acceleration noise std (m/s^2) */
+    double sigma_z[2];      /* linear: (sx, sy) m; range-bearing: (s_r m, s_theta rad) */
+    double sensor[2];       /* range-bearing sensor position */
+    double region[4];       /* x_min, x_max, y_min, y_max: birth support, linear clutter support */
+    double r_max;           /* range-bearing clutter support [0, r_max] x (-pi, pi] */
+    double p_s;             /* survival probability e_{k|k-1} (Eq. 5) */
+    double p_d;             /* detection probability P_D (Eq. 4) */
+    double clutter_rate;    /* lambda: kappa(z) = lambda / |measurement space| */
+    double birth_mass;      /* nu_b: expected births per step; each birth weighs nu_b / J_j */
+    double birth_vel_sigma; /* birth velocity std per axis (m/s) */
+    double particles_per_target; /* rho: a PE resamples to round((rho/K) max(1, N^j)) */
+    double exchange_frac;   /* ring exchange: floor(frac * min_j n_j) particles per PE (Step 6) */
+    uint64_t seed;          /* Philox-4x32-10 key for the in-kernel random numbers */
+} phd_config;
+
+typedef struct phd_handle phd_handle;
+
+/* ---- lifetime ------------------------------------------------------------ */
+
+/* Bytes of device workspace phd_init needs for cfg (>= 256-byte aligned). */
+phd_status phd_workspace_size(const phd_config *cfg, size_t *bytes);
+
+/* Create a filter.  d_workspace: caller-owned device buffer of at least
+ * phd_workspace_size bytes, 256-byte aligned, that must outlive the handle;
+ * the handle owns host metadata only.  stream: a cudaStream_t (NULL = the
+ * legacy default stream), borrowed.  The filter starts empty (no particles,
+ * mass 0): targets enter through birth (Eq. 6).  Synchronises. */
+phd_status phd_init(phd_handle **h, const phd_config *cfg, void *d_workspace, size_t bytes,
+                    void *stream);
+
+/* Release the handle (not the workspace).  Synchronises. */
+phd_status phd_destroy(phd_handle *h);
+
+/* Borrowed, NUL-terminated description of the handle's last error. */
+const char *phd_last_error_string(const phd_handle *h);
+const char *phd_status_string(phd_status s);
+
+/* ---- the step's stages (Algorithm 1 order) -------------------------------- */
+
+/* Prediction, Eq. 5 (survivors: CV transition, weight p_S w) and Eq. 6
+ * (births: J_j particles per PE, position uniform over cfg.region, velocity
+ * N(0, birth_vel_sigma^2 I), weight birth_mass / J_j).  d_noise: NULL to draw
+ * in-kernel (Philox), or real [K][pe_cap][4] rows (n1, n2, u1, u2): survivor
+ * slot i uses n1, n2 as its standard normal accelerations; birth slot i uses
+ * n1, n2 as standard normal velocity draws and u1, u2 in [0, 1) as position
+ * fractions.  Errors: PHD_ERR_STATE if called twice without an update. */
+phd_status phd_predict(phd_handle *h, const void *d_noise);
+
+/* Update, Eq. 7-8: C^j_p = sum_i p_D g(z_p|x_i) w_i per PE (FP64 accumulation),
+ * w_i <- [(1 - p_D) + sum_p p_D g(z_p|x_i) / (kappa + C_p)] w_i with C_p the
+ * PE's own C^j_p (LOCAL) or the PE mean (GLOBAL).  d_Z: real [M][2]; it is
+ * copied into the workspace on the stream, so the caller may overwrite it
+ * once the stream has passed this call.
+ * Errors: PHD_ERR_CAPACITY if M > m_max; PHD_ERR_INVALID_ARG if M < 0;
+ * PHD_ERR_STATE unless a predict came first.  Non-finite measurements set the
+ * handle's device error word, reported by the next synchronising call. */
+phd_status phd_update(phd_handle *h, const void *d_Z, int32_t M);
+
+/* Measurement-labelled extraction (Eq. 10-18, Step 3) and CU fusion (Step 4).
+ * Per PE j: LT_j = round(N^j) with N^j the updated mass; the LT_j largest
+ * sub-weight masses dW^{j,p} = C^j_p / (kappa + C_p) (ties: lower label;
+ * dW = 0 never taken); zeta_p = sum_i dw^{i,p} x_i / dW^p (Eq. 18).  Fusion
+ * keeps a label reported by more than K/2 PEs with the mean of their states
+ * (for K = 1 every selected label).  Output, ascending label: d_states real
+ * [cap][4], d_labels int32 [cap]; d_count (device int32, may be NULL) gets the
+ * true count.  If h_count is non-NULL the call synchronises, stores the true
+ * count and returns PHD_ERR_CAPACITY when it exceeds cap (the first cap
+ * estimates are still written).  Errors: PHD_ERR_STATE unless after update. */
+phd_status phd_extract(phd_handle *h, void *d_states, int32_t *d_labels, int32_t cap,
+                       int32_t *d_count, int32_t *h_count);
+
+/* Resampling (Sec. 2.2 step 3; Algorithm 1 "Resample") then, for K > 1 and
+ * exchange_frac > 0, the ring exchange (Step 6).  Per PE: systematic
+ * resampling on the exact integer CDF Q_i = sum_{k<=i} floor(w_k 2^s),
+ * s = 52 - ceil(log2 n) - e, max w < 2^e; L_j = min(pe_cap - J_j,
+ * round((rho/K) max(1, N^j))); child t's parent is the least i with
+ * Q_i > floor((t 2^32 + U_j) Q_n / (L_j 2^32)); new weights N^j / L_j.  Then
+ * PE j moves floor(frac min_j L_j) random particles (partial Fisher-Yates,
+ * r = t + floor(u_t (L_j - t) / 2^32)) into the same number of slots that
+ * PE j+1 vacated.  d_u: NULL (Philox) or uint32 [K]; d_xu: NULL (Philox) or
+ * uint32 [K][pe_cap] exchange draws.  Errors: PHD_ERR_STATE unless after update. */
+phd_status phd_resample(phd_handle *h, const uint32_t *d_u, const uint32_t *d_xu);
+
+/* One whole step with in-kernel random numbers: predict, update, extract,
+ * resample (+ exchange).  Arguments as for phd_update and phd_extract
+ * (h_count non-NULL synchronises). */
+phd_status phd_step(phd_handle *h, const void *d_Z, int32_t M, void *d_states, int32_t *d_labels,
+                    int32_t cap, int32_t *d_count, int32_t *h_count);
+
+/* phd_step from host memory: copies h_Z [M][2] to the device, runs the step,
+ * copies the estimates back to h_states [cap][4] / h_labels [cap] and their
+ * true count to *h_count.  Host buffers may be pageable; pinned is faster.
+ * Synchronises.  Errors as phd_step; PHD_ERR_INVALID_ARG for non-finite h_Z. */
+phd_status phd_step_host(phd_handle *h, const void *h_Z, int32_t M, void *h_states,
+                         int32_t *h_labels, int32_t cap, int32_t *h_count);
+
+/* ---- state access (parity tests, checkpoint / resume) --------------------- */
+
+/* Replace the particle set: d_x real [K][pe_cap][4], d_w real [K][pe_cap],
+ * h_counts int32 [K] (each <= pe_cap - J_j).  Resets the stage order to
+ * "ready to predict".  Synchronises. */
+phd_status phd_set_state(phd_handle *h, const void *d_x, const void *d_w, const int32_t *h_counts);
+
+/* Copy the current particle set (layout as phd_set_state; slots beyond n_j
+ * are unspecified) and h_counts int32 [K].  After phd_predict / phd_update
+ * this is the predicted / updated set.  Synchronises. */
+phd_status phd_get_state(phd_handle *h, void *d_x, void *d_w, int32_t *h_counts);
+
+/* After phd_update: d_C double [K][m_max] with C^j_p of Eq. 7 per PE, and
+ * h_mass double [K] (may be NULL) with the updated masses N^j.  Synchronises. */
+phd_status phd_get_update(phd_handle *h, double *d_C, double *h_mass);
+
+/* After phd_extract: per-PE local estimates before fusion, d_states real
+ * [K][m_max][4], d_labels int32 [K][m_max] in selection order, h_counts int32
+ * [K].  Synchronises. */
+phd_status phd_get_local_estimates(phd_handle *h, void *d_states, int32_t *d_labels,
+                                   int32_t *h_counts);
+
+/* After phd_resample: d_parents int32 [K][pe_cap] (parent slot of each child
+ * before the exchange) and h_lx (may be NULL) = particles moved per PE.
+ * Synchronises. */
+phd_status phd_get_resample(phd_handle *h, int32_t *d_parents, int32_t *h_lx);
+
+/* Step counter (drives the Philox counters); set it to resume a checkpoint. */
+phd_status phd_get_step(phd_handle *h, uint64_t *step);
+phd_status phd_set_step(phd_handle *h, uint64_t step);
+
+/* Wait for the stream and report a device-side error (non-finite input,
+ * bounded-wait timeout) recorded since the last check.  Synchronises. */
+phd_status phd_sync(phd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHD_H */

@@ -1,0 +1,108 @@
+// Prediction (Eq. 5-6) and measurement staging.
+//
+// k_predict: one thread per particle slot of every PE.  Survivor slots
+// (i < n_cur[j]) move by the constant-velocity model of Sec. 4,
+//   x' = x + T vx + T^2/2 a_x,  vx' = vx + T a_x  (same for y),
+// with a = sigma_a (n1, n2), and take weight p_S w (proposal = transition, so
+// Eq. 5's phi/q is the survival probability).  Birth slots
+// (n_cur[j] <= i < n_cur[j] + J_j) draw position U(region) and velocity
+// N(0, s_b^2 I) and take weight nu_b / J_j (Eq. 6 with gamma = nu_b p_k).
+// The update is in place: survivors keep their slots, births append.
+// Random numbers come from the caller (noise rows n1, n2, u1, u2) or from
+// Philox-4x32-10 keyed by the seed with counter (slot, step, tag).
+//
+// Memory traffic per particle: 16 B (float) state read + 16 B written, 4 B
+// weight read + written, plus 16 B of injected noise when given.
+#include "phd_internal.cuh"
+
+namespace phd {
+
+template <class R>
+__global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __restrict__ noise) {
+  St4<R>* x = static_cast<St4<R>*>(d.x);
+  R* w = static_cast<R*>(d.w);
+  const unsigned long long step = *d.step;
+  const long total = (long)m.K * m.pe_cap;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / m.pe_cap);
+    const int i = (int)(g - (long)j * m.pe_cap);
+    const int L = d.n_cur[j];
+    const int Jj = births_of(m.J, m.K, j);
+    if (i >= L + Jj) continue;
+    R n1, n2, u1, u2;
+    if (noise) {
+      const St4<R> nz = reinterpret_cast<const St4<R>*>(noise)[g];
+      n1 = nz.x; n2 = nz.vx; u1 = nz.y; u2 = nz.vy;
+    } else {
+      U4 r = philox4x32_10(U4{(uint32_t)g, (uint32_t)step, kTagPredict, (uint32_t)(step >> 32)},
+                           (uint32_t)m.seed, (uint32_t)(m.seed >> 32));
+      // Box-Muller on two open-interval uniforms
+      R ua = unit_open<R>(r.a), ub = unit_open<R>(r.b);
+      R rad = sqrt((R)-2 * log(ua));
+      R sn, cs;
+      sincospi((R)2 * ub, &sn, &cs);
+      n1 = rad * cs;
+      n2 = rad * sn;
+      u1 = unit_open<R>(r.c);
+      u2 = unit_open<R>(r.d);
+    }
+    if (i < L) {
+      const R T = (R)m.dt;
+      const R ax = (R)m.sigma_a * n1, ay = (R)m.sigma_a * n2;
+      St4<R> s = x[g];
+      St4<R> o;
+      o.x = s.x + T * s.vx + (R)0.5 * T * T * ax;
+      o.vx = s.vx + T * ax;
+      o.y = s.y + T * s.vy + (R)0.5 * T * T * ay;
+      o.vy = s.vy + T * ay;
+      x[g] = o;
+      w[g] = (R)m.p_s * w[g];
+    } else {
+      St4<R> o;
+      o.x = (R)m.rx0 + u1 * (R)(m.rx1 - m.rx0);
+      o.vx = (R)m.birth_vel_sigma * n1;
+      o.y = (R)m.ry0 + u2 * (R)(m.ry1 - m.ry0);
+      o.vy = (R)m.birth_vel_sigma * n2;
+      x[g] = o;
+      w[g] = (R)(m.birth_mass / (double)Jj);
+    }
+    if (i == 0) d.n_pred[j] = L + Jj;
+  }
+}
+
+// Copy Z_k into the workspace (in place when it is already there), publish M,
+// and flag non-finite measurements.
+template <class R>
+__global__ void k_stage_z(Dev d, Model, const R* Z, int M) {
+  V2<R>* zs = static_cast<V2<R>*>(d.Z);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
+    V2<R> z = reinterpret_cast<const V2<R>*>(Z)[p];
+    if (!isfinite(z.a) || !isfinite(z.b)) atomicOr(d.err, kErrNonFinite);
+    zs[p] = z;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d.M = M;
+}
+
+template <class R>
+cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s) {
+  long total = (long)m.K * m.pe_cap;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_predict<R><<<blocks, 256, 0, s>>>(d, m, noise);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_stage_z(const Dev& d, const Model& m, const R* Z, int M, cudaStream_t s) {
+  int blocks = (M + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  k_stage_z<R><<<blocks, 256, 0, s>>>(d, m, Z, M);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_predict<float>(const Dev&, const Model&, const float*, cudaStream_t);
+template cudaError_t launch_predict<double>(const Dev&, const Model&, const double*, cudaStream_t);
+template cudaError_t launch_stage_z<float>(const Dev&, const Model&, const float*, int, cudaStream_t);
+template cudaError_t launch_stage_z<double>(const Dev&, const Model&, const double*, int, cudaStream_t);
+
+}  // namespace phd

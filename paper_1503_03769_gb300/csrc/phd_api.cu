@@ -1,0 +1,492 @@
+// Host side of the C ABI declared in include/phd.h: configuration checks,
+// workspace carve, stage ordering, and stream-ordered launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "phd.h"
+#include "phd_internal.cuh"
+
+using phd::Dev;
+using phd::Model;
+
+namespace {
+
+enum Stage { kReady = 0, kPredicted = 1, kUpdated = 2 };
+
+}  // namespace
+
+struct phd_handle {
+  phd_config cfg;
+  Model m;
+  Dev d;
+  cudaStream_t stream;
+  int device;
+  int stage;
+  std::string err;
+  void* out_states;   // St4<R> [m_max] staging for phd_step_host
+  int* out_labels;    // [m_max]
+};
+
+namespace {
+
+size_t real_size(const phd_config& c) { return c.precision == PHD_FP64 ? 8 : 4; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T> T* take(size_t n_elems, size_t elem = sizeof(T)) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n_elems * elem;
+    return p;
+  }
+};
+
+// Lays out the workspace; with base == nullptr only measures it.
+size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** out_labels) {
+  const size_t rs = real_size(c);
+  const size_t K = (size_t)c.num_pe, P = (size_t)c.pe_cap, Mm = (size_t)c.m_max;
+  const size_t items = K * ((P + phd::kTile - 1) / phd::kTile);
+  Carver cv{base};
+  Dev t{};
+  t.x = cv.take<char>(K * P, 4 * rs);
+  t.w = cv.take<char>(K * P, rs);
+  t.wu = cv.take<char>(K * P, rs);
+  t.x_alt = cv.take<char>(K * P, 4 * rs);
+  t.w_alt = cv.take<char>(K * P, rs);
+  t.n_cur = cv.take<int>(K);
+  t.n_pred = cv.take<int>(K);
+  t.Z = cv.take<char>(Mm, 2 * rs);
+  t.anchors = cv.take<phd::Anchor>(phd::kAnchors);
+  t.M = cv.take<int>(1);
+  t.colpart = cv.take<double>(items * Mm);
+  t.C = cv.take<double>(K * Mm);
+  t.Cused = cv.take<double>(K * Mm);
+  t.ginv = cv.take<char>(K * Mm, rs);
+  t.rowpart = cv.take<double>(items);
+  t.mass = cv.take<double>(K);
+  t.nsel = cv.take<int>(K);
+  t.sel = cv.take<int>(K * Mm);
+  t.selrank = cv.take<int>(K * Mm);
+  t.spart = cv.take<double>(items * Mm * 5);
+  t.est_local = cv.take<char>(K * Mm, 4 * rs);
+  t.out_count = cv.take<int>(1);
+  t.rs_mass = cv.take<double>(K);
+  t.rs_s = cv.take<int>(K);
+  t.rs_L = cv.take<int>(K);
+  t.Q = cv.take<unsigned long long>(K * P);
+  t.child_end = cv.take<int>(K * P);
+  t.parent = cv.take<int>(K * P);
+  t.xslots = cv.take<int>(K * P);
+  t.lx = cv.take<int>(1);
+  t.step = cv.take<unsigned long long>(1);
+  t.err = cv.take<int>(1);
+  void* os = cv.take<char>(Mm, 4 * rs);
+  int* ol = cv.take<int>(Mm);
+  t.max_items = (int)items;
+  if (d) *d = t;
+  if (out_states) *out_states = os;
+  if (out_labels) *out_labels = ol;
+  return (cv.off + 255) & ~(size_t)255;
+}
+
+const char* check_config(const phd_config& c) {
+  if (c.meas_model != PHD_MEAS_LINEAR && c.meas_model != PHD_MEAS_RANGE_BEARING) return "meas_model";
+  if (c.precision != PHD_FP32 && c.precision != PHD_FP64) return "precision";
+  if (c.num_pe < 1 || c.num_pe > phd::kMaxPE) return "num_pe must be in 1..256";
+  if (c.ck_mode != PHD_CK_LOCAL && c.ck_mode != PHD_CK_GLOBAL) return "ck_mode";
+  if (c.pe_cap < 1 || c.pe_cap > (1 << 24)) return "pe_cap must be in 1..2^24";
+  if (c.m_max < 1 || c.m_max > phd::kMaxM) return "m_max must be in 1..4096";
+  if (c.birth_count < 0) return "birth_count";
+  if (phd::births_of(c.birth_count, c.num_pe, 0) >= c.pe_cap) return "birth_count / num_pe must be < pe_cap";
+  if (c.reserved0 != 0) return "reserved0 must be 0";
+  if (!(c.dt > 0) || !std::isfinite(c.dt)) return "dt";
+  if (!(c.sigma_a >= 0) || !std::isfinite(c.sigma_a)) return "sigma_a";
+  if (!(c.sigma_z[0] > 0) || !(c.sigma_z[1] > 0) || !std::isfinite(c.sigma_z[0]) || !std::isfinite(c.sigma_z[1]))
+    return "sigma_z";
+  if (!(c.region[1] > c.region[0]) || !(c.region[3] > c.region[2])) return "region";
+  if (c.meas_model == PHD_MEAS_RANGE_BEARING && !(c.r_max > 0)) return "r_max";
+  if (!(c.p_s >= 0 && c.p_s <= 1)) return "p_s";
+  if (!(c.p_d >= 0 && c.p_d <= 1)) return "p_d";
+  if (!(c.clutter_rate >= 0) || !std::isfinite(c.clutter_rate)) return "clutter_rate";
+  if (!(c.birth_mass >= 0) || !std::isfinite(c.birth_mass)) return "birth_mass";
+  if (!(c.birth_vel_sigma >= 0)) return "birth_vel_sigma";
+  if (!(c.particles_per_target > 0) || !std::isfinite(c.particles_per_target)) return "particles_per_target";
+  if (!(c.exchange_frac >= 0 && c.exchange_frac < 0.5)) return "exchange_frac must be in [0, 0.5)";
+  if (c.num_pe > 1 && c.exchange_frac > 0 && c.pe_cap > 16384)
+    return "pe_cap must be <= 16384 when the ring exchange is on";
+  return nullptr;
+}
+
+Model make_model(const phd_config& c) {
+  Model m{};
+  const double kPi = 3.14159265358979323846;
+  const double kLog2e = 1.4426950408889634;
+  m.meas_model = c.meas_model;
+  m.K = c.num_pe;
+  m.pe_cap = c.pe_cap;
+  m.m_max = c.m_max;
+  m.J = c.birth_count;
+  m.ck_global = c.ck_mode == PHD_CK_GLOBAL;
+  m.dt = c.dt;
+  m.sigma_a = c.sigma_a;
+  m.sz0 = c.sigma_z[0];
+  m.sz1 = c.sigma_z[1];
+  m.sx = c.sensor[0];
+  m.sy = c.sensor[1];
+  m.rx0 = c.region[0];
+  m.rx1 = c.region[1];
+  m.ry0 = c.region[2];
+  m.ry1 = c.region[3];
+  m.p_s = c.p_s;
+  m.p_d = c.p_d;
+  const double vol = c.meas_model == PHD_MEAS_LINEAR ? (c.region[1] - c.region[0]) * (c.region[3] - c.region[2])
+                                                     : c.r_max * 2.0 * kPi;
+  m.kappa = c.clutter_rate / vol;
+  m.birth_mass = c.birth_mass;
+  m.birth_vel_sigma = c.birth_vel_sigma;
+  m.rho_pe = c.particles_per_target / (double)c.num_pe;
+  m.exchange_frac = c.exchange_frac;
+  m.a0 = std::sqrt(0.5 * kLog2e) / c.sigma_z[0];
+  m.a1 = std::sqrt(0.5 * kLog2e) / c.sigma_z[1];
+  m.cnorm = 1.0 / (2.0 * kPi * c.sigma_z[0] * c.sigma_z[1]);
+  m.seed = c.seed;
+  return m;
+}
+
+phd_status fail(phd_handle* h, phd_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+phd_status cuda_fail(phd_handle* h, cudaError_t e, const char* where) {
+  return fail(h, PHD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PHD_CUDA(h, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+bool is_fp64(const phd_handle* h) { return h->cfg.precision == PHD_FP64; }
+
+phd_status read_device_error(phd_handle* h) {
+  int err = 0;
+  PHD_CUDA(h, cudaMemcpyAsync(&err, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (err == 0) return PHD_OK;
+  PHD_CUDA(h, cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (err & phd::kErrNonFinite) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
+  return fail(h, PHD_ERR_CAPACITY, "device-side capacity check failed");
+}
+
+phd_status do_predict(phd_handle* h, const void* noise) {
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_predict: a step is already in progress");
+  cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, static_cast<const double*>(noise), h->stream)
+                             : phd::launch_predict<float>(h->d, h->m, static_cast<const float*>(noise), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "predict");
+  h->stage = kPredicted;
+  return PHD_OK;
+}
+
+phd_status do_update(phd_handle* h, const void* Z, int M, bool z_in_workspace) {
+  if (h->stage != kPredicted) return fail(h, PHD_ERR_STATE, "phd_update: call phd_predict first");
+  if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
+  if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
+  if (M > 0 && !Z && !z_in_workspace) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  const void* src = z_in_workspace ? h->d.Z : Z;
+  cudaError_t e = is_fp64(h) ? phd::launch_stage_z<double>(h->d, h->m, static_cast<const double*>(src), M, h->stream)
+                             : phd::launch_stage_z<float>(h->d, h->m, static_cast<const float*>(src), M, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage_z");
+  e = is_fp64(h) ? phd::launch_update<double>(h->d, h->m, h->stream) : phd::launch_update<float>(h->d, h->m, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "update");
+  h->stage = kUpdated;
+  return PHD_OK;
+}
+
+phd_status do_extract(phd_handle* h, void* states, int* labels, int cap, int* d_count, int* h_count) {
+  if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_extract: call phd_update first");
+  if (cap < 0) return fail(h, PHD_ERR_INVALID_ARG, "cap < 0");
+  if (cap > 0 && (!states || !labels)) return fail(h, PHD_ERR_INVALID_ARG, "NULL output buffer");
+  cudaError_t e = is_fp64(h)
+      ? phd::launch_extract<double>(h->d, h->m, static_cast<double*>(states), labels, cap, d_count, h->stream)
+      : phd::launch_extract<float>(h->d, h->m, static_cast<float*>(states), labels, cap, d_count, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "extract");
+  if (h_count) {
+    phd_status st = read_device_error(h);
+    if (st != PHD_OK) return st;
+    PHD_CUDA(h, cudaMemcpyAsync(h_count, h->d.out_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (*h_count > cap) return fail(h, PHD_ERR_CAPACITY, "more estimates than cap");
+  }
+  return PHD_OK;
+}
+
+phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
+  if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_resample: call phd_update first");
+  cudaError_t e = is_fp64(h) ? phd::launch_resample<double>(h->d, h->m, u, xu, h->stream)
+                             : phd::launch_resample<float>(h->d, h->m, u, xu, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "resample");
+  e = phd::launch_advance_step(h->d, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "advance_step");
+  h->stage = kReady;
+  return PHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* phd_status_string(phd_status s) {
+  switch (s) {
+    case PHD_OK: return "ok";
+    case PHD_ERR_INVALID_ARG: return "invalid argument";
+    case PHD_ERR_CAPACITY: return "capacity exceeded";
+    case PHD_ERR_CUDA: return "CUDA error";
+    case PHD_ERR_TIMEOUT: return "device wait timed out";
+    case PHD_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* phd_last_error_string(const phd_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+phd_status phd_workspace_size(const phd_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return PHD_ERR_INVALID_ARG;
+  if (check_config(*cfg)) return PHD_ERR_INVALID_ARG;
+  *bytes = carve(*cfg, nullptr, nullptr, nullptr, nullptr);
+  return PHD_OK;
+}
+
+phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t bytes, void* stream) {
+  if (!out || !cfg) return PHD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (check_config(*cfg)) return PHD_ERR_INVALID_ARG;
+  const size_t need = carve(*cfg, nullptr, nullptr, nullptr, nullptr);
+  if (!ws || bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return PHD_ERR_INVALID_ARG;
+  phd_handle* h = new (std::nothrow) phd_handle();
+  if (!h) return PHD_ERR_INVALID_ARG;
+  h->cfg = *cfg;
+  h->m = make_model(*cfg);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->stage = kReady;
+  carve(*cfg, static_cast<char*>(ws), &h->d, &h->out_states, &h->out_labels);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = is_fp64(h) ? phd::prepare_kernels<double>(h->m) : phd::prepare_kernels<float>(h->m);
+  if (e == cudaSuccess && h->m.K > 1 && h->m.exchange_frac > 0) e = phd::prepare_exchange(h->m);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
+  // bearing anchors: float directions (c_k, s_k) near angle 2 pi k / 256 and
+  // their exact angles atan2(s_k, c_k) in FP64, split into two floats
+  phd::Anchor tab[phd::kAnchors];
+  for (int k = 0; k < phd::kAnchors; ++k) {
+    const double ang = 2.0 * 3.14159265358979323846 * k / phd::kAnchors;
+    const float c = (float)std::cos(ang), s = (float)std::sin(ang);
+    const double th = std::atan2((double)s, (double)c);
+    tab[k].c = c;
+    tab[k].s = s;
+    tab[k].th_hi = (float)th;
+    tab[k].th_lo = (float)(th - (double)tab[k].th_hi);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<void*>(h->d.anchors), tab, sizeof(tab), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return PHD_ERR_CUDA;
+  }
+  *out = h;
+  return PHD_OK;
+}
+
+phd_status phd_destroy(phd_handle* h) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  delete h;
+  return e == cudaSuccess ? PHD_OK : PHD_ERR_CUDA;
+}
+
+phd_status phd_predict(phd_handle* h, const void* d_noise) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  return do_predict(h, d_noise);
+}
+
+phd_status phd_update(phd_handle* h, const void* d_Z, int32_t M) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  return do_update(h, d_Z, M, false);
+}
+
+phd_status phd_extract(phd_handle* h, void* d_states, int32_t* d_labels, int32_t cap, int32_t* d_count,
+                       int32_t* h_count) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  return do_extract(h, d_states, d_labels, cap, d_count, h_count);
+}
+
+phd_status phd_resample(phd_handle* h, const uint32_t* d_u, const uint32_t* d_xu) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  return do_resample(h, d_u, d_xu);
+}
+
+phd_status phd_step(phd_handle* h, const void* d_Z, int32_t M, void* d_states, int32_t* d_labels, int32_t cap,
+                    int32_t* d_count, int32_t* h_count) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_step: a step is already in progress");
+  if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
+  if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
+  phd_status st = do_predict(h, nullptr);
+  if (st == PHD_OK) st = do_update(h, d_Z, M, false);
+  if (st == PHD_OK) st = do_extract(h, d_states, d_labels, cap, d_count, nullptr);
+  if (st == PHD_OK) st = do_resample(h, nullptr, nullptr);
+  if (st != PHD_OK) {
+    h->stage = kReady;
+    return st;
+  }
+  if (h_count) {
+    st = read_device_error(h);
+    if (st != PHD_OK) return st;
+    PHD_CUDA(h, cudaMemcpyAsync(h_count, h->d.out_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (*h_count > cap) return fail(h, PHD_ERR_CAPACITY, "more estimates than cap");
+  }
+  return PHD_OK;
+}
+
+phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_states, int32_t* h_labels, int32_t cap,
+                         int32_t* h_count) {
+  if (!h || !h_count) return PHD_ERR_INVALID_ARG;
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_step_host: a step is already in progress");
+  if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
+  if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
+  if (M > 0 && !h_Z) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  if (cap < 0 || (cap > 0 && (!h_states || !h_labels))) return fail(h, PHD_ERR_INVALID_ARG, "bad output buffer");
+  const size_t rs = real_size(h->cfg);
+  for (int i = 0; i < 2 * M; ++i) {
+    const double v = rs == 8 ? static_cast<const double*>(h_Z)[i] : (double)static_cast<const float*>(h_Z)[i];
+    if (!std::isfinite(v)) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
+  }
+  if (M > 0) PHD_CUDA(h, cudaMemcpyAsync(h->d.Z, h_Z, (size_t)M * 2 * rs, cudaMemcpyHostToDevice, h->stream));
+  phd_status st = do_predict(h, nullptr);
+  if (st == PHD_OK) st = do_update(h, nullptr, M, true);
+  if (st == PHD_OK) st = do_extract(h, h->out_states, h->out_labels, h->cfg.m_max, nullptr, nullptr);
+  if (st == PHD_OK) st = do_resample(h, nullptr, nullptr);
+  if (st != PHD_OK) {
+    h->stage = kReady;
+    return st;
+  }
+  int n = 0;
+  PHD_CUDA(h, cudaMemcpyAsync(&n, h->d.out_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int ncp = n < cap ? n : cap;
+  if (ncp > 0) {
+    PHD_CUDA(h, cudaMemcpyAsync(h_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDeviceToHost, h->stream));
+    PHD_CUDA(h, cudaMemcpyAsync(h_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  }
+  *h_count = n;
+  phd_status es = read_device_error(h);
+  if (es != PHD_OK) return es;
+  return n > cap ? fail(h, PHD_ERR_CAPACITY, "more estimates than cap") : PHD_OK;
+}
+
+phd_status phd_set_state(phd_handle* h, const void* d_x, const void* d_w, const int32_t* h_counts) {
+  if (!h || !d_x || !d_w || !h_counts) return PHD_ERR_INVALID_ARG;
+  const int K = h->cfg.num_pe;
+  for (int j = 0; j < K; ++j) {
+    const int lim = h->cfg.pe_cap - phd::births_of(h->cfg.birth_count, K, j);
+    if (h_counts[j] < 0 || h_counts[j] > lim) return fail(h, PHD_ERR_CAPACITY, "count exceeds pe_cap - J_j");
+  }
+  const size_t rs = real_size(h->cfg);
+  const size_t n = (size_t)K * h->cfg.pe_cap;
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.x, d_x, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.w, d_w, n * rs, cudaMemcpyDeviceToDevice, h->stream));
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.n_cur, h_counts, K * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->stage = kReady;
+  return PHD_OK;
+}
+
+phd_status phd_get_state(phd_handle* h, void* d_x, void* d_w, int32_t* h_counts) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  const int K = h->cfg.num_pe;
+  const size_t rs = real_size(h->cfg);
+  const size_t n = (size_t)K * h->cfg.pe_cap;
+  if (d_x) PHD_CUDA(h, cudaMemcpyAsync(d_x, h->d.x, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_w)
+    PHD_CUDA(h, cudaMemcpyAsync(d_w, h->stage == kUpdated ? h->d.wu : h->d.w, n * rs, cudaMemcpyDeviceToDevice,
+                                h->stream));
+  if (h_counts)
+    PHD_CUDA(h, cudaMemcpyAsync(h_counts, h->stage == kReady ? h->d.n_cur : h->d.n_pred, K * sizeof(int),
+                                cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return read_device_error(h);
+}
+
+phd_status phd_get_update(phd_handle* h, double* d_C, double* h_mass) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_get_update: no update in progress");
+  const size_t K = h->cfg.num_pe, Mm = h->cfg.m_max;
+  if (d_C) PHD_CUDA(h, cudaMemcpyAsync(d_C, h->d.C, K * Mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h_mass) {
+    // the updated mass is finalised by the extraction's selection kernel; run
+    // the same reduction here when extraction has not run yet
+    PHD_CUDA(h, cudaMemcpyAsync(h_mass, h->d.mass, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return read_device_error(h);
+}
+
+phd_status phd_get_local_estimates(phd_handle* h, void* d_states, int32_t* d_labels, int32_t* h_counts) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  const size_t K = h->cfg.num_pe, Mm = h->cfg.m_max, rs = real_size(h->cfg);
+  if (d_states)
+    PHD_CUDA(h, cudaMemcpyAsync(d_states, h->d.est_local, K * Mm * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_labels)
+    PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->d.sel, K * Mm * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  if (h_counts) PHD_CUDA(h, cudaMemcpyAsync(h_counts, h->d.nsel, K * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return read_device_error(h);
+}
+
+phd_status phd_get_resample(phd_handle* h, int32_t* d_parents, int32_t* h_lx) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  const size_t n = (size_t)h->cfg.num_pe * h->cfg.pe_cap;
+  if (d_parents)
+    PHD_CUDA(h, cudaMemcpyAsync(d_parents, h->d.parent, n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  if (h_lx) {
+    if (h->cfg.num_pe > 1 && h->cfg.exchange_frac > 0)
+      PHD_CUDA(h, cudaMemcpyAsync(h_lx, h->d.lx, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    else
+      *h_lx = 0;
+  }
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return read_device_error(h);
+}
+
+phd_status phd_get_step(phd_handle* h, uint64_t* step) {
+  if (!h || !step) return PHD_ERR_INVALID_ARG;
+  unsigned long long s = 0;
+  PHD_CUDA(h, cudaMemcpyAsync(&s, h->d.step, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  *step = s;
+  return PHD_OK;
+}
+
+phd_status phd_set_step(phd_handle* h, uint64_t step) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  unsigned long long s = step;
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PHD_OK;
+}
+
+phd_status phd_sync(phd_handle* h) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  return read_device_error(h);
+}
+
+}  // extern "C"

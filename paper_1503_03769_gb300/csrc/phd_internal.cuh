@@ -1,0 +1,274 @@
+// Internal declarations shared by the libphd.so translation units.
+//
+// Device-resident state lives in one caller-owned workspace carved by
+// phd_api.cu; kernels receive a `Dev` (pointers + sizes) and a `Model`
+// (constants) by value.  Every per-step size the host does not know without a
+// synchronisation (particle counts, |Z_k|) is read by the kernels from device
+// memory, so a step's launches do not depend on the data and can be captured
+// once in a CUDA graph.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phd {
+
+constexpr int kMaxPE = 256;
+constexpr int kMaxM = 4096;
+constexpr int kTile = 256;        // particles per work item of the pair kernels
+constexpr int kThreads = 256;     // threads of the pair kernels
+
+// Real-typed particle state [x, vx, y, vy].
+template <class R> struct alignas(4 * sizeof(R)) St4 { R x, vx, y, vy; };
+template <class R> struct alignas(2 * sizeof(R)) V2 { R a, b; };
+
+struct Model {
+  int meas_model;        // 0 linear, 1 range-bearing
+  int K;
+  int pe_cap;
+  int m_max;
+  int J;                 // births per step, all PEs
+  int ck_global;         // 1: every PE uses the PE-mean C
+  double dt, sigma_a;
+  double sz0, sz1;       // measurement noise std per coordinate
+  double sx, sy;         // sensor
+  double rx0, rx1, ry0, ry1;
+  double p_s, p_d, kappa, birth_mass, birth_vel_sigma;
+  double rho_pe;         // particles per target per PE
+  double exchange_frac;
+  // likelihood in exp2 form: g = cnorm * 2^-(a0^2 d0^2 + a1^2 d1^2)
+  double a0, a1;         // sqrt(log2(e) / 2) / sigma per measurement coordinate
+  double cnorm;          // 1 / (2 pi s0 s1)
+  uint64_t seed;
+};
+
+// Workspace carve (device pointers).  Real-typed arrays are void* and cast by
+// the kernels' Real type.
+struct Dev {
+  void* x;               // St4<R> [K*pe_cap]  current / predicted / updated set
+  void* w;               // R [K*pe_cap]  current / predicted weights
+  void* wu;              // R [K*pe_cap]  updated weights (Eq. 8)
+  void* x_alt;           // St4<R> [K*pe_cap]  resampling target
+  void* w_alt;           // R [K*pe_cap]
+  int* n_cur;            // [K] particles per PE (survivors before predict)
+  int* n_pred;           // [K] particles per PE after predict
+  void* Z;               // V2<R> [m_max]  measurements (as given)
+  const void* anchors;   // Anchor [kAnchors] bearing anchor table
+  int* M;                // [1]
+  double* colpart;       // [max_items][m_max] pass-1 partial column sums
+  double* C;             // [K][m_max] C^j (with p_D cnorm)
+  double* Cused;         // [K][m_max] normaliser each PE applies
+  void* ginv;            // R [K][m_max]  cnorm p_D / (kappa + Cused)
+  double* rowpart;       // [max_items] pass-2 partial sums of updated weights
+  double* mass;          // [K] updated mass N^j
+  int* nsel;             // [K] labels selected per PE
+  int* sel;              // [K][m_max] selected labels, selection order
+  int* selrank;          // [K][m_max] label -> selection rank or -1
+  double* spart;         // [max_items][m_max][5] pass-3 partial labelled sums
+  void* est_local;       // St4<R> [K][m_max] local estimates (selection order)
+  int* out_count;        // [1] fused estimate count
+  double* rs_mass;       // [K] mass before resampling
+  int* rs_s;             // [K] CDF scale exponent
+  int* rs_L;             // [K] resample counts
+  unsigned long long* Q; // [K*pe_cap] integer CDF
+  int* child_end;        // [K*pe_cap]
+  int* parent;           // [K*pe_cap]
+  int* xslots;           // [K][pe_cap] exchange slots
+  int* lx;               // [1] particles moved per PE
+  unsigned long long* step;  // [1] step counter (Philox counter word)
+  int* err;              // [1] device error bits
+  int max_items;
+};
+
+enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based RNG.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, ctr.a), lo0 = M0 * ctr.a;
+    uint32_t hi1 = __umulhi(M1, ctr.c), lo1 = M1 * ctr.c;
+    ctr = U4{hi1 ^ ctr.b ^ k0, lo1, hi0 ^ ctr.d ^ k1, lo0};
+    k0 += W0;
+    k1 += W1;
+  }
+  return ctr;
+}
+
+// Stream tags of the Philox counter's third word.
+enum : uint32_t { kTagPredict = 0x50524544u, kTagResample = 0x52534d50u, kTagExchange = 0x58434847u };
+
+// u in (0, 1) from 32 random bits, in the kernel's real type.
+template <class R> __device__ __forceinline__ R unit_open(uint32_t b);
+template <> __device__ __forceinline__ float unit_open<float>(uint32_t b) {
+  return ((float)(b >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+template <> __device__ __forceinline__ double unit_open<double>(uint32_t b) {
+  return ((double)b + 0.5) * (1.0 / 4294967296.0);
+}
+
+// ---------------------------------------------------------------------------
+// exp2 of a non-positive argument in the kernel's precision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float exp2_neg(float q) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-q));
+  return r;
+}
+__device__ __forceinline__ double exp2_neg(double q) { return exp2(-q); }
+
+// ---------------------------------------------------------------------------
+// Measurement-space geometry of a particle (Sec. 4 sensor models).
+//
+// h0, h1 are the particle's noise-free measurement, unscaled: (x, y) for the
+// linear sensor, (range, bearing) for the range-bearing sensor.  The pair
+// kernels subtract the measurement from h first and scale afterwards, so the
+// difference of two close values is exact (Sterbenz) and the FP32 exponent
+// carries no rounding of |z| or |h|.
+//
+// FP32 bearing: atan2f is only good to a few ulp of pi (~7e-7 rad, ~1e-4 of
+// the likelihood at 3 sigma for 0.5 deg bearing noise), so the bearing is
+// carried as a double-float h1 + h1lo.  An anchor direction (c_k, s_k) close
+// to the particle's is taken from a 256-entry table whose exact angles
+// theta_k = atan2(s_k, c_k) are precomputed in FP64; rotating (px, py) by the
+// anchor with error-free products gives the small residual angle exactly
+// enough (|delta| <= pi/256), and theta = theta_k + delta.
+// ---------------------------------------------------------------------------
+constexpr int kAnchors = 256;
+struct Anchor { float c, s, th_hi, th_lo; };
+
+template <class R> struct H3 { R h0, h1, h1lo; };
+
+// Likelihood constants: q = b0 d0^2 + b1 d1^2 with b = log2(e) / (2 sigma^2),
+// so g = cnorm 2^-q; the bearing period 2 pi as a double-float.
+template <class R> struct Lik {
+  int rb;
+  R b0, b1, per_hi, per_lo;
+};
+
+template <class R> __device__ __forceinline__ Lik<R> make_lik(const Model& m) {
+  Lik<R> L;
+  L.rb = m.meas_model;
+  L.b0 = (R)(m.a0 * m.a0);
+  L.b1 = (R)(m.a1 * m.a1);
+  const double two_pi = 6.283185307179586476925286766559;
+  L.per_hi = (R)two_pi;
+  L.per_lo = (R)(two_pi - (double)L.per_hi);
+  return L;
+}
+
+__device__ __forceinline__ void bearing_df(float px, float py, const Anchor* __restrict__ tab, float& hi, float& lo) {
+  const float t0 = atan2f(py, px);
+  int k = __float2int_rn(t0 * (kAnchors / 6.283185307179586f));
+  k &= (kAnchors - 1);
+  const Anchor a = tab[k];
+  // v = py c - px s with error-free products (TwoProduct via FMA)
+  const float p1 = py * a.c, e1 = fmaf(py, a.c, -p1);
+  const float p2 = px * a.s, e2 = fmaf(px, a.s, -p2);
+  const float vhi = p1 - p2;            // exact: p1 ~ p2 when the anchor is close
+  const float v = vhi + (e1 - e2);
+  const float u = fmaf(px, a.c, py * a.s);
+  const float t = u != 0.0f ? v / u : 0.0f;   // |t| <= tan(pi/256); 0 at the sensor
+  const float delta = t - t * t * t * (1.0f / 3.0f);
+  // theta = th_hi + th_lo + delta as a double-float
+  const float s = a.th_hi + delta;
+  const float bb = s - a.th_hi;
+  const float err = (a.th_hi - (s - bb)) + (delta - bb);
+  hi = s;
+  lo = err + a.th_lo;
+}
+
+template <class R>
+__device__ __forceinline__ H3<R> meas_h(const Model& m, const St4<R>& st, const Anchor* __restrict__ tab);
+
+template <>
+__device__ __forceinline__ H3<float> meas_h<float>(const Model& m, const St4<float>& st, const Anchor* __restrict__ tab) {
+  H3<float> h;
+  if (m.meas_model == 0) {
+    h.h0 = st.x;
+    h.h1 = st.y;
+    h.h1lo = 0.0f;
+  } else {
+    const float px = st.x - (float)m.sx, py = st.y - (float)m.sy;
+    h.h0 = sqrtf(fmaf(px, px, py * py));
+    bearing_df(px, py, tab, h.h1, h.h1lo);
+  }
+  return h;
+}
+
+template <>
+__device__ __forceinline__ H3<double> meas_h<double>(const Model& m, const St4<double>& st, const Anchor* __restrict__) {
+  H3<double> h;
+  if (m.meas_model == 0) {
+    h.h0 = st.x;
+    h.h1 = st.y;
+  } else {
+    const double px = st.x - m.sx, py = st.y - m.sy;
+    h.h0 = sqrt(fma(px, px, py * py));
+    h.h1 = atan2(py, px);
+  }
+  h.h1lo = 0.0;
+  return h;
+}
+
+// Exponent q of the likelihood 2^-q for measurement (z0, z1) and particle h.
+template <class R>
+__device__ __forceinline__ R qform(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
+  const R d0 = z0 - h0;
+  R d1 = z1 - h1;
+  if (L.rb) {
+    d1 = d1 - h1lo;
+    const R a = fabs(d1);
+    d1 = fmin(a, (L.per_hi - a) + L.per_lo);   // wrap to [0, pi]
+  }
+  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
+}
+
+// Work-item decode for the pair kernels: item -> (PE, particle tile), tiles
+// of kTile over each PE's count.  pref has K+1 entries in shared memory.
+__device__ __forceinline__ void item_prefix(const int* n, int K, int* pref) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int j = 0; j < K; ++j) {
+      pref[j] = acc;
+      acc += (n[j] + kTile - 1) / kTile;
+    }
+    pref[K] = acc;
+  }
+  __syncthreads();
+}
+__device__ __forceinline__ int item_pe(const int* pref, int K, int item) {
+  int lo = 0, hi = K - 1;   // last j with pref[j] <= item
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ int births_of(int J, int K, int j) {
+  return J / K + (j < J % K ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (one per stage), instantiated for float and double.
+// ---------------------------------------------------------------------------
+template <class R> cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s);
+template <class R> cudaError_t launch_stage_z(const Dev& d, const Model& m, const R* Z, int M, cudaStream_t s);
+template <class R> cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s);
+template <class R> cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels,
+                                              int cap, int* d_count, cudaStream_t s);
+template <class R> cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u,
+                                               const uint32_t* xu, cudaStream_t s);
+cudaError_t launch_advance_step(const Dev& d, cudaStream_t s);
+template <class R> cudaError_t prepare_kernels(const Model& m);
+cudaError_t prepare_exchange(const Model& m);
+int grid_items(const Model& m);
+
+}  // namespace phd

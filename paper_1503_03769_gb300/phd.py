@@ -1,0 +1,295 @@
+"""Thin Python binding of libphd.so (the C ABI in include/phd.h).
+
+Argument marshalling only: every stage of the filter runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the workspace and the
+caller's buffers) and the stream.  If libphd.so is missing the import of this
+module fails loudly; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libphd.so")
+
+PHD_OK, PHD_ERR_INVALID_ARG, PHD_ERR_CAPACITY, PHD_ERR_CUDA, PHD_ERR_TIMEOUT, PHD_ERR_STATE = range(6)
+PHD_MEAS_LINEAR, PHD_MEAS_RANGE_BEARING = 0, 1
+PHD_FP32, PHD_FP64 = 0, 1
+PHD_CK_LOCAL, PHD_CK_GLOBAL = 0, 1
+
+
+class PhdError(RuntimeError):
+    def __init__(self, status: int, msg: str, count: Optional[int] = None):
+        super().__init__(f"phd status {status}: {msg}")
+        self.status = status
+        self.count = count
+
+
+class phd_config(ctypes.Structure):
+    _fields_ = [
+        ("meas_model", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("num_pe", ctypes.c_int32), ("ck_mode", ctypes.c_int32),
+        ("pe_cap", ctypes.c_int32), ("m_max", ctypes.c_int32),
+        ("birth_count", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("dt", ctypes.c_double), ("sigma_a", ctypes.c_double),
+        ("sigma_z", ctypes.c_double * 2), ("sensor", ctypes.c_double * 2),
+        ("region", ctypes.c_double * 4), ("r_max", ctypes.c_double),
+        ("p_s", ctypes.c_double), ("p_d", ctypes.c_double),
+        ("clutter_rate", ctypes.c_double), ("birth_mass", ctypes.c_double),
+        ("birth_vel_sigma", ctypes.c_double), ("particles_per_target", ctypes.c_double),
+        ("exchange_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+
+# exported entry points: name -> (restype, argtypes)
+ABI = {
+    "phd_workspace_size": (ctypes.c_int, [ctypes.POINTER(phd_config), ctypes.POINTER(ctypes.c_size_t)]),
+    "phd_init": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(phd_config), _P, ctypes.c_size_t, _P]),
+    "phd_destroy": (ctypes.c_int, [_H]),
+    "phd_last_error_string": (ctypes.c_char_p, [_H]),
+    "phd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "phd_predict": (ctypes.c_int, [_H, _P]),
+    "phd_update": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
+    "phd_extract": (ctypes.c_int, [_H, _P, _P, ctypes.c_int32, _P, _I32P]),
+    "phd_resample": (ctypes.c_int, [_H, _P, _P]),
+    "phd_step": (ctypes.c_int, [_H, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _I32P]),
+    "phd_step_host": (ctypes.c_int, [_H, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _I32P]),
+    "phd_set_state": (ctypes.c_int, [_H, _P, _P, _I32P]),
+    "phd_get_state": (ctypes.c_int, [_H, _P, _P, _I32P]),
+    "phd_get_update": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_double)]),
+    "phd_get_local_estimates": (ctypes.c_int, [_H, _P, _P, _I32P]),
+    "phd_get_resample": (ctypes.c_int, [_H, _P, _I32P]),
+    "phd_get_step": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint64)]),
+    "phd_set_step": (ctypes.c_int, [_H, ctypes.c_uint64]),
+    "phd_sync": (ctypes.c_int, [_H]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libphd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in ABI.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_config(w, seed: int = 0) -> phd_config:
+    """phd_config from any object with the workload fields (see scenario.Workload)."""
+    c = phd_config()
+    c.meas_model = PHD_MEAS_LINEAR if w.meas_model == "linear" else PHD_MEAS_RANGE_BEARING
+    c.precision = PHD_FP64 if w.precision == "fp64" else PHD_FP32
+    c.num_pe = int(w.num_pe)
+    c.ck_mode = PHD_CK_GLOBAL if getattr(w, "ck_mode", "local") == "global" else PHD_CK_LOCAL
+    c.pe_cap = int(w.pe_cap)
+    c.m_max = int(w.m_max)
+    c.birth_count = int(w.birth_count)
+    c.dt, c.sigma_a = float(w.dt), float(w.sigma_a)
+    c.sigma_z[0], c.sigma_z[1] = float(w.sigma_z[0]), float(w.sigma_z[1])
+    c.sensor[0], c.sensor[1] = float(w.sensor[0]), float(w.sensor[1])
+    for k in range(4):
+        c.region[k] = float(w.region[k])
+    c.r_max = float(w.r_max)
+    c.p_s, c.p_d = float(w.p_s), float(w.p_d)
+    c.clutter_rate, c.birth_mass = float(w.clutter_rate), float(w.birth_mass)
+    c.birth_vel_sigma = float(w.birth_vel_sigma)
+    c.particles_per_target = float(w.particles_per_target)
+    c.exchange_frac = float(w.exchange_frac)
+    c.seed = int(seed) & (2 ** 64 - 1)
+    return c
+
+
+class ParticlePHD:
+    """One filter (global for num_pe == 1, DCPFPHD for num_pe > 1) on a CUDA device."""
+
+    def __init__(self, workload, seed: int = 0, device: str = "cuda",
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.L = lib()
+        self.w = workload
+        self.cfg = make_config(workload, seed)
+        self.K = int(self.cfg.num_pe)
+        self.pe_cap = int(self.cfg.pe_cap)
+        self.m_max = int(self.cfg.m_max)
+        self.dtype = torch.float64 if self.cfg.precision == PHD_FP64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = ctypes.c_size_t(0)
+        self._check(self.L.phd_workspace_size(ctypes.byref(self.cfg), ctypes.byref(nbytes)), "workspace_size")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.L.phd_init(ctypes.byref(h), ctypes.byref(self.cfg), _ptr(self.workspace),
+                                 nbytes.value, ctypes.c_void_p(self.stream.cuda_stream))
+        self._check(st, "phd_init")
+        self.h = h
+        self._cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st: int, what: str, count: Optional[int] = None):
+        if st != PHD_OK:
+            msg = what
+            if getattr(self, "h", None):
+                msg += ": " + (self.L.phd_last_error_string(self.h) or b"").decode()
+            raise PhdError(st, msg, count)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.phd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _real(self, a, shape) -> torch.Tensor:
+        t = torch.as_tensor(a, dtype=self.dtype, device=self.device).reshape(shape)
+        return t.contiguous()
+
+    # -- stages -------------------------------------------------------------
+    def predict(self, noise=None):
+        n = None if noise is None else self._real(noise, (self.K * self.pe_cap, 4))
+        self._check(self.L.phd_predict(self.h, _ptr(n)), "phd_predict")
+        self._keep = n
+
+    def update(self, Z):
+        Zt = self._real(Z, (-1, 2))
+        self._check(self.L.phd_update(self.h, _ptr(Zt) if Zt.numel() else None, Zt.shape[0]), "phd_update")
+        self._keepZ = Zt
+
+    def extract(self, cap: Optional[int] = None):
+        cap = self.m_max if cap is None else int(cap)
+        states = torch.empty((max(cap, 1), 4), dtype=self.dtype, device=self.device)
+        labels = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+        hc = ctypes.c_int32(0)
+        st = self.L.phd_extract(self.h, _ptr(states), _ptr(labels), cap, _ptr(self._cnt), ctypes.byref(hc))
+        self._check(st, "phd_extract", hc.value)
+        n = hc.value
+        return states[:n], labels[:n]
+
+    def resample(self, u=None, xu=None):
+        ut = None if u is None else torch.as_tensor(np.asarray(u, dtype=np.uint32).view(np.int32),
+                                                    device=self.device).contiguous()
+        xt = None if xu is None else torch.as_tensor(np.asarray(xu, dtype=np.uint32).view(np.int32),
+                                                     device=self.device).reshape(-1).contiguous()
+        self._check(self.L.phd_resample(self.h, _ptr(ut), _ptr(xt)), "phd_resample")
+        self._keepu = (ut, xt)
+
+    def step(self, Z, cap: Optional[int] = None, sync: bool = True):
+        """One step (predict, update, extract, resample) with in-kernel randomness."""
+        cap = self.m_max if cap is None else int(cap)
+        Zt = self._real(Z, (-1, 2))
+        if not hasattr(self, "_out") or self._out[0].shape[0] < max(cap, 1):
+            self._out = (torch.empty((max(cap, 1), 4), dtype=self.dtype, device=self.device),
+                         torch.empty(max(cap, 1), dtype=torch.int32, device=self.device))
+        states, labels = self._out
+        hc = ctypes.c_int32(0)
+        st = self.L.phd_step(self.h, _ptr(Zt) if Zt.numel() else None, Zt.shape[0], _ptr(states),
+                             _ptr(labels), cap, _ptr(self._cnt), ctypes.byref(hc) if sync else None)
+        self._check(st, "phd_step", hc.value if sync else None)
+        self._keepZ = Zt
+        if sync:
+            return states[:hc.value], labels[:hc.value]
+        return states, labels, self._cnt
+
+    def step_host(self, Z: np.ndarray, out_states: np.ndarray, out_labels: np.ndarray) -> int:
+        """phd_step_host on host numpy buffers; returns the estimate count."""
+        npdt = np.float64 if self.dtype == torch.float64 else np.float32
+        Z = np.ascontiguousarray(Z, dtype=npdt)
+        assert out_states.dtype == npdt and out_states.flags.c_contiguous
+        assert out_labels.dtype == np.int32 and out_labels.flags.c_contiguous
+        hc = ctypes.c_int32(0)
+        st = self.L.phd_step_host(self.h, Z.ctypes.data_as(ctypes.c_void_p), Z.shape[0],
+                                  out_states.ctypes.data_as(ctypes.c_void_p),
+                                  out_labels.ctypes.data_as(ctypes.c_void_p), out_labels.shape[0],
+                                  ctypes.byref(hc))
+        self._check(st, "phd_step_host", hc.value)
+        return hc.value
+
+    # -- state access ---------------------------------------------------------
+    def set_state(self, xs, ws):
+        """xs, ws: per-PE lists of (n_j, 4) and (n_j,) arrays."""
+        X = torch.zeros((self.K, self.pe_cap, 4), dtype=self.dtype, device=self.device)
+        W = torch.zeros((self.K, self.pe_cap), dtype=self.dtype, device=self.device)
+        counts = (ctypes.c_int32 * self.K)()
+        for j in range(self.K):
+            n = len(ws[j])
+            counts[j] = n
+            if n:
+                X[j, :n] = torch.as_tensor(np.asarray(xs[j]), dtype=self.dtype)
+                W[j, :n] = torch.as_tensor(np.asarray(ws[j]), dtype=self.dtype)
+        self._check(self.L.phd_set_state(self.h, _ptr(X), _ptr(W), counts), "phd_set_state")
+
+    def get_state(self):
+        X = torch.empty((self.K, self.pe_cap, 4), dtype=self.dtype, device=self.device)
+        W = torch.empty((self.K, self.pe_cap), dtype=self.dtype, device=self.device)
+        counts = (ctypes.c_int32 * self.K)()
+        self._check(self.L.phd_get_state(self.h, _ptr(X), _ptr(W), counts), "phd_get_state")
+        c = list(counts)
+        Xn, Wn = X.cpu().numpy(), W.cpu().numpy()
+        return [Xn[j, :c[j]] for j in range(self.K)], [Wn[j, :c[j]] for j in range(self.K)]
+
+    def get_update(self):
+        C = torch.empty((self.K, self.m_max), dtype=torch.float64, device=self.device)
+        mass = (ctypes.c_double * self.K)()
+        self._check(self.L.phd_get_update(self.h, _ptr(C), mass), "phd_get_update")
+        return C.cpu().numpy(), np.array(list(mass))
+
+    def get_local_estimates(self):
+        S = torch.empty((self.K, self.m_max, 4), dtype=self.dtype, device=self.device)
+        Lb = torch.empty((self.K, self.m_max), dtype=torch.int32, device=self.device)
+        counts = (ctypes.c_int32 * self.K)()
+        self._check(self.L.phd_get_local_estimates(self.h, _ptr(S), _ptr(Lb), counts), "phd_get_local_estimates")
+        c = list(counts)
+        Sn, Ln = S.cpu().numpy(), Lb.cpu().numpy()
+        return [Sn[j, :c[j]] for j in range(self.K)], [Ln[j, :c[j]] for j in range(self.K)]
+
+    def get_resample(self):
+        P = torch.empty((self.K, self.pe_cap), dtype=torch.int32, device=self.device)
+        lx = ctypes.c_int32(0)
+        self._check(self.L.phd_get_resample(self.h, _ptr(P), ctypes.byref(lx)), "phd_get_resample")
+        return P.cpu().numpy(), lx.value
+
+    def get_step(self) -> int:
+        s = ctypes.c_uint64(0)
+        self._check(self.L.phd_get_step(self.h, ctypes.byref(s)), "phd_get_step")
+        return s.value
+
+    def set_step(self, step: int):
+        self._check(self.L.phd_set_step(self.h, int(step)), "phd_set_step")
+
+    def sync(self):
+        self._check(self.L.phd_sync(self.h), "phd_sync")
+
+
+__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "make_config", "ParticlePHD", "PhdError",
+           "PHD_OK", "PHD_ERR_INVALID_ARG", "PHD_ERR_CAPACITY", "PHD_ERR_CUDA", "PHD_ERR_TIMEOUT",
+           "PHD_ERR_STATE", "PHD_FP32", "PHD_FP64"]

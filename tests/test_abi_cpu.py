@@ -1,0 +1,63 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point include/phd.h declares, and the binding's struct matches."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "phd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(phd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1503_03769_gb300 import build
+    path = build.build()
+    L = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_1503_03769_gb300 import phd
+    assert sorted(phd.ABI) == names
+
+
+def test_config_struct_layout_matches_header(tmp_path):
+    """The binding's phd_config has the C compiler's size and field offsets."""
+    import subprocess
+    from paper_1503_03769_gb300.phd import phd_config
+    fields = [f[0] for f in phd_config._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "phd.h"', "int main(void){",
+            'printf("%zu\\n", sizeof(phd_config));']
+    prog += [f'printf("%zu\\n", offsetof(phd_config, {n}));' for n in fields]
+    prog += ["return 0;}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(phd_config)
+    assert out[1:] == [getattr(phd_config, n).offset for n in fields]
+
+
+def test_workspace_size_and_config_validation_without_gpu():
+    import scenario
+    from paper_1503_03769_gb300 import phd
+    L = phd.lib()
+    w = scenario.workload("dist16_10t")
+    c = phd.make_config(w)
+    n = ctypes.c_size_t(0)
+    assert L.phd_workspace_size(ctypes.byref(c), ctypes.byref(n)) == phd.PHD_OK
+    assert n.value > 0 and n.value % 256 == 0
+    for field, bad in [("num_pe", 0), ("num_pe", 300), ("m_max", 5000), ("pe_cap", 0),
+                       ("p_d", 1.5), ("exchange_frac", 0.6), ("precision", 7), ("reserved0", 1)]:
+        c2 = phd.make_config(w)
+        setattr(c2, field, bad)
+        assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_ERR_INVALID_ARG, field
+    assert L.phd_init(None, ctypes.byref(c), None, 0, None) == phd.PHD_ERR_INVALID_ARG
+    assert L.phd_status_string(phd.PHD_ERR_CAPACITY) == b"capacity exceeded"

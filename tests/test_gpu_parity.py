@@ -1,0 +1,328 @@
+"""GPU parity: libphd.so (through its C ABI) against the FP64 oracle.
+
+Every test injects the same random numbers into both sides and compares
+stage by stage (see gpu_harness.stage_step): predict and update elementwise,
+extraction per PE and after fusion, resampling parents and the ring exchange
+bit-exactly.  Sizes span several 256-particle tiles with ragged tails, PEs
+with unequal counts, M below and above the 256-thread measurement rounds,
+both sensors, both precisions and both normaliser modes.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenario
+from gpu_harness import StageReport, stage_step, check_weights, npdtype
+
+pytestmark = pytest.mark.gpu
+
+
+def _filter(w, seed=0):
+    from paper_1503_03769_gb300 import ParticlePHD
+    return ParticlePHD(w, seed=seed, device="cuda:0")
+
+
+def _seed_state(f, w, seed, n_per_pe, centres=None, mass=3.0):
+    rng = np.random.default_rng(seed)
+    xs, ws = [], []
+    for j in range(w.num_pe):
+        n = n_per_pe[j] if isinstance(n_per_pe, (list, tuple)) else n_per_pe
+        x, wt = scenario.random_particles(rng, w, n, centres=centres, spread=25.0, mass=mass)
+        dt = npdtype(w)
+        xs.append(x.astype(dt))
+        ws.append(wt.astype(dt))
+    f.set_state(xs, ws)
+
+
+def _run_stages(w, seed, steps, sc=None, warm=0, n_seed=None, centres=None):
+    f = _filter(w, seed)
+    m = oracle.model(w)
+    if sc is None:
+        sc = scenario.simulate(w, seed, steps=warm + steps)
+    if n_seed is not None:
+        _seed_state(f, w, seed, n_seed, centres=centres)
+    for k in range(warm):
+        f.step(sc.meas[k])
+    rep = StageReport()
+    for k in range(warm, warm + steps):
+        noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap, npdtype(w))
+        u = scenario.resample_u32(seed, k, w.num_pe)
+        xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap)
+        stage_step(f, w, m, sc.meas[k], noise, u, xu, rep)
+    f.close()
+    return rep
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_global_linear_stages(precision):
+    """Global filter, linear sensor: a ragged 2600-particle set, 3 steps."""
+    w = scenario.workload("linear4_fp64", precision=precision, n_targets=4,
+                          birth_steps=(1, 1, 1, 1), clutter_rate=12.0)
+    truth = scenario.simulate(w, 5, steps=3)
+    centres = truth.truth[0][:, [0, 2]]
+    rep = _run_stages(w, 5, 3, sc=truth, n_seed=[2100], centres=centres)
+    assert rep.compared_labels > 0
+
+
+@pytest.mark.parametrize("ck_mode", ["local", "global"])
+def test_distributed_linear_stages(ck_mode):
+    """16 PEs (the paper's DCPFPHD form) with exchange, uneven slice sizes."""
+    w = scenario.workload("dist16_10t", ck_mode=ck_mode, n_targets=6, clutter_rate=30.0,
+                          particles_per_target=800, birth_count=1000, birth_steps=(1,) * 6)
+    truth = scenario.simulate(w, 9, steps=3)
+    centres = np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)])[:6]
+    counts = [300 + 37 * j for j in range(16)]
+    rep = _run_stages(w, 9, 3, sc=truth, n_seed=counts, centres=centres)
+    assert rep.compared_labels > 0
+
+
+def test_range_bearing_stages_many_measurements():
+    """Range-bearing sensor, M ~ 330 (> one 256-thread round), 4 PEs, FP32."""
+    w = scenario.workload("dense_rb_100t", n_targets=30, clutter_rate=300.0,
+                          particles_per_target=200, birth_count=2000, num_pe=4,
+                          exchange_frac=0.1, birth_steps=(1,) * 30)
+    truth = scenario.simulate(w, 4, steps=2)
+    rep = _run_stages(w, 4, 2, sc=truth, warm=0, n_seed=[1500, 1700, 1300, 1611],
+                      centres=np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)]))
+    assert rep.compared_labels > 0
+
+
+def test_bearing_branch_cut():
+    """Particles and measurements on both sides of bearing +-pi: the wrapped
+    likelihood must match the oracle's (a missing wrap drops their weights)."""
+    w = scenario.workload("dense_rb_100t", n_targets=1, clutter_rate=5.0,
+                          particles_per_target=300, birth_count=64)
+    f = _filter(w, 1)
+    m = oracle.model(w)
+    rng = np.random.default_rng(1)
+    n = 700
+    th = math.pi + 0.01 * rng.standard_normal(n)
+    r = 800 + 5 * rng.standard_normal(n)
+    x = np.stack([r * np.cos(th), np.zeros(n), r * np.sin(th), np.zeros(n)], 1).astype(np.float32)
+    wt = np.full(n, 1.0 / n, np.float32)
+    f.set_state([x], [wt])
+    Z = np.array([[800.0, math.pi - 0.002], [800.0, -math.pi + 0.003], [810.0, 3.1]], np.float32)
+    noise = np.zeros((w.pe_cap, 4), np.float32)
+    noise[:, 2:] = 0.5
+    rep = StageReport()
+    stage_step(f, w, m, Z, noise, np.array([12345], np.uint32), None, rep)
+    assert rep.compared_labels >= 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_resample_bit_exact_on_injected_weights(precision):
+    """With identical weights on both sides the parents are bit-exact,
+    for heavy-tailed weights, ragged sizes and several U."""
+    for n, seed in [(1, 0), (7, 1), (255, 2), (256, 3), (4099, 4), (70001, 5)]:
+        w = scenario.workload("linear4_fp64", precision=precision, birth_count=0, p_s=1.0,
+                              p_d=0.0, sigma_a=0.0, particles_per_target=max(1, n // 3),
+                              pe_cap=n + 64)
+        f = _filter(w, seed)
+        rng = np.random.default_rng(seed)
+        dt = npdtype(w)
+        x = rng.standard_normal((n, 4)).astype(dt)
+        wt = (rng.random(n) ** 6 * 3.7).astype(dt)
+        for U in [0, 1, 2 ** 31, 2 ** 32 - 1, int(rng.integers(0, 2 ** 32))]:
+            f.set_state([x], [wt])
+            f.predict(torch.zeros((w.pe_cap, 4), dtype=torch.float64 if dt == np.float64 else torch.float32,
+                                  device="cuda"))
+            f.update(torch.zeros((0, 2), device="cuda"))
+            xp, wp = f.get_state()
+            np.testing.assert_array_equal(wp[0], wt)     # p_S = 1, p_D = 0: weights unchanged
+            f.resample(np.array([U], np.uint32))
+            par, _ = f.get_resample()
+            xr, wr = f.get_state()
+            xo, wo, po = oracle.resample(xp[0].astype(np.float64), wt.astype(np.float64),
+                                         w.particles_per_target, w.pe_cap, U)
+            assert np.array_equal(par[0, :len(po)], po), (n, U)
+            np.testing.assert_array_equal(xr[0].astype(np.float64), xo)
+            check_weights(wr[0], wo, dict(w_rel=1e-15 if dt == np.float64 else 1e-7), "new weights")
+        f.close()
+
+
+def test_free_running_fp64_matches_oracle_over_many_steps():
+    """The 4-target linear workload in FP64 (one of the published workloads):
+    20 steps with the oracle running its own recursion from the same start,
+    fed the same random numbers; estimates and particle sets agree."""
+    w = scenario.workload("linear4_fp64", steps=20)
+    sc = scenario.simulate(w, 0)
+    f = _filter(w, 0)
+    orc = oracle.OracleFilter(w)
+    worst = 0.0
+    for k, Z in enumerate(sc.meas):
+        noise = scenario.step_noise(0, k, 1, w.pe_cap)
+        u = scenario.resample_u32(0, k, 1)
+        f.predict(torch.as_tensor(noise).cuda())
+        f.update(torch.as_tensor(Z.astype(np.float64)).cuda())
+        states, labels = f.extract()
+        f.resample(u)
+        lab_o, zet_o = orc.step(Z, noise, u)
+        assert list(labels.cpu().numpy()) == list(lab_o), k
+        if len(lab_o):
+            worst = max(worst, float(np.abs(states.cpu().numpy() - zet_o).max()))
+        xs, ws = f.get_state()
+        assert len(xs[0]) == len(orc.x[0])
+        np.testing.assert_allclose(xs[0], orc.x[0], rtol=0, atol=1e-7)
+        np.testing.assert_allclose(ws[0], orc.wt[0], rtol=1e-10)
+    assert worst < 1e-6
+
+
+def test_published_distributed_workload_sizes():
+    """The 16-PE workload at its published sizes (10 targets, lambda = 50,
+    1000 particles per target, 1000 births): stage parity after a free-running
+    warm-up on the GPU's own random numbers."""
+    w = scenario.workload("dist16_10t")
+    rep = _run_stages(w, 2, 2, warm=12)
+    assert rep.max_mass_rel <= 1e-5
+
+
+def test_dense_workload_sampled():
+    """The dense range-bearing workload at full size (~2.2e5 particles, ~600
+    measurements): C on a sample of measurements and the updated weights on a
+    sample of particles against the oracle; the mass closed form of Eq. 8 at
+    full size."""
+    w = scenario.workload("dense_rb_100t")
+    sc = scenario.simulate(w, 3, steps=1)
+    f = _filter(w, 3)
+    rng = np.random.default_rng(3)
+    centres = sc.truth[0][:, [0, 2]]
+    n = 200_000
+    x, wt = scenario.random_particles(rng, w, n, centres=centres, spread=20.0, mass=100.0)
+    f.set_state([x.astype(np.float32)], [wt.astype(np.float32)])
+    m = oracle.model(w)
+    noise = scenario.step_noise(3, 0, 1, w.pe_cap, np.float32)
+    f.predict(torch.as_tensor(noise).cuda())
+    xp, wp = f.get_state()
+    Z = sc.meas[0]
+    M = len(Z)
+    assert M > 450
+    f.update(torch.as_tensor(Z).cuda())
+    C, mass = f.get_update()
+    xu_, wu = f.get_state()
+    sel_p = rng.choice(M, 24, replace=False)
+    Co = oracle.colsum(m, xp[0], wp[0], Z[sel_p].astype(np.float64))
+    kap = oracle.kappa(m)
+    assert np.all(np.abs(C[0, sel_p] - Co) <= 1e-5 * Co + 1e-9 * kap)
+    sel_i = rng.choice(len(xp[0]), 3000, replace=False)
+    wo = oracle.weight_update(m, xp[0][sel_i], wp[0][sel_i], Z.astype(np.float64), C[0, :M])
+    check_weights(wu[0][sel_i], wo, dict(w_rel=1e-4), "sampled weights")
+    ref = (1 - w.p_d) * wp[0].astype(np.float64).sum() + np.sum(C[0, :M] / (kap + C[0, :M]))
+    assert abs(mass[0] - ref) <= 1e-5 * ref
+    f.close()
+
+
+def test_edge_cases_and_errors():
+    from paper_1503_03769_gb300 import PhdError
+    from paper_1503_03769_gb300 import phd as P
+    w = scenario.workload("linear4_fp64", precision="fp32", birth_count=50, particles_per_target=20)
+    f = _filter(w, 0)
+    # empty filter, no measurements: births only, mass = (1 - p_D) nu_b
+    f.predict()
+    f.update(torch.zeros((0, 2), device="cuda"))
+    C, mass = f.get_update()
+    assert mass[0] == pytest.approx((1 - w.p_d) * w.birth_mass, rel=1e-6)
+    s, l = f.extract()
+    assert len(l) == 0
+    f.resample()
+    xs, ws = f.get_state()
+    assert len(xs[0]) == 20          # rho * max(1, N) with N < 1
+    # stage order
+    with pytest.raises(PhdError) as e:
+        f.update(torch.zeros((1, 2), device="cuda"))
+    assert e.value.status == P.PHD_ERR_STATE
+    with pytest.raises(PhdError) as e:
+        f.extract()
+    assert e.value.status == P.PHD_ERR_STATE
+    # too many measurements
+    f.predict()
+    with pytest.raises(PhdError) as e:
+        f.update(torch.zeros((w.m_max + 1, 2), device="cuda"))
+    assert e.value.status == P.PHD_ERR_CAPACITY
+    # non-finite measurement: reported at the next synchronising call
+    Z = torch.tensor([[1.0, 2.0], [float("nan"), 0.0]], device="cuda")
+    f.update(Z)
+    with pytest.raises(PhdError) as e:
+        f.get_update()
+    assert e.value.status == P.PHD_ERR_INVALID_ARG
+    f.resample()
+    # exactly m_max measurements, extraction capacity overflow reports the count
+    rng = np.random.default_rng(0)
+    xs = [rng.uniform(-900, 900, (w.pe_cap - 50, 4)).astype(np.float32)]
+    xs[0][:, [1, 3]] = 0
+    f.set_state(xs, [np.full(len(xs[0]), 0.05, np.float32)])
+    f.predict()
+    Zf = np.asarray(xs[0][:w.m_max][:, [0, 2]], np.float32)
+    f.update(torch.as_tensor(Zf).cuda())
+    with pytest.raises(PhdError) as e:
+        f.extract(cap=1)
+    assert e.value.status == P.PHD_ERR_CAPACITY and e.value.count > 1
+    f.resample()
+    f.close()
+
+
+def test_free_running_philox_moments():
+    """In-kernel randomness (Philox-4x32-10 + Box-Muller): predicted survivors
+    have the CV model's mean and covariance; births cover the region."""
+    w = scenario.workload("linear4_fp64", precision="fp32", birth_count=100000,
+                          particles_per_target=1, pe_cap=300000)
+    f = _filter(w, 11)
+    n = 150000
+    x0 = np.array([10.0, 2.0, -5.0, 1.0], np.float32)
+    f.set_state([np.tile(x0, (n, 1))], [np.full(n, 1.0 / n, np.float32)])
+    f.predict()
+    xp, wp = f.get_state()
+    sv, bi = xp[0][:n].astype(np.float64), xp[0][n:].astype(np.float64)
+    sa2 = w.sigma_a ** 2
+    blk = sa2 * np.array([[0.25, 0.5], [0.5, 1.0]])
+    cov = np.cov(sv.T)
+    assert np.allclose(cov[:2, :2], blk, rtol=0.03) and np.allclose(cov[2:, 2:], blk, rtol=0.03)
+    assert abs(cov[0, 2]) < 0.05 * sa2
+    assert np.allclose(sv.mean(0), [12.0, 2.0, -4.0, 1.0], atol=0.05)
+    assert len(bi) == 100000
+    assert bi[:, 0].min() >= -1000 and bi[:, 0].max() <= 1000
+    assert bi[:, 0].var() == pytest.approx(2000.0 ** 2 / 12, rel=0.02)
+    assert bi[:, 1].std() == pytest.approx(20.0, rel=0.02)
+    f.update(torch.zeros((0, 2), device="cuda"))
+    f.resample()
+    f.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    w = scenario.workload("dist16_10t", num_pe=4, n_targets=4, clutter_rate=20.0,
+                          particles_per_target=300, birth_count=400)
+    sc = scenario.simulate(w, 6, steps=8)
+    a = _filter(w, 6)
+    for k in range(4):
+        a.step(sc.meas[k])
+    xs, ws = a.get_state()
+    st = a.get_step()
+    b = _filter(w, 6)
+    b.set_state(xs, ws)
+    b.set_step(st)
+    for k in range(4, 8):
+        sa, la = a.step(sc.meas[k])
+        sb, lb = b.step(sc.meas[k])
+        assert torch.equal(la, lb) and torch.equal(sa, sb)
+    xa, wa = a.get_state()
+    xb, wb = b.get_state()
+    for j in range(4):
+        np.testing.assert_array_equal(xa[j], xb[j])
+        np.testing.assert_array_equal(wa[j], wb[j])
+
+
+def test_step_host_matches_device_step():
+    w = scenario.workload("dist16_10t", num_pe=4, n_targets=4, clutter_rate=20.0,
+                          particles_per_target=300, birth_count=400)
+    sc = scenario.simulate(w, 8, steps=5)
+    a, b = _filter(w, 8), _filter(w, 8)
+    out_s = np.zeros((w.m_max, 4), np.float32)
+    out_l = np.zeros(w.m_max, np.int32)
+    for Z in sc.meas:
+        sa, la = a.step(Z)
+        n = b.step_host(Z, out_s, out_l)
+        assert n == len(la)
+        np.testing.assert_array_equal(out_l[:n], la.cpu().numpy())
+        np.testing.assert_array_equal(out_s[:n], sa.cpu().numpy())
