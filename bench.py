@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the particle PHD filter step on GB300 (one JSON line on stdout).
+
+Metric: particle x measurement pairs per second per PHD update (the update's
+pairs, N_k x M_k summed over the timed steps, divided by the timed device
+time of the whole steps), plus steps/s.  A step is one full filter step:
+predict + birth, update, labelled extraction + CU fusion, resampling + ring
+exchange, through libphd.so's phd_step (a CUDA graph of the step's kernels).
+
+Default workload: the 16-PE distributed scheme (10 targets, clutter rate 50,
+1000 particles per target, 1000 births per step, 10 % ring exchange, FP32
+bulk / FP64 normalisers and CDF).  A run of that workload is 100 scans; K
+timed steps are K / 100 independent runs back to back (fresh filter state
+and scenario seed per run, reset between timed steps).  All measurement sets
+are resident in device memory before timing; L2 is flushed (512 MiB write)
+between timed steps, outside the timed events.
+
+--impl reference times the FP64 CPU oracle (tests' reference implementation)
+on the same workload; the driver divides the two.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import scenario
+
+METRIC = "particle×measurement pairs/s per PHD update and steps/s on 1 GB300 at matched OSPA"
+UNIT = "pairs/s"
+# MUFU ex2 peak: 152 SMs x 32 ex2/clk/SM x 2.07 GHz (max SM clock); one ex2 per pair
+EX2_PEAK_TEXP = 152 * 32 * 2.070e9 / 1e12
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def workload_config(w, runs, l2_note):
+    return {"workload": w.name, "model": "particle PHD filter (DCPFPHD)" if w.num_pe > 1 else "particle PHD filter",
+            "sensor": w.meas_model, "targets": w.n_targets, "clutter_rate": w.clutter_rate,
+            "particles_per_target": w.particles_per_target, "births_per_step": w.birth_count,
+            "num_pe": w.num_pe, "exchange_frac": w.exchange_frac, "ck_mode": w.ck_mode,
+            "scans_per_run": w.steps, "runs": runs, "precision": w.precision, "l2": l2_note,
+            "global_batch": 1, "seq_len": w.steps, "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.02)
+        self.mark = len(self.lines)
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def begin(self):
+        self.mark = len(self.lines)
+
+    def end(self):
+        time.sleep(0.12)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        for _, ln in self.lines[max(0, self.mark - 1):]:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _bad_clocks(c):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if any(r in bad for r in c.get("reasons", [])):
+        return True
+    if c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.6 * c["sm_max_mhz"] and \
+            "sw_power_cap" not in c.get("reasons", []):
+        return True
+    return False
+
+
+# ----------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+def oracle_run(w, seeds, max_steps, budget_s, skip=0):
+    """Run the FP64 oracle filter over the scenarios of `seeds` (100 scans each);
+    returns (pairs, seconds, steps, ospa_list) for the timed steps after `skip`."""
+    import oracle
+    pairs, secs, steps, ospas = 0, 0.0, 0, []
+    done = 0
+    for seed in seeds:
+        sc = scenario.simulate(w, seed)
+        f = oracle.OracleFilter(w)
+        for k, Z in enumerate(sc.meas):
+            noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap)
+            u = scenario.resample_u32(seed, k, w.num_pe)
+            xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap) if w.num_pe > 1 else None
+            n_before = sum(len(a) for a in f.x) + w.birth_count
+            t0 = time.perf_counter()
+            lab, zet = f.step(Z, noise, u, xu)
+            dt = time.perf_counter() - t0
+            done += 1
+            if done <= skip:
+                continue
+            pairs += n_before * len(Z)
+            secs += dt
+            steps += 1
+            ospas.append(_ospa(zet, sc.truth[k]))
+            if steps >= max_steps or secs >= budget_s:
+                return pairs, secs, steps, ospas
+    return pairs, secs, steps, ospas
+
+
+def _ospa(zet, truth):
+    import oracle
+    X = np.asarray(zet, np.float64)[:, [0, 2]] if len(zet) else np.zeros((0, 2))
+    Y = truth[:, [0, 2]] if len(truth) else np.zeros((0, 2))
+    return oracle.ospa(X, Y, 100.0, 2.0)
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    budget = float(os.environ.get("PHD_REF_BUDGET_S", "150"))
+    seeds = [args.seed + r for r in range(64)]
+    pairs, secs, steps, ospas = oracle_run(w, seeds, args.steps, budget, skip=args.warmup)
+    value = pairs / secs if secs > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, None, "n/a (CPU)"),
+        "steps_per_s": steps / secs if secs > 0 else 0.0,
+        "ospa_mean": float(np.mean(ospas)) if ospas else None,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} filter steps of {w.name} (seeds from {args.seed}), "
+                                   f"after {args.warmup} untimed, single-threaded FP64 C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+
+def _traffic_from_profile():
+    """Per-update DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "update_dist16_ncu.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    want = None
+    traffic = None
+    for ln in txt.splitlines():
+        if ln.startswith("source_sha256:"):
+            want = ln.split(":", 1)[1].strip()
+        if ln.startswith("traffic_bytes_per_update:"):
+            try:
+                traffic = float(ln.split(":", 1)[1].strip())
+            except ValueError:
+                traffic = None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1503_03769_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return traffic if want == h.hexdigest() else None
+
+
+def run_gpu(args, w, rank, world, local_rank):
+    import torch
+    from paper_1503_03769_gb300 import ParticlePHD
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    steps_per_run = w.steps
+    runs = max(1, math.ceil((args.warmup + args.steps) / steps_per_run))
+    base_seed = args.seed + 1000 * rank
+    scen = [scenario.simulate(w, base_seed + r) for r in range(runs)]
+    seq = [(r, k) for r in range(runs) for k in range(steps_per_run)][: args.warmup + args.steps]
+    dtype = torch.float64 if w.precision == "fp64" else torch.float32
+    Zdev = {(r, k): torch.as_tensor(scen[r].meas[k], dtype=dtype, device=dev) for r, k in seq}
+
+    f = ParticlePHD(w, seed=base_seed, device=f"cuda:{local_rank}")
+    empty_x = [np.zeros((0, 4))] * w.num_pe
+    empty_w = [np.zeros(0)] * w.num_pe
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    cap = w.m_max
+    out_s = torch.empty((cap, 4), dtype=dtype, device=dev)
+    out_l = torch.empty(cap, dtype=torch.int32, device=dev)
+
+    def begin_run_if_needed(r, k):
+        if k == 0:
+            f.set_state(empty_x, empty_w)
+
+    # warm-up (also captures the step graphs)
+    f.set_stage_timer(True)
+    for r, k in seq[: args.warmup]:
+        begin_run_if_needed(r, k)
+        f.step(Zdev[(r, k)], cap=cap, sync=False)
+    torch.cuda.synchronize()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = str(local_rank)
+
+    def timed_loop():
+        f.reset_stats()
+        evs = []
+        est_log = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(gpu_id)
+        clk.begin()
+        for r, k in seq[args.warmup:]:
+            if k == 0:
+                f.set_state(empty_x, empty_w)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s, l, c = f.step(Zdev[(r, k)], cap=cap, sync=False)
+            e1.record()
+            evs.append((e0, e1))
+            if k % 10 == 0:
+                est_log.append((r, k, s.clone(), c.clone()))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = clk.end()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, f.stats(), clocks, est_log
+
+    ms, st, clocks, est_log = timed_loop()
+    if _bad_clocks(clocks):
+        ms, st, clocks, est_log = timed_loop()
+        clocks["remeasured"] = True
+
+    pairs = st["pairs"]
+    K = len(seq) - args.warmup
+    # whole-job aggregation: sum of pairs over ranks, max time over ranks
+    if world > 1:
+        t = torch.tensor([float(pairs), ms], dtype=torch.float64, device=dev)
+        tp = t.clone()
+        torch.distributed.all_reduce(tp, op=torch.distributed.ReduceOp.SUM)
+        tm = t.clone()
+        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        pairs_all, ms_max = tp[0].item(), tm[1].item()
+    else:
+        pairs_all, ms_max = float(pairs), ms
+    value = pairs_all / (ms_max * 1e-3)
+    steps_per_s = world * K / (ms_max * 1e-3)
+
+    # OSPA of the logged estimates against the truth (c = 100, p = 2)
+    ospa_vals = []
+    try:
+        import oracle as _orc
+        for r, k, s, c in est_log:
+            n = int(c.item())
+            est = s[:n].double().cpu().numpy()
+            tr = scen[r].truth[k]
+            ospa_vals.append(_orc.ospa(est[:, [0, 2]] if n else np.zeros((0, 2)),
+                                       tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+    except Exception:
+        ospa_vals = []
+
+    # roofline of the update stage (Eq. 7-8 pair passes): one ex2 per pair
+    upd_ms = st["update_ms"]
+    achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "update stage (k_colsum, k_finalize, k_rowsum, k_mass)",
+                "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
+                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(),
+                "peak_source": "derived: 152 SMs x 32 MUFU ex2/clk x 2.07 GHz (one ex2 per pair)",
+                "update_ms_per_step": upd_ms / max(st["timed_updates"], 1),
+                "pairs_per_update": pairs / max(st["updates"], 1)}
+
+    # end to end through the public host-buffer call (pinned host memory)
+    f.set_stage_timer(False)
+    npdt = np.float64 if w.precision == "fp64" else np.float32
+    Zhost = {key: torch.as_tensor(scen[key[0]].meas[key[1]], dtype=dtype).pin_memory().numpy()
+             for key in seq}
+    hs = torch.empty((cap, 4), dtype=dtype).pin_memory().numpy()
+    hl = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+    f.reset_stats()
+    e2e_s, h2d, d2h = 0.0, 0, 0
+    for r, k in seq[: args.warmup]:
+        if k == 0:
+            f.set_state(empty_x, empty_w)
+        f.step_host(Zhost[(r, k)], hs, hl)
+    f.reset_stats()
+    for r, k in seq[args.warmup:]:
+        if k == 0:
+            f.set_state(empty_x, empty_w)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = f.step_host(Zhost[(r, k)], hs, hl)
+        e2e_s += time.perf_counter() - t0
+        h2d += Zhost[(r, k)].nbytes
+        d2h += min(n, cap) * (hs.itemsize * 4 + 4) + 4
+    st2 = f.stats()
+    if world > 1:
+        t = torch.tensor([float(st2["pairs"]), e2e_s], dtype=torch.float64, device=dev)
+        tp = t.clone()
+        torch.distributed.all_reduce(tp, op=torch.distributed.ReduceOp.SUM)
+        tm = t.clone()
+        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = tp[0].item() / tm[1].item()
+    else:
+        e2e_val = st2["pairs"] / e2e_s
+    f.close()
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": workload_config(w, runs, "flushed between timed steps (512 MiB write, outside the events)"),
+        "steps_per_s": steps_per_s,
+        "ospa_mean": float(np.mean(ospa_vals)) if ospa_vals else None,
+        "roofline": roofline,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K,
+                "note": "phd_step_host: pinned host Z in, estimates + count out, synchronous per step"},
+        "gpu_launches": int(st["launches"]),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        budget = float(os.environ.get("PHD_CPU_BASELINE_S", "15"))
+        cp, cs, cn, _ = oracle_run(w, [args.seed], 10 ** 9, budget)
+        line["cpu_baseline"] = {"value": cp / cs if cs > 0 else None, "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {cn} filter steps of {w.name} seed {args.seed} "
+                                          f"({cs:.1f} s), single-threaded FP64 C oracle"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dist16_10t")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    w = scenario.workload(args.workload)
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, w, rank, world)
+        return run_gpu(args, w, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -49,6 +49,7 @@ typedef enum {
 enum { PHD_MEAS_LINEAR = 0, PHD_MEAS_RANGE_BEARING = 1 };
 enum { PHD_FP32 = 0, PHD_FP64 = 1 };
 enum { PHD_CK_LOCAL = 0, PHD_CK_GLOBAL = 1 };
+enum { PHD_PATH_AUTO = 0, PHD_PATH_STAGED = 1, PHD_PATH_FUSED = 2 };
 
 /* Filter configuration (plain data, copied by phd_init). */
 typedef struct phd_config {
@@ -151,6 +152,35 @@ phd_status phd_resample(phd_handle *h, const uint32_t *d_u, const uint32_t *d_xu
 phd_status phd_step(phd_handle *h, const void *d_Z, int32_t M, void *d_states, int32_t *d_labels,
                     int32_t cap, int32_t *d_count, int32_t *h_count);
 
+/* phd_step with caller-supplied random numbers (layouts as phd_predict and
+ * phd_resample; any of them may be NULL for in-kernel Philox draws).  Runs
+ * the same kernels phd_step would (see phd_set_path). */
+phd_status phd_step_inject(phd_handle *h, const void *d_Z, int32_t M, const void *d_noise, const uint32_t *d_u,
+                           const uint32_t *d_xu, void *d_states, int32_t *d_labels, int32_t cap, int32_t *d_count,
+                           int32_t *h_count);
+
+/* S consecutive steps in one call (offline replay of recorded scans, Monte
+ * Carlo runs).  d_Z: real rows of all scans back to back; d_offsets: device
+ * int32 [S+1], scan s is rows d_offsets[s] .. d_offsets[s+1]-1 (each at most
+ * m_max rows, else the scan is skipped and PHD_ERR_CAPACITY is reported at the
+ * next synchronising call).  Outputs per scan s: d_states real [S][cap][4],
+ * d_labels int32 [S][cap], d_counts int32 [S] (true counts).  On the fused
+ * path this is one kernel launch for all S steps; on the staged path one
+ * graph launch per step (the offsets are read back once).  Asynchronous. */
+phd_status phd_run(phd_handle *h, const void *d_Z, const int32_t *d_offsets, int32_t S, void *d_states,
+                   int32_t *d_labels, int32_t *d_counts, int32_t cap);
+
+/* Kernel path of phd_step / phd_step_host / phd_step_inject / phd_run.
+ * PHD_PATH_FUSED: one cooperative kernel per call, one CTA per PE with the PE's
+ * slice in shared memory (available when the slice of pe_cap particles and
+ * m_max measurements fits an SM's shared memory and all K CTAs can be
+ * co-resident); PHD_PATH_STAGED: the stage kernels of phd_predict ..
+ * phd_resample as a CUDA graph; PHD_PATH_AUTO (default): fused when
+ * available.  phd_set_path returns PHD_ERR_INVALID_ARG for an unavailable
+ * path; phd_get_path reports the path in use. */
+phd_status phd_set_path(phd_handle *h, int32_t path);
+phd_status phd_get_path(phd_handle *h, int32_t *path);
+
 /* phd_step from host memory: copies h_Z [M][2] to the device, runs the step,
  * copies the estimates back to h_states [cap][4] / h_labels [cap] and their
  * true count to *h_count.  Host buffers may be pageable; pinned is faster.
@@ -166,13 +196,21 @@ phd_status phd_step_host(phd_handle *h, const void *h_Z, int32_t M, void *h_stat
 phd_status phd_set_state(phd_handle *h, const void *d_x, const void *d_w, const int32_t *h_counts);
 
 /* Copy the current particle set (layout as phd_set_state; slots beyond n_j
- * are unspecified) and h_counts int32 [K].  After phd_predict / phd_update
- * this is the predicted / updated set.  Synchronises. */
+ * are unspecified) and h_counts int32 [K].  Between phd_predict and
+ * phd_resample this is the predicted set, with the predicted weights after
+ * phd_predict and the updated weights (Eq. 8) after phd_update.
+ * Synchronises. */
 phd_status phd_get_state(phd_handle *h, void *d_x, void *d_w, int32_t *h_counts);
 
-/* After phd_update: d_C double [K][m_max] with C^j_p of Eq. 7 per PE, and
- * h_mass double [K] (may be NULL) with the updated masses N^j.  Synchronises. */
+/* After an update (phd_update or a whole step): d_C double [K][m_max] with
+ * C^j_p of Eq. 7 per PE, and h_mass double [K] (may be NULL) with the updated
+ * masses N^j of the most recent update.  Synchronises. */
 phd_status phd_get_update(phd_handle *h, double *d_C, double *h_mass);
+
+/* After an update: the most recent predicted set d_x real [K][pe_cap][4], its
+ * predicted weights d_w_pred and updated weights d_w_upd (real [K][pe_cap];
+ * any pointer may be NULL) and h_counts int32 [K].  Synchronises. */
+phd_status phd_get_predicted(phd_handle *h, void *d_x, void *d_w_pred, void *d_w_upd, int32_t *h_counts);
 
 /* After phd_extract: per-PE local estimates before fusion, d_states real
  * [K][m_max][4], d_labels int32 [K][m_max] in selection order, h_counts int32
@@ -188,6 +226,30 @@ phd_status phd_get_resample(phd_handle *h, int32_t *d_parents, int32_t *h_lx);
 /* Step counter (drives the Philox counters); set it to resume a checkpoint. */
 phd_status phd_get_step(phd_handle *h, uint64_t *step);
 phd_status phd_set_step(phd_handle *h, uint64_t step);
+
+/* ---- counters and the update-stage timer ---------------------------------- */
+
+typedef struct phd_stats {
+    uint64_t pairs;          /* sum over updates of particles x measurements */
+    uint64_t particles;      /* sum over updates of predicted particles (all PEs) */
+    uint64_t measurements;   /* sum over updates of |Z_k| */
+    uint64_t updates;        /* updates run */
+    uint64_t launches;       /* CUDA kernels this handle launched */
+    uint64_t timed_updates;  /* updates bracketed by the stage timer */
+    double update_ms;        /* their summed device time (CUDA events), ms: the update
+                                stage's kernels on the staged path, the whole fused
+                                step kernel on the fused path */
+} phd_stats;
+
+/* Read the counters accumulated since phd_init / phd_reset_stats.  Synchronises. */
+phd_status phd_get_stats(phd_handle *h, phd_stats *out);
+phd_status phd_reset_stats(phd_handle *h);
+
+/* on != 0: phd_step / phd_step_host bracket the update stage (Eq. 7-8 pair
+ * passes) with CUDA events on the handle's stream; the times add up in
+ * phd_stats.update_ms.  The step then runs as three graph launches instead of
+ * one.  Does not synchronise. */
+phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
 
 /* Wait for the stream and report a device-side error (non-finite input,
  * bounded-wait timeout) recorded since the last check.  Synchronises. */

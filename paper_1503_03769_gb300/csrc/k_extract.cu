@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   item_prefix(d.n_pred, K, pref);
   const int total = pref[K];
   const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
-  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
-  const R* __restrict__ w = static_cast<const R*>(d.w);
+  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
+  const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
 

@@ -1,0 +1,608 @@
+// Fused filter step: one cooperative launch runs S whole steps (Algorithm 1)
+// with one CTA per processing element.
+//
+// Each PE (CTA j, 1024 threads) keeps its predicted slice in shared memory
+// for the step: states, the sensor-space geometry h(x) and the weights.  The
+// stages are the staged path's, in order, separated by __syncthreads:
+//   predict (Eq. 5-6)       current set (global) -> predicted slice (smem + x_alt)
+//   pass 1 (Eq. 7)          C^j_p: threads own (measurement, particle split)
+//   [GLOBAL mode]           grid barrier, C_p = mean over PEs
+//   pass 2 (Eq. 8)          updated weights, mass N^j and max weight
+//   selection (Step 3)      LT_j = round(N^j), rank counting over dW^{j,p}
+//   pass 3 (Eq. 18)         labelled sums for the selected labels -> zeta
+//   resampling (Step 5)     exact integer CDF scan, offspring counts, gather
+//   grid barrier            all L_j, local estimates visible
+//   exchange plan (Step 6)  L_x = floor(frac min L_j), Fisher-Yates slots,
+//                           outgoing couples to the outbox; CTA 0 fuses the
+//                           local estimates (Step 4) into the step's output
+//   grid barrier
+//   exchange in             PE j's slots take PE j-1's outbox
+// The only cross-PE waits are the two (three) grid barriers the scheme needs:
+// the exchange count and the CU fusion depend on every PE.  Barriers spin
+// with an iteration limit; on expiry the kernel records kErrTimeout and every
+// CTA returns.  All arithmetic matches the staged kernels (same helpers), but
+// reductions run in a different fixed order.
+#include "phd_internal.cuh"
+
+namespace phd {
+
+constexpr int kFusedThreads = 1024;
+constexpr long kSpinLimit = 20000000;   // ~2 s with 100 ns sleeps
+
+struct FusedArgs {
+  const void* Z;            // packed measurements of S steps
+  const int* zoff;          // [S+1] row offsets into Z, or NULL for one step of M1 rows
+  int M1;
+  const void* noise;        // injected predict draws (S == 1) or NULL
+  const uint32_t* u;        // injected resampling uniforms (S == 1) or NULL
+  const uint32_t* xu;       // injected exchange draws (S == 1) or NULL
+  void* out_states;         // [S][cap][4] fused estimates
+  int* out_labels;          // [S][cap]
+  int* out_count;           // [S]
+  int cap;
+  int S;
+};
+
+// Grid-wide barrier over gridDim.x CTAs with a bounded wait.  Returns false
+// (in every thread of the CTA) when the wait gave up or another CTA recorded
+// an error; the caller then returns from the kernel.
+__device__ __forceinline__ bool grid_sync(const Dev& d) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = d.bar + 1;
+    volatile int* err = d.err;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(d.bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(d.bar, 0u);
+      __threadfence();
+      atomicAdd(d.bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*gen == g) {
+        if (*err != 0) { ok = 0; break; }
+        if (++it > kSpinLimit) {
+          atomicOr(d.err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (*err != 0) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Shared-memory layout of the fused kernel (bytes), for pe_cap P and m_max Mm.
+struct FusedSmem {
+  size_t sx, sh0, sh1, shl, sw, swu, zs, ginv, Cd, Cu, dW, sel, selrank, red, total;
+};
+
+template <class R>
+__host__ __device__ inline FusedSmem fused_smem(int P, int Mm) {
+  FusedSmem L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = (o + 15) & ~(size_t)15;
+    o = at + bytes;
+    return at;
+  };
+  L.sx = take(sizeof(St4<R>) * P);
+  // sh0..sw are reused for the resampling CDF (8 B), offspring ends (4 B) and
+  // the Fisher-Yates permutation (4 B) once the pair passes are done
+  const size_t per = (4 * sizeof(R) > 16 ? 4 * sizeof(R) : 16);
+  const size_t blk = take(per * P);
+  L.sh0 = blk;
+  L.sh1 = blk + sizeof(R) * P;
+  L.shl = blk + 2 * sizeof(R) * P;
+  L.sw = blk + 3 * sizeof(R) * P;
+  L.swu = take(sizeof(R) * P);
+  L.zs = take(sizeof(V2<R>) * Mm);
+  L.ginv = take(sizeof(R) * Mm);
+  L.Cd = take(sizeof(double) * Mm);
+  L.Cu = take(sizeof(double) * Mm);
+  L.dW = take(sizeof(double) * Mm);
+  L.sel = take(sizeof(int) * Mm);
+  L.selrank = take(sizeof(int) * Mm);
+  L.red = take(sizeof(double) * kFusedThreads);
+  L.total = (o + 15) & ~(size_t)15;
+  return L;
+}
+
+// Deterministic block sum of one double per thread (fixed order).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int k = 0; k < nw; ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int k = 0; k < nw; ++k) s = fmax(s, red[k]);
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ int block_sum_int(int v, double* red) {
+  return (int)block_sum((double)v, red);
+}
+
+// Cartesian point of a measurement (offset origin of the labelled sums).
+template <class R>
+__device__ __forceinline__ void meas_point_f(const Model& m, V2<R> z, R& rx, R& ry) {
+  if (m.meas_model == 0) {
+    rx = z.a;
+    ry = z.b;
+  } else {
+    R sn, cs;
+    sincos(z.b, &sn, &cs);
+    rx = (R)m.sx + z.a * cs;
+    ry = (R)m.sy + z.a * sn;
+  }
+}
+
+// CU fusion of one step by one CTA (Step 4): labels taken by more than K/2
+// PEs, FP64 mean of their local states, ascending label order.
+template <class R>
+__device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* out_lab, int cap, int* count,
+                        double* red) {
+  int* wsum = reinterpret_cast<int*>(red);
+  __shared__ int carry_s;
+  const St4<R>* est = static_cast<const St4<R>*>(d.est_local);
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p0 = 0; p0 < M; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    int votes = 0;
+    if (p < M)
+      for (int k = 0; k < m.K; ++k) votes += d.selrank[k * m.m_max + p] >= 0 ? 1 : 0;
+    const int valid = (p < M && 2 * votes > m.K) ? 1 : 0;
+    int incl = valid;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < nw) wsum[lane] = v;
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
+    if (valid && idx < cap) {
+      double a[4] = {0, 0, 0, 0};
+      for (int k = 0; k < m.K; ++k) {
+        const int r = d.selrank[k * m.m_max + p];
+        if (r >= 0) {
+          const St4<R> e = est[k * m.m_max + r];
+          a[0] += (double)e.x;
+          a[1] += (double)e.vx;
+          a[2] += (double)e.y;
+          a[3] += (double)e.vy;
+        }
+      }
+      out[idx] = St4<R>{(R)(a[0] / votes), (R)(a[1] / votes), (R)(a[2] / votes), (R)(a[3] / votes)};
+      out_lab[idx] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + wsum[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *count = carry_s;
+    *d.out_count = carry_s;
+  }
+  __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m, FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const FusedSmem SL = fused_smem<R>(m.pe_cap, m.m_max);
+  St4<R>* sx = reinterpret_cast<St4<R>*>(smem + SL.sx);
+  R* sh0 = reinterpret_cast<R*>(smem + SL.sh0);
+  R* sh1 = reinterpret_cast<R*>(smem + SL.sh1);
+  R* shl = reinterpret_cast<R*>(smem + SL.shl);
+  R* sw = reinterpret_cast<R*>(smem + SL.sw);
+  R* swu = reinterpret_cast<R*>(smem + SL.swu);
+  V2<R>* zs = reinterpret_cast<V2<R>*>(smem + SL.zs);
+  R* ginv = reinterpret_cast<R*>(smem + SL.ginv);
+  double* Cd = reinterpret_cast<double*>(smem + SL.Cd);
+  double* Cu = reinterpret_cast<double*>(smem + SL.Cu);
+  double* dW = reinterpret_cast<double*>(smem + SL.dW);
+  int* sel = reinterpret_cast<int*>(smem + SL.sel);
+  int* selrank = reinterpret_cast<int*>(smem + SL.selrank);
+  double* red = reinterpret_cast<double*>(smem + SL.red);
+  // resampling arrays alias the pair-pass block (sh0 .. sw)
+  unsigned long long* Q = reinterpret_cast<unsigned long long*>(smem + SL.sh0);
+  int* cend = reinterpret_cast<int*>(smem + SL.sh0 + sizeof(unsigned long long) * m.pe_cap);
+  int* perm = cend + m.pe_cap;
+  __shared__ double bcast_d[2];
+  __shared__ int bcast_i[4];
+
+  const int j = blockIdx.x;
+  const int T = blockDim.x, tid = threadIdx.x;
+  const long base = (long)j * m.pe_cap;
+  const int Jj = births_of(m.J, m.K, j);
+  const unsigned long long step0 = *d.step;
+  const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
+  const Lik<R> L = make_lik<R>(m);
+  const double cs = m.p_d * m.cnorm;
+  const R miss = (R)(1.0 - m.p_d);
+  St4<R>* gx = static_cast<St4<R>*>(d.x);
+  R* gw = static_cast<R*>(d.w);
+  St4<R>* gxp = static_cast<St4<R>*>(d.x_alt);
+  R* gwp = static_cast<R*>(d.w_alt);
+  R* gwu = static_cast<R*>(d.wu);
+  St4<R>* gest = static_cast<St4<R>*>(d.est_local);
+  const bool xchg = m.K > 1 && m.exchange_frac > 0.0;
+  int n = d.n_cur[j];
+
+  for (int s = 0; s < a.S; ++s) {
+    const unsigned long long step = step0 + (unsigned long long)s;
+    const int z0 = a.zoff ? a.zoff[s] : 0;
+    int M = a.zoff ? a.zoff[s + 1] - z0 : a.M1;
+    if (M < 0 || M > m.m_max) {
+      if (tid == 0) atomicOr(d.err, kErrCapacity);
+      M = 0;
+    }
+    const V2<R>* Zg = static_cast<const V2<R>*>(a.Z) + z0;
+    for (int p = tid; p < M; p += T) {
+      const V2<R> z = Zg[p];
+      if (!isfinite(z.a) || !isfinite(z.b)) atomicOr(d.err, kErrNonFinite);
+      zs[p] = z;
+    }
+    if (j == 0 && tid == 0) *d.M = M;
+    // ---- predict (Eq. 5-6)
+    const int np = n + Jj;
+    for (int i = tid; i < np; i += T) {
+      R n1, n2, u1, u2;
+      draw_noise<R>(m, static_cast<const R*>(a.noise), base + i, step, n1, n2, u1, u2);
+      const bool surv = i < n;
+      St4<R> o;
+      R wo;
+      predict_slot<R>(m, surv, surv ? gx[base + i] : St4<R>{0, 0, 0, 0}, surv ? gw[base + i] : (R)0, Jj, n1, n2,
+                      u1, u2, o, wo);
+      gxp[base + i] = o;
+      gwp[base + i] = wo;
+      sx[i] = o;
+      const H3<R> h = meas_h<R>(m, o, tab);
+      sh0[i] = h.h0;
+      sh1[i] = h.h1;
+      shl[i] = h.h1lo;
+      sw[i] = wo;
+    }
+    if (tid == 0) d.n_pred[j] = np;
+    __syncthreads();
+    // ---- pass 1: C^j_p (Eq. 7)
+    if (M > 0) {
+      const int mper = M < T ? M : T;
+      const int nsplit = T / mper;
+      const int pl = tid % mper, split = tid / mper;
+      for (int p0 = 0; p0 < M; p0 += mper) {
+        const int p = p0 + pl;
+        R acc = 0;
+        if (split < nsplit && p < M) {
+          const V2<R> z = zs[p];
+          R part = 0;
+          int k = 0;
+          for (int i = split; i < np; i += nsplit) {
+            const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
+            part = fma(exp2_neg(q), sw[i], part);
+            if (++k == 32) { acc += part; part = 0; k = 0; }
+          }
+          acc += part;
+        }
+        red[tid] = (double)acc;
+        __syncthreads();
+        if (split == 0 && p < M) {
+          double c = red[tid];
+          for (int k = 1; k < nsplit; ++k) c += red[tid + k * mper];
+          c *= cs;
+          Cd[p] = c;
+          d.C[j * m.m_max + p] = c;
+        }
+        __syncthreads();
+      }
+    }
+    if (m.ck_global && m.K > 1) {
+      if (!grid_sync(d)) return;
+      for (int p = tid; p < M; p += T) {
+        double mean = 0.0;
+        for (int k = 0; k < m.K; ++k) mean += d.C[k * m.m_max + p];
+        Cu[p] = mean / (double)m.K;
+      }
+    } else {
+      for (int p = tid; p < M; p += T) Cu[p] = Cd[p];
+    }
+    __syncthreads();
+    for (int p = tid; p < M; p += T) {
+      const double den = m.kappa + Cu[p];
+      ginv[p] = den > 0.0 ? (R)(cs / den) : (R)0;
+      dW[p] = den > 0.0 ? Cd[p] / den : 0.0;
+      d.Cused[j * m.m_max + p] = Cu[p];
+    }
+    __syncthreads();
+    // ---- pass 2: updated weights (Eq. 8), mass and largest weight
+    double msum = 0.0, mmax = 0.0;
+    for (int i = tid; i < np; i += T) {
+      const R h0 = sh0[i], h1 = sh1[i], hl = shl[i];
+      R acc = 0, part = 0;
+      int k = 0;
+      for (int p = 0; p < M; ++p) {
+        const V2<R> z = zs[p];
+        part = fma(exp2_neg(qform<R>(L, z.a, z.b, h0, h1, hl)), ginv[p], part);
+        if (++k == 64) { acc += part; part = 0; k = 0; }
+      }
+      acc += part;
+      const R wv = (miss + acc) * sw[i];
+      swu[i] = wv;
+      gwu[base + i] = wv;
+      msum += (double)wv;
+      mmax = fmax(mmax, (double)wv);
+    }
+    const double N = block_sum(msum, red);
+    const double wmax = block_max(mmax, red);
+    if (tid == 0) d.mass[j] = N;
+    // ---- selection (Step 3)
+    int npos_t = 0;
+    for (int p = tid; p < M; p += T) npos_t += dW[p] > 0.0 ? 1 : 0;
+    const int npos = block_sum_int(npos_t, red);
+    long long LTl = llround(N);
+    if (LTl > npos) LTl = npos;
+    if (LTl < 0) LTl = 0;
+    const int LT = (int)LTl;
+    for (int p = tid; p < M; p += T) {
+      const double v = dW[p];
+      int rank = 0;
+      for (int q = 0; q < M; ++q) {
+        const double u = dW[q];
+        rank += (u > v || (u == v && q < p)) ? 1 : 0;
+      }
+      const bool take = v > 0.0 && rank < LT;
+      selrank[p] = take ? rank : -1;
+      d.selrank[j * m.m_max + p] = take ? rank : -1;
+      if (take) {
+        sel[rank] = p;
+        d.sel[j * m.m_max + rank] = p;
+      }
+    }
+    if (tid == 0) d.nsel[j] = LT;
+    __syncthreads();
+    // ---- pass 3: labelled sums for the selected labels (Eq. 18)
+    if (LT > 0) {
+      const int mper = LT < T ? LT : T;
+      const int nsplit = T / mper;
+      const int rl = tid % mper, split = tid / mper;
+      for (int r0 = 0; r0 < LT; r0 += mper) {
+        const int r = r0 + rl;
+        R acc5[5] = {0, 0, 0, 0, 0};
+        R px = 0, py = 0;
+        if (split < nsplit && r < LT) {
+          const int p = sel[r];
+          const V2<R> z = zs[p];
+          meas_point_f<R>(m, z, px, py);
+          for (int i = split; i < np; i += nsplit) {
+            const R ew = exp2_neg(qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i])) * sw[i];
+            const St4<R> st = sx[i];
+            acc5[0] += ew;
+            acc5[1] = fma(ew, st.x - px, acc5[1]);
+            acc5[2] = fma(ew, st.vx, acc5[2]);
+            acc5[3] = fma(ew, st.y - py, acc5[3]);
+            acc5[4] = fma(ew, st.vy, acc5[4]);
+          }
+        }
+        double tot[5];
+        for (int c = 0; c < 5; ++c) {
+          red[tid] = (double)acc5[c];
+          __syncthreads();
+          tot[c] = 0.0;
+          if (split == 0 && r < LT) {
+            double t = red[tid];
+            for (int k = 1; k < nsplit; ++k) t += red[tid + k * mper];
+            tot[c] = t;
+          }
+          __syncthreads();
+        }
+        if (split == 0 && r < LT) {
+          St4<R> o;
+          if (tot[0] > 0.0) {
+            o.x = (R)((double)px + tot[1] / tot[0]);
+            o.vx = (R)(tot[2] / tot[0]);
+            o.y = (R)((double)py + tot[3] / tot[0]);
+            o.vy = (R)(tot[4] / tot[0]);
+          } else {
+            o = St4<R>{px, (R)0, py, (R)0};
+          }
+          gest[j * m.m_max + r] = o;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- resampling (Step 5): exact integer CDF, offspring counts, gather
+    int Lc, sc;
+    resample_plan(m, j, np, N, wmax, Lc, sc);
+    {
+      constexpr int IT = 4;
+      unsigned long long carry = 0ull;
+      unsigned long long* wt = reinterpret_cast<unsigned long long*>(red);
+      const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+      for (int c0 = 0; c0 < np; c0 += T * IT) {
+        unsigned long long q[IT];
+        unsigned long long run = 0ull;
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+          const int i = c0 + tid * IT + k;
+          q[k] = i < np ? (unsigned long long)floor(ldexp((double)swu[i], sc)) : 0ull;
+          run += q[k];
+          q[k] = run;
+        }
+        unsigned long long incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == 31) wt[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+          unsigned long long v = lane < nw ? wt[lane] : 0ull;
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+          }
+          if (lane < nw) wt[lane] = v;
+        }
+        __syncthreads();
+        const unsigned long long off = carry + (wid > 0 ? wt[wid - 1] : 0ull) + (incl - run);
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+          const int i = c0 + tid * IT + k;
+          if (i < np) Q[i] = off + q[k];
+        }
+        carry += wt[nw - 1];
+        __syncthreads();
+      }
+    }
+    const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
+    const unsigned long long Qn = np > 0 ? Q[np - 1] : 0ull;
+    for (int i = tid; i < np; i += T) cend[i] = offspring_end(Q[i], Qn, (unsigned long long)Lc, U);
+    __syncthreads();
+    const R wnew = Lc > 0 ? (R)(N / (double)Lc) : (R)0;
+    for (int t = tid; t < Lc; t += T) {
+      int lo = 0, hi = np - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cend[mid] > t) hi = mid; else lo = mid + 1;
+      }
+      gx[base + t] = sx[lo];
+      gw[base + t] = wnew;
+      d.parent[base + t] = lo;
+    }
+    if (tid == 0) {
+      d.rs_L[j] = Lc;
+      d.rs_mass[j] = N;
+      d.rs_s[j] = sc;
+    }
+    n = Lc;
+    // ---- CU fusion (Step 4) and ring exchange (Step 6)
+    St4<R>* out_s = static_cast<St4<R>*>(a.out_states) + (long)s * a.cap;
+    int* out_l = a.out_labels + (long)s * a.cap;
+    if (m.K > 1) {
+      if (!grid_sync(d)) return;
+      int lx = 0;
+      if (xchg) {
+        int nmin = d.rs_L[0];
+        for (int k = 1; k < m.K; ++k) nmin = min(nmin, d.rs_L[k]);
+        lx = (int)floor(m.exchange_frac * (double)nmin);
+        if (j == 0 && tid == 0) *d.lx = lx;
+        if (lx > 0) {
+          for (int i = tid; i < Lc; i += T) perm[i] = i;
+          __syncthreads();
+          if (tid == 0) {
+            for (int t = 0; t < lx; ++t) {
+              const uint32_t uu = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
+              const int r = t + (int)(((unsigned long long)uu * (unsigned long long)(Lc - t)) >> 32);
+              const int tmp = perm[t];
+              perm[t] = perm[r];
+              perm[r] = tmp;
+            }
+          }
+          __syncthreads();
+          St4<R>* xo = static_cast<St4<R>*>(d.x_out);
+          R* wo = static_cast<R*>(d.w_out);
+          for (int t = tid; t < lx; t += T) {
+            const int slot = perm[t];
+            d.xslots[base + t] = slot;
+            xo[base + t] = gx[base + slot];
+            wo[base + t] = gw[base + slot];
+          }
+        }
+      }
+      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, red);
+      if (!grid_sync(d)) return;
+      if (xchg && lx > 0) {
+        const int from = (j + m.K - 1) % m.K;
+        const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
+        const R* wo = static_cast<const R*>(d.w_out);
+        for (int t = tid; t < lx; t += T) {
+          const long dst = base + perm[t];
+          gx[dst] = xo[(long)from * m.pe_cap + t];
+          gw[dst] = wo[(long)from * m.pe_cap + t];
+        }
+      }
+    } else {
+      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, red);
+    }
+    if (tid == 0) d.n_cur[j] = n;
+    __syncthreads();
+  }
+  if (j == 0 && tid == 0) *d.step = step0 + (unsigned long long)a.S;
+}
+
+template <class R>
+size_t fused_smem_bytes(const Model& m) {
+  return fused_smem<R>(m.pe_cap, m.m_max).total;
+}
+
+// Whether the fused kernel can run this configuration: the shared-memory
+// layout fits and all K CTAs are co-resident.
+template <class R>
+bool fused_eligible(const Model& m, int device) {
+  const size_t sm = fused_smem_bytes<R>(m);
+  int optin = 0, nsm = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return false;
+  if (sm + 2048 > (size_t)optin) return false;
+  if (cudaFuncSetAttribute(k_step_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return false;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_fused<R>, kFusedThreads, sm) != cudaSuccess)
+    return false;
+  return (long)per * nsm >= m.K;
+}
+
+template <class R>
+cudaError_t launch_fused(const Dev& d, const Model& m, const void* Z, const int* zoff, int M1, int S, const R* noise,
+                         const uint32_t* u, const uint32_t* xu, R* out_states, int* out_labels, int* out_count,
+                         int cap, cudaStream_t s) {
+  FusedArgs a{Z, zoff, M1, noise, u, xu, out_states, out_labels, out_count, cap, S};
+  const size_t sm = fused_smem_bytes<R>(m);
+  cudaError_t e = cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&d, (void*)&m, (void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)k_step_fused<R>, dim3(m.K), dim3(kFusedThreads), args, sm, s);
+}
+
+template bool fused_eligible<float>(const Model&, int);
+template bool fused_eligible<double>(const Model&, int);
+template cudaError_t launch_fused<float>(const Dev&, const Model&, const void*, const int*, int, int, const float*,
+                                         const uint32_t*, const uint32_t*, float*, int*, int*, int, cudaStream_t);
+template cudaError_t launch_fused<double>(const Dev&, const Model&, const void*, const int*, int, int, const double*,
+                                          const uint32_t*, const uint32_t*, double*, int*, int*, int, cudaStream_t);
+
+}  // namespace phd

@@ -7,7 +7,8 @@
 // Eq. 5's phi/q is the survival probability).  Birth slots
 // (n_cur[j] <= i < n_cur[j] + J_j) draw position U(region) and velocity
 // N(0, s_b^2 I) and take weight nu_b / J_j (Eq. 6 with gamma = nu_b p_k).
-// The update is in place: survivors keep their slots, births append.
+// Survivors keep their slot index, births follow them; the predicted set is
+// written to the alternate buffers (x_alt, w_alt), the current set is read.
 // Random numbers come from the caller (noise rows n1, n2, u1, u2) or from
 // Philox-4x32-10 keyed by the seed with counter (slot, step, tag).
 //
@@ -19,8 +20,10 @@ namespace phd {
 
 template <class R>
 __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __restrict__ noise) {
-  St4<R>* x = static_cast<St4<R>*>(d.x);
-  R* w = static_cast<R*>(d.w);
+  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
+  const R* __restrict__ w = static_cast<const R*>(d.w);
+  St4<R>* __restrict__ xp = static_cast<St4<R>*>(d.x_alt);
+  R* __restrict__ wp = static_cast<R*>(d.w_alt);
   const unsigned long long step = *d.step;
   const long total = (long)m.K * m.pe_cap;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
@@ -28,45 +31,16 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
     const int i = (int)(g - (long)j * m.pe_cap);
     const int L = d.n_cur[j];
     const int Jj = births_of(m.J, m.K, j);
+    if (i == 0) d.n_pred[j] = L + Jj;
     if (i >= L + Jj) continue;
     R n1, n2, u1, u2;
-    if (noise) {
-      const St4<R> nz = reinterpret_cast<const St4<R>*>(noise)[g];
-      n1 = nz.x; n2 = nz.vx; u1 = nz.y; u2 = nz.vy;
-    } else {
-      U4 r = philox4x32_10(U4{(uint32_t)g, (uint32_t)step, kTagPredict, (uint32_t)(step >> 32)},
-                           (uint32_t)m.seed, (uint32_t)(m.seed >> 32));
-      // Box-Muller on two open-interval uniforms
-      R ua = unit_open<R>(r.a), ub = unit_open<R>(r.b);
-      R rad = sqrt((R)-2 * log(ua));
-      R sn, cs;
-      sincospi((R)2 * ub, &sn, &cs);
-      n1 = rad * cs;
-      n2 = rad * sn;
-      u1 = unit_open<R>(r.c);
-      u2 = unit_open<R>(r.d);
-    }
-    if (i < L) {
-      const R T = (R)m.dt;
-      const R ax = (R)m.sigma_a * n1, ay = (R)m.sigma_a * n2;
-      St4<R> s = x[g];
-      St4<R> o;
-      o.x = s.x + T * s.vx + (R)0.5 * T * T * ax;
-      o.vx = s.vx + T * ax;
-      o.y = s.y + T * s.vy + (R)0.5 * T * T * ay;
-      o.vy = s.vy + T * ay;
-      x[g] = o;
-      w[g] = (R)m.p_s * w[g];
-    } else {
-      St4<R> o;
-      o.x = (R)m.rx0 + u1 * (R)(m.rx1 - m.rx0);
-      o.vx = (R)m.birth_vel_sigma * n1;
-      o.y = (R)m.ry0 + u2 * (R)(m.ry1 - m.ry0);
-      o.vy = (R)m.birth_vel_sigma * n2;
-      x[g] = o;
-      w[g] = (R)(m.birth_mass / (double)Jj);
-    }
-    if (i == 0) d.n_pred[j] = L + Jj;
+    draw_noise<R>(m, noise, g, step, n1, n2, u1, u2);
+    const bool surv = i < L;
+    St4<R> o;
+    R wo;
+    predict_slot<R>(m, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, Jj, n1, n2, u1, u2, o, wo);
+    xp[g] = o;
+    wp[g] = wo;
   }
 }
 

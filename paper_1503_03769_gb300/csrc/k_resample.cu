@@ -16,11 +16,12 @@
 //               ((V - U) >> 32) + 1).  Child t's parent is then the least i
 //               with c_i > t, i.e. the least i with Q_i > T_t.
 //   k_rs_gather: one thread per child: binary search of c, copy the parent's
-//               state, weight N^j / L_j.
+//               predicted state into the current set, weight N^j / L_j.
 // Ring exchange (K > 1): L_x = floor(frac min_j L_j); PE j takes the first L_x
 // entries of a Fisher-Yates shuffle of its L_j slots (r = t + floor(u_t
-// (L_j - t) / 2^32)); the particles in PE j's slots move into the slots PE
-// j+1 chose, so slice sizes and the union of particles are unchanged.
+// (L_j - t) / 2^32)); the particles in PE j's slots move, through an outbox,
+// into the slots PE j+1 chose, so slice sizes and the union of particles are
+// unchanged.
 #include "phd_internal.cuh"
 
 namespace phd {
@@ -52,22 +53,11 @@ __global__ void __launch_bounds__(256) k_rs_mass(Dev d, Model m) {
       N += rs[k];
       wmax = fmax(wmax, rm[k]);
     }
-    long long L = 0;
-    int sc = 0;
-    if (n > 0 && wmax > 0.0) {
-      int e;
-      frexp(wmax, &e);
-      int c = 0;
-      while ((1LL << c) < (long long)n) ++c;
-      sc = 52 - c - e;
-      L = llround(m.rho_pe * (N > 1.0 ? N : 1.0));
-      const long long lmax = m.pe_cap - births_of(m.J, m.K, j);
-      if (L > lmax) L = lmax;
-      if (L < 0) L = 0;
-    }
+    int L, sc;
+    resample_plan(m, j, n, N, wmax, L, sc);
     d.rs_mass[j] = N;
     d.rs_s[j] = sc;
-    d.rs_L[j] = (int)L;
+    d.rs_L[j] = L;
   }
 }
 
@@ -122,61 +112,47 @@ __global__ void __launch_bounds__(1024) k_rs_scan(Dev d, Model m) {
   }
 }
 
-__device__ __forceinline__ uint32_t resample_u(const Dev& d, const Model& m, const uint32_t* u, int j) {
-  if (u) return u[j];
-  const unsigned long long st = *d.step;
-  U4 r = philox4x32_10(U4{(uint32_t)j, (uint32_t)st, kTagResample, (uint32_t)(st >> 32)},
-                       (uint32_t)m.seed, (uint32_t)(m.seed >> 32));
-  return r.a;
-}
-
 __global__ void k_rs_count(Dev d, Model m, const uint32_t* __restrict__ u) {
   const long total = (long)m.K * m.pe_cap;
+  const unsigned long long st = *d.step;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / m.pe_cap);
     const int i = (int)(g - (long)j * m.pe_cap);
     const int n = d.n_pred[j];
     if (i >= n) continue;
-    const unsigned long long L = (unsigned long long)d.rs_L[j];
-    int c = 0;
-    if (L > 0) {
-      const unsigned long long Qn = d.Q[(long)j * m.pe_cap + n - 1];
-      const unsigned long long Qi = d.Q[g];
-      const unsigned __int128 X = ((unsigned __int128)Qi * L) << 32;
-      if (X > 0 && Qn > 0) {
-        const unsigned long long V = (unsigned long long)((X - 1) / Qn);
-        const unsigned long long U = resample_u(d, m, u, j);
-        unsigned long long cc = V < U ? 0ull : ((V - U) >> 32) + 1ull;
-        c = (int)(cc < L ? cc : L);
-      }
-    }
-    d.child_end[g] = c;
+    const uint32_t U = u ? u[j] : philox_u32(m, (uint32_t)j, st, kTagResample);
+    d.child_end[g] = offspring_end(d.Q[g], d.Q[(long)j * m.pe_cap + n - 1], (unsigned long long)d.rs_L[j], U);
   }
 }
 
+// Children t < L_j of PE j: parent = least i with child_end[i] > t; the
+// predicted state is gathered into the current set with weight N^j / L_j.
 template <class R>
 __global__ void k_rs_gather(Dev d, Model m) {
-  const St4<R>* x = static_cast<const St4<R>*>(d.x);
-  St4<R>* xa = static_cast<St4<R>*>(d.x_alt);
-  R* wa = static_cast<R*>(d.w_alt);
+  const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
+  St4<R>* x = static_cast<St4<R>*>(d.x);
+  R* w = static_cast<R*>(d.w);
   const long total = (long)m.K * m.pe_cap;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / m.pe_cap);
     const int t = (int)(g - (long)j * m.pe_cap);
     const int L = d.rs_L[j];
+    if (t == 0) d.n_cur[j] = L;
     if (t >= L) continue;
     const long base = (long)j * m.pe_cap;
-    int lo = 0, hi = d.n_pred[j] - 1;   // least i with child_end[i] > t
+    int lo = 0, hi = d.n_pred[j] - 1;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if (d.child_end[base + mid] > t) hi = mid; else lo = mid + 1;
     }
-    xa[g] = x[base + lo];
-    wa[g] = (R)(d.rs_mass[j] / (double)L);
+    x[g] = xp[base + lo];
+    w[g] = (R)(d.rs_mass[j] / (double)L);
     d.parent[g] = lo;
   }
 }
 
+// Ring exchange plan: L_x = floor(frac min_j L_j); PE j's slots are the first
+// L_x entries of a partial Fisher-Yates shuffle of 0..L_j-1.
 __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
   extern __shared__ int perm[];
   const int j = blockIdx.x;
@@ -192,14 +168,8 @@ __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
   if (threadIdx.x == 0) {
     const unsigned long long st = *d.step;
     for (int t = 0; t < lx; ++t) {
-      uint32_t u;
-      if (xu) {
-        u = xu[(long)j * m.pe_cap + t];
-      } else {
-        U4 r = philox4x32_10(U4{(uint32_t)((long)j * m.pe_cap + t), (uint32_t)st, kTagExchange, (uint32_t)(st >> 32)},
-                             (uint32_t)m.seed, (uint32_t)(m.seed >> 32));
-        u = r.a;
-      }
+      const uint32_t u = xu ? xu[(long)j * m.pe_cap + t]
+                            : philox_u32(m, (uint32_t)((long)j * m.pe_cap + t), st, kTagExchange);
       const int r = t + (int)(((unsigned long long)u * (unsigned long long)(n - t)) >> 32);
       const int tmp = perm[t];
       perm[t] = perm[r];
@@ -209,40 +179,40 @@ __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
   }
 }
 
+// Outgoing particle-weight couples of each PE into the outbox.
 template <class R>
-__global__ void k_copyback(Dev d, Model m) {
-  St4<R>* x = static_cast<St4<R>*>(d.x);
-  R* w = static_cast<R*>(d.w);
-  const St4<R>* xa = static_cast<const St4<R>*>(d.x_alt);
-  const R* wa = static_cast<const R*>(d.w_alt);
-  const long total = (long)m.K * m.pe_cap;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(g / m.pe_cap);
-    const int t = (int)(g - (long)j * m.pe_cap);
-    const int L = d.rs_L[j];
-    if (t == 0) d.n_cur[j] = L;
-    if (t >= L) continue;
-    x[g] = xa[g];
-    w[g] = wa[g];
-  }
-}
-
-template <class R>
-__global__ void k_xmove(Dev d, Model m) {
-  St4<R>* x = static_cast<St4<R>*>(d.x);
-  R* w = static_cast<R*>(d.w);
-  const St4<R>* xa = static_cast<const St4<R>*>(d.x_alt);
-  const R* wa = static_cast<const R*>(d.w_alt);
+__global__ void k_xout(Dev d, Model m) {
+  const St4<R>* x = static_cast<const St4<R>*>(d.x);
+  const R* w = static_cast<const R*>(d.w);
+  St4<R>* xo = static_cast<St4<R>*>(d.x_out);
+  R* wo = static_cast<R*>(d.w_out);
   const int lx = *d.lx;
   const long total = (long)m.K * lx;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / lx);
     const int t = (int)(g - (long)j * lx);
-    const int k = (j + 1) % m.K;
     const long src = (long)j * m.pe_cap + d.xslots[(long)j * m.pe_cap + t];
-    const long dst = (long)k * m.pe_cap + d.xslots[(long)k * m.pe_cap + t];
-    x[dst] = xa[src];
-    w[dst] = wa[src];
+    xo[(long)j * m.pe_cap + t] = x[src];
+    wo[(long)j * m.pe_cap + t] = w[src];
+  }
+}
+
+// PE j's chosen slots receive PE j-1's outbox (ring).
+template <class R>
+__global__ void k_xin(Dev d, Model m) {
+  St4<R>* x = static_cast<St4<R>*>(d.x);
+  R* w = static_cast<R*>(d.w);
+  const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
+  const R* wo = static_cast<const R*>(d.w_out);
+  const int lx = *d.lx;
+  const long total = (long)m.K * lx;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / lx);
+    const int t = (int)(g - (long)j * lx);
+    const int from = (j + m.K - 1) % m.K;
+    const long dst = (long)j * m.pe_cap + d.xslots[(long)j * m.pe_cap + t];
+    x[dst] = xo[(long)from * m.pe_cap + t];
+    w[dst] = wo[(long)from * m.pe_cap + t];
   }
 }
 
@@ -258,14 +228,13 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   k_rs_scan<R><<<m.K, 1024, 0, s>>>(d, m);
   k_rs_count<<<b, 256, 0, s>>>(d, m, u);
   k_rs_gather<R><<<b, 256, 0, s>>>(d, m);
-  const bool xchg = m.K > 1 && m.exchange_frac > 0.0;
-  if (xchg) k_xplan<<<m.K, 256, sizeof(int) * (size_t)m.pe_cap, s>>>(d, m, xu);
-  k_copyback<R><<<b, 256, 0, s>>>(d, m);
-  if (xchg) {
+  if (m.K > 1 && m.exchange_frac > 0.0) {
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
     if (bx < 1) bx = 1;
     if (bx > 152 * 8) bx = 152 * 8;
-    k_xmove<R><<<bx, 256, 0, s>>>(d, m);
+    k_xplan<<<m.K, 256, sizeof(int) * (size_t)m.pe_cap, s>>>(d, m, xu);
+    k_xout<R><<<bx, 256, 0, s>>>(d, m);
+    k_xin<R><<<bx, 256, 0, s>>>(d, m);
   }
   return cudaGetLastError();
 }

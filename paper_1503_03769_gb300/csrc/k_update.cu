@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   const int M = *d.M;
   if (M <= 0) return;
   const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
-  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
-  const R* __restrict__ w = static_cast<const R*>(d.w);
+  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
+  const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
   const int mper = M < kThreads ? M : kThreads;
@@ -119,6 +119,14 @@ __global__ void k_finalize(Dev d, Model m) {
       ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long n = 0;
+    for (int j = 0; j < K; ++j) n += (unsigned long long)d.n_pred[j];
+    d.stats[0] += n * (unsigned long long)M;
+    d.stats[1] += n;
+    d.stats[2] += (unsigned long long)M;
+    d.stats[3] += 1ull;
+  }
 }
 
 template <class R>
@@ -134,8 +142,8 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const int M = *d.M;
   const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
   const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
-  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
-  const R* __restrict__ w = static_cast<const R*>(d.w);
+  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
+  const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   R* __restrict__ wu = static_cast<R*>(d.wu);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);

@@ -27,8 +27,21 @@ struct phd_handle {
   int device;
   int stage;
   std::string err;
-  void* out_states;   // St4<R> [m_max] staging for phd_step_host
+  void* out_states;   // St4<R> [m_max] fused estimates of phd_step / phd_step_host
   int* out_labels;    // [m_max]
+  // CUDA graphs of the step body (in-kernel randomness): the whole body, and
+  // the same body split around the update for the stage timer
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_all = nullptr, g_pre = nullptr, g_upd = nullptr, g_post = nullptr;
+  bool timer = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  double timer_ms = 0.0;
+  unsigned long long timer_calls = 0;
+  unsigned long long launches = 0;
+  bool fused_ok = false;   // the fused step kernel fits this configuration
+  int path = 0;            // PHD_PATH_AUTO / PHD_PATH_STAGED / PHD_PATH_FUSED
+  bool have_update = false;
 };
 
 namespace {
@@ -58,6 +71,8 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.wu = cv.take<char>(K * P, rs);
   t.x_alt = cv.take<char>(K * P, 4 * rs);
   t.w_alt = cv.take<char>(K * P, rs);
+  t.x_out = cv.take<char>(K * P, 4 * rs);
+  t.w_out = cv.take<char>(K * P, rs);
   t.n_cur = cv.take<int>(K);
   t.n_pred = cv.take<int>(K);
   t.Z = cv.take<char>(Mm, 2 * rs);
@@ -83,7 +98,9 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.parent = cv.take<int>(K * P);
   t.xslots = cv.take<int>(K * P);
   t.lx = cv.take<int>(1);
+  t.bar = cv.take<unsigned int>(2);
   t.step = cv.take<unsigned long long>(1);
+  t.stats = cv.take<unsigned long long>(4);
   t.err = cv.take<int>(1);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
@@ -175,6 +192,10 @@ phd_status cuda_fail(phd_handle* h, cudaError_t e, const char* where) {
 
 bool is_fp64(const phd_handle* h) { return h->cfg.precision == PHD_FP64; }
 
+// kernels each stage launches (for the launch counter)
+constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1;
+int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
+
 phd_status read_device_error(phd_handle* h) {
   int err = 0;
   PHD_CUDA(h, cudaMemcpyAsync(&err, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -192,6 +213,7 @@ phd_status do_predict(phd_handle* h, const void* noise) {
   cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, static_cast<const double*>(noise), h->stream)
                              : phd::launch_predict<float>(h->d, h->m, static_cast<const float*>(noise), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "predict");
+  h->launches += kNPredict;
   h->stage = kPredicted;
   return PHD_OK;
 }
@@ -207,7 +229,9 @@ phd_status do_update(phd_handle* h, const void* Z, int M, bool z_in_workspace) {
   if (e != cudaSuccess) return cuda_fail(h, e, "stage_z");
   e = is_fp64(h) ? phd::launch_update<double>(h->d, h->m, h->stream) : phd::launch_update<float>(h->d, h->m, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "update");
+  h->launches += kNStageZ + kNUpdate;
   h->stage = kUpdated;
+  h->have_update = true;
   return PHD_OK;
 }
 
@@ -219,6 +243,7 @@ phd_status do_extract(phd_handle* h, void* states, int* labels, int cap, int* d_
       ? phd::launch_extract<double>(h->d, h->m, static_cast<double*>(states), labels, cap, d_count, h->stream)
       : phd::launch_extract<float>(h->d, h->m, static_cast<float*>(states), labels, cap, d_count, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "extract");
+  h->launches += kNExtract;
   if (h_count) {
     phd_status st = read_device_error(h);
     if (st != PHD_OK) return st;
@@ -236,7 +261,183 @@ phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
   if (e != cudaSuccess) return cuda_fail(h, e, "resample");
   e = phd::launch_advance_step(h->d, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "advance_step");
+  h->launches += n_resample(h->m) + kNAdvance;
   h->stage = kReady;
+  return PHD_OK;
+}
+
+// Step body with in-kernel randomness, split in three parts around the update.
+cudaError_t enq_pre(phd_handle* h, cudaStream_t s) {
+  return is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, nullptr, s)
+                    : phd::launch_predict<float>(h->d, h->m, nullptr, s);
+}
+cudaError_t enq_upd(phd_handle* h, cudaStream_t s) {
+  return is_fp64(h) ? phd::launch_update<double>(h->d, h->m, s) : phd::launch_update<float>(h->d, h->m, s);
+}
+cudaError_t enq_post(phd_handle* h, cudaStream_t s) {
+  const int cap = h->cfg.m_max;
+  cudaError_t e = is_fp64(h)
+      ? phd::launch_extract<double>(h->d, h->m, static_cast<double*>(h->out_states), h->out_labels, cap, nullptr, s)
+      : phd::launch_extract<float>(h->d, h->m, static_cast<float*>(h->out_states), h->out_labels, cap, nullptr, s);
+  if (e == cudaSuccess)
+    e = is_fp64(h) ? phd::launch_resample<double>(h->d, h->m, nullptr, nullptr, s)
+                   : phd::launch_resample<float>(h->d, h->m, nullptr, nullptr, s);
+  if (e == cudaSuccess) e = phd::launch_advance_step(h->d, s);
+  return e;
+}
+cudaError_t enq_all(phd_handle* h, cudaStream_t s) {
+  cudaError_t e = enq_pre(h, s);
+  if (e == cudaSuccess) e = enq_upd(h, s);
+  if (e == cudaSuccess) e = enq_post(h, s);
+  return e;
+}
+
+cudaError_t capture(phd_handle* h, cudaError_t (*body)(phd_handle*, cudaStream_t), cudaGraphExec_t* out) {
+  if (!h->cap_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t eb = body(h, h->cap_stream);
+  e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (eb != cudaSuccess) e = eb;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+void destroy_graphs(phd_handle* h) {
+  for (cudaGraphExec_t* g : {&h->g_all, &h->g_pre, &h->g_upd, &h->g_post})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+}
+
+// Sum the timer's recorded event pairs into timer_ms (synchronises).
+cudaError_t drain_timer(phd_handle* h) {
+  if (h->ev_used == 0) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(h->ev[h->ev_used - 1].second);
+  for (size_t i = 0; e == cudaSuccess && i < h->ev_used; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, h->ev[i].first, h->ev[i].second);
+    h->timer_ms += ms;
+  }
+  h->timer_calls += h->ev_used;
+  h->ev_used = 0;
+  return e;
+}
+
+// The step body on h->stream (Z already staged): one graph launch, or three
+// with the update bracketed by events when the stage timer is on.
+phd_status run_step_body(phd_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->timer) {
+    if (!h->g_all) e = capture(h, enq_all, &h->g_all);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->g_all, h->stream);
+  } else {
+    if (!h->g_pre) e = capture(h, enq_pre, &h->g_pre);
+    if (e == cudaSuccess && !h->g_upd) e = capture(h, enq_upd, &h->g_upd);
+    if (e == cudaSuccess && !h->g_post) e = capture(h, enq_post, &h->g_post);
+    if (e == cudaSuccess && h->ev_used >= 4096) e = drain_timer(h);
+    if (e == cudaSuccess && h->ev_used == h->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+      e = cudaEventCreate(&p.first);
+      if (e == cudaSuccess) e = cudaEventCreate(&p.second);
+      if (e == cudaSuccess) h->ev.push_back(p);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->g_pre, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].first, h->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->g_upd, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].second, h->stream);
+    if (e == cudaSuccess) ++h->ev_used;
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->g_post, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
+  h->launches += kNPredict + kNUpdate + kNExtract + n_resample(h->m) + kNAdvance;
+  return PHD_OK;
+}
+
+phd_status stage_z_only(phd_handle* h, const void* Z, int M);
+bool use_fused(const phd_handle* h) { return h->fused_ok && h->path != PHD_PATH_STAGED; }
+
+// One fused launch of S steps.  With zoff == NULL: one step of M rows at Z.
+phd_status run_fused(phd_handle* h, const void* Z, const int* zoff, int M, int S, const void* noise,
+                     const uint32_t* u, const uint32_t* xu, void* states, int* labels, int* counts, int cap) {
+  const bool timed = h->timer;
+  cudaError_t e = cudaSuccess;
+  if (timed) {
+    if (h->ev_used >= 4096) e = drain_timer(h);
+    if (e == cudaSuccess && h->ev_used == h->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+      e = cudaEventCreate(&p.first);
+      if (e == cudaSuccess) e = cudaEventCreate(&p.second);
+      if (e == cudaSuccess) h->ev.push_back(p);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].first, h->stream);
+  }
+  if (e == cudaSuccess)
+    e = is_fp64(h) ? phd::launch_fused<double>(h->d, h->m, Z, zoff, M, S, static_cast<const double*>(noise), u, xu,
+                                               static_cast<double*>(states), labels, counts, cap, h->stream)
+                   : phd::launch_fused<float>(h->d, h->m, Z, zoff, M, S, static_cast<const float*>(noise), u, xu,
+                                              static_cast<float*>(states), labels, counts, cap, h->stream);
+  if (e == cudaSuccess && timed) {
+    e = cudaEventRecord(h->ev[h->ev_used].second, h->stream);
+    if (e == cudaSuccess) ++h->ev_used;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "fused step");
+  h->launches += 1;
+  h->have_update = true;
+  return PHD_OK;
+}
+
+// The output contract of phd_step: estimates into the caller's buffers (or
+// the workspace's), the true count on the device.
+phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u,
+                       const uint32_t* xu, void* d_states, int* d_labels, int cap, int* d_count) {
+  phd_status st;
+  if (use_fused(h)) {
+    const bool direct = cap > 0 && d_states && d_labels;
+    st = run_fused(h, Z, nullptr, M, 1, noise, u, xu, direct ? d_states : h->out_states,
+                   direct ? d_labels : h->out_labels, h->d.out_count, direct ? cap : h->cfg.m_max);
+  } else if (noise || u || xu) {
+    st = do_predict(h, noise);
+    if (st == PHD_OK) st = do_update(h, Z, M, Z == h->d.Z);
+    if (st == PHD_OK) st = do_extract(h, h->out_states, h->out_labels, h->cfg.m_max, nullptr, nullptr);
+    if (st == PHD_OK) st = do_resample(h, u, xu);
+    if (st != PHD_OK) h->stage = kReady;
+    if (st == PHD_OK && cap > 0) {
+      const size_t rs = real_size(h->cfg);
+      const int ncp = cap < h->cfg.m_max ? cap : h->cfg.m_max;
+      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDeviceToDevice,
+                                  h->stream));
+    }
+  } else {
+    st = stage_z_only(h, Z, M);
+    if (st == PHD_OK) st = run_step_body(h);
+    if (st == PHD_OK && cap > 0) {
+      const size_t rs = real_size(h->cfg);
+      const int ncp = cap < h->cfg.m_max ? cap : h->cfg.m_max;
+      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDeviceToDevice,
+                                  h->stream));
+    }
+  }
+  if (st != PHD_OK) return st;
+  h->have_update = true;
+  if (d_count)
+    PHD_CUDA(h, cudaMemcpyAsync(d_count, h->d.out_count, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  return PHD_OK;
+}
+
+phd_status stage_z_only(phd_handle* h, const void* Z, int M) {
+  cudaError_t e = is_fp64(h) ? phd::launch_stage_z<double>(h->d, h->m, static_cast<const double*>(Z), M, h->stream)
+                             : phd::launch_stage_z<float>(h->d, h->m, static_cast<const float*>(Z), M, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage_z");
+  h->launches += kNStageZ;
   return PHD_OK;
 }
 
@@ -281,6 +482,9 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = is_fp64(h) ? phd::prepare_kernels<double>(h->m) : phd::prepare_kernels<float>(h->m);
   if (e == cudaSuccess && h->m.K > 1 && h->m.exchange_frac > 0) e = phd::prepare_exchange(h->m);
+  if (e == cudaSuccess)
+    h->fused_ok = is_fp64(h) ? phd::fused_eligible<double>(h->m, h->device) : phd::fused_eligible<float>(h->m, h->device);
+  (void)cudaGetLastError();   // an ineligible attribute query leaves no sticky error
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
   // bearing anchors: float directions (c_k, s_k) near angle 2 pi k / 256 and
   // their exact angles atan2(s_k, c_k) in FP64, split into two floats
@@ -308,6 +512,12 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
 phd_status phd_destroy(phd_handle* h) {
   if (!h) return PHD_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  for (auto& p : h->ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return e == cudaSuccess ? PHD_OK : PHD_ERR_CUDA;
 }
@@ -335,18 +545,20 @@ phd_status phd_resample(phd_handle* h, const uint32_t* d_u, const uint32_t* d_xu
 
 phd_status phd_step(phd_handle* h, const void* d_Z, int32_t M, void* d_states, int32_t* d_labels, int32_t cap,
                     int32_t* d_count, int32_t* h_count) {
+  return phd_step_inject(h, d_Z, M, nullptr, nullptr, nullptr, d_states, d_labels, cap, d_count, h_count);
+}
+
+phd_status phd_step_inject(phd_handle* h, const void* d_Z, int32_t M, const void* d_noise, const uint32_t* d_u,
+                           const uint32_t* d_xu, void* d_states, int32_t* d_labels, int32_t cap, int32_t* d_count,
+                           int32_t* h_count) {
   if (!h) return PHD_ERR_INVALID_ARG;
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_step: a step is already in progress");
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
-  phd_status st = do_predict(h, nullptr);
-  if (st == PHD_OK) st = do_update(h, d_Z, M, false);
-  if (st == PHD_OK) st = do_extract(h, d_states, d_labels, cap, d_count, nullptr);
-  if (st == PHD_OK) st = do_resample(h, nullptr, nullptr);
-  if (st != PHD_OK) {
-    h->stage = kReady;
-    return st;
-  }
+  if (M > 0 && !d_Z) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  if (cap < 0 || (cap > 0 && (!d_states || !d_labels))) return fail(h, PHD_ERR_INVALID_ARG, "bad output buffer");
+  phd_status st = step_common(h, d_Z, M, d_noise, d_u, d_xu, d_states, d_labels, cap, d_count);
+  if (st != PHD_OK) return st;
   if (h_count) {
     st = read_device_error(h);
     if (st != PHD_OK) return st;
@@ -371,14 +583,9 @@ phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_stat
     if (!std::isfinite(v)) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
   }
   if (M > 0) PHD_CUDA(h, cudaMemcpyAsync(h->d.Z, h_Z, (size_t)M * 2 * rs, cudaMemcpyHostToDevice, h->stream));
-  phd_status st = do_predict(h, nullptr);
-  if (st == PHD_OK) st = do_update(h, nullptr, M, true);
-  if (st == PHD_OK) st = do_extract(h, h->out_states, h->out_labels, h->cfg.m_max, nullptr, nullptr);
-  if (st == PHD_OK) st = do_resample(h, nullptr, nullptr);
-  if (st != PHD_OK) {
-    h->stage = kReady;
-    return st;
-  }
+  phd_status st = step_common(h, h->d.Z, M, nullptr, nullptr, nullptr, h->out_states, h->out_labels, h->cfg.m_max,
+                              nullptr);
+  if (st != PHD_OK) return st;
   int n = 0;
   PHD_CUDA(h, cudaMemcpyAsync(&n, h->d.out_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -391,6 +598,61 @@ phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_stat
   phd_status es = read_device_error(h);
   if (es != PHD_OK) return es;
   return n > cap ? fail(h, PHD_ERR_CAPACITY, "more estimates than cap") : PHD_OK;
+}
+
+phd_status phd_run(phd_handle* h, const void* d_Z, const int32_t* d_offsets, int32_t S, void* d_states,
+                   int32_t* d_labels, int32_t* d_counts, int32_t cap) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_run: a step is already in progress");
+  if (S < 0 || !d_offsets || (S > 0 && (!d_counts || cap < 1 || !d_states || !d_labels)))
+    return fail(h, PHD_ERR_INVALID_ARG, "bad phd_run arguments");
+  if (S == 0) return PHD_OK;
+  const size_t rs = real_size(h->cfg);
+  if (use_fused(h)) return run_fused(h, d_Z, d_offsets, 0, S, nullptr, nullptr, nullptr, d_states, d_labels, d_counts, cap);
+  // staged path: one graph-launched step per scan
+  std::vector<int32_t> off((size_t)S + 1);
+  PHD_CUDA(h, cudaMemcpyAsync(off.data(), d_offsets, off.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int s = 0; s < S; ++s) {
+    const int M = off[s + 1] - off[s];
+    if (M < 0 || M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "a scan has M > m_max");
+    const char* Zs = static_cast<const char*>(d_Z) + (size_t)off[s] * 2 * rs;
+    phd_status st = step_common(h, Zs, M, nullptr, nullptr, nullptr, static_cast<char*>(d_states) + (size_t)s * cap * 4 * rs,
+                                d_labels + (size_t)s * cap, cap, d_counts + s);
+    if (st != PHD_OK) return st;
+  }
+  return PHD_OK;
+}
+
+phd_status phd_set_path(phd_handle* h, int32_t path) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (path != PHD_PATH_AUTO && path != PHD_PATH_STAGED && path != PHD_PATH_FUSED)
+    return fail(h, PHD_ERR_INVALID_ARG, "unknown path");
+  if (path == PHD_PATH_FUSED && !h->fused_ok)
+    return fail(h, PHD_ERR_INVALID_ARG, "the fused step kernel does not fit this configuration");
+  h->path = path;
+  return PHD_OK;
+}
+
+phd_status phd_get_path(phd_handle* h, int32_t* path) {
+  if (!h || !path) return PHD_ERR_INVALID_ARG;
+  *path = use_fused(h) ? PHD_PATH_FUSED : PHD_PATH_STAGED;
+  return PHD_OK;
+}
+
+phd_status phd_get_predicted(phd_handle* h, void* d_x, void* d_w_pred, void* d_w_upd, int32_t* h_counts) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_get_predicted: no update has run");
+  const int K = h->cfg.num_pe;
+  const size_t rs = real_size(h->cfg);
+  const size_t n = (size_t)K * h->cfg.pe_cap;
+  if (d_x) PHD_CUDA(h, cudaMemcpyAsync(d_x, h->d.x_alt, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_w_pred) PHD_CUDA(h, cudaMemcpyAsync(d_w_pred, h->d.w_alt, n * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_w_upd) PHD_CUDA(h, cudaMemcpyAsync(d_w_upd, h->d.wu, n * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (h_counts)
+    PHD_CUDA(h, cudaMemcpyAsync(h_counts, h->d.n_pred, K * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return read_device_error(h);
 }
 
 phd_status phd_set_state(phd_handle* h, const void* d_x, const void* d_w, const int32_t* h_counts) {
@@ -415,10 +677,10 @@ phd_status phd_get_state(phd_handle* h, void* d_x, void* d_w, int32_t* h_counts)
   const int K = h->cfg.num_pe;
   const size_t rs = real_size(h->cfg);
   const size_t n = (size_t)K * h->cfg.pe_cap;
-  if (d_x) PHD_CUDA(h, cudaMemcpyAsync(d_x, h->d.x, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
-  if (d_w)
-    PHD_CUDA(h, cudaMemcpyAsync(d_w, h->stage == kUpdated ? h->d.wu : h->d.w, n * rs, cudaMemcpyDeviceToDevice,
-                                h->stream));
+  const void* xs = h->stage == kReady ? h->d.x : h->d.x_alt;
+  const void* ws = h->stage == kReady ? h->d.w : (h->stage == kUpdated ? h->d.wu : h->d.w_alt);
+  if (d_x) PHD_CUDA(h, cudaMemcpyAsync(d_x, xs, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_w) PHD_CUDA(h, cudaMemcpyAsync(d_w, ws, n * rs, cudaMemcpyDeviceToDevice, h->stream));
   if (h_counts)
     PHD_CUDA(h, cudaMemcpyAsync(h_counts, h->stage == kReady ? h->d.n_cur : h->d.n_pred, K * sizeof(int),
                                 cudaMemcpyDeviceToHost, h->stream));
@@ -428,7 +690,7 @@ phd_status phd_get_state(phd_handle* h, void* d_x, void* d_w, int32_t* h_counts)
 
 phd_status phd_get_update(phd_handle* h, double* d_C, double* h_mass) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_get_update: no update in progress");
+  if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_get_update: no update has run");
   const size_t K = h->cfg.num_pe, Mm = h->cfg.m_max;
   if (d_C) PHD_CUDA(h, cudaMemcpyAsync(d_C, h->d.C, K * Mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (h_mass) {
@@ -481,6 +743,39 @@ phd_status phd_set_step(phd_handle* h, uint64_t step) {
   unsigned long long s = step;
   PHD_CUDA(h, cudaMemcpyAsync(h->d.step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PHD_OK;
+}
+
+phd_status phd_set_stage_timer(phd_handle* h, int32_t on) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  h->timer = on != 0;
+  return PHD_OK;
+}
+
+phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
+  if (!h || !out) return PHD_ERR_INVALID_ARG;
+  unsigned long long v[4] = {0, 0, 0, 0};
+  PHD_CUDA(h, cudaMemcpyAsync(v, h->d.stats, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  PHD_CUDA(h, drain_timer(h));
+  out->pairs = v[0];
+  out->particles = v[1];
+  out->measurements = v[2];
+  out->updates = v[3];
+  out->launches = h->launches;
+  out->timed_updates = h->timer_calls;
+  out->update_ms = h->timer_ms;
+  return read_device_error(h);
+}
+
+phd_status phd_reset_stats(phd_handle* h) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  PHD_CUDA(h, drain_timer(h));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.stats, 0, 4 * sizeof(unsigned long long), h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->launches = 0;
+  h->timer_ms = 0.0;
+  h->timer_calls = 0;
   return PHD_OK;
 }
 

@@ -45,11 +45,13 @@ struct Model {
 // Workspace carve (device pointers).  Real-typed arrays are void* and cast by
 // the kernels' Real type.
 struct Dev {
-  void* x;               // St4<R> [K*pe_cap]  current / predicted / updated set
-  void* w;               // R [K*pe_cap]  current / predicted weights
-  void* wu;              // R [K*pe_cap]  updated weights (Eq. 8)
-  void* x_alt;           // St4<R> [K*pe_cap]  resampling target
-  void* w_alt;           // R [K*pe_cap]
+  void* x;               // St4<R> [K*pe_cap]  current set (after resampling / exchange)
+  void* w;               // R [K*pe_cap]
+  void* x_alt;           // St4<R> [K*pe_cap]  predicted set (survivors + births)
+  void* w_alt;           // R [K*pe_cap]       predicted weights
+  void* wu;              // R [K*pe_cap]       updated weights (Eq. 8)
+  void* x_out;           // St4<R> [K*pe_cap]  exchange outbox
+  void* w_out;           // R [K*pe_cap]
   int* n_cur;            // [K] particles per PE (survivors before predict)
   int* n_pred;           // [K] particles per PE after predict
   void* Z;               // V2<R> [m_max]  measurements (as given)
@@ -75,7 +77,9 @@ struct Dev {
   int* parent;           // [K*pe_cap]
   int* xslots;           // [K][pe_cap] exchange slots
   int* lx;               // [1] particles moved per PE
+  unsigned int* bar;     // [2] grid barrier: arrival count, generation
   unsigned long long* step;  // [1] step counter (Philox counter word)
+  unsigned long long* stats; // [4] sums over updates: pairs, particles, measurements, updates
   int* err;              // [1] device error bits
   int max_items;
 };
@@ -231,15 +235,25 @@ __device__ __forceinline__ R qform(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1
 }
 
 // Work-item decode for the pair kernels: item -> (PE, particle tile), tiles
-// of kTile over each PE's count.  pref has K+1 entries in shared memory.
+// of kTile over each PE's count.  pref gets K+1 entries in shared memory; the
+// block needs at least kMaxPE threads (tile counts are scanned in parallel).
 __device__ __forceinline__ void item_prefix(const int* n, int K, int* pref) {
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int j = 0; j < K; ++j) {
-      pref[j] = acc;
-      acc += (n[j] + kTile - 1) / kTile;
-    }
-    pref[K] = acc;
+  __shared__ int wt[kMaxPE / 32];
+  const int t = threadIdx.x;
+  const int v = t < K ? (n[t] + kTile - 1) / kTile : 0;
+  const int lane = t & 31, wid = t >> 5;
+  int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (t < kMaxPE && lane == 31) wt[wid] = incl;
+  __syncthreads();
+  if (t < K) {
+    int off = 0;
+    for (int k = 0; k < wid; ++k) off += wt[k];
+    pref[t] = off + incl - v;
+    if (t == K - 1) pref[K] = off + incl;
   }
   __syncthreads();
 }
@@ -257,6 +271,90 @@ __host__ __device__ __forceinline__ int births_of(int J, int K, int j) {
 }
 
 // ---------------------------------------------------------------------------
+// Prediction of one particle slot (Eq. 5-6), shared by the staged and fused
+// paths.  Slot i of PE j: a survivor when i < L (CV transition, weight p_S w),
+// else a birth (position U(region), velocity N(0, s_b^2 I), weight nu_b / J_j).
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void draw_noise(const Model& m, const R* noise, long g, unsigned long long step,
+                                           R& n1, R& n2, R& u1, R& u2) {
+  if (noise) {
+    const St4<R> nz = reinterpret_cast<const St4<R>*>(noise)[g];
+    n1 = nz.x;
+    n2 = nz.vx;
+    u1 = nz.y;
+    u2 = nz.vy;
+  } else {
+    const U4 r = philox4x32_10(U4{(uint32_t)g, (uint32_t)step, kTagPredict, (uint32_t)(step >> 32)},
+                               (uint32_t)m.seed, (uint32_t)(m.seed >> 32));
+    // Box-Muller on two open-interval uniforms
+    const R ua = unit_open<R>(r.a), ub = unit_open<R>(r.b);
+    const R rad = sqrt((R)-2 * log(ua));
+    R sn, cs;
+    sincospi((R)2 * ub, &sn, &cs);
+    n1 = rad * cs;
+    n2 = rad * sn;
+    u1 = unit_open<R>(r.c);
+    u2 = unit_open<R>(r.d);
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void predict_slot(const Model& m, bool survivor, const St4<R>& s, R w, int Jj,
+                                             R n1, R n2, R u1, R u2, St4<R>& o, R& wo) {
+  if (survivor) {
+    const R T = (R)m.dt;
+    const R ax = (R)m.sigma_a * n1, ay = (R)m.sigma_a * n2;
+    o.x = s.x + T * s.vx + (R)0.5 * T * T * ax;
+    o.vx = s.vx + T * ax;
+    o.y = s.y + T * s.vy + (R)0.5 * T * T * ay;
+    o.vy = s.vy + T * ay;
+    wo = (R)m.p_s * w;
+  } else {
+    o.x = (R)m.rx0 + u1 * (R)(m.rx1 - m.rx0);
+    o.vx = (R)m.birth_vel_sigma * n1;
+    o.y = (R)m.ry0 + u2 * (R)(m.ry1 - m.ry0);
+    o.vy = (R)m.birth_vel_sigma * n2;
+    wo = (R)(m.birth_mass / (double)Jj);
+  }
+}
+
+// Systematic resampling: number of children whose pointer falls below Q_i,
+// c = #{t : floor((t 2^32 + U) Q_n / (L 2^32)) < Q_i}, with 128-bit integers.
+__device__ __forceinline__ int offspring_end(unsigned long long Qi, unsigned long long Qn, unsigned long long L,
+                                             uint32_t U) {
+  if (L == 0 || Qn == 0) return 0;
+  const unsigned __int128 X = ((unsigned __int128)Qi * L) << 32;
+  if (X == 0) return 0;
+  const unsigned long long V = (unsigned long long)((X - 1) / Qn);
+  const unsigned long long cc = V < (unsigned long long)U ? 0ull : ((V - U) >> 32) + 1ull;
+  return (int)(cc < L ? cc : L);
+}
+
+// Resample count and CDF scale of a PE from its mass, largest weight and size.
+__device__ __forceinline__ void resample_plan(const Model& m, int j, int n, double N, double wmax, int& L, int& s) {
+  L = 0;
+  s = 0;
+  if (n > 0 && wmax > 0.0) {
+    int e;
+    frexp(wmax, &e);
+    int c = 0;
+    while ((1LL << c) < (long long)n) ++c;
+    s = 52 - c - e;
+    long long Ll = llround(m.rho_pe * (N > 1.0 ? N : 1.0));
+    const long long lmax = m.pe_cap - births_of(m.J, m.K, j);
+    if (Ll > lmax) Ll = lmax;
+    if (Ll < 0) Ll = 0;
+    L = (int)Ll;
+  }
+}
+
+__device__ __forceinline__ uint32_t philox_u32(const Model& m, uint32_t a, unsigned long long step, uint32_t tag) {
+  return philox4x32_10(U4{a, (uint32_t)step, tag, (uint32_t)(step >> 32)}, (uint32_t)m.seed,
+                       (uint32_t)(m.seed >> 32)).a;
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (one per stage), instantiated for float and double.
 // ---------------------------------------------------------------------------
 template <class R> cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s);
@@ -269,6 +367,11 @@ template <class R> cudaError_t launch_resample(const Dev& d, const Model& m, con
 cudaError_t launch_advance_step(const Dev& d, cudaStream_t s);
 template <class R> cudaError_t prepare_kernels(const Model& m);
 cudaError_t prepare_exchange(const Model& m);
+template <class R> bool fused_eligible(const Model& m, int device);
+template <class R>
+cudaError_t launch_fused(const Dev& d, const Model& m, const void* Z, const int* zoff, int M1, int S, const R* noise,
+                         const uint32_t* u, const uint32_t* xu, R* out_states, int* out_labels, int* out_count,
+                         int cap, cudaStream_t s);
 int grid_items(const Model& m);
 
 }  // namespace phd

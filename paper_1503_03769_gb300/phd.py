@@ -22,6 +22,8 @@ PHD_OK, PHD_ERR_INVALID_ARG, PHD_ERR_CAPACITY, PHD_ERR_CUDA, PHD_ERR_TIMEOUT, PH
 PHD_MEAS_LINEAR, PHD_MEAS_RANGE_BEARING = 0, 1
 PHD_FP32, PHD_FP64 = 0, 1
 PHD_CK_LOCAL, PHD_CK_GLOBAL = 0, 1
+PHD_PATH_AUTO, PHD_PATH_STAGED, PHD_PATH_FUSED = 0, 1, 2
+_PATHS = {"auto": PHD_PATH_AUTO, "staged": PHD_PATH_STAGED, "fused": PHD_PATH_FUSED}
 
 
 class PhdError(RuntimeError):
@@ -45,6 +47,13 @@ class phd_config(ctypes.Structure):
         ("birth_vel_sigma", ctypes.c_double), ("particles_per_target", ctypes.c_double),
         ("exchange_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
     ]
+
+
+class phd_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("particles", ctypes.c_uint64),
+                ("measurements", ctypes.c_uint64), ("updates", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("timed_updates", ctypes.c_uint64),
+                ("update_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -72,6 +81,14 @@ ABI = {
     "phd_get_step": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint64)]),
     "phd_set_step": (ctypes.c_int, [_H, ctypes.c_uint64]),
     "phd_sync": (ctypes.c_int, [_H]),
+    "phd_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(phd_stats)]),
+    "phd_reset_stats": (ctypes.c_int, [_H]),
+    "phd_set_stage_timer": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "phd_step_inject": (ctypes.c_int, [_H, _P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32, _P, _I32P]),
+    "phd_run": (ctypes.c_int, [_H, _P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
+    "phd_set_path": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "phd_get_path": (ctypes.c_int, [_H, _I32P]),
+    "phd_get_predicted": (ctypes.c_int, [_H, _P, _P, _P, _I32P]),
 }
 
 _lib = None
@@ -220,6 +237,66 @@ class ParticlePHD:
             return states[:hc.value], labels[:hc.value]
         return states, labels, self._cnt
 
+    def _u32(self, a, shape=None):
+        if a is None:
+            return None
+        t = torch.as_tensor(np.ascontiguousarray(np.asarray(a, dtype=np.uint32)).view(np.int32), device=self.device)
+        return t.reshape(-1).contiguous()
+
+    def step_inject(self, Z, noise=None, u=None, xu=None, cap: Optional[int] = None):
+        """One step with injected random numbers (phd_step_inject); synchronises."""
+        cap = self.m_max if cap is None else int(cap)
+        Zt = self._real(Z, (-1, 2))
+        nz = None if noise is None else self._real(noise, (self.K * self.pe_cap, 4))
+        ut, xt = self._u32(u), self._u32(xu)
+        states = torch.empty((max(cap, 1), 4), dtype=self.dtype, device=self.device)
+        labels = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+        hc = ctypes.c_int32(0)
+        st = self.L.phd_step_inject(self.h, _ptr(Zt) if Zt.numel() else None, Zt.shape[0], _ptr(nz), _ptr(ut),
+                                    _ptr(xt), _ptr(states), _ptr(labels), cap, _ptr(self._cnt), ctypes.byref(hc))
+        self._check(st, "phd_step_inject", hc.value)
+        return states[:hc.value], labels[:hc.value]
+
+    def run(self, Zs, cap: Optional[int] = None, sync: bool = True):
+        """phd_run over a list of scans; returns per-scan (states, labels)."""
+        cap = self.m_max if cap is None else int(cap)
+        S = len(Zs)
+        rows = [np.asarray(z).reshape(-1, 2) for z in Zs]
+        off = np.zeros(S + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(r) for r in rows])
+        Zp = self._real(np.concatenate(rows) if off[-1] else np.zeros((1, 2)), (-1, 2))
+        offt = torch.as_tensor(off, device=self.device)
+        states = torch.empty((S, cap, 4), dtype=self.dtype, device=self.device)
+        labels = torch.empty((S, cap), dtype=torch.int32, device=self.device)
+        counts = torch.empty(S, dtype=torch.int32, device=self.device)
+        self._check(self.L.phd_run(self.h, _ptr(Zp), _ptr(offt), S, _ptr(states), _ptr(labels), _ptr(counts), cap),
+                    "phd_run")
+        self._keeprun = (Zp, offt)
+        if not sync:
+            return states, labels, counts
+        self.sync()
+        c = counts.cpu().numpy()
+        return [(states[s, :min(c[s], cap)], labels[s, :min(c[s], cap)]) for s in range(S)]
+
+    def set_path(self, path: str):
+        self._check(self.L.phd_set_path(self.h, _PATHS[path]), "phd_set_path")
+
+    def get_path(self) -> str:
+        v = ctypes.c_int32(0)
+        self._check(self.L.phd_get_path(self.h, ctypes.byref(v)), "phd_get_path")
+        return {PHD_PATH_STAGED: "staged", PHD_PATH_FUSED: "fused"}[v.value]
+
+    def get_predicted(self):
+        X = torch.empty((self.K, self.pe_cap, 4), dtype=self.dtype, device=self.device)
+        Wp = torch.empty((self.K, self.pe_cap), dtype=self.dtype, device=self.device)
+        Wu = torch.empty((self.K, self.pe_cap), dtype=self.dtype, device=self.device)
+        counts = (ctypes.c_int32 * self.K)()
+        self._check(self.L.phd_get_predicted(self.h, _ptr(X), _ptr(Wp), _ptr(Wu), counts), "phd_get_predicted")
+        c = list(counts)
+        Xn, Wpn, Wun = X.cpu().numpy(), Wp.cpu().numpy(), Wu.cpu().numpy()
+        return ([Xn[j, :c[j]] for j in range(self.K)], [Wpn[j, :c[j]] for j in range(self.K)],
+                [Wun[j, :c[j]] for j in range(self.K)])
+
     def step_host(self, Z: np.ndarray, out_states: np.ndarray, out_labels: np.ndarray) -> int:
         """phd_step_host on host numpy buffers; returns the estimate count."""
         npdt = np.float64 if self.dtype == torch.float64 else np.float32
@@ -289,7 +366,18 @@ class ParticlePHD:
     def sync(self):
         self._check(self.L.phd_sync(self.h), "phd_sync")
 
+    def stats(self) -> dict:
+        st = phd_stats()
+        self._check(self.L.phd_get_stats(self.h, ctypes.byref(st)), "phd_get_stats")
+        return {k: getattr(st, k) for k, _ in phd_stats._fields_}
 
-__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "make_config", "ParticlePHD", "PhdError",
+    def reset_stats(self):
+        self._check(self.L.phd_reset_stats(self.h), "phd_reset_stats")
+
+    def set_stage_timer(self, on: bool):
+        self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
+
+
+__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "phd_stats", "make_config", "ParticlePHD", "PhdError",
            "PHD_OK", "PHD_ERR_INVALID_ARG", "PHD_ERR_CAPACITY", "PHD_ERR_CUDA", "PHD_ERR_TIMEOUT",
            "PHD_ERR_STATE", "PHD_FP32", "PHD_FP64"]

@@ -62,16 +62,44 @@ def check_weights(w_gpu, w_ref, tol, what=""):
     return float((err[nz] / np.abs(w_ref[nz])).max()) if nz.any() else 0.0
 
 
-def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True):
-    """One filter step on the GPU with every stage compared to the oracle."""
+def gpu_stages(f, w, Z, noise, u, xu, path):
+    """Run one step on the GPU and collect its intermediates.
+
+    path "staged": phd_predict / phd_update / phd_extract / phd_resample with
+    the intermediates read between the calls; path "fused": one
+    phd_step_inject on the fused kernel, intermediates read afterwards."""
+    dt = npdtype(w)
+    g = {}
+    g["xs0"], g["ws0"] = f.get_state()
+    if path == "staged":
+        f.predict(torch.as_tensor(noise).cuda())
+        g["xp"], g["wp"] = f.get_state()
+        f.update(torch.as_tensor(np.asarray(Z, dt)).cuda())
+        g["C"], g["mass"] = f.get_update()
+        _, g["wu"] = f.get_state()
+        g["states"], g["labels"] = f.extract()
+        g["loc_s"], g["loc_l"] = f.get_local_estimates()
+        f.resample(u, xu)
+    else:
+        assert f.get_path() == "fused"
+        g["states"], g["labels"] = f.step_inject(np.asarray(Z, dt), noise, u, xu)
+        g["xp"], g["wp"], g["wu"] = f.get_predicted()
+        g["C"], g["mass"] = f.get_update()
+        g["loc_s"], g["loc_l"] = f.get_local_estimates()
+    g["par"], g["lx"] = f.get_resample()
+    g["xr"], g["wr"] = f.get_state()
+    return g
+
+
+def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
+    """Compare one step's GPU intermediates with the oracle, stage by stage,
+    the oracle always starting from the GPU's own input to that stage."""
     tol = tol_for(w)
     K = w.num_pe
     dt = npdtype(w)
     kap = oracle.kappa(m)
-    xs0, ws0 = f.get_state()
+    xs0, ws0, xp, wp, wu = g["xs0"], g["ws0"], g["xp"], g["wp"], g["wu"]
     # --- predict (Eq. 5-6)
-    f.predict(torch.as_tensor(noise).cuda())
-    xp, wp = f.get_state()
     nz = np.asarray(noise, np.float64).reshape(K, w.pe_cap, 4)
     for j in range(K):
         Jj = scenario.births_per_pe(w)[j]
@@ -82,9 +110,7 @@ def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True):
         np.testing.assert_allclose(xp[j], xo, rtol=0, atol=atol)
         check_weights(wp[j], wo, tol, f"predict PE {j}")
     # --- update (Eq. 7-8)
-    f.update(torch.as_tensor(np.asarray(Z, dt)).cuda())
-    C, mass = f.get_update()
-    xu_, wu = f.get_state()
+    C, mass = g["C"], g["mass"]
     M = len(Z)
     Zd = np.asarray(Z, np.float64)
     Cloc = [oracle.colsum(m, xp[j], wp[j], Zd) for j in range(K)]
@@ -107,18 +133,15 @@ def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True):
             rep.max_mass_rel = max(rep.max_mass_rel, rel)
             assert rel <= tol["mass_rel"], (j, mass[j], Nref)
     # --- extraction (Eq. 10-18) and fusion (Step 4)
-    states, labels = f.extract()
-    loc_s, loc_l = f.get_local_estimates()
-    exs = []
+    loc_s, loc_l = g["loc_s"], g["loc_l"]
     for j in range(K):
-        ex = oracle.extract(m, xp[j], wp[j], Zd, Cu[j], float(wu[j].astype(np.float64).sum()))
-        exs.append(ex)
+        Nk = float(wu[j].astype(np.float64).sum())
+        ex = oracle.extract(m, xp[j], wp[j], Zd, Cu[j], Nk)
         got = list(loc_l[j])
         want = list(ex.labels)
         if got != want:
             # acceptable only at a genuine tie: LT near a .5 boundary or the
             # boundary dW values within 1e-6 relative
-            Nk = float(wu[j].astype(np.float64).sum())
             dW = np.sort(ex.dW)[::-1]
             lt = max(len(got), len(want))
             near_half = abs(Nk - math.floor(Nk) - 0.5) < 1e-5 * max(1.0, Nk)
@@ -132,19 +155,17 @@ def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True):
                 rep.max_state_err = max(rep.max_state_err, float(e))
                 assert e <= tol["state_abs"], (j, p, loc_s[j][r], zi)
                 rep.compared_labels += 1
-    # fusion of the GPU's own local estimates (bit-level inputs identical)
+    # fusion of the GPU's own local estimates (identical inputs)
     gl = [oracle.Extraction(np.asarray(loc_l[j], np.int32), np.asarray(loc_s[j], np.float64),
                             np.zeros(M), 0.0, len(loc_l[j])) for j in range(K)]
     fl, fz = oracle.fuse(gl, M)
-    assert list(labels.cpu().numpy()) == list(fl), (labels, fl)
-    np.testing.assert_allclose(states.cpu().numpy().astype(np.float64), fz,
+    assert list(g["labels"].cpu().numpy()) == list(fl), (g["labels"], fl)
+    np.testing.assert_allclose(g["states"].cpu().numpy().astype(np.float64), fz,
                                rtol=0, atol=1e-4 if dt == np.float32 else 1e-9)
     # --- resampling (exact CDF) + ring exchange
-    f.resample(u, xu)
     if not check_resample:
         return
-    par, lx = f.get_resample()
-    xr, wr = f.get_state()
+    par, lx, xr, wr = g["par"], g["lx"], g["xr"], g["wr"]
     rxs, rws = [], []
     for j in range(K):
         rho = w.particles_per_target / K
@@ -160,3 +181,10 @@ def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True):
         assert len(xr[j]) == len(rxs[j])
         np.testing.assert_array_equal(xr[j].astype(np.float64), rxs[j].astype(dt).astype(np.float64))
         check_weights(wr[j], rws[j], tol, f"resampled weights PE {j}")
+
+
+def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True, path="staged"):
+    """One filter step on the GPU with every stage compared to the oracle."""
+    g = gpu_stages(f, w, Z, noise, u, xu, path)
+    check_step(w, m, Z, noise, u, xu, g, rep, check_resample)
+    return g
