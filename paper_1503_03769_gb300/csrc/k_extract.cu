@@ -6,7 +6,8 @@
 //   form), and the LT_j largest dW by rank counting: rank_p = #{q : dW_q > dW_p
 //   or (dW_q = dW_p and q < p)}; label p is taken when dW_p > 0 and
 //   rank_p < LT_j.  O(M^2) comparisons per PE on M <= 4096 values in shared
-//   memory.
+//   memory, made on the FP64 values' bit patterns as unsigned integers (same
+//   order, integer instructions).
 // k_selsum (pass 3, selected labels only): per label the sums of
 //   e w, e w (x - r_x), e w vx, e w (y - r_y), e w vy over the PE's particles,
 //   with e = 2^-q the unnormalised likelihood and r the measurement's
@@ -24,33 +25,33 @@ namespace phd {
 template <class R>
 __global__ void __launch_bounds__(1024) k_select(Dev d, Model m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* dW = reinterpret_cast<double*>(smem_raw);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
   const int j = blockIdx.x;
   const int M = *d.M;
   if (threadIdx.x == 0) npos_s = 0;
   for (int p = threadIdx.x; p < M; p += blockDim.x) {
     const double den = m.kappa + d.Cused[j * m.m_max + p];
-    const double v = den > 0.0 ? d.C[j * m.m_max + p] / den : 0.0;
-    dW[p] = v;
+    key[p] = order_key(den > 0.0 ? d.C[j * m.m_max + p] / den : 0.0);
   }
   __syncthreads();
   const double mass = d.mass[j];
   int npos_t = 0;
-  for (int p = threadIdx.x; p < M; p += blockDim.x) npos_t += dW[p] > 0.0 ? 1 : 0;
-  atomicAdd(&npos_s, npos_t);
+  for (int p = threadIdx.x; p < M; p += blockDim.x) npos_t += key[p] > 0ull ? 1 : 0;
+  npos_t = __reduce_add_sync(0xffffffffu, npos_t);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&npos_s, npos_t);
   __syncthreads();
   long long LT = llround(mass);
   if (LT > npos_s) LT = npos_s;
   if (LT < 0) LT = 0;
   for (int p = threadIdx.x; p < M; p += blockDim.x) {
-    const double v = dW[p];
+    const unsigned long long v = key[p];
     int rank = 0;
     for (int q = 0; q < M; ++q) {
-      const double u = dW[q];
+      const unsigned long long u = key[q];
       rank += (u > v || (u == v && q < p)) ? 1 : 0;
     }
-    const bool take = v > 0.0 && rank < LT;
+    const bool take = v > 0ull && rank < LT;
     d.selrank[j * m.m_max + p] = take ? rank : -1;
     if (take) d.sel[j * m.m_max + rank] = p;
   }
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
 template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
-  k_select<R><<<m.K, 1024, sizeof(double) * (size_t)m.m_max, s>>>(d, m);
+  k_select<R><<<m.K, 1024, sizeof(unsigned long long) * (size_t)m.m_max, s>>>(d, m);
   k_selsum<R><<<grid_items(m), kThreads, 0, s>>>(d, m);
   long tot = (long)m.K * m.m_max;
   int b = (int)((tot + 255) / 256);

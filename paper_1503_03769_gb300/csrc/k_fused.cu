@@ -108,7 +108,7 @@ __host__ __device__ inline FusedSmem fused_smem(int P, int Mm) {
   L.ginv = take(sizeof(R) * Mm);
   L.Cd = take(sizeof(double) * Mm);
   L.Cu = take(sizeof(double) * Mm);
-  L.dW = take(sizeof(double) * Mm);
+  L.dW = take(sizeof(unsigned long long) * Mm);
   L.sel = take(sizeof(int) * Mm);
   L.selrank = take(sizeof(int) * Mm);
   L.red = take(sizeof(double) * kFusedThreads);
@@ -116,46 +116,67 @@ __host__ __device__ inline FusedSmem fused_smem(int P, int Mm) {
   return L;
 }
 
-// Deterministic block sum of one double per thread (fixed order).
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+// Block reduction of per-thread values in the kernel's precision: within each
+// warp in R, the 32 warp totals in FP64 by warp 0 (fixed order), result
+// broadcast to every thread.  In FP32 mode the FP64 work is 5 shuffle-adds
+// in one warp; in FP64 mode everything is FP64.
+template <class R>
+__device__ __forceinline__ double block_sum_r(R v, R* wred, double* out) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? (double)wred[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *out = t;
+  }
   __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int k = 0; k < nw; ++k) s += red[k];
-  __syncthreads();
-  return s;
+  return *out;
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+template <class R>
+__device__ __forceinline__ R block_max_r(R v, R* wred) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const R u = __shfl_down_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int k = 0; k < nw; ++k) s = fmax(s, red[k]);
+  R r = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = wred[k] > r ? wred[k] : r;
   __syncthreads();
-  return s;
+  return r;
 }
 
-__device__ __forceinline__ int block_sum_int(int v, double* red) {
-  return (int)block_sum((double)v, red);
+__device__ __forceinline__ int block_sum_i(int v, int* ired) {
+  v = __reduce_add_sync(0xffffffffu, v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) ired[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += ired[k];
+  __syncthreads();
+  return r;
 }
 
 // Cartesian point of a measurement (offset origin of the labelled sums).
 template <class R>
-__device__ __forceinline__ void meas_point_f(const Model& m, V2<R> z, R& rx, R& ry) {
-  if (m.meas_model == 0) {
+__device__ __forceinline__ void meas_point_f(const Cst<R>& c, int rb, V2<R> z, R& rx, R& ry) {
+  if (rb == 0) {
     rx = z.a;
     ry = z.b;
   } else {
     R sn, cs;
     sincos(z.b, &sn, &cs);
-    rx = (R)m.sx + z.a * cs;
-    ry = (R)m.sy + z.a * sn;
+    rx = c.sx + z.a * cs;
+    ry = c.sy + z.a * sn;
   }
 }
 
@@ -163,8 +184,7 @@ __device__ __forceinline__ void meas_point_f(const Model& m, V2<R> z, R& rx, R& 
 // PEs, FP64 mean of their local states, ascending label order.
 template <class R>
 __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* out_lab, int cap, int* count,
-                        double* red) {
-  int* wsum = reinterpret_cast<int*>(red);
+                        int* wsum) {
   __shared__ int carry_s;
   const St4<R>* est = static_cast<const St4<R>*>(d.est_local);
   if (threadIdx.x == 0) carry_s = 0;
@@ -173,8 +193,10 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
   for (int p0 = 0; p0 < M; p0 += blockDim.x) {
     const int p = p0 + threadIdx.x;
     int votes = 0;
-    if (p < M)
+    if (p < M) {
+#pragma unroll 8
       for (int k = 0; k < m.K; ++k) votes += d.selrank[k * m.m_max + p] >= 0 ? 1 : 0;
+    }
     const int valid = (p < M && 2 * votes > m.K) ? 1 : 0;
     int incl = valid;
     for (int o = 1; o < 32; o <<= 1) {
@@ -195,18 +217,19 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
     const int carry = carry_s;
     const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
     if (valid && idx < cap) {
-      double a[4] = {0, 0, 0, 0};
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
       for (int k = 0; k < m.K; ++k) {
         const int r = d.selrank[k * m.m_max + p];
         if (r >= 0) {
           const St4<R> e = est[k * m.m_max + r];
-          a[0] += (double)e.x;
-          a[1] += (double)e.vx;
-          a[2] += (double)e.y;
-          a[3] += (double)e.vy;
+          a0 += (double)e.x;
+          a1 += (double)e.vx;
+          a2 += (double)e.y;
+          a3 += (double)e.vy;
         }
       }
-      out[idx] = St4<R>{(R)(a[0] / votes), (R)(a[1] / votes), (R)(a[2] / votes), (R)(a[3] / votes)};
+      out[idx] = St4<R>{(R)(a0 / votes), (R)(a1 / votes), (R)(a2 / votes), (R)(a3 / votes)};
       out_lab[idx] = p;
     }
     __syncthreads();
@@ -234,26 +257,31 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   R* ginv = reinterpret_cast<R*>(smem + SL.ginv);
   double* Cd = reinterpret_cast<double*>(smem + SL.Cd);
   double* Cu = reinterpret_cast<double*>(smem + SL.Cu);
-  double* dW = reinterpret_cast<double*>(smem + SL.dW);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem + SL.dW);
   int* sel = reinterpret_cast<int*>(smem + SL.sel);
   int* selrank = reinterpret_cast<int*>(smem + SL.selrank);
-  double* red = reinterpret_cast<double*>(smem + SL.red);
+  R* wred = reinterpret_cast<R*>(smem + SL.red);
+  int* ired = reinterpret_cast<int*>(smem + SL.red + 256);
   // resampling arrays alias the pair-pass block (sh0 .. sw)
   unsigned long long* Q = reinterpret_cast<unsigned long long*>(smem + SL.sh0);
   int* cend = reinterpret_cast<int*>(smem + SL.sh0 + sizeof(unsigned long long) * m.pe_cap);
   int* perm = cend + m.pe_cap;
-  __shared__ double bcast_d[2];
-  __shared__ int bcast_i[4];
+  __shared__ double bN;
+  __shared__ int bL, bS;
+  __shared__ R bW;
 
   const int j = blockIdx.x;
-  const int T = blockDim.x, tid = threadIdx.x;
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
   const long base = (long)j * m.pe_cap;
   const int Jj = births_of(m.J, m.K, j);
   const unsigned long long step0 = *d.step;
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
+  const Cst<R> cc = consts<R>(m);
+  const R bw = birth_weight<R>(cc, m, j);
   const double cs = m.p_d * m.cnorm;
-  const R miss = (R)(1.0 - m.p_d);
+  const R csr = (R)cs;
+  const R kapr = (R)m.kappa;
   St4<R>* gx = static_cast<St4<R>*>(d.x);
   R* gw = static_cast<R*>(d.w);
   St4<R>* gxp = static_cast<St4<R>*>(d.x_alt);
@@ -286,7 +314,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       const bool surv = i < n;
       St4<R> o;
       R wo;
-      predict_slot<R>(m, surv, surv ? gx[base + i] : St4<R>{0, 0, 0, 0}, surv ? gw[base + i] : (R)0, Jj, n1, n2,
+      predict_slot<R>(cc, surv, surv ? gx[base + i] : St4<R>{0, 0, 0, 0}, surv ? gw[base + i] : (R)0, bw, n1, n2,
                       u1, u2, o, wo);
       gxp[base + i] = o;
       gwp[base + i] = wo;
@@ -297,37 +325,52 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       shl[i] = h.h1lo;
       sw[i] = wo;
     }
-    if (tid == 0) d.n_pred[j] = np;
+    if (tid == 0) {
+      d.n_pred[j] = np;
+      atomicAdd(&d.stats[0], (unsigned long long)np * (unsigned long long)M);
+      atomicAdd(&d.stats[1], (unsigned long long)np);
+      if (j == 0) {
+        atomicAdd(&d.stats[2], (unsigned long long)M);
+        atomicAdd(&d.stats[3], 1ull);
+      }
+    }
     __syncthreads();
-    // ---- pass 1: C^j_p (Eq. 7)
+    // ---- pass 1: C^j_p (Eq. 7).  Groups of nsplit consecutive lanes share a
+    // measurement and split the particles; FP32 runs of <= 256 pairs per
+    // thread, FP64 across runs and across the group (shuffle tree).
     if (M > 0) {
-      const int mper = M < T ? M : T;
-      const int nsplit = T / mper;
-      const int pl = tid % mper, split = tid / mper;
+      const int nsplit = pow2_floor(min(32, max(1, T / M)));
+      const int mper = T / nsplit;
+      const int pl = tid / nsplit, split = tid % nsplit;
       for (int p0 = 0; p0 < M; p0 += mper) {
         const int p = p0 + pl;
-        R acc = 0;
-        if (split < nsplit && p < M) {
+        double acc = 0.0;
+        if (p < M) {
           const V2<R> z = zs[p];
-          R part = 0;
-          int k = 0;
+          R mid = 0, part = 0;
+          int k = 0, kk = 0;
           for (int i = split; i < np; i += nsplit) {
             const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
             part = fma(exp2_neg(q), sw[i], part);
-            if (++k == 32) { acc += part; part = 0; k = 0; }
+            if (++k == 32) {
+              mid += part;
+              part = 0;
+              k = 0;
+              if (++kk == 8) {
+                acc += (double)mid;
+                mid = 0;
+                kk = 0;
+              }
+            }
           }
-          acc += part;
+          acc += (double)(mid + part);
         }
-        red[tid] = (double)acc;
-        __syncthreads();
+        for (int o = nsplit >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, nsplit);
         if (split == 0 && p < M) {
-          double c = red[tid];
-          for (int k = 1; k < nsplit; ++k) c += red[tid + k * mper];
-          c *= cs;
+          const double c = acc * cs;
           Cd[p] = c;
           d.C[j * m.m_max + p] = c;
         }
-        __syncthreads();
       }
     }
     if (m.ck_global && m.K > 1) {
@@ -338,18 +381,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         Cu[p] = mean / (double)m.K;
       }
     } else {
+      __syncthreads();
       for (int p = tid; p < M; p += T) Cu[p] = Cd[p];
     }
     __syncthreads();
+    // ginv in the kernel's precision; dW order keys in FP64 (one divide per
+    // measurement, by M threads)
     for (int p = tid; p < M; p += T) {
       const double den = m.kappa + Cu[p];
-      ginv[p] = den > 0.0 ? (R)(cs / den) : (R)0;
-      dW[p] = den > 0.0 ? Cd[p] / den : 0.0;
+      ginv[p] = den > 0.0 ? csr / (R)den : (R)0;
+      key[p] = order_key(den > 0.0 ? Cd[p] / den : 0.0);
       d.Cused[j * m.m_max + p] = Cu[p];
     }
     __syncthreads();
     // ---- pass 2: updated weights (Eq. 8), mass and largest weight
-    double msum = 0.0, mmax = 0.0;
+    R msum = 0, mmax = 0;
     for (int i = tid; i < np; i += T) {
       const R h0 = sh0[i], h1 = sh1[i], hl = shl[i];
       R acc = 0, part = 0;
@@ -360,31 +406,31 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         if (++k == 64) { acc += part; part = 0; k = 0; }
       }
       acc += part;
-      const R wv = (miss + acc) * sw[i];
+      const R wv = (cc.miss + acc) * sw[i];
       swu[i] = wv;
       gwu[base + i] = wv;
-      msum += (double)wv;
-      mmax = fmax(mmax, (double)wv);
+      msum += wv;
+      mmax = wv > mmax ? wv : mmax;
     }
-    const double N = block_sum(msum, red);
-    const double wmax = block_max(mmax, red);
+    const double N = block_sum_r<R>(msum, wred, &bN);
+    const R wmaxr = block_max_r<R>(mmax, wred);
     if (tid == 0) d.mass[j] = N;
-    // ---- selection (Step 3)
+    // ---- selection (Step 3): rank of dW by integer compares of the keys
     int npos_t = 0;
-    for (int p = tid; p < M; p += T) npos_t += dW[p] > 0.0 ? 1 : 0;
-    const int npos = block_sum_int(npos_t, red);
+    for (int p = tid; p < M; p += T) npos_t += key[p] > 0ull ? 1 : 0;
+    const int npos = block_sum_i(npos_t, ired);
     long long LTl = llround(N);
     if (LTl > npos) LTl = npos;
     if (LTl < 0) LTl = 0;
     const int LT = (int)LTl;
     for (int p = tid; p < M; p += T) {
-      const double v = dW[p];
+      const unsigned long long v = key[p];
       int rank = 0;
       for (int q = 0; q < M; ++q) {
-        const double u = dW[q];
+        const unsigned long long u = key[q];
         rank += (u > v || (u == v && q < p)) ? 1 : 0;
       }
-      const bool take = v > 0.0 && rank < LT;
+      const bool take = v > 0ull && rank < LT;
       selrank[p] = take ? rank : -1;
       d.selrank[j * m.m_max + p] = take ? rank : -1;
       if (take) {
@@ -394,48 +440,45 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     }
     if (tid == 0) d.nsel[j] = LT;
     __syncthreads();
-    // ---- pass 3: labelled sums for the selected labels (Eq. 18)
+    // ---- pass 3: labelled sums for the selected labels (Eq. 18); groups of
+    // nsplit lanes per label, FP32 sums of offsets from the label's point,
+    // shuffle-reduced in FP32, zeta formed in FP64 by the group's lane 0
     if (LT > 0) {
-      const int mper = LT < T ? LT : T;
-      const int nsplit = T / mper;
-      const int rl = tid % mper, split = tid / mper;
+      const int nsplit = pow2_floor(min(32, max(1, T / LT)));
+      const int mper = T / nsplit;
+      const int rl = tid / nsplit, split = tid % nsplit;
       for (int r0 = 0; r0 < LT; r0 += mper) {
         const int r = r0 + rl;
-        R acc5[5] = {0, 0, 0, 0, 0};
+        R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
         R px = 0, py = 0;
-        if (split < nsplit && r < LT) {
-          const int p = sel[r];
-          const V2<R> z = zs[p];
-          meas_point_f<R>(m, z, px, py);
+        if (r < LT) {
+          const V2<R> z = zs[sel[r]];
+          meas_point_f<R>(cc, m.meas_model, z, px, py);
           for (int i = split; i < np; i += nsplit) {
             const R ew = exp2_neg(qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i])) * sw[i];
             const St4<R> st = sx[i];
-            acc5[0] += ew;
-            acc5[1] = fma(ew, st.x - px, acc5[1]);
-            acc5[2] = fma(ew, st.vx, acc5[2]);
-            acc5[3] = fma(ew, st.y - py, acc5[3]);
-            acc5[4] = fma(ew, st.vy, acc5[4]);
+            s0 += ew;
+            s1 = fma(ew, st.x - px, s1);
+            s2 = fma(ew, st.vx, s2);
+            s3 = fma(ew, st.y - py, s3);
+            s4 = fma(ew, st.vy, s4);
           }
         }
-        double tot[5];
-        for (int c = 0; c < 5; ++c) {
-          red[tid] = (double)acc5[c];
-          __syncthreads();
-          tot[c] = 0.0;
-          if (split == 0 && r < LT) {
-            double t = red[tid];
-            for (int k = 1; k < nsplit; ++k) t += red[tid + k * mper];
-            tot[c] = t;
-          }
-          __syncthreads();
+        for (int o = nsplit >> 1; o > 0; o >>= 1) {
+          s0 += __shfl_down_sync(0xffffffffu, s0, o, nsplit);
+          s1 += __shfl_down_sync(0xffffffffu, s1, o, nsplit);
+          s2 += __shfl_down_sync(0xffffffffu, s2, o, nsplit);
+          s3 += __shfl_down_sync(0xffffffffu, s3, o, nsplit);
+          s4 += __shfl_down_sync(0xffffffffu, s4, o, nsplit);
         }
         if (split == 0 && r < LT) {
           St4<R> o;
-          if (tot[0] > 0.0) {
-            o.x = (R)((double)px + tot[1] / tot[0]);
-            o.vx = (R)(tot[2] / tot[0]);
-            o.y = (R)((double)py + tot[3] / tot[0]);
-            o.vy = (R)(tot[4] / tot[0]);
+          if (s0 > (R)0) {
+            const double c0 = (double)s0;
+            o.x = (R)((double)px + (double)s1 / c0);
+            o.vx = (R)((double)s2 / c0);
+            o.y = (R)((double)py + (double)s3 / c0);
+            o.vy = (R)((double)s4 / c0);
           } else {
             o = St4<R>{px, (R)0, py, (R)0};
           }
@@ -443,22 +486,28 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         }
       }
     }
-    __syncthreads();
     // ---- resampling (Step 5): exact integer CDF, offspring counts, gather
-    int Lc, sc;
-    resample_plan(m, j, np, N, wmax, Lc, sc);
+    if (tid == 0) {
+      int Lc, sc;
+      resample_plan(m, j, np, N, (double)wmaxr, Lc, sc);
+      bL = Lc;
+      bS = sc;
+      bW = Lc > 0 ? (R)(N / (double)Lc) : (R)0;
+    }
+    __syncthreads();
+    const int Lc = bL, sc = bS;
     {
       constexpr int IT = 4;
       unsigned long long carry = 0ull;
-      unsigned long long* wt = reinterpret_cast<unsigned long long*>(red);
-      const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+      unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem + SL.red);
+      const int wid = tid >> 5, nw = T >> 5;
       for (int c0 = 0; c0 < np; c0 += T * IT) {
         unsigned long long q[IT];
         unsigned long long run = 0ull;
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
           const int i = c0 + tid * IT + k;
-          q[k] = i < np ? (unsigned long long)floor(ldexp((double)swu[i], sc)) : 0ull;
+          q[k] = i < np ? scaled_floor(swu[i], sc) : 0ull;
           run += q[k];
           q[k] = run;
         }
@@ -492,7 +541,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     const unsigned long long Qn = np > 0 ? Q[np - 1] : 0ull;
     for (int i = tid; i < np; i += T) cend[i] = offspring_end(Q[i], Qn, (unsigned long long)Lc, U);
     __syncthreads();
-    const R wnew = Lc > 0 ? (R)(N / (double)Lc) : (R)0;
+    const R wnew = bW;
     for (int t = tid; t < Lc; t += T) {
       int lo = 0, hi = np - 1;
       while (lo < hi) {
@@ -521,12 +570,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         lx = (int)floor(m.exchange_frac * (double)nmin);
         if (j == 0 && tid == 0) *d.lx = lx;
         if (lx > 0) {
+          // the draws are independent: make them in parallel, swap serially
+          unsigned int* ud = reinterpret_cast<unsigned int*>(cend);
           for (int i = tid; i < Lc; i += T) perm[i] = i;
+          for (int t = tid; t < lx; t += T)
+            ud[t] = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
           __syncthreads();
           if (tid == 0) {
             for (int t = 0; t < lx; ++t) {
-              const uint32_t uu = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
-              const int r = t + (int)(((unsigned long long)uu * (unsigned long long)(Lc - t)) >> 32);
+              const int r = t + (int)(((unsigned long long)ud[t] * (unsigned long long)(Lc - t)) >> 32);
               const int tmp = perm[t];
               perm[t] = perm[r];
               perm[r] = tmp;
@@ -543,7 +595,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           }
         }
       }
-      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, red);
+      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired);
       if (!grid_sync(d)) return;
       if (xchg && lx > 0) {
         const int from = (j + m.K - 1) % m.K;
@@ -556,7 +608,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         }
       }
     } else {
-      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, red);
+      __syncthreads();
+      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired);
     }
     if (tid == 0) d.n_cur[j] = n;
     __syncthreads();

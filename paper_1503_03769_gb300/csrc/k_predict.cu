@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
   St4<R>* __restrict__ xp = static_cast<St4<R>*>(d.x_alt);
   R* __restrict__ wp = static_cast<R*>(d.w_alt);
   const unsigned long long step = *d.step;
+  const Cst<R> c = consts<R>(m);
   const long total = (long)m.K * m.pe_cap;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / m.pe_cap);
@@ -38,7 +39,8 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
     const bool surv = i < L;
     St4<R> o;
     R wo;
-    predict_slot<R>(m, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, Jj, n1, n2, u1, u2, o, wo);
+    predict_slot<R>(c, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, birth_weight<R>(c, m, j), n1, n2,
+                    u1, u2, o, wo);
     xp[g] = o;
     wp[g] = wo;
   }

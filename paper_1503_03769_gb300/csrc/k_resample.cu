@@ -32,12 +32,22 @@ __global__ void __launch_bounds__(256) k_rs_mass(Dev d, Model m) {
   const int j = blockIdx.x;
   const int n = d.n_pred[j];
   const R* w = static_cast<const R*>(d.wu) + (long)j * m.pe_cap;
-  double s = 0.0, mx = 0.0;
+  // FP32 runs of 64 weights per thread, FP64 across runs and threads
+  double s = 0.0;
+  R run = 0, mxr = 0;
+  int k = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = (double)w[i];
-    s += v;
-    mx = fmax(mx, v);
+    const R v = w[i];
+    run += v;
+    mxr = v > mxr ? v : mxr;
+    if (++k == 64) {
+      s += (double)run;
+      run = 0;
+      k = 0;
+    }
   }
+  s += (double)run;
+  double mx = (double)mxr;
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_down_sync(0xffffffffu, s, o);
     mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
@@ -80,7 +90,7 @@ __global__ void __launch_bounds__(1024) k_rs_scan(Dev d, Model m) {
 #pragma unroll
     for (int k = 0; k < IT; ++k) {
       const int i = c0 + threadIdx.x * IT + k;
-      q[k] = i < n ? (unsigned long long)floor(ldexp((double)w[i], s)) : 0ull;
+      q[k] = i < n ? scaled_floor(w[i], s) : 0ull;
       run += q[k];
       q[k] = run;
     }
@@ -163,13 +173,16 @@ __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
   const int lx = (int)floor(m.exchange_frac * (double)nmin);
   if (j == 0 && threadIdx.x == 0) *d.lx = lx;
   if (lx <= 0) return;
+  // perm in the first n ints, the (independent) draws after it; swaps serial
+  unsigned int* ud = reinterpret_cast<unsigned int*>(perm + n);
+  const unsigned long long st = *d.step;
   for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
+  for (int t = threadIdx.x; t < lx; t += blockDim.x)
+    ud[t] = xu ? xu[(long)j * m.pe_cap + t] : philox_u32(m, (uint32_t)((long)j * m.pe_cap + t), st, kTagExchange);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned long long st = *d.step;
     for (int t = 0; t < lx; ++t) {
-      const uint32_t u = xu ? xu[(long)j * m.pe_cap + t]
-                            : philox_u32(m, (uint32_t)((long)j * m.pe_cap + t), st, kTagExchange);
+      const uint32_t u = ud[t];
       const int r = t + (int)(((unsigned long long)u * (unsigned long long)(n - t)) >> 32);
       const int tmp = perm[t];
       perm[t] = perm[r];
@@ -232,7 +245,7 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
     if (bx < 1) bx = 1;
     if (bx > 152 * 8) bx = 152 * 8;
-    k_xplan<<<m.K, 256, sizeof(int) * (size_t)m.pe_cap, s>>>(d, m, xu);
+    k_xplan<<<m.K, 256, sizeof(int) * 2 * (size_t)m.pe_cap, s>>>(d, m, xu);
     k_xout<R><<<bx, 256, 0, s>>>(d, m);
     k_xin<R><<<bx, 256, 0, s>>>(d, m);
   }
@@ -246,7 +259,7 @@ cudaError_t launch_advance_step(const Dev& d, cudaStream_t s) {
 
 cudaError_t prepare_exchange(const Model& m) {
   return cudaFuncSetAttribute(k_xplan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(int) * (size_t)m.pe_cap));
+                              (int)(sizeof(int) * 2 * (size_t)m.pe_cap));
 }
 
 template cudaError_t launch_resample<float>(const Dev&, const Model&, const uint32_t*, const uint32_t*, cudaStream_t);

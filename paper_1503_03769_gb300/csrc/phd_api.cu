@@ -134,8 +134,8 @@ const char* check_config(const phd_config& c) {
   if (!(c.birth_vel_sigma >= 0)) return "birth_vel_sigma";
   if (!(c.particles_per_target > 0) || !std::isfinite(c.particles_per_target)) return "particles_per_target";
   if (!(c.exchange_frac >= 0 && c.exchange_frac < 0.5)) return "exchange_frac must be in [0, 0.5)";
-  if (c.num_pe > 1 && c.exchange_frac > 0 && c.pe_cap > 16384)
-    return "pe_cap must be <= 16384 when the ring exchange is on";
+  if (c.num_pe > 1 && c.exchange_frac > 0 && c.pe_cap > 24576)
+    return "pe_cap must be <= 24576 when the ring exchange is on";
   return nullptr;
 }
 
@@ -172,6 +172,22 @@ Model make_model(const phd_config& c) {
   m.a1 = std::sqrt(0.5 * kLog2e) / c.sigma_z[1];
   m.cnorm = 1.0 / (2.0 * kPi * c.sigma_z[0] * c.sigma_z[1]);
   m.seed = c.seed;
+  m.f_dt = (float)c.dt;
+  m.f_sigma_a = (float)c.sigma_a;
+  m.f_ps = (float)c.p_s;
+  m.f_rx0 = (float)c.region[0];
+  m.f_rw = (float)(c.region[1] - c.region[0]);
+  m.f_ry0 = (float)c.region[2];
+  m.f_rh = (float)(c.region[3] - c.region[2]);
+  m.f_bv = (float)c.birth_vel_sigma;
+  m.f_sx = (float)c.sensor[0];
+  m.f_sy = (float)c.sensor[1];
+  m.f_miss = (float)(1.0 - c.p_d);
+  const int jlo = c.birth_count / c.num_pe;
+  m.bw_lo = jlo > 0 ? c.birth_mass / (double)jlo : 0.0;
+  m.bw_hi = c.birth_mass / (double)(jlo + 1);
+  m.f_bw_lo = (float)m.bw_lo;
+  m.f_bw_hi = (float)m.bw_hi;
   return m;
 }
 

@@ -40,7 +40,24 @@ struct Model {
   double a0, a1;         // sqrt(log2(e) / 2) / sigma per measurement coordinate
   double cnorm;          // 1 / (2 pi s0 s1)
   uint64_t seed;
+  // FP32 copies of the per-particle constants (FP64 is ~1/60 of the FP32 rate
+  // on this part: no conversion in the FP32 kernels' inner code)
+  float f_dt, f_sigma_a, f_ps, f_rx0, f_rw, f_ry0, f_rh, f_bv, f_sx, f_sy, f_miss;
+  float f_bw_lo, f_bw_hi;  // birth weight nu_b / J_j for J_j = J / K and J / K + 1
+  double bw_lo, bw_hi;
 };
+
+// Per-particle model constants in the kernel's precision.
+template <class R> struct Cst { R dt, sa, ps, rx0, rw, ry0, rh, bv, sx, sy, miss, bw_lo, bw_hi; };
+template <class R> __device__ __forceinline__ Cst<R> consts(const Model& m);
+template <> __device__ __forceinline__ Cst<float> consts<float>(const Model& m) {
+  return Cst<float>{m.f_dt, m.f_sigma_a, m.f_ps, m.f_rx0, m.f_rw, m.f_ry0, m.f_rh, m.f_bv, m.f_sx, m.f_sy,
+                    m.f_miss, m.f_bw_lo, m.f_bw_hi};
+}
+template <> __device__ __forceinline__ Cst<double> consts<double>(const Model& m) {
+  return Cst<double>{m.dt, m.sigma_a, m.p_s, m.rx0, m.rx1 - m.rx0, m.ry0, m.ry1 - m.ry0, m.birth_vel_sigma, m.sx,
+                     m.sy, 1.0 - m.p_d, m.bw_lo, m.bw_hi};
+}
 
 // Workspace carve (device pointers).  Real-typed arrays are void* and cast by
 // the kernels' Real type.
@@ -199,7 +216,7 @@ __device__ __forceinline__ H3<float> meas_h<float>(const Model& m, const St4<flo
     h.h1 = st.y;
     h.h1lo = 0.0f;
   } else {
-    const float px = st.x - (float)m.sx, py = st.y - (float)m.sy;
+    const float px = st.x - m.f_sx, py = st.y - m.f_sy;
     h.h0 = sqrtf(fmaf(px, px, py * py));
     bearing_df(px, py, tab, h.h1, h.h1lo);
   }
@@ -300,23 +317,65 @@ __device__ __forceinline__ void draw_noise(const Model& m, const R* noise, long 
 }
 
 template <class R>
-__device__ __forceinline__ void predict_slot(const Model& m, bool survivor, const St4<R>& s, R w, int Jj,
-                                             R n1, R n2, R u1, R u2, St4<R>& o, R& wo) {
+__device__ __forceinline__ void predict_slot(const Cst<R>& c, bool survivor, const St4<R>& s, R w, R bw, R n1, R n2,
+                                             R u1, R u2, St4<R>& o, R& wo) {
   if (survivor) {
-    const R T = (R)m.dt;
-    const R ax = (R)m.sigma_a * n1, ay = (R)m.sigma_a * n2;
+    const R T = c.dt;
+    const R ax = c.sa * n1, ay = c.sa * n2;
     o.x = s.x + T * s.vx + (R)0.5 * T * T * ax;
     o.vx = s.vx + T * ax;
     o.y = s.y + T * s.vy + (R)0.5 * T * T * ay;
     o.vy = s.vy + T * ay;
-    wo = (R)m.p_s * w;
+    wo = c.ps * w;
   } else {
-    o.x = (R)m.rx0 + u1 * (R)(m.rx1 - m.rx0);
-    o.vx = (R)m.birth_vel_sigma * n1;
-    o.y = (R)m.ry0 + u2 * (R)(m.ry1 - m.ry0);
-    o.vy = (R)m.birth_vel_sigma * n2;
-    wo = (R)(m.birth_mass / (double)Jj);
+    o.x = c.rx0 + u1 * c.rw;
+    o.vx = c.bv * n1;
+    o.y = c.ry0 + u2 * c.rh;
+    o.vy = c.bv * n2;
+    wo = bw;
   }
+}
+
+// Birth weight nu_b / J_j of PE j.
+template <class R> __device__ __forceinline__ R birth_weight(const Cst<R>& c, const Model& m, int j) {
+  return (j < m.J % m.K) ? c.bw_hi : c.bw_lo;
+}
+
+// floor(w 2^s) for a finite w >= 0, exactly, from the bits of w (the value
+// an FP64 multiply by 2^s followed by floor gives; no FP64 instruction).
+__device__ __forceinline__ unsigned long long scaled_floor(float w, int s) {
+  const unsigned int b = __float_as_uint(w);
+  int e = (int)((b >> 23) & 0xffu);
+  unsigned long long mant = b & 0x7fffffu;
+  if (e == 0) {
+    if (mant == 0) return 0ull;
+    e = 1;
+  } else {
+    mant |= 0x800000ull;
+  }
+  const int sh = e - 150 + s;   // w = mant 2^(e - 150)
+  if (sh >= 0) return sh < 64 ? mant << sh : 0ull;
+  return -sh < 64 ? mant >> (-sh) : 0ull;
+}
+__device__ __forceinline__ unsigned long long scaled_floor(double w, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  int e = (int)((b >> 52) & 0x7ffull);
+  unsigned long long mant = b & 0xfffffffffffffull;
+  if (e == 0) {
+    if (mant == 0) return 0ull;
+    e = 1;
+  } else {
+    mant |= 0x10000000000000ull;
+  }
+  const int sh = e - 1075 + s;  // w = mant 2^(e - 1075)
+  if (sh >= 0) return sh < 64 ? mant << sh : 0ull;
+  return -sh < 64 ? mant >> (-sh) : 0ull;
+}
+
+// Order key of a non-negative double: its bit pattern as an unsigned integer
+// orders exactly as the value (integer compares instead of FP64 compares).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  return (unsigned long long)__double_as_longlong(v);
 }
 
 // Systematic resampling: number of children whose pointer falls below Q_i,
