@@ -251,6 +251,35 @@ phd_status phd_reset_stats(phd_handle *h);
  * one.  Does not synchronise. */
 phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
 
+/* ---- normaliser column sums without device allocation ---------------------- */
+
+/* C_p = sum_i p_D g(z_p | x_i) w_i for one particle set (the Eq. 7 column sums
+ * of phd_update, same kernel arithmetic and summation order as a one-PE
+ * filter), for callers that may not allocate device memory at all: trackers
+ * whose device memory is fixed when they start (cudaMalloc and cudaFree can
+ * synchronise the device and take unbounded time, which a real-time loop
+ * cannot afford) and plug-ins running inside a host application that owns
+ * every device allocation.  It needs no handle and no workspace; the paper has
+ * no counterpart of this entry point.
+ *  cfg: as for phd_init (must pass its checks); only the sensor model,
+ *       sigma_z, sensor, p_d and precision are used.
+ *  d_x: real [n][4] states, d_w: real [n] weights, d_Z: real [M][2]
+ *       measurements, d_C: double [M] output; stream: a cudaStream_t or NULL.
+ * Its scratch (per-tile partial sums) is a 4 MiB array in the library's own
+ * device memory, held by every GPU that loads the library until the process
+ * exits: ceil(n / 256) * M must not exceed 524288, else PHD_ERR_CAPACITY and
+ * nothing runs.  No cudaMalloc, cudaFree or allocating library call is made.
+ * The first call on a device, with that device current, looks up the array's
+ * device address and copies in a 4 KB lookup table (a synchronous copy): make
+ * that first call before any stream capture.  Later calls are asynchronous.
+ * Every call uses the same array; each call writes every partial it reads,
+ * so nothing needs clearing, but calls that overlap on the GPU (concurrent
+ * streams, several host threads) race on it: order them on one stream.
+ * Errors: PHD_ERR_INVALID_ARG for a bad cfg, negative sizes or NULL buffers;
+ * PHD_ERR_CUDA if the set-up or a launch fails. */
+phd_status phd_colsum_static(const phd_config *cfg, const void *d_x, const void *d_w, int32_t n,
+                             const void *d_Z, int32_t M, double *d_C, void *stream);
+
 /* Wait for the stream and report a device-side error (non-finite input,
  * bounded-wait timeout) recorded since the last check.  Synchronises. */
 phd_status phd_sync(phd_handle *h);

@@ -7,7 +7,6 @@
 #include <string>
 #include <vector>
 
-#include "phd.h"
 #include "phd_internal.cuh"
 
 using phd::Dev;
@@ -459,6 +458,27 @@ phd_status stage_z_only(phd_handle* h, const void* Z, int M) {
 
 }  // namespace
 
+namespace phd {
+
+// Bearing anchors: float directions (c_k, s_k) near angle 2 pi k / 256 and
+// their exact angles atan2(s_k, c_k) in FP64, split into two floats.
+void fill_anchor_table(Anchor* tab) {
+  for (int k = 0; k < kAnchors; ++k) {
+    const double ang = 2.0 * 3.14159265358979323846 * k / kAnchors;
+    const float c = (float)std::cos(ang), s = (float)std::sin(ang);
+    const double th = std::atan2((double)s, (double)c);
+    tab[k].c = c;
+    tab[k].s = s;
+    tab[k].th_hi = (float)th;
+    tab[k].th_lo = (float)(th - (double)tab[k].th_hi);
+  }
+}
+
+Model model_from_config(const phd_config& c) { return make_model(c); }
+const char* config_problem(const phd_config& c) { return check_config(c); }
+
+}  // namespace phd
+
 extern "C" {
 
 const char* phd_status_string(phd_status s) {
@@ -502,18 +522,8 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
     h->fused_ok = is_fp64(h) ? phd::fused_eligible<double>(h->m, h->device) : phd::fused_eligible<float>(h->m, h->device);
   (void)cudaGetLastError();   // an ineligible attribute query leaves no sticky error
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
-  // bearing anchors: float directions (c_k, s_k) near angle 2 pi k / 256 and
-  // their exact angles atan2(s_k, c_k) in FP64, split into two floats
   phd::Anchor tab[phd::kAnchors];
-  for (int k = 0; k < phd::kAnchors; ++k) {
-    const double ang = 2.0 * 3.14159265358979323846 * k / phd::kAnchors;
-    const float c = (float)std::cos(ang), s = (float)std::sin(ang);
-    const double th = std::atan2((double)s, (double)c);
-    tab[k].c = c;
-    tab[k].s = s;
-    tab[k].th_hi = (float)th;
-    tab[k].th_lo = (float)(th - (double)tab[k].th_hi);
-  }
+  phd::fill_anchor_table(tab);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(const_cast<void*>(h->d.anchors), tab, sizeof(tab), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "phd.h"
+
 namespace phd {
 
 constexpr int kMaxPE = 256;
@@ -427,6 +429,9 @@ cudaError_t launch_advance_step(const Dev& d, cudaStream_t s);
 template <class R> cudaError_t prepare_kernels(const Model& m);
 cudaError_t prepare_exchange(const Model& m);
 template <class R> bool fused_eligible(const Model& m, int device);
+void fill_anchor_table(Anchor* tab);
+Model model_from_config(const phd_config& c);
+const char* config_problem(const phd_config& c);
 template <class R>
 cudaError_t launch_fused(const Dev& d, const Model& m, const void* Z, const int* zoff, int M1, int S, const R* noise,
                          const uint32_t* u, const uint32_t* xu, R* out_states, int* out_labels, int* out_count,

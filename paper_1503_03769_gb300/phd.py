@@ -89,6 +89,8 @@ ABI = {
     "phd_set_path": (ctypes.c_int, [_H, ctypes.c_int32]),
     "phd_get_path": (ctypes.c_int, [_H, _I32P]),
     "phd_get_predicted": (ctypes.c_int, [_H, _P, _P, _P, _I32P]),
+    "phd_colsum_static": (ctypes.c_int, [ctypes.POINTER(phd_config), _P, _P, ctypes.c_int32, _P,
+                                         ctypes.c_int32, _P, _P]),
 }
 
 _lib = None
@@ -141,6 +143,18 @@ def make_config(w, seed: int = 0) -> phd_config:
     c.exchange_frac = float(w.exchange_frac)
     c.seed = int(seed) & (2 ** 64 - 1)
     return c
+
+
+def colsum_static(cfg: phd_config, x: torch.Tensor, w: torch.Tensor, Z: torch.Tensor, C: torch.Tensor,
+                  stream: Optional[torch.cuda.Stream] = None) -> int:
+    """phd_colsum_static: Eq. 7 column sums into C (double [M]) with no device
+    allocation; returns the phd status."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = int(w.shape[0])
+    M = int(Z.shape[0])
+    return lib().phd_colsum_static(ctypes.byref(cfg), _ptr(x) if n else None, _ptr(w) if n else None, n,
+                                   _ptr(Z) if M else None, M, _ptr(C) if M else None,
+                                   ctypes.c_void_p(st.cuda_stream))
 
 
 class ParticlePHD:
@@ -378,6 +392,6 @@ class ParticlePHD:
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
 
 
-__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "phd_stats", "make_config", "ParticlePHD", "PhdError",
+__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "phd_stats", "make_config", "colsum_static", "ParticlePHD", "PhdError",
            "PHD_OK", "PHD_ERR_INVALID_ARG", "PHD_ERR_CAPACITY", "PHD_ERR_CUDA", "PHD_ERR_TIMEOUT",
            "PHD_ERR_STATE", "PHD_FP32", "PHD_FP64"]
