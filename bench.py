@@ -196,11 +196,12 @@ def run_reference(args, w, rank, world):
 # the GPU arm
 # ----------------------------------------------------------------------------
 
-def _traffic_from_profile():
-    """Per-update DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def _traffic_from_profile(path):
+    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "update_dist16_ncu.md")
+    name = "k_step_fused_dist16_ncu.md" if path == "fused" else "update_dist16_ncu.md"
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -321,15 +322,44 @@ def run_gpu(args, w, rank, world, local_rank):
     except Exception:
         ospa_vals = []
 
-    # roofline of the update stage (Eq. 7-8 pair passes): one ex2 per pair
+    # roofline of the timed kernel: the fused step kernel (fused path) or the
+    # update stage's kernels (staged path); one ex2 per pair is the unit
+    path = f.get_path()
     upd_ms = st["update_ms"]
     achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "update stage (k_colsum, k_finalize, k_rowsum, k_mass)",
+    kname = ("k_step_fused (whole step, one CTA per PE)" if path == "fused"
+             else "update stage (k_colsum, k_finalize, k_rowsum, k_mass)")
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
-                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(),
+                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(path),
                 "peak_source": "derived: 152 SMs x 32 MUFU ex2/clk x 2.07 GHz (one ex2 per pair)",
-                "update_ms_per_step": upd_ms / max(st["timed_updates"], 1),
+                "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                 "pairs_per_update": pairs / max(st["updates"], 1)}
+
+    # whole runs in one launch each (phd_run): S scans per call, L2 flushed
+    # between runs (outside the events)
+    run_ms, run_pairs, run_steps = 0.0, 0, 0
+    by_run = {}
+    for r, k in seq[args.warmup:]:
+        by_run.setdefault(r, []).append(k)
+    packed = {r: f.pack([Zdev[(r, k)] for k in ks]) for r, ks in by_run.items()}
+    f.reset_stats()
+    for r, ks in by_run.items():
+        f.set_state(empty_x, empty_w)
+        if ks[0] != 0:                   # a run the timed window entered mid-way: replay its head untimed
+            f.run([scen[r].meas[k] for k in range(ks[0])], sync=False)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        before = f.stats()["pairs"]
+        Zp, offt = packed[r]
+        e0.record()
+        f.run_packed(Zp, offt, len(ks), cap)
+        e1.record()
+        torch.cuda.synchronize()
+        run_ms += e0.elapsed_time(e1)
+        run_pairs += f.stats()["pairs"] - before
+        run_steps += len(ks)
 
     # end to end through the public host-buffer call (pinned host memory)
     f.set_stage_timer(False)
@@ -376,6 +406,10 @@ def run_gpu(args, w, rank, world, local_rank):
         "data": "synthetic",
         "config": workload_config(w, runs, "flushed between timed steps (512 MiB write, outside the events)"),
         "steps_per_s": steps_per_s,
+        "path": path,
+        "run_mode": {"api": "phd_run (one launch per run of scans)",
+                     "value": run_pairs / (run_ms * 1e-3) if run_ms > 0 else None, "unit": UNIT,
+                     "ms_per_step": run_ms / max(run_steps, 1), "steps": run_steps},
         "ospa_mean": float(np.mean(ospa_vals)) if ospa_vals else None,
         "roofline": roofline,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / K,

@@ -271,26 +271,35 @@ class ParticlePHD:
         self._check(st, "phd_step_inject", hc.value)
         return states[:hc.value], labels[:hc.value]
 
-    def run(self, Zs, cap: Optional[int] = None, sync: bool = True):
-        """phd_run over a list of scans; returns per-scan (states, labels)."""
+    def pack(self, Zs):
+        """Pack a list of scans into (device rows, device int32 offsets) for run_packed."""
+        rows = [torch.as_tensor(z, dtype=self.dtype, device=self.device).reshape(-1, 2) for z in Zs]
+        off = np.zeros(len(rows) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([r.shape[0] for r in rows])
+        Zp = torch.cat(rows).contiguous() if off[-1] else torch.zeros((1, 2), dtype=self.dtype, device=self.device)
+        return Zp, torch.as_tensor(off, device=self.device)
+
+    def run_packed(self, Zp, offsets, S: int, cap: Optional[int] = None):
+        """phd_run on packed device scans; returns device (states, labels, counts)."""
         cap = self.m_max if cap is None else int(cap)
-        S = len(Zs)
-        rows = [np.asarray(z).reshape(-1, 2) for z in Zs]
-        off = np.zeros(S + 1, dtype=np.int32)
-        off[1:] = np.cumsum([len(r) for r in rows])
-        Zp = self._real(np.concatenate(rows) if off[-1] else np.zeros((1, 2)), (-1, 2))
-        offt = torch.as_tensor(off, device=self.device)
         states = torch.empty((S, cap, 4), dtype=self.dtype, device=self.device)
         labels = torch.empty((S, cap), dtype=torch.int32, device=self.device)
         counts = torch.empty(S, dtype=torch.int32, device=self.device)
-        self._check(self.L.phd_run(self.h, _ptr(Zp), _ptr(offt), S, _ptr(states), _ptr(labels), _ptr(counts), cap),
-                    "phd_run")
-        self._keeprun = (Zp, offt)
+        self._check(self.L.phd_run(self.h, _ptr(Zp), _ptr(offsets), S, _ptr(states), _ptr(labels), _ptr(counts),
+                                   cap), "phd_run")
+        self._keeprun = (Zp, offsets)
+        return states, labels, counts
+
+    def run(self, Zs, cap: Optional[int] = None, sync: bool = True):
+        """phd_run over a list of scans; returns per-scan (states, labels)."""
+        cap = self.m_max if cap is None else int(cap)
+        Zp, offt = self.pack(Zs)
+        states, labels, counts = self.run_packed(Zp, offt, len(Zs), cap)
         if not sync:
             return states, labels, counts
         self.sync()
         c = counts.cpu().numpy()
-        return [(states[s, :min(c[s], cap)], labels[s, :min(c[s], cap)]) for s in range(S)]
+        return [(states[s, :min(c[s], cap)], labels[s, :min(c[s], cap)]) for s in range(len(Zs))]
 
     def set_path(self, path: str):
         self._check(self.L.phd_set_path(self.h, _PATHS[path]), "phd_set_path")
