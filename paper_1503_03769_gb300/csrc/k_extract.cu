@@ -23,39 +23,41 @@
 namespace phd {
 
 template <class R>
-__global__ void __launch_bounds__(1024) k_select(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
   const int j = blockIdx.x;
   const int M = *d.M;
   if (threadIdx.x == 0) npos_s = 0;
-  for (int p = threadIdx.x; p < M; p += blockDim.x) {
-    const double den = m.kappa + d.Cused[j * m.m_max + p];
-    key[p] = order_key(den > 0.0 ? d.C[j * m.m_max + p] / den : 0.0);
-  }
+  for (int p = threadIdx.x; p < M; p += blockDim.x) key[p] = d.dwkey[j * m.m_max + p];
   __syncthreads();
-  const double mass = d.mass[j];
   int npos_t = 0;
   for (int p = threadIdx.x; p < M; p += blockDim.x) npos_t += key[p] > 0ull ? 1 : 0;
   npos_t = __reduce_add_sync(0xffffffffu, npos_t);
   if ((threadIdx.x & 31) == 0) atomicAdd(&npos_s, npos_t);
   __syncthreads();
-  long long LT = llround(mass);
+  long long LT = llround(d.mass[j]);
   if (LT > npos_s) LT = npos_s;
   if (LT < 0) LT = 0;
-  for (int p = threadIdx.x; p < M; p += blockDim.x) {
+  // one warp per measurement, lanes split the comparisons
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int p = blockIdx.y * wpb + (threadIdx.x >> 5); p < M; p += gridDim.y * wpb) {
     const unsigned long long v = key[p];
-    int rank = 0;
-    for (int q = 0; q < M; ++q) {
+    int cnt = 0;
+    for (int q = lane; q < M; q += 32) {
       const unsigned long long u = key[q];
-      rank += (u > v || (u == v && q < p)) ? 1 : 0;
+      cnt += (u > v || (u == v && q < p)) ? 1 : 0;
     }
-    const bool take = v > 0ull && rank < LT;
-    d.selrank[j * m.m_max + p] = take ? rank : -1;
-    if (take) d.sel[j * m.m_max + rank] = p;
+    const int rank = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) {
+      const bool take = v > 0ull && rank < LT;
+      d.selrank[j * m.m_max + p] = take ? rank : -1;
+      if (take) d.sel[j * m.m_max + rank] = p;
+    }
   }
-  if (threadIdx.x == 0) d.nsel[j] = (int)LT;
+  if (blockIdx.y == 0 && threadIdx.x == 0) d.nsel[j] = (int)LT;
 }
 
 // Cartesian point of a measurement, the offset origin of the labelled sums.
@@ -75,9 +77,8 @@ __device__ __forceinline__ void meas_point(const Model& m, V2<R> z, R& rx, R& ry
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
-  __shared__ R sh0[kTile], sh1[kTile], shl[kTile], sw[kTile];
+  __shared__ P4<R> sp[kTile];
   __shared__ St4<R> sx[kTile];
-  __shared__ double red[kThreads];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   const int total = pref[K];
@@ -94,89 +95,110 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
     const int tile = item - pref[j];
     const long base = (long)j * m.pe_cap + (long)tile * kTile;
     const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
-    const int mper = ns < kThreads ? ns : kThreads;
-    const int nsplit = kThreads / mper;
-    const int rl = threadIdx.x % mper;
-    const int split = threadIdx.x / mper;
-    const bool active = split < nsplit;
     __syncthreads();
     for (int i = threadIdx.x; i < kTile; i += kThreads) {
-      H3<R> h = {0, 0, 0};
-      R wi = 0;
+      P4<R> q = {0, 0, 0, 0};
       St4<R> s = {0, 0, 0, 0};
       if (i < cnt) {
         s = x[base + i];
-        h = meas_h<R>(m, s, tab);
-        wi = w[base + i];
+        const H3<R> h = meas_h<R>(m, s, tab);
+        q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
       }
-      sh0[i] = h.h0;
-      sh1[i] = h.h1;
-      shl[i] = h.h1lo;
-      sw[i] = wi;
+      sp[i] = q;
       sx[i] = s;
     }
     __syncthreads();
+    // groups of nsplit consecutive lanes per label; FP32 sums of offsets from
+    // the label's point, reduced by shuffles within the group
+    int nsplit = 1;
+    while (nsplit * 2 <= 32 && nsplit * 2 * ns <= kThreads) nsplit *= 2;
+    const int mper = kThreads / nsplit;
+    const int rl = threadIdx.x / nsplit, split = threadIdx.x % nsplit;
     for (int r0 = 0; r0 < ns; r0 += mper) {
       const int r = r0 + rl;
-      R a[5] = {0, 0, 0, 0, 0};
-      if (active && r < ns) {
-        const int p = d.sel[j * m.m_max + r];
-        const V2<R> z = Z[p];
-        R px, py;
+      R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+      R px = 0, py = 0;
+      if (r < ns) {
+        const V2<R> z = Z[d.sel[j * m.m_max + r]];
         meas_point<R>(m, z, px, py);
         for (int i = split; i < cnt; i += nsplit) {
-          const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
-          const R ew = exp2_neg(q) * sw[i];
-          const St4<R> s = sx[i];
-          a[0] += ew;
-          a[1] = fma(ew, s.x - px, a[1]);
-          a[2] = fma(ew, s.vx, a[2]);
-          a[3] = fma(ew, s.y - py, a[3]);
-          a[4] = fma(ew, s.vy, a[4]);
+          const P4<R> q = sp[i];
+          const R ew = exp2_neg(qform<R>(L, z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
+          const St4<R> st = sx[i];
+          s0 += ew;
+          s1 = fma(ew, st.x - px, s1);
+          s2 = fma(ew, st.vx, s2);
+          s3 = fma(ew, st.y - py, s3);
+          s4 = fma(ew, st.vy, s4);
         }
       }
-      for (int c = 0; c < 5; ++c) {
-        red[threadIdx.x] = (double)a[c];
-        __syncthreads();
-        if (split == 0 && r < ns) {
-          double t = red[threadIdx.x];
-          for (int k = 1; k < nsplit; ++k) t += red[threadIdx.x + k * mper];
-          d.spart[((long)item * m.m_max + r) * 5 + c] = t;
-        }
-        __syncthreads();
+      for (int o = nsplit >> 1; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o, nsplit);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o, nsplit);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o, nsplit);
+        s3 += __shfl_down_sync(0xffffffffu, s3, o, nsplit);
+        s4 += __shfl_down_sync(0xffffffffu, s4, o, nsplit);
+      }
+      if (split == 0 && r < ns) {
+        double* o = d.spart + ((long)item * m.m_max + r) * 5;
+        o[0] = (double)s0;
+        o[1] = (double)s1;
+        o[2] = (double)s2;
+        o[3] = (double)s3;
+        o[4] = (double)s4;
       }
     }
   }
 }
 
+// One warp per (PE, rank): lanes take the PE's pass-3 tile partials in a
+// strided order, an FP64 shuffle tree combines them (fixed order), then
+// zeta = r + S / C (Eq. 18).
 template <class R>
-__global__ void k_est_local(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   St4<R>* est = static_cast<St4<R>*>(d.est_local);
   const V2<R>* Zr = static_cast<const V2<R>*>(d.Z);
+  const int lane = threadIdx.x & 31;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
   const long total = (long)K * m.m_max;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(g / m.m_max);
-    const int r = (int)(g - (long)j * m.m_max);
-    if (r >= d.nsel[j]) continue;
-    double a[5] = {0, 0, 0, 0, 0};
-    for (int it = pref[j]; it < pref[j + 1]; ++it)
-      for (int c = 0; c < 5; ++c) a[c] += d.spart[((long)it * m.m_max + r) * 5 + c];
-    const int p = d.sel[j * m.m_max + r];
-    R px, py;
-    meas_point<R>(m, Zr[p], px, py);
-    St4<R> o;
-    if (a[0] > 0.0) {
-      o.x = (R)((double)px + a[1] / a[0]);
-      o.vx = (R)(a[2] / a[0]);
-      o.y = (R)((double)py + a[3] / a[0]);
-      o.vy = (R)(a[4] / a[0]);
-    } else {
-      o = St4<R>{px, (R)0, py, (R)0};
+  for (long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < total; gw += nwarps) {
+    const int j = (int)(gw / m.m_max);
+    const int r = (int)(gw - (long)j * m.m_max);
+    if (r >= d.nsel[j]) continue;   // uniform over the warp
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    for (int it = pref[j] + lane; it < pref[j + 1]; it += 32) {
+      const double* q = d.spart + ((long)it * m.m_max + r) * 5;
+      a0 += q[0];
+      a1 += q[1];
+      a2 += q[2];
+      a3 += q[3];
+      a4 += q[4];
     }
-    est[g] = o;
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o);
+      a2 += __shfl_down_sync(0xffffffffu, a2, o);
+      a3 += __shfl_down_sync(0xffffffffu, a3, o);
+      a4 += __shfl_down_sync(0xffffffffu, a4, o);
+    }
+    if (lane == 0) {
+      const int p = d.sel[j * m.m_max + r];
+      R px, py;
+      meas_point<R>(m, Zr[p], px, py);
+      St4<R> o;
+      if (a0 > 0.0) {
+        o.x = (R)((double)px + a1 / a0);
+        o.vx = (R)(a2 / a0);
+        o.y = (R)((double)py + a3 / a0);
+        o.vy = (R)(a4 / a0);
+      } else {
+        o = St4<R>{px, (R)0, py, (R)0};
+      }
+      est[gw] = o;
+    }
   }
 }
 
@@ -245,10 +267,10 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
 template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
-  k_select<R><<<m.K, 1024, sizeof(unsigned long long) * (size_t)m.m_max, s>>>(d, m);
+  k_select<R><<<dim3(m.K, (m.m_max + 63) / 64), 256, sizeof(unsigned long long) * (size_t)m.m_max, s>>>(d, m);
   k_selsum<R><<<grid_items(m), kThreads, 0, s>>>(d, m);
-  long tot = (long)m.K * m.m_max;
-  int b = (int)((tot + 255) / 256);
+  long warps = (long)m.K * m.m_max;
+  int b = (int)((warps + 7) / 8);
   if (b > 152 * 8) b = 152 * 8;
   k_est_local<R><<<b, 256, 0, s>>>(d, m);
   k_fuse<R><<<1, 1024, 0, s>>>(d, m, out_states, out_labels, cap, d_count);

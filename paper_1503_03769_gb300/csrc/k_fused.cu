@@ -90,7 +90,7 @@ __host__ __device__ inline FusedSmem fused_smem(int P, int Mm) {
   FusedSmem L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
-    size_t at = (o + 15) & ~(size_t)15;
+    size_t at = (o + 31) & ~(size_t)31;
     o = at + bytes;
     return at;
   };
@@ -112,7 +112,7 @@ __host__ __device__ inline FusedSmem fused_smem(int P, int Mm) {
   L.sel = take(sizeof(int) * Mm);
   L.selrank = take(sizeof(int) * Mm);
   L.red = take(sizeof(double) * kFusedThreads);
-  L.total = (o + 15) & ~(size_t)15;
+  L.total = (o + 31) & ~(size_t)31;
   return L;
 }
 
@@ -248,10 +248,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   extern __shared__ __align__(16) unsigned char smem[];
   const FusedSmem SL = fused_smem<R>(m.pe_cap, m.m_max);
   St4<R>* sx = reinterpret_cast<St4<R>*>(smem + SL.sx);
-  R* sh0 = reinterpret_cast<R*>(smem + SL.sh0);
-  R* sh1 = reinterpret_cast<R*>(smem + SL.sh1);
-  R* shl = reinterpret_cast<R*>(smem + SL.shl);
-  R* sw = reinterpret_cast<R*>(smem + SL.sw);
+  P4<R>* sp = reinterpret_cast<P4<R>*>(smem + SL.sh0);
   R* swu = reinterpret_cast<R*>(smem + SL.swu);
   V2<R>* zs = reinterpret_cast<V2<R>*>(smem + SL.zs);
   R* ginv = reinterpret_cast<R*>(smem + SL.ginv);
@@ -320,10 +317,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       gwp[base + i] = wo;
       sx[i] = o;
       const H3<R> h = meas_h<R>(m, o, tab);
-      sh0[i] = h.h0;
-      sh1[i] = h.h1;
-      shl[i] = h.h1lo;
-      sw[i] = wo;
+      sp[i] = P4<R>{h.h0, h.h1, h.h1lo, wo};
     }
     if (tid == 0) {
       d.n_pred[j] = np;
@@ -346,24 +340,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         const int p = p0 + pl;
         double acc = 0.0;
         if (p < M) {
+          // four independent partial sums (ILP); FP64 every 256 pairs
           const V2<R> z = zs[p];
-          R mid = 0, part = 0;
-          int k = 0, kk = 0;
-          for (int i = split; i < np; i += nsplit) {
-            const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
-            part = fma(exp2_neg(q), sw[i], part);
-            if (++k == 32) {
-              mid += part;
-              part = 0;
+          R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+          int i = split, k = 0;
+          for (; i + 3 * nsplit < np; i += 4 * nsplit) {
+            const P4<R> q0 = sp[i], q1 = sp[i + nsplit], q2 = sp[i + 2 * nsplit], q3 = sp[i + 3 * nsplit];
+            a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+            a1 = fma(exp2_neg(qform<R>(L, z.a, z.b, q1.h0, q1.h1, q1.h1lo)), q1.w, a1);
+            a2 = fma(exp2_neg(qform<R>(L, z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
+            a3 = fma(exp2_neg(qform<R>(L, z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
+            if (++k == 64) {
+              acc += (double)((a0 + a1) + (a2 + a3));
+              a0 = a1 = a2 = a3 = 0;
               k = 0;
-              if (++kk == 8) {
-                acc += (double)mid;
-                mid = 0;
-                kk = 0;
-              }
             }
           }
-          acc += (double)(mid + part);
+          for (; i < np; i += nsplit) {
+            const P4<R> q0 = sp[i];
+            a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+          }
+          acc += (double)((a0 + a1) + (a2 + a3));
         }
         for (int o = nsplit >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, nsplit);
         if (split == 0 && p < M) {
@@ -397,16 +394,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     // ---- pass 2: updated weights (Eq. 8), mass and largest weight
     R msum = 0, mmax = 0;
     for (int i = tid; i < np; i += T) {
-      const R h0 = sh0[i], h1 = sh1[i], hl = shl[i];
-      R acc = 0, part = 0;
-      int k = 0;
-      for (int p = 0; p < M; ++p) {
-        const V2<R> z = zs[p];
-        part = fma(exp2_neg(qform<R>(L, z.a, z.b, h0, h1, hl)), ginv[p], part);
-        if (++k == 64) { acc += part; part = 0; k = 0; }
+      const P4<R> q = sp[i];
+      R acc = 0, a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int p = 0, k = 0;
+      for (; p + 3 < M; p += 4) {
+        const V2<R> z0 = zs[p], z1 = zs[p + 1], z2 = zs[p + 2], z3 = zs[p + 3];
+        a0 = fma(exp2_neg(qform<R>(L, z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
+        a1 = fma(exp2_neg(qform<R>(L, z1.a, z1.b, q.h0, q.h1, q.h1lo)), ginv[p + 1], a1);
+        a2 = fma(exp2_neg(qform<R>(L, z2.a, z2.b, q.h0, q.h1, q.h1lo)), ginv[p + 2], a2);
+        a3 = fma(exp2_neg(qform<R>(L, z3.a, z3.b, q.h0, q.h1, q.h1lo)), ginv[p + 3], a3);
+        if (++k == 32) {
+          acc += (a0 + a1) + (a2 + a3);
+          a0 = a1 = a2 = a3 = 0;
+          k = 0;
+        }
       }
-      acc += part;
-      const R wv = (cc.miss + acc) * sw[i];
+      for (; p < M; ++p) {
+        const V2<R> z0 = zs[p];
+        a0 = fma(exp2_neg(qform<R>(L, z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
+      }
+      acc += (a0 + a1) + (a2 + a3);
+      const R wv = (cc.miss + acc) * q.w;
       swu[i] = wv;
       gwu[base + i] = wv;
       msum += wv;
@@ -455,7 +463,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           const V2<R> z = zs[sel[r]];
           meas_point_f<R>(cc, m.meas_model, z, px, py);
           for (int i = split; i < np; i += nsplit) {
-            const R ew = exp2_neg(qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i])) * sw[i];
+            const P4<R> q = sp[i];
+            const R ew = exp2_neg(qform<R>(L, z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
             const St4<R> st = sx[i];
             s0 += ew;
             s1 = fma(ew, st.x - px, s1);

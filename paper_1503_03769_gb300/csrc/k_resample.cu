@@ -2,19 +2,20 @@
 // exchange (Step 6).
 //
 // Systematic resampling on an exact integer-valued CDF, per PE j:
-//   k_rs_mass : N^j = sum_i w_i (FP64, fixed order), e with max w < 2^e,
-//               c = ceil(log2 n), s = 52 - c - e,
+//   plan (k_mass, after the update): N^j = sum_i w_i (FP64, fixed order),
+//               e with max w < 2^e, c = ceil(log2 n), s = 52 - c - e,
 //               L_j = min(pe_cap - J_j, round((rho / K) max(1, N^j))).
-//   k_rs_scan : q_i = floor(w_i 2^s) (an FP64 power-of-two scaling then
-//               floor: exact), Q_i = q_0 + ... + q_i.  Every Q_i < 2^52 is an
-//               exact FP64 integer, so the prefix is accumulated in 64-bit
+//   k_rs_q / k_rs_off: q_i = floor(w_i 2^s) (exact, from the float's bits),
+//               chunk totals and their exclusive scan.  Every Q_i < 2^52 is
+//               an exact FP64 integer, so the prefix is accumulated in 64-bit
 //               integers, which gives the same values as FP64 and cannot
 //               depend on the summation order.
-//   k_rs_count: c_i = #{t : T_t < Q_i} with T_t = floor((t 2^32 + U) Q_n /
-//               (L 2^32)), in closed form with 128-bit integers:
-//               V = floor((Q_i L 2^32 - 1) / Q_n), c_i = min(L, V < U ? 0 :
-//               ((V - U) >> 32) + 1).  Child t's parent is then the least i
-//               with c_i > t, i.e. the least i with Q_i > T_t.
+//   k_rs_count: Q_i = chunk offset + in-chunk prefix; c_i = #{t : T_t < Q_i}
+//               with T_t = floor((t 2^32 + U) Q_n / (L 2^32)), in closed form
+//               with 128-bit integers: V = floor((Q_i L 2^32 - 1) / Q_n),
+//               c_i = min(L, V < U ? 0 : ((V - U) >> 32) + 1).  Child t's
+//               parent is then the least i with c_i > t, i.e. the least i
+//               with Q_i > T_t.
 //   k_rs_gather: one thread per child: binary search of c, copy the parent's
 //               predicted state into the current set, weight N^j / L_j.
 // Ring exchange (K > 1): L_x = floor(frac min_j L_j); PE j takes the first L_x
@@ -26,117 +27,92 @@
 
 namespace phd {
 
+// Exact CDF in three passes over chunks of kChunk particles (any PE size):
+// chunk totals of q_i = floor(w_i 2^s), an exclusive scan of the totals per
+// PE, then every chunk rescans its own q_i and turns Q_i into offspring ends.
 template <class R>
-__global__ void __launch_bounds__(256) k_rs_mass(Dev d, Model m) {
-  __shared__ double rs[8], rm[8];
-  const int j = blockIdx.x;
-  const int n = d.n_pred[j];
-  const R* w = static_cast<const R*>(d.wu) + (long)j * m.pe_cap;
-  // FP32 runs of 64 weights per thread, FP64 across runs and threads
-  double s = 0.0;
-  R run = 0, mxr = 0;
-  int k = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const R v = w[i];
-    run += v;
-    mxr = v > mxr ? v : mxr;
-    if (++k == 64) {
-      s += (double)run;
-      run = 0;
-      k = 0;
-    }
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long* wt,
+                                                             unsigned long long* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
-  s += (double)run;
-  double mx = (double)mxr;
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_down_sync(0xffffffffu, s, o);
-    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    rs[threadIdx.x >> 5] = s;
-    rm[threadIdx.x >> 5] = mx;
-  }
+  if (lane == 31) wt[wid] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double N = 0.0, wmax = 0.0;
-    for (int k = 0; k < 8; ++k) {
-      N += rs[k];
-      wmax = fmax(wmax, rm[k]);
-    }
-    int L, sc;
-    resample_plan(m, j, n, N, wmax, L, sc);
-    d.rs_mass[j] = N;
-    d.rs_s[j] = sc;
-    d.rs_L[j] = L;
-  }
-}
-
-template <class R>
-__global__ void __launch_bounds__(1024) k_rs_scan(Dev d, Model m) {
-  constexpr int IT = 4;
-  __shared__ unsigned long long wtot[32];
-  __shared__ unsigned long long carry_s;
-  const int j = blockIdx.x;
-  const int n = d.n_pred[j];
-  const int s = d.rs_s[j];
-  const R* w = static_cast<const R*>(d.wu) + (long)j * m.pe_cap;
-  unsigned long long* Q = d.Q + (long)j * m.pe_cap;
-  if (threadIdx.x == 0) carry_s = 0ull;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < n; c0 += 1024 * IT) {
-    unsigned long long q[IT];
-    unsigned long long run = 0ull;
-#pragma unroll
-    for (int k = 0; k < IT; ++k) {
-      const int i = c0 + threadIdx.x * IT + k;
-      q[k] = i < n ? scaled_floor(w[i], s) : 0ull;
-      run += q[k];
-      q[k] = run;
-    }
-    unsigned long long incl = run;
+  if (wid == 0) {
+    unsigned long long u = lane < nw ? wt[lane] : 0ull;
     for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += t;
     }
-    if (lane == 31) wtot[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      unsigned long long v = wtot[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-      }
-      wtot[lane] = v;
-    }
-    __syncthreads();
-    const unsigned long long off = carry_s + (wid > 0 ? wtot[wid - 1] : 0ull) + (incl - run);
-#pragma unroll
-    for (int k = 0; k < IT; ++k) {
-      const int i = c0 + threadIdx.x * IT + k;
-      if (i < n) Q[i] = off + q[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s += wtot[31];
-    __syncthreads();
+    if (lane < nw) wt[lane] = u;
+  }
+  __syncthreads();
+  const unsigned long long r = (wid > 0 ? wt[wid - 1] : 0ull) + incl;
+  if (total) *total = wt[nw - 1];
+  __syncthreads();
+  return r;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kChunk) k_rs_q(Dev d, Model m) {
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ unsigned long long wt[32];
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  const R* wu = static_cast<const R*>(d.wu);
+  for (int c = blockIdx.x; c < pref[m.K]; c += gridDim.x) {
+    const int j = item_pe(pref, m.K, c);
+    const int i = (c - pref[j]) * kChunk + threadIdx.x;
+    const unsigned long long q = i < d.n_pred[j] ? scaled_floor(wu[(long)j * m.pe_cap + i], d.rs_s[j]) : 0ull;
+    unsigned long long tot = 0;
+    block_scan_u64<R>(q, wt, &tot);
+    if (threadIdx.x == 0) d.csum[c] = tot;
   }
 }
 
-__global__ void k_rs_count(Dev d, Model m, const uint32_t* __restrict__ u) {
-  const long total = (long)m.K * m.pe_cap;
+__global__ void __launch_bounds__(1024) k_rs_off(Dev d, Model m) {
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ unsigned long long wt[32];
+  const int j = blockIdx.x;
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  unsigned long long carry = 0ull;
+  for (int c0 = pref[j]; c0 < pref[j + 1]; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    const unsigned long long v = c < pref[j + 1] ? d.csum[c] : 0ull;
+    unsigned long long tot = 0;
+    const unsigned long long incl = block_scan_u64<float>(v, wt, &tot);
+    if (c < pref[j + 1]) d.coff[c] = carry + incl - v;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) d.rs_Qn[j] = carry;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint32_t* __restrict__ u) {
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ unsigned long long wt[32];
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  const R* wu = static_cast<const R*>(d.wu);
   const unsigned long long st = *d.step;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(g / m.pe_cap);
-    const int i = (int)(g - (long)j * m.pe_cap);
-    const int n = d.n_pred[j];
-    if (i >= n) continue;
-    const uint32_t U = u ? u[j] : philox_u32(m, (uint32_t)j, st, kTagResample);
-    d.child_end[g] = offspring_end(d.Q[g], d.Q[(long)j * m.pe_cap + n - 1], (unsigned long long)d.rs_L[j], U);
+  for (int c = blockIdx.x; c < pref[m.K]; c += gridDim.x) {
+    const int j = item_pe(pref, m.K, c);
+    const int i = (c - pref[j]) * kChunk + threadIdx.x;
+    const long g = (long)j * m.pe_cap + i;
+    const bool live = i < d.n_pred[j];
+    const unsigned long long q = live ? scaled_floor(wu[g], d.rs_s[j]) : 0ull;
+    const unsigned long long Qi = d.coff[c] + block_scan_u64<R>(q, wt, nullptr);
+    if (live) {
+      const uint32_t U = u ? u[j] : philox_u32(m, (uint32_t)j, st, kTagResample);
+      d.child_end[g] = offspring_end(Qi, d.rs_Qn[j], (unsigned long long)d.rs_L[j], U);
+    }
   }
 }
 
-// Children t < L_j of PE j: parent = least i with child_end[i] > t; the
-// predicted state is gathered into the current set with weight N^j / L_j.
+// Scatter by parent: particle i of PE j has children child_end[i-1] ..
+// child_end[i]-1 (parents in order, children in order), which get its
+// predicted state and the weight N^j / L_j.
 template <class R>
 __global__ void k_rs_gather(Dev d, Model m) {
   const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
@@ -145,19 +121,21 @@ __global__ void k_rs_gather(Dev d, Model m) {
   const long total = (long)m.K * m.pe_cap;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / m.pe_cap);
-    const int t = (int)(g - (long)j * m.pe_cap);
+    const int i = (int)(g - (long)j * m.pe_cap);
     const int L = d.rs_L[j];
-    if (t == 0) d.n_cur[j] = L;
-    if (t >= L) continue;
+    if (i == 0) d.n_cur[j] = L;
+    if (i >= d.n_pred[j] || L == 0) continue;
+    const int t1 = d.child_end[g];
+    const int t0 = i > 0 ? d.child_end[g - 1] : 0;
+    if (t1 <= t0) continue;
     const long base = (long)j * m.pe_cap;
-    int lo = 0, hi = d.n_pred[j] - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (d.child_end[base + mid] > t) hi = mid; else lo = mid + 1;
+    const St4<R> s = xp[g];
+    const R wn = (R)(d.rs_mass[j] / (double)L);
+    for (int t = t0; t < t1; ++t) {
+      x[base + t] = s;
+      w[base + t] = wn;
+      d.parent[base + t] = i;
     }
-    x[g] = xp[base + lo];
-    w[g] = (R)(d.rs_mass[j] / (double)L);
-    d.parent[g] = lo;
   }
 }
 
@@ -237,9 +215,11 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   const long total = (long)m.K * m.pe_cap;
   int b = (int)((total + 255) / 256);
   if (b > 152 * 16) b = 152 * 16;
-  k_rs_mass<R><<<m.K, 256, 0, s>>>(d, m);
-  k_rs_scan<R><<<m.K, 1024, 0, s>>>(d, m);
-  k_rs_count<<<b, 256, 0, s>>>(d, m, u);
+  const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
+  const int gc = (int)(chunks < 152L * 2 ? (chunks > 0 ? chunks : 1) : 152L * 2);
+  k_rs_q<R><<<gc, kChunk, 0, s>>>(d, m);
+  k_rs_off<<<m.K, 1024, 0, s>>>(d, m);
+  k_rs_count<R><<<gc, kChunk, 0, s>>>(d, m, u);
   k_rs_gather<R><<<b, 256, 0, s>>>(d, m);
   if (m.K > 1 && m.exchange_frac > 0.0) {
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);

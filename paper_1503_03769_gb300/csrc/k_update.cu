@@ -7,19 +7,19 @@
 // to [0, pi].  The N x M likelihood matrix is never stored.
 //
 // Pass 1 (k_colsum): C^j_p = p_D cnorm sum_i 2^-q_ip w_i.  A work item is a
-//   tile of kTile particles of one PE, staged in shared memory as
-//   (h0, h1, h1lo, w);
-//   threads own measurements (and, when M < 256, a split of the tile) and
-//   accumulate in FP32 over at most one tile; the per-item partials go to
+//   tile of kTile particles of one PE (staged in shared memory as packed
+//   (h0, h1, h1lo, w)) times a chunk of kMChunk measurements; threads own
+//   measurements (and, when the chunk is short, a split of the tile) and
+//   accumulate in FP32 over at most one tile; the per-tile partials go to
 //   memory in FP64 and are summed in a fixed order by k_finalize, so the
 //   normaliser is accumulated in FP64 and is deterministic.
 // Finalize: C^j, the normaliser each PE applies (its own, or the PE mean),
 //   and ginv_p = cnorm p_D / (kappa + C_p) (0 when kappa + C_p = 0).
-// Pass 2 (k_rowsum): w_i <- [(1 - p_D) + sum_p 2^-q_ip ginv_p] w_i with one
-//   thread per particle and Z_k, ginv staged in shared memory; per-item FP64
-//   partial sums of the updated weights feed N^j.  The updated weights go to
-//   their own buffer: the extraction (Eq. 13, 18) still needs the predicted
-//   ones.
+// Pass 2 (k_rowsum): w_i <- [(1 - p_D) + sum_p 2^-q_ip ginv_p] w_i with four
+//   lanes per particle and Z_k, ginv staged in shared memory; per-tile FP64
+//   sums and maxima of the updated weights feed N^j and the resampling plan
+//   (k_mass).  The updated weights go to their own buffer: the extraction
+//   (Eq. 13, 18) still needs the predicted ones.
 //
 // Algorithmic work per pair and pass: one ex2 and ~5 FP32 operations; bytes
 // per particle and pass: 16 B state + 4 B weight (+ 4 B weight written in
@@ -31,92 +31,106 @@ namespace phd {
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
-  __shared__ R sh0[kTile], sh1[kTile], shl[kTile], sw[kTile];
+  __shared__ P4<R> sp[kTile];
   __shared__ double red[kThreads];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
-  const int total = pref[K];
   const int M = *d.M;
   if (M <= 0) return;
+  const int chunks = (M + kMChunk - 1) / kMChunk;
+  const int total = pref[K] * chunks;
   const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
-  const int mper = M < kThreads ? M : kThreads;
-  const int nsplit = kThreads / mper;
-  const int pl = threadIdx.x % mper;
-  const int split = threadIdx.x / mper;
-  const bool active = split < nsplit;
-
+  int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int j = item_pe(pref, K, item);
-    const int tile = item - pref[j];
+    const int titem = item / chunks, chunk = item - titem * chunks;
+    const int j = item_pe(pref, K, titem);
+    const int tile = titem - pref[j];
     const long base = (long)j * m.pe_cap + (long)tile * kTile;
     const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kTile; i += kThreads) {
-      H3<R> h = {0, 0, 0};
-      R wi = 0;
-      if (i < cnt) {
-        h = meas_h<R>(m, x[base + i], tab);
-        wi = w[base + i];
-      }
-      sh0[i] = h.h0;
-      sh1[i] = h.h1;
-      shl[i] = h.h1lo;
-      sw[i] = wi;
-    }
-    __syncthreads();
-    for (int p0 = 0; p0 < M; p0 += mper) {
-      const int p = p0 + pl;
-      R acc = 0;
-      if (active && p < M) {
-        const V2<R> z = Z[p];
-        R part = 0;
-        int i = split, k = 0;
-        for (; i < cnt; i += nsplit) {
-          const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
-          part = fma(exp2_neg(q), sw[i], part);
-          if (++k == 32) { acc += part; part = 0; k = 0; }
+    if (titem != staged) {   // consecutive items of a CTA often share the tile
+      __syncthreads();
+      for (int i = threadIdx.x; i < kTile; i += kThreads) {
+        P4<R> q = {0, 0, 0, 0};
+        if (i < cnt) {
+          const H3<R> h = meas_h<R>(m, x[base + i], tab);
+          q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
         }
-        acc += part;
-      }
-      red[threadIdx.x] = (double)acc;
-      __syncthreads();
-      if (split == 0 && p < M) {
-        double s = red[threadIdx.x];
-        for (int k = 1; k < nsplit; ++k) s += red[threadIdx.x + k * mper];
-        d.colpart[(long)item * m.m_max + p] = s;
+        sp[i] = q;
       }
       __syncthreads();
+      staged = titem;
     }
+    const int pbeg = chunk * kMChunk;
+    const int Mc = min(kMChunk, M - pbeg);
+    const int nsplit = kThreads / Mc;
+    const int pl = threadIdx.x % Mc;
+    const int split = threadIdx.x / Mc;
+    const int p = pbeg + pl;
+    R acc = 0;
+    if (split < nsplit) {
+      // four independent partial sums (ILP), each over at most 64 pairs
+      const V2<R> z = Z[p];
+      R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int i = split;
+      for (; i + 3 * nsplit < cnt; i += 4 * nsplit) {
+        const P4<R> q0 = sp[i], q1 = sp[i + nsplit], q2 = sp[i + 2 * nsplit], q3 = sp[i + 3 * nsplit];
+        a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+        a1 = fma(exp2_neg(qform<R>(L, z.a, z.b, q1.h0, q1.h1, q1.h1lo)), q1.w, a1);
+        a2 = fma(exp2_neg(qform<R>(L, z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
+        a3 = fma(exp2_neg(qform<R>(L, z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
+      }
+      for (; i < cnt; i += nsplit) {
+        const P4<R> q0 = sp[i];
+        a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+      }
+      acc = (a0 + a1) + (a2 + a3);
+    }
+    red[threadIdx.x] = (double)acc;
+    __syncthreads();
+    if (split == 0) {
+      double s = red[threadIdx.x];
+      for (int k = 1; k < nsplit; ++k) s += red[threadIdx.x + k * Mc];
+      d.colpart[(long)titem * m.m_max + p] = s;
+    }
+    __syncthreads();
   }
 }
 
+// One warp per measurement: C^j_p = p_D cnorm * (FP64 tree over PE j's tile
+// partials, fixed order), the normaliser each PE applies, ginv and the dW
+// order keys.
 template <class R>
-__global__ void k_finalize(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   const int M = *d.M;
   const double cs = m.p_d * m.cnorm;
   R* ginv = static_cast<R*>(d.ginv);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < M; p += nwarps) {
     double mean = 0.0;
     for (int j = 0; j < K; ++j) {
       double c = 0.0;
-      for (int it = pref[j]; it < pref[j + 1]; ++it) c += d.colpart[(long)it * m.m_max + p];
-      c *= cs;
-      d.C[j * m.m_max + p] = c;
+      for (int it = pref[j] + lane; it < pref[j + 1]; it += 32) c += d.colpart[(long)it * m.m_max + p];
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+      c = __shfl_sync(0xffffffffu, c, 0) * cs;
+      if (lane == 0) d.C[j * m.m_max + p] = c;
       mean += c;
     }
     mean /= (double)K;
-    for (int j = 0; j < K; ++j) {
-      const double cu = m.ck_global ? mean : d.C[j * m.m_max + p];
+    for (int j = lane; j < K; j += 32) {
+      const double cj = d.C[j * m.m_max + p];
+      const double cu = m.ck_global ? mean : cj;
       d.Cused[j * m.m_max + p] = cu;
       const double den = m.kappa + cu;
       ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
+      d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? cj / den : 0.0);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -129,15 +143,17 @@ __global__ void k_finalize(Dev d, Model m) {
   }
 }
 
+// Pass 2: tiles of kRowTile particles; four consecutive lanes share a particle
+// and split the measurements (p = g, g+4, ...), combined by shuffles.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int pref[kMaxPE + 1];
-  __shared__ double red[kThreads / 32];
-  V2<R>* zs = reinterpret_cast<V2<R>*>(smem_raw);
-  R* gs = reinterpret_cast<R*>(smem_raw + sizeof(V2<R>) * m.m_max);
+  __shared__ double rs[kThreads / 32];
+  __shared__ double rm[kThreads / 32];
+  Z4<R>* zs = reinterpret_cast<Z4<R>*>(smem_raw);
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref);
+  item_prefix(d.n_pred, K, pref, kRowTile);
   const int total = pref[K];
   const int M = *d.M;
   const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
@@ -147,62 +163,113 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   R* __restrict__ wu = static_cast<R*>(d.wu);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
-  const R miss = (R)(1.0 - m.p_d);
-
+  const R miss = consts<R>(m).miss;
+  const int il = threadIdx.x >> 2, g = threadIdx.x & 3;
+  int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int tile = item - pref[j];
-    __syncthreads();
-    for (int p = threadIdx.x; p < M; p += kThreads) {
-      zs[p] = Z[p];
-      gs[p] = ginv[j * m.m_max + p];
-    }
-    __syncthreads();
-    const int i = tile * kTile + threadIdx.x;
-    double wn = 0.0;
-    if (i < d.n_pred[j]) {
-      const long g = (long)j * m.pe_cap + i;
-      const H3<R> h = meas_h<R>(m, x[g], tab);
-      R acc = 0, part = 0;
-      int k = 0;
-      for (int p = 0; p < M; ++p) {
-        const V2<R> z = zs[p];
-        const R q = qform<R>(L, z.a, z.b, h.h0, h.h1, h.h1lo);
-        part = fma(exp2_neg(q), gs[p], part);
-        if (++k == 64) { acc += part; part = 0; k = 0; }
+    if (j != staged) {
+      __syncthreads();
+      for (int p = threadIdx.x; p < M; p += kThreads) {
+        const V2<R> z = Z[p];
+        zs[p] = Z4<R>{z.a, z.b, ginv[j * m.m_max + p], (R)0};
       }
-      acc += part;
-      const R wv = (miss + acc) * w[g];
-      wu[g] = wv;
-      wn = (double)wv;
+      __syncthreads();
+      staged = j;
     }
-    // fixed-order block reduction of the updated weights (FP64)
-    for (int o = 16; o > 0; o >>= 1) wn += __shfl_down_sync(0xffffffffu, wn, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wn;
+    const int i = tile * kRowTile + il;
+    const bool live = i < d.n_pred[j];
+    const long gi = (long)j * m.pe_cap + i;
+    R acc = 0;
+    if (live) {
+      // four independent partial sums (ILP) over measurements g, g+4, ...,
+      // folded into acc every 32 rounds
+      const H3<R> h = meas_h<R>(m, x[gi], tab);
+      R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int p = g, k = 0;
+      for (; p + 12 < M; p += 16) {
+        const Z4<R> z0 = zs[p], z1 = zs[p + 4], z2 = zs[p + 8], z3 = zs[p + 12];
+        a0 = fma(exp2_neg(qform<R>(L, z0.z0, z0.z1, h.h0, h.h1, h.h1lo)), z0.g, a0);
+        a1 = fma(exp2_neg(qform<R>(L, z1.z0, z1.z1, h.h0, h.h1, h.h1lo)), z1.g, a1);
+        a2 = fma(exp2_neg(qform<R>(L, z2.z0, z2.z1, h.h0, h.h1, h.h1lo)), z2.g, a2);
+        a3 = fma(exp2_neg(qform<R>(L, z3.z0, z3.z1, h.h0, h.h1, h.h1lo)), z3.g, a3);
+        if (++k == 32) {
+          acc += (a0 + a1) + (a2 + a3);
+          a0 = a1 = a2 = a3 = 0;
+          k = 0;
+        }
+      }
+      for (; p < M; p += 4) {
+        const Z4<R> z0 = zs[p];
+        a0 = fma(exp2_neg(qform<R>(L, z0.z0, z0.z1, h.h0, h.h1, h.h1lo)), z0.g, a0);
+      }
+      acc += (a0 + a1) + (a2 + a3);
+    }
+    acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
+    acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
+    R wv = 0;
+    if (live && g == 0) {
+      wv = (miss + acc) * w[gi];
+      wu[gi] = wv;
+    }
+    // tile sum (FP64 over the warp's 8 particles, then the 8 warps) and max
+    double sv = (double)wv, mv = (double)wv;
+    for (int o = 16; o > 0; o >>= 1) {
+      sv += __shfl_down_sync(0xffffffffu, sv, o);
+      mv = fmax(mv, __shfl_down_sync(0xffffffffu, mv, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      rs[threadIdx.x >> 5] = sv;
+      rm[threadIdx.x >> 5] = mv;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int k2 = 0; k2 < kThreads / 32; ++k2) s += red[k2];
+      double s = 0.0, mx = 0.0;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        s += rs[k];
+        mx = fmax(mx, rm[k]);
+      }
       d.rowpart[item] = s;
+      d.rowmax[item] = mx;
     }
+    __syncthreads();
   }
 }
 
-// N^j = sum of PE j's pass-2 partials, in item order (deterministic).
+// Per PE: N^j = sum of the pass-2 tile sums (fixed order), the largest
+// updated weight, and the resampling plan (L_j and the CDF scale).
 __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
-  __shared__ double red[8];
+  __shared__ double red[8], redm[8];
   const int j = blockIdx.x;
-  item_prefix(d.n_pred, m.K, pref);
-  double s = 0.0;
-  for (int it = pref[j] + threadIdx.x; it < pref[j + 1]; it += blockDim.x) s += d.rowpart[it];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  item_prefix(d.n_pred, m.K, pref, kRowTile);
+  double s = 0.0, mx = 0.0;
+  for (int it = pref[j] + threadIdx.x; it < pref[j + 1]; it += blockDim.x) {
+    s += d.rowpart[it];
+    mx = fmax(mx, d.rowmax[it]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = s;
+    redm[threadIdx.x >> 5] = mx;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k];
+    double t = 0.0, tm = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      t += red[k];
+      tm = fmax(tm, redm[k]);
+    }
     d.mass[j] = t;
+    int L, sc;
+    resample_plan(m, j, d.n_pred[j], t, tm, L, sc);
+    d.rs_mass[j] = t;
+    d.rs_s[j] = sc;
+    d.rs_L[j] = L;
   }
 }
 
@@ -212,19 +279,22 @@ int grid_items(const Model& m) {
   return (int)(items < g ? (items > 0 ? items : 1) : g);
 }
 
+static int grid_cap(long items, long cap) { return (int)(items < cap ? (items > 0 ? items : 1) : cap); }
+
 template <class R>
 cudaError_t prepare_kernels(const Model& m) {
-  size_t sm = (sizeof(V2<R>) + sizeof(R)) * (size_t)m.m_max;
+  size_t sm = sizeof(Z4<R>) * (size_t)m.m_max;
   return cudaFuncSetAttribute(k_rowsum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 template <class R>
 cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
-  const int g = grid_items(m);
-  k_colsum<R><<<g, kThreads, 0, s>>>(d, m);
-  k_finalize<R><<<(m.m_max + 255) / 256, 256, 0, s>>>(d, m);
-  size_t sm = (sizeof(V2<R>) + sizeof(R)) * (size_t)m.m_max;
-  k_rowsum<R><<<g, kThreads, sm, s>>>(d, m);
+  const long tiles = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
+  const long chunks = (m.m_max + kMChunk - 1) / kMChunk;
+  k_colsum<R><<<grid_cap(tiles * chunks, 152L * 8), kThreads, 0, s>>>(d, m);
+  k_finalize<R><<<grid_cap((m.m_max + 7) / 8, 152L * 4), 256, 0, s>>>(d, m);
+  const long rtiles = (long)m.K * ((m.pe_cap + kRowTile - 1) / kRowTile);
+  k_rowsum<R><<<grid_cap(rtiles, 152L * 8), kThreads, sizeof(Z4<R>) * (size_t)m.m_max, s>>>(d, m);
   k_mass<<<m.K, 256, 0, s>>>(d, m);
   return cudaGetLastError();
 }

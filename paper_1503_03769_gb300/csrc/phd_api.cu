@@ -81,7 +81,11 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.C = cv.take<double>(K * Mm);
   t.Cused = cv.take<double>(K * Mm);
   t.ginv = cv.take<char>(K * Mm, rs);
-  t.rowpart = cv.take<double>(items);
+  const size_t ritems = K * ((P + phd::kRowTile - 1) / phd::kRowTile);
+  const size_t chunks = K * ((P + phd::kChunk - 1) / phd::kChunk);
+  t.rowpart = cv.take<double>(ritems);
+  t.rowmax = cv.take<double>(ritems);
+  t.dwkey = cv.take<unsigned long long>(K * Mm);
   t.mass = cv.take<double>(K);
   t.nsel = cv.take<int>(K);
   t.sel = cv.take<int>(K * Mm);
@@ -92,7 +96,9 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.rs_mass = cv.take<double>(K);
   t.rs_s = cv.take<int>(K);
   t.rs_L = cv.take<int>(K);
-  t.Q = cv.take<unsigned long long>(K * P);
+  t.csum = cv.take<unsigned long long>(chunks);
+  t.coff = cv.take<unsigned long long>(chunks);
+  t.rs_Qn = cv.take<unsigned long long>(K);
   t.child_end = cv.take<int>(K * P);
   t.parent = cv.take<int>(K * P);
   t.xslots = cv.take<int>(K * P);

@@ -17,7 +17,10 @@ namespace phd {
 
 constexpr int kMaxPE = 256;
 constexpr int kMaxM = 4096;
-constexpr int kTile = 256;        // particles per work item of the pair kernels
+constexpr int kTile = 256;        // particles per work item of pass 1 and pass 3
+constexpr int kRowTile = 64;      // particles per work item of pass 2 (4 lanes each)
+constexpr int kChunk = 1024;      // particles per chunk of the resampling scan
+constexpr int kMChunk = 256;      // measurements per work item of pass 1
 constexpr int kThreads = 256;     // threads of the pair kernels
 
 // Real-typed particle state [x, vx, y, vy].
@@ -80,7 +83,9 @@ struct Dev {
   double* C;             // [K][m_max] C^j (with p_D cnorm)
   double* Cused;         // [K][m_max] normaliser each PE applies
   void* ginv;            // R [K][m_max]  cnorm p_D / (kappa + Cused)
-  double* rowpart;       // [max_items] pass-2 partial sums of updated weights
+  double* rowpart;       // [K*ceil(pe_cap/kRowTile)] pass-2 sums of updated weights
+  double* rowmax;        // same: largest updated weight per tile
+  unsigned long long* dwkey; // [K][m_max] order keys of dW^{j,p}
   double* mass;          // [K] updated mass N^j
   int* nsel;             // [K] labels selected per PE
   int* sel;              // [K][m_max] selected labels, selection order
@@ -91,7 +96,9 @@ struct Dev {
   double* rs_mass;       // [K] mass before resampling
   int* rs_s;             // [K] CDF scale exponent
   int* rs_L;             // [K] resample counts
-  unsigned long long* Q; // [K*pe_cap] integer CDF
+  unsigned long long* csum;  // [K*ceil(pe_cap/kChunk)] CDF chunk totals
+  unsigned long long* coff;  // same: exclusive chunk offsets
+  unsigned long long* rs_Qn; // [K] CDF total
   int* child_end;        // [K*pe_cap]
   int* parent;           // [K*pe_cap]
   int* xslots;           // [K][pe_cap] exchange slots
@@ -167,6 +174,10 @@ constexpr int kAnchors = 256;
 struct Anchor { float c, s, th_hi, th_lo; };
 
 template <class R> struct H3 { R h0, h1, h1lo; };
+// a particle's sensor-space geometry and weight, packed for one shared load
+template <class R> struct alignas(4 * sizeof(R)) P4 { R h0, h1, h1lo, w; };
+// a measurement and its 1 / normaliser, packed for one shared load
+template <class R> struct alignas(4 * sizeof(R)) Z4 { R z0, z1, g, pad; };
 
 // Likelihood constants: q = b0 d0^2 + b1 d1^2 with b = log2(e) / (2 sigma^2),
 // so g = cnorm 2^-q; the bearing period 2 pi as a double-float.
@@ -256,10 +267,10 @@ __device__ __forceinline__ R qform(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1
 // Work-item decode for the pair kernels: item -> (PE, particle tile), tiles
 // of kTile over each PE's count.  pref gets K+1 entries in shared memory; the
 // block needs at least kMaxPE threads (tile counts are scanned in parallel).
-__device__ __forceinline__ void item_prefix(const int* n, int K, int* pref) {
+__device__ __forceinline__ void item_prefix(const int* n, int K, int* pref, int tile = kTile) {
   __shared__ int wt[kMaxPE / 32];
   const int t = threadIdx.x;
-  const int v = t < K ? (n[t] + kTile - 1) / kTile : 0;
+  const int v = t < K ? (n[t] + tile - 1) / tile : 0;
   const int lane = t & 31, wid = t >> 5;
   int incl = v;
   for (int o = 1; o < 32; o <<= 1) {
