@@ -227,6 +227,44 @@ phd_status phd_get_resample(phd_handle *h, int32_t *d_parents, int32_t *h_lx);
 phd_status phd_get_step(phd_handle *h, uint64_t *step);
 phd_status phd_set_step(phd_handle *h, uint64_t step);
 
+/* ---- batches of independent filters --------------------------------------- */
+
+/* A batch runs `runs` independent one-PE filters (Monte-Carlo runs, sensors
+ * or sectors tracked separately) as one stage-synchronous pipeline: every
+ * stage of every run is split into work items (particle tiles x measurement
+ * chunks) that the kernels balance over the whole GPU, and a batched step is
+ * one CUDA graph for all runs.  cfgs[j] describes run j (num_pe must be 1);
+ * the runs must share the sensor model, precision, noise, region, dynamics,
+ * p_S, p_D and seed, and may differ in clutter_rate, birth_count,
+ * birth_mass, particles_per_target, pe_cap and m_max.  1 <= runs <= 256.
+ * The paper's filter is run per run; batching is this library's addition. */
+phd_status phd_batch_workspace_size(const phd_config *cfgs, int32_t runs, size_t *bytes);
+
+/* As phd_init for a batch (same workspace and stream ownership).  The state
+ * accessors (phd_get_state, phd_set_state, phd_get_update, ...) see the runs
+ * as K = runs slices of the largest pe_cap / m_max.  Synchronises. */
+phd_status phd_batch_init(phd_handle **h, const phd_config *cfgs, int32_t runs, void *d_workspace, size_t bytes,
+                          void *stream);
+
+/* One step of every run with in-kernel random numbers.  d_Z: real rows of all
+ * runs' scans back to back; d_offsets: device int32 [runs+1], run j's scan is
+ * rows d_offsets[j] .. d_offsets[j+1]-1 (at most the largest m_max of the
+ * runs; a run over it is given no measurements and PHD_ERR_CAPACITY is
+ * reported at the next synchronising call).  Outputs per run j, ascending label:
+ * d_states real [runs][cap][4], d_labels int32 [runs][cap], d_counts int32
+ * [runs] (true counts).  Asynchronous.  Errors: PHD_ERR_STATE on a one-filter
+ * handle; PHD_ERR_INVALID_ARG for NULL buffers. */
+phd_status phd_batch_step(phd_handle *h, const void *d_Z, const int32_t *d_offsets, void *d_states,
+                          int32_t *d_labels, int32_t *d_counts, int32_t cap);
+
+/* phd_batch_step with caller random numbers (either may be NULL for Philox):
+ * d_noise real [runs][pe_cap][4] as for phd_predict (pe_cap the largest of the
+ * runs), d_u uint32 [runs] resampling uniforms.  The stages run one by one
+ * instead of as a graph. */
+phd_status phd_batch_step_inject(phd_handle *h, const void *d_Z, const int32_t *d_offsets, const void *d_noise,
+                                 const uint32_t *d_u, void *d_states, int32_t *d_labels, int32_t *d_counts,
+                                 int32_t cap);
+
 /* ---- counters and the update-stage timer ---------------------------------- */
 
 typedef struct phd_stats {

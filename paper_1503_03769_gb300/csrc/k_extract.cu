@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
   const int j = blockIdx.x;
-  const int M = *d.M;
+  const int M = slice_M(d, j);
   if (threadIdx.x == 0) npos_s = 0;
   for (int p = threadIdx.x; p < M; p += blockDim.x) key[p] = d.dwkey[j * m.m_max + p];
   __syncthreads();
@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   const int total = pref[K];
-  const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
@@ -92,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
     const int j = item_pe(pref, K, item);
     const int ns = d.nsel[j];
     if (ns <= 0) continue;   // uniform over the block
+    const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
     const int tile = item - pref[j];
     const long base = (long)j * m.pe_cap + (long)tile * kTile;
     const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   St4<R>* est = static_cast<St4<R>*>(d.est_local);
-  const V2<R>* Zr = static_cast<const V2<R>*>(d.Z);
   const int lane = threadIdx.x & 31;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
   const long total = (long)K * m.m_max;
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
     if (lane == 0) {
       const int p = d.sel[j * m.m_max + r];
       R px, py;
-      meas_point<R>(m, Zr[p], px, py);
+      meas_point<R>(m, slice_Z<R>(d, j)[p], px, py);
       St4<R> o;
       if (a0 > 0.0) {
         o.x = (R)((double)px + a1 / a0);
@@ -264,6 +263,61 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
   }
 }
 
+// Independent runs (a batch): run j's estimates are its local estimates, in
+// ascending label order (the fusion rule with one voter).  One CTA per run.
+template <class R>
+__global__ void __launch_bounds__(1024) k_batch_out(Dev d, Model m, R* out_states, int* out_labels, int* counts,
+                                                    int cap) {
+  __shared__ int wsum[32];
+  __shared__ int carry_s;
+  const int j = blockIdx.x;
+  const int M = slice_M(d, j);
+  const St4<R>* est = static_cast<const St4<R>*>(d.est_local);
+  St4<R>* out = reinterpret_cast<St4<R>*>(out_states) + (long)j * cap;
+  int* lab = out_labels + (long)j * cap;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int p0 = 0; p0 < M; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const int r = p < M ? d.selrank[j * m.m_max + p] : -1;
+    const int valid = r >= 0 ? 1 : 0;
+    int incl = valid;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < nw) wsum[lane] = v;
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
+    if (valid && idx < cap) {
+      out[idx] = est[j * m.m_max + r];
+      lab[idx] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + wsum[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) counts[j] = carry_s;
+}
+
+template <class R>
+cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* out_labels, int* counts, int cap,
+                             cudaStream_t s) {
+  k_batch_out<R><<<m.K, 1024, 0, s>>>(d, m, out_states, out_labels, counts, cap);
+  return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
@@ -273,10 +327,12 @@ cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out
   int b = (int)((warps + 7) / 8);
   if (b > 152 * 8) b = 152 * 8;
   k_est_local<R><<<b, 256, 0, s>>>(d, m);
-  k_fuse<R><<<1, 1024, 0, s>>>(d, m, out_states, out_labels, cap, d_count);
+  if (d.zshared) k_fuse<R><<<1, 1024, 0, s>>>(d, m, out_states, out_labels, cap, d_count);
   return cudaGetLastError();
 }
 
+template cudaError_t launch_batch_out<float>(const Dev&, const Model&, float*, int*, int*, int, cudaStream_t);
+template cudaError_t launch_batch_out<double>(const Dev&, const Model&, double*, int*, int*, int, cudaStream_t);
 template cudaError_t launch_extract<float>(const Dev&, const Model&, float*, int*, int, int*, cudaStream_t);
 template cudaError_t launch_extract<double>(const Dev&, const Model&, double*, int*, int, int*, cudaStream_t);
 

@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     // ---- resampling (Step 5): exact integer CDF, offspring counts, gather
     if (tid == 0) {
       int Lc, sc;
-      resample_plan(m, j, np, N, (double)wmaxr, Lc, sc);
+      resample_plan(m.rho_pe, m.pe_cap - Jj, np, N, (double)wmaxr, Lc, sc);
       bL = Lc;
       bS = sc;
       bW = Lc > 0 ? (R)(N / (double)Lc) : (R)0;

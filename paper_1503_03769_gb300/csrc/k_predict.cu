@@ -18,28 +18,36 @@
 
 namespace phd {
 
+template <class R> __device__ __forceinline__ R slice_bw(const Dev& d, int j);
+template <> __device__ __forceinline__ float slice_bw<float>(const Dev& d, int j) { return d.bwf[j]; }
+template <> __device__ __forceinline__ double slice_bw<double>(const Dev& d, int j) { return d.bwd[j]; }
+
 template <class R>
 __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __restrict__ noise) {
+  __shared__ int pref[kMaxPE + 1];
+  const int K = m.K;
+  // work items: tiles of 256 over each slice's survivors + births
+  slice_prefix(K, pref, [&](int j) { return (d.n_cur[j] + d.Jb[j] + 255) / 256; });
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) d.n_pred[j] = d.n_cur[j] + d.Jb[j];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
   const R* __restrict__ w = static_cast<const R*>(d.w);
   St4<R>* __restrict__ xp = static_cast<St4<R>*>(d.x_alt);
   R* __restrict__ wp = static_cast<R*>(d.w_alt);
   const unsigned long long step = *d.step;
   const Cst<R> c = consts<R>(m);
-  const long total = (long)m.K * m.pe_cap;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(g / m.pe_cap);
-    const int i = (int)(g - (long)j * m.pe_cap);
+  for (int item = blockIdx.x; item < pref[K]; item += gridDim.x) {
+    const int j = item_pe(pref, K, item);
+    const int i = (item - pref[j]) * 256 + threadIdx.x;
     const int L = d.n_cur[j];
-    const int Jj = births_of(m.J, m.K, j);
-    if (i == 0) d.n_pred[j] = L + Jj;
-    if (i >= L + Jj) continue;
+    if (i >= L + d.Jb[j]) continue;
+    const long g = (long)j * m.pe_cap + i;
     R n1, n2, u1, u2;
     draw_noise<R>(m, noise, g, step, n1, n2, u1, u2);
     const bool surv = i < L;
     St4<R> o;
     R wo;
-    predict_slot<R>(c, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, birth_weight<R>(c, m, j), n1, n2,
+    predict_slot<R>(c, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j), n1, n2,
                     u1, u2, o, wo);
     xp[g] = o;
     wp[g] = wo;
@@ -61,12 +69,49 @@ __global__ void k_stage_z(Dev d, Model, const R* Z, int M) {
 
 template <class R>
 cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s) {
-  long total = (long)m.K * m.pe_cap;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  long items = (long)m.K * ((m.pe_cap + 255) / 256);
+  int blocks = (int)(items < 152 * 16 ? (items > 0 ? items : 1) : 152 * 16);
   k_predict<R><<<blocks, 256, 0, s>>>(d, m, noise);
   return cudaGetLastError();
 }
+
+// Batch staging: the scans of all runs back to back; run j owns rows
+// off[j] .. off[j+1]-1 (each at most m_max, all within the workspace).
+template <class R>
+__global__ void k_stage_zb(Dev d, Model m, const R* Z, const int* __restrict__ off) {
+  const int K = m.K;
+  const int rows = off[K];
+  const bool ok_total = rows >= 0 && rows <= K * m.m_max;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+    int Mj = off[j + 1] - off[j];
+    if (!ok_total || off[j] < 0 || Mj < 0 || Mj > m.m_max) {
+      atomicOr(d.err, kErrCapacity);
+      Mj = 0;
+    }
+    d.zoff[j] = ok_total && off[j] >= 0 ? off[j] : 0;
+    d.Mj[j] = Mj;
+  }
+  if (!ok_total) return;
+  V2<R>* zs = static_cast<V2<R>*>(d.Z);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows; p += gridDim.x * blockDim.x) {
+    V2<R> z = reinterpret_cast<const V2<R>*>(Z)[p];
+    if (!isfinite(z.a) || !isfinite(z.b)) atomicOr(d.err, kErrNonFinite);
+    zs[p] = z;
+  }
+}
+
+template <class R>
+cudaError_t launch_stage_zb(const Dev& d, const Model& m, const R* Z, const int* off, cudaStream_t s) {
+  long rows = (long)m.K * m.m_max;
+  int blocks = (int)((rows + 255) / 256);
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks < 1) blocks = 1;
+  k_stage_zb<R><<<blocks, 256, 0, s>>>(d, m, Z, off);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_stage_zb<float>(const Dev&, const Model&, const float*, const int*, cudaStream_t);
+template cudaError_t launch_stage_zb<double>(const Dev&, const Model&, const double*, const int*, cudaStream_t);
 
 template <class R>
 cudaError_t launch_stage_z(const Dev& d, const Model& m, const R* Z, int M, cudaStream_t s) {

@@ -112,23 +112,28 @@ __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint3
 
 // Scatter by parent: particle i of PE j has children child_end[i-1] ..
 // child_end[i]-1 (parents in order, children in order), which get its
-// predicted state and the weight N^j / L_j.
+// predicted state and the weight N^j / L_j.  Work items: tiles of 256 over
+// each slice's predicted particles.
 template <class R>
-__global__ void k_rs_gather(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
+  __shared__ int pref[kMaxPE + 1];
+  const int K = m.K;
+  item_prefix(d.n_pred, K, pref);
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) d.n_cur[j] = d.rs_L[j];
   const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
   St4<R>* x = static_cast<St4<R>*>(d.x);
   R* w = static_cast<R*>(d.w);
-  const long total = (long)m.K * m.pe_cap;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(g / m.pe_cap);
-    const int i = (int)(g - (long)j * m.pe_cap);
+  for (int item = blockIdx.x; item < pref[K]; item += gridDim.x) {
+    const int j = item_pe(pref, K, item);
+    const int i = (item - pref[j]) * kTile + threadIdx.x;
     const int L = d.rs_L[j];
-    if (i == 0) d.n_cur[j] = L;
     if (i >= d.n_pred[j] || L == 0) continue;
+    const long base = (long)j * m.pe_cap;
+    const long g = base + i;
     const int t1 = d.child_end[g];
     const int t0 = i > 0 ? d.child_end[g - 1] : 0;
     if (t1 <= t0) continue;
-    const long base = (long)j * m.pe_cap;
     const St4<R> s = xp[g];
     const R wn = (R)(d.rs_mass[j] / (double)L);
     for (int t = t0; t < t1; ++t) {
@@ -220,7 +225,8 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   k_rs_q<R><<<gc, kChunk, 0, s>>>(d, m);
   k_rs_off<<<m.K, 1024, 0, s>>>(d, m);
   k_rs_count<R><<<gc, kChunk, 0, s>>>(d, m, u);
-  k_rs_gather<R><<<b, 256, 0, s>>>(d, m);
+  const long gitems = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
+  k_rs_gather<R><<<(int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16), 256, 0, s>>>(d, m);
   if (m.K > 1 && m.exchange_frac > 0.0) {
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
     if (bx < 1) bx = 1;

@@ -30,25 +30,29 @@ namespace phd {
 
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
-  __shared__ int pref[kMaxPE + 1];
+  __shared__ int tpref[kMaxPE + 1];   // tiles per slice (pass-1 partial rows)
+  __shared__ int ipref[kMaxPE + 1];   // work items per slice (tiles x measurement chunks)
   __shared__ P4<R> sp[kTile];
   __shared__ double red[kThreads];
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref);
-  const int M = *d.M;
-  if (M <= 0) return;
-  const int chunks = (M + kMChunk - 1) / kMChunk;
-  const int total = pref[K] * chunks;
-  const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
+  item_prefix(d.n_pred, K, tpref);
+  slice_prefix(K, ipref, [&](int j) {
+    return ((d.n_pred[j] + kTile - 1) / kTile) * ((slice_M(d, j) + kMChunk - 1) / kMChunk);
+  });
+  const int total = ipref[K];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int titem = item / chunks, chunk = item - titem * chunks;
-    const int j = item_pe(pref, K, titem);
-    const int tile = titem - pref[j];
+    const int j = item_pe(ipref, K, item);
+    const int M = slice_M(d, j);
+    const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+    const int chunks = (M + kMChunk - 1) / kMChunk;
+    const int local = item - ipref[j];
+    const int tile = local / chunks, chunk = local - tile * chunks;
+    const int titem = tpref[j] + tile;
     const long base = (long)j * m.pe_cap + (long)tile * kTile;
     const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
     if (titem != staged) {   // consecutive items of a CTA often share the tile
@@ -100,45 +104,72 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   }
 }
 
-// One warp per measurement: C^j_p = p_D cnorm * (FP64 tree over PE j's tile
-// partials, fixed order), the normaliser each PE applies, ginv and the dW
-// order keys.
+// One warp per (slice, measurement): C^j_p = p_D cnorm * (FP64 tree over
+// slice j's tile partials, fixed order), the normaliser the slice applies
+// (its own, or for one filter's PEs in "global" mode the PE mean), ginv and
+// the dW order keys.
 template <class R>
 __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
+  __shared__ int mpref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
-  const int M = *d.M;
+  slice_prefix(K, mpref, [&](int j) { return slice_M(d, j); });
   const double cs = m.p_d * m.cnorm;
   R* ginv = static_cast<R*>(d.ginv);
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < M; p += nwarps) {
-    double mean = 0.0;
-    for (int j = 0; j < K; ++j) {
+  const int wid0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (m.ck_global && d.zshared) {
+    // one filter's PEs share Z: a warp per measurement handles every PE
+    const int M = *d.M;
+    for (int p = wid0; p < M; p += nwarps) {
+      double mean = 0.0;
+      for (int j = 0; j < K; ++j) {
+        double c = 0.0;
+        for (int it = pref[j] + lane; it < pref[j + 1]; it += 32) c += d.colpart[(long)it * m.m_max + p];
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        c = __shfl_sync(0xffffffffu, c, 0) * cs;
+        if (lane == 0) d.C[j * m.m_max + p] = c;
+        mean += c;
+      }
+      mean /= (double)K;
+      for (int j = lane; j < K; j += 32) {
+        const double cj = d.C[j * m.m_max + p];
+        d.Cused[j * m.m_max + p] = mean;
+        const double den = d.kap[j] + mean;
+        ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
+        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? cj / den : 0.0);
+      }
+    }
+  } else {
+    for (int gw = wid0; gw < mpref[K]; gw += nwarps) {
+      const int j = item_pe(mpref, K, gw);
+      const int p = gw - mpref[j];
       double c = 0.0;
       for (int it = pref[j] + lane; it < pref[j + 1]; it += 32) c += d.colpart[(long)it * m.m_max + p];
       for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      c = __shfl_sync(0xffffffffu, c, 0) * cs;
-      if (lane == 0) d.C[j * m.m_max + p] = c;
-      mean += c;
-    }
-    mean /= (double)K;
-    for (int j = lane; j < K; j += 32) {
-      const double cj = d.C[j * m.m_max + p];
-      const double cu = m.ck_global ? mean : cj;
-      d.Cused[j * m.m_max + p] = cu;
-      const double den = m.kappa + cu;
-      ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
-      d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? cj / den : 0.0);
+      if (lane == 0) {
+        c *= cs;
+        d.C[j * m.m_max + p] = c;
+        d.Cused[j * m.m_max + p] = c;
+        const double den = d.kap[j] + c;
+        ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
+        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? c / den : 0.0);
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    unsigned long long n = 0;
-    for (int j = 0; j < K; ++j) n += (unsigned long long)d.n_pred[j];
-    d.stats[0] += n * (unsigned long long)M;
+    unsigned long long n = 0, pairs = 0, meas = 0;
+    for (int j = 0; j < K; ++j) {
+      const unsigned long long Mj = (unsigned long long)slice_M(d, j);
+      n += (unsigned long long)d.n_pred[j];
+      pairs += (unsigned long long)d.n_pred[j] * Mj;
+      meas += Mj;
+    }
+    d.stats[0] += pairs;
     d.stats[1] += n;
-    d.stats[2] += (unsigned long long)M;
+    d.stats[2] += d.zshared ? (unsigned long long)*d.M : meas;
     d.stats[3] += 1ull;
   }
 }
@@ -155,8 +186,6 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const int K = m.K;
   item_prefix(d.n_pred, K, pref, kRowTile);
   const int total = pref[K];
-  const int M = *d.M;
-  const V2<R>* __restrict__ Z = static_cast<const V2<R>*>(d.Z);
   const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
@@ -169,6 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int tile = item - pref[j];
+    const int M = slice_M(d, j);
+    const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
     if (j != staged) {
       __syncthreads();
       for (int p = threadIdx.x; p < M; p += kThreads) {
@@ -266,7 +297,7 @@ __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
     }
     d.mass[j] = t;
     int L, sc;
-    resample_plan(m, j, d.n_pred[j], t, tm, L, sc);
+    resample_plan(d.rho[j], d.lmax[j], d.n_pred[j], t, tm, L, sc);
     d.rs_mass[j] = t;
     d.rs_s[j] = sc;
     d.rs_L[j] = L;
@@ -292,7 +323,7 @@ cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
   const long tiles = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
   const long chunks = (m.m_max + kMChunk - 1) / kMChunk;
   k_colsum<R><<<grid_cap(tiles * chunks, 152L * 8), kThreads, 0, s>>>(d, m);
-  k_finalize<R><<<grid_cap((m.m_max + 7) / 8, 152L * 4), 256, 0, s>>>(d, m);
+  k_finalize<R><<<grid_cap(((long)m.K * m.m_max + 7) / 8, 152L * 8), 256, 0, s>>>(d, m);
   const long rtiles = (long)m.K * ((m.pe_cap + kRowTile - 1) / kRowTile);
   k_rowsum<R><<<grid_cap(rtiles, 152L * 8), kThreads, sizeof(Z4<R>) * (size_t)m.m_max, s>>>(d, m);
   k_mass<<<m.K, 256, 0, s>>>(d, m);

@@ -41,6 +41,8 @@ struct phd_handle {
   bool fused_ok = false;   // the fused step kernel fits this configuration
   int path = 0;            // PHD_PATH_AUTO / PHD_PATH_STAGED / PHD_PATH_FUSED
   bool have_update = false;
+  int batch_runs = 0;      // > 0: a batch of independent one-PE filters
+  std::vector<int> slice_J;  // births per step of each slice (host copy)
 };
 
 namespace {
@@ -59,9 +61,10 @@ struct Carver {
 };
 
 // Lays out the workspace; with base == nullptr only measures it.
-size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** out_labels) {
+size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** out_labels, int batch_runs = 0) {
   const size_t rs = real_size(c);
-  const size_t K = (size_t)c.num_pe, P = (size_t)c.pe_cap, Mm = (size_t)c.m_max;
+  const size_t K = batch_runs > 0 ? (size_t)batch_runs : (size_t)c.num_pe, P = (size_t)c.pe_cap,
+               Mm = (size_t)c.m_max;
   const size_t items = K * ((P + phd::kTile - 1) / phd::kTile);
   Carver cv{base};
   Dev t{};
@@ -74,7 +77,16 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.w_out = cv.take<char>(K * P, rs);
   t.n_cur = cv.take<int>(K);
   t.n_pred = cv.take<int>(K);
-  t.Z = cv.take<char>(Mm, 2 * rs);
+  t.Z = cv.take<char>(batch_runs > 0 ? K * Mm : Mm, 2 * rs);
+  t.zshared = batch_runs > 0 ? 0 : 1;
+  t.zoff = cv.take<int>(K);
+  t.Mj = cv.take<int>(K);
+  t.kap = cv.take<double>(K);
+  t.rho = cv.take<double>(K);
+  t.Jb = cv.take<int>(K);
+  t.bwf = cv.take<float>(K);
+  t.bwd = cv.take<double>(K);
+  t.lmax = cv.take<int>(K);
   t.anchors = cv.take<phd::Anchor>(phd::kAnchors);
   t.M = cv.take<int>(1);
   t.colpart = cv.take<double>(items * Mm);
@@ -213,6 +225,46 @@ phd_status cuda_fail(phd_handle* h, cudaError_t e, const char* where) {
 
 bool is_fp64(const phd_handle* h) { return h->cfg.precision == PHD_FP64; }
 
+// Per-slice descriptors: one per PE of a filter (each PE a full filter on its
+// slice, births split J/K) or one per run of a batch (slice j = run j).
+cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
+  const int K = (int)cf.size();
+  const bool batch = h->batch_runs > 0;
+  std::vector<double> kap(K), rho(K), bwd(K);
+  std::vector<float> bwf(K);
+  std::vector<int> Jb(K), lmax(K), zero(K, 0);
+  const double kPi = 3.14159265358979323846;
+  for (int j = 0; j < K; ++j) {
+    const phd_config& c = cf[j];
+    const double vol = c.meas_model == PHD_MEAS_LINEAR ? (c.region[1] - c.region[0]) * (c.region[3] - c.region[2])
+                                                       : c.r_max * 2.0 * kPi;
+    kap[j] = c.clutter_rate / vol;
+    if (batch) {
+      rho[j] = c.particles_per_target;
+      Jb[j] = c.birth_count;
+      lmax[j] = c.pe_cap - c.birth_count;
+    } else {
+      rho[j] = c.particles_per_target / (double)c.num_pe;
+      Jb[j] = phd::births_of(c.birth_count, c.num_pe, j);
+      lmax[j] = c.pe_cap - Jb[j];
+    }
+    bwd[j] = Jb[j] > 0 ? c.birth_mass / (double)Jb[j] : 0.0;
+    bwf[j] = (float)bwd[j];
+  }
+  h->slice_J = Jb;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemcpyAsync(h->d.kap, kap.data(), K * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.rho, rho.data(), K * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.bwd, bwd.data(), K * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.bwf, bwf.data(), K * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.Jb, Jb.data(), K * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.lmax, lmax.data(), K * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.zoff, zero.data(), K * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.Mj, zero.data(), K * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope
+  return e;
+}
+
 // kernels each stage launches (for the launch counter)
 constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
@@ -240,6 +292,7 @@ phd_status do_predict(phd_handle* h, const void* noise) {
 }
 
 phd_status do_update(phd_handle* h, const void* Z, int M, bool z_in_workspace) {
+  if (h->batch_runs) return fail(h, PHD_ERR_STATE, "a batch handle updates through phd_batch_step");
   if (h->stage != kPredicted) return fail(h, PHD_ERR_STATE, "phd_update: call phd_predict first");
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
@@ -377,7 +430,7 @@ phd_status run_step_body(phd_handle* h) {
     if (e == cudaSuccess) e = cudaGraphLaunch(h->g_post, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
-  h->launches += kNPredict + kNUpdate + kNExtract + n_resample(h->m) + kNAdvance;
+  h->launches += kNPredict + kNUpdate + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) + kNAdvance;
   return PHD_OK;
 }
 
@@ -532,6 +585,7 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
   phd::fill_anchor_table(tab);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(const_cast<void*>(h->d.anchors), tab, sizeof(tab), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = upload_slices(h, std::vector<phd_config>(cfg->num_pe, *cfg));
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     delete h;
@@ -584,6 +638,7 @@ phd_status phd_step_inject(phd_handle* h, const void* d_Z, int32_t M, const void
                            const uint32_t* d_xu, void* d_states, int32_t* d_labels, int32_t cap, int32_t* d_count,
                            int32_t* h_count) {
   if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->batch_runs) return fail(h, PHD_ERR_STATE, "a batch handle steps through phd_batch_step");
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_step: a step is already in progress");
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
@@ -604,6 +659,7 @@ phd_status phd_step_inject(phd_handle* h, const void* d_Z, int32_t M, const void
 phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_states, int32_t* h_labels, int32_t cap,
                          int32_t* h_count) {
   if (!h || !h_count) return PHD_ERR_INVALID_ARG;
+  if (h->batch_runs) return fail(h, PHD_ERR_STATE, "a batch handle steps through phd_batch_step");
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_step_host: a step is already in progress");
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
@@ -635,6 +691,7 @@ phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_stat
 phd_status phd_run(phd_handle* h, const void* d_Z, const int32_t* d_offsets, int32_t S, void* d_states,
                    int32_t* d_labels, int32_t* d_counts, int32_t cap) {
   if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->batch_runs) return fail(h, PHD_ERR_STATE, "a batch handle steps through phd_batch_step");
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_run: a step is already in progress");
   if (S < 0 || !d_offsets || (S > 0 && (!d_counts || cap < 1 || !d_states || !d_labels)))
     return fail(h, PHD_ERR_INVALID_ARG, "bad phd_run arguments");
@@ -675,7 +732,7 @@ phd_status phd_get_path(phd_handle* h, int32_t* path) {
 phd_status phd_get_predicted(phd_handle* h, void* d_x, void* d_w_pred, void* d_w_upd, int32_t* h_counts) {
   if (!h) return PHD_ERR_INVALID_ARG;
   if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_get_predicted: no update has run");
-  const int K = h->cfg.num_pe;
+  const int K = h->m.K;
   const size_t rs = real_size(h->cfg);
   const size_t n = (size_t)K * h->cfg.pe_cap;
   if (d_x) PHD_CUDA(h, cudaMemcpyAsync(d_x, h->d.x_alt, n * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
@@ -689,9 +746,9 @@ phd_status phd_get_predicted(phd_handle* h, void* d_x, void* d_w_pred, void* d_w
 
 phd_status phd_set_state(phd_handle* h, const void* d_x, const void* d_w, const int32_t* h_counts) {
   if (!h || !d_x || !d_w || !h_counts) return PHD_ERR_INVALID_ARG;
-  const int K = h->cfg.num_pe;
+  const int K = h->m.K;
   for (int j = 0; j < K; ++j) {
-    const int lim = h->cfg.pe_cap - phd::births_of(h->cfg.birth_count, K, j);
+    const int lim = h->cfg.pe_cap - h->slice_J[j];
     if (h_counts[j] < 0 || h_counts[j] > lim) return fail(h, PHD_ERR_CAPACITY, "count exceeds pe_cap - J_j");
   }
   const size_t rs = real_size(h->cfg);
@@ -706,7 +763,7 @@ phd_status phd_set_state(phd_handle* h, const void* d_x, const void* d_w, const 
 
 phd_status phd_get_state(phd_handle* h, void* d_x, void* d_w, int32_t* h_counts) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  const int K = h->cfg.num_pe;
+  const int K = h->m.K;
   const size_t rs = real_size(h->cfg);
   const size_t n = (size_t)K * h->cfg.pe_cap;
   const void* xs = h->stage == kReady ? h->d.x : h->d.x_alt;
@@ -723,7 +780,7 @@ phd_status phd_get_state(phd_handle* h, void* d_x, void* d_w, int32_t* h_counts)
 phd_status phd_get_update(phd_handle* h, double* d_C, double* h_mass) {
   if (!h) return PHD_ERR_INVALID_ARG;
   if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_get_update: no update has run");
-  const size_t K = h->cfg.num_pe, Mm = h->cfg.m_max;
+  const size_t K = h->m.K, Mm = h->cfg.m_max;
   if (d_C) PHD_CUDA(h, cudaMemcpyAsync(d_C, h->d.C, K * Mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (h_mass) {
     // the updated mass is finalised by the extraction's selection kernel; run
@@ -736,7 +793,7 @@ phd_status phd_get_update(phd_handle* h, double* d_C, double* h_mass) {
 
 phd_status phd_get_local_estimates(phd_handle* h, void* d_states, int32_t* d_labels, int32_t* h_counts) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  const size_t K = h->cfg.num_pe, Mm = h->cfg.m_max, rs = real_size(h->cfg);
+  const size_t K = h->m.K, Mm = h->cfg.m_max, rs = real_size(h->cfg);
   if (d_states)
     PHD_CUDA(h, cudaMemcpyAsync(d_states, h->d.est_local, K * Mm * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
   if (d_labels)
@@ -748,11 +805,11 @@ phd_status phd_get_local_estimates(phd_handle* h, void* d_states, int32_t* d_lab
 
 phd_status phd_get_resample(phd_handle* h, int32_t* d_parents, int32_t* h_lx) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  const size_t n = (size_t)h->cfg.num_pe * h->cfg.pe_cap;
+  const size_t n = (size_t)h->m.K * h->cfg.pe_cap;
   if (d_parents)
     PHD_CUDA(h, cudaMemcpyAsync(d_parents, h->d.parent, n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
   if (h_lx) {
-    if (h->cfg.num_pe > 1 && h->cfg.exchange_frac > 0)
+    if (h->m.K > 1 && h->cfg.exchange_frac > 0)
       PHD_CUDA(h, cudaMemcpyAsync(h_lx, h->d.lx, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     else
       *h_lx = 0;
@@ -808,6 +865,141 @@ phd_status phd_reset_stats(phd_handle* h) {
   h->launches = 0;
   h->timer_ms = 0.0;
   h->timer_calls = 0;
+  return PHD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Fields every run of a batch must share (the sensor model and dynamics the
+// kernels take as constants); per-run fields are clutter, births, rho, sizes.
+const char* batch_problem(const phd_config* c, int runs) {
+  if (!c || runs < 1 || runs > phd::kMaxPE) return "runs must be in 1..256";
+  for (int j = 0; j < runs; ++j) {
+    if (check_config(c[j])) return check_config(c[j]);
+    if (c[j].num_pe != 1) return "every run of a batch is a one-PE filter";
+    const phd_config& a = c[0];
+    const phd_config& b = c[j];
+    if (b.meas_model != a.meas_model || b.precision != a.precision || b.sigma_z[0] != a.sigma_z[0] ||
+        b.sigma_z[1] != a.sigma_z[1] || b.sensor[0] != a.sensor[0] || b.sensor[1] != a.sensor[1] ||
+        b.region[0] != a.region[0] || b.region[1] != a.region[1] || b.region[2] != a.region[2] ||
+        b.region[3] != a.region[3] || b.r_max != a.r_max || b.dt != a.dt || b.sigma_a != a.sigma_a ||
+        b.p_s != a.p_s || b.p_d != a.p_d || b.birth_vel_sigma != a.birth_vel_sigma || b.seed != a.seed)
+      return "runs of a batch differ in a shared model field";
+  }
+  return nullptr;
+}
+
+phd_config batch_envelope(const phd_config* c, int runs) {
+  phd_config e = c[0];
+  for (int j = 1; j < runs; ++j) {
+    if (c[j].pe_cap > e.pe_cap) e.pe_cap = c[j].pe_cap;
+    if (c[j].m_max > e.m_max) e.m_max = c[j].m_max;
+  }
+  e.num_pe = 1;
+  e.ck_mode = PHD_CK_LOCAL;
+  e.exchange_frac = 0.0;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+phd_status phd_batch_workspace_size(const phd_config* cfgs, int32_t runs, size_t* bytes) {
+  if (!bytes || batch_problem(cfgs, runs)) return PHD_ERR_INVALID_ARG;
+  const phd_config e = batch_envelope(cfgs, runs);
+  *bytes = carve(e, nullptr, nullptr, nullptr, nullptr, runs);
+  return PHD_OK;
+}
+
+phd_status phd_batch_init(phd_handle** out, const phd_config* cfgs, int32_t runs, void* ws, size_t bytes,
+                          void* stream) {
+  if (!out) return PHD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (batch_problem(cfgs, runs)) return PHD_ERR_INVALID_ARG;
+  const phd_config e = batch_envelope(cfgs, runs);
+  const size_t need = carve(e, nullptr, nullptr, nullptr, nullptr, runs);
+  if (!ws || bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return PHD_ERR_INVALID_ARG;
+  phd_handle* h = new (std::nothrow) phd_handle();
+  if (!h) return PHD_ERR_INVALID_ARG;
+  h->cfg = e;
+  h->batch_runs = runs;
+  h->m = make_model(e);
+  h->m.K = runs;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->stage = kReady;
+  carve(e, static_cast<char*>(ws), &h->d, &h->out_states, &h->out_labels, runs);
+  cudaError_t err = cudaGetDevice(&h->device);
+  if (err == cudaSuccess) err = is_fp64(h) ? phd::prepare_kernels<double>(h->m) : phd::prepare_kernels<float>(h->m);
+  if (err == cudaSuccess) err = cudaMemsetAsync(ws, 0, need, h->stream);
+  phd::Anchor tab[phd::kAnchors];
+  phd::fill_anchor_table(tab);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(const_cast<void*>(h->d.anchors), tab, sizeof(tab), cudaMemcpyHostToDevice, h->stream);
+  if (err == cudaSuccess) err = upload_slices(h, std::vector<phd_config>(cfgs, cfgs + runs));
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  if (err != cudaSuccess) {
+    delete h;
+    return PHD_ERR_CUDA;
+  }
+  h->fused_ok = false;
+  *out = h;
+  return PHD_OK;
+}
+
+phd_status phd_batch_step(phd_handle* h, const void* d_Z, const int32_t* d_offsets, void* d_states,
+                          int32_t* d_labels, int32_t* d_counts, int32_t cap) {
+  return phd_batch_step_inject(h, d_Z, d_offsets, nullptr, nullptr, d_states, d_labels, d_counts, cap);
+}
+
+phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* d_offsets, const void* d_noise,
+                                 const uint32_t* d_u, void* d_states, int32_t* d_labels, int32_t* d_counts,
+                                 int32_t cap) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (!h->batch_runs) return fail(h, PHD_ERR_STATE, "phd_batch_step needs a handle from phd_batch_init");
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_batch_step: a step is already in progress");
+  if (!d_Z || !d_offsets || !d_counts || cap < 0 || (cap > 0 && (!d_states || !d_labels)))
+    return fail(h, PHD_ERR_INVALID_ARG, "bad phd_batch_step arguments");
+  cudaError_t e = is_fp64(h)
+      ? phd::launch_stage_zb<double>(h->d, h->m, static_cast<const double*>(d_Z), d_offsets, h->stream)
+      : phd::launch_stage_zb<float>(h->d, h->m, static_cast<const float*>(d_Z), d_offsets, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage_zb");
+  h->launches += 1;
+  phd_status st = PHD_OK;
+  if (d_noise || d_u) {
+    // caller random numbers: the stages one by one (no graph)
+    st = do_predict(h, d_noise);
+    if (st == PHD_OK) {
+      e = is_fp64(h) ? phd::launch_update<double>(h->d, h->m, h->stream)
+                     : phd::launch_update<float>(h->d, h->m, h->stream);
+      if (e != cudaSuccess) st = cuda_fail(h, e, "update");
+      h->launches += kNUpdate;
+      h->stage = kUpdated;
+    }
+    if (st == PHD_OK) {
+      e = is_fp64(h) ? phd::launch_extract<double>(h->d, h->m, nullptr, nullptr, 0, nullptr, h->stream)
+                     : phd::launch_extract<float>(h->d, h->m, nullptr, nullptr, 0, nullptr, h->stream);
+      if (e != cudaSuccess) st = cuda_fail(h, e, "extract");
+      h->launches += kNExtract - 1;
+    }
+    if (st == PHD_OK) st = do_resample(h, d_u, nullptr);
+    if (st != PHD_OK) {
+      h->stage = kReady;
+      return st;
+    }
+  } else {
+    st = run_step_body(h);
+    if (st != PHD_OK) return st;
+  }
+  e = is_fp64(h) ? phd::launch_batch_out<double>(h->d, h->m, static_cast<double*>(d_states), d_labels, d_counts,
+                                                 cap, h->stream)
+                 : phd::launch_batch_out<float>(h->d, h->m, static_cast<float*>(d_states), d_labels, d_counts, cap,
+                                                h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch_out");
+  h->launches += 1;
+  h->have_update = true;
   return PHD_OK;
 }
 

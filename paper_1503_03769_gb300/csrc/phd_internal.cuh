@@ -104,6 +104,17 @@ struct Dev {
   int* xslots;           // [K][pe_cap] exchange slots
   int* lx;               // [1] particles moved per PE
   unsigned int* bar;     // [2] grid barrier: arrival count, generation
+  // per-slice descriptors (a slice is a PE of one filter, or one run of a
+  // batch of independent filters); slot j*pe_cap .. of every [K][pe_cap] array
+  int zshared;           // 1: every slice uses Z rows 0 .. *M-1 (one filter)
+  int* zoff;             // [K] first measurement row of slice j (zshared == 0)
+  int* Mj;               // [K] measurement count of slice j (zshared == 0)
+  double* kap;           // [K] clutter intensity kappa of slice j
+  double* rho;           // [K] particles per target of slice j
+  int* Jb;               // [K] births per step of slice j
+  float* bwf;            // [K] birth weight nu_b / J_j (FP32 copy)
+  double* bwd;           // [K] birth weight nu_b / J_j
+  int* lmax;             // [K] largest resample count of slice j
   unsigned long long* step;  // [1] step counter (Philox counter word)
   unsigned long long* stats; // [4] sums over updates: pairs, particles, measurements, updates
   int* err;              // [1] device error bits
@@ -287,6 +298,30 @@ __device__ __forceinline__ void item_prefix(const int* n, int K, int* pref, int 
   }
   __syncthreads();
 }
+// Prefix over slices of per-slice item counts computed by cnt(j) (block of
+// >= kMaxPE threads); pref gets K+1 entries.
+template <class F>
+__device__ __forceinline__ void slice_prefix(int K, int* pref, F cnt) {
+  __shared__ int wt2[kMaxPE / 32];
+  const int t = threadIdx.x;
+  const int v = t < K ? cnt(t) : 0;
+  const int lane = t & 31, wid = t >> 5;
+  int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (t < kMaxPE && lane == 31) wt2[wid] = incl;
+  __syncthreads();
+  if (t < K) {
+    int off = 0;
+    for (int k = 0; k < wid; ++k) off += wt2[k];
+    pref[t] = off + incl - v;
+    if (t == K - 1) pref[K] = off + incl;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ int item_pe(const int* pref, int K, int item) {
   int lo = 0, hi = K - 1;   // last j with pref[j] <= item
   while (lo < hi) {
@@ -403,8 +438,8 @@ __device__ __forceinline__ int offspring_end(unsigned long long Qi, unsigned lon
   return (int)(cc < L ? cc : L);
 }
 
-// Resample count and CDF scale of a PE from its mass, largest weight and size.
-__device__ __forceinline__ void resample_plan(const Model& m, int j, int n, double N, double wmax, int& L, int& s) {
+// Resample count and CDF scale of a slice from its mass, largest weight and size.
+__device__ __forceinline__ void resample_plan(double rho, int lmax, int n, double N, double wmax, int& L, int& s) {
   L = 0;
   s = 0;
   if (n > 0 && wmax > 0.0) {
@@ -413,12 +448,17 @@ __device__ __forceinline__ void resample_plan(const Model& m, int j, int n, doub
     int c = 0;
     while ((1LL << c) < (long long)n) ++c;
     s = 52 - c - e;
-    long long Ll = llround(m.rho_pe * (N > 1.0 ? N : 1.0));
-    const long long lmax = m.pe_cap - births_of(m.J, m.K, j);
+    long long Ll = llround(rho * (N > 1.0 ? N : 1.0));
     if (Ll > lmax) Ll = lmax;
     if (Ll < 0) Ll = 0;
     L = (int)Ll;
   }
+}
+
+// Measurements of slice j.
+__device__ __forceinline__ int slice_M(const Dev& d, int j) { return d.zshared ? *d.M : d.Mj[j]; }
+template <class R> __device__ __forceinline__ const V2<R>* slice_Z(const Dev& d, int j) {
+  return static_cast<const V2<R>*>(d.Z) + (d.zshared ? 0 : d.zoff[j]);
 }
 
 __device__ __forceinline__ uint32_t philox_u32(const Model& m, uint32_t a, unsigned long long step, uint32_t tag) {
@@ -431,6 +471,11 @@ __device__ __forceinline__ uint32_t philox_u32(const Model& m, uint32_t a, unsig
 // ---------------------------------------------------------------------------
 template <class R> cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s);
 template <class R> cudaError_t launch_stage_z(const Dev& d, const Model& m, const R* Z, int M, cudaStream_t s);
+template <class R>
+cudaError_t launch_stage_zb(const Dev& d, const Model& m, const R* Z, const int* off, cudaStream_t s);
+template <class R>
+cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* out_labels, int* counts, int cap,
+                             cudaStream_t s);
 template <class R> cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels,
                                               int cap, int* d_count, cudaStream_t s);

@@ -91,6 +91,12 @@ ABI = {
     "phd_get_predicted": (ctypes.c_int, [_H, _P, _P, _P, _I32P]),
     "phd_colsum_static": (ctypes.c_int, [ctypes.POINTER(phd_config), _P, _P, ctypes.c_int32, _P,
                                          ctypes.c_int32, _P, _P]),
+    "phd_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(phd_config), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "phd_batch_init": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(phd_config), ctypes.c_int32, _P,
+                                      ctypes.c_size_t, _P]),
+    "phd_batch_step": (ctypes.c_int, [_H, _P, _P, _P, _P, _P, ctypes.c_int32]),
+    "phd_batch_step_inject": (ctypes.c_int, [_H, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
 }
 
 _lib = None
@@ -401,6 +407,61 @@ class ParticlePHD:
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
 
 
-__all__ = ["lib", "LIB_PATH", "ABI", "phd_config", "phd_stats", "make_config", "colsum_static", "ParticlePHD", "PhdError",
+class ParticlePHDBatch(ParticlePHD):
+    """A batch of independent one-PE filters (phd_batch_*): run j follows workloads[j]."""
+
+    def __init__(self, workloads, seed: int = 0, device: str = "cuda",
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.L = lib()
+        self.ws_list = list(workloads)
+        R = len(self.ws_list)
+        arr = (phd_config * R)(*[make_config(w, seed) for w in self.ws_list])
+        self._cfgs = arr
+        self.cfg = arr[0]
+        self.K = R
+        self.pe_cap = max(int(w.pe_cap) for w in self.ws_list)
+        self.m_max = max(int(w.m_max) for w in self.ws_list)
+        self.dtype = torch.float64 if self.cfg.precision == PHD_FP64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = ctypes.c_size_t(0)
+        self._check(self.L.phd_batch_workspace_size(arr, R, ctypes.byref(nbytes)), "phd_batch_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.L.phd_batch_init(ctypes.byref(h), arr, R, _ptr(self.workspace), nbytes.value,
+                                       ctypes.c_void_p(self.stream.cuda_stream))
+        self._check(st, "phd_batch_init")
+        self.h = h
+        self._cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def pack_batch(self, Zs):
+        """Per-run scans -> (device rows, device int32 offsets [runs+1])."""
+        return self.pack(Zs)
+
+    def batch_step(self, Zs=None, packed=None, cap: Optional[int] = None, noise=None, u=None, sync: bool = True):
+        cap = self.m_max if cap is None else int(cap)
+        Zp, offt = packed if packed is not None else self.pack(Zs)
+        states = torch.empty((self.K, cap, 4), dtype=self.dtype, device=self.device)
+        labels = torch.empty((self.K, cap), dtype=torch.int32, device=self.device)
+        counts = torch.empty(self.K, dtype=torch.int32, device=self.device)
+        if noise is None and u is None:
+            st = self.L.phd_batch_step(self.h, _ptr(Zp), _ptr(offt), _ptr(states), _ptr(labels), _ptr(counts), cap)
+        else:
+            nz = None if noise is None else self._real(noise, (self.K * self.pe_cap, 4))
+            ut = self._u32(u)
+            st = self.L.phd_batch_step_inject(self.h, _ptr(Zp), _ptr(offt), _ptr(nz), _ptr(ut), _ptr(states),
+                                              _ptr(labels), _ptr(counts), cap)
+            self._keepb = (nz, ut)
+        self._check(st, "phd_batch_step")
+        self._keeprun = (Zp, offt)
+        if not sync:
+            return states, labels, counts
+        self.sync()
+        c = counts.cpu().numpy()
+        return [(states[j, :min(c[j], cap)], labels[j, :min(c[j], cap)]) for j in range(self.K)]
+
+
+__all__ = ["lib", "LIB_PATH", "ABI", "ParticlePHDBatch", "phd_config", "phd_stats", "make_config", "colsum_static", "ParticlePHD", "PhdError",
            "PHD_OK", "PHD_ERR_INVALID_ARG", "PHD_ERR_CAPACITY", "PHD_ERR_CUDA", "PHD_ERR_TIMEOUT",
            "PHD_ERR_STATE", "PHD_FP32", "PHD_FP64"]

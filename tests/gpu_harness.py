@@ -104,7 +104,7 @@ def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
     for j in range(K):
         Jj = scenario.births_per_pe(w)[j]
         xo, wo = oracle.predict(m, xs0[j], ws0[j], Jj, nz[j])
-        assert len(xp[j]) == len(xo)
+        assert len(xp[j]) == len(xo), ("predicted count", j, len(xs0[j]), Jj, len(xp[j]), len(xo))
         # FP32 rounding of x + T vx + T^2/2 a: a few ulp of |x| <= 2e3 m
         atol = 1e-3 if dt == np.float32 else 1e-9
         np.testing.assert_allclose(xp[j], xo, rtol=0, atol=atol)

@@ -1,0 +1,86 @@
+"""GPU parity of the batch of independent filters (phd_batch_*).
+
+Five runs with different clutter rates, birth counts, particles per target
+and measurement capacities, uneven particle sets, stepped together; every
+run is checked stage by stage against the FP64 oracle of its own
+configuration (the same harness as the one-filter tests), on injected random
+numbers."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenario
+from gpu_harness import StageReport, check_step, npdtype
+
+pytestmark = pytest.mark.gpu
+
+
+def _runs():
+    base = scenario.workload("linear4_fp64", precision="fp32", birth_steps=(1, 1, 1, 1))
+    specs = [dict(clutter_rate=5.0, birth_count=300, particles_per_target=200, n_targets=2),
+             dict(clutter_rate=60.0, birth_count=800, particles_per_target=500, n_targets=4),
+             dict(clutter_rate=20.0, birth_count=100, particles_per_target=300, n_targets=3),
+             dict(clutter_rate=150.0, birth_count=1200, particles_per_target=256, n_targets=1),
+             dict(clutter_rate=0.5, birth_count=64, particles_per_target=1000, n_targets=4)]
+    ws = [scenario.workload("linear4_fp64", precision="fp32", birth_steps=(1,) * s["n_targets"], **s)
+          for s in specs]
+    cap = max(w.pe_cap for w in ws)
+    return [w.with_(pe_cap=cap) for w in ws]
+
+
+def test_batch_runs_match_their_oracles():
+    from paper_1503_03769_gb300 import ParticlePHDBatch
+    ws = _runs()
+    R = len(ws)
+    b = ParticlePHDBatch(ws, seed=2)
+    rng = np.random.default_rng(2)
+    scs = [scenario.simulate(w, 40 + j, steps=3) for j, w in enumerate(ws)]
+    xs, wts = [], []
+    for j, w in enumerate(ws):
+        cen = np.concatenate([t[:, [0, 2]] for t in scs[j].truth if len(t)])
+        x, wt = scenario.random_particles(rng, w, 700 + 333 * j, centres=cen, spread=25.0, mass=2.0 + j)
+        xs.append(x.astype(np.float32))
+        wts.append(wt.astype(np.float32))
+    b.set_state(xs, wts)
+    rep = StageReport()
+    for k in range(3):
+        Zs = [scs[j].meas[k] for j in range(R)]
+        noise = scenario.step_noise(9, k, R, b.pe_cap, np.float32)
+        u = scenario.resample_u32(9, k, R)
+        pre_x, pre_w = b.get_state()
+        outs = b.batch_step(Zs, noise=noise, u=u)
+        xp, wp, wu = b.get_predicted()
+        C, mass = b.get_update()
+        loc_s, loc_l = b.get_local_estimates()
+        par, _ = b.get_resample()
+        xr, wr = b.get_state()
+        nz = np.asarray(noise).reshape(R, b.pe_cap, 4)
+        for j, w in enumerate(ws):
+            g = dict(xs0=[pre_x[j]], ws0=[pre_w[j]], xp=[xp[j]], wp=[wp[j]], wu=[wu[j]],
+                     C=C[j:j + 1], mass=mass[j:j + 1], loc_s=[loc_s[j]], loc_l=[loc_l[j]],
+                     states=outs[j][0], labels=outs[j][1], par=par[j:j + 1], lx=0,
+                     xr=[xr[j]], wr=[wr[j]])
+            check_step(w, oracle.model(w), Zs[j], nz[j], u[j:j + 1], None, g, rep)
+    assert rep.compared_labels > 0
+    b.close()
+
+
+def test_batch_free_running_and_capacity_errors():
+    from paper_1503_03769_gb300 import ParticlePHDBatch, PhdError
+    from paper_1503_03769_gb300 import phd as P
+    ws = _runs()
+    b = ParticlePHDBatch(ws, seed=4)
+    scs = [scenario.simulate(w, 70 + j, steps=6) for j, w in enumerate(ws)]
+    for k in range(6):
+        outs = b.batch_step([scs[j].meas[k] for j in range(len(ws))])
+        assert len(outs) == len(ws)
+    st = b.stats()
+    assert st["updates"] == 6 and st["pairs"] > 0
+    # a run with more measurements than its capacity is reported
+    Zs = [scs[j].meas[0] for j in range(len(ws))]
+    Zs[2] = np.zeros((b.m_max + 5, 2), np.float32)
+    with pytest.raises(PhdError) as e:
+        b.batch_step(Zs)
+    assert e.value.status == P.PHD_ERR_CAPACITY
+    b.close()
