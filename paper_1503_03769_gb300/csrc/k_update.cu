@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   __shared__ int tpref[kMaxPE + 1];   // tiles per slice (pass-1 partial rows)
   __shared__ int ipref[kMaxPE + 1];   // work items per slice (tiles x measurement chunks)
   __shared__ P4<R> sp[kTile];
-  __shared__ double red[kThreads];
+  __shared__ R red[kThreads];
   const int K = m.K;
   item_prefix(d.n_pred, K, tpref);
   slice_prefix(K, ipref, [&](int j) {
@@ -93,12 +93,14 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       }
       acc = (a0 + a1) + (a2 + a3);
     }
-    red[threadIdx.x] = (double)acc;
+    // the tile's partial for measurement p: splits combined in the kernel's
+    // precision (a tile is at most 256 particles), one conversion to FP64
+    red[threadIdx.x] = acc;
     __syncthreads();
     if (split == 0) {
-      double s = red[threadIdx.x];
+      R s = red[threadIdx.x];
       for (int k = 1; k < nsplit; ++k) s += red[threadIdx.x + k * Mc];
-      d.colpart[(long)titem * m.m_max + p] = s;
+      d.colpart[(long)titem * m.m_max + p] = (double)s;
     }
     __syncthreads();
   }
@@ -244,15 +246,17 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       wv = (miss + acc) * w[gi];
       wu[gi] = wv;
     }
-    // tile sum (FP64 over the warp's 8 particles, then the 8 warps) and max
-    double sv = (double)wv, mv = (double)wv;
+    // tile sum and max: the warp's 8 particles in the kernel's precision, the
+    // 8 warp totals in FP64 by one thread (FP64 is ~1/60 of the FP32 rate)
+    R sv = wv, mv = wv;
     for (int o = 16; o > 0; o >>= 1) {
       sv += __shfl_down_sync(0xffffffffu, sv, o);
-      mv = fmax(mv, __shfl_down_sync(0xffffffffu, mv, o));
+      const R u = __shfl_down_sync(0xffffffffu, mv, o);
+      mv = u > mv ? u : mv;
     }
     if ((threadIdx.x & 31) == 0) {
-      rs[threadIdx.x >> 5] = sv;
-      rm[threadIdx.x >> 5] = mv;
+      rs[threadIdx.x >> 5] = (double)sv;
+      rm[threadIdx.x >> 5] = (double)mv;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -118,6 +118,30 @@ def workload(name: str, **overrides) -> Workload:
     return _derive_caps(base[name].with_(**overrides))
 
 
+def batch_workloads(seed: int = 1000, runs: int = 256, steps: int = 60) -> List[Workload]:
+    """The batched Monte-Carlo workload: `runs` independent linear-sensor
+    filters whose sizes are drawn per run from a seeded generator: targets
+    U{1..50}, clutter rate U[5, 200], particles per target U{256..4096}, births
+    per step equal to particles per target (a reading; the count is not
+    given), `steps` scans.  All runs share one pe_cap (the largest need)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xBA7C, seed]))
+    out = []
+    for r in range(runs):
+        nt = int(rng.integers(1, 51))
+        lam = float(rng.uniform(5.0, 200.0))
+        rho = int(rng.integers(256, 4097))
+        out.append(Workload(name=f"batch_run{r}", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+                            clutter_rate=lam, n_targets=nt, particles_per_target=rho,
+                            birth_count=rho, steps=steps, precision="fp32"))
+    caps = []
+    for w in out:
+        m_exp = w.clutter_rate + w.n_targets
+        m_max = int(-(-int(m_exp + 8 * math.sqrt(m_exp) + 32) // 64) * 64)
+        caps.append((w.particles_per_target * (2 * w.n_targets + 8) + w.birth_count, m_max))
+    pe_cap = int(-(-max(c for c, _ in caps) // 256) * 256)
+    return [w.with_(pe_cap=pe_cap, m_max=mm) for w, (_, mm) in zip(out, caps)]
+
+
 # ----------------------------------------------------------------------------
 # Truth and sensor simulation
 # ----------------------------------------------------------------------------
@@ -266,6 +290,6 @@ def random_particles(rng: np.random.Generator, w: Workload, n: int,
 
 
 __all__ = [
-    "Workload", "workload", "Scenario", "simulate", "births_per_pe", "step_noise",
+    "Workload", "workload", "batch_workloads", "Scenario", "simulate", "births_per_pe", "step_noise",
     "resample_u32", "exchange_u32", "random_particles", "LINEAR", "RANGE_BEARING", "DEG",
 ]
