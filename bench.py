@@ -437,18 +437,27 @@ def run_gpu_batch(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ws = scenario.batch_workloads(seed=1000 + 7919 * rank)
+    ws = scenario.batch_workloads(seed=1000 + 7919 * rank, runs=args.runs)
     R = len(ws)
     steps_per_run = ws[0].steps
     total = args.warmup + args.steps
     scen = [scenario.simulate(w, 1000 + r + 7919 * rank, steps=steps_per_run) for r, w in enumerate(ws)]
     b = ParticlePHDBatch(ws, seed=1000 + rank, device=f"cuda:{local_rank}")
-    packed = [b.pack([scen[r].meas[k % steps_per_run] for r in range(R)]) for k in range(min(total, steps_per_run))]
+    packed = [b.pack([scen[r].meas[k] for r in range(R)]) for k in range(steps_per_run)]
     empty_x = [np.zeros((0, 4))] * R
     empty_w = [np.zeros(0)] * R
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     cap = 64
     states = torch.empty((R, cap, 4), dtype=torch.float32, device=dev)
+    # set-up: the pair passes' launch shape is autotuned on the batch's own
+    # slices half-way through a run (representative particle and measurement
+    # counts), then the runs restart from empty
+    t_tune = time.perf_counter()
+    for k in range(steps_per_run // 2):
+        b.batch_step(packed=packed[k % len(packed)], cap=cap, sync=False)
+    tuning = b.autotune(3) if not args.no_autotune else b.get_tuning()
+    t_tune = time.perf_counter() - t_tune
+    b.set_state(empty_x, empty_w)
     b.set_stage_timer(True)
     for k in range(args.warmup):
         if k % steps_per_run == 0:
@@ -500,7 +509,7 @@ def run_gpu_batch(args, rank, world, local_rank):
         "metric": METRIC, "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch256", "runs": R, "scans_per_run": steps_per_run,
+        "config": {"workload": "batch256" if R == 256 else f"batch{R}", "runs": R, "scans_per_run": steps_per_run,
                    "targets": "U{1..50}", "clutter_rate": "U[5,200]", "particles_per_target": "U{256..4096}",
                    "births_per_step": "= particles per target", "pe_cap": ws[0].pe_cap,
                    "l2": "flushed between timed batched steps (512 MiB write, outside the events)",
@@ -513,6 +522,9 @@ def run_gpu_batch(args, rank, world, local_rank):
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                      "pairs_per_update": st["pairs"] / max(st["updates"], 1)},
         "gpu_launches": int(st["launches"]), "clocks": clocks,
+        "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2")},
+                   "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
+                   "autotuned": not args.no_autotune, "setup_s": round(t_tune, 3)},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -526,6 +538,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dist16_10t")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--runs", type=int, default=256, help="filters in the batched workload (batch256)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of the pair passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -289,11 +289,52 @@ phd_status phd_reset_stats(phd_handle *h);
  * one.  Does not synchronise. */
 phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
 
+/* ---- launch shapes of the update's pair passes, and their autotuner -------- */
+
+/* How the update's two pair passes (Eq. 7 column sums, Eq. 8 row sums) map
+ * onto the GPU.  Every supported shape computes the same quantities; results
+ * differ between shapes only by FP32 summation order (the FP64 accumulation
+ * of C and of the masses stays in a fixed order for a given shape).
+ *  c_tile: pass 1 particles per work item: 256, 512 or 1024;
+ *  c_mb:   pass 1 measurements per thread: 1, 2 or 4 (64 * c_mb per item);
+ *  r_pb:   pass 2 particles per thread: 1, 2 or 4;
+ *  r_g:    pass 2 lanes sharing a particle: 1, 2, 4 or 8; (r_pb, r_g) is one
+ *          of (1,1) (2,1) (4,1) (1,2) (2,2) (1,4) (1,8);
+ *  grid1, grid2: CTA caps of pass 1 and pass 2 (1 .. 9728);
+ *  pass1_us, pass2_us: filled by phd_autotune with the measured mean duration
+ *          of each pass in the chosen shape (0 elsewhere; ignored on input).
+ * FP64 handles support c_mb 2 and (r_pb, r_g) = (1, 4) only.  The default is
+ * c_tile 512, c_mb 4 (2 in FP64), (1, 4), grid1 = grid2 = 1216.  The fused
+ * step kernel (phd_set_path) does not use these shapes. */
+typedef struct phd_tuning {
+    int32_t c_tile, c_mb, r_pb, r_g, grid1, grid2;
+    float pass1_us, pass2_us;
+} phd_tuning;
+
+phd_status phd_get_tuning(phd_handle *h, phd_tuning *out);
+
+/* Select a shape.  Synchronises the stream (captured step graphs are rebuilt
+ * on the next step).  PHD_ERR_INVALID_ARG for an unsupported shape. */
+phd_status phd_set_tuning(phd_handle *h, const phd_tuning *t);
+
+/* Autotuner: times every supported shape of pass 1 (c_tile x c_mb x grid1 in
+ * {608, 1216, 2432}) and then of pass 2 ((r_pb, r_g) x grid2), each as the
+ * mean of `reps` launches (1 .. 1000) after one untimed launch, on the
+ * handle's current predicted set and measurements, i.e. the input of the last
+ * update (call it after a representative step: the best shape depends on the
+ * slices' particle and measurement counts).  Keeps the fastest shape of each
+ * pass, re-runs the update with it (so the update's outputs are the chosen
+ * shape's), leaves phd_stats unchanged and returns the choice in *out (may be
+ * NULL).  Works on one-filter and batch handles.  Synchronous.  Errors:
+ * PHD_ERR_STATE when no update has run; PHD_ERR_CUDA (the previous shape is
+ * kept). */
+phd_status phd_autotune(phd_handle *h, int32_t reps, phd_tuning *out);
+
 /* ---- normaliser column sums without device allocation ---------------------- */
 
 /* C_p = sum_i p_D g(z_p | x_i) w_i for one particle set (the Eq. 7 column sums
- * of phd_update, same kernel arithmetic and summation order as a one-PE
- * filter), for callers that may not allocate device memory at all: trackers
+ * of phd_update with the same pair arithmetic: FP32 pair terms, FP64 per-tile
+ * partials summed in a fixed order, tiles of 256 particles), for callers that may not allocate device memory at all: trackers
  * whose device memory is fixed when they start (cudaMalloc and cudaFree can
  * synchronise the device and take unbounded time, which a real-time loop
  * cannot afford) and plug-ins running inside a host application that owns

@@ -4,40 +4,61 @@
 //   g(z|x) = cnorm * 2^-q,  q = b0 (z0 - h0(x))^2 + b1 (z1 - h1(x))^2,
 //   b = log2(e) / (2 sigma^2),
 // so one MUFU ex2 per pair evaluates it; the bearing difference is wrapped
-// to [0, pi].  The N x M likelihood matrix is never stored.
+// to [0, pi].  The N x M likelihood matrix is never stored.  The sensor model
+// is a template parameter of the pair loops (no per-pair branch).
 //
 // Pass 1 (k_colsum): C^j_p = p_D cnorm sum_i 2^-q_ip w_i.  A work item is a
-//   tile of kTile particles of one PE (staged in shared memory as packed
-//   (h0, h1, h1lo, w)) times a chunk of kMChunk measurements; threads own
-//   measurements (and, when the chunk is short, a split of the tile) and
-//   accumulate in FP32 over at most one tile; the per-tile partials go to
-//   memory in FP64 and are summed in a fixed order by k_finalize, so the
-//   normaliser is accumulated in FP64 and is deterministic.
-// Finalize: C^j, the normaliser each PE applies (its own, or the PE mean),
+//   tile of c_tile particles of one slice (staged in shared memory as packed
+//   (h0, h1, h1lo, w)) times a chunk of 64 c_mb measurements.  A thread holds
+//   c_mb measurements in registers (one broadcast shared load then feeds c_mb
+//   pairs) and runs over a strided split of the tile; the splits of a
+//   measurement are combined by a fixed-shape tree in shared memory, and the
+//   per-tile partial goes to memory in FP64.  k_finalize sums the partials of
+//   a slice in a fixed order, so C is accumulated in FP64 and deterministic.
+// Finalize: C^j, the normaliser each slice applies (its own, or the PE mean),
 //   and ginv_p = cnorm p_D / (kappa + C_p) (0 when kappa + C_p = 0).
-// Pass 2 (k_rowsum): w_i <- [(1 - p_D) + sum_p 2^-q_ip ginv_p] w_i with four
-//   lanes per particle and Z_k, ginv staged in shared memory; per-tile FP64
-//   sums and maxima of the updated weights feed N^j and the resampling plan
-//   (k_mass).  The updated weights go to their own buffer: the extraction
-//   (Eq. 13, 18) still needs the predicted ones.
+// Pass 2 (k_rowsum): w_i <- [(1 - p_D) + sum_p 2^-q_ip ginv_p] w_i.  A thread
+//   holds r_pb particles in registers and r_g lanes share them, splitting the
+//   measurements (combined by shuffles); Z_k and ginv are staged in shared
+//   memory.  Per-tile FP64 sums and maxima of the updated weights feed N^j and
+//   the resampling plan (k_mass).  The updated weights go to their own
+//   buffer: the extraction (Eq. 13, 18) still needs the predicted ones.
 //
-// Algorithmic work per pair and pass: one ex2 and ~5 FP32 operations; bytes
-// per particle and pass: 16 B state + 4 B weight (+ 4 B weight written in
-// pass 2); per measurement: 8 B (+ 8 B of FP64 partial per work item).
+// Algorithmic work per pair and pass: one ex2 and 7 FP32 operations (linear
+// sensor; 10 with the bearing wrap); bytes per particle and pass: 16 B state
+// + 4 B weight (+ 4 B weight written in pass 2); per measurement: 8 B (+ 8 B
+// of FP64 partial per pass-1 tile).
 #include "phd_internal.cuh"
 
 namespace phd {
 
-template <class R>
+// Exponent q of the likelihood with the sensor model fixed at compile time
+// (same arithmetic as qform).
+template <class R, int RB>
+__device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
+  const R d0 = z0 - h0;
+  R d1 = z1 - h1;
+  if (RB) {
+    d1 = d1 - h1lo;
+    const R a = fabs(d1);
+    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
+  }
+  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
+}
+
+template <class R, int RB, int MB>
 __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int tpref[kMaxPE + 1];   // tiles per slice (pass-1 partial rows)
   __shared__ int ipref[kMaxPE + 1];   // work items per slice (tiles x measurement chunks)
-  __shared__ P4<R> sp[kTile];
-  __shared__ R red[kThreads];
+  constexpr int MC = 64 * MB;         // measurements per work item
+  const int TP = m.tune.c_tile;
+  P4<R>* sp = reinterpret_cast<P4<R>*>(smem_raw);   // [TP]
+  R* red = reinterpret_cast<R*>(sp + TP);           // [kThreads * MB]
   const int K = m.K;
-  item_prefix(d.n_pred, K, tpref);
+  item_prefix(d.n_pred, K, tpref, TP);
   slice_prefix(K, ipref, [&](int j) {
-    return ((d.n_pred[j] + kTile - 1) / kTile) * ((slice_M(d, j) + kMChunk - 1) / kMChunk);
+    return ((d.n_pred[j] + TP - 1) / TP) * ((slice_M(d, j) + MC - 1) / MC);
   });
   const int total = ipref[K];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
@@ -49,15 +70,15 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
     const int j = item_pe(ipref, K, item);
     const int M = slice_M(d, j);
     const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
-    const int chunks = (M + kMChunk - 1) / kMChunk;
+    const int chunks = (M + MC - 1) / MC;
     const int local = item - ipref[j];
     const int tile = local / chunks, chunk = local - tile * chunks;
     const int titem = tpref[j] + tile;
-    const long base = (long)j * m.pe_cap + (long)tile * kTile;
-    const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
-    if (titem != staged) {   // consecutive items of a CTA often share the tile
+    const long base = (long)j * m.pe_cap + (long)tile * TP;
+    const int cnt = min(TP, d.n_pred[j] - tile * TP);
+    if (titem != staged) {   // consecutive items of a CTA can share the tile
       __syncthreads();
-      for (int i = threadIdx.x; i < kTile; i += kThreads) {
+      for (int i = threadIdx.x; i < TP; i += kThreads) {
         P4<R> q = {0, 0, 0, 0};
         if (i < cnt) {
           const H3<R> h = meas_h<R>(m, x[base + i], tab);
@@ -68,40 +89,52 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       __syncthreads();
       staged = titem;
     }
-    const int pbeg = chunk * kMChunk;
-    const int Mc = min(kMChunk, M - pbeg);
-    const int nsplit = kThreads / Mc;
-    const int pl = threadIdx.x % Mc;
-    const int split = threadIdx.x / Mc;
-    const int p = pbeg + pl;
-    R acc = 0;
-    if (split < nsplit) {
-      // four independent partial sums (ILP), each over at most 64 pairs
-      const V2<R> z = Z[p];
-      R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int i = split;
-      for (; i + 3 * nsplit < cnt; i += 4 * nsplit) {
-        const P4<R> q0 = sp[i], q1 = sp[i + nsplit], q2 = sp[i + 2 * nsplit], q3 = sp[i + 3 * nsplit];
-        a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
-        a1 = fma(exp2_neg(qform<R>(L, z.a, z.b, q1.h0, q1.h1, q1.h1lo)), q1.w, a1);
-        a2 = fma(exp2_neg(qform<R>(L, z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
-        a3 = fma(exp2_neg(qform<R>(L, z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
+    const int pbeg = chunk * MC;
+    const int Mc = min(MC, M - pbeg);
+    const int G = (Mc + MB - 1) / MB;   // measurement groups (threads per split)
+    const int S = kThreads / G;         // splits of the tile
+    const int GM = G * MB;
+    const int g = threadIdx.x % G, sidx = threadIdx.x / G;
+    R acc[MB];
+#pragma unroll
+    for (int k = 0; k < MB; ++k) acc[k] = 0;
+    if (sidx < S) {
+      R z0[MB], z1[MB];
+#pragma unroll
+      for (int k = 0; k < MB; ++k) {
+        const int p = g + k * G;
+        const V2<R> z = p < Mc ? Z[pbeg + p] : V2<R>{0, 0};
+        z0[k] = z.a;
+        z1[k] = z.b;
       }
-      for (; i < cnt; i += nsplit) {
-        const P4<R> q0 = sp[i];
-        a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+      int i = sidx;
+      for (; i + S < cnt; i += 2 * S) {
+        const P4<R> qa = sp[i], qb = sp[i + S];
+#pragma unroll
+        for (int k = 0; k < MB; ++k)
+          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+#pragma unroll
+        for (int k = 0; k < MB; ++k)
+          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
       }
-      acc = (a0 + a1) + (a2 + a3);
+      if (i < cnt) {
+        const P4<R> qa = sp[i];
+#pragma unroll
+        for (int k = 0; k < MB; ++k)
+          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < MB; ++k) red[sidx * GM + g + k * G] = acc[k];
     }
-    // the tile's partial for measurement p: splits combined in the kernel's
-    // precision (a tile is at most 256 particles), one conversion to FP64
-    red[threadIdx.x] = acc;
     __syncthreads();
-    if (split == 0) {
-      R s = red[threadIdx.x];
-      for (int k = 1; k < nsplit; ++k) s += red[threadIdx.x + k * Mc];
-      d.colpart[(long)titem * m.m_max + p] = (double)s;
+    // the S splits of each measurement: fixed-shape pairwise tree
+    for (int width = S; width > 1;) {
+      const int half = (width + 1) >> 1;
+      for (int t = threadIdx.x; t < (width - half) * GM; t += kThreads) red[t] += red[t + half * GM];
+      __syncthreads();
+      width = half;
     }
+    for (int p = threadIdx.x; p < Mc; p += kThreads) d.colpart[(long)titem * m.m_max + pbeg + p] = (double)red[p];
     __syncthreads();
   }
 }
@@ -115,7 +148,7 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
   __shared__ int mpref[kMaxPE + 1];
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref);
+  item_prefix(d.n_pred, K, pref, m.tune.c_tile);
   slice_prefix(K, mpref, [&](int j) { return slice_M(d, j); });
   const double cs = m.p_d * m.cnorm;
   R* ginv = static_cast<R*>(d.ginv);
@@ -176,17 +209,20 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
   }
 }
 
-// Pass 2: tiles of kRowTile particles; four consecutive lanes share a particle
-// and split the measurements (p = g, g+4, ...), combined by shuffles.
-template <class R>
+// Pass 2: a thread holds PB particles (k * GR + il of the tile, so loads are
+// coalesced) and G consecutive lanes share them, splitting the measurements
+// (p = g, g + G, ...); two accumulators per particle for ILP.
+template <class R, int RB, int PB, int G>
 __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int GR = kThreads / G;   // particle groups per tile
+  constexpr int TPR = GR * PB;       // particles per work item
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int pref[kMaxPE + 1];
   __shared__ double rs[kThreads / 32];
   __shared__ double rm[kThreads / 32];
   Z4<R>* zs = reinterpret_cast<Z4<R>*>(smem_raw);
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref, kRowTile);
+  item_prefix(d.n_pred, K, pref, TPR);
   const int total = pref[K];
   const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
@@ -195,14 +231,29 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
   const R miss = consts<R>(m).miss;
-  const int il = threadIdx.x >> 2, g = threadIdx.x & 3;
+  const int il = threadIdx.x / G, g = threadIdx.x % G;
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int tile = item - pref[j];
     const int M = slice_M(d, j);
-    const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+    const int n = d.n_pred[j];
+    R h0[PB], h1[PB], hl[PB], wi[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      const int i = tile * TPR + k * GR + il;
+      h0[k] = h1[k] = hl[k] = wi[k] = 0;
+      if (i < n) {
+        const long gi = (long)j * m.pe_cap + i;
+        const H3<R> h = meas_h<R>(m, x[gi], tab);
+        h0[k] = h.h0;
+        h1[k] = h.h1;
+        hl[k] = h.h1lo;
+        wi[k] = w[gi];
+      }
+    }
     if (j != staged) {
+      const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
       __syncthreads();
       for (int p = threadIdx.x; p < M; p += kThreads) {
         const V2<R> z = Z[p];
@@ -211,44 +262,41 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       __syncthreads();
       staged = j;
     }
-    const int i = tile * kRowTile + il;
-    const bool live = i < d.n_pred[j];
-    const long gi = (long)j * m.pe_cap + i;
-    R acc = 0;
-    if (live) {
-      // four independent partial sums (ILP) over measurements g, g+4, ...,
-      // folded into acc every 32 rounds
-      const H3<R> h = meas_h<R>(m, x[gi], tab);
-      R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int p = g, k = 0;
-      for (; p + 12 < M; p += 16) {
-        const Z4<R> z0 = zs[p], z1 = zs[p + 4], z2 = zs[p + 8], z3 = zs[p + 12];
-        a0 = fma(exp2_neg(qform<R>(L, z0.z0, z0.z1, h.h0, h.h1, h.h1lo)), z0.g, a0);
-        a1 = fma(exp2_neg(qform<R>(L, z1.z0, z1.z1, h.h0, h.h1, h.h1lo)), z1.g, a1);
-        a2 = fma(exp2_neg(qform<R>(L, z2.z0, z2.z1, h.h0, h.h1, h.h1lo)), z2.g, a2);
-        a3 = fma(exp2_neg(qform<R>(L, z3.z0, z3.z1, h.h0, h.h1, h.h1lo)), z3.g, a3);
-        if (++k == 32) {
-          acc += (a0 + a1) + (a2 + a3);
-          a0 = a1 = a2 = a3 = 0;
-          k = 0;
-        }
-      }
-      for (; p < M; p += 4) {
-        const Z4<R> z0 = zs[p];
-        a0 = fma(exp2_neg(qform<R>(L, z0.z0, z0.z1, h.h0, h.h1, h.h1lo)), z0.g, a0);
-      }
-      acc += (a0 + a1) + (a2 + a3);
+    R a0[PB], a1[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) a0[k] = a1[k] = 0;
+    int p = g;
+    for (; p + G < M; p += 2 * G) {
+      const Z4<R> za = zs[p], zb = zs[p + G];
+#pragma unroll
+      for (int k = 0; k < PB; ++k)
+        a0[k] = fma(exp2_neg(qform_t<R, RB>(L, za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+#pragma unroll
+      for (int k = 0; k < PB; ++k)
+        a1[k] = fma(exp2_neg(qform_t<R, RB>(L, zb.z0, zb.z1, h0[k], h1[k], hl[k])), zb.g, a1[k]);
     }
-    acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
-    acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
-    R wv = 0;
-    if (live && g == 0) {
-      wv = (miss + acc) * w[gi];
-      wu[gi] = wv;
+    if (p < M) {
+      const Z4<R> za = zs[p];
+#pragma unroll
+      for (int k = 0; k < PB; ++k)
+        a0[k] = fma(exp2_neg(qform_t<R, RB>(L, za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
     }
-    // tile sum and max: the warp's 8 particles in the kernel's precision, the
-    // 8 warp totals in FP64 by one thread (FP64 is ~1/60 of the FP32 rate)
-    R sv = wv, mv = wv;
+    R sv = 0, mv = 0;
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      R acc = a0[k] + a1[k];
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const int i = tile * TPR + k * GR + il;
+      if (g == 0 && i < n) {
+        const R wv = (miss + acc) * wi[k];
+        wu[(long)j * m.pe_cap + i] = wv;
+        sv += wv;
+        mv = wv > mv ? wv : mv;
+      }
+    }
+    // tile sum and max: the warp's values in the kernel's precision, the
+    // warp totals in FP64 by one thread (FP64 is ~1/60 of the FP32 rate)
     for (int o = 16; o > 0; o >>= 1) {
       sv += __shfl_down_sync(0xffffffffu, sv, o);
       const R u = __shfl_down_sync(0xffffffffu, mv, o);
@@ -278,7 +326,7 @@ __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
   __shared__ double red[8], redm[8];
   const int j = blockIdx.x;
-  item_prefix(d.n_pred, m.K, pref, kRowTile);
+  item_prefix(d.n_pred, m.K, pref, row_tile(m.tune));
   double s = 0.0, mx = 0.0;
   for (int it = pref[j] + threadIdx.x; it < pref[j + 1]; it += blockDim.x) {
     s += d.rowpart[it];
@@ -316,26 +364,135 @@ int grid_items(const Model& m) {
 
 static int grid_cap(long items, long cap) { return (int)(items < cap ? (items > 0 ? items : 1) : cap); }
 
-template <class R>
-cudaError_t prepare_kernels(const Model& m) {
-  size_t sm = sizeof(Z4<R>) * (size_t)m.m_max;
-  return cudaFuncSetAttribute(k_rowsum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+Tune default_tune(bool fp64) {
+  Tune t;
+  t.c_tile = 512;
+  t.c_mb = fp64 ? 2 : 4;
+  t.r_pb = 1;
+  t.r_g = 4;
+  t.grid1 = 152 * 8;
+  t.grid2 = 152 * 8;
+  return t;
+}
+
+bool tune_supported(const Tune& t, bool fp64) {
+  if (t.c_tile != 256 && t.c_tile != 512 && t.c_tile != 1024) return false;
+  if (t.grid1 < 1 || t.grid2 < 1 || t.grid1 > 152 * 64 || t.grid2 > 152 * 64) return false;
+  if (fp64) return t.c_mb == 2 && t.r_pb == 1 && t.r_g == 4;
+  if (t.c_mb != 1 && t.c_mb != 2 && t.c_mb != 4) return false;
+  const int pg = t.r_pb * 16 + t.r_g;
+  return pg == 16 + 1 || pg == 32 + 1 || pg == 64 + 1 || pg == 16 + 2 || pg == 32 + 2 || pg == 16 + 4 ||
+         pg == 16 + 8;
+}
+
+template <class R, int RB, int MB>
+static void colsum_go(const Dev& d, const Model& m, cudaStream_t s) {
+  const long tiles = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
+  const long chunks = (m.m_max + 64 * MB - 1) / (64 * MB);
+  const size_t smem = sizeof(P4<R>) * (size_t)m.tune.c_tile + sizeof(R) * kThreads * MB;
+  k_colsum<R, RB, MB><<<grid_cap(tiles * chunks, m.tune.grid1), kThreads, smem, s>>>(d, m);
+}
+
+template <class R, int RB, int PB, int G>
+static void rowsum_go(const Dev& d, const Model& m, cudaStream_t s) {
+  const int tpr = kThreads / G * PB;
+  const long tiles = (long)m.K * ((m.pe_cap + tpr - 1) / tpr);
+  k_rowsum<R, RB, PB, G><<<grid_cap(tiles, m.tune.grid2), kThreads, sizeof(Z4<R>) * (size_t)m.m_max, s>>>(d, m);
+}
+
+template <class R, int RB>
+static cudaError_t prepare_rowsum(size_t sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_rowsum<R, RB, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if constexpr (sizeof(R) == 4) {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 1, 1>, a, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 2, 1>, a, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 4, 1>, a, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 1, 2>, a, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 2, 2>, a, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowsum<R, RB, 1, 8>, a, (int)sm);
+  }
+  return e;
 }
 
 template <class R>
-cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
-  const long tiles = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
-  const long chunks = (m.m_max + kMChunk - 1) / kMChunk;
-  k_colsum<R><<<grid_cap(tiles * chunks, 152L * 8), kThreads, 0, s>>>(d, m);
+cudaError_t prepare_kernels(const Model& m) {
+  const size_t sm = sizeof(Z4<R>) * (size_t)m.m_max;
+  cudaError_t e = prepare_rowsum<R, 0>(sm);
+  if (e == cudaSuccess) e = prepare_rowsum<R, 1>(sm);
+  return e;
+}
+
+template <class R, int RB>
+static cudaError_t colsum_model(const Dev& d, const Model& m, cudaStream_t s) {
+  if constexpr (sizeof(R) == 8) {
+    colsum_go<R, RB, 2>(d, m, s);
+  } else {
+    switch (m.tune.c_mb) {
+      case 1: colsum_go<R, RB, 1>(d, m, s); break;
+      case 2: colsum_go<R, RB, 2>(d, m, s); break;
+      default: colsum_go<R, RB, 4>(d, m, s); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <class R, int RB>
+static cudaError_t rowsum_model(const Dev& d, const Model& m, cudaStream_t s) {
+  if constexpr (sizeof(R) == 8) {
+    rowsum_go<R, RB, 1, 4>(d, m, s);
+  } else {
+    switch (m.tune.r_pb * 16 + m.tune.r_g) {
+      case 16 + 1: rowsum_go<R, RB, 1, 1>(d, m, s); break;
+      case 32 + 1: rowsum_go<R, RB, 2, 1>(d, m, s); break;
+      case 64 + 1: rowsum_go<R, RB, 4, 1>(d, m, s); break;
+      case 16 + 2: rowsum_go<R, RB, 1, 2>(d, m, s); break;
+      case 32 + 2: rowsum_go<R, RB, 2, 2>(d, m, s); break;
+      case 16 + 8: rowsum_go<R, RB, 1, 8>(d, m, s); break;
+      default: rowsum_go<R, RB, 1, 4>(d, m, s); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s) {
+  return m.meas_model ? colsum_model<R, 1>(d, m, s) : colsum_model<R, 0>(d, m, s);
+}
+
+template <class R>
+cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s) {
   k_finalize<R><<<grid_cap(((long)m.K * m.m_max + 7) / 8, 152L * 8), 256, 0, s>>>(d, m);
-  const long rtiles = (long)m.K * ((m.pe_cap + kRowTile - 1) / kRowTile);
-  k_rowsum<R><<<grid_cap(rtiles, 152L * 8), kThreads, sizeof(Z4<R>) * (size_t)m.m_max, s>>>(d, m);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s) {
+  return m.meas_model ? rowsum_model<R, 1>(d, m, s) : rowsum_model<R, 0>(d, m, s);
+}
+
+cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s) {
   k_mass<<<m.K, 256, 0, s>>>(d, m);
   return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
+  cudaError_t e = launch_colsum<R>(d, m, s);
+  if (e == cudaSuccess) e = launch_finalize<R>(d, m, s);
+  if (e == cudaSuccess) e = launch_rowsum<R>(d, m, s);
+  if (e == cudaSuccess) e = launch_mass(d, m, s);
+  return e;
+}
+
 template cudaError_t launch_update<float>(const Dev&, const Model&, cudaStream_t);
 template cudaError_t launch_update<double>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_colsum<float>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_colsum<double>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_finalize<float>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_finalize<double>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_rowsum<float>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_rowsum<double>(const Dev&, const Model&, cudaStream_t);
 template cudaError_t prepare_kernels<float>(const Model&);
 template cudaError_t prepare_kernels<double>(const Model&);
 

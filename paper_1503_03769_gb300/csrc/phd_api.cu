@@ -93,7 +93,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.C = cv.take<double>(K * Mm);
   t.Cused = cv.take<double>(K * Mm);
   t.ginv = cv.take<char>(K * Mm, rs);
-  const size_t ritems = K * ((P + phd::kRowTile - 1) / phd::kRowTile);
+  const size_t ritems = K * ((P + phd::kRowTileMin - 1) / phd::kRowTileMin);
   const size_t chunks = K * ((P + phd::kChunk - 1) / phd::kChunk);
   t.rowpart = cv.take<double>(ritems);
   t.rowmax = cv.take<double>(ritems);
@@ -205,6 +205,7 @@ Model make_model(const phd_config& c) {
   m.bw_hi = c.birth_mass / (double)(jlo + 1);
   m.f_bw_lo = (float)m.bw_lo;
   m.f_bw_hi = (float)m.bw_hi;
+  m.tune = phd::default_tune(c.precision == PHD_FP64);
   return m;
 }
 
@@ -389,6 +390,28 @@ void destroy_graphs(phd_handle* h) {
       *g = nullptr;
     }
 }
+
+// Mean duration in microseconds of `reps` back-to-back launches of one pass
+// (after one untimed launch) on the handle's stream.
+template <class F>
+cudaError_t time_pass(phd_handle* h, int reps, F launch, float* us) {
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  *us = 1000.0f * ms / (float)reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
+}
+
 
 // Sum the timer's recorded event pairs into timer_ms (synchronises).
 cudaError_t drain_timer(phd_handle* h) {
@@ -866,6 +889,106 @@ phd_status phd_reset_stats(phd_handle* h) {
   h->timer_ms = 0.0;
   h->timer_calls = 0;
   return PHD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch shapes of the update's pair passes and their autotuner
+// ---------------------------------------------------------------------------
+
+phd_status phd_get_tuning(phd_handle* h, phd_tuning* out) {
+  if (!h || !out) return PHD_ERR_INVALID_ARG;
+  const phd::Tune& t = h->m.tune;
+  *out = phd_tuning{t.c_tile, t.c_mb, t.r_pb, t.r_g, t.grid1, t.grid2, 0.0f, 0.0f};
+  return PHD_OK;
+}
+
+phd_status phd_set_tuning(phd_handle* h, const phd_tuning* t) {
+  if (!h || !t) return PHD_ERR_INVALID_ARG;
+  const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2};
+  if (!phd::tune_supported(u, is_fp64(h))) return fail(h, PHD_ERR_INVALID_ARG, "phd_set_tuning: unsupported shape");
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->m.tune = u;
+  destroy_graphs(h);
+  return PHD_OK;
+}
+
+phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
+  if (!h || reps < 1 || reps > 1000) return PHD_ERR_INVALID_ARG;
+  if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_autotune: no update has run (nothing to time on)");
+  const bool fp64 = is_fp64(h);
+  unsigned long long saved[4];
+  PHD_CUDA(h, cudaMemcpyAsync(saved, h->d.stats, sizeof(saved), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  const phd::Tune base = h->m.tune;
+  const int grids[3] = {152 * 4, 152 * 8, 152 * 16};
+  const int tiles[3] = {256, 512, 1024};
+  const int mbs[3] = {1, 2, 4};
+  const int pgs[7][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {1, 4}, {1, 8}};
+  phd::Model m = h->m;
+  phd::Tune best = base;
+  float best1 = 0.0f, best2 = 0.0f;
+  bool have1 = false, have2 = false;
+  cudaError_t e = cudaSuccess;
+  // pass 1 over its shapes
+  for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti)
+    for (int mi = 0; mi < 3 && e == cudaSuccess; ++mi)
+      for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+        m.tune = base;
+        m.tune.c_tile = tiles[ti];
+        m.tune.c_mb = mbs[mi];
+        m.tune.grid1 = grids[gi];
+        if (!phd::tune_supported(m.tune, fp64)) continue;
+        float us = 0.0f;
+        e = time_pass(h, reps, [&] {
+          return fp64 ? phd::launch_colsum<double>(h->d, m, h->stream) : phd::launch_colsum<float>(h->d, m, h->stream);
+        }, &us);
+        if (e == cudaSuccess && (!have1 || us < best1)) {
+          best1 = us;
+          have1 = true;
+          best.c_tile = m.tune.c_tile;
+          best.c_mb = m.tune.c_mb;
+          best.grid1 = m.tune.grid1;
+        }
+      }
+  // ginv from the chosen pass 1, then pass 2 over its shapes
+  m.tune = best;
+  if (e == cudaSuccess)
+    e = fp64 ? phd::launch_colsum<double>(h->d, m, h->stream) : phd::launch_colsum<float>(h->d, m, h->stream);
+  if (e == cudaSuccess)
+    e = fp64 ? phd::launch_finalize<double>(h->d, m, h->stream) : phd::launch_finalize<float>(h->d, m, h->stream);
+  for (int pi = 0; pi < 7 && e == cudaSuccess; ++pi)
+    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+      m.tune = best;
+      m.tune.r_pb = pgs[pi][0];
+      m.tune.r_g = pgs[pi][1];
+      m.tune.grid2 = grids[gi];
+      if (!phd::tune_supported(m.tune, fp64)) continue;
+      float us = 0.0f;
+      e = time_pass(h, reps, [&] {
+        return fp64 ? phd::launch_rowsum<double>(h->d, m, h->stream) : phd::launch_rowsum<float>(h->d, m, h->stream);
+      }, &us);
+      if (e == cudaSuccess && (!have2 || us < best2)) {
+        best2 = us;
+        have2 = true;
+        best.r_pb = m.tune.r_pb;
+        best.r_g = m.tune.r_g;
+        best.grid2 = m.tune.grid2;
+      }
+    }
+  // leave the update's outputs as the chosen shapes compute them, and the
+  // statistics as they were
+  h->m.tune = best;
+  if (e == cudaSuccess)
+    e = fp64 ? phd::launch_update<double>(h->d, h->m, h->stream) : phd::launch_update<float>(h->d, h->m, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.stats, saved, sizeof(saved), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  if (e != cudaSuccess) {
+    h->m.tune = base;
+    return cuda_fail(h, e, "phd_autotune");
+  }
+  if (out) *out = phd_tuning{best.c_tile, best.c_mb, best.r_pb, best.r_g, best.grid1, best.grid2, best1, best2};
+  return read_device_error(h);
 }
 
 }  // extern "C"

@@ -17,11 +17,22 @@ namespace phd {
 
 constexpr int kMaxPE = 256;
 constexpr int kMaxM = 4096;
-constexpr int kTile = 256;        // particles per work item of pass 1 and pass 3
-constexpr int kRowTile = 64;      // particles per work item of pass 2 (4 lanes each)
+constexpr int kTile = 256;        // particles per work item of pass 3; smallest pass-1 tile
+constexpr int kRowTileMin = 32;   // smallest pass-2 tile (8 lanes per particle)
 constexpr int kChunk = 1024;      // particles per chunk of the resampling scan
-constexpr int kMChunk = 256;      // measurements per work item of pass 1
 constexpr int kThreads = 256;     // threads of the pair kernels
+
+// Launch shape of the two pair passes (picked by phd_autotune or
+// phd_set_tuning; results differ between shapes only by FP32 summation order).
+struct Tune {
+  int c_tile;    // pass 1: particles per work item (256, 512, 1024)
+  int c_mb;      // pass 1: measurements per thread (1, 2, 4); 64 * c_mb per item
+  int r_pb;      // pass 2: particles per thread (1, 2, 4)
+  int r_g;       // pass 2: lanes sharing a particle (1, 2, 4, 8)
+  int grid1;     // pass 1: CTA cap
+  int grid2;     // pass 2: CTA cap
+};
+__host__ __device__ __forceinline__ int row_tile(const Tune& t) { return kThreads / t.r_g * t.r_pb; }
 
 // Real-typed particle state [x, vx, y, vy].
 template <class R> struct alignas(4 * sizeof(R)) St4 { R x, vx, y, vy; };
@@ -50,6 +61,7 @@ struct Model {
   float f_dt, f_sigma_a, f_ps, f_rx0, f_rw, f_ry0, f_rh, f_bv, f_sx, f_sy, f_miss;
   float f_bw_lo, f_bw_hi;  // birth weight nu_b / J_j for J_j = J / K and J / K + 1
   double bw_lo, bw_hi;
+  Tune tune;
 };
 
 // Per-particle model constants in the kernel's precision.
@@ -83,7 +95,7 @@ struct Dev {
   double* C;             // [K][m_max] C^j (with p_D cnorm)
   double* Cused;         // [K][m_max] normaliser each PE applies
   void* ginv;            // R [K][m_max]  cnorm p_D / (kappa + Cused)
-  double* rowpart;       // [K*ceil(pe_cap/kRowTile)] pass-2 sums of updated weights
+  double* rowpart;       // [K*ceil(pe_cap/kRowTileMin)] pass-2 sums of updated weights
   double* rowmax;        // same: largest updated weight per tile
   unsigned long long* dwkey; // [K][m_max] order keys of dW^{j,p}
   double* mass;          // [K] updated mass N^j
@@ -477,6 +489,13 @@ template <class R>
 cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* out_labels, int* counts, int cap,
                              cudaStream_t s);
 template <class R> cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s);
+// the update's passes one at a time (the autotuner times pass 1 and pass 2 alone)
+template <class R> cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s);
+template <class R> cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s);
+template <class R> cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s);
+cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s);
+Tune default_tune(bool fp64);
+bool tune_supported(const Tune& t, bool fp64);
 template <class R> cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels,
                                               int cap, int* d_count, cudaStream_t s);
 template <class R> cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u,

@@ -56,6 +56,12 @@ class phd_stats(ctypes.Structure):
                 ("update_ms", ctypes.c_double)]
 
 
+class phd_tuning(ctypes.Structure):
+    _fields_ = [("c_tile", ctypes.c_int32), ("c_mb", ctypes.c_int32), ("r_pb", ctypes.c_int32),
+                ("r_g", ctypes.c_int32), ("grid1", ctypes.c_int32), ("grid2", ctypes.c_int32),
+                ("pass1_us", ctypes.c_float), ("pass2_us", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _H = ctypes.c_void_p
 _I32P = ctypes.POINTER(ctypes.c_int32)
@@ -84,6 +90,9 @@ ABI = {
     "phd_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(phd_stats)]),
     "phd_reset_stats": (ctypes.c_int, [_H]),
     "phd_set_stage_timer": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "phd_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(phd_tuning)]),
+    "phd_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(phd_tuning)]),
+    "phd_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(phd_tuning)]),
     "phd_step_inject": (ctypes.c_int, [_H, _P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32, _P, _I32P]),
     "phd_run": (ctypes.c_int, [_H, _P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
     "phd_set_path": (ctypes.c_int, [_H, ctypes.c_int32]),
@@ -405,6 +414,26 @@ class ParticlePHD:
 
     def set_stage_timer(self, on: bool):
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
+
+    def get_tuning(self) -> dict:
+        t = phd_tuning()
+        self._check(self.L.phd_get_tuning(self.h, ctypes.byref(t)), "phd_get_tuning")
+        return {k: getattr(t, k) for k, _ in phd_tuning._fields_}
+
+    def set_tuning(self, **shape):
+        """Select the pair passes' launch shape (keys of phd_tuning; missing
+        keys keep their current value)."""
+        cur = self.get_tuning()
+        cur.update(shape)
+        t = phd_tuning(**{k: cur[k] for k, _ in phd_tuning._fields_})
+        self._check(self.L.phd_set_tuning(self.h, ctypes.byref(t)), "phd_set_tuning")
+
+    def autotune(self, reps: int = 5) -> dict:
+        """Time every supported shape on the current predicted set and keep
+        the fastest (phd_autotune); returns the chosen shape and its times."""
+        t = phd_tuning()
+        self._check(self.L.phd_autotune(self.h, int(reps), ctypes.byref(t)), "phd_autotune")
+        return {k: getattr(t, k) for k, _ in phd_tuning._fields_}
 
 
 class ParticlePHDBatch(ParticlePHD):

@@ -27,22 +27,24 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert sorted(phd.ABI) == names
 
 
-def test_config_struct_layout_matches_header(tmp_path):
-    """The binding's phd_config has the C compiler's size and field offsets."""
+@pytest.mark.parametrize("name", ["phd_config", "phd_stats", "phd_tuning"])
+def test_struct_layout_matches_header(tmp_path, name):
+    """The binding's structs have the C compiler's size and field offsets."""
     import subprocess
-    from paper_1503_03769_gb300.phd import phd_config
-    fields = [f[0] for f in phd_config._fields_]
+    from paper_1503_03769_gb300 import phd
+    st = getattr(phd, name)
+    fields = [f[0] for f in st._fields_]
     prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "phd.h"', "int main(void){",
-            'printf("%zu\\n", sizeof(phd_config));']
-    prog += [f'printf("%zu\\n", offsetof(phd_config, {n}));' for n in fields]
+            f'printf("%zu\\n", sizeof({name}));']
+    prog += [f'printf("%zu\\n", offsetof({name}, {n}));' for n in fields]
     prog += ["return 0;}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(prog))
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
-    assert out[0] == ctypes.sizeof(phd_config)
-    assert out[1:] == [getattr(phd_config, n).offset for n in fields]
+    assert out[0] == ctypes.sizeof(st)
+    assert out[1:] == [getattr(st, n).offset for n in fields]
 
 
 def test_workspace_size_and_config_validation_without_gpu():

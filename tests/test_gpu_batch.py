@@ -29,7 +29,11 @@ def _runs():
     return [w.with_(pe_cap=cap) for w in ws]
 
 
-def test_batch_runs_match_their_oracles():
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_runs_match_their_oracles(autotune):
+    """With autotune, the pair passes' launch shape is re-chosen after the
+    first step (timed on the batch's own slices) and the runs stay on their
+    oracles."""
     from paper_1503_03769_gb300 import ParticlePHDBatch
     ws = _runs()
     R = len(ws)
@@ -62,6 +66,9 @@ def test_batch_runs_match_their_oracles():
                      states=outs[j][0], labels=outs[j][1], par=par[j:j + 1], lx=0,
                      xr=[xr[j]], wr=[wr[j]])
             check_step(w, oracle.model(w), Zs[j], nz[j], u[j:j + 1], None, g, rep)
+        if autotune and k == 0:
+            t = b.autotune(2)
+            assert t["pass1_us"] > 0 and t["pass2_us"] > 0
     assert rep.compared_labels > 0
     b.close()
 

@@ -1,0 +1,137 @@
+"""GPU parity of every launch shape of the update's pair passes (Eq. 7 column
+sums, Eq. 8 row sums), and of the autotuner that picks among them.
+
+Each shape is checked stage by stage against the FP64 oracle (the harness of
+the one-filter tests) on a configuration whose slices span several work
+items with ragged tails and whose measurement count crosses the pass-1 chunk
+of every shape, with CTA caps small enough that every CTA walks several work
+items (and restages particles and measurements between slices)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenario
+from gpu_harness import StageReport, stage_step, npdtype
+
+pytestmark = pytest.mark.gpu
+
+PASS1 = [(t, mb) for t in (256, 512, 1024) for mb in (1, 2, 4)]
+PASS2 = [(1, 1), (2, 1), (4, 1), (1, 2), (2, 2), (1, 4), (1, 8)]
+
+
+def _filter(w, seed, counts, centres, **shape):
+    from paper_1503_03769_gb300 import ParticlePHD
+    f = ParticlePHD(w, seed=seed, device="cuda:0")
+    f.set_path("staged")
+    if shape:
+        f.set_tuning(**shape)
+    rng = np.random.default_rng(seed)
+    xs, ws = [], []
+    for j in range(w.num_pe):
+        x, wt = scenario.random_particles(rng, w, counts[j], centres=centres, spread=25.0, mass=3.0)
+        xs.append(x.astype(npdtype(w)))
+        ws.append(wt.astype(npdtype(w)))
+    f.set_state(xs, ws)
+    return f
+
+
+def _step(f, w, sc, seed, k, rep):
+    noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap, npdtype(w))
+    u = scenario.resample_u32(seed, k, w.num_pe)
+    xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap)
+    return stage_step(f, w, oracle.model(w), sc.meas[k], noise, u, xu, rep)
+
+
+def _rb_case():
+    w = scenario.workload("dense_rb_100t", n_targets=30, clutter_rate=300.0,
+                          particles_per_target=200, birth_count=2000, num_pe=4,
+                          exchange_frac=0.1, birth_steps=(1,) * 30)
+    sc = scenario.simulate(w, 4, steps=2)
+    cen = np.concatenate([t[:, [0, 2]] for t in sc.truth if len(t)])
+    return w, sc, cen, [1500, 1700, 1300, 1611]
+
+
+def _lin_case():
+    w = scenario.workload("dist16_10t", n_targets=6, clutter_rate=30.0, num_pe=8,
+                          particles_per_target=800, birth_count=1000, birth_steps=(1,) * 6)
+    sc = scenario.simulate(w, 9, steps=2)
+    cen = np.concatenate([t[:, [0, 2]] for t in sc.truth if len(t)])[:6]
+    return w, sc, cen, [300 + 97 * j for j in range(8)]
+
+
+@pytest.mark.parametrize("c_tile,c_mb", PASS1)
+def test_pass1_shapes_range_bearing(c_tile, c_mb):
+    """M ~ 330 crosses the 64/128/256-measurement chunks; 5 CTAs walk all items."""
+    w, sc, cen, counts = _rb_case()
+    f = _filter(w, 4, counts, cen, c_tile=c_tile, c_mb=c_mb, grid1=5)
+    rep = StageReport()
+    _step(f, w, sc, 4, 0, rep)
+    f.close()
+    assert rep.compared_labels > 0
+
+
+@pytest.mark.parametrize("r_pb,r_g", PASS2)
+@pytest.mark.parametrize("case", ["linear", "range_bearing"])
+def test_pass2_shapes(r_pb, r_g, case):
+    w, sc, cen, counts = _lin_case() if case == "linear" else _rb_case()
+    f = _filter(w, 9, counts, cen, r_pb=r_pb, r_g=r_g, grid2=7, c_mb=1, grid1=11)
+    rep = StageReport()
+    _step(f, w, sc, 9, 0, rep)
+    f.close()
+    assert rep.compared_labels > 0
+
+
+def test_fp64_shapes():
+    """FP64 handles: the tile and the CTA caps are free, the lane shapes fixed."""
+    from paper_1503_03769_gb300 import PhdError
+    w = scenario.workload("linear4_fp64", n_targets=4, birth_steps=(1, 1, 1, 1), clutter_rate=12.0)
+    sc = scenario.simulate(w, 5, steps=2)
+    cen = sc.truth[0][:, [0, 2]]
+    f = _filter(w, 5, [2100], cen, c_tile=1024, grid1=3, grid2=2)
+    with pytest.raises(PhdError):
+        f.set_tuning(c_mb=4)
+    with pytest.raises(PhdError):
+        f.set_tuning(r_pb=2, r_g=1)
+    assert f.get_tuning()["c_tile"] == 1024
+    rep = StageReport()
+    _step(f, w, sc, 5, 0, rep)
+    f.close()
+    assert rep.compared_labels > 0
+
+
+def test_unsupported_shapes_are_refused():
+    from paper_1503_03769_gb300 import PhdError
+    w, sc, cen, counts = _lin_case()
+    f = _filter(w, 9, counts, cen)
+    before = f.get_tuning()
+    for bad in [dict(c_tile=128), dict(c_mb=3), dict(r_pb=4, r_g=2), dict(r_g=16), dict(grid1=0),
+                dict(grid2=10 ** 6)]:
+        with pytest.raises(PhdError):
+            f.set_tuning(**bad)
+    assert f.get_tuning() == before
+    f.close()
+
+
+def test_autotune_keeps_parity_and_statistics():
+    """The autotuner needs an update to time on, returns a supported shape with
+    its measured times, leaves the counters alone, and the filter stays on the
+    oracle afterwards."""
+    from paper_1503_03769_gb300 import PhdError
+    w, sc, cen, counts = _rb_case()
+    f = _filter(w, 4, counts, cen)
+    with pytest.raises(PhdError):
+        f.autotune(2)                      # no update yet
+    rep = StageReport()
+    _step(f, w, sc, 4, 0, rep)
+    st0 = f.stats()
+    t = f.autotune(2)
+    assert t["pass1_us"] > 0 and t["pass2_us"] > 0
+    assert (t["c_tile"], t["c_mb"]) in PASS1 and (t["r_pb"], t["r_g"]) in PASS2
+    cur = f.get_tuning()
+    assert all(cur[k] == t[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2"))
+    st1 = f.stats()
+    for k in ("pairs", "particles", "measurements", "updates"):
+        assert st1[k] == st0[k], k
+    _step(f, w, sc, 4, 1, rep)
+    f.close()
+    assert rep.compared_labels > 0
