@@ -248,6 +248,20 @@ def run_gpu(args, w, rank, world, local_rank):
         if k == 0:
             f.set_state(empty_x, empty_w)
 
+    # set-up on the staged path: the pair passes' launch shape is autotuned
+    # half-way through a run of the same workload, then the state is reset
+    tuning = None
+    if f.get_path() == "staged" and not args.no_autotune:
+        t_tune = time.perf_counter()
+        tune_sc = scenario.simulate(w, base_seed + 7777, steps=steps_per_run // 2 + 1)
+        for k in range(steps_per_run // 2):
+            f.step(torch.as_tensor(tune_sc.meas[k], dtype=dtype, device=dev), cap=cap, sync=False)
+        tuning = f.autotune(3)
+        tuning = {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2")},
+                  "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
+                  "setup_s": round(time.perf_counter() - t_tune, 3)}
+        f.set_state(empty_x, empty_w)
+
     # warm-up (also captures the step graphs)
     f.set_stage_timer(True)
     for r, k in seq[: args.warmup]:
@@ -418,6 +432,8 @@ def run_gpu(args, w, rank, world, local_rank):
         "gpu_launches": int(st["launches"]),
         "clocks": clocks,
     }
+    if tuning is not None:
+        line["tuning"] = tuning
     if world == 1 and not args.no_cpu_baseline:
         budget = float(os.environ.get("PHD_CPU_BASELINE_S", "15"))
         cp, cs, cn, _ = oracle_run(w, [args.seed], 10 ** 9, budget)

@@ -30,7 +30,8 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "phd_oracle.c")
+_SRCS = [os.path.join(_HERE, "phd_oracle.c"), os.path.join(_HERE, "birth_oracle.c")]
+_DEPS = _SRCS + [os.path.join(_HERE, "orc_model.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -39,10 +40,11 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
 
 
 def build(force: bool = False) -> str:
-    """Compile phd_oracle.c into liboracle.so beside it (gcc, no CUDA)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle's C sources into liboracle.so beside them (gcc, no CUDA)."""
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in _DEPS)
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-I", _HERE, *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -89,6 +91,18 @@ def lib():
                                        _U, _I]
             L.orc_fuse.restype = ctypes.c_int
             L.orc_fuse.argtypes = [ctypes.c_int, _I, _I, _D, ctypes.c_int, ctypes.c_int, _I, _D]
+            L.orc_mlp_nparams.restype = ctypes.c_int
+            L.orc_gelu.restype = ctypes.c_double
+            L.orc_gelu.argtypes = [ctypes.c_double]
+            L.orc_gelu_grad.restype = ctypes.c_double
+            L.orc_gelu_grad.argtypes = [ctypes.c_double]
+            L.orc_birth_features.argtypes = [_M, _D, ctypes.c_int, _D]
+            L.orc_mlp_forward.argtypes = [_D, _D, ctypes.c_int, _D]
+            L.orc_mlp_loss_grad.restype = ctypes.c_double
+            L.orc_mlp_loss_grad.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_double, _D]
+            L.orc_birth_learned.argtypes = [_M, _D, ctypes.c_int, _D, ctypes.c_double, ctypes.c_int,
+                                            _D, _D, _D, _D, _I]
+            L.orc_birth_cdf.argtypes = [_M, _D, ctypes.c_int, _D]
             _lib = L
     return _lib
 
@@ -262,6 +276,79 @@ def fuse(per_pe: Sequence[Extraction], M: int) -> tuple:
 # ----------------------------------------------------------------------------
 # OSPA (Schuhmacher, Vo & Vo), on positions
 # ----------------------------------------------------------------------------
+
+# ----------------------------------------------------------------------------
+# Measurement-driven birth proposal (Eq. 6 with a learned p_k(.|Z_k)) and its
+# network (birth_oracle.c states the readings)
+# ----------------------------------------------------------------------------
+
+def mlp_nparams() -> int:
+    return lib().orc_mlp_nparams()
+
+
+def gelu(a: float) -> float:
+    return lib().orc_gelu(float(a))
+
+
+def gelu_grad(a: float) -> float:
+    return lib().orc_gelu_grad(float(a))
+
+
+def birth_features(m: _Model, Z) -> np.ndarray:
+    """Network input per measurement: scaled plane position, log1p(neighbours)."""
+    Z = _f64(Z, (-1, 2))
+    X = np.empty((len(Z), 3))
+    lib().orc_birth_features(ctypes.byref(m), _d(Z), len(Z), _d(X))
+    return X
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    P, X = _f64(params, (-1,)), _f64(X, (-1, 3))
+    assert len(P) == mlp_nparams()
+    Y = np.empty((len(X), 5))
+    lib().orc_mlp_forward(_d(P), _d(X), len(X), _d(Y))
+    return Y
+
+
+def mlp_loss_grad(params, X, T, vel_scale: float):
+    """Mean training loss and its gradient; T rows (t, vx, vy)."""
+    P, X, T = _f64(params, (-1,)), _f64(X, (-1, 3)), _f64(T, (-1, 3))
+    assert len(P) == mlp_nparams() and len(X) == len(T)
+    G = np.empty(len(P))
+    loss = lib().orc_mlp_loss_grad(_d(P), _d(X), _d(T), len(X), float(vel_scale), _d(G))
+    return loss, G
+
+
+def adam(params, grad, m1, m2, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam step (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns
+    the new (params, m1, m2)."""
+    g = _f64(grad)
+    m1 = b1 * _f64(m1) + (1.0 - b1) * g
+    m2 = b2 * _f64(m2) + (1.0 - b2) * g * g
+    mh = m1 / (1.0 - b1 ** t)
+    vh = m2 / (1.0 - b2 ** t)
+    return _f64(params) - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
+def birth_learned(m: _Model, Z, head, alpha: float, J: int, noise, extra):
+    """Births of one PE from the defensive mixture proposal; noise rows
+    (n1, n2, u1, u2), extra rows (u_c, nz1, nz2, -).  Returns (x, w, comp)."""
+    Z, head = _f64(Z, (-1, 2)), _f64(head, (-1, 5))
+    assert len(head) == len(Z)
+    noise, extra = _f64(noise, (-1, 4)), _f64(extra, (-1, 4))
+    assert len(noise) >= J and len(extra) >= J
+    x, w, comp = np.empty((J, 4)), np.empty(J), np.empty(J, np.int32)
+    lib().orc_birth_learned(ctypes.byref(m), _d(Z), len(Z), _d(head), float(alpha), int(J), _d(noise),
+                            _d(extra), _d(x), _d(w), _i(comp))
+    return x, w, comp
+
+
+def birth_cdf(m: _Model, head) -> np.ndarray:
+    head = _f64(head, (-1, 5))
+    out = np.empty(len(head))
+    lib().orc_birth_cdf(ctypes.byref(m), _d(head), len(head), _d(out))
+    return out
+
 
 def ospa(X, Y, c: float = 100.0, p: float = 2.0) -> float:
     """OSPA distance between two point sets (rows are points)."""

@@ -258,6 +258,35 @@ def step_noise(seed: int, step: int, K: int, pe_cap: int, dtype=np.float64) -> n
     return np.ascontiguousarray(out)
 
 
+def birth_extra_noise(seed: int, step: int, K: int, jmax: int, dtype=np.float64) -> np.ndarray:
+    """Extra draws of the measurement-driven birth, shape (K * jmax, 4):
+    (u_c, nz1, nz2, 0) per birth slot of each PE (jmax = most births of a PE)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xB1E7, seed, step]))
+    n = K * jmax
+    out = np.zeros((n, 4), dtype=np.float64)
+    out[:, 0] = rng.random(n)
+    out[:, 1:3] = rng.standard_normal((n, 2))
+    if dtype == np.float32:
+        out = out.astype(np.float32)
+        out[:, 0] = np.minimum(out[:, 0], np.float32(1.0 - 2.0 ** -24))
+    return np.ascontiguousarray(out)
+
+
+def mlp_params(seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded parameters of the 3-64-64-5 birth network (4741 values, layout
+    W1[64][3], b1[64], W2[64][64], b2[64], W3[5][64], b3[5]), every value an
+    integer in [-127, 127] times a power of two, so it is exact in bfloat16,
+    float32 and float64 alike.  Magnitudes follow 1/sqrt(fan-in) (times
+    `scale`, a power of two)."""
+    assert scale > 0 and math.log2(scale) == int(math.log2(scale))
+    rng = np.random.default_rng(np.random.SeedSequence([0x3A1E, seed]))
+    parts = []
+    for shape, e in [((64, 3), -8), ((64,), -9), ((64, 64), -10), ((64,), -9), ((5, 64), -10), ((5,), -8)]:
+        k = rng.integers(-127, 128, size=shape).astype(np.float64)
+        parts.append((k * 2.0 ** e * scale).ravel())
+    return np.concatenate(parts)
+
+
 def resample_u32(seed: int, step: int, K: int) -> np.ndarray:
     rng = np.random.default_rng(np.random.SeedSequence([0x5E5A, seed, step]))
     return rng.integers(0, 2 ** 32, size=K, dtype=np.uint64).astype(np.uint32)
