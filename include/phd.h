@@ -111,6 +111,104 @@ const char *phd_status_string(phd_status s);
  * fractions.  Errors: PHD_ERR_STATE if called twice without an update. */
 phd_status phd_predict(phd_handle *h, const void *d_noise);
 
+/* ---- measurement-driven birth (Eq. 6 with a learned proposal) ------------- */
+
+/* Eq. 6 draws the births from a proposal p_k(x | Z_k) that may depend on the
+ * current scan and weights them gamma(x) / (J p_k(x | Z_k)).  With a birth
+ * network loaded, each PE's J_j births come from the defensive mixture
+ *   q(x | Z) = alpha p_plain(x) + (1 - alpha) sum_p pi_p q_p(x),
+ * p_plain = U(region) x N(0, birth_vel_sigma^2 I) the plain birth,
+ * pi = softmax of the network's logit over the M measurements, q_p the
+ * position draw around z_p (linear sensor: z_p + sensor noise; range-bearing:
+ * range |z_r + s_r n1|, bearing z_th + s_th n2 around the sensor) times a
+ * velocity Gaussian N(s_b (m_x, m_y), diag (s_b e^l)^2) (l clamped to
+ * [log 0.05, log 5]; s_b = birth_vel_sigma), and weight
+ *   w = (birth_mass / J_j) / (alpha + (1 - alpha) R(x)),
+ *   R(x) = sum_p pi_p q_p(x) / p_plain(x),
+ * 0 outside the region: the intensity sum_b w_b delta(x_b) is an unbiased
+ * estimate of the plain birth intensity (gamma = birth_mass p_plain), so the
+ * PHD recursion is unchanged in expectation; alpha = 1 (or M = 0) gives the
+ * plain birth exactly.  The network (inputs per measurement: its position in
+ * the plane scaled to the region, (p - centre) / half-width, and log1p of the
+ * number of other measurements within 3 sigma per measurement coordinate;
+ * 3 -> 64 -> 64 -> 5, exact-erf GELU, bfloat16 operands, FP32 sums) is the
+ * one of phd_mlp_forward.
+ *
+ * Random numbers: each birth slot uses its plain-birth row (n1, n2, u1, u2)
+ * (velocity normals; position fractions of the plain branch) and an extra
+ * row (u_c, nz1, nz2, unused): u_c < alpha takes the plain branch, else the
+ * component is the smallest p with CDF_p > (u_c - alpha) / (1 - alpha) and
+ * nz1, nz2 are its position normals.  Injected noise then holds K * pe_cap
+ * plain rows followed by K * jmax extra rows, jmax = ceil(J / K), PE j's
+ * birth b at extra row j * jmax + b; without injected noise Philox draws them.
+ *
+ * Load (d_params: device FP32 [phd_mlp_nparams()], rounded to bfloat16 into
+ * the workspace) or, with d_params NULL, unload the network.  alpha in (0, 1].
+ * FP32 one-filter handles only (PHD_ERR_STATE otherwise).  With a network
+ * loaded: the fused step kernel is not used; phd_predict refuses
+ * (PHD_ERR_STATE: use phd_predict_z); phd_step, phd_step_inject,
+ * phd_step_host and phd_run draw the births from the scan they are given.
+ * Synchronises. */
+phd_status phd_set_birth_proposal(phd_handle *h, const float *d_params, double alpha);
+
+/* Prediction with the scan: stages Z (real [M][2] device rows, as for
+ * phd_update), runs phd_predict's survivor and plain-birth draws, then, with
+ * a network loaded, evaluates it on Z (or takes d_head, device FP32 [M][5]
+ * network outputs (m_x, m_y, l_x, l_y, logit), when not NULL) and redraws
+ * the births from the mixture.  Without a network it is phd_predict.
+ * Asynchronous.  Errors as phd_predict and phd_update's checks of Z. */
+phd_status phd_predict_z(phd_handle *h, const void *d_Z, int32_t M, const float *d_head, const void *d_noise);
+
+/* Copy the network outputs [M][5] of the last learned-birth prediction to
+ * d_out (at most cap rows); *h_M gets M.  Synchronises.  PHD_ERR_CAPACITY if
+ * M > cap (cap rows copied), PHD_ERR_STATE without a network. */
+phd_status phd_get_birth_head(phd_handle *h, float *d_out, int32_t cap, int32_t *h_M);
+
+/* ---- the birth network: stateless inference and training ------------------ */
+
+/* The network input per measurement (FP32): X[M][3] = ((p_x - c_x) / h_x,
+ * (p_y - c_y) / h_y, log1p(n)) with p the measurement's position in the plane
+ * (the measurement itself for the linear sensor; sensor + r (cos th, sin th)
+ * for range-bearing), c and h the centre and half-widths of cfg.region, and
+ * n the number of other measurements q with |z_q0 - z_p0| <= 3 sigma_z[0]
+ * and |wrap(z_q1 - z_p1)| <= 3 sigma_z[1] (bearing wrapped to [-pi, pi]).
+ * d_Z FP32 [M][2], device; stream a cudaStream_t or NULL.  Asynchronous.
+ * PHD_ERR_INVALID_ARG for a bad cfg (phd_init's checks), M < 0 or NULL
+ * buffers. */
+phd_status phd_birth_features(const phd_config *cfg, const float *d_Z, int32_t M, float *d_X, void *stream);
+
+/* Number of parameters (4741): W1[64][3], b1[64], W2[64][64], b2[64],
+ * W3[5][64], b3[5], W[j][k] the weight from input k into unit j. */
+int32_t phd_mlp_nparams(void);
+
+/* Y[n][5] = network(X[n][3]) with bfloat16 operands (parameters, inputs and
+ * hidden activations rounded to nearest even) and FP32 sums; d_params FP32
+ * [phd_mlp_nparams()].  All pointers device; stream a cudaStream_t or NULL.
+ * Asynchronous.  PHD_ERR_INVALID_ARG for n < 0 or NULL buffers. */
+phd_status phd_mlp_forward(const float *d_params, const float *d_X, int32_t n, float *d_Y, void *stream);
+
+/* Scratch bytes phd_mlp_grad needs for n inputs. */
+phd_status phd_mlp_grad_scratch_size(int32_t n, size_t *bytes);
+
+/* Mean training loss over n >= 1 inputs and its gradient d_grad
+ * [phd_mlp_nparams()] (FP32).  Targets d_T[n][3] = (t, vx, vy): t = 1 when the
+ * filter extracted an estimate for the measurement, with its velocity in m/s
+ * (ignored when t = 0); vel_scale s_b > 0.  Per input, with v~ = v / s_b and
+ * outputs y = (m_x, m_y, l_x, l_y, logit):
+ *   L = softplus(logit) - t logit + t sum_d [ l_d + (v~_d - m_d)^2 e^{-2 l_d} / 2 ].
+ * The forward pass is phd_mlp_forward's; the backward pass uses its bfloat16
+ * weights and activations with FP32 deltas; per-CTA partial sums are added in
+ * a fixed order (deterministic).  d_loss may be NULL.  Asynchronous.
+ * PHD_ERR_CAPACITY if scratch_bytes is below phd_mlp_grad_scratch_size. */
+phd_status phd_mlp_grad(const float *d_params, const float *d_X, const float *d_T, int32_t n, float vel_scale,
+                        float *d_grad, float *d_loss, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* One Adam step (Kingma & Ba, ICLR 2015, Algorithm 1) on the FP32 parameters
+ * with moment buffers d_m, d_v (zero before step t = 1), step t >= 1.
+ * Asynchronous. */
+phd_status phd_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int32_t t, float lr,
+                        float beta1, float beta2, float eps, void *stream);
+
 /* Update, Eq. 7-8: C^j_p = sum_i p_D g(z_p|x_i) w_i per PE (FP64 accumulation),
  * w_i <- [(1 - p_D) + sum_p p_D g(z_p|x_i) / (kappa + C_p)] w_i with C_p the
  * PE's own C^j_p (LOCAL) or the PE mean (GLOBAL).  d_Z: real [M][2]; it is

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "mlp_device.cuh"
 #include "phd_internal.cuh"
 
 using phd::Dev;
@@ -119,6 +120,10 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.step = cv.take<unsigned long long>(1);
   t.stats = cv.take<unsigned long long>(4);
   t.err = cv.take<int>(1);
+  t.mlp_w = cv.take<char>(phd::kNParams, 2);
+  t.bhead = cv.take<float>(Mm * 5);
+  t.bcomp = cv.take<float>(Mm * 8);
+  t.bcdf = cv.take<float>(Mm);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -206,6 +211,20 @@ Model make_model(const phd_config& c) {
   m.f_bw_lo = (float)m.bw_lo;
   m.f_bw_hi = (float)m.bw_hi;
   m.tune = phd::default_tune(c.precision == PHD_FP64);
+  m.learned = 0;
+  m.jmax = (c.birth_count + c.num_pe - 1) / c.num_pe;
+  m.f_alpha = 1.0f;
+  {
+    const double area = (c.region[1] - c.region[0]) * (c.region[3] - c.region[2]);
+    const double sb = c.birth_vel_sigma;
+    m.f_blog = (float)std::log2(area * sb * sb / (2.0 * kPi * c.sigma_z[0] * c.sigma_z[1]));
+  }
+  m.f_win0 = (float)(3.0 * c.sigma_z[0]);
+  m.f_win1 = (float)(3.0 * c.sigma_z[1]);
+  m.f_cx = (float)(0.5 * (c.region[0] + c.region[1]));
+  m.f_cy = (float)(0.5 * (c.region[2] + c.region[3]));
+  m.f_ihx = (float)(2.0 / (c.region[1] - c.region[0]));
+  m.f_ihy = (float)(2.0 / (c.region[3] - c.region[2]));
   return m;
 }
 
@@ -267,7 +286,7 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
 }
 
 // kernels each stage launches (for the launch counter)
-constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1;
+constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1, kNBirth = 3;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
 
 phd_status read_device_error(phd_handle* h) {
@@ -282,12 +301,30 @@ phd_status read_device_error(phd_handle* h) {
   return fail(h, PHD_ERR_CAPACITY, "device-side capacity check failed");
 }
 
-phd_status do_predict(phd_handle* h, const void* noise) {
+// Prediction; with a birth network loaded the births are then redrawn from
+// its proposal, which needs Z_k staged (z_staged) and, unless `head` is given
+// ([M][5] network outputs), runs the network on it.
+phd_status do_predict(phd_handle* h, const void* noise, bool z_staged = false, const float* head = nullptr,
+                      int M = 0) {
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_predict: a step is already in progress");
+  if (h->m.learned && !z_staged)
+    return fail(h, PHD_ERR_STATE, "phd_predict: a birth network is loaded; births need the scan (phd_predict_z)");
   cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, static_cast<const double*>(noise), h->stream)
                              : phd::launch_predict<float>(h->d, h->m, static_cast<const float*>(noise), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "predict");
   h->launches += kNPredict;
+  if (h->m.learned) {
+    if (head) {
+      if (M > 0) e = cudaMemcpyAsync(h->d.bhead, head, sizeof(float) * 5 * (size_t)M, cudaMemcpyDeviceToDevice,
+                                     h->stream);
+    } else {
+      e = phd::launch_birth_head(h->d, h->m, h->stream);
+      h->launches += 1;
+    }
+    if (e == cudaSuccess) e = phd::launch_birth_draw(h->d, h->m, static_cast<const float*>(noise), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned birth");
+    h->launches += kNBirth - 1;
+  }
   h->stage = kPredicted;
   return PHD_OK;
 }
@@ -343,8 +380,11 @@ phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
 
 // Step body with in-kernel randomness, split in three parts around the update.
 cudaError_t enq_pre(phd_handle* h, cudaStream_t s) {
-  return is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, nullptr, s)
-                    : phd::launch_predict<float>(h->d, h->m, nullptr, s);
+  cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, nullptr, s)
+                             : phd::launch_predict<float>(h->d, h->m, nullptr, s);
+  if (e == cudaSuccess && h->m.learned) e = phd::launch_birth_head(h->d, h->m, s);
+  if (e == cudaSuccess && h->m.learned) e = phd::launch_birth_draw(h->d, h->m, nullptr, s);
+  return e;
 }
 cudaError_t enq_upd(phd_handle* h, cudaStream_t s) {
   return is_fp64(h) ? phd::launch_update<double>(h->d, h->m, s) : phd::launch_update<float>(h->d, h->m, s);
@@ -453,12 +493,13 @@ phd_status run_step_body(phd_handle* h) {
     if (e == cudaSuccess) e = cudaGraphLaunch(h->g_post, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
-  h->launches += kNPredict + kNUpdate + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) + kNAdvance;
+  h->launches += kNPredict + kNUpdate + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) + kNAdvance +
+                 (h->m.learned ? kNBirth : 0);
   return PHD_OK;
 }
 
 phd_status stage_z_only(phd_handle* h, const void* Z, int M);
-bool use_fused(const phd_handle* h) { return h->fused_ok && h->path != PHD_PATH_STAGED; }
+bool use_fused(const phd_handle* h) { return h->fused_ok && !h->m.learned && h->path != PHD_PATH_STAGED; }
 
 // One fused launch of S steps.  With zoff == NULL: one step of M rows at Z.
 phd_status run_fused(phd_handle* h, const void* Z, const int* zoff, int M, int S, const void* noise,
@@ -500,8 +541,14 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
     st = run_fused(h, Z, nullptr, M, 1, noise, u, xu, direct ? d_states : h->out_states,
                    direct ? d_labels : h->out_labels, h->d.out_count, direct ? cap : h->cfg.m_max);
   } else if (noise || u || xu) {
-    st = do_predict(h, noise);
-    if (st == PHD_OK) st = do_update(h, Z, M, Z == h->d.Z);
+    if (h->m.learned) {
+      st = stage_z_only(h, Z, M);
+      if (st == PHD_OK) st = do_predict(h, noise, true);
+      if (st == PHD_OK) st = do_update(h, h->d.Z, M, true);
+    } else {
+      st = do_predict(h, noise);
+      if (st == PHD_OK) st = do_update(h, Z, M, Z == h->d.Z);
+    }
     if (st == PHD_OK) st = do_extract(h, h->out_states, h->out_labels, h->cfg.m_max, nullptr, nullptr);
     if (st == PHD_OK) st = do_resample(h, u, xu);
     if (st != PHD_OK) h->stage = kReady;
@@ -639,6 +686,54 @@ phd_status phd_predict(phd_handle* h, const void* d_noise) {
 phd_status phd_update(phd_handle* h, const void* d_Z, int32_t M) {
   if (!h) return PHD_ERR_INVALID_ARG;
   return do_update(h, d_Z, M, false);
+}
+
+phd_status phd_set_birth_proposal(phd_handle* h, const float* d_params, double alpha) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (!d_params) {
+    PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->m.learned = 0;
+    h->m.f_alpha = 1.0f;
+    destroy_graphs(h);
+    return PHD_OK;
+  }
+  if (is_fp64(h) || h->batch_runs)
+    return fail(h, PHD_ERR_STATE, "phd_set_birth_proposal: FP32 one-filter handles only");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(h, PHD_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+  PHD_CUDA(h, phd::launch_params_bf16(h->d.mlp_w, d_params, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->m.learned = 1;
+  h->m.f_alpha = (float)alpha;
+  destroy_graphs(h);
+  return PHD_OK;
+}
+
+phd_status phd_predict_z(phd_handle* h, const void* d_Z, int32_t M, const float* d_head, const void* d_noise) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  if (h->batch_runs) return fail(h, PHD_ERR_STATE, "a batch handle steps through phd_batch_step");
+  if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_predict_z: a step is already in progress");
+  if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
+  if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
+  if (M > 0 && !d_Z) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  phd_status st = stage_z_only(h, d_Z, M);
+  if (st != PHD_OK) return st;
+  return do_predict(h, d_noise, true, d_head, M);
+}
+
+phd_status phd_get_birth_head(phd_handle* h, float* d_out, int32_t cap, int32_t* h_M) {
+  if (!h || !h_M || cap < 0 || (cap > 0 && !d_out)) return PHD_ERR_INVALID_ARG;
+  if (!h->m.learned) return fail(h, PHD_ERR_STATE, "phd_get_birth_head: no birth network loaded");
+  int M = 0;
+  PHD_CUDA(h, cudaMemcpyAsync(&M, h->d.M, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  *h_M = M;
+  const int n = M < cap ? M : cap;
+  if (n > 0) {
+    PHD_CUDA(h, cudaMemcpyAsync(d_out, h->d.bhead, sizeof(float) * 5 * (size_t)n, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return M > cap ? fail(h, PHD_ERR_CAPACITY, "more measurements than cap") : PHD_OK;
 }
 
 phd_status phd_extract(phd_handle* h, void* d_states, int32_t* d_labels, int32_t cap, int32_t* d_count,

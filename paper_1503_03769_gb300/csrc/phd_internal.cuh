@@ -62,6 +62,13 @@ struct Model {
   float f_bw_lo, f_bw_hi;  // birth weight nu_b / J_j for J_j = J / K and J / K + 1
   double bw_lo, bw_hi;
   Tune tune;
+  // measurement-driven birth (Eq. 6 with a learned p_k(.|Z_k)); FP32 handles
+  int learned;           // 1: births from the network's mixture proposal
+  int jmax;              // most births of one PE (rows of the injected extra draws)
+  float f_alpha;         // weight of the plain birth in the defensive mixture
+  float f_blog;          // log2(area s_b^2 / (2 pi s_z0 s_z1))
+  float f_win0, f_win1;  // feature window: 3 sigma per measurement coordinate
+  float f_cx, f_cy, f_ihx, f_ihy;  // region centre and 1 / half-width
 };
 
 // Per-particle model constants in the kernel's precision.
@@ -131,6 +138,11 @@ struct Dev {
   unsigned long long* stats; // [4] sums over updates: pairs, particles, measurements, updates
   int* err;              // [1] device error bits
   int max_items;
+  // measurement-driven birth
+  void* mlp_w;           // bfloat16 [kNParams] network parameters
+  float* bhead;          // [m_max][5] network output per measurement
+  float* bcomp;          // [m_max][8] proposal component constants
+  float* bcdf;           // [m_max] mixture CDF
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
@@ -155,7 +167,9 @@ __device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
 }
 
 // Stream tags of the Philox counter's third word.
-enum : uint32_t { kTagPredict = 0x50524544u, kTagResample = 0x52534d50u, kTagExchange = 0x58434847u };
+enum : uint32_t {
+  kTagPredict = 0x50524544u, kTagResample = 0x52534d50u, kTagExchange = 0x58434847u, kTagBirth = 0x42495254u
+};
 
 // u in (0, 1) from 32 random bits, in the kernel's real type.
 template <class R> __device__ __forceinline__ R unit_open(uint32_t b);
@@ -495,6 +509,11 @@ template <class R> cudaError_t launch_finalize(const Dev& d, const Model& m, cud
 template <class R> cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s);
 cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s);
 Tune default_tune(bool fp64);
+// measurement-driven birth (FP32): network head per measurement (unless the
+// head was supplied), mixture table, births drawn over the plain ones
+cudaError_t launch_birth_head(const Dev& d, const Model& m, cudaStream_t s);
+cudaError_t launch_birth_draw(const Dev& d, const Model& m, const float* noise, cudaStream_t s);
+cudaError_t launch_params_bf16(void* dst, const float* src, cudaStream_t s);
 bool tune_supported(const Tune& t, bool fp64);
 template <class R> cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels,
                                               int cap, int* d_count, cudaStream_t s);

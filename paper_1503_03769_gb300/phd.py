@@ -106,6 +106,16 @@ ABI = {
                                       ctypes.c_size_t, _P]),
     "phd_batch_step": (ctypes.c_int, [_H, _P, _P, _P, _P, _P, ctypes.c_int32]),
     "phd_batch_step_inject": (ctypes.c_int, [_H, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
+    "phd_set_birth_proposal": (ctypes.c_int, [_H, _P, ctypes.c_double]),
+    "phd_predict_z": (ctypes.c_int, [_H, _P, ctypes.c_int32, _P, _P]),
+    "phd_get_birth_head": (ctypes.c_int, [_H, _P, ctypes.c_int32, _I32P]),
+    "phd_mlp_nparams": (ctypes.c_int32, []),
+    "phd_birth_features": (ctypes.c_int, [ctypes.POINTER(phd_config), _P, ctypes.c_int32, _P, _P]),
+    "phd_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "phd_mlp_grad_scratch_size": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "phd_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phd_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, _P]),
 }
 
 _lib = None
@@ -172,6 +182,75 @@ def colsum_static(cfg: phd_config, x: torch.Tensor, w: torch.Tensor, Z: torch.Te
                                    ctypes.c_void_p(st.cuda_stream))
 
 
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(st.cuda_stream)
+
+
+def _check_status(st: int, what: str):
+    if st != PHD_OK:
+        raise PhdError(st, what)
+
+
+def mlp_nparams() -> int:
+    return int(lib().phd_mlp_nparams())
+
+
+def mlp_forward(params: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+    """Birth network outputs Y[n][5] for inputs X[n][3] (phd_mlp_forward)."""
+    n = int(X.shape[0])
+    Y = torch.empty((n, 5), dtype=torch.float32, device=X.device)
+    _check_status(lib().phd_mlp_forward(_ptr(params), _ptr(X) if n else None, n, _ptr(Y) if n else None,
+                                        _stream_ptr(stream)), "phd_mlp_forward")
+    return Y
+
+
+def birth_features(cfg: phd_config, Z: torch.Tensor, stream=None) -> torch.Tensor:
+    """Birth network inputs X[M][3] of a scan Z[M][2] (FP32, device)."""
+    M = int(Z.shape[0])
+    X = torch.empty((M, 3), dtype=torch.float32, device=Z.device)
+    _check_status(lib().phd_birth_features(ctypes.byref(cfg), _ptr(Z) if M else None, M, _ptr(X) if M else None,
+                                           _stream_ptr(stream)), "phd_birth_features")
+    return X
+
+
+class MlpTrainer:
+    """Adam training of the birth network through phd_mlp_grad / phd_mlp_adam
+    (FP32 master parameters on the device)."""
+
+    def __init__(self, params: torch.Tensor, batch_max: int, lr: float = 1e-3, betas=(0.9, 0.999),
+                 eps: float = 1e-8, vel_scale: float = 20.0, stream=None):
+        self.L = lib()
+        self.params = params.detach().to(torch.float32).contiguous().clone()
+        self.m1 = torch.zeros_like(self.params)
+        self.m2 = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.params.device)
+        nb = ctypes.c_size_t(0)
+        _check_status(self.L.phd_mlp_grad_scratch_size(int(batch_max), ctypes.byref(nb)), "scratch_size")
+        self.scratch = torch.empty(int(nb.value), dtype=torch.uint8, device=self.params.device)
+        self.batch_max = int(batch_max)
+        self.lr, self.betas, self.eps, self.vel_scale = float(lr), betas, float(eps), float(vel_scale)
+        self.t = 0
+        self.stream = stream
+
+    def grad_of(self, X: torch.Tensor, T: torch.Tensor) -> torch.Tensor:
+        """Mean-loss gradient for inputs X[n][3], targets T[n][3] into self.grad."""
+        n = int(X.shape[0])
+        assert 0 < n <= self.batch_max
+        _check_status(self.L.phd_mlp_grad(_ptr(self.params), _ptr(X), _ptr(T), n, self.vel_scale,
+                                          _ptr(self.grad), _ptr(self.loss), _ptr(self.scratch),
+                                          self.scratch.numel(), _stream_ptr(self.stream)), "phd_mlp_grad")
+        return self.grad
+
+    def step(self, X: torch.Tensor, T: torch.Tensor):
+        self.grad_of(X, T)
+        self.t += 1
+        _check_status(self.L.phd_mlp_adam(_ptr(self.params), _ptr(self.grad), _ptr(self.m1), _ptr(self.m2),
+                                          self.t, self.lr, float(self.betas[0]), float(self.betas[1]),
+                                          self.eps, _stream_ptr(self.stream)), "phd_mlp_adam")
+
+
 class ParticlePHD:
     """One filter (global for num_pe == 1, DCPFPHD for num_pe > 1) on a CUDA device."""
 
@@ -196,6 +275,8 @@ class ParticlePHD:
         self._check(st, "phd_init")
         self.h = h
         self._cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.learned = False
+        self.jmax = -(-int(self.cfg.birth_count) // self.K)
 
     # -- plumbing -----------------------------------------------------------
     def _check(self, st: int, what: str, count: Optional[int] = None):
@@ -221,10 +302,40 @@ class ParticlePHD:
         return t.contiguous()
 
     # -- stages -------------------------------------------------------------
+    def _noise_rows(self) -> int:
+        """Rows of injected noise: the plain rows, then (with a birth network)
+        the extra rows of the measurement-driven births."""
+        return self.K * self.pe_cap + (self.K * self.jmax if self.learned else 0)
+
     def predict(self, noise=None):
         n = None if noise is None else self._real(noise, (self.K * self.pe_cap, 4))
         self._check(self.L.phd_predict(self.h, _ptr(n)), "phd_predict")
         self._keep = n
+
+    def predict_z(self, Z, noise=None, head=None):
+        """phd_predict_z: prediction with the scan (measurement-driven births
+        when a birth network is loaded; `head` [M][5] replaces its output)."""
+        Zt = self._real(Z, (-1, 2))
+        M = int(Zt.shape[0])
+        n = None if noise is None else self._real(noise, (self._noise_rows(), 4))
+        hd = None if head is None else torch.as_tensor(head, dtype=torch.float32,
+                                                       device=self.device).reshape(M, 5).contiguous()
+        self._check(self.L.phd_predict_z(self.h, _ptr(Zt) if M else None, M, _ptr(hd) if (hd is not None and M)
+                                         else None, _ptr(n)), "phd_predict_z")
+        self._keep = (Zt, n, hd)
+
+    def set_birth_proposal(self, params: Optional[torch.Tensor], alpha: float = 0.1):
+        """Load the birth network (FP32 device parameters) or unload it (None)."""
+        p = None if params is None else params.to(device=self.device, dtype=torch.float32).contiguous()
+        self._check(self.L.phd_set_birth_proposal(self.h, _ptr(p), float(alpha)), "phd_set_birth_proposal")
+        self.learned = p is not None
+
+    def get_birth_head(self) -> np.ndarray:
+        out = torch.empty((self.m_max, 5), dtype=torch.float32, device=self.device)
+        M = ctypes.c_int32(0)
+        self._check(self.L.phd_get_birth_head(self.h, _ptr(out), self.m_max, ctypes.byref(M)),
+                    "phd_get_birth_head")
+        return out[:M.value].cpu().numpy()
 
     def update(self, Z):
         Zt = self._real(Z, (-1, 2))
@@ -276,7 +387,7 @@ class ParticlePHD:
         """One step with injected random numbers (phd_step_inject); synchronises."""
         cap = self.m_max if cap is None else int(cap)
         Zt = self._real(Z, (-1, 2))
-        nz = None if noise is None else self._real(noise, (self.K * self.pe_cap, 4))
+        nz = None if noise is None else self._real(noise, (self._noise_rows(), 4))
         ut, xt = self._u32(u), self._u32(xu)
         states = torch.empty((max(cap, 1), 4), dtype=self.dtype, device=self.device)
         labels = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)

@@ -1,0 +1,246 @@
+"""GPU parity of the birth network (forward, loss gradient, Adam, features)
+and of the measurement-driven birth draws (Eq. 6 with a learned proposal)
+against the FP64 oracle, through the C ABI.
+
+Tolerances come from the arithmetic: the kernels round every matrix-product
+operand (inputs, weights, hidden activations) to bfloat16 (unit roundoff
+u = 2^-8) and sum in FP32; the seeded parameters are exact in bfloat16, so
+the only differences from the FP64 oracle are the rounding of the inputs and
+of the two hidden layers, propagated through |W| (GELU' <= 1.13) and bounded
+per output below.  The birth draws take the network head as an input shared
+by both sides and compare positions to 1e-3 m and weights to 1e-4 relative,
+except where the component choice sits within FP32 rounding of a CDF
+boundary (checked to be such a case)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenario
+
+pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -8
+
+
+def _np_forward_bound(P, X):
+    """Per-output bound on |y_bf16 - y_exact| from bfloat16 rounding of the
+    inputs and hidden activations (first order; FP32 sums add <= 2^-20 rel)."""
+    o = 0
+    W1 = P[o:o + 192].reshape(64, 3); o += 192
+    b1 = P[o:o + 64]; o += 64
+    W2 = P[o:o + 4096].reshape(64, 64); o += 4096
+    b2 = P[o:o + 64]; o += 64
+    W3 = P[o:o + 320].reshape(5, 64); o += 320
+    gelu = np.vectorize(oracle.gelu)
+    a1 = X @ W1.T + b1
+    h1 = gelu(a1)
+    a2 = h1 @ W2.T + b2
+    h2 = gelu(a2)
+    e_a1 = U_BF16 * (np.abs(X) @ np.abs(W1).T)
+    e_h1 = 1.13 * e_a1 + U_BF16 * np.abs(h1)
+    e_a2 = e_h1 @ np.abs(W2).T + 2.0 ** -20 * (np.abs(h1) @ np.abs(W2).T + np.abs(b2))
+    e_h2 = 1.13 * e_a2 + U_BF16 * np.abs(h2)
+    e_y = e_h2 @ np.abs(W3).T + 2.0 ** -20 * (np.abs(h2) @ np.abs(W3).T)
+    return e_y
+
+
+def _inputs(seed, n):
+    rng = np.random.default_rng(seed)
+    X = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), np.log1p(rng.integers(0, 6, n))])
+    return X
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 1000])
+def test_forward_matches_oracle(n):
+    from paper_1503_03769_gb300 import mlp_forward
+    P = scenario.mlp_params(1, scale=4.0)
+    X = _inputs(2, n)
+    Y = mlp_forward(torch.tensor(P, dtype=torch.float32, device="cuda"),
+                    torch.tensor(X, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    ref = oracle.mlp_forward(P, X.astype(np.float32).astype(np.float64))
+    bound = 1.5 * _np_forward_bound(P, X) + 1e-6
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+
+
+def _targets(seed, n, X):
+    rng = np.random.default_rng(seed)
+    t = (rng.random(n) < 0.3).astype(np.float64)
+    v = 20.0 * np.column_stack([X[:, 0] + 0.3 * rng.standard_normal(n), -X[:, 1] + 0.3 * rng.standard_normal(n)])
+    return np.column_stack([t, v * t[:, None]])
+
+
+@pytest.mark.parametrize("n", [5, 64, 777])
+def test_gradient_matches_oracle(n):
+    from paper_1503_03769_gb300 import MlpTrainer
+    # fan-in scaled weights keep the outputs O(1), as in training; the loss's
+    # e^{-2 l} amplifies head errors exponentially for extreme log-stds
+    P = scenario.mlp_params(3, scale=1.0)
+    X = _inputs(4, n).astype(np.float32).astype(np.float64)
+    T = _targets(5, n, X).astype(np.float32).astype(np.float64)
+    tr = MlpTrainer(torch.tensor(P, dtype=torch.float32, device="cuda"), batch_max=n, vel_scale=20.0)
+    g = tr.grad_of(torch.tensor(X, dtype=torch.float32, device="cuda"),
+                   torch.tensor(T, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    loss = float(tr.loss.item())
+    lref, gref = oracle.mlp_loss_grad(P, X, T, 20.0)
+    # each gradient entry is a sum over inputs of delta x activation with
+    # both factors carrying ~u relative error: 1e-2 of the block's scale
+    assert abs(loss - lref) <= 1e-2 * abs(lref) + 1e-6
+    for a, b in [(0, 192), (192, 256), (256, 4352), (4352, 4416), (4416, 4736), (4736, 4741)]:
+        gb, rb = g[a:b], gref[a:b]
+        scale = np.abs(rb).max()
+        assert np.linalg.norm(gb - rb) <= 1e-2 * np.linalg.norm(rb) + 1e-7, (a, b)
+        assert np.all(np.abs(gb - rb) <= 3e-2 * np.abs(rb) + 2e-2 * scale + 1e-7), (a, b)
+
+
+def test_adam_matches_oracle():
+    from paper_1503_03769_gb300 import phd as P_
+    rng = np.random.default_rng(6)
+    n = P_.mlp_nparams()
+    p = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    m1 = np.zeros(n)
+    m2 = np.zeros(n)
+    dp = torch.tensor(p, dtype=torch.float32, device="cuda")
+    dm1 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dm2 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    L = P_.lib()
+    for t in range(1, 4):
+        g = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+        dg = torch.tensor(g, dtype=torch.float32, device="cuda")
+        st = L.phd_mlp_adam(P_._ptr(dp), P_._ptr(dg), P_._ptr(dm1), P_._ptr(dm2), t, 1e-3, 0.9, 0.999, 1e-8, None)
+        assert st == 0
+        # the kernel's betas are the FP32 values the caller passed
+        p, m1, m2 = oracle.adam(p, g, m1, m2, t, 1e-3, b1=float(np.float32(0.9)), b2=float(np.float32(0.999)))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dp.cpu().numpy(), p, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(dm2.cpu().numpy(), m2, rtol=1e-5)
+
+
+@pytest.mark.parametrize("model_name", ["linear4_fp64", "dense_rb_100t"])
+def test_features_match_oracle(model_name):
+    from paper_1503_03769_gb300 import phd as P_
+    w = scenario.workload(model_name, precision="fp32")
+    sc = scenario.simulate(w.with_(clutter_rate=200.0), 8, steps=3)
+    Z = np.asarray(sc.meas[2], np.float32)
+    X = P_.birth_features(P_.make_config(w), torch.tensor(Z, device="cuda")).cpu().numpy()
+    ref = oracle.birth_features(oracle.model(w), Z.astype(np.float64))
+    np.testing.assert_allclose(X[:, :2], ref[:, :2], atol=2e-6)
+    bad = np.flatnonzero(X[:, 2] != ref[:, 2].astype(np.float32))
+    # a differing count needs a neighbour within FP32 rounding of the window edge
+    for p in bad:
+        d = np.abs(Z.astype(np.float64) - Z[p].astype(np.float64))
+        if w.meas_model != "linear":
+            d[:, 1] = np.abs(np.angle(np.exp(1j * d[:, 1])))
+        edge = np.abs(d - 3 * np.asarray(w.sigma_z)) <= 1e-4 * (1 + 3 * np.asarray(w.sigma_z))
+        assert edge.any(), p
+    assert len(bad) <= 1
+
+
+def _learned_filter(w, params, alpha, seed=0):
+    from paper_1503_03769_gb300 import ParticlePHD
+    f = ParticlePHD(w, seed=seed, device="cuda:0")
+    f.set_path("staged")
+    f.set_birth_proposal(torch.tensor(params, dtype=torch.float32, device="cuda"), alpha)
+    return f
+
+
+@pytest.mark.parametrize("model_name", ["linear4_fp64", "dense_rb_100t"])
+def test_head_in_the_filter_matches_oracle(model_name):
+    w = scenario.workload(model_name, precision="fp32", num_pe=2, birth_count=600, pe_cap=4096, m_max=256)
+    P = scenario.mlp_params(7, scale=4.0)
+    f = _learned_filter(w, P, 0.25)
+    sc = scenario.simulate(w.with_(clutter_rate=80.0), 9, steps=2)
+    Z = np.asarray(sc.meas[1], np.float32)
+    f.predict_z(Z)
+    head = f.get_birth_head().astype(np.float64)
+    X = oracle.birth_features(oracle.model(w), Z.astype(np.float64))
+    ref = oracle.mlp_forward(P, X)
+    bound = 1.5 * _np_forward_bound(P, X) + 1e-5
+    assert head.shape == ref.shape
+    assert np.all(np.abs(head - ref) <= bound)
+    f.close()
+
+
+@pytest.mark.parametrize("model_name,alpha", [("linear4_fp64", 0.25), ("dense_rb_100t", 0.25),
+                                              ("dense_rb_100t", 1.0), ("linear4_fp64", 0.02)])
+def test_learned_births_match_oracle(model_name, alpha):
+    """Injected head and random numbers: every birth slot of every PE against
+    oracle.birth_learned; survivors are untouched by the learned draw."""
+    K = 3
+    w = scenario.workload(model_name, precision="fp32", num_pe=K, birth_count=1000, pe_cap=2048, m_max=256)
+    f = _learned_filter(w, scenario.mlp_params(2), alpha)
+    m = oracle.model(w)
+    rng = np.random.default_rng(11)
+    sc = scenario.simulate(w.with_(clutter_rate=60.0), 12, steps=2)
+    Z = np.asarray(sc.meas[1], np.float32)
+    # a seeded head with a spread of logits, means and stds
+    M = len(Z)
+    head = np.column_stack([rng.normal(0, 0.7, M), rng.normal(0, 0.7, M), rng.normal(-0.3, 0.4, M),
+                            rng.normal(-0.3, 0.4, M), rng.normal(0, 1.5, M)]).astype(np.float32)
+    n_seed = [300, 0, 517]
+    xs, ws = [], []
+    for j in range(K):
+        x, wt = scenario.random_particles(rng, w, n_seed[j], spread=30.0, mass=2.0)
+        xs.append(x.astype(np.float32))
+        ws.append(wt.astype(np.float32))
+    f.set_state(xs, ws)
+    jmax = -(-w.birth_count // K)
+    plain = scenario.step_noise(13, 0, K, w.pe_cap, np.float32)
+    extra = scenario.birth_extra_noise(13, 0, K, jmax, np.float32)
+    f.predict_z(Z, noise=np.concatenate([plain, extra]), head=head)
+    xp, wp = f.get_state()
+    Zd, hd = Z.astype(np.float64), head.astype(np.float64)
+    cdf = oracle.birth_cdf(m, hd)
+    nz = plain.reshape(K, w.pe_cap, 4).astype(np.float64)
+    ex = extra.reshape(K, jmax, 4).astype(np.float64)
+    mism = 0
+    for j in range(K):
+        Jj = scenario.births_per_pe(w)[j]
+        L = n_seed[j]
+        assert len(xp[j]) == L + Jj
+        so, _ = oracle.predict(m, xs[j], ws[j], 0, nz[j])
+        np.testing.assert_allclose(xp[j][:L], so[:L], atol=1e-3)
+        bx, bw, comp = oracle.birth_learned(m, Zd, hd, alpha, Jj, nz[j][L:L + Jj], ex[j][:Jj])
+        gx, gw = xp[j][L:].astype(np.float64), wp[j][L:].astype(np.float64)
+        for b in range(Jj):
+            ok_x = np.all(np.abs(gx[b] - bx[b]) <= 1e-3 * np.maximum(1.0, np.abs(bx[b])))
+            ok_w = abs(gw[b] - bw[b]) <= 1e-4 * abs(bw[b]) + 1e-12
+            if ok_x and ok_w:
+                continue
+            # only a component choice within rounding of a CDF boundary may differ
+            uc = ex[j][b, 0]
+            uu = (uc - alpha) / (1 - alpha) if alpha < 1 else -1.0
+            near = abs(uc - alpha) < 1e-6 or (uu >= 0 and np.min(np.abs(cdf - uu)) < 1e-5)
+            assert near, (j, b, gx[b], bx[b], gw[b], bw[b], comp[b])
+            mism += 1
+    assert mism <= 2
+    f.close()
+
+
+def test_learned_step_graph_and_unload():
+    """Free-running steps with the network (graph path), the plain path back
+    after unloading, and the refusals."""
+    from paper_1503_03769_gb300 import PhdError
+    w = scenario.workload("dense_rb_100t", precision="fp32", n_targets=10, clutter_rate=50.0,
+                          particles_per_target=300, birth_count=2000, birth_steps=(1,) * 10)
+    f = _learned_filter(w, scenario.mlp_params(4), 0.2)
+    sc = scenario.simulate(w, 21, steps=6)
+    with pytest.raises(PhdError):
+        f.predict()                     # the learned birth needs the scan
+    for k in range(4):
+        f.step(sc.meas[k])
+    st = f.stats()
+    assert st["updates"] == 4
+    x, wt = f.get_state()
+    assert np.isfinite(x[0]).all() and np.isfinite(wt[0]).all()
+    f.set_birth_proposal(None)
+    f.predict()                         # plain again
+    f.close()
+    wf = scenario.workload("linear4_fp64")  # FP64 handles refuse the network
+    from paper_1503_03769_gb300 import ParticlePHD
+    g = ParticlePHD(wf, device="cuda:0")
+    with pytest.raises(PhdError):
+        g.set_birth_proposal(torch.zeros(4741, device="cuda"), 0.5)
+    g.close()
