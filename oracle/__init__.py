@@ -274,10 +274,6 @@ def fuse(per_pe: Sequence[Extraction], M: int) -> tuple:
 
 
 # ----------------------------------------------------------------------------
-# OSPA (Schuhmacher, Vo & Vo), on positions
-# ----------------------------------------------------------------------------
-
-# ----------------------------------------------------------------------------
 # Measurement-driven birth proposal (Eq. 6 with a learned p_k(.|Z_k)) and its
 # network (birth_oracle.c states the readings)
 # ----------------------------------------------------------------------------
@@ -349,6 +345,10 @@ def birth_cdf(m: _Model, head) -> np.ndarray:
     lib().orc_birth_cdf(ctypes.byref(m), _d(head), len(head), _d(out))
     return out
 
+
+# ----------------------------------------------------------------------------
+# OSPA (Schuhmacher, Vo & Vo), on positions
+# ----------------------------------------------------------------------------
 
 def ospa(X, Y, c: float = 100.0, p: float = 2.0) -> float:
     """OSPA distance between two point sets (rows are points)."""

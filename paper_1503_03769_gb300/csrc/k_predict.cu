@@ -6,7 +6,8 @@
 // with a = sigma_a (n1, n2), and take weight p_S w (proposal = transition, so
 // Eq. 5's phi/q is the survival probability).  Birth slots
 // (n_cur[j] <= i < n_cur[j] + J_j) draw position U(region) and velocity
-// N(0, s_b^2 I) and take weight nu_b / J_j (Eq. 6 with gamma = nu_b p_k).
+// N(0, s_b^2 I) and take weight nu_b / J_j (Eq. 6 with gamma = nu_b p_k);
+// with a birth network loaded the birth slots are left to k_birth_draw.
 // Survivors keep their slot index, births follow them; the predicted set is
 // written to the alternate buffers (x_alt, w_alt), the current set is read.
 // Random numbers come from the caller (noise rows n1, n2, u1, u2) or from
@@ -27,7 +28,9 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   // work items: tiles of 256 over each slice's survivors + births
-  slice_prefix(K, pref, [&](int j) { return (d.n_cur[j] + d.Jb[j] + 255) / 256; });
+  // with a birth network loaded k_birth_draw fills the birth slots
+  const bool births = !m.learned;
+  slice_prefix(K, pref, [&](int j) { return (d.n_cur[j] + (births ? d.Jb[j] : 0) + 255) / 256; });
   if (blockIdx.x == 0)
     for (int j = threadIdx.x; j < K; j += blockDim.x) d.n_pred[j] = d.n_cur[j] + d.Jb[j];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
@@ -40,7 +43,7 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
     const int j = item_pe(pref, K, item);
     const int i = (item - pref[j]) * 256 + threadIdx.x;
     const int L = d.n_cur[j];
-    if (i >= L + d.Jb[j]) continue;
+    if (i >= L + (births ? d.Jb[j] : 0)) continue;
     const long g = (long)j * m.pe_cap + i;
     R n1, n2, u1, u2;
     draw_noise<R>(m, noise, g, step, n1, n2, u1, u2);

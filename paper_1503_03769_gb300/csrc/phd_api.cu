@@ -32,6 +32,8 @@ struct phd_handle {
   // CUDA graphs of the step body (in-kernel randomness): the whole body, and
   // the same body split around the update for the stage timer
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side = nullptr;          // second capture branch (measurement-driven births)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t g_all = nullptr, g_pre = nullptr, g_upd = nullptr, g_post = nullptr;
   bool timer = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -124,6 +126,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.bhead = cv.take<float>(Mm * 5);
   t.bcomp = cv.take<float>(Mm * 8);
   t.bcdf = cv.take<float>(Mm);
+  t.bdone = cv.take<unsigned int>(1);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -286,7 +289,7 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
 }
 
 // kernels each stage launches (for the launch counter)
-constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1, kNBirth = 3;
+constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1, kNBirth = 2;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
 
 phd_status read_device_error(phd_handle* h) {
@@ -317,13 +320,13 @@ phd_status do_predict(phd_handle* h, const void* noise, bool z_staged = false, c
     if (head) {
       if (M > 0) e = cudaMemcpyAsync(h->d.bhead, head, sizeof(float) * 5 * (size_t)M, cudaMemcpyDeviceToDevice,
                                      h->stream);
+      if (e == cudaSuccess) e = phd::launch_birth_table(h->d, h->m, h->stream);
     } else {
-      e = phd::launch_birth_head(h->d, h->m, h->stream);
-      h->launches += 1;
+      e = phd::launch_birth_head(h->d, h->m, h->stream);   // builds the table too
     }
     if (e == cudaSuccess) e = phd::launch_birth_draw(h->d, h->m, static_cast<const float*>(noise), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "learned birth");
-    h->launches += kNBirth - 1;
+    h->launches += kNBirth;
   }
   h->stage = kPredicted;
   return PHD_OK;
@@ -380,10 +383,23 @@ phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
 
 // Step body with in-kernel randomness, split in three parts around the update.
 cudaError_t enq_pre(phd_handle* h, cudaStream_t s) {
-  cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, nullptr, s)
-                             : phd::launch_predict<float>(h->d, h->m, nullptr, s);
-  if (e == cudaSuccess && h->m.learned) e = phd::launch_birth_head(h->d, h->m, s);
-  if (e == cudaSuccess && h->m.learned) e = phd::launch_birth_draw(h->d, h->m, nullptr, s);
+  if (!h->m.learned)
+    return is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, nullptr, s)
+                      : phd::launch_predict<float>(h->d, h->m, nullptr, s);
+  // measurement-driven births on a second branch of the graph (network head,
+  // mixture table, draws into the birth slots), beside the survivors'
+  // prediction (k_predict leaves the birth slots alone on such a handle)
+  cudaError_t e = cudaSuccess;
+  if (!h->side) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !h->ev_fork) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !h->ev_join) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+  if (e == cudaSuccess) e = phd::launch_birth_head(h->d, h->m, h->side);
+  if (e == cudaSuccess) e = phd::launch_birth_draw(h->d, h->m, nullptr, h->side);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+  if (e == cudaSuccess) e = phd::launch_predict<float>(h->d, h->m, nullptr, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
   return e;
 }
 cudaError_t enq_upd(phd_handle* h, cudaStream_t s) {
@@ -674,6 +690,9 @@ phd_status phd_destroy(phd_handle* h) {
     cudaEventDestroy(p.second);
   }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return e == cudaSuccess ? PHD_OK : PHD_ERR_CUDA;
 }
@@ -700,6 +719,7 @@ phd_status phd_set_birth_proposal(phd_handle* h, const float* d_params, double a
   if (is_fp64(h) || h->batch_runs)
     return fail(h, PHD_ERR_STATE, "phd_set_birth_proposal: FP32 one-filter handles only");
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(h, PHD_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+  PHD_CUDA(h, phd::prepare_birth(h->m));
   PHD_CUDA(h, phd::launch_params_bf16(h->d.mlp_w, d_params, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->m.learned = 1;

@@ -143,6 +143,7 @@ struct Dev {
   float* bhead;          // [m_max][5] network output per measurement
   float* bcomp;          // [m_max][8] proposal component constants
   float* bcdf;           // [m_max] mixture CDF
+  unsigned int* bdone;   // [1] CTAs of k_birth_head finished (the last builds the table)
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
@@ -512,6 +513,8 @@ Tune default_tune(bool fp64);
 // measurement-driven birth (FP32): network head per measurement (unless the
 // head was supplied), mixture table, births drawn over the plain ones
 cudaError_t launch_birth_head(const Dev& d, const Model& m, cudaStream_t s);
+cudaError_t launch_birth_table(const Dev& d, const Model& m, cudaStream_t s);
+cudaError_t prepare_birth(const Model& m);
 cudaError_t launch_birth_draw(const Dev& d, const Model& m, const float* noise, cudaStream_t s);
 cudaError_t launch_params_bf16(void* dst, const float* src, cudaStream_t s);
 bool tune_supported(const Tune& t, bool fp64);

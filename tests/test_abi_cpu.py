@@ -63,3 +63,30 @@ def test_workspace_size_and_config_validation_without_gpu():
         assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_ERR_INVALID_ARG, field
     assert L.phd_init(None, ctypes.byref(c), None, 0, None) == phd.PHD_ERR_INVALID_ARG
     assert L.phd_status_string(phd.PHD_ERR_CAPACITY) == b"capacity exceeded"
+
+
+def test_bench_ospa_metric_matches_permutation_brute_force():
+    """bench.py scores the GPU arms with its own OSPA; check it against the
+    definition by brute force over assignments on small sets."""
+    import itertools
+    import math
+    import sys
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(0)
+    for m, n in [(0, 0), (0, 3), (2, 0), (3, 3), (2, 5), (5, 4)]:
+        X = rng.uniform(0, 150, (m, 2))
+        Y = rng.uniform(0, 150, (n, 2))
+        c, p = 100.0, 2.0
+        if m == 0 and n == 0:
+            want = 0.0
+        elif m == 0 or n == 0:
+            want = c
+        else:
+            A, B = (X, Y) if m <= n else (Y, X)
+            a, b = len(A), len(B)
+            best = min(sum(min(c, float(np.linalg.norm(A[i] - B[perm[i]]))) ** p for i in range(a))
+                       for perm in itertools.permutations(range(b), a))
+            want = ((best + c ** p * (b - a)) / b) ** (1 / p)
+        assert math.isclose(bench.ospa_metric(X, Y, c, p), want, rel_tol=1e-12, abs_tol=1e-12)
