@@ -8,7 +8,7 @@
 //   rank_p < LT_j.  O(M^2) comparisons per PE on M <= 4096 values in shared
 //   memory, made on the FP64 values' bit patterns as unsigned integers (same
 //   order, integer instructions).
-// k_selsum (pass 3, selected labels only): per label the sums of
+// k_selsum (pass 3, selected labels only; pass-1 tiles): per label the sums of
 //   e w, e w (x - r_x), e w vx, e w (y - r_y), e w vy over the PE's particles,
 //   with e = 2^-q the unnormalised likelihood and r the measurement's
 //   Cartesian point; the offsets keep the FP32 sums small.  Eq. 18's
@@ -24,7 +24,7 @@ namespace phd {
 
 template <class R>
 __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
   const int j = blockIdx.x;
@@ -74,78 +74,112 @@ __device__ __forceinline__ void meas_point(const Model& m, V2<R> z, R& rx, R& ry
   }
 }
 
-template <class R>
+// qform with the sensor model fixed at compile time (same arithmetic).
+template <class R, int RB>
+__device__ __forceinline__ R qform_s(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
+  const R d0 = z0 - h0;
+  R d1 = z1 - h1;
+  if (RB) {
+    d1 = d1 - h1lo;
+    const R a = fabs(d1);
+    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
+  }
+  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
+}
+
+// Pass 3: a work item is a tile of c_tile particles of one slice (the pass-1
+// tile), staged as packed geometry + weight and state; groups of nsplit
+// consecutive lanes own kSelLB selected labels each (one pair of shared loads
+// feeds kSelLB pairs) and split the tile; FP32 sums of offsets from each
+// label's point, reduced by shuffles within the group, one FP64 partial per
+// (tile, label).
+constexpr int kSelLB = 2;
+
+template <class R, int RB>
 __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int pref[kMaxPE + 1];
-  __shared__ P4<R> sp[kTile];
-  __shared__ St4<R> sx[kTile];
+  const int TP = m.tune.c_tile;
+  P4<R>* sp = reinterpret_cast<P4<R>*>(smem_raw);   // [TP]
+  St4<R>* sx = reinterpret_cast<St4<R>*>(sp + TP);  // [TP]
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref);
+  item_prefix(d.n_pred, K, pref, TP);
   const int total = pref[K];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const Lik<R> L = make_lik<R>(m);
-
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int ns = d.nsel[j];
     if (ns <= 0) continue;   // uniform over the block
     const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
     const int tile = item - pref[j];
-    const long base = (long)j * m.pe_cap + (long)tile * kTile;
-    const int cnt = min(kTile, d.n_pred[j] - tile * kTile);
+    const long base = (long)j * m.pe_cap + (long)tile * TP;
+    const int cnt = min(TP, d.n_pred[j] - tile * TP);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTile; i += kThreads) {
+    for (int i = threadIdx.x; i < TP; i += kThreads) {
       P4<R> q = {0, 0, 0, 0};
-      St4<R> s = {0, 0, 0, 0};
+      St4<R> st = {0, 0, 0, 0};
       if (i < cnt) {
-        s = x[base + i];
-        const H3<R> h = meas_h<R>(m, s, tab);
+        st = x[base + i];
+        const H3<R> h = meas_h<R>(m, st, tab);
         q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
       }
       sp[i] = q;
-      sx[i] = s;
+      sx[i] = st;
     }
     __syncthreads();
-    // groups of nsplit consecutive lanes per label; FP32 sums of offsets from
-    // the label's point, reduced by shuffles within the group
+    const int ng = (ns + kSelLB - 1) / kSelLB;   // label groups
     int nsplit = 1;
-    while (nsplit * 2 <= 32 && nsplit * 2 * ns <= kThreads) nsplit *= 2;
-    const int mper = kThreads / nsplit;
+    while (nsplit * 2 <= 32 && nsplit * 2 * ng <= kThreads) nsplit *= 2;
+    const int gpr = kThreads / nsplit;           // label groups per round
     const int rl = threadIdx.x / nsplit, split = threadIdx.x % nsplit;
-    for (int r0 = 0; r0 < ns; r0 += mper) {
-      const int r = r0 + rl;
-      R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-      R px = 0, py = 0;
-      if (r < ns) {
-        const V2<R> z = Z[d.sel[j * m.m_max + r]];
-        meas_point<R>(m, z, px, py);
+    for (int g0 = 0; g0 < ng; g0 += gpr) {
+      const int g = g0 + rl;
+      R s[kSelLB][5];
+      R z0[kSelLB], z1[kSelLB], px[kSelLB], py[kSelLB];
+#pragma unroll
+      for (int k = 0; k < kSelLB; ++k) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) s[k][c] = 0;
+        const int r = g * kSelLB + k;
+        V2<R> z = {0, 0};
+        if (g < ng && r < ns) z = Z[d.sel[j * m.m_max + r]];
+        z0[k] = z.a;
+        z1[k] = z.b;
+        meas_point<R>(m, z, px[k], py[k]);
+      }
+      if (g < ng) {
         for (int i = split; i < cnt; i += nsplit) {
           const P4<R> q = sp[i];
-          const R ew = exp2_neg(qform<R>(L, z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
           const St4<R> st = sx[i];
-          s0 += ew;
-          s1 = fma(ew, st.x - px, s1);
-          s2 = fma(ew, st.vx, s2);
-          s3 = fma(ew, st.y - py, s3);
-          s4 = fma(ew, st.vy, s4);
+#pragma unroll
+          for (int k = 0; k < kSelLB; ++k) {
+            const R ew = exp2_neg(qform_s<R, RB>(L, z0[k], z1[k], q.h0, q.h1, q.h1lo)) * q.w;
+            s[k][0] += ew;
+            s[k][1] = fma(ew, st.x - px[k], s[k][1]);
+            s[k][2] = fma(ew, st.vx, s[k][2]);
+            s[k][3] = fma(ew, st.y - py[k], s[k][3]);
+            s[k][4] = fma(ew, st.vy, s[k][4]);
+          }
         }
       }
-      for (int o = nsplit >> 1; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o, nsplit);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o, nsplit);
-        s2 += __shfl_down_sync(0xffffffffu, s2, o, nsplit);
-        s3 += __shfl_down_sync(0xffffffffu, s3, o, nsplit);
-        s4 += __shfl_down_sync(0xffffffffu, s4, o, nsplit);
-      }
-      if (split == 0 && r < ns) {
-        double* o = d.spart + ((long)item * m.m_max + r) * 5;
-        o[0] = (double)s0;
-        o[1] = (double)s1;
-        o[2] = (double)s2;
-        o[3] = (double)s3;
-        o[4] = (double)s4;
+#pragma unroll
+      for (int k = 0; k < kSelLB; ++k)
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          for (int o = nsplit >> 1; o > 0; o >>= 1) s[k][c] += __shfl_down_sync(0xffffffffu, s[k][c], o, nsplit);
+      if (split == 0 && g < ng) {
+#pragma unroll
+        for (int k = 0; k < kSelLB; ++k) {
+          const int r = g * kSelLB + k;
+          if (r < ns) {
+            double* o = d.spart + ((long)item * m.m_max + r) * 5;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) o[c] = (double)s[k][c];
+          }
+        }
       }
     }
   }
@@ -158,7 +192,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
-  item_prefix(d.n_pred, K, pref);
+  item_prefix(d.n_pred, K, pref, m.tune.c_tile);
   St4<R>* est = static_cast<St4<R>*>(d.est_local);
   const int lane = threadIdx.x & 31;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
@@ -322,7 +356,13 @@ template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
   k_select<R><<<dim3(m.K, (m.m_max + 63) / 64), 256, sizeof(unsigned long long) * (size_t)m.m_max, s>>>(d, m);
-  k_selsum<R><<<grid_items(m), kThreads, 0, s>>>(d, m);
+  {
+    const long items = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
+    const int g = (int)(items < 152L * 8 ? (items > 0 ? items : 1) : 152L * 8);
+    const size_t smem = (sizeof(P4<R>) + sizeof(St4<R>)) * (size_t)m.tune.c_tile;
+    if (m.meas_model) k_selsum<R, 1><<<g, kThreads, smem, s>>>(d, m);
+    else k_selsum<R, 0><<<g, kThreads, smem, s>>>(d, m);
+  }
   long warps = (long)m.K * m.m_max;
   int b = (int)((warps + 7) / 8);
   if (b > 152 * 8) b = 152 * 8;
@@ -336,4 +376,16 @@ template cudaError_t launch_batch_out<double>(const Dev&, const Model&, double*,
 template cudaError_t launch_extract<float>(const Dev&, const Model&, float*, int*, int, int*, cudaStream_t);
 template cudaError_t launch_extract<double>(const Dev&, const Model&, double*, int*, int, int*, cudaStream_t);
 
+}  // namespace phd
+
+namespace phd {
+template <class R>
+cudaError_t prepare_extract() {
+  const int sm = (int)((sizeof(P4<R>) + sizeof(St4<R>)) * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_selsum<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selsum<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+template cudaError_t prepare_extract<float>();
+template cudaError_t prepare_extract<double>();
 }  // namespace phd

@@ -548,7 +548,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     }
     const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
     const unsigned long long Qn = np > 0 ? Q[np - 1] : 0ull;
-    for (int i = tid; i < np; i += T) cend[i] = offspring_end(Q[i], Qn, (unsigned long long)Lc, U);
+    __shared__ Recip rq_s;
+    if (tid == 0) rq_s = make_recip(Qn);
+    __syncthreads();
+    const Recip rq = rq_s;
+    for (int i = tid; i < np; i += T) cend[i] = offspring_end(Q[i], Qn, (unsigned long long)Lc, U, rq);
     __syncthreads();
     const R wnew = bW;
     for (int t = tid; t < Lc; t += T) {

@@ -12,7 +12,8 @@
 //               depend on the summation order.
 //   k_rs_count: Q_i = chunk offset + in-chunk prefix; c_i = #{t : T_t < Q_i}
 //               with T_t = floor((t 2^32 + U) Q_n / (L 2^32)), in closed form
-//               with 128-bit integers: V = floor((Q_i L 2^32 - 1) / Q_n),
+//               with 128-bit integers: V = floor((Q_i L 2^32 - 1) / Q_n) (one
+//               multiply by the reciprocal of Q_n that k_rs_off prepares),
 //               c_i = min(L, V < U ? 0 : ((V - U) >> 32) + 1).  Child t's
 //               parent is then the least i with c_i > t, i.e. the least i
 //               with Q_i > T_t.
@@ -86,7 +87,12 @@ __global__ void __launch_bounds__(1024) k_rs_off(Dev d, Model m) {
     if (c < pref[j + 1]) d.coff[c] = carry + incl - v;
     carry += tot;
   }
-  if (threadIdx.x == 0) d.rs_Qn[j] = carry;
+  if (threadIdx.x == 0) {
+    d.rs_Qn[j] = carry;
+    const Recip r = make_recip(carry);
+    d.rs_rcp[2 * j] = r.d;
+    d.rs_rcp[2 * j + 1] = r.v;
+  }
 }
 
 template <class R>
@@ -105,7 +111,9 @@ __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint3
     const unsigned long long Qi = d.coff[c] + block_scan_u64<R>(q, wt, nullptr);
     if (live) {
       const uint32_t U = u ? u[j] : philox_u32(m, (uint32_t)j, st, kTagResample);
-      d.child_end[g] = offspring_end(Qi, d.rs_Qn[j], (unsigned long long)d.rs_L[j], U);
+      const unsigned long long Qn = d.rs_Qn[j];
+      const Recip rq{d.rs_rcp[2 * j], d.rs_rcp[2 * j + 1], Qn ? __clzll((long long)Qn) : 0};
+      d.child_end[g] = offspring_end(Qi, Qn, (unsigned long long)d.rs_L[j], U, rq);
     }
   }
 }

@@ -420,6 +420,7 @@ cudaError_t prepare_kernels(const Model& m) {
   const size_t sm = sizeof(Z4<R>) * (size_t)m.m_max;
   cudaError_t e = prepare_rowsum<R, 0>(sm);
   if (e == cudaSuccess) e = prepare_rowsum<R, 1>(sm);
+  if (e == cudaSuccess) e = prepare_extract<R>();
   return e;
 }
 

@@ -114,6 +114,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.csum = cv.take<unsigned long long>(chunks);
   t.coff = cv.take<unsigned long long>(chunks);
   t.rs_Qn = cv.take<unsigned long long>(K);
+  t.rs_rcp = cv.take<unsigned long long>(2 * K);
   t.child_end = cv.take<int>(K * P);
   t.parent = cv.take<int>(K * P);
   t.xslots = cv.take<int>(K * P);

@@ -118,6 +118,7 @@ struct Dev {
   unsigned long long* csum;  // [K*ceil(pe_cap/kChunk)] CDF chunk totals
   unsigned long long* coff;  // same: exclusive chunk offsets
   unsigned long long* rs_Qn; // [K] CDF total
+  unsigned long long* rs_rcp;  // [K][2] normalised CDF total and its reciprocal (make_recip)
   int* child_end;        // [K*pe_cap]
   int* parent;           // [K*pe_cap]
   int* xslots;           // [K][pe_cap] exchange slots
@@ -453,14 +454,62 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
   return (unsigned long long)__double_as_longlong(v);
 }
 
+// Division of a 128-bit dividend by a fixed 64-bit divisor through a
+// precomputed reciprocal of the normalised divisor (Moller & Granlund,
+// "Improved division by invariant integers", IEEE Trans. Computers 60(2),
+// 2011, Algorithm 4): one 64 x 64 -> 128-bit product and at most two
+// corrections per quotient instead of a 128-bit division.
+struct Recip {
+  unsigned long long d;   // divisor shifted left until its top bit is set
+  unsigned long long v;   // floor((2^128 - 1) / d) - 2^64
+  int s;                  // the shift
+};
+
+__device__ __forceinline__ Recip make_recip(unsigned long long d) {
+  Recip r{0ull, 0ull, 0};
+  if (d == 0ull) return r;
+  r.s = __clzll((long long)d);
+  r.d = d << r.s;
+  const unsigned __int128 all = ~(unsigned __int128)0;
+  r.v = (unsigned long long)(all / r.d);   // the quotient is 2^64 + v; its low word is v
+  return r;
+}
+
+// floor((u1 2^64 + u0) / d) for a normalised dividend (u1 < r.d).
+__device__ __forceinline__ unsigned long long div_2by1(unsigned long long u1, unsigned long long u0, const Recip& r) {
+  unsigned long long q0 = r.v * u1;
+  unsigned long long q1 = __umul64hi(r.v, u1);
+  const unsigned long long t = q0 + u0;
+  q1 += u1 + 1ull + (t < q0 ? 1ull : 0ull);
+  q0 = t;
+  unsigned long long rem = u0 - q1 * r.d;
+  if (rem > q0) {
+    q1 -= 1ull;
+    rem += r.d;
+  }
+  if (rem >= r.d) q1 += 1ull;
+  return q1;
+}
+
 // Systematic resampling: number of children whose pointer falls below Q_i,
-// c = #{t : floor((t 2^32 + U) Q_n / (L 2^32)) < Q_i}, with 128-bit integers.
+// c = #{t : floor((t 2^32 + U) Q_n / (L 2^32)) < Q_i}, with 128-bit integers:
+// V = floor((Q_i L 2^32 - 1) / Q_n), c = min(L, V < U ? 0 : ((V - U) >> 32) + 1).
+// rq is make_recip(Q_n).
 __device__ __forceinline__ int offspring_end(unsigned long long Qi, unsigned long long Qn, unsigned long long L,
-                                             uint32_t U) {
+                                             uint32_t U, const Recip& rq) {
   if (L == 0 || Qn == 0) return 0;
-  const unsigned __int128 X = ((unsigned __int128)Qi * L) << 32;
-  if (X == 0) return 0;
-  const unsigned long long V = (unsigned long long)((X - 1) / Qn);
+  // X = Q_i L 2^32 as (hi, lo); Q_i < 2^53 and L < 2^31, so X < 2^116
+  const unsigned long long ph = __umul64hi(Qi, L), pl = Qi * L;
+  unsigned long long hi = (ph << 32) | (pl >> 32), lo = pl << 32;
+  if ((hi | lo) == 0ull) return 0;
+  if (lo == 0ull) hi -= 1ull;   // X - 1
+  lo -= 1ull;
+  // normalise: (X - 1) 2^s < Q_n 2^s 2^64 since L 2^32 < 2^64
+  if (rq.s > 0) {
+    hi = (hi << rq.s) | (lo >> (64 - rq.s));
+    lo <<= rq.s;
+  }
+  const unsigned long long V = div_2by1(hi, lo, rq);
   const unsigned long long cc = V < (unsigned long long)U ? 0ull : ((V - U) >> 32) + 1ull;
   return (int)(cc < L ? cc : L);
 }
@@ -524,6 +573,7 @@ template <class R> cudaError_t launch_resample(const Dev& d, const Model& m, con
                                                const uint32_t* xu, cudaStream_t s);
 cudaError_t launch_advance_step(const Dev& d, cudaStream_t s);
 template <class R> cudaError_t prepare_kernels(const Model& m);
+template <class R> cudaError_t prepare_extract();
 cudaError_t prepare_exchange(const Model& m);
 template <class R> bool fused_eligible(const Model& m, int device);
 void fill_anchor_table(Anchor* tab);
