@@ -118,10 +118,13 @@ __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint3
   }
 }
 
-// Scatter by parent: particle i of PE j has children child_end[i-1] ..
-// child_end[i]-1 (parents in order, children in order), which get its
-// predicted state and the weight N^j / L_j.  Work items: tiles of 256 over
-// each slice's predicted particles.
+// Scatter by parent, a warp per 32 consecutive parents: parent i of PE j has
+// children child_end[i-1] .. child_end[i]-1 (parents in order, children in
+// order); the warp writes its parents' children as one contiguous range,
+// lane by lane (coalesced), each child finding its parent among the warp's
+// 32 by a shuffle search and taking its predicted state (shuffled from the
+// parent's lane) and the weight N^j / L_j.  Work items: 256-particle tiles
+// of each slice.
 template <class R>
 __global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
   __shared__ int pref[kMaxPE + 1];
@@ -132,22 +135,38 @@ __global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
   const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
   St4<R>* x = static_cast<St4<R>*>(d.x);
   R* w = static_cast<R*>(d.w);
+  const int lane = threadIdx.x & 31;
   for (int item = blockIdx.x; item < pref[K]; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
-    const int i = (item - pref[j]) * kTile + threadIdx.x;
+    const int n = d.n_pred[j];
     const int L = d.rs_L[j];
-    if (i >= d.n_pred[j] || L == 0) continue;
+    if (L == 0) continue;   // uniform over the block
+    const int wb = (item - pref[j]) * kTile + (threadIdx.x & ~31);   // the warp's first parent
+    if (wb >= n) continue;   // uniform over the warp
     const long base = (long)j * m.pe_cap;
-    const long g = base + i;
-    const int t1 = d.child_end[g];
-    const int t0 = i > 0 ? d.child_end[g - 1] : 0;
-    if (t1 <= t0) continue;
-    const St4<R> s = xp[g];
-    const R wn = (R)(d.rs_mass[j] / (double)L);
-    for (int t = t0; t < t1; ++t) {
-      x[base + t] = s;
-      w[base + t] = wn;
-      d.parent[base + t] = i;
+    const int i = wb + lane;
+    const bool live = i < n;
+    const int ce = d.child_end[base + (live ? i : n - 1)];
+    const int c0 = __shfl_sync(0xffffffffu, wb > 0 ? d.child_end[base + wb - 1] : 0, 0);
+    const int c1 = __shfl_sync(0xffffffffu, ce, 31);
+    const St4<R> s = live ? xp[base + i] : St4<R>{0, 0, 0, 0};
+    const R wn = (R)d.rs_wn[j];
+    for (int t0 = c0; t0 < c1; t0 += 32) {
+      const int t = t0 + lane;
+      // smallest lane k with child_end > t (lanes past the slice repeat the last end)
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, ce, lo + step - 1);
+        if (e <= t) lo += step;
+      }
+      const R sx = __shfl_sync(0xffffffffu, s.x, lo), svx = __shfl_sync(0xffffffffu, s.vx, lo);
+      const R sy = __shfl_sync(0xffffffffu, s.y, lo), svy = __shfl_sync(0xffffffffu, s.vy, lo);
+      if (t < c1) {
+        x[base + t] = St4<R>{sx, svx, sy, svy};
+        w[base + t] = wn;
+        d.parent[base + t] = wb + lo;
+      }
     }
   }
 }

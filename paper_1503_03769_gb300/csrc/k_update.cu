@@ -194,18 +194,39 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0) {
+    // counters: one slice per thread (K <= blockDim), warp sums, then thread 0
+    __shared__ unsigned long long cs[3][8];
     unsigned long long n = 0, pairs = 0, meas = 0;
-    for (int j = 0; j < K; ++j) {
-      const unsigned long long Mj = (unsigned long long)slice_M(d, j);
-      n += (unsigned long long)d.n_pred[j];
-      pairs += (unsigned long long)d.n_pred[j] * Mj;
-      meas += Mj;
+    if ((int)threadIdx.x < K) {
+      const unsigned long long Mj = (unsigned long long)slice_M(d, threadIdx.x);
+      n = (unsigned long long)d.n_pred[threadIdx.x];
+      pairs = n * Mj;
+      meas = Mj;
     }
-    d.stats[0] += pairs;
-    d.stats[1] += n;
-    d.stats[2] += d.zshared ? (unsigned long long)*d.M : meas;
-    d.stats[3] += 1ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      n += __shfl_down_sync(0xffffffffu, n, o);
+      pairs += __shfl_down_sync(0xffffffffu, pairs, o);
+      meas += __shfl_down_sync(0xffffffffu, meas, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      cs[0][threadIdx.x >> 5] = pairs;
+      cs[1][threadIdx.x >> 5] = n;
+      cs[2][threadIdx.x >> 5] = meas;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long a = 0, b = 0, c = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        a += cs[0][k];
+        b += cs[1][k];
+        c += cs[2][k];
+      }
+      d.stats[0] += a;
+      d.stats[1] += b;
+      d.stats[2] += d.zshared ? (unsigned long long)*d.M : c;
+      d.stats[3] += 1ull;
+    }
   }
 }
 
@@ -351,6 +372,7 @@ __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
     int L, sc;
     resample_plan(d.rho[j], d.lmax[j], d.n_pred[j], t, tm, L, sc);
     d.rs_mass[j] = t;
+    d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
     d.rs_s[j] = sc;
     d.rs_L[j] = L;
   }

@@ -109,6 +109,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.est_local = cv.take<char>(K * Mm, 4 * rs);
   t.out_count = cv.take<int>(1);
   t.rs_mass = cv.take<double>(K);
+  t.rs_wn = cv.take<double>(K);
   t.rs_s = cv.take<int>(K);
   t.rs_L = cv.take<int>(K);
   t.csum = cv.take<unsigned long long>(chunks);

@@ -113,6 +113,7 @@ struct Dev {
   void* est_local;       // St4<R> [K][m_max] local estimates (selection order)
   int* out_count;        // [1] fused estimate count
   double* rs_mass;       // [K] mass before resampling
+  double* rs_wn;         // [K] weight of a resampled particle, N^j / L_j
   int* rs_s;             // [K] CDF scale exponent
   int* rs_L;             // [K] resample counts
   unsigned long long* csum;  // [K*ceil(pe_cap/kChunk)] CDF chunk totals
