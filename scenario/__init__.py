@@ -115,7 +115,17 @@ def workload(name: str, **overrides) -> Workload:
     }
     if name not in base:
         raise KeyError(f"unknown workload {name!r}; known: {sorted(base)}")
-    return _derive_caps(base[name].with_(**overrides))
+    w = base[name].with_(**overrides)
+    if name != "linear4_fp64" and "birth_mass" not in overrides:
+        w = w.with_(birth_mass=matched_birth_mass(w))
+    return _derive_caps(w)
+
+
+def matched_birth_mass(w: Workload) -> float:
+    """Expected truth births per scan of a workload whose targets appear at
+    seeded scans spread over the first 40 % of the run (the birth intensity
+    nu_b the filter is given for it)."""
+    return w.n_targets / (0.4 * w.steps)
 
 
 def batch_workloads(seed: int = 1000, runs: int = 256, steps: int = 60) -> List[Workload]:
@@ -130,9 +140,10 @@ def batch_workloads(seed: int = 1000, runs: int = 256, steps: int = 60) -> List[
         nt = int(rng.integers(1, 51))
         lam = float(rng.uniform(5.0, 200.0))
         rho = int(rng.integers(256, 4097))
-        out.append(Workload(name=f"batch_run{r}", meas_model=LINEAR, sigma_z=(10.0, 10.0),
-                            clutter_rate=lam, n_targets=nt, particles_per_target=rho,
-                            birth_count=rho, steps=steps, precision="fp32"))
+        wr = Workload(name=f"batch_run{r}", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+                      clutter_rate=lam, n_targets=nt, particles_per_target=rho,
+                      birth_count=rho, steps=steps, precision="fp32")
+        out.append(wr.with_(birth_mass=matched_birth_mass(wr)))
     caps = []
     for w in out:
         m_exp = w.clutter_rate + w.n_targets
