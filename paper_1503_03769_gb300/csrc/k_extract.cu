@@ -74,19 +74,6 @@ __device__ __forceinline__ void meas_point(const Model& m, V2<R> z, R& rx, R& ry
   }
 }
 
-// qform with the sensor model fixed at compile time (same arithmetic).
-template <class R, int RB>
-__device__ __forceinline__ R qform_s(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
-  const R d0 = z0 - h0;
-  R d1 = z1 - h1;
-  if (RB) {
-    d1 = d1 - h1lo;
-    const R a = fabs(d1);
-    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
-  }
-  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
-}
-
 // Pass 3: a work item is a tile of c_tile particles of one slice (the pass-1
 // tile), staged as packed geometry + weight and state; groups of nsplit
 // consecutive lanes own kSelLB selected labels each (one pair of shared loads
@@ -108,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const Lik<R> L = make_lik<R>(m);
+  const PairQ<R, RB> Q(m);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int ns = d.nsel[j];
@@ -156,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
           const St4<R> st = sx[i];
 #pragma unroll
           for (int k = 0; k < kSelLB; ++k) {
-            const R ew = exp2_neg(qform_s<R, RB>(L, z0[k], z1[k], q.h0, q.h1, q.h1lo)) * q.w;
+            const R ew = exp2_neg(Q(z0[k], z1[k], q.h0, q.h1, q.h1lo)) * q.w;
             s[k][0] += ew;
             s[k][1] = fma(ew, st.x - px[k], s[k][1]);
             s[k][2] = fma(ew, st.vx, s[k][2]);

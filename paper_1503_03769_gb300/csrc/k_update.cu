@@ -32,20 +32,6 @@
 
 namespace phd {
 
-// Exponent q of the likelihood with the sensor model fixed at compile time
-// (same arithmetic as qform).
-template <class R, int RB>
-__device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
-  const R d0 = z0 - h0;
-  R d1 = z1 - h1;
-  if (RB) {
-    d1 = d1 - h1lo;
-    const R a = fabs(d1);
-    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
-  }
-  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
-}
-
 template <class R, int RB, int MB>
 __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -64,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const Lik<R> L = make_lik<R>(m);
+  const PairQ<R, RB> Q(m);
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(ipref, K, item);
@@ -112,16 +98,16 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
         const P4<R> qa = sp[i], qb = sp[i + S];
 #pragma unroll
         for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
 #pragma unroll
         for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
+          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
       }
       if (i < cnt) {
         const P4<R> qa = sp[i];
 #pragma unroll
         for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(qform_t<R, RB>(L, z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
       }
 #pragma unroll
       for (int k = 0; k < MB; ++k) red[sidx * GM + g + k * G] = acc[k];
@@ -250,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   R* __restrict__ wu = static_cast<R*>(d.wu);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const Lik<R> L = make_lik<R>(m);
+  const PairQ<R, RB> Q(m);
   const R miss = consts<R>(m).miss;
   const int il = threadIdx.x / G, g = threadIdx.x % G;
   int staged = -1;
@@ -291,16 +277,16 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       const Z4<R> za = zs[p], zb = zs[p + G];
 #pragma unroll
       for (int k = 0; k < PB; ++k)
-        a0[k] = fma(exp2_neg(qform_t<R, RB>(L, za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+        a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
 #pragma unroll
       for (int k = 0; k < PB; ++k)
-        a1[k] = fma(exp2_neg(qform_t<R, RB>(L, zb.z0, zb.z1, h0[k], h1[k], hl[k])), zb.g, a1[k]);
+        a1[k] = fma(exp2_neg(Q(zb.z0, zb.z1, h0[k], h1[k], hl[k])), zb.g, a1[k]);
     }
     if (p < M) {
       const Z4<R> za = zs[p];
 #pragma unroll
       for (int k = 0; k < PB; ++k)
-        a0[k] = fma(exp2_neg(qform_t<R, RB>(L, za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+        a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
     }
     R sv = 0, mv = 0;
 #pragma unroll

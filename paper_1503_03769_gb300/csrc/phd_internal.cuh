@@ -304,6 +304,85 @@ __device__ __forceinline__ R qform(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1
   return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
 }
 
+// Exponent q of the likelihood with the sensor model fixed at compile time
+// (same arithmetic as qform).
+template <class R, int RB>
+__device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
+  const R d0 = z0 - h0;
+  R d1 = z1 - h1;
+  if (RB) {
+    d1 = d1 - h1lo;
+    const R a = fabs(d1);
+    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
+  }
+  return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
+}
+
+// FP32 pair exponent with packed two-lane instructions (f32x2, sm_100 and
+// later): (z0 - h0, z1 - h1) in one subtract and (a0 d0, a1 d1) in one
+// multiply, a = sqrt(b); q = (a0 d0)^2 + (a1 d1)^2.  Same subtract-then-scale
+// order as qform (the bearing's low word and wrap on the second lane).
+struct LikP {
+  unsigned long long a01;   // packed (a0, a1)
+  float per_hi, per_lo;
+};
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ LikP make_likp(const Model& m) {
+  const double two_pi = 6.283185307179586476925286766559;
+  LikP L;
+  L.a01 = f2_pack((float)m.a0, (float)m.a1);
+  L.per_hi = (float)two_pi;
+  L.per_lo = (float)(two_pi - (double)L.per_hi);
+  return L;
+}
+template <int RB>
+__device__ __forceinline__ float qform_p(const LikP& L, unsigned long long z, unsigned long long h, float h1lo) {
+  float d0, d1;
+  f2_unpack(f2_sub(z, h), d0, d1);
+  if (RB) {
+    d1 = d1 - h1lo;
+    const float a = fabsf(d1);
+    d1 = fminf(a, (L.per_hi - a) + L.per_lo);
+  }
+  float e0, e1;
+  f2_unpack(f2_mul(f2_pack(d0, d1), L.a01), e0, e1);
+  return fmaf(e0, e0, e1 * e1);
+}
+
+// Pair exponent in the kernels' precision: packed FP32, or plain FP64.
+template <class R, int RB> struct PairQ;
+template <int RB> struct PairQ<float, RB> {
+  LikP L;
+  __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_likp(m)) {}
+  __device__ __forceinline__ float operator()(float z0, float z1, float h0, float h1, float h1lo) const {
+    return qform_p<RB>(L, f2_pack(z0, z1), f2_pack(h0, h1), h1lo);
+  }
+};
+template <int RB> struct PairQ<double, RB> {
+  Lik<double> L;
+  __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_lik<double>(m)) {}
+  __device__ __forceinline__ double operator()(double z0, double z1, double h0, double h1, double h1lo) const {
+    return qform_t<double, RB>(L, z0, z1, h0, h1, h1lo);
+  }
+};
+
 // Work-item decode for the pair kernels: item -> (PE, particle tile), tiles
 // of kTile over each PE's count.  pref gets K+1 entries in shared memory; the
 // block needs at least kMaxPE threads (tile counts are scanned in parallel).
