@@ -70,6 +70,7 @@ __device__ __forceinline__ float3 birth_feature(const Model& m, const V2<float>*
 __device__ void birth_table_block(const Dev& d, const Model& m);
 
 __global__ void __launch_bounds__(256) k_birth_head(Dev d, Model m) {
+  pdl_enter();
   __shared__ float W[kWarpImage];
   stage_params_warp(W, static_cast<const __nv_bfloat16*>(d.mlp_w));
   __syncthreads();
@@ -166,7 +167,8 @@ __device__ void birth_table_block(const Dev& d, const Model& m) {
 }
 
 // Table only (the network head was supplied by the caller).
-__global__ void __launch_bounds__(kTableThreads) k_birth_table(Dev d, Model m) { birth_table_block(d, m); }
+__global__ void __launch_bounds__(kTableThreads) k_birth_table(Dev d, Model m) {
+  pdl_enter(); birth_table_block(d, m); }
 
 static size_t birth_draw_smem(const Model& m) { return (size_t)m.m_max * (2 * sizeof(float4) + sizeof(float)); }
 
@@ -176,6 +178,7 @@ static size_t birth_draw_smem(const Model& m) { return (size_t)m.m_max * (2 * si
 constexpr int kDrawLanes = 8;
 
 __global__ void __launch_bounds__(256) k_birth_draw(Dev d, Model m, const float* __restrict__ noise) {
+  pdl_enter();
   const int K = m.K;
   const int M = *d.M;
   const float alpha = M > 0 ? m.f_alpha : 1.0f;
@@ -294,12 +297,12 @@ __global__ void k_params_bf16(__nv_bfloat16* __restrict__ dst, const float* __re
 cudaError_t launch_birth_head(const Dev& d, const Model& m, cudaStream_t s) {
   int blocks = (m.m_max + 7) / 8;   // a warp per measurement slot
   if (blocks > 152 * 2) blocks = 152 * 2;
-  k_birth_head<<<blocks, 256, 0, s>>>(d, m);
+  launch_k(k_birth_head, dim3(blocks), dim3(256), 0, s, d, m);
   return cudaGetLastError();
 }
 
 cudaError_t launch_birth_table(const Dev& d, const Model& m, cudaStream_t s) {
-  k_birth_table<<<1, kTableThreads, 0, s>>>(d, m);
+  launch_k(k_birth_table, dim3(1), dim3(kTableThreads), 0, s, d, m);
   return cudaGetLastError();
 }
 
@@ -308,7 +311,7 @@ cudaError_t launch_birth_draw(const Dev& d, const Model& m, const float* noise, 
   int blocks = (int)((items + 255) / 256);
   if (blocks > 152 * 4) blocks = 152 * 4;
   if (blocks < 1) blocks = 1;
-  k_birth_draw<<<blocks, 256, birth_draw_smem(m), s>>>(d, m, noise);
+  launch_k(k_birth_draw, dim3(blocks), dim3(256), birth_draw_smem(m), s, d, m, noise);
   return cudaGetLastError();
 }
 

@@ -16,14 +16,17 @@
 //   factor p_D cnorm / (kappa + C_p), which cancels.
 // k_est_local: per (PE, rank) FP64 reduction of the pass-3 partials to zeta.
 // k_fuse (one CTA): for every label the PEs that took it vote; a label is
-//   valid with more than K/2 votes, and its state is the FP64 mean of the
-//   voters' local states in PE order.  Output in ascending label order.
+//   valid with more than K/2 votes, and its state is the mean of the voters'
+//   local states in PE order (FP32 kernels: offsets from the first voter
+//   summed and scaled in FP32; FP64 kernels: FP64 sums).  Output in
+//   ascending label order.
 #include "phd_internal.cuh"
 
 namespace phd {
 
 template <class R>
 __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
+  pdl_enter();
   extern __shared__ __align__(32) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
@@ -84,6 +87,7 @@ constexpr int kSelLB = 2;
 
 template <class R, int RB>
 __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
+  pdl_enter();
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int pref[kMaxPE + 1];
   const int TP = m.tune.c_tile;
@@ -177,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
 // zeta = r + S / C (Eq. 18).
 template <class R>
 __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref, m.tune.c_tile);
@@ -210,10 +215,19 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
       meas_point<R>(m, slice_Z<R>(d, j)[p], px, py);
       St4<R> o;
       if (a0 > 0.0) {
-        o.x = (R)((double)px + a1 / a0);
-        o.vx = (R)(a2 / a0);
-        o.y = (R)((double)py + a3 / a0);
-        o.vy = (R)(a4 / a0);
+        if constexpr (sizeof(R) == 4) {
+          // the offsets from the label's point are small: FP32 suffices
+          const float inv = 1.0f / (float)a0;
+          o.x = px + (float)a1 * inv;
+          o.vx = (float)a2 * inv;
+          o.y = py + (float)a3 * inv;
+          o.vy = (float)a4 * inv;
+        } else {
+          o.x = (R)((double)px + a1 / a0);
+          o.vx = (R)(a2 / a0);
+          o.y = (R)((double)py + a3 / a0);
+          o.vy = (R)(a4 / a0);
+        }
       } else {
         o = St4<R>{px, (R)0, py, (R)0};
       }
@@ -225,6 +239,7 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
 template <class R>
 __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, int* out_labels, int cap,
                                                int* d_count) {
+  pdl_enter();
   __shared__ int wsum[32];
   __shared__ int carry_s;
   const int K = m.K;
@@ -260,18 +275,42 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
     const int carry = carry_s;
     const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
     if (valid && idx < cap) {
-      double a[4] = {0, 0, 0, 0};
-      for (int j = 0; j < K; ++j) {
-        const int r = d.selrank[j * m.m_max + p];
-        if (r >= 0) {
-          const St4<R> e = est[j * m.m_max + r];
-          a[0] += (double)e.x;
-          a[1] += (double)e.vx;
-          a[2] += (double)e.y;
-          a[3] += (double)e.vy;
+      if constexpr (sizeof(R) == 4) {
+        // offsets from the first voter, FP32 sums and scale (as the fused CU)
+        St4<R> e0 = {0, 0, 0, 0};
+        float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        bool first = true;
+        for (int j = 0; j < K; ++j) {
+          const int r = d.selrank[j * m.m_max + p];
+          if (r >= 0) {
+            const St4<R> e = est[j * m.m_max + r];
+            if (first) {
+              e0 = e;
+              first = false;
+            } else {
+              a0 += e.x - e0.x;
+              a1 += e.vx - e0.vx;
+              a2 += e.y - e0.y;
+              a3 += e.vy - e0.vy;
+            }
+          }
         }
+        const float iv = 1.0f / (float)votes;
+        out[idx] = St4<R>{e0.x + a0 * iv, e0.vx + a1 * iv, e0.y + a2 * iv, e0.vy + a3 * iv};
+      } else {
+        double a[4] = {0, 0, 0, 0};
+        for (int j = 0; j < K; ++j) {
+          const int r = d.selrank[j * m.m_max + p];
+          if (r >= 0) {
+            const St4<R> e = est[j * m.m_max + r];
+            a[0] += (double)e.x;
+            a[1] += (double)e.vx;
+            a[2] += (double)e.y;
+            a[3] += (double)e.vy;
+          }
+        }
+        out[idx] = St4<R>{(R)(a[0] / votes), (R)(a[1] / votes), (R)(a[2] / votes), (R)(a[3] / votes)};
       }
-      out[idx] = St4<R>{(R)(a[0] / votes), (R)(a[1] / votes), (R)(a[2] / votes), (R)(a[3] / votes)};
       out_labels[idx] = p;
     }
     __syncthreads();
@@ -289,6 +328,7 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
 template <class R>
 __global__ void __launch_bounds__(1024) k_batch_out(Dev d, Model m, R* out_states, int* out_labels, int* counts,
                                                     int cap) {
+  pdl_enter();
   __shared__ int wsum[32];
   __shared__ int carry_s;
   const int j = blockIdx.x;
@@ -335,26 +375,26 @@ __global__ void __launch_bounds__(1024) k_batch_out(Dev d, Model m, R* out_state
 template <class R>
 cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* out_labels, int* counts, int cap,
                              cudaStream_t s) {
-  k_batch_out<R><<<m.K, 1024, 0, s>>>(d, m, out_states, out_labels, counts, cap);
+  launch_k(k_batch_out<R>, dim3(m.K), dim3(1024), 0, s, d, m, out_states, out_labels, counts, cap);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
-  k_select<R><<<dim3(m.K, (m.m_max + 63) / 64), 256, sizeof(unsigned long long) * (size_t)m.m_max, s>>>(d, m);
+  launch_k(k_select<R>, dim3(dim3(m.K, (m.m_max + 63) / 64)), dim3(256), sizeof(unsigned long long) * (size_t)m.m_max, s, d, m);
   {
     const long items = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
     const int g = (int)(items < 152L * 8 ? (items > 0 ? items : 1) : 152L * 8);
     const size_t smem = (sizeof(P4<R>) + sizeof(St4<R>)) * (size_t)m.tune.c_tile;
-    if (m.meas_model) k_selsum<R, 1><<<g, kThreads, smem, s>>>(d, m);
-    else k_selsum<R, 0><<<g, kThreads, smem, s>>>(d, m);
+    if (m.meas_model) launch_k(k_selsum<R, 1>, dim3(g), dim3(kThreads), smem, s, d, m);
+    else launch_k(k_selsum<R, 0>, dim3(g), dim3(kThreads), smem, s, d, m);
   }
   long warps = (long)m.K * m.m_max;
   int b = (int)((warps + 7) / 8);
   if (b > 152 * 8) b = 152 * 8;
-  k_est_local<R><<<b, 256, 0, s>>>(d, m);
-  if (d.zshared) k_fuse<R><<<1, 1024, 0, s>>>(d, m, out_states, out_labels, cap, d_count);
+  launch_k(k_est_local<R>, dim3(b), dim3(256), 0, s, d, m);
+  if (d.zshared) launch_k(k_fuse<R>, dim3(1), dim3(1024), 0, s, d, m, out_states, out_labels, cap, d_count);
   return cudaGetLastError();
 }
 

@@ -182,22 +182,77 @@ __device__ __forceinline__ void meas_point_f(const Cst<R>& c, int rb, V2<R> z, R
 
 // CU fusion of one step by one CTA (Step 4): labels taken by more than K/2
 // PEs, FP64 mean of their local states, ascending label order.
+// Mean of the voters' local states, in PE order.  FP32: offsets from the
+// first voter (close states subtract exactly), summed and scaled in FP32;
+// FP64: plain sums and divides.
+template <class R>
+__device__ __forceinline__ St4<R> fuse_mean(const St4<R>* __restrict__ est, const int* srank, int Pc, int q, int K,
+                                            int m_max, int votes) {
+  if constexpr (sizeof(R) == 4) {
+    St4<R> e0 = {0, 0, 0, 0};
+    R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    bool first = true;
+#pragma unroll 8
+    for (int k = 0; k < K; ++k) {
+      const int r = srank[k * Pc + q];
+      if (r >= 0) {
+        const St4<R> e = est[k * m_max + r];
+        if (first) {
+          e0 = e;
+          first = false;
+        } else {
+          a0 += e.x - e0.x;
+          a1 += e.vx - e0.vx;
+          a2 += e.y - e0.y;
+          a3 += e.vy - e0.vy;
+        }
+      }
+    }
+    const R iv = (R)1 / (R)votes;
+    return St4<R>{e0.x + a0 * iv, e0.vx + a1 * iv, e0.y + a2 * iv, e0.vy + a3 * iv};
+  } else {
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int k = 0; k < K; ++k) {
+      const int r = srank[k * Pc + q];
+      if (r >= 0) {
+        const St4<R> e = est[k * m_max + r];
+        a0 += (double)e.x;
+        a1 += (double)e.vx;
+        a2 += (double)e.y;
+        a3 += (double)e.vy;
+      }
+    }
+    return St4<R>{(R)(a0 / votes), (R)(a1 / votes), (R)(a2 / votes), (R)(a3 / votes)};
+  }
+}
+
 template <class R>
 __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* out_lab, int cap, int* count,
-                        int* wsum) {
+                        int* wsum, int* srank, int srank_cap) {
+  // Step 4 on CTA 0: the K PEs' ranks of a chunk of measurements are staged
+  // in shared memory with independent loads (srank[k][q]); a label's votes
+  // are counted from there and the voters' local states read in PE order.
   __shared__ int carry_s;
   const St4<R>* est = static_cast<const St4<R>*>(d.est_local);
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
+  const int K = m.K;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p0 = 0; p0 < M; p0 += blockDim.x) {
-    const int p = p0 + threadIdx.x;
-    int votes = 0;
-    if (p < M) {
-#pragma unroll 8
-      for (int k = 0; k < m.K; ++k) votes += d.selrank[k * m.m_max + p] >= 0 ? 1 : 0;
+  int chunk = srank_cap / K;
+  if (chunk > (int)blockDim.x) chunk = blockDim.x;
+  for (int p0 = 0; p0 < M; p0 += chunk) {
+    const int Pc = min(chunk, M - p0);
+    for (int idx = threadIdx.x; idx < K * Pc; idx += blockDim.x) {
+      const int k = idx / Pc, q = idx - k * Pc;
+      srank[idx] = d.selrank[k * m.m_max + p0 + q];
     }
-    const int valid = (p < M && 2 * votes > m.K) ? 1 : 0;
+    __syncthreads();
+    const int q = threadIdx.x;
+    const int p = p0 + q;
+    int votes = 0;
+    if (q < Pc)
+      for (int k = 0; k < K; ++k) votes += srank[k * Pc + q] >= 0 ? 1 : 0;
+    const int valid = (q < Pc && 2 * votes > K) ? 1 : 0;
     int incl = valid;
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -217,19 +272,7 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
     const int carry = carry_s;
     const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
     if (valid && idx < cap) {
-      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll 4
-      for (int k = 0; k < m.K; ++k) {
-        const int r = d.selrank[k * m.m_max + p];
-        if (r >= 0) {
-          const St4<R> e = est[k * m.m_max + r];
-          a0 += (double)e.x;
-          a1 += (double)e.vx;
-          a2 += (double)e.y;
-          a3 += (double)e.vy;
-        }
-      }
-      out[idx] = St4<R>{(R)(a0 / votes), (R)(a1 / votes), (R)(a2 / votes), (R)(a3 / votes)};
+      out[idx] = fuse_mean<R>(est, srank, Pc, q, K, m.m_max, votes);
       out_lab[idx] = p;
     }
     __syncthreads();
@@ -263,6 +306,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   unsigned long long* Q = reinterpret_cast<unsigned long long*>(smem + SL.sh0);
   int* cend = reinterpret_cast<int*>(smem + SL.sh0 + sizeof(unsigned long long) * m.pe_cap);
   int* perm = cend + m.pe_cap;
+  // CU fusion's rank scratch: the predicted states' block, free after the gather
+  int* srank = reinterpret_cast<int*>(smem + SL.sx);
+  const int srank_cap = (int)(sizeof(St4<R>) * m.pe_cap / sizeof(int));
   __shared__ double bN;
   __shared__ int bL, bS;
   __shared__ R bW;
@@ -387,7 +433,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     for (int p = tid; p < M; p += T) {
       const double den = m.kappa + Cu[p];
       ginv[p] = den > 0.0 ? csr / (R)den : (R)0;
-      key[p] = order_key(den > 0.0 ? Cd[p] / den : 0.0);
+      key[p] = order_key(den > 0.0 ? (double)quot<R>(Cd[p], den) : 0.0);
       d.Cused[j * m.m_max + p] = Cu[p];
     }
     __syncthreads();
@@ -431,19 +477,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     if (LTl > npos) LTl = npos;
     if (LTl < 0) LTl = 0;
     const int LT = (int)LTl;
-    for (int p = tid; p < M; p += T) {
+    // a warp per measurement, lanes split the comparisons
+    for (int p = tid >> 5; p < M; p += T >> 5) {
       const unsigned long long v = key[p];
-      int rank = 0;
-      for (int q = 0; q < M; ++q) {
+      int cnt = 0;
+      for (int q = lane; q < M; q += 32) {
         const unsigned long long u = key[q];
-        rank += (u > v || (u == v && q < p)) ? 1 : 0;
+        cnt += (u > v || (u == v && q < p)) ? 1 : 0;
       }
-      const bool take = v > 0ull && rank < LT;
-      selrank[p] = take ? rank : -1;
-      d.selrank[j * m.m_max + p] = take ? rank : -1;
-      if (take) {
-        sel[rank] = p;
-        d.sel[j * m.m_max + rank] = p;
+      const int rank = __reduce_add_sync(0xffffffffu, cnt);
+      if (lane == 0) {
+        const bool take = v > 0ull && rank < LT;
+        selrank[p] = take ? rank : -1;
+        d.selrank[j * m.m_max + p] = take ? rank : -1;
+        if (take) {
+          sel[rank] = p;
+          d.sel[j * m.m_max + rank] = p;
+        }
       }
     }
     if (tid == 0) d.nsel[j] = LT;
@@ -483,11 +533,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
         if (split == 0 && r < LT) {
           St4<R> o;
           if (s0 > (R)0) {
-            const double c0 = (double)s0;
-            o.x = (R)((double)px + (double)s1 / c0);
-            o.vx = (R)((double)s2 / c0);
-            o.y = (R)((double)py + (double)s3 / c0);
-            o.vy = (R)((double)s4 / c0);
+            if constexpr (sizeof(R) == 4) {
+              const R inv = (R)1 / s0;
+              o.x = px + s1 * inv;
+              o.vx = s2 * inv;
+              o.y = py + s3 * inv;
+              o.vy = s4 * inv;
+            } else {
+              o.x = px + s1 / s0;
+              o.vx = s2 / s0;
+              o.y = py + s3 / s0;
+              o.vy = s4 / s0;
+            }
           } else {
             o = St4<R>{px, (R)0, py, (R)0};
           }
@@ -608,7 +665,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           }
         }
       }
-      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired);
+      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap);
       if (!grid_sync(d)) return;
       if (xchg && lx > 0) {
         const int from = (j + m.K - 1) % m.K;
@@ -622,7 +679,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
     } else {
       __syncthreads();
-      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired);
+      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap);
     }
     if (tid == 0) d.n_cur[j] = n;
     __syncthreads();
@@ -658,8 +715,8 @@ cudaError_t launch_fused(const Dev& d, const Model& m, const void* Z, const int*
                          int cap, cudaStream_t s) {
   FusedArgs a{Z, zoff, M1, noise, u, xu, out_states, out_labels, out_count, cap, S};
   const size_t sm = fused_smem_bytes<R>(m);
-  cudaError_t e = cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
+  // the grid barrier resets itself (the last arrival clears the count); it is
+  // zeroed with the workspace and again whenever a device error is read
   void* args[] = {(void*)&d, (void*)&m, (void*)&a};
   return cudaLaunchCooperativeKernel((const void*)k_step_fused<R>, dim3(m.K), dim3(kFusedThreads), args, sm, s);
 }

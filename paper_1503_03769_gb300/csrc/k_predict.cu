@@ -25,6 +25,7 @@ template <> __device__ __forceinline__ double slice_bw<double>(const Dev& d, int
 
 template <class R>
 __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __restrict__ noise) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   // work items: tiles of 256 over each slice's survivors + births
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __rest
 // and flag non-finite measurements.
 template <class R>
 __global__ void k_stage_z(Dev d, Model, const R* Z, int M) {
+  pdl_enter();
   V2<R>* zs = static_cast<V2<R>*>(d.Z);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
     V2<R> z = reinterpret_cast<const V2<R>*>(Z)[p];
@@ -74,7 +76,7 @@ template <class R>
 cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s) {
   long items = (long)m.K * ((m.pe_cap + 255) / 256);
   int blocks = (int)(items < 152 * 16 ? (items > 0 ? items : 1) : 152 * 16);
-  k_predict<R><<<blocks, 256, 0, s>>>(d, m, noise);
+  launch_k(k_predict<R>, dim3(blocks), dim3(256), 0, s, d, m, noise);
   return cudaGetLastError();
 }
 
@@ -82,6 +84,7 @@ cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStr
 // off[j] .. off[j+1]-1 (each at most m_max, all within the workspace).
 template <class R>
 __global__ void k_stage_zb(Dev d, Model m, const R* Z, const int* __restrict__ off) {
+  pdl_enter();
   const int K = m.K;
   const int rows = off[K];
   const bool ok_total = rows >= 0 && rows <= K * m.m_max;
@@ -109,7 +112,7 @@ cudaError_t launch_stage_zb(const Dev& d, const Model& m, const R* Z, const int*
   int blocks = (int)((rows + 255) / 256);
   if (blocks > 152 * 4) blocks = 152 * 4;
   if (blocks < 1) blocks = 1;
-  k_stage_zb<R><<<blocks, 256, 0, s>>>(d, m, Z, off);
+  launch_k(k_stage_zb<R>, dim3(blocks), dim3(256), 0, s, d, m, Z, off);
   return cudaGetLastError();
 }
 
@@ -120,7 +123,7 @@ template <class R>
 cudaError_t launch_stage_z(const Dev& d, const Model& m, const R* Z, int M, cudaStream_t s) {
   int blocks = (M + 255) / 256;
   if (blocks < 1) blocks = 1;
-  k_stage_z<R><<<blocks, 256, 0, s>>>(d, m, Z, M);
+  launch_k(k_stage_z<R>, dim3(blocks), dim3(256), 0, s, d, m, Z, M);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ __device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long 
 
 template <class R>
 __global__ void __launch_bounds__(kChunk) k_rs_q(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ unsigned long long wt[32];
   item_prefix(d.n_pred, m.K, pref, kChunk);
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kChunk) k_rs_q(Dev d, Model m) {
 }
 
 __global__ void __launch_bounds__(1024) k_rs_off(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ unsigned long long wt[32];
   const int j = blockIdx.x;
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(1024) k_rs_off(Dev d, Model m) {
 
 template <class R>
 __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint32_t* __restrict__ u) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ unsigned long long wt[32];
   item_prefix(d.n_pred, m.K, pref, kChunk);
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint3
 // of each slice.
 template <class R>
 __global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
 // Ring exchange plan: L_x = floor(frac min_j L_j); PE j's slots are the first
 // L_x entries of a partial Fisher-Yates shuffle of 0..L_j-1.
 __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
+  pdl_enter();
   extern __shared__ int perm[];
   const int j = blockIdx.x;
   const int K = m.K;
@@ -205,6 +210,7 @@ __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
 // Outgoing particle-weight couples of each PE into the outbox.
 template <class R>
 __global__ void k_xout(Dev d, Model m) {
+  pdl_enter();
   const St4<R>* x = static_cast<const St4<R>*>(d.x);
   const R* w = static_cast<const R*>(d.w);
   St4<R>* xo = static_cast<St4<R>*>(d.x_out);
@@ -223,6 +229,7 @@ __global__ void k_xout(Dev d, Model m) {
 // PE j's chosen slots receive PE j-1's outbox (ring).
 template <class R>
 __global__ void k_xin(Dev d, Model m) {
+  pdl_enter();
   St4<R>* x = static_cast<St4<R>*>(d.x);
   R* w = static_cast<R*>(d.w);
   const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
@@ -239,7 +246,8 @@ __global__ void k_xin(Dev d, Model m) {
   }
 }
 
-__global__ void k_advance(Dev d) { *d.step += 1ull; }
+__global__ void k_advance(Dev d) {
+  pdl_enter(); *d.step += 1ull; }
 
 template <class R>
 cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, const uint32_t* xu,
@@ -249,24 +257,24 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   if (b > 152 * 16) b = 152 * 16;
   const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
   const int gc = (int)(chunks < 152L * 2 ? (chunks > 0 ? chunks : 1) : 152L * 2);
-  k_rs_q<R><<<gc, kChunk, 0, s>>>(d, m);
-  k_rs_off<<<m.K, 1024, 0, s>>>(d, m);
-  k_rs_count<R><<<gc, kChunk, 0, s>>>(d, m, u);
+  launch_k(k_rs_q<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
+  launch_k(k_rs_off, dim3(m.K), dim3(1024), 0, s, d, m);
+  launch_k(k_rs_count<R>, dim3(gc), dim3(kChunk), 0, s, d, m, u);
   const long gitems = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
-  k_rs_gather<R><<<(int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16), 256, 0, s>>>(d, m);
+  launch_k(k_rs_gather<R>, dim3((int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16)), dim3(256), 0, s, d, m);
   if (m.K > 1 && m.exchange_frac > 0.0) {
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
     if (bx < 1) bx = 1;
     if (bx > 152 * 8) bx = 152 * 8;
-    k_xplan<<<m.K, 256, sizeof(int) * 2 * (size_t)m.pe_cap, s>>>(d, m, xu);
-    k_xout<R><<<bx, 256, 0, s>>>(d, m);
-    k_xin<R><<<bx, 256, 0, s>>>(d, m);
+    launch_k(k_xplan, dim3(m.K), dim3(256), sizeof(int) * 2 * (size_t)m.pe_cap, s, d, m, xu);
+    launch_k(k_xout<R>, dim3(bx), dim3(256), 0, s, d, m);
+    launch_k(k_xin<R>, dim3(bx), dim3(256), 0, s, d, m);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance_step(const Dev& d, cudaStream_t s) {
-  k_advance<<<1, 1, 0, s>>>(d);
+  launch_k(k_advance, dim3(1), dim3(1), 0, s, d);
   return cudaGetLastError();
 }
 

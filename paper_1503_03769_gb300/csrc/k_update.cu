@@ -34,6 +34,7 @@ namespace phd {
 
 template <class R, int RB, int MB>
 __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
+  pdl_enter();
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int tpref[kMaxPE + 1];   // tiles per slice (pass-1 partial rows)
   __shared__ int ipref[kMaxPE + 1];   // work items per slice (tiles x measurement chunks)
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
 // the dW order keys.
 template <class R>
 __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ int mpref[kMaxPE + 1];
   const int K = m.K;
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
         const double cj = d.C[j * m.m_max + p];
         d.Cused[j * m.m_max + p] = mean;
         const double den = d.kap[j] + mean;
-        ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
-        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? cj / den : 0.0);
+        ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
+        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? (double)quot<R>(cj, den) : 0.0);
       }
     }
   } else {
@@ -175,8 +177,8 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
         d.C[j * m.m_max + p] = c;
         d.Cused[j * m.m_max + p] = c;
         const double den = d.kap[j] + c;
-        ginv[j * m.m_max + p] = den > 0.0 ? (R)(cs / den) : (R)0;
-        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? c / den : 0.0);
+        ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
+        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
       }
     }
   }
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(256) k_finalize(Dev d, Model m) {
 // (p = g, g + G, ...); two accumulators per particle for ILP.
 template <class R, int RB, int PB, int G>
 __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
+  pdl_enter();
   constexpr int GR = kThreads / G;   // particle groups per tile
   constexpr int TPR = GR * PB;       // particles per work item
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
 // Per PE: N^j = sum of the pass-2 tile sums (fixed order), the largest
 // updated weight, and the resampling plan (L_j and the CDF scale).
 __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
+  pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ double red[8], redm[8];
   const int j = blockIdx.x;
@@ -398,14 +402,14 @@ static void colsum_go(const Dev& d, const Model& m, cudaStream_t s) {
   const long tiles = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
   const long chunks = (m.m_max + 64 * MB - 1) / (64 * MB);
   const size_t smem = sizeof(P4<R>) * (size_t)m.tune.c_tile + sizeof(R) * kThreads * MB;
-  k_colsum<R, RB, MB><<<grid_cap(tiles * chunks, m.tune.grid1), kThreads, smem, s>>>(d, m);
+  launch_k(k_colsum<R, RB, MB>, dim3(grid_cap(tiles * chunks, m.tune.grid1)), dim3(kThreads), smem, s, d, m);
 }
 
 template <class R, int RB, int PB, int G>
 static void rowsum_go(const Dev& d, const Model& m, cudaStream_t s) {
   const int tpr = kThreads / G * PB;
   const long tiles = (long)m.K * ((m.pe_cap + tpr - 1) / tpr);
-  k_rowsum<R, RB, PB, G><<<grid_cap(tiles, m.tune.grid2), kThreads, sizeof(Z4<R>) * (size_t)m.m_max, s>>>(d, m);
+  launch_k(k_rowsum<R, RB, PB, G>, dim3(grid_cap(tiles, m.tune.grid2)), dim3(kThreads), sizeof(Z4<R>) * (size_t)m.m_max, s, d, m);
 }
 
 template <class R, int RB>
@@ -471,7 +475,7 @@ cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s) {
 
 template <class R>
 cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s) {
-  k_finalize<R><<<grid_cap(((long)m.K * m.m_max + 7) / 8, 152L * 8), 256, 0, s>>>(d, m);
+  launch_k(k_finalize<R>, dim3(grid_cap(((long)m.K * m.m_max + 7) / 8, 152L * 8)), dim3(256), 0, s, d, m);
   return cudaGetLastError();
 }
 
@@ -481,7 +485,7 @@ cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s) {
 }
 
 cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s) {
-  k_mass<<<m.K, 256, 0, s>>>(d, m);
+  launch_k(k_mass, dim3(m.K), dim3(256), 0, s, d, m);
   return cudaGetLastError();
 }
 

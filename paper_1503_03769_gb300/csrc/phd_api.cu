@@ -300,6 +300,8 @@ phd_status read_device_error(phd_handle* h) {
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err == 0) return PHD_OK;
   PHD_CUDA(h, cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
+  // a wait that gave up may have left the grid barrier mid-count
+  PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 2 * sizeof(unsigned int), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (err & phd::kErrNonFinite) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
@@ -554,10 +556,13 @@ phd_status run_fused(phd_handle* h, const void* Z, const int* zoff, int M, int S
 phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u,
                        const uint32_t* xu, void* d_states, int* d_labels, int cap, int* d_count) {
   phd_status st;
-  if (use_fused(h)) {
+  const bool fused = use_fused(h);
+  if (fused) {
+    // the kernel writes the count to the caller's buffer and the workspace
     const bool direct = cap > 0 && d_states && d_labels;
     st = run_fused(h, Z, nullptr, M, 1, noise, u, xu, direct ? d_states : h->out_states,
-                   direct ? d_labels : h->out_labels, h->d.out_count, direct ? cap : h->cfg.m_max);
+                   direct ? d_labels : h->out_labels, d_count ? d_count : h->d.out_count,
+                   direct ? cap : h->cfg.m_max);
   } else if (noise || u || xu) {
     if (h->m.learned) {
       st = stage_z_only(h, Z, M);
@@ -590,7 +595,7 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
   }
   if (st != PHD_OK) return st;
   h->have_update = true;
-  if (d_count)
+  if (d_count && !fused)
     PHD_CUDA(h, cudaMemcpyAsync(d_count, h->d.out_count, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
   return PHD_OK;
 }

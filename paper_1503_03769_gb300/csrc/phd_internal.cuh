@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "phd.h"
@@ -382,6 +383,43 @@ template <int RB> struct PairQ<double, RB> {
     return qform_t<double, RB>(L, z0, z1, h0, h1, h1lo);
   }
 };
+
+// Quotient in the kernel's precision: the FP32 kernels round the operands to
+// FP32 and divide in FP32 (the FP64 divide is a long sequence on the ~2
+// lanes/clk/SM FP64 pipe and dominated the small per-label phases); the FP64
+// kernels divide in FP64.
+template <class R> __device__ __forceinline__ R quot(double a, double b);
+template <> __device__ __forceinline__ float quot<float>(double a, double b) { return (float)a / (float)b; }
+template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  The staged kernels are
+// launched with programmatic stream serialisation: a kernel may be scheduled
+// while its predecessor's last CTAs still run, and its first statement waits
+// (griddepcontrol.wait) until the predecessor has completed and its writes are
+// visible, so no dependent read can come early; each kernel then lets its own
+// successor be scheduled.  This hides the launch gap between the ~15 kernels
+// of a staged step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // Work-item decode for the pair kernels: item -> (PE, particle tile), tiles
 // of kTile over each PE's count.  pref gets K+1 entries in shared memory; the
