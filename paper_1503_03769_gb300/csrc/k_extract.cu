@@ -17,8 +17,9 @@
 // k_est_local: per (PE, rank) FP64 reduction of the pass-3 partials to zeta.
 // k_fuse (one CTA): for every label the PEs that took it vote; a label is
 //   valid with more than K/2 votes, and its state is the mean of the voters'
-//   local states in PE order (FP32 kernels: offsets from the first voter
-//   summed and scaled in FP32; FP64 kernels: FP64 sums).  Output in
+//   local states in PE order (FP32 kernels: positions as offsets from the
+//   label's measurement point, summed and scaled in FP32; FP64 kernels: FP64
+//   sums).  Output in
 //   ascending label order.
 #include "phd_internal.cuh"
 
@@ -276,27 +277,23 @@ __global__ void __launch_bounds__(1024) k_fuse(Dev d, Model m, R* out_states, in
     const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
     if (valid && idx < cap) {
       if constexpr (sizeof(R) == 4) {
-        // offsets from the first voter, FP32 sums and scale (as the fused CU)
-        St4<R> e0 = {0, 0, 0, 0};
+        // positions as offsets from the label's measurement point, FP32 sums
+        // and scale (as the fused CU)
+        R px, py;
+        meas_point<R>(m, slice_Z<R>(d, 0)[p], px, py);
         float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        bool first = true;
         for (int j = 0; j < K; ++j) {
           const int r = d.selrank[j * m.m_max + p];
           if (r >= 0) {
             const St4<R> e = est[j * m.m_max + r];
-            if (first) {
-              e0 = e;
-              first = false;
-            } else {
-              a0 += e.x - e0.x;
-              a1 += e.vx - e0.vx;
-              a2 += e.y - e0.y;
-              a3 += e.vy - e0.vy;
-            }
+            a0 += e.x - px;
+            a1 += e.vx;
+            a2 += e.y - py;
+            a3 += e.vy;
           }
         }
         const float iv = 1.0f / (float)votes;
-        out[idx] = St4<R>{e0.x + a0 * iv, e0.vx + a1 * iv, e0.y + a2 * iv, e0.vy + a3 * iv};
+        out[idx] = St4<R>{px + a0 * iv, a1 * iv, py + a2 * iv, a3 * iv};
       } else {
         double a[4] = {0, 0, 0, 0};
         for (int j = 0; j < K; ++j) {

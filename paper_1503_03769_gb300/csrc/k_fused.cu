@@ -182,34 +182,28 @@ __device__ __forceinline__ void meas_point_f(const Cst<R>& c, int rb, V2<R> z, R
 
 // CU fusion of one step by one CTA (Step 4): labels taken by more than K/2
 // PEs, FP64 mean of their local states, ascending label order.
-// Mean of the voters' local states, in PE order.  FP32: offsets from the
-// first voter (close states subtract exactly), summed and scaled in FP32;
-// FP64: plain sums and divides.
+// Mean of the voters' local states, in PE order.  FP32: positions as offsets
+// from the label's measurement point (close values subtract exactly; the
+// point's own rounding cancels), summed and scaled in FP32, with loads that
+// do not wait on one another; FP64: plain sums and divides.
 template <class R>
 __device__ __forceinline__ St4<R> fuse_mean(const St4<R>* __restrict__ est, const int* srank, int Pc, int q, int K,
-                                            int m_max, int votes) {
+                                            int m_max, int votes, R px, R py) {
   if constexpr (sizeof(R) == 4) {
-    St4<R> e0 = {0, 0, 0, 0};
     R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    bool first = true;
 #pragma unroll 8
     for (int k = 0; k < K; ++k) {
       const int r = srank[k * Pc + q];
       if (r >= 0) {
         const St4<R> e = est[k * m_max + r];
-        if (first) {
-          e0 = e;
-          first = false;
-        } else {
-          a0 += e.x - e0.x;
-          a1 += e.vx - e0.vx;
-          a2 += e.y - e0.y;
-          a3 += e.vy - e0.vy;
-        }
+        a0 += e.x - px;
+        a1 += e.vx;
+        a2 += e.y - py;
+        a3 += e.vy;
       }
     }
     const R iv = (R)1 / (R)votes;
-    return St4<R>{e0.x + a0 * iv, e0.vx + a1 * iv, e0.y + a2 * iv, e0.vy + a3 * iv};
+    return St4<R>{px + a0 * iv, a1 * iv, py + a2 * iv, a3 * iv};
   } else {
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int k = 0; k < K; ++k) {
@@ -228,7 +222,7 @@ __device__ __forceinline__ St4<R> fuse_mean(const St4<R>* __restrict__ est, cons
 
 template <class R>
 __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* out_lab, int cap, int* count,
-                        int* wsum, int* srank, int srank_cap) {
+                        int* wsum, int* srank, int srank_cap, const V2<R>* zs, const Cst<R>& cc) {
   // Step 4 on CTA 0: the K PEs' ranks of a chunk of measurements are staged
   // in shared memory with independent loads (srank[k][q]); a label's votes
   // are counted from there and the voters' local states read in PE order.
@@ -272,7 +266,9 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
     const int carry = carry_s;
     const int idx = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - valid;
     if (valid && idx < cap) {
-      out[idx] = fuse_mean<R>(est, srank, Pc, q, K, m.m_max, votes);
+      R px, py;
+      meas_point_f<R>(cc, m.meas_model, zs[p], px, py);
+      out[idx] = fuse_mean<R>(est, srank, Pc, q, K, m.m_max, votes, px, py);
       out_lab[idx] = p;
     }
     __syncthreads();
@@ -665,7 +661,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           }
         }
       }
-      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap);
+      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap, zs, cc);
       if (!grid_sync(d)) return;
       if (xchg && lx > 0) {
         const int from = (j + m.K - 1) % m.K;
@@ -679,7 +675,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
     } else {
       __syncthreads();
-      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap);
+      cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap, zs, cc);
     }
     if (tid == 0) d.n_cur[j] = n;
     __syncthreads();
