@@ -399,13 +399,19 @@ phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
  *  r_g:    pass 2 lanes sharing a particle: 1, 2, 4 or 8; (r_pb, r_g) is one
  *          of (1,1) (2,1) (4,1) (1,2) (2,2) (1,4) (1,8);
  *  grid1, grid2: CTA caps of pass 1 and pass 2 (1 .. 9728);
+ *  gate:   1 (default) to skip pairs past the exact likelihood gate, 0 to
+ *          evaluate every pair.  The FP32 exp2 flushes 2^-q to exactly 0 for
+ *          q > 126 (FP64: q > 1074); a box around each work item's particles
+ *          in measurement space bounds q from below, and pairs whose bound is
+ *          at least 130 (FP64: 1100) are skipped: they add exactly nothing,
+ *          so results are bit-identical with the gate on or off;
  *  pass1_us, pass2_us: filled by phd_autotune with the measured mean duration
  *          of each pass in the chosen shape (0 elsewhere; ignored on input).
  * FP64 handles support c_mb 2 and (r_pb, r_g) = (1, 4) only.  The default is
  * c_tile 512, c_mb 4 (2 in FP64), (1, 4), grid1 = grid2 = 1216.  The fused
  * step kernel (phd_set_path) does not use these shapes. */
 typedef struct phd_tuning {
-    int32_t c_tile, c_mb, r_pb, r_g, grid1, grid2;
+    int32_t c_tile, c_mb, r_pb, r_g, grid1, grid2, gate;
     float pass1_us, pass2_us;
 } phd_tuning;
 

@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
+  const Lik<R> LB = make_lik<R>(m);
+  __shared__ R bsh[4 * (kThreads / 32)];
+  Box<R> box{0, 0, 0, 0};
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(ipref, K, item);
@@ -65,14 +68,21 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
     const int cnt = min(TP, d.n_pred[j] - tile * TP);
     if (titem != staged) {   // consecutive items of a CTA can share the tile
       __syncthreads();
+      const R inf = (R)INFINITY;
+      R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
       for (int i = threadIdx.x; i < TP; i += kThreads) {
         P4<R> q = {0, 0, 0, 0};
         if (i < cnt) {
           const H3<R> h = meas_h<R>(m, x[base + i], tab);
           q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
+          lo0 = fmin(lo0, h.h0);
+          hi0 = fmax(hi0, h.h0);
+          lo1 = fmin(lo1, h.h1);
+          hi1 = fmax(hi1, h.h1);
         }
         sp[i] = q;
       }
+      box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
       __syncthreads();
       staged = titem;
     }
@@ -87,14 +97,16 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
     for (int k = 0; k < MB; ++k) acc[k] = 0;
     if (sidx < S) {
       R z0[MB], z1[MB];
+      bool live = false;   // some measurement of this thread can reach the tile
 #pragma unroll
       for (int k = 0; k < MB; ++k) {
         const int p = g + k * G;
         const V2<R> z = p < Mc ? Z[pbeg + p] : V2<R>{0, 0};
         z0[k] = z.a;
         z1[k] = z.b;
+        live = live || (p < Mc && (!m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>()));
       }
-      int i = sidx;
+      int i = live ? sidx : cnt;
       for (; i + S < cnt; i += 2 * S) {
         const P4<R> qa = sp[i], qb = sp[i + S];
 #pragma unroll
@@ -240,8 +252,11 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   R* __restrict__ wu = static_cast<R*>(d.wu);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
+  const Lik<R> LB = make_lik<R>(m);
   const R miss = consts<R>(m).miss;
   const int il = threadIdx.x / G, g = threadIdx.x % G;
+  __shared__ R bsh[4 * (kThreads / 32)];
+  __shared__ unsigned int gmask[kMaxM / 32];   // bit p: measurement p cannot reach the tile
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
@@ -249,6 +264,8 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
     const int M = slice_M(d, j);
     const int n = d.n_pred[j];
     R h0[PB], h1[PB], hl[PB], wi[PB];
+    const R inf = (R)INFINITY;
+    R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
 #pragma unroll
     for (int k = 0; k < PB; ++k) {
       const int i = tile * TPR + k * GR + il;
@@ -260,6 +277,10 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
         h1[k] = h.h1;
         hl[k] = h.h1lo;
         wi[k] = w[gi];
+        lo0 = fmin(lo0, h.h0);
+        hi0 = fmax(hi0, h.h0);
+        lo1 = fmin(lo1, h.h1);
+        hi1 = fmax(hi1, h.h1);
       }
     }
     if (j != staged) {
@@ -272,11 +293,22 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       __syncthreads();
       staged = j;
     }
+    // measurements whose pairs with every particle of the tile are past the gate
+    const Box<R> box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
+    for (int p0 = threadIdx.x & ~31; p0 < M; p0 += kThreads) {
+      const int p = p0 + (threadIdx.x & 31);
+      const bool gated = m.tune.gate && p < M && box_qmin<R, RB>(box, LB.b0, LB.b1, zs[p].z0, zs[p].z1) >= gate_q<R>();
+      const unsigned int bits = __ballot_sync(0xffffffffu, gated);
+      if ((threadIdx.x & 31) == 0) gmask[p0 >> 5] = bits;
+    }
+    __syncthreads();
     R a0[PB], a1[PB];
 #pragma unroll
     for (int k = 0; k < PB; ++k) a0[k] = a1[k] = 0;
     int p = g;
     for (; p + G < M; p += 2 * G) {
+      // a pair of measurements both past the gate adds exactly nothing
+      if (((gmask[p >> 5] >> (p & 31)) & (gmask[(p + G) >> 5] >> ((p + G) & 31)) & 1u) != 0u) continue;
       const Z4<R> za = zs[p], zb = zs[p + G];
 #pragma unroll
       for (int k = 0; k < PB; ++k)
@@ -384,12 +416,14 @@ Tune default_tune(bool fp64) {
   t.r_g = 4;
   t.grid1 = 152 * 8;
   t.grid2 = 152 * 8;
+  t.gate = 1;
   return t;
 }
 
 bool tune_supported(const Tune& t, bool fp64) {
   if (t.c_tile != 256 && t.c_tile != 512 && t.c_tile != 1024) return false;
   if (t.grid1 < 1 || t.grid2 < 1 || t.grid1 > 152 * 64 || t.grid2 > 152 * 64) return false;
+  if (t.gate != 0 && t.gate != 1) return false;
   if (fp64) return t.c_mb == 2 && t.r_pb == 1 && t.r_g == 4;
   if (t.c_mb != 1 && t.c_mb != 2 && t.c_mb != 4) return false;
   const int pg = t.r_pb * 16 + t.r_g;

@@ -1020,13 +1020,13 @@ phd_status phd_reset_stats(phd_handle* h) {
 phd_status phd_get_tuning(phd_handle* h, phd_tuning* out) {
   if (!h || !out) return PHD_ERR_INVALID_ARG;
   const phd::Tune& t = h->m.tune;
-  *out = phd_tuning{t.c_tile, t.c_mb, t.r_pb, t.r_g, t.grid1, t.grid2, 0.0f, 0.0f};
+  *out = phd_tuning{t.c_tile, t.c_mb, t.r_pb, t.r_g, t.grid1, t.grid2, t.gate, 0.0f, 0.0f};
   return PHD_OK;
 }
 
 phd_status phd_set_tuning(phd_handle* h, const phd_tuning* t) {
   if (!h || !t) return PHD_ERR_INVALID_ARG;
-  const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2};
+  const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2, t->gate};
   if (!phd::tune_supported(u, is_fp64(h))) return fail(h, PHD_ERR_INVALID_ARG, "phd_set_tuning: unsupported shape");
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->m.tune = u;
@@ -1109,7 +1109,8 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
     h->m.tune = base;
     return cuda_fail(h, e, "phd_autotune");
   }
-  if (out) *out = phd_tuning{best.c_tile, best.c_mb, best.r_pb, best.r_g, best.grid1, best.grid2, best1, best2};
+  if (out)
+    *out = phd_tuning{best.c_tile, best.c_mb, best.r_pb, best.r_g, best.grid1, best.grid2, best.gate, best1, best2};
   return read_device_error(h);
 }
 

@@ -32,6 +32,7 @@ struct Tune {
   int r_g;       // pass 2: lanes sharing a particle (1, 2, 4, 8)
   int grid1;     // pass 1: CTA cap
   int grid2;     // pass 2: CTA cap
+  int gate;      // 1: skip pairs past the exact likelihood gate (bit-identical results)
 };
 __host__ __device__ __forceinline__ int row_tile(const Tune& t) { return kThreads / t.r_g * t.r_pb; }
 
@@ -365,6 +366,77 @@ __device__ __forceinline__ float qform_p(const LikP& L, unsigned long long z, un
   float e0, e1;
   f2_unpack(f2_mul(f2_pack(d0, d1), L.a01), e0, e1);
   return fmaf(e0, e0, e1 * e1);
+}
+
+// ---------------------------------------------------------------------------
+// Exact likelihood gate.  ex2.approx.ftz returns exactly 0 for an exponent
+// q > 126 (2^-q is below the smallest normal float and is flushed), and the
+// FP64 exp2 underflows to 0 beyond q = 1074: a pair with q >= gate_q<R>() adds
+// exactly nothing to any sum of the update.  A box around a tile's particles
+// in measurement space bounds q from below for every pair of the tile with a
+// measurement; pairs are skipped only when that bound reaches the gate (with
+// margin over 126 / 1074 for rounding), so every sum is bit-identical to the
+// ungated one.
+// ---------------------------------------------------------------------------
+template <class R> __host__ __device__ constexpr R gate_q();
+template <> __host__ __device__ constexpr float gate_q<float>() { return 130.0f; }
+template <> __host__ __device__ constexpr double gate_q<double>() { return 1100.0; }
+
+// Box of a tile in measurement space: [lo0, hi0] in the first coordinate;
+// the second as an interval [lo1, hi1] (linear sensor) or an arc of centre c1
+// and half-width hw1 (bearing; hw1 < 0: the tile spans more than a half
+// circle and the bearing gives no bound).
+template <class R> struct Box { R lo0, hi0, lo1, hi1; };
+
+// Lower bound of q over the box for measurement (z0, z1); b = log2(e)/(2 s^2).
+template <class R, int RB>
+__device__ __forceinline__ R box_qmin(const Box<R>& B, R b0, R b1, R z0, R z1) {
+  const R d0 = fmax(fmax(B.lo0 - z0, z0 - B.hi0), (R)0);
+  R d1;
+  if (RB) {
+    const R c = (R)0.5 * (B.lo1 + B.hi1), hw = (R)0.5 * (B.hi1 - B.lo1);
+    if (hw > (R)1.5707963267948966) {
+      d1 = 0;
+    } else {
+      const R two_pi = (R)6.283185307179586;
+      R t = z1 - c;
+      t = t - two_pi * rint(t / two_pi);
+      d1 = fmax(fabs(t) - hw, (R)0);
+    }
+  } else {
+    d1 = fmax(fmax(B.lo1 - z1, z1 - B.hi1), (R)0);
+  }
+  return fma(b1 * d1, d1, (b0 * d0) * d0);
+}
+
+// Block-wide box of the values each thread passes (threads with none pass
+// +inf / -inf); every thread gets the box.  Two barriers; `sh` holds 4 *
+// (blockDim / 32) reals.
+template <class R>
+__device__ __forceinline__ Box<R> block_box(R lo0, R hi0, R lo1, R hi1, R* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    lo0 = fmin(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+    hi0 = fmax(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+    lo1 = fmin(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+    hi1 = fmax(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+  }
+  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sh[wid] = lo0;
+    sh[nw + wid] = hi0;
+    sh[2 * nw + wid] = lo1;
+    sh[3 * nw + wid] = hi1;
+  }
+  __syncthreads();
+  Box<R> B{sh[0], sh[nw], sh[2 * nw], sh[3 * nw]};
+  for (int k = 1; k < nw; ++k) {
+    B.lo0 = fmin(B.lo0, sh[k]);
+    B.hi0 = fmax(B.hi0, sh[nw + k]);
+    B.lo1 = fmin(B.lo1, sh[2 * nw + k]);
+    B.hi1 = fmax(B.hi1, sh[3 * nw + k]);
+  }
+  return B;
 }
 
 // Pair exponent in the kernels' precision: packed FP32, or plain FP64.

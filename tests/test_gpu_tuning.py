@@ -135,3 +135,29 @@ def test_autotune_keeps_parity_and_statistics():
     _step(f, w, sc, 4, 1, rep)
     f.close()
     assert rep.compared_labels > 0
+
+
+@pytest.mark.parametrize("case", ["linear", "range_bearing"])
+def test_likelihood_gate_is_exact(case):
+    """The gate skips only pairs whose FP32 likelihood term is exactly 0 (the
+    exp2 result flushed to zero): the update's outputs are bit-identical with
+    the gate on or off, for every pass-2 shape."""
+    w, sc, cen, counts = _lin_case() if case == "linear" else _rb_case()
+    seed = 9 if case == "linear" else 4
+    noise = scenario.step_noise(seed, 0, w.num_pe, w.pe_cap, np.float32)
+    Z = np.asarray(sc.meas[0], np.float32)
+    for r_pb, r_g in [(1, 4), (2, 1), (1, 8)]:
+        outs = []
+        for gate in (0, 1):
+            f = _filter(w, seed, counts, cen, gate=gate, r_pb=r_pb, r_g=r_g, c_mb=2)
+            f.predict(noise)
+            f.update(Z)
+            C, mass = f.get_update()
+            _, wu = f.get_state()
+            outs.append((np.asarray(C), np.asarray(mass), [np.asarray(a) for a in wu]))
+            f.close()
+        (C0, m0, w0), (C1, m1, w1) = outs
+        assert np.array_equal(C0, C1)
+        assert np.array_equal(m0, m1)
+        for a, b in zip(w0, w1):
+            assert np.array_equal(a, b)
