@@ -282,7 +282,7 @@ def run_gpu(args, w, rank, world, local_rank):
         for k in range(steps_per_run // 2):
             f.step(torch.as_tensor(tune_sc.meas[k], dtype=dtype, device=dev), cap=cap, sync=False)
         tuning = f.autotune(3)
-        tuning = {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate")},
+        tuning = {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
                   "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
                   "setup_s": round(time.perf_counter() - t_tune, 3)}
         f.set_state(empty_x, empty_w)
@@ -557,7 +557,7 @@ def run_gpu_batch(args, rank, world, local_rank):
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                      "pairs_per_update": st["pairs"] / max(st["updates"], 1)},
         "gpu_launches": int(st["launches"]), "clocks": clocks,
-        "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate")},
+        "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
                    "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
                    "autotuned": not args.no_autotune, "setup_s": round(t_tune, 3)},
     }

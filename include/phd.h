@@ -405,13 +405,19 @@ phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
  *          in measurement space bounds q from below, and pairs whose bound is
  *          at least 130 (FP64: 1100) are skipped: they add exactly nothing,
  *          so results are bit-identical with the gate on or off;
+ *  order:  1 to walk the particles of passes 1 and 2 in the order of a 16 x 16
+ *          grid over measurement space (a stable counting sort of each
+ *          slice's predicted set before pass 1; the particles stay in their
+ *          slots), which keeps a tile's particles close so that the gate
+ *          skips most pairs; only the grouping of FP32 partial sums changes.
+ *          Default 1 on FP32 handles, 0 on FP64 handles;
  *  pass1_us, pass2_us: filled by phd_autotune with the measured mean duration
  *          of each pass in the chosen shape (0 elsewhere; ignored on input).
  * FP64 handles support c_mb 2 and (r_pb, r_g) = (1, 4) only.  The default is
  * c_tile 512, c_mb 4 (2 in FP64), (1, 4), grid1 = grid2 = 1216.  The fused
  * step kernel (phd_set_path) does not use these shapes. */
 typedef struct phd_tuning {
-    int32_t c_tile, c_mb, r_pb, r_g, grid1, grid2, gate;
+    int32_t c_tile, c_mb, r_pb, r_g, grid1, grid2, gate, order;
     float pass1_us, pass2_us;
 } phd_tuning;
 
@@ -423,7 +429,8 @@ phd_status phd_set_tuning(phd_handle *h, const phd_tuning *t);
 
 /* Autotuner: times every supported shape of pass 1 (c_tile x c_mb x grid1 in
  * {608, 1216, 2432}) and then of pass 2 ((r_pb, r_g) x grid2), each as the
- * mean of `reps` launches (1 .. 1000) after one untimed launch, on the
+ * mean of `reps` launches (1 .. 1000) after one untimed launch, then the whole
+ * update with the spatial order on and off (the gate setting is kept), on the
  * handle's current predicted set and measurements, i.e. the input of the last
  * update (call it after a representative step: the best shape depends on the
  * slices' particle and measurement counts).  Keeps the fastest shape of each

@@ -1,0 +1,142 @@
+// Spatial order of the predicted set for the update's pair passes.
+//
+// The exact likelihood gate skips a (tile, measurement) when every particle
+// of the tile is far from the measurement; it pays only when a tile's
+// particles are close to one another, which slot order does not give (births
+// are spread over the region and resampling keeps parents in slot order).
+// Before pass 1, every slice's predicted particles are put in the order of a
+// 16 x 16 grid over measurement space (Morton order of the cells), by a
+// stable counting sort: the permutation perm[sorted position] = slot is read
+// by passes 1 and 2 (the particles themselves stay where they are, and every
+// per-particle result goes to its own slot), so the only effect on results is
+// which particles share a pass-1 / pass-2 tile (the grouping of FP32 partial
+// sums); the order is deterministic.
+//
+// k_cell_hist: per chunk of kChunk particles: the cell key of each particle
+//   (from its measurement-space point) and the chunk's 256-bin histogram.
+// k_cell_scan: per slice: bin totals over its chunks, exclusive scan over the
+//   bins, then every (chunk, bin) start (bin-major, chunk-minor).
+// k_cell_scatter: per chunk: each particle's stable rank among the chunk's
+//   particles with its key (a warp's peers by match, earlier warps by their
+//   per-bin counts) gives its sorted position.
+#include "phd_internal.cuh"
+
+namespace phd {
+
+constexpr int kCells = 256;   // 16 x 16, Morton order
+
+__device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
+  int cx = (int)floorf((h0 - m.f_cell_o0) * m.f_cell_s0);
+  int cy = (int)floorf((h1 - m.f_cell_o1) * m.f_cell_s1);
+  cx = min(max(cx, 0), 15);
+  cy = min(max(cy, 0), 15);
+  int k = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) k |= (((cx >> b) & 1) << (2 * b)) | (((cy >> b) & 1) << (2 * b + 1));
+  return k;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
+  pdl_enter();
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ int hist[kCells];
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
+  const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
+  for (int c = blockIdx.x; c < pref[m.K]; c += gridDim.x) {
+    const int j = item_pe(pref, m.K, c);
+    const int i = (c - pref[j]) * kChunk + threadIdx.x;
+    for (int b = threadIdx.x; b < kCells; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    if (i < d.n_pred[j]) {
+      const long g = (long)j * m.pe_cap + i;
+      const H3<R> h = meas_h<R>(m, x[g], tab);
+      const int k = cell_key(m, (float)h.h0, (float)h.h1);
+      d.ckey[g] = (unsigned char)k;
+      atomicAdd(&hist[k], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kCells; b += blockDim.x) d.chist[(long)c * kCells + b] = hist[b];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kCells) k_cell_scan(Dev d, Model m) {
+  pdl_enter();
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ int wt[kCells / 32];
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  const int j = blockIdx.x;
+  const int b = threadIdx.x;
+  int tot = 0;
+  for (int c = pref[j]; c < pref[j + 1]; ++c) tot += d.chist[(long)c * kCells + b];
+  // exclusive scan of the bin totals
+  const int lane = b & 31, wid = b >> 5;
+  int incl = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wt[wid] = incl;
+  __syncthreads();
+  int run = incl - tot;
+  for (int k = 0; k < wid; ++k) run += wt[k];
+  for (int c = pref[j]; c < pref[j + 1]; ++c) {
+    const long a = (long)c * kCells + b;
+    const int v = d.chist[a];
+    d.chist[a] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kChunk) k_cell_scatter(Dev d, Model m) {
+  pdl_enter();
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ int wc[kChunk / 32][kCells];   // per-warp key counts, then their exclusive prefix over warps
+  item_prefix(d.n_pred, m.K, pref, kChunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = blockIdx.x; c < pref[m.K]; c += gridDim.x) {
+    const int j = item_pe(pref, m.K, c);
+    const int i = (c - pref[j]) * kChunk + threadIdx.x;
+    const bool live = i < d.n_pred[j];
+    const long g = (long)j * m.pe_cap + i;
+    const int key = live ? (int)d.ckey[g] : kCells;   // dead lanes form their own group
+    for (int t = threadIdx.x; t < (kChunk / 32) * kCells; t += blockDim.x) (&wc[0][0])[t] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int rank_w = __popc(peers & ((1u << lane) - 1u));
+    if (live && rank_w == 0) wc[wid][key] = __popc(peers);
+    __syncthreads();
+    // exclusive prefix over warps, one bin per thread
+    for (int b = threadIdx.x; b < kCells; b += blockDim.x) {
+      int run = 0;
+      for (int w = 0; w < kChunk / 32; ++w) {
+        const int v = wc[w][b];
+        wc[w][b] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    if (live) {
+      const int dst = d.chist[(long)c * kCells + key] + wc[wid][key] + rank_w;
+      d.perm[(long)j * m.pe_cap + dst] = i;
+    }
+    __syncthreads();
+  }
+}
+
+template <class R>
+cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s) {
+  const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
+  const int gc = (int)(chunks < 152 * 4 ? (chunks > 0 ? chunks : 1) : 152 * 4);
+  launch_k(k_cell_hist<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
+  launch_k(k_cell_scan, dim3(m.K), dim3(kCells), 0, s, d, m);
+  launch_k(k_cell_scatter, dim3(gc), dim3(kChunk), 0, s, d, m);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_order<float>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_order<double>(const Dev&, const Model&, cudaStream_t);
+
+}  // namespace phd

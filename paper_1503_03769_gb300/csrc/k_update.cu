@@ -54,6 +54,9 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
   __shared__ R bsh[4 * (kThreads / 32)];
+  __shared__ int live[MC];             // the chunk's measurements past no gate
+  __shared__ int wcnt[kThreads / 32];
+  __shared__ int nlive;
   Box<R> box{0, 0, 0, 0};
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -73,8 +76,9 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       for (int i = threadIdx.x; i < TP; i += kThreads) {
         P4<R> q = {0, 0, 0, 0};
         if (i < cnt) {
-          const H3<R> h = meas_h<R>(m, x[base + i], tab);
-          q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
+          const long src = m.tune.order ? (long)j * m.pe_cap + d.perm[base + i] : base + i;
+          const H3<R> h = meas_h<R>(m, x[src], tab);
+          q = P4<R>{h.h0, h.h1, h.h1lo, w[src]};
           lo0 = fmin(lo0, h.h0);
           hi0 = fmax(hi0, h.h0);
           lo1 = fmin(lo1, h.h1);
@@ -88,52 +92,76 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
     }
     const int pbeg = chunk * MC;
     const int Mc = min(MC, M - pbeg);
-    const int G = (Mc + MB - 1) / MB;   // measurement groups (threads per split)
-    const int S = kThreads / G;         // splits of the tile
-    const int GM = G * MB;
-    const int g = threadIdx.x % G, sidx = threadIdx.x / G;
-    R acc[MB];
-#pragma unroll
-    for (int k = 0; k < MB; ++k) acc[k] = 0;
-    if (sidx < S) {
-      R z0[MB], z1[MB];
-      bool live = false;   // some measurement of this thread can reach the tile
-#pragma unroll
-      for (int k = 0; k < MB; ++k) {
-        const int p = g + k * G;
-        const V2<R> z = p < Mc ? Z[pbeg + p] : V2<R>{0, 0};
-        z0[k] = z.a;
-        z1[k] = z.b;
-        live = live || (p < Mc && (!m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>()));
+    // the chunk's measurements that can reach the tile, in order (all of them
+    // with the gate off); the pair work is spread over the live ones only
+    {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      bool keep = false;
+      if ((int)threadIdx.x < Mc) {
+        const V2<R> z = Z[pbeg + threadIdx.x];
+        keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>();
       }
-      int i = live ? sidx : cnt;
-      for (; i + S < cnt; i += 2 * S) {
-        const P4<R> qa = sp[i], qb = sp[i + S];
-#pragma unroll
-        for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
-#pragma unroll
-        for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
-      }
-      if (i < cnt) {
-        const P4<R> qa = sp[i];
-#pragma unroll
-        for (int k = 0; k < MB; ++k)
-          acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < MB; ++k) red[sidx * GM + g + k * G] = acc[k];
-    }
-    __syncthreads();
-    // the S splits of each measurement: fixed-shape pairwise tree
-    for (int width = S; width > 1;) {
-      const int half = (width + 1) >> 1;
-      for (int t = threadIdx.x; t < (width - half) * GM; t += kThreads) red[t] += red[t + half * GM];
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) wcnt[wid] = __popc(bal);
       __syncthreads();
-      width = half;
+      int before = 0, all = 0;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        before += k < wid ? wcnt[k] : 0;
+        all += wcnt[k];
+      }
+      if (keep) live[before + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
+      if (threadIdx.x == 0) nlive = all;
+      __syncthreads();
     }
-    for (int p = threadIdx.x; p < Mc; p += kThreads) d.colpart[(long)titem * m.m_max + pbeg + p] = (double)red[p];
+    const int Ml = nlive;
+    for (int p = threadIdx.x; p < Mc; p += kThreads) d.colpart[(long)titem * m.m_max + pbeg + p] = 0.0;
+    if (Ml > 0) {
+      const int G = (Ml + MB - 1) / MB;   // measurement groups (threads per split)
+      const int S = kThreads / G;         // splits of the tile
+      const int GM = G * MB;
+      const int g = threadIdx.x % G, sidx = threadIdx.x / G;
+      R acc[MB];
+#pragma unroll
+      for (int k = 0; k < MB; ++k) acc[k] = 0;
+      if (sidx < S) {
+        R z0[MB], z1[MB];
+#pragma unroll
+        for (int k = 0; k < MB; ++k) {
+          const int q = g + k * G;
+          const V2<R> z = q < Ml ? Z[pbeg + live[q]] : V2<R>{0, 0};
+          z0[k] = z.a;
+          z1[k] = z.b;
+        }
+        int i = sidx;
+        for (; i + S < cnt; i += 2 * S) {
+          const P4<R> qa = sp[i], qb = sp[i + S];
+#pragma unroll
+          for (int k = 0; k < MB; ++k)
+            acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+#pragma unroll
+          for (int k = 0; k < MB; ++k)
+            acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
+        }
+        if (i < cnt) {
+          const P4<R> qa = sp[i];
+#pragma unroll
+          for (int k = 0; k < MB; ++k)
+            acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < MB; ++k) red[sidx * GM + g + k * G] = acc[k];
+      }
+      __syncthreads();
+      // the S splits of each measurement: fixed-shape pairwise tree
+      for (int width = S; width > 1;) {
+        const int half = (width + 1) >> 1;
+        for (int t = threadIdx.x; t < (width - half) * GM; t += kThreads) red[t] += red[t + half * GM];
+        __syncthreads();
+        width = half;
+      }
+      for (int q = threadIdx.x; q < Ml; q += kThreads)
+        d.colpart[(long)titem * m.m_max + pbeg + live[q]] = (double)red[q];
+    }
     __syncthreads();
   }
 }
@@ -256,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const R miss = consts<R>(m).miss;
   const int il = threadIdx.x / G, g = threadIdx.x % G;
   __shared__ R bsh[4 * (kThreads / 32)];
-  __shared__ unsigned int gmask[kMaxM / 32];   // bit p: measurement p cannot reach the tile
+  __shared__ int wcnt[kThreads / 32];
+  int* lidx = reinterpret_cast<int*>(zs + m.m_max);   // [m_max] the gate's survivors
   int staged = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
@@ -271,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       const int i = tile * TPR + k * GR + il;
       h0[k] = h1[k] = hl[k] = wi[k] = 0;
       if (i < n) {
-        const long gi = (long)j * m.pe_cap + i;
+        const long gi = (long)j * m.pe_cap + (m.tune.order ? d.perm[(long)j * m.pe_cap + i] : i);
         const H3<R> h = meas_h<R>(m, x[gi], tab);
         h0[k] = h.h0;
         h1[k] = h.h1;
@@ -293,35 +322,67 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       __syncthreads();
       staged = j;
     }
-    // measurements whose pairs with every particle of the tile are past the gate
+    // the measurements that can reach the tile, in order (the gate's survivors)
     const Box<R> box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
-    for (int p0 = threadIdx.x & ~31; p0 < M; p0 += kThreads) {
-      const int p = p0 + (threadIdx.x & 31);
-      const bool gated = m.tune.gate && p < M && box_qmin<R, RB>(box, LB.b0, LB.b1, zs[p].z0, zs[p].z1) >= gate_q<R>();
-      const unsigned int bits = __ballot_sync(0xffffffffu, gated);
-      if ((threadIdx.x & 31) == 0) gmask[p0 >> 5] = bits;
+    int nl = M;
+    if (m.tune.gate) {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      int base_w = 0;
+      for (int p0 = 0; p0 < M; p0 += kThreads) {
+        const int p = p0 + (int)threadIdx.x;
+        const bool keep = p < M && box_qmin<R, RB>(box, LB.b0, LB.b1, zs[p].z0, zs[p].z1) < gate_q<R>();
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int k = 0; k < kThreads / 32; ++k) {
+          before += k < wid ? wcnt[k] : 0;
+          all += wcnt[k];
+        }
+        if (keep) lidx[base_w + before + __popc(bal & ((1u << lane) - 1u))] = p;
+        base_w += all;
+        __syncthreads();
+      }
+      nl = base_w;
     }
-    __syncthreads();
     R a0[PB], a1[PB];
 #pragma unroll
     for (int k = 0; k < PB; ++k) a0[k] = a1[k] = 0;
-    int p = g;
-    for (; p + G < M; p += 2 * G) {
-      // a pair of measurements both past the gate adds exactly nothing
-      if (((gmask[p >> 5] >> (p & 31)) & (gmask[(p + G) >> 5] >> ((p + G) & 31)) & 1u) != 0u) continue;
-      const Z4<R> za = zs[p], zb = zs[p + G];
+    if (nl == M) {
+      int p = g;
+      for (; p + G < M; p += 2 * G) {
+        const Z4<R> za = zs[p], zb = zs[p + G];
 #pragma unroll
-      for (int k = 0; k < PB; ++k)
-        a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+        for (int k = 0; k < PB; ++k)
+          a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
 #pragma unroll
-      for (int k = 0; k < PB; ++k)
-        a1[k] = fma(exp2_neg(Q(zb.z0, zb.z1, h0[k], h1[k], hl[k])), zb.g, a1[k]);
-    }
-    if (p < M) {
-      const Z4<R> za = zs[p];
+        for (int k = 0; k < PB; ++k)
+          a1[k] = fma(exp2_neg(Q(zb.z0, zb.z1, h0[k], h1[k], hl[k])), zb.g, a1[k]);
+      }
+      if (p < M) {
+        const Z4<R> za = zs[p];
 #pragma unroll
-      for (int k = 0; k < PB; ++k)
-        a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+        for (int k = 0; k < PB; ++k)
+          a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+      }
+    } else {
+      // the survivors only, each in the lane and accumulator the full loop
+      // gives it (p = g mod G, accumulator by the parity of p / G): the sums
+      // are those of the full loop without its exact zeros
+      for (int e = 0; e < nl; ++e) {
+        const int p = lidx[e];
+        if (p % G != g) continue;
+        const Z4<R> za = zs[p];
+        if ((p / G) & 1) {
+#pragma unroll
+          for (int k = 0; k < PB; ++k)
+            a1[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a1[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < PB; ++k)
+            a0[k] = fma(exp2_neg(Q(za.z0, za.z1, h0[k], h1[k], hl[k])), za.g, a0[k]);
+        }
+      }
     }
     R sv = 0, mv = 0;
 #pragma unroll
@@ -332,7 +393,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       const int i = tile * TPR + k * GR + il;
       if (g == 0 && i < n) {
         const R wv = (miss + acc) * wi[k];
-        wu[(long)j * m.pe_cap + i] = wv;
+        wu[(long)j * m.pe_cap + (m.tune.order ? d.perm[(long)j * m.pe_cap + i] : i)] = wv;
         sv += wv;
         mv = wv > mv ? wv : mv;
       }
@@ -417,6 +478,7 @@ Tune default_tune(bool fp64) {
   t.grid1 = 152 * 8;
   t.grid2 = 152 * 8;
   t.gate = 1;
+  t.order = fp64 ? 0 : 1;
   return t;
 }
 
@@ -424,6 +486,7 @@ bool tune_supported(const Tune& t, bool fp64) {
   if (t.c_tile != 256 && t.c_tile != 512 && t.c_tile != 1024) return false;
   if (t.grid1 < 1 || t.grid2 < 1 || t.grid1 > 152 * 64 || t.grid2 > 152 * 64) return false;
   if (t.gate != 0 && t.gate != 1) return false;
+  if (t.order != 0 && t.order != 1) return false;
   if (fp64) return t.c_mb == 2 && t.r_pb == 1 && t.r_g == 4;
   if (t.c_mb != 1 && t.c_mb != 2 && t.c_mb != 4) return false;
   const int pg = t.r_pb * 16 + t.r_g;
@@ -443,7 +506,8 @@ template <class R, int RB, int PB, int G>
 static void rowsum_go(const Dev& d, const Model& m, cudaStream_t s) {
   const int tpr = kThreads / G * PB;
   const long tiles = (long)m.K * ((m.pe_cap + tpr - 1) / tpr);
-  launch_k(k_rowsum<R, RB, PB, G>, dim3(grid_cap(tiles, m.tune.grid2)), dim3(kThreads), sizeof(Z4<R>) * (size_t)m.m_max, s, d, m);
+  launch_k(k_rowsum<R, RB, PB, G>, dim3(grid_cap(tiles, m.tune.grid2)), dim3(kThreads),
+           (sizeof(Z4<R>) + sizeof(int)) * (size_t)m.m_max, s, d, m);
 }
 
 template <class R, int RB>
@@ -463,7 +527,7 @@ static cudaError_t prepare_rowsum(size_t sm) {
 
 template <class R>
 cudaError_t prepare_kernels(const Model& m) {
-  const size_t sm = sizeof(Z4<R>) * (size_t)m.m_max;
+  const size_t sm = (sizeof(Z4<R>) + sizeof(int)) * (size_t)m.m_max;
   cudaError_t e = prepare_rowsum<R, 0>(sm);
   if (e == cudaSuccess) e = prepare_rowsum<R, 1>(sm);
   if (e == cudaSuccess) e = prepare_extract<R>();
@@ -525,7 +589,8 @@ cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s) {
 
 template <class R>
 cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
-  cudaError_t e = launch_colsum<R>(d, m, s);
+  cudaError_t e = m.tune.order ? launch_order<R>(d, m, s) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_colsum<R>(d, m, s);
   if (e == cudaSuccess) e = launch_finalize<R>(d, m, s);
   if (e == cudaSuccess) e = launch_rowsum<R>(d, m, s);
   if (e == cudaSuccess) e = launch_mass(d, m, s);

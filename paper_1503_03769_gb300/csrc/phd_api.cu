@@ -129,6 +129,9 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.bcomp = cv.take<float>(Mm * 8);
   t.bcdf = cv.take<float>(Mm);
   t.bdone = cv.take<unsigned int>(1);
+  t.ckey = cv.take<unsigned char>(K * P);
+  t.chist = cv.take<int>(chunks * 256);
+  t.perm = cv.take<int>(K * P);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -230,6 +233,17 @@ Model make_model(const phd_config& c) {
   m.f_cy = (float)(0.5 * (c.region[2] + c.region[3]));
   m.f_ihx = (float)(2.0 / (c.region[1] - c.region[0]));
   m.f_ihy = (float)(2.0 / (c.region[3] - c.region[2]));
+  if (c.meas_model == PHD_MEAS_LINEAR) {
+    m.f_cell_o0 = (float)c.region[0];
+    m.f_cell_s0 = (float)(16.0 / (c.region[1] - c.region[0]));
+    m.f_cell_o1 = (float)c.region[2];
+    m.f_cell_s1 = (float)(16.0 / (c.region[3] - c.region[2]));
+  } else {
+    m.f_cell_o0 = 0.0f;
+    m.f_cell_s0 = (float)(16.0 / c.r_max);
+    m.f_cell_o1 = (float)-kPi;
+    m.f_cell_s1 = (float)(16.0 / (2.0 * kPi));
+  }
   return m;
 }
 
@@ -1020,13 +1034,13 @@ phd_status phd_reset_stats(phd_handle* h) {
 phd_status phd_get_tuning(phd_handle* h, phd_tuning* out) {
   if (!h || !out) return PHD_ERR_INVALID_ARG;
   const phd::Tune& t = h->m.tune;
-  *out = phd_tuning{t.c_tile, t.c_mb, t.r_pb, t.r_g, t.grid1, t.grid2, t.gate, 0.0f, 0.0f};
+  *out = phd_tuning{t.c_tile, t.c_mb, t.r_pb, t.r_g, t.grid1, t.grid2, t.gate, t.order, 0.0f, 0.0f};
   return PHD_OK;
 }
 
 phd_status phd_set_tuning(phd_handle* h, const phd_tuning* t) {
   if (!h || !t) return PHD_ERR_INVALID_ARG;
-  const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2, t->gate};
+  const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2, t->gate, t->order};
   if (!phd::tune_supported(u, is_fp64(h))) return fail(h, PHD_ERR_INVALID_ARG, "phd_set_tuning: unsupported shape");
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->m.tune = u;
@@ -1051,6 +1065,8 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
   float best1 = 0.0f, best2 = 0.0f;
   bool have1 = false, have2 = false;
   cudaError_t e = cudaSuccess;
+  // the passes read the spatial order when it is on: build it once first
+  if (base.order) e = fp64 ? phd::launch_order<double>(h->d, m, h->stream) : phd::launch_order<float>(h->d, m, h->stream);
   // pass 1 over its shapes
   for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti)
     for (int mi = 0; mi < 3 && e == cudaSuccess; ++mi)
@@ -1097,6 +1113,21 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
         best.grid2 = m.tune.grid2;
       }
     }
+  // spatial order on or off: the whole update timed both ways
+  if (e == cudaSuccess) {
+    float t_on = 0.0f, t_off = 0.0f;
+    m.tune = best;
+    m.tune.order = 1;
+    e = time_pass(h, reps, [&] {
+      return fp64 ? phd::launch_update<double>(h->d, m, h->stream) : phd::launch_update<float>(h->d, m, h->stream);
+    }, &t_on);
+    m.tune.order = 0;
+    if (e == cudaSuccess)
+      e = time_pass(h, reps, [&] {
+        return fp64 ? phd::launch_update<double>(h->d, m, h->stream) : phd::launch_update<float>(h->d, m, h->stream);
+      }, &t_off);
+    if (e == cudaSuccess) best.order = t_on < t_off ? 1 : 0;
+  }
   // leave the update's outputs as the chosen shapes compute them, and the
   // statistics as they were
   h->m.tune = best;
@@ -1110,7 +1141,8 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
     return cuda_fail(h, e, "phd_autotune");
   }
   if (out)
-    *out = phd_tuning{best.c_tile, best.c_mb, best.r_pb, best.r_g, best.grid1, best.grid2, best.gate, best1, best2};
+    *out = phd_tuning{best.c_tile, best.c_mb, best.r_pb, best.r_g, best.grid1,
+                      best.grid2, best.gate, best.order, best1, best2};
   return read_device_error(h);
 }
 

@@ -33,6 +33,7 @@ struct Tune {
   int grid1;     // pass 1: CTA cap
   int grid2;     // pass 2: CTA cap
   int gate;      // 1: skip pairs past the exact likelihood gate (bit-identical results)
+  int order;     // 1: passes 1 and 2 walk the particles in spatial (cell) order
 };
 __host__ __device__ __forceinline__ int row_tile(const Tune& t) { return kThreads / t.r_g * t.r_pb; }
 
@@ -71,6 +72,8 @@ struct Model {
   float f_blog;          // log2(area s_b^2 / (2 pi s_z0 s_z1))
   float f_win0, f_win1;  // feature window: 3 sigma per measurement coordinate
   float f_cx, f_cy, f_ihx, f_ihy;  // region centre and 1 / half-width
+  // 16 x 16 cell grid over measurement space (spatial order of the pair passes)
+  float f_cell_o0, f_cell_s0, f_cell_o1, f_cell_s1;
 };
 
 // Per-particle model constants in the kernel's precision.
@@ -148,6 +151,10 @@ struct Dev {
   float* bcomp;          // [m_max][8] proposal component constants
   float* bcdf;           // [m_max] mixture CDF
   unsigned int* bdone;   // [1] CTAs of k_birth_head finished (the last builds the table)
+  // spatial order of the predicted set
+  unsigned char* ckey;   // [K*pe_cap] cell key of each predicted particle
+  int* chist;            // [chunks][256] per-chunk cell counts, then their starts
+  int* perm;             // [K][pe_cap] slot of the particle at each sorted position
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
@@ -743,6 +750,7 @@ template <class R>
 cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* out_labels, int* counts, int cap,
                              cudaStream_t s);
 template <class R> cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s);
+template <class R> cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s);
 // the update's passes one at a time (the autotuner times pass 1 and pass 2 alone)
 template <class R> cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s);

@@ -59,7 +59,8 @@ class phd_stats(ctypes.Structure):
 class phd_tuning(ctypes.Structure):
     _fields_ = [("c_tile", ctypes.c_int32), ("c_mb", ctypes.c_int32), ("r_pb", ctypes.c_int32),
                 ("r_g", ctypes.c_int32), ("grid1", ctypes.c_int32), ("grid2", ctypes.c_int32),
-                ("gate", ctypes.c_int32), ("pass1_us", ctypes.c_float), ("pass2_us", ctypes.c_float)]
+                ("gate", ctypes.c_int32), ("order", ctypes.c_int32), ("pass1_us", ctypes.c_float),
+                ("pass2_us", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p
