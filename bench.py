@@ -368,7 +368,10 @@ def run_gpu(args, w, rank, world, local_rank):
                 "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(path),
                 "peak_source": "derived: 152 SMs x 32 MUFU ex2/clk x 2.07 GHz (one ex2 per pair)",
                 "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
-                "pairs_per_update": pairs / max(st["updates"], 1)}
+                "pairs_per_update": pairs / max(st["updates"], 1),
+                "pairs_evaluated_frac": st["pairs_evaluated"] / pairs if pairs else None,
+                "note": "achieved counts every particle x measurement pair (the metric's unit); pairs past "
+                        "the exact likelihood gate contribute exactly 0 and are skipped"}
 
     # whole runs in one launch each (phd_run): S scans per call, L2 flushed
     # between runs (outside the events)
@@ -555,7 +558,8 @@ def run_gpu_batch(args, rank, world, local_rank):
                      "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
                      "frac": achieved / EX2_PEAK_TEXP, "traffic": None,
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
-                     "pairs_per_update": st["pairs"] / max(st["updates"], 1)},
+                     "pairs_per_update": st["pairs"] / max(st["updates"], 1),
+                     "pairs_evaluated_frac": st["pairs_evaluated"] / st["pairs"] if st["pairs"] else None},
         "gpu_launches": int(st["launches"]), "clocks": clocks,
         "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
                    "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),

@@ -375,6 +375,8 @@ typedef struct phd_stats {
     double update_ms;        /* their summed device time (CUDA events), ms: the update
                                 stage's kernels on the staged path, the whole fused
                                 step kernel on the fused path */
+    uint64_t pairs_evaluated; /* pass-1 pairs actually evaluated (pairs of a tile with a
+                                 measurement past the exact likelihood gate are not) */
 } phd_stats;
 
 /* Read the counters accumulated since phd_init / phd_reset_stats.  Synchronises. */

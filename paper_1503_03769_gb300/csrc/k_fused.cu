@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     if (tid == 0) {
       d.n_pred[j] = np;
       atomicAdd(&d.stats[0], (unsigned long long)np * (unsigned long long)M);
+      atomicAdd(&d.stats[4], (unsigned long long)np * (unsigned long long)M);
       atomicAdd(&d.stats[1], (unsigned long long)np);
       if (j == 0) {
         atomicAdd(&d.stats[2], (unsigned long long)M);

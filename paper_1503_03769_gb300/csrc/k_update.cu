@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       __syncthreads();
     }
     const int Ml = nlive;
+    if (threadIdx.x == 0 && Ml > 0) atomicAdd(&d.stats[4], (unsigned long long)Ml * (unsigned long long)cnt);
     for (int p = threadIdx.x; p < Mc; p += kThreads) d.colpart[(long)titem * m.m_max + pbeg + p] = 0.0;
     if (Ml > 0) {
       const int G = (Ml + MB - 1) / MB;   // measurement groups (threads per split)

@@ -122,7 +122,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.lx = cv.take<int>(1);
   t.bar = cv.take<unsigned int>(2);
   t.step = cv.take<unsigned long long>(1);
-  t.stats = cv.take<unsigned long long>(4);
+  t.stats = cv.take<unsigned long long>(5);
   t.err = cv.take<int>(1);
   t.mlp_w = cv.take<char>(phd::kNParams, 2);
   t.bhead = cv.take<float>(Mm * 5);
@@ -1002,7 +1002,7 @@ phd_status phd_set_stage_timer(phd_handle* h, int32_t on) {
 
 phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
   if (!h || !out) return PHD_ERR_INVALID_ARG;
-  unsigned long long v[4] = {0, 0, 0, 0};
+  unsigned long long v[5] = {0, 0, 0, 0, 0};
   PHD_CUDA(h, cudaMemcpyAsync(v, h->d.stats, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   PHD_CUDA(h, drain_timer(h));
@@ -1010,6 +1010,7 @@ phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
   out->particles = v[1];
   out->measurements = v[2];
   out->updates = v[3];
+  out->pairs_evaluated = v[4];
   out->launches = h->launches;
   out->timed_updates = h->timer_calls;
   out->update_ms = h->timer_ms;
@@ -1019,7 +1020,7 @@ phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
 phd_status phd_reset_stats(phd_handle* h) {
   if (!h) return PHD_ERR_INVALID_ARG;
   PHD_CUDA(h, drain_timer(h));
-  PHD_CUDA(h, cudaMemsetAsync(h->d.stats, 0, 4 * sizeof(unsigned long long), h->stream));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.stats, 0, 5 * sizeof(unsigned long long), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->launches = 0;
   h->timer_ms = 0.0;
@@ -1052,7 +1053,7 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
   if (!h || reps < 1 || reps > 1000) return PHD_ERR_INVALID_ARG;
   if (!h->have_update) return fail(h, PHD_ERR_STATE, "phd_autotune: no update has run (nothing to time on)");
   const bool fp64 = is_fp64(h);
-  unsigned long long saved[4];
+  unsigned long long saved[5];
   PHD_CUDA(h, cudaMemcpyAsync(saved, h->d.stats, sizeof(saved), cudaMemcpyDeviceToHost, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   const phd::Tune base = h->m.tune;

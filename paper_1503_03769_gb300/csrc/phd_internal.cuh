@@ -142,7 +142,8 @@ struct Dev {
   double* bwd;           // [K] birth weight nu_b / J_j
   int* lmax;             // [K] largest resample count of slice j
   unsigned long long* step;  // [1] step counter (Philox counter word)
-  unsigned long long* stats; // [4] sums over updates: pairs, particles, measurements, updates
+  unsigned long long* stats; // [5] sums over updates: pairs, particles, measurements, updates,
+                             //     pass-1 pairs evaluated (the rest were past the gate)
   int* err;              // [1] device error bits
   int max_items;
   // measurement-driven birth

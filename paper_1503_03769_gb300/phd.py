@@ -53,7 +53,7 @@ class phd_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("particles", ctypes.c_uint64),
                 ("measurements", ctypes.c_uint64), ("updates", ctypes.c_uint64),
                 ("launches", ctypes.c_uint64), ("timed_updates", ctypes.c_uint64),
-                ("update_ms", ctypes.c_double)]
+                ("update_ms", ctypes.c_double), ("pairs_evaluated", ctypes.c_uint64)]
 
 
 class phd_tuning(ctypes.Structure):
