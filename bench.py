@@ -701,6 +701,82 @@ def run_gpu_learned(args, rank, world, local_rank):
     return 0
 
 
+def run_gpu_compare(args, rank, world, local_rank):
+    """The paper's three-way comparison on the 16-PE workload: the global
+    filter (PHD, all particles), the distributed scheme (DCPFPHD, 16 PEs, ring
+    exchange, CU fusion) and the global filter on 1/16 of the particles
+    (partPHD), each over the same scenarios; steps/s and OSPA (c = 100 m,
+    p = 2) per variant."""
+    import torch
+    from paper_1503_03769_gb300 import ParticlePHD
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wd = scenario.workload("dist16_10t")
+    K = wd.num_pe
+    variants = [("PHD", scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0)),
+                ("DCPFPHD", wd),
+                ("partPHD", scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0,
+                                              particles_per_target=wd.particles_per_target // K,
+                                              birth_count=wd.birth_count // K))]
+    runs = max(1, -(-args.steps // wd.steps))
+    seeds = [args.seed + r + 7919 * rank for r in range(runs)]
+    scen = {s_: scenario.simulate(wd, s_) for s_ in seeds}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, w in variants:
+        f = ParticlePHD(w, seed=5 + rank, device=f"cuda:{local_rank}")
+        Zd = {(s_, k): torch.as_tensor(scen[s_].meas[k], dtype=torch.float32, device=dev)
+              for s_ in seeds for k in range(w.steps)}
+        for k in range(min(args.warmup, w.steps)):
+            f.step(Zd[(seeds[0], k)], sync=False)
+        f.reset_stats()
+        torch.cuda.synchronize()
+        evs, logs = [], []
+        for s_ in seeds:
+            f.set_state([np.zeros((0, 4))] * f.K, [np.zeros(0)] * f.K)
+            for k in range(w.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st_, lb_, cnt = f.step(Zd[(s_, k)], sync=False)
+                e1.record()
+                evs.append((e0, e1))
+                logs.append((s_, k, st_.clone(), cnt.clone()))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        st = f.stats()
+        osp = []
+        for s_, k, st_, cnt in logs:
+            n = int(cnt.item())
+            est = st_[:n].double().cpu().numpy()[:, [0, 2]] if n else np.zeros((0, 2))
+            tr = scen[s_].truth[k]
+            osp.append(ospa_metric(est, tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+        res[name] = {"path": f.get_path(), "num_pe": w.num_pe, "particles_per_target": w.particles_per_target,
+                     "birth_count": w.birth_count, "steps_per_s": len(evs) / (ms * 1e-3),
+                     "ms_per_step": ms / len(evs), "pairs_per_s": st["pairs"] / (ms * 1e-3),
+                     "ospa_mean": float(np.mean(osp)), "launches": st["launches"], "steps": len(evs)}
+        f.close()
+    if rank != 0:
+        return 0
+    D = res["DCPFPHD"]
+    line = {
+        "metric": METRIC, "value": D["pairs_per_s"], "unit": UNIT, "n_gpus": world, "steps": D["steps"],
+        "warmup": args.warmup, "ms_per_step": D["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "dist16_compare", "targets": wd.n_targets, "clutter_rate": wd.clutter_rate,
+                   "runs": len(seeds), "scans_per_run": wd.steps, "birth_mass": wd.birth_mass,
+                   "l2": "flushed between timed steps (512 MiB write, outside the events)",
+                   "global_batch": 1, "seq_len": wd.steps, "parallelism": "replicas"},
+        "steps_per_s": D["steps_per_s"], "variants": res,
+        "speedup_vs_PHD": {k: res[k]["steps_per_s"] / res["PHD"]["steps_per_s"] for k in res},
+        "gpu_launches": int(D["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,6 +793,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.workload == "dist16_compare" and args.impl == "ours":
+        world = _env_int("WORLD_SIZE", 1)
+        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group(backend="nccl")
+        try:
+            return run_gpu_compare(args, rank, world, local_rank)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
     if args.workload == "rb_50t_learned" and args.impl == "ours":
         world = _env_int("WORLD_SIZE", 1)
         rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
@@ -745,7 +835,8 @@ def main():
             if world > 1:
                 import torch.distributed as dist
                 dist.destroy_process_group()
-    w = scenario.workload({"batch256": "linear4_fp64", "rb_50t_learned": "rb_50t"}.get(args.workload, args.workload))
+    w = scenario.workload({"batch256": "linear4_fp64", "rb_50t_learned": "rb_50t",
+                           "dist16_compare": "dist16_10t"}.get(args.workload, args.workload))
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     local_rank = _env_int("LOCAL_RANK", 0)

@@ -411,7 +411,8 @@ phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
  *          grid over measurement space (a stable counting sort of each
  *          slice's predicted set before pass 1; the particles stay in their
  *          slots), which keeps a tile's particles close so that the gate
- *          skips most pairs; only the grouping of FP32 partial sums changes.
+ *          skips most pairs; the extraction's label sums (pass 3) walk the
+ *          same tiles.  Only the grouping of FP32 partial sums changes.
  *          Default 1 on FP32 handles, 0 on FP64 handles;
  *  pass1_us, pass2_us: filled by phd_autotune with the measured mean duration
  *          of each pass in the chosen shape (0 elsewhere; ignored on input).
@@ -426,7 +427,9 @@ typedef struct phd_tuning {
 phd_status phd_get_tuning(phd_handle *h, phd_tuning *out);
 
 /* Select a shape.  Synchronises the stream (captured step graphs are rebuilt
- * on the next step).  PHD_ERR_INVALID_ARG for an unsupported shape. */
+ * on the next step).  PHD_ERR_INVALID_ARG for an unsupported shape;
+ * PHD_ERR_STATE for a change of `order` between phd_update and the step's
+ * phd_resample (the extraction reads the order the update built). */
 phd_status phd_set_tuning(phd_handle *h, const phd_tuning *t);
 
 /* Autotuner: times every supported shape of pass 1 (c_tile x c_mb x grid1 in

@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   const int TP = m.tune.c_tile;
   P4<R>* sp = reinterpret_cast<P4<R>*>(smem_raw);   // [TP]
   St4<R>* sx = reinterpret_cast<St4<R>*>(sp + TP);  // [TP]
+  int* lr = reinterpret_cast<int*>(sx + TP);        // [m_max] selected ranks past no gate
+  __shared__ R bsh[4 * (kThreads / 32)];
+  __shared__ int wcnt[kThreads / 32];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref, TP);
   const int total = pref[K];
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
+  const Lik<R> LB = make_lik<R>(m);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = item_pe(pref, K, item);
     const int ns = d.nsel[j];
@@ -110,19 +114,53 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
     const long base = (long)j * m.pe_cap + (long)tile * TP;
     const int cnt = min(TP, d.n_pred[j] - tile * TP);
     __syncthreads();
+    const R inf = (R)INFINITY;
+    R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
     for (int i = threadIdx.x; i < TP; i += kThreads) {
       P4<R> q = {0, 0, 0, 0};
       St4<R> st = {0, 0, 0, 0};
       if (i < cnt) {
-        st = x[base + i];
+        // the pass-1 tiles: the spatial order when the update built it
+        const long src = m.tune.order ? (long)j * m.pe_cap + d.perm[base + i] : base + i;
+        st = x[src];
         const H3<R> h = meas_h<R>(m, st, tab);
-        q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
+        q = P4<R>{h.h0, h.h1, h.h1lo, w[src]};
+        lo0 = fmin(lo0, h.h0);
+        hi0 = fmax(hi0, h.h0);
+        lo1 = fmin(lo1, h.h1);
+        hi1 = fmax(hi1, h.h1);
       }
       sp[i] = q;
       sx[i] = st;
     }
-    __syncthreads();
-    const int ng = (ns + kSelLB - 1) / kSelLB;   // label groups
+    const Box<R> box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
+    // every selected label's partial is written: zeros first, then the
+    // labels that can reach the tile (the gate's survivors, in rank order)
+    for (int t = threadIdx.x; t < ns * 5; t += kThreads) d.spart[(long)item * m.m_max * 5 + t] = 0.0;
+    int nl = 0;
+    {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (int r0 = 0; r0 < ns; r0 += kThreads) {
+        const int r = r0 + (int)threadIdx.x;
+        bool keep = false;
+        if (r < ns) {
+          const V2<R> z = Z[d.sel[j * m.m_max + r]];
+          keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>();
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int k = 0; k < kThreads / 32; ++k) {
+          before += k < wid ? wcnt[k] : 0;
+          all += wcnt[k];
+        }
+        if (keep) lr[nl + before + __popc(bal & ((1u << lane) - 1u))] = r;
+        nl += all;
+        __syncthreads();
+      }
+    }
+    const int ng = (nl + kSelLB - 1) / kSelLB;   // label groups
     int nsplit = 1;
     while (nsplit * 2 <= 32 && nsplit * 2 * ng <= kThreads) nsplit *= 2;
     const int gpr = kThreads / nsplit;           // label groups per round
@@ -135,9 +173,9 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
       for (int k = 0; k < kSelLB; ++k) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) s[k][c] = 0;
-        const int r = g * kSelLB + k;
+        const int q = g * kSelLB + k;
         V2<R> z = {0, 0};
-        if (g < ng && r < ns) z = Z[d.sel[j * m.m_max + r]];
+        if (g < ng && q < nl) z = Z[d.sel[j * m.m_max + lr[q]]];
         z0[k] = z.a;
         z1[k] = z.b;
         meas_point<R>(m, z, px[k], py[k]);
@@ -165,9 +203,9 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
       if (split == 0 && g < ng) {
 #pragma unroll
         for (int k = 0; k < kSelLB; ++k) {
-          const int r = g * kSelLB + k;
-          if (r < ns) {
-            double* o = d.spart + ((long)item * m.m_max + r) * 5;
+          const int q = g * kSelLB + k;
+          if (q < nl) {
+            double* o = d.spart + ((long)item * m.m_max + lr[q]) * 5;
 #pragma unroll
             for (int c = 0; c < 5; ++c) o[c] = (double)s[k][c];
           }
@@ -383,7 +421,7 @@ cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out
   {
     const long items = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
     const int g = (int)(items < 152L * 8 ? (items > 0 ? items : 1) : 152L * 8);
-    const size_t smem = (sizeof(P4<R>) + sizeof(St4<R>)) * (size_t)m.tune.c_tile;
+    const size_t smem = (sizeof(P4<R>) + sizeof(St4<R>)) * (size_t)m.tune.c_tile + sizeof(int) * (size_t)m.m_max;
     if (m.meas_model) launch_k(k_selsum<R, 1>, dim3(g), dim3(kThreads), smem, s, d, m);
     else launch_k(k_selsum<R, 0>, dim3(g), dim3(kThreads), smem, s, d, m);
   }
@@ -405,7 +443,7 @@ template cudaError_t launch_extract<double>(const Dev&, const Model&, double*, i
 namespace phd {
 template <class R>
 cudaError_t prepare_extract() {
-  const int sm = (int)((sizeof(P4<R>) + sizeof(St4<R>)) * 1024);
+  const int sm = (int)((sizeof(P4<R>) + sizeof(St4<R>)) * 1024 + sizeof(int) * kMaxM);
   cudaError_t e = cudaFuncSetAttribute(k_selsum<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selsum<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;

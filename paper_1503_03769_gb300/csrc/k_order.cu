@@ -14,8 +14,9 @@
 //
 // k_cell_hist: per chunk of kChunk particles: the cell key of each particle
 //   (from its measurement-space point) and the chunk's 256-bin histogram.
-// k_cell_scan: per slice: bin totals over its chunks, exclusive scan over the
-//   bins, then every (chunk, bin) start (bin-major, chunk-minor).
+// k_cell_scan: per slice: bin totals over its chunks (four threads per bin
+//   on quarters of the chunks), exclusive scan over the bins, then every
+//   (chunk, bin) start (bin-major, chunk-minor).
 // k_cell_scatter: per chunk: each particle's stable rank among the chunk's
 //   particles with its key (a warp's peers by match, earlier warps by their
 //   per-bin counts) gives its sorted position.
@@ -62,27 +63,48 @@ __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
   }
 }
 
-__global__ void __launch_bounds__(kCells) k_cell_scan(Dev d, Model m) {
+// Four threads per bin, each over a quarter of the slice's chunks (the
+// chunk loads of a quarter are independent and issued ahead).
+constexpr int kScanT = 4 * kCells;
+
+__global__ void __launch_bounds__(kScanT) k_cell_scan(Dev d, Model m) {
   pdl_enter();
   __shared__ int pref[kMaxPE + 1];
+  __shared__ int part[4][kCells];   // per-quarter bin counts, then their starts
   __shared__ int wt[kCells / 32];
   item_prefix(d.n_pred, m.K, pref, kChunk);
   const int j = blockIdx.x;
-  const int b = threadIdx.x;
+  const int b = threadIdx.x % kCells, qtr = threadIdx.x / kCells;
+  const int c0 = pref[j], nc = pref[j + 1] - pref[j];
+  const int q0 = c0 + (nc * qtr) / 4, q1 = c0 + (nc * (qtr + 1)) / 4;
   int tot = 0;
-  for (int c = pref[j]; c < pref[j + 1]; ++c) tot += d.chist[(long)c * kCells + b];
-  // exclusive scan of the bin totals
-  const int lane = b & 31, wid = b >> 5;
-  int incl = tot;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wt[wid] = incl;
+#pragma unroll 8
+  for (int c = q0; c < q1; ++c) tot += d.chist[(long)c * kCells + b];
+  part[qtr][b] = tot;
   __syncthreads();
-  int run = incl - tot;
-  for (int k = 0; k < wid; ++k) run += wt[k];
-  for (int c = pref[j]; c < pref[j + 1]; ++c) {
+  if (qtr == 0) {
+    // bin totals, exclusive scan over the bins, then each quarter's start
+    const int t0 = part[0][b], t1 = part[1][b], t2 = part[2][b], t3 = part[3][b];
+    const int all = t0 + t1 + t2 + t3;
+    const int lane = b & 31, wid = b >> 5;
+    int incl = all;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wt[wid] = incl;
+    __syncwarp();
+    asm volatile("bar.sync 1, %0;" ::"r"(kCells));   // the kCells threads of quarter 0
+    int base = incl - all;
+    for (int k = 0; k < wid; ++k) base += wt[k];
+    part[0][b] = base;
+    part[1][b] = base + t0;
+    part[2][b] = base + t0 + t1;
+    part[3][b] = base + t0 + t1 + t2;
+  }
+  __syncthreads();
+  int run = part[qtr][b];
+  for (int c = q0; c < q1; ++c) {
     const long a = (long)c * kCells + b;
     const int v = d.chist[a];
     d.chist[a] = run;
@@ -131,7 +153,7 @@ cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s) {
   const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
   const int gc = (int)(chunks < 152 * 4 ? (chunks > 0 ? chunks : 1) : 152 * 4);
   launch_k(k_cell_hist<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
-  launch_k(k_cell_scan, dim3(m.K), dim3(kCells), 0, s, d, m);
+  launch_k(k_cell_scan, dim3(m.K), dim3(kScanT), 0, s, d, m);
   launch_k(k_cell_scatter, dim3(gc), dim3(kChunk), 0, s, d, m);
   return cudaGetLastError();
 }

@@ -1043,6 +1043,9 @@ phd_status phd_set_tuning(phd_handle* h, const phd_tuning* t) {
   if (!h || !t) return PHD_ERR_INVALID_ARG;
   const phd::Tune u{t->c_tile, t->c_mb, t->r_pb, t->r_g, t->grid1, t->grid2, t->gate, t->order};
   if (!phd::tune_supported(u, is_fp64(h))) return fail(h, PHD_ERR_INVALID_ARG, "phd_set_tuning: unsupported shape");
+  // the extraction's pass 3 walks the order the update built
+  if (h->stage == kUpdated && u.order != h->m.tune.order)
+    return fail(h, PHD_ERR_STATE, "phd_set_tuning: the spatial order changes only between steps");
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->m.tune = u;
   destroy_graphs(h);

@@ -157,13 +157,41 @@ def test_likelihood_gate_is_exact(case):
             f.update(Z)
             C, mass = f.get_update()
             _, wu = f.get_state()
-            outs.append((np.asarray(C), np.asarray(mass), [np.asarray(a) for a in wu]))
+            f.extract()
+            ls, ll = f.get_local_estimates()
+            outs.append((np.asarray(C), np.asarray(mass), [np.asarray(a) for a in wu],
+                         [np.asarray(a) for a in ls], [np.asarray(a) for a in ll]))
             f.close()
-        (C0, m0, w0), (C1, m1, w1) = outs
+        (C0, m0, w0, s0, l0), (C1, m1, w1, s1, l1) = outs
         np.testing.assert_allclose(C1, C0, rtol=2e-6, atol=1e-30)
         np.testing.assert_allclose(m1, m0, rtol=2e-6)
         for a, b in zip(w0, w1):
             np.testing.assert_allclose(b, a, rtol=2e-6, atol=1e-12 * max(float(np.abs(a).max()), 1e-30))
+        # pass 3 (label sums of the extraction) gates labels per tile as well:
+        # same labels, estimates to FP32 summation rounding
+        assert sum(len(a) for a in l0) > 0
+        for a, b in zip(l0, l1):
+            np.testing.assert_array_equal(b, a)
+        for a, b in zip(s0, s1):
+            np.testing.assert_allclose(b, a, rtol=1e-5, atol=1e-3)
+
+
+def test_order_change_waits_for_the_step():
+    """The extraction walks the order the update built: switching it between
+    the update and the resample is refused, and allowed again after."""
+    from paper_1503_03769_gb300 import PhdError
+    w, sc, cen, counts = _lin_case()
+    f = _filter(w, 9, counts, cen, order=1)
+    f.predict(scenario.step_noise(9, 0, w.num_pe, w.pe_cap, np.float32))
+    f.update(np.asarray(sc.meas[0], np.float32))
+    with pytest.raises(PhdError):
+        f.set_tuning(order=0)
+    f.set_tuning(gate=1, c_tile=1024)   # other fields may change
+    f.extract()
+    f.resample(scenario.resample_u32(9, 0, w.num_pe), scenario.exchange_u32(9, 0, w.num_pe, w.pe_cap))
+    f.set_tuning(order=0)
+    assert f.get_tuning()["order"] == 0
+    f.close()
 
 
 @pytest.mark.parametrize("order", [0, 1])
