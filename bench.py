@@ -214,18 +214,38 @@ def run_reference(args, w, rank, world):
 # the GPU arm
 # ----------------------------------------------------------------------------
 
-def _traffic_from_profile(path):
-    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary,
-    if it was taken on the current kernel sources (else None)."""
+# Committed ncu summaries that carry per-update DRAM traffic: (summary file,
+# the kernel sources the counters were taken on).  The traffic is reported
+# only while those sources are unchanged.
+_TRAFFIC_PROFILES = {
+    ("fused", "dist16_10t"): ("k_step_fused_dist16_ncu.md", ("k_fused.cu", "phd_internal.cuh")),
+    ("staged", "dense_rb_100t"): ("update_dense_rb_100t_ncu.md",
+                                  ("k_update.cu", "k_order.cu", "phd_internal.cuh")),
+}
+UPDATE_KERNELS = "update stage (k_cell_hist, k_cell_scan, k_cell_scatter, k_colsum, k_finalize, k_rowsum, k_mass)"
+
+
+def kernel_sources_sha256(files):
     import hashlib
-    name = "k_step_fused_dist16_ncu.md" if path == "fused" else "update_dist16_ncu.md"
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1503_03769_gb300", "csrc")
+    for fn in files:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()
+
+
+def _traffic_from_profile(path, workload):
+    """Per-update DRAM bytes of the timed kernels from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    entry = _TRAFFIC_PROFILES.get((path, workload))
+    if entry is None:
+        return None
+    name, files = entry
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
-    txt = open(p).read()
-    want = None
-    traffic = None
-    for ln in txt.splitlines():
+    want = traffic = None
+    for ln in open(p).read().splitlines():
         if ln.startswith("source_sha256:"):
             want = ln.split(":", 1)[1].strip()
         if ln.startswith("traffic_bytes_per_update:"):
@@ -233,11 +253,7 @@ def _traffic_from_profile(path):
                 traffic = float(ln.split(":", 1)[1].strip())
             except ValueError:
                 traffic = None
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1503_03769_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
-    return traffic if want == h.hexdigest() else None
+    return traffic if want == kernel_sources_sha256(files) else None
 
 
 def run_gpu(args, w, rank, world, local_rank):
@@ -276,7 +292,11 @@ def run_gpu(args, w, rank, world, local_rank):
     # set-up on the staged path: the pair passes' launch shape is autotuned
     # half-way through a run of the same workload, then the state is reset
     tuning = None
-    if f.get_path() == "staged" and not args.no_autotune:
+    if f.get_path() == "staged" and args.tuning:
+        f.set_tuning(**args.tuning)
+        tuning = {**{k: f.get_tuning()[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
+                  "autotuned": False}
+    elif f.get_path() == "staged" and not args.no_autotune:
         t_tune = time.perf_counter()
         tune_sc = scenario.simulate(w, base_seed + 7777, steps=steps_per_run // 2 + 1)
         for k in range(steps_per_run // 2):
@@ -309,6 +329,7 @@ def run_gpu(args, w, rank, world, local_rank):
         torch.cuda.synchronize()
         clk = ClockSampler(gpu_id)
         clk.begin()
+        nvtx_push("timed")
         for r, k in seq[args.warmup:]:
             begin_run_if_needed(r, k)
             flush.zero_()
@@ -320,6 +341,7 @@ def run_gpu(args, w, rank, world, local_rank):
             evs.append((e0, e1))
             if k % 10 == 0:
                 est_log.append((r, k, s.clone(), c.clone()))
+        nvtx_pop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -361,11 +383,10 @@ def run_gpu(args, w, rank, world, local_rank):
     path = f.get_path()
     upd_ms = st["update_ms"]
     achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
-    kname = ("k_step_fused (whole step, one CTA per PE)" if path == "fused"
-             else "update stage (k_colsum, k_finalize, k_rowsum, k_mass)")
+    kname = "k_step_fused (whole step, one CTA per PE)" if path == "fused" else UPDATE_KERNELS
     roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
-                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(path),
+                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(path, w.name),
                 "peak_source": "derived: 152 SMs x 32 MUFU ex2/clk x 2.07 GHz (one ex2 per pair)",
                 "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                 "pairs_per_update": pairs / max(st["updates"], 1),
@@ -493,7 +514,11 @@ def run_gpu_batch(args, rank, world, local_rank):
     t_tune = time.perf_counter()
     for k in range(steps_per_run // 2):
         b.batch_step(packed=packed[k % len(packed)], cap=cap, sync=False)
-    tuning = b.autotune(3) if not args.no_autotune else b.get_tuning()
+    if args.tuning:
+        b.set_tuning(**args.tuning)
+        tuning = b.get_tuning()
+    else:
+        tuning = b.autotune(3) if not args.no_autotune else b.get_tuning()
     t_tune = time.perf_counter() - t_tune
     b.set_state(empty_x, empty_w)
     b.set_stage_timer(True)
@@ -514,6 +539,7 @@ def run_gpu_batch(args, rank, world, local_rank):
     clk = ClockSampler(gpu_id)
     clk.begin()
     evs = []
+    nvtx_push("timed")
     for k in range(args.warmup, total):
         if k % steps_per_run == 0:
             b.set_state(empty_x, empty_w)
@@ -524,6 +550,7 @@ def run_gpu_batch(args, rank, world, local_rank):
         b.batch_step(packed=packed[k % steps_per_run], cap=cap, sync=False)
         e1.record()
         evs.append((e0, e1))
+    nvtx_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -554,7 +581,7 @@ def run_gpu_batch(args, rank, world, local_rank):
                    "global_batch": R, "seq_len": steps_per_run, "parallelism": "replicas"},
         "run_steps_per_s": world * R * args.steps / (ms * 1e-3),
         "per_run_latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
-        "roofline": {"bound": "alu", "kernel": "update stage (k_colsum, k_finalize, k_rowsum, k_mass)",
+        "roofline": {"bound": "alu", "kernel": UPDATE_KERNELS,
                      "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
                      "frac": achieved / EX2_PEAK_TEXP, "traffic": None,
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
@@ -563,7 +590,7 @@ def run_gpu_batch(args, rank, world, local_rank):
         "gpu_launches": int(st["launches"]), "clocks": clocks,
         "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
                    "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
-                   "autotuned": not args.no_autotune, "setup_s": round(t_tune, 3)},
+                   "autotuned": not (args.no_autotune or args.tuning), "setup_s": round(t_tune, 3)},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -692,7 +719,7 @@ def run_gpu_learned(args, rank, world, local_rank):
                           "note": "fastest plain-birth variant with OSPA within 5 % of the learned proposal's"},
         "training": {"pairs": int(X.shape[0]), "extracted_frac": float(T[:, 0].mean()), "adam_steps": 1500,
                      "loss": loss, "setup_s": round(t_train, 2)},
-        "roofline": {"bound": "alu", "kernel": "update stage (k_colsum, k_finalize, k_rowsum, k_mass)",
+        "roofline": {"bound": "alu", "kernel": UPDATE_KERNELS,
                      "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
                      "frac": achieved / EX2_PEAK_TEXP, "traffic": None},
         "gpu_launches": int(L["launches"]), "clocks": clocks,
@@ -777,6 +804,34 @@ def run_gpu_compare(args, rank, world, local_rank):
     return 0
 
 
+def _parse_tuning(text):
+    keys = ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")
+    out = {}
+    for part in text.split(","):
+        k, _, v = part.partition("=")
+        if k.strip() not in keys:
+            raise argparse.ArgumentTypeError(f"unknown tuning key {k!r}; known: {', '.join(keys)}")
+        out[k.strip()] = int(v)
+    return out
+
+
+def nvtx_push(name):
+    """NVTX range around a timed region (lets a profiler select its kernels)."""
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    import torch
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -791,6 +846,9 @@ def main():
                     help="time scans from this index of every run (earlier ones replayed untimed); "
                          "default 50 for dense_rb_100t, else 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", type=_parse_tuning, default=None,
+                    help="fixed launch shape of the pair passes instead of autotuning, "
+                         "e.g. c_tile=512,c_mb=4,r_pb=1,r_g=1,grid1=1216,grid2=608,gate=1,order=1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.workload == "dist16_compare" and args.impl == "ours":

@@ -232,7 +232,11 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
     const int j = (int)(gw / m.m_max);
     const int r = (int)(gw - (long)j * m.m_max);
     if (r >= d.nsel[j]) continue;   // uniform over the warp
+    // the label's measurement, fetched ahead of the partials
+    const int p = d.sel[j * m.m_max + r];
+    const V2<R> z = slice_Z<R>(d, j)[p];
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+#pragma unroll 4
     for (int it = pref[j] + lane; it < pref[j + 1]; it += 32) {
       const double* q = d.spart + ((long)it * m.m_max + r) * 5;
       a0 += q[0];
@@ -249,9 +253,8 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
       a4 += __shfl_down_sync(0xffffffffu, a4, o);
     }
     if (lane == 0) {
-      const int p = d.sel[j * m.m_max + r];
       R px, py;
-      meas_point<R>(m, slice_Z<R>(d, j)[p], px, py);
+      meas_point<R>(m, z, px, py);
       St4<R> o;
       if (a0 > 0.0) {
         if constexpr (sizeof(R) == 4) {

@@ -13,10 +13,11 @@
 // sums); the order is deterministic.
 //
 // k_cell_hist: per chunk of kChunk particles: the cell key of each particle
-//   (from its measurement-space point) and the chunk's 256-bin histogram.
-// k_cell_scan: per slice: bin totals over its chunks (four threads per bin
-//   on quarters of the chunks), exclusive scan over the bins, then every
-//   (chunk, bin) start (bin-major, chunk-minor).
+//   (from its measurement-space point) and the chunk's 256-bin histogram;
+//   the CTA that finishes a slice's last chunk then scans the slice: bin
+//   totals over its chunks (four threads per bin on quarters of the chunks),
+//   exclusive scan over the bins, then every (chunk, bin) start (bin-major,
+//   chunk-minor).
 // k_cell_scatter: per chunk: each particle's stable rank among the chunk's
 //   particles with its key (a warp's peers by match, earlier warps by their
 //   per-bin counts) gives its sorted position.
@@ -37,11 +38,66 @@ __device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
   return k;
 }
 
+static_assert(kChunk == 4 * kCells, "the slice scan uses four threads per bin");
+
+// Scan of slice j's chunk histograms by a whole CTA of kChunk threads (the
+// other CTAs' histograms read through L2), in place: chist[c][b] becomes the
+// sorted position of chunk c's first particle with key b.
+__device__ void scan_slice(const Dev& d, int c0, int nc, int (*part)[kCells], int* wt) {
+  const int b = threadIdx.x % kCells, qtr = threadIdx.x / kCells;
+  const int q0 = c0 + (nc * qtr) / 4, q1 = c0 + (nc * (qtr + 1)) / 4;
+  constexpr int U = 8;   // chunk loads in flight per thread
+  int tot = 0;
+  for (int c = q0; c < q1; c += U) {
+    int v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = c + u < q1 ? __ldcg(d.chist + (long)(c + u) * kCells + b) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) tot += v[u];
+  }
+  part[qtr][b] = tot;
+  __syncthreads();
+  if (qtr == 0) {
+    // bin totals, exclusive scan over the bins, then each quarter's start
+    const int t0 = part[0][b], t1 = part[1][b], t2 = part[2][b], t3 = part[3][b];
+    const int all = t0 + t1 + t2 + t3;
+    const int lane = b & 31, wid = b >> 5;
+    int incl = all;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wt[wid] = incl;
+    asm volatile("bar.sync 1, %0;" ::"r"(kCells));   // the kCells threads of quarter 0
+    int base = incl - all;
+    for (int k = 0; k < wid; ++k) base += wt[k];
+    part[0][b] = base;
+    part[1][b] = base + t0;
+    part[2][b] = base + t0 + t1;
+    part[3][b] = base + t0 + t1 + t2;
+  }
+  __syncthreads();
+  int run = part[qtr][b];
+  for (int c = q0; c < q1; c += U) {
+    int v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = c + u < q1 ? __ldcg(d.chist + (long)(c + u) * kCells + b) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c + u < q1) d.chist[(long)(c + u) * kCells + b] = run;
+      run += v[u];
+    }
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
   pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   __shared__ int hist[kCells];
+  __shared__ int part[4][kCells];   // scan: per-quarter bin counts, then their starts
+  __shared__ int wt[kCells / 32];
+  __shared__ int last_chunk;
   item_prefix(d.n_pred, m.K, pref, kChunk);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
@@ -60,55 +116,17 @@ __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
     __syncthreads();
     for (int b = threadIdx.x; b < kCells; b += blockDim.x) d.chist[(long)c * kCells + b] = hist[b];
     __syncthreads();
-  }
-}
-
-// Four threads per bin, each over a quarter of the slice's chunks (the
-// chunk loads of a quarter are independent and issued ahead).
-constexpr int kScanT = 4 * kCells;
-
-__global__ void __launch_bounds__(kScanT) k_cell_scan(Dev d, Model m) {
-  pdl_enter();
-  __shared__ int pref[kMaxPE + 1];
-  __shared__ int part[4][kCells];   // per-quarter bin counts, then their starts
-  __shared__ int wt[kCells / 32];
-  item_prefix(d.n_pred, m.K, pref, kChunk);
-  const int j = blockIdx.x;
-  const int b = threadIdx.x % kCells, qtr = threadIdx.x / kCells;
-  const int c0 = pref[j], nc = pref[j + 1] - pref[j];
-  const int q0 = c0 + (nc * qtr) / 4, q1 = c0 + (nc * (qtr + 1)) / 4;
-  int tot = 0;
-#pragma unroll 8
-  for (int c = q0; c < q1; ++c) tot += d.chist[(long)c * kCells + b];
-  part[qtr][b] = tot;
-  __syncthreads();
-  if (qtr == 0) {
-    // bin totals, exclusive scan over the bins, then each quarter's start
-    const int t0 = part[0][b], t1 = part[1][b], t2 = part[2][b], t3 = part[3][b];
-    const int all = t0 + t1 + t2 + t3;
-    const int lane = b & 31, wid = b >> 5;
-    int incl = all;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last_chunk = atomicAdd(d.hdone + j, 1u) == (unsigned)(pref[j + 1] - pref[j] - 1);
     }
-    if (lane == 31) wt[wid] = incl;
-    __syncwarp();
-    asm volatile("bar.sync 1, %0;" ::"r"(kCells));   // the kCells threads of quarter 0
-    int base = incl - all;
-    for (int k = 0; k < wid; ++k) base += wt[k];
-    part[0][b] = base;
-    part[1][b] = base + t0;
-    part[2][b] = base + t0 + t1;
-    part[3][b] = base + t0 + t1 + t2;
-  }
-  __syncthreads();
-  int run = part[qtr][b];
-  for (int c = q0; c < q1; ++c) {
-    const long a = (long)c * kCells + b;
-    const int v = d.chist[a];
-    d.chist[a] = run;
-    run += v;
+    __syncthreads();
+    if (last_chunk) {
+      __threadfence();
+      scan_slice(d, pref[j], pref[j + 1] - pref[j], part, wt);
+      if (threadIdx.x == 0) d.hdone[j] = 0u;
+    }
+    __syncthreads();
   }
 }
 
@@ -153,10 +171,11 @@ cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s) {
   const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
   const int gc = (int)(chunks < 152 * 4 ? (chunks > 0 ? chunks : 1) : 152 * 4);
   launch_k(k_cell_hist<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
-  launch_k(k_cell_scan, dim3(m.K), dim3(kScanT), 0, s, d, m);
   launch_k(k_cell_scatter, dim3(gc), dim3(kChunk), 0, s, d, m);
   return cudaGetLastError();
 }
+
+int n_order_launches() { return 2; }
 
 template cudaError_t launch_order<float>(const Dev&, const Model&, cudaStream_t);
 template cudaError_t launch_order<double>(const Dev&, const Model&, cudaStream_t);

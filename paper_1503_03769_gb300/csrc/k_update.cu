@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   }
 }
 
-// Per PE: N^j = sum of the pass-2 tile sums (fixed order), the largest
+// Per slice: N^j = sum of the pass-2 tile sums (fixed order), the largest
 // updated weight, and the resampling plan (L_j and the CDF scale).
 __global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
   pdl_enter();
@@ -587,6 +587,8 @@ cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s) {
   launch_k(k_mass, dim3(m.K), dim3(256), 0, s, d, m);
   return cudaGetLastError();
 }
+
+int n_update_launches(const Model& m) { return (m.tune.order ? n_order_launches() : 0) + 4; }
 
 template <class R>
 cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {

@@ -132,6 +132,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.ckey = cv.take<unsigned char>(K * P);
   t.chist = cv.take<int>(chunks * 256);
   t.perm = cv.take<int>(K * P);
+  t.hdone = cv.take<unsigned int>(K);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -305,7 +306,7 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
 }
 
 // kernels each stage launches (for the launch counter)
-constexpr int kNPredict = 1, kNStageZ = 1, kNUpdate = 4, kNExtract = 4, kNAdvance = 1, kNBirth = 2;
+constexpr int kNPredict = 1, kNStageZ = 1, kNExtract = 4, kNAdvance = 1, kNBirth = 2;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
 
 phd_status read_device_error(phd_handle* h) {
@@ -362,7 +363,7 @@ phd_status do_update(phd_handle* h, const void* Z, int M, bool z_in_workspace) {
   if (e != cudaSuccess) return cuda_fail(h, e, "stage_z");
   e = is_fp64(h) ? phd::launch_update<double>(h->d, h->m, h->stream) : phd::launch_update<float>(h->d, h->m, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "update");
-  h->launches += kNStageZ + kNUpdate;
+  h->launches += kNStageZ + phd::n_update_launches(h->m);
   h->stage = kUpdated;
   h->have_update = true;
   return PHD_OK;
@@ -527,8 +528,8 @@ phd_status run_step_body(phd_handle* h) {
     if (e == cudaSuccess) e = cudaGraphLaunch(h->g_post, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
-  h->launches += kNPredict + kNUpdate + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) + kNAdvance +
-                 (h->m.learned ? kNBirth : 0);
+  h->launches += kNPredict + phd::n_update_launches(h->m) + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) +
+                 kNAdvance + (h->m.learned ? kNBirth : 0);
   return PHD_OK;
 }
 
@@ -1257,7 +1258,7 @@ phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* 
       e = is_fp64(h) ? phd::launch_update<double>(h->d, h->m, h->stream)
                      : phd::launch_update<float>(h->d, h->m, h->stream);
       if (e != cudaSuccess) st = cuda_fail(h, e, "update");
-      h->launches += kNUpdate;
+      h->launches += phd::n_update_launches(h->m);
       h->stage = kUpdated;
     }
     if (st == PHD_OK) {

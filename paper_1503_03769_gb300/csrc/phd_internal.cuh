@@ -156,6 +156,7 @@ struct Dev {
   unsigned char* ckey;   // [K*pe_cap] cell key of each predicted particle
   int* chist;            // [chunks][256] per-chunk cell counts, then their starts
   int* perm;             // [K][pe_cap] slot of the particle at each sorted position
+  unsigned int* hdone;   // [K] cell-histogram chunks finished per slice (the last scans the slice)
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
@@ -752,6 +753,8 @@ cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* o
                              cudaStream_t s);
 template <class R> cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s);
+int n_update_launches(const Model& m);   // kernels one launch_update enqueues
+int n_order_launches();                  // kernels one launch_order enqueues
 // the update's passes one at a time (the autotuner times pass 1 and pass 2 alone)
 template <class R> cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s);
