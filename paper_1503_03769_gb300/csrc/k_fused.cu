@@ -191,15 +191,24 @@ __device__ __forceinline__ St4<R> fuse_mean(const St4<R>* __restrict__ est, cons
                                             int m_max, int votes, R px, R py) {
   if constexpr (sizeof(R) == 4) {
     R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll 8
-    for (int k = 0; k < K; ++k) {
-      const int r = srank[k * Pc + q];
-      if (r >= 0) {
-        const St4<R> e = est[k * m_max + r];
-        a0 += e.x - px;
-        a1 += e.vx;
-        a2 += e.y - py;
-        a3 += e.vy;
+    constexpr int U = 8;   // PEs' states in flight per thread
+    for (int k0 = 0; k0 < K; k0 += U) {
+      St4<R> e[U];
+      bool v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = k0 + u < K ? srank[(k0 + u) * Pc + q] : -1;
+        v[u] = r >= 0;
+        e[u] = v[u] ? est[(k0 + u) * m_max + r] : St4<R>{0, 0, 0, 0};
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (v[u]) {
+          a0 += e[u].x - px;
+          a1 += e[u].vx;
+          a2 += e[u].y - py;
+          a3 += e[u].vy;
+        }
       }
     }
     const R iv = (R)1 / (R)votes;
@@ -282,7 +291,7 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
   __syncthreads();
 }
 
-template <class R>
+template <class R, int RB>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FusedSmem SL = fused_smem<R>(m.pe_cap, m.m_max);
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   const int Jj = births_of(m.J, m.K, j);
   const unsigned long long step0 = *d.step;
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const Lik<R> L = make_lik<R>(m);
+  const PairQ<R, RB> PQ(m);   // pair exponent, sensor model fixed at compile time
   const Cst<R> cc = consts<R>(m);
   const R bw = birth_weight<R>(cc, m, j);
   const double cs = m.p_d * m.cnorm;
@@ -381,33 +390,36 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       const int pl = tid / nsplit, split = tid % nsplit;
       for (int p0 = 0; p0 < M; p0 += mper) {
         const int p = p0 + pl;
-        double acc = 0.0;
+        R acc = 0;
         if (p < M) {
-          // four independent partial sums (ILP); FP64 every 256 pairs
+          // four independent partial sums (ILP), folded every 256 pairs; the
+          // slice is one tile: its sums stay in the kernel's precision and
+          // the measurement's total goes to FP64 once (the FP64 pipe runs
+          // ~2 lanes/clk/SM)
           const V2<R> z = zs[p];
           R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
           int i = split, k = 0;
           for (; i + 3 * nsplit < np; i += 4 * nsplit) {
             const P4<R> q0 = sp[i], q1 = sp[i + nsplit], q2 = sp[i + 2 * nsplit], q3 = sp[i + 3 * nsplit];
-            a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
-            a1 = fma(exp2_neg(qform<R>(L, z.a, z.b, q1.h0, q1.h1, q1.h1lo)), q1.w, a1);
-            a2 = fma(exp2_neg(qform<R>(L, z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
-            a3 = fma(exp2_neg(qform<R>(L, z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
+            a0 = fma(exp2_neg(PQ(z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+            a1 = fma(exp2_neg(PQ(z.a, z.b, q1.h0, q1.h1, q1.h1lo)), q1.w, a1);
+            a2 = fma(exp2_neg(PQ(z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
+            a3 = fma(exp2_neg(PQ(z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
             if (++k == 64) {
-              acc += (double)((a0 + a1) + (a2 + a3));
+              acc += (a0 + a1) + (a2 + a3);
               a0 = a1 = a2 = a3 = 0;
               k = 0;
             }
           }
           for (; i < np; i += nsplit) {
             const P4<R> q0 = sp[i];
-            a0 = fma(exp2_neg(qform<R>(L, z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
+            a0 = fma(exp2_neg(PQ(z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
           }
-          acc += (double)((a0 + a1) + (a2 + a3));
+          acc += (a0 + a1) + (a2 + a3);
         }
         for (int o = nsplit >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, nsplit);
         if (split == 0 && p < M) {
-          const double c = acc * cs;
+          const double c = (double)acc * cs;
           Cd[p] = c;
           d.C[j * m.m_max + p] = c;
         }
@@ -442,10 +454,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       int p = 0, k = 0;
       for (; p + 3 < M; p += 4) {
         const V2<R> z0 = zs[p], z1 = zs[p + 1], z2 = zs[p + 2], z3 = zs[p + 3];
-        a0 = fma(exp2_neg(qform<R>(L, z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
-        a1 = fma(exp2_neg(qform<R>(L, z1.a, z1.b, q.h0, q.h1, q.h1lo)), ginv[p + 1], a1);
-        a2 = fma(exp2_neg(qform<R>(L, z2.a, z2.b, q.h0, q.h1, q.h1lo)), ginv[p + 2], a2);
-        a3 = fma(exp2_neg(qform<R>(L, z3.a, z3.b, q.h0, q.h1, q.h1lo)), ginv[p + 3], a3);
+        a0 = fma(exp2_neg(PQ(z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
+        a1 = fma(exp2_neg(PQ(z1.a, z1.b, q.h0, q.h1, q.h1lo)), ginv[p + 1], a1);
+        a2 = fma(exp2_neg(PQ(z2.a, z2.b, q.h0, q.h1, q.h1lo)), ginv[p + 2], a2);
+        a3 = fma(exp2_neg(PQ(z3.a, z3.b, q.h0, q.h1, q.h1lo)), ginv[p + 3], a3);
         if (++k == 32) {
           acc += (a0 + a1) + (a2 + a3);
           a0 = a1 = a2 = a3 = 0;
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
       for (; p < M; ++p) {
         const V2<R> z0 = zs[p];
-        a0 = fma(exp2_neg(qform<R>(L, z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
+        a0 = fma(exp2_neg(PQ(z0.a, z0.b, q.h0, q.h1, q.h1lo)), ginv[p], a0);
       }
       acc += (a0 + a1) + (a2 + a3);
       const R wv = (cc.miss + acc) * q.w;
@@ -511,7 +523,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           meas_point_f<R>(cc, m.meas_model, z, px, py);
           for (int i = split; i < np; i += nsplit) {
             const P4<R> q = sp[i];
-            const R ew = exp2_neg(qform<R>(L, z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
+            const R ew = exp2_neg(PQ(z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
             const St4<R> st = sx[i];
             s0 += ew;
             s1 = fma(ew, st.x - px, s1);
@@ -685,6 +697,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
 }
 
 template <class R>
+static const void* fused_fn(const Model& m) {
+  return m.meas_model ? (const void*)k_step_fused<R, 1> : (const void*)k_step_fused<R, 0>;
+}
+
+template <class R>
 size_t fused_smem_bytes(const Model& m) {
   return fused_smem<R>(m.pe_cap, m.m_max).total;
 }
@@ -698,10 +715,10 @@ bool fused_eligible(const Model& m, int device) {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return false;
   if (sm + 2048 > (size_t)optin) return false;
-  if (cudaFuncSetAttribute(k_step_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+  if (cudaFuncSetAttribute(fused_fn<R>(m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return false;
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_fused<R>, kFusedThreads, sm) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fused_fn<R>(m), kFusedThreads, sm) != cudaSuccess)
     return false;
   return (long)per * nsm >= m.K;
 }
@@ -715,7 +732,7 @@ cudaError_t launch_fused(const Dev& d, const Model& m, const void* Z, const int*
   // the grid barrier resets itself (the last arrival clears the count); it is
   // zeroed with the workspace and again whenever a device error is read
   void* args[] = {(void*)&d, (void*)&m, (void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)k_step_fused<R>, dim3(m.K), dim3(kFusedThreads), args, sm, s);
+  return cudaLaunchCooperativeKernel(fused_fn<R>(m), dim3(m.K), dim3(kFusedThreads), args, sm, s);
 }
 
 template bool fused_eligible<float>(const Model&, int);
