@@ -291,6 +291,112 @@ __device__ void cu_fuse(const Dev& d, const Model& m, int M, St4<R>* out, int* o
   __syncthreads();
 }
 
+// Step 4 shared by the K CTAs after the grid barrier, on the CTA's threads
+// tid0 .. blockDim.x - 1 (named barrier 2; warps below tid0 are busy with
+// the exchange swaps): every CTA stages all PEs' ranks and counts the votes
+// and the output positions of all labels, and forms the states of the valid
+// labels p with p mod K == j (CTA 0 writes the count).  The voters' states
+// of the CTA's own labels are fetched while the ranks are staged (one load
+// per (PE, label) pair, all in flight at once), then summed per label in PE
+// order as fuse_mean does.  Same output as cu_fuse on one CTA.
+// Labels per chunk of cu_fuse_share in `bytes` of scratch: K ranks per label
+// plus at most chunk + K states of the CTA's own labels (0: too small).
+template <class R>
+__device__ __forceinline__ int share_chunk(int K, size_t bytes, int NT) {
+  const long need0 = 16 + (long)sizeof(St4<R>) * K;
+  if ((long)bytes <= need0) return 0;
+  const long c = ((long)bytes - need0) / ((long)sizeof(int) * K + (long)sizeof(St4<R>));
+  return (int)(c < NT ? c : NT);
+}
+
+template <class R>
+__device__ void cu_fuse_share(const Dev& d, const Model& m, int j, int M, St4<R>* out, int* out_lab, int cap,
+                              int* count, int* wsum, unsigned char* scratch, int chunk, const V2<R>* zs,
+                              const Cst<R>& cc, int tid0) {
+  const int NT = (int)blockDim.x - tid0, lt = (int)threadIdx.x - tid0;
+  const int lane = threadIdx.x & 31, lw = lt >> 5, nw = NT >> 5;
+  const St4<R>* est = static_cast<const St4<R>*>(d.est_local);
+  const int K = m.K;
+  int* srank = reinterpret_cast<int*>(scratch);
+  St4<R>* sest = reinterpret_cast<St4<R>*>(scratch + ((sizeof(int) * K * chunk + 15) & ~(size_t)15));
+  int carry = 0;
+  for (int p0 = 0; p0 < M; p0 += chunk) {
+    const int Pc = min(chunk, M - p0);
+    // own labels of the chunk: p = p0 + q with p mod K == j, i.e. q = q0 + K o
+    const int q0 = ((j - p0) % K + K) % K;
+    const int no = q0 < Pc ? (Pc - 1 - q0) / K + 1 : 0;
+    for (int idx = lt; idx < K * Pc; idx += NT) {
+      const int k = idx / Pc, q = idx - k * Pc;
+      const int r = __ldcg(d.selrank + k * m.m_max + p0 + q);
+      srank[idx] = r;
+      if (q >= q0 && (q - q0) % K == 0 && r >= 0) sest[k * no + (q - q0) / K] = est[k * m.m_max + r];
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(NT));
+    const int q = lt, p = p0 + q;
+    int votes = 0;
+    if (q < Pc)
+      for (int k = 0; k < K; ++k) votes += srank[k * Pc + q] >= 0 ? 1 : 0;
+    const int valid = (q < Pc && 2 * votes > K) ? 1 : 0;
+    int incl = valid;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[lw] = incl;
+    asm volatile("bar.sync 2, %0;" ::"r"(NT));
+    if (lw == 0) {
+      int v = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < nw) wsum[lane] = v;
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(NT));
+    const int idx = carry + (lw > 0 ? wsum[lw - 1] : 0) + incl - valid;
+    if (valid && idx < cap && p % K == j) {
+      R px, py;
+      meas_point_f<R>(cc, m.meas_model, zs[p], px, py);
+      const int o = (q - q0) / K;
+      St4<R> f;
+      if constexpr (sizeof(R) == 4) {
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int k = 0; k < K; ++k) {
+          if (srank[k * Pc + q] >= 0) {
+            const St4<R> e = sest[k * no + o];
+            a0 += e.x - px;
+            a1 += e.vx;
+            a2 += e.y - py;
+            a3 += e.vy;
+          }
+        }
+        const R iv = (R)1 / (R)votes;
+        f = St4<R>{px + a0 * iv, a1 * iv, py + a2 * iv, a3 * iv};
+      } else {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int k = 0; k < K; ++k) {
+          if (srank[k * Pc + q] >= 0) {
+            const St4<R> e = sest[k * no + o];
+            a0 += (double)e.x;
+            a1 += (double)e.vx;
+            a2 += (double)e.y;
+            a3 += (double)e.vy;
+          }
+        }
+        f = St4<R>{(R)(a0 / votes), (R)(a1 / votes), (R)(a2 / votes), (R)(a3 / votes)};
+      }
+      out[idx] = f;
+      out_lab[idx] = p;
+    }
+    carry += wsum[nw - 1];
+    asm volatile("bar.sync 2, %0;" ::"r"(NT));   // srank, sest and wsum are reused
+  }
+  if (j == 0 && lt == 0) {
+    *count = carry;
+    *d.out_count = carry;
+  }
+}
+
 template <class R, int RB>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -644,37 +750,50 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       if (!grid_sync(d)) return;
       int lx = 0;
       if (xchg) {
-        int nmin = d.rs_L[0];
-        for (int k = 1; k < m.K; ++k) nmin = min(nmin, d.rs_L[k]);
+        // smallest resample count over the PEs: the K counts loaded at once
+        int nmin = INT_MAX;
+        for (int k = lane; k < m.K; k += 32) nmin = min(nmin, __ldcg(d.rs_L + k));
+        nmin = __reduce_min_sync(0xffffffffu, nmin);
         lx = (int)floor(m.exchange_frac * (double)nmin);
         if (j == 0 && tid == 0) *d.lx = lx;
-        if (lx > 0) {
-          // the draws are independent: make them in parallel, swap serially
-          unsigned int* ud = reinterpret_cast<unsigned int*>(cend);
-          for (int i = tid; i < Lc; i += T) perm[i] = i;
-          for (int t = tid; t < lx; t += T)
-            ud[t] = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
-          __syncthreads();
-          if (tid == 0) {
-            for (int t = 0; t < lx; ++t) {
-              const int r = t + (int)(((unsigned long long)ud[t] * (unsigned long long)(Lc - t)) >> 32);
-              const int tmp = perm[t];
-              perm[t] = perm[r];
-              perm[r] = tmp;
-            }
-          }
-          __syncthreads();
-          St4<R>* xo = static_cast<St4<R>*>(d.x_out);
-          R* wo = static_cast<R*>(d.w_out);
-          for (int t = tid; t < lx; t += T) {
-            const int slot = perm[t];
-            d.xslots[base + t] = slot;
-            xo[base + t] = gx[base + slot];
-            wo[base + t] = gw[base + slot];
+      }
+      // the exchange draws are independent: made in parallel; the swaps are
+      // serial (lane 0 of warp 0) while the other warps do this CTA's share
+      // of the CU fusion
+      unsigned int* ud = reinterpret_cast<unsigned int*>(cend);
+      if (lx > 0) {
+        for (int i = tid; i < Lc; i += T) perm[i] = i;
+        for (int t = tid; t < lx; t += T)
+          ud[t] = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
+      }
+      __syncthreads();
+      // (the predicted states' block, free after the gather, is the scratch)
+      const int fchunk = share_chunk<R>(m.K, sizeof(St4<R>) * (size_t)m.pe_cap, T - 32);
+      if (tid < 32) {
+        if (tid == 0) {
+          for (int t = 0; t < lx; ++t) {
+            const int r = t + (int)(((unsigned long long)ud[t] * (unsigned long long)(Lc - t)) >> 32);
+            const int tmp = perm[t];
+            perm[t] = perm[r];
+            perm[r] = tmp;
           }
         }
+      } else if (fchunk > 0) {
+        cu_fuse_share<R>(d, m, j, M, out_s, out_l, a.cap, a.out_count + s, ired, smem + SL.sx, fchunk, zs, cc, 32);
       }
-      if (j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap, zs, cc);
+      __syncthreads();
+      // scratch too small for a share (many PEs, tiny slices): CTA 0 fuses alone
+      if (fchunk <= 0 && j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap, zs, cc);
+      if (lx > 0) {
+        St4<R>* xo = static_cast<St4<R>*>(d.x_out);
+        R* wo = static_cast<R*>(d.w_out);
+        for (int t = tid; t < lx; t += T) {
+          const int slot = perm[t];
+          d.xslots[base + t] = slot;
+          xo[base + t] = gx[base + slot];
+          wo[base + t] = gw[base + slot];
+        }
+      }
       if (!grid_sync(d)) return;
       if (xchg && lx > 0) {
         const int from = (j + m.K - 1) % m.K;

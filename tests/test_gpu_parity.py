@@ -87,6 +87,25 @@ def test_distributed_linear_stages(ck_mode, path):
     assert rep.compared_labels > 0
 
 
+@pytest.mark.parametrize("pe_cap", [64, 128])
+def test_fused_many_pes_small_slices(pe_cap):
+    """64 PEs with slices of a few dozen particles on the fused path: CU
+    fusion is shared over the CTAs in chunks of a few labels (pe_cap 128,
+    M ~ 30 spans ~10 chunks) or, when a slice's scratch cannot hold a chunk
+    (pe_cap 64), done by CTA 0 alone; both must give the oracle's fusion."""
+    w = scenario.workload("dist16_10t", num_pe=64, n_targets=3, clutter_rate=20.0,
+                          particles_per_target=640, birth_count=640, birth_steps=(1, 1, 1),
+                          pe_cap=pe_cap, exchange_frac=0.1)
+    truth = scenario.simulate(w, 13, steps=3)
+    centres = np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)])
+    f = _filter(w, 13, "fused")
+    assert f.get_path() == "fused"
+    f.close()
+    rep = _run_stages(w, 13, 3, sc=truth, n_seed=[30 + (j % 7) for j in range(64)], centres=centres,
+                      path="fused")
+    assert rep.compared_labels > 0
+
+
 @pytest.mark.parametrize("path", ["staged", "fused"])
 def test_range_bearing_stages_many_measurements(path):
     """Range-bearing sensor, M ~ 330 (> one 256-thread round), 4 PEs, FP32."""
