@@ -728,26 +728,20 @@ def run_gpu_learned(args, rank, world, local_rank):
     return 0
 
 
-def run_gpu_compare(args, rank, world, local_rank):
-    """The paper's three-way comparison on the 16-PE workload: the global
-    filter (PHD, all particles), the distributed scheme (DCPFPHD, 16 PEs, ring
-    exchange, CU fusion) and the global filter on 1/16 of the particles
-    (partPHD), each over the same scenarios; steps/s and OSPA (c = 100 m,
-    p = 2) per variant."""
+def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p):
+    """The paper's three filters on the same scenarios of workload wd: the
+    global filter (PHD, all particles), the distributed scheme (DCPFPHD, wd's
+    PEs, ring exchange, CU fusion) and the global filter on 1/K of the
+    particles (partPHD); steps/s and OSPA (c = 100 m, order ospa_p) each."""
     import torch
     from paper_1503_03769_gb300 import ParticlePHD
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    wd = scenario.workload("dist16_10t")
     K = wd.num_pe
-    variants = [("PHD", scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0)),
+    variants = [("PHD", wd.with_(num_pe=1, exchange_frac=0.0)),
                 ("DCPFPHD", wd),
-                ("partPHD", scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0,
-                                              particles_per_target=wd.particles_per_target // K,
-                                              birth_count=wd.birth_count // K))]
-    runs = max(1, -(-args.steps // wd.steps))
-    seeds = [args.seed + r + 7919 * rank for r in range(runs)]
+                ("partPHD", wd.with_(num_pe=1, exchange_frac=0.0,
+                                     particles_per_target=wd.particles_per_target // K,
+                                     birth_count=wd.birth_count // K))]
     scen = {s_: scenario.simulate(wd, s_) for s_ in seeds}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     res = {}
@@ -779,12 +773,25 @@ def run_gpu_compare(args, rank, world, local_rank):
             n = int(cnt.item())
             est = st_[:n].double().cpu().numpy()[:, [0, 2]] if n else np.zeros((0, 2))
             tr = scen[s_].truth[k]
-            osp.append(ospa_metric(est, tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+            osp.append(ospa_metric(est, tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, ospa_p))
         res[name] = {"path": f.get_path(), "num_pe": w.num_pe, "particles_per_target": w.particles_per_target,
                      "birth_count": w.birth_count, "steps_per_s": len(evs) / (ms * 1e-3),
                      "ms_per_step": ms / len(evs), "pairs_per_s": st["pairs"] / (ms * 1e-3),
                      "ospa_mean": float(np.mean(osp)), "launches": st["launches"], "steps": len(evs)}
         f.close()
+    return res
+
+
+def run_gpu_compare(args, rank, world, local_rank):
+    """The paper's three-way comparison on the 16-PE workload (OSPA p = 2)."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wd = scenario.workload("dist16_10t")
+    runs = max(1, -(-args.steps // wd.steps))
+    seeds = [args.seed + r + 7919 * rank for r in range(runs)]
+    res = _three_way(args, wd, seeds, dev, rank, local_rank, 2.0)
     if rank != 0:
         return 0
     D = res["DCPFPHD"]
@@ -798,6 +805,45 @@ def run_gpu_compare(args, rank, world, local_rank):
                    "global_batch": 1, "seq_len": wd.steps, "parallelism": "replicas"},
         "steps_per_s": D["steps_per_s"], "variants": res,
         "speedup_vs_PHD": {k: res[k]["steps_per_s"] / res["PHD"]["steps_per_s"] for k in res},
+        "gpu_launches": int(D["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu_table1(args, rank, world, local_rank):
+    """The paper's own scenario shape (Sec. 4: bearing-range sensor with a
+    half-plane view over 200 m, Gaussian birth, p_S 0.9, p_D 1, 4 PEs of 200
+    particles per target) at clutter rates 0, 10 and 20, PHD / DCPFPHD /
+    partPHD each: steps/s and OSPA (c = 100 m, p = 1, the paper's order), the
+    shape of Table 1 (context only: the paper's figures are MATLAB times)."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    base = scenario.workload("paper_bot")
+    runs = max(1, -(-args.steps // base.steps))
+    seeds = [args.seed + r + 7919 * rank for r in range(runs)]
+    table = {}
+    for lam in (0.0, 10.0, 20.0):
+        wd = base.with_(clutter_rate=lam)
+        table[str(int(lam))] = _three_way(args, wd, seeds, dev, rank, local_rank, 1.0)
+    if rank != 0:
+        return 0
+    D = table["10"]["DCPFPHD"]
+    line = {
+        "metric": METRIC, "value": D["pairs_per_s"], "unit": UNIT, "n_gpus": world, "steps": D["steps"],
+        "warmup": args.warmup, "ms_per_step": D["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "paper_table1", "targets": base.n_targets, "clutter_rates": [0, 10, 20],
+                   "num_pe": base.num_pe, "particles_per_target_per_pe": base.particles_per_target // base.num_pe,
+                   "runs": len(seeds), "scans_per_run": base.steps, "birth_mass": base.birth_mass,
+                   "ospa": {"c": 100.0, "p": 1.0},
+                   "l2": "flushed between timed steps (512 MiB write, outside the events)",
+                   "global_batch": 1, "seq_len": base.steps, "parallelism": "replicas"},
+        "steps_per_s": D["steps_per_s"],
+        "table": {lam: {k: {"steps_per_s": v["steps_per_s"], "ospa_mean": v["ospa_mean"], "path": v["path"]}
+                        for k, v in arms.items()} for lam, arms in table.items()},
         "gpu_launches": int(D["launches"]),
     }
     print(json.dumps(line), flush=True)
@@ -851,6 +897,20 @@ def main():
                          "e.g. c_tile=512,c_mb=4,r_pb=1,r_g=1,grid1=1216,grid2=608,gate=1,order=1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.workload == "paper_table1" and args.impl == "ours":
+        world = _env_int("WORLD_SIZE", 1)
+        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group(backend="nccl")
+        try:
+            return run_gpu_table1(args, rank, world, local_rank)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
     if args.workload == "dist16_compare" and args.impl == "ours":
         world = _env_int("WORLD_SIZE", 1)
         rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)

@@ -50,6 +50,7 @@ enum { PHD_MEAS_LINEAR = 0, PHD_MEAS_RANGE_BEARING = 1 };
 enum { PHD_FP32 = 0, PHD_FP64 = 1 };
 enum { PHD_CK_LOCAL = 0, PHD_CK_GLOBAL = 1 };
 enum { PHD_PATH_AUTO = 0, PHD_PATH_STAGED = 1, PHD_PATH_FUSED = 2 };
+enum { PHD_BIRTH_UNIFORM = 0, PHD_BIRTH_GAUSSIAN = 1 };
 
 /* Filter configuration (plain data, copied by phd_init). */
 typedef struct phd_config {
@@ -61,13 +62,16 @@ typedef struct phd_config {
     int32_t pe_cap;         /* particle slots per PE (survivors + births), <= 2^24 */
     int32_t m_max;          /* largest |Z_k| accepted, 1..4096 */
     int32_t birth_count;    /* J birth particles per step, split J/K per PE (Step 1) */
-    int32_t reserved0;      /* must be 0 */
+    int32_t birth_model;    /* birth density of Eq. 6 (drawn from as the proposal, weight
+                               nu_b / J_j): PHD_BIRTH_UNIFORM: position U(region), velocity
+                               N(0, birth_vel_sigma^2 I); PHD_BIRTH_GAUSSIAN: the state
+                               N(birth_mean, diag(birth_std^2)) (Sec. 4's N(.; x_bar, Q)) */
     double dt;              /* sampling period T */
-    double sigma_a;         /* acceleration noise std (m/s^2) */
+    double sigma_a;         /* acceleration noise std (m/s^2), x axis (both axes if sigma_a_y = 0) */
     double sigma_z[2];      /* linear: (sx, sy) m; range-bearing: (s_r m, s_theta rad) */
     double sensor[2];       /* range-bearing sensor position */
     double region[4];       /* x_min, x_max, y_min, y_max: birth support, linear clutter support */
-    double r_max;           /* range-bearing clutter support [0, r_max] x (-pi, pi] */
+    double r_max;           /* range-bearing clutter support [0, r_max] x (bearing span) */
     double p_s;             /* survival probability e_{k|k-1} (Eq. 5) */
     double p_d;             /* detection probability P_D (Eq. 4) */
     double clutter_rate;    /* lambda: kappa(z) = lambda / |measurement space| */
@@ -76,6 +80,11 @@ typedef struct phd_config {
     double particles_per_target; /* rho: a PE resamples to round((rho/K) max(1, N^j)) */
     double exchange_frac;   /* ring exchange: floor(frac * min_j n_j) particles per PE (Step 6) */
     uint64_t seed;          /* Philox-4x32-10 key for the in-kernel random numbers */
+    double sigma_a_y;       /* acceleration noise std of the y axis; 0: sigma_a */
+    double theta_span;      /* range-bearing clutter bearing extent in (0, 2 pi]; 0: 2 pi
+                               (kappa = lambda / (r_max theta_span)) */
+    double birth_mean[4];   /* PHD_BIRTH_GAUSSIAN: mean state [x, vx, y, vy] */
+    double birth_std[4];    /* PHD_BIRTH_GAUSSIAN: std per state component (diagonal Q) */
 } phd_config;
 
 typedef struct phd_handle phd_handle;
@@ -102,13 +111,17 @@ const char *phd_status_string(phd_status s);
 
 /* ---- the step's stages (Algorithm 1 order) -------------------------------- */
 
-/* Prediction, Eq. 5 (survivors: CV transition, weight p_S w) and Eq. 6
- * (births: J_j particles per PE, position uniform over cfg.region, velocity
- * N(0, birth_vel_sigma^2 I), weight birth_mass / J_j).  d_noise: NULL to draw
- * in-kernel (Philox), or real [K][pe_cap][4] rows (n1, n2, u1, u2): survivor
- * slot i uses n1, n2 as its standard normal accelerations; birth slot i uses
- * n1, n2 as standard normal velocity draws and u1, u2 in [0, 1) as position
- * fractions.  Errors: PHD_ERR_STATE if called twice without an update. */
+/* Prediction, Eq. 5 (survivors: CV transition with accelerations
+ * (sigma_a n1, sigma_a_y n2), weight p_S w) and Eq. 6 (births: J_j particles
+ * per PE drawn from the birth density, weight birth_mass / J_j).  d_noise:
+ * NULL to draw in-kernel (Philox), or real [K][pe_cap][4] rows (n1, n2, u1,
+ * u2): survivor slot i uses n1, n2 as its standard normal accelerations;
+ * birth slot i uses n1, n2 as standard normal velocity draws and u1, u2 in
+ * [0, 1) as the position draws: uniform birth x = x_min + u1 (x_max - x_min),
+ * y likewise with u2; Gaussian birth x = mean_x + std_x r cos(2 pi u2),
+ * y = mean_y + std_y r sin(2 pi u2), r = sqrt(-2 ln(1 - u1)) (Box-Muller),
+ * vx = mean_vx + std_vx n1, vy = mean_vy + std_vy n2.
+ * Errors: PHD_ERR_STATE if called twice without an update. */
 phd_status phd_predict(phd_handle *h, const void *d_noise);
 
 /* ---- measurement-driven birth (Eq. 6 with a learned proposal) ------------- */
@@ -144,7 +157,8 @@ phd_status phd_predict(phd_handle *h, const void *d_noise);
  *
  * Load (d_params: device FP32 [phd_mlp_nparams()], rounded to bfloat16 into
  * the workspace) or, with d_params NULL, unload the network.  alpha in (0, 1].
- * FP32 one-filter handles only (PHD_ERR_STATE otherwise).  With a network
+ * FP32 one-filter handles with the uniform birth density only (PHD_ERR_STATE
+ * otherwise: the defensive part is the plain uniform birth).  With a network
  * loaded: the fused step kernel is not used; phd_predict refuses
  * (PHD_ERR_STATE: use phd_predict_z); phd_step, phd_step_inject,
  * phd_step_host and phd_run draw the births from the scan they are given.

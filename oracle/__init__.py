@@ -51,13 +51,15 @@ def build(force: bool = False) -> str:
 
 class _Model(ctypes.Structure):
     _fields_ = [
-        ("meas_model", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("meas_model", ctypes.c_int), ("birth_model", ctypes.c_int),
         ("dt", ctypes.c_double), ("sigma_a", ctypes.c_double),
         ("sigma_z", ctypes.c_double * 2), ("sensor", ctypes.c_double * 2),
         ("region", ctypes.c_double * 4), ("r_max", ctypes.c_double),
         ("p_s", ctypes.c_double), ("p_d", ctypes.c_double),
         ("clutter_rate", ctypes.c_double), ("birth_mass", ctypes.c_double),
         ("birth_vel_sigma", ctypes.c_double),
+        ("sigma_a_y", ctypes.c_double), ("theta_span", ctypes.c_double),
+        ("birth_mean", ctypes.c_double * 4), ("birth_std", ctypes.c_double * 4),
     ]
 
 
@@ -139,6 +141,13 @@ def model(w) -> _Model:
     m.p_s, m.p_d = float(w.p_s), float(w.p_d)
     m.clutter_rate, m.birth_mass = float(w.clutter_rate), float(w.birth_mass)
     m.birth_vel_sigma = float(w.birth_vel_sigma)
+    m.sigma_a_y = float(getattr(w, "sigma_a_y", 0.0))
+    m.theta_span = float(getattr(w, "theta_span", 0.0))
+    m.birth_model = 1 if getattr(w, "birth_model", "uniform") == "gaussian" else 0
+    for k, v in enumerate(getattr(w, "birth_mean", (0.0,) * 4)):
+        m.birth_mean[k] = float(v)
+    for k, v in enumerate(getattr(w, "birth_std", (0.0,) * 4)):
+        m.birth_std[k] = float(v)
     return m
 
 

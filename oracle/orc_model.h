@@ -7,10 +7,12 @@
 
 #define ORC_LINEAR 0
 #define ORC_RANGE_BEARING 1
+#define ORC_BIRTH_UNIFORM 0
+#define ORC_BIRTH_GAUSSIAN 1
 
 typedef struct {
     int meas_model;       /* ORC_LINEAR or ORC_RANGE_BEARING */
-    int pad_;
+    int birth_model;      /* ORC_BIRTH_UNIFORM or ORC_BIRTH_GAUSSIAN */
     double dt;            /* sampling period T (Sec. 4: T = 1) */
     double sigma_a;       /* std of the acceleration noise w_k */
     double sigma_z[2];    /* linear: (sx, sy) m; range-bearing: (sr m, stheta rad) */
@@ -22,6 +24,10 @@ typedef struct {
     double clutter_rate;  /* lambda_k: mean clutter count per scan */
     double birth_mass;    /* nu_b: expected number of births per step */
     double birth_vel_sigma;
+    double sigma_a_y;     /* acceleration noise std of the y axis (0: sigma_a) */
+    double theta_span;    /* range-bearing clutter bearing extent (0: 2 pi) */
+    double birth_mean[4]; /* Gaussian birth N(x_bar, Q) of Sec. 4: mean [x, vx, y, vy] */
+    double birth_std[4];  /* and the square roots of Q's diagonal */
 } orc_model;
 
 #endif /* ORC_MODEL_H */

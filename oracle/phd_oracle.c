@@ -34,11 +34,13 @@ static const double ORC_PI = 3.14159265358979323846;
  * sensor; [0, r_max] x (-pi, pi] for the range-bearing sensor. */
 double orc_kappa(const orc_model *m)
 {
+    /* kappa = lambda V_u(z) (Sec. 4): the uniform density over the
+     * measurement space, the region (linear) or [0, r_max] x the bearing span */
     double vol;
     if (m->meas_model == ORC_LINEAR)
         vol = (m->region[1] - m->region[0]) * (m->region[3] - m->region[2]);
     else
-        vol = m->r_max * 2.0 * ORC_PI;
+        vol = m->r_max * (m->theta_span > 0.0 ? m->theta_span : 2.0 * ORC_PI);
     return m->clutter_rate / vol;
 }
 
@@ -80,9 +82,13 @@ double orc_likelihood(const orc_model *m, const double *z, const double *x)
 
 /* Prediction, Eq. 5 (survivors) and Eq. 6 (births).
  * Survivors: proposal q = f (the CV transition of Sec. 4), so phi/q = e_{k|k-1}
- * and w~ = p_S w;  x~ = F x + G a with a = sigma_a (n1, n2).
- * Births: J particles from p_k(.|Z_k) = U(region) x N(0, s_b^2 I) for the
- * velocity; with gamma = nu_b * p_k the weight gamma / p_k / J = nu_b / J.
+ * and w~ = p_S w;  x~ = F x + G a with a = (sigma_a n1, sigma_a_y n2).
+ * Births: J particles drawn from the birth density itself, so with
+ * gamma = nu_b * p_k the weight gamma / p_k / J = nu_b / J:
+ *   uniform: p_k = U(region) x N(0, s_b^2 I) for the velocity;
+ *   Gaussian (Sec. 4's N(.; x_bar, Q), Q diagonal): every component
+ *   x_bar_c + sqrt(Q_cc) n_c, the position normals by the Box-Muller map of
+ *   (u1, u2): r = sqrt(-2 ln(1 - u1)), (r cos 2 pi u2, r sin 2 pi u2).
  * noise rows (n1, n2, u1, u2): survivors use n1, n2; births use n1, n2 for the
  * velocity and u1, u2 for the position.  Output: L survivors then J births. */
 void orc_predict(const orc_model *m, const double *x_in, const double *w_in, int L, int J,
@@ -92,7 +98,7 @@ void orc_predict(const orc_model *m, const double *x_in, const double *w_in, int
     for (int i = 0; i < L; ++i) {
         const double *x = x_in + 4 * i;
         double ax = m->sigma_a * noise[4 * i + 0];
-        double ay = m->sigma_a * noise[4 * i + 1];
+        double ay = (m->sigma_a_y > 0.0 ? m->sigma_a_y : m->sigma_a) * noise[4 * i + 1];
         double *y = x_out + 4 * i;
         y[0] = x[0] + T * x[1] + 0.5 * T * T * ax;
         y[1] = x[1] + T * ax;
@@ -104,10 +110,18 @@ void orc_predict(const orc_model *m, const double *x_in, const double *w_in, int
         int i = L + b;
         const double *n = noise + 4 * i;
         double *y = x_out + 4 * i;
-        y[0] = m->region[0] + n[2] * (m->region[1] - m->region[0]);
-        y[1] = m->birth_vel_sigma * n[0];
-        y[2] = m->region[2] + n[3] * (m->region[3] - m->region[2]);
-        y[3] = m->birth_vel_sigma * n[1];
+        if (m->birth_model == ORC_BIRTH_GAUSSIAN) {
+            const double r = sqrt(-2.0 * log(1.0 - n[2]));
+            y[0] = m->birth_mean[0] + m->birth_std[0] * r * cos(2.0 * ORC_PI * n[3]);
+            y[1] = m->birth_mean[1] + m->birth_std[1] * n[0];
+            y[2] = m->birth_mean[2] + m->birth_std[2] * r * sin(2.0 * ORC_PI * n[3]);
+            y[3] = m->birth_mean[3] + m->birth_std[3] * n[1];
+        } else {
+            y[0] = m->region[0] + n[2] * (m->region[1] - m->region[0]);
+            y[1] = m->birth_vel_sigma * n[0];
+            y[2] = m->region[2] + n[3] * (m->region[3] - m->region[2]);
+            y[3] = m->birth_vel_sigma * n[1];
+        }
         w_out[i] = m->birth_mass / (double)J;
     }
 }

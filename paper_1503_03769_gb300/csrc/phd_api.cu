@@ -151,7 +151,12 @@ const char* check_config(const phd_config& c) {
   if (c.m_max < 1 || c.m_max > phd::kMaxM) return "m_max must be in 1..4096";
   if (c.birth_count < 0) return "birth_count";
   if (phd::births_of(c.birth_count, c.num_pe, 0) >= c.pe_cap) return "birth_count / num_pe must be < pe_cap";
-  if (c.reserved0 != 0) return "reserved0 must be 0";
+  if (c.birth_model != PHD_BIRTH_UNIFORM && c.birth_model != PHD_BIRTH_GAUSSIAN) return "birth_model";
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(c.birth_mean[k]) || !(c.birth_std[k] >= 0) || !std::isfinite(c.birth_std[k]))
+      return "birth_mean / birth_std";
+  if (!(c.sigma_a_y >= 0) || !std::isfinite(c.sigma_a_y)) return "sigma_a_y";
+  if (!(c.theta_span >= 0 && c.theta_span <= 2.0 * 3.14159265358979323846)) return "theta_span must be in [0, 2 pi]";
   if (!(c.dt > 0) || !std::isfinite(c.dt)) return "dt";
   if (!(c.sigma_a >= 0) || !std::isfinite(c.sigma_a)) return "sigma_a";
   if (!(c.sigma_z[0] > 0) || !(c.sigma_z[1] > 0) || !std::isfinite(c.sigma_z[0]) || !std::isfinite(c.sigma_z[1]))
@@ -170,6 +175,14 @@ const char* check_config(const phd_config& c) {
   return nullptr;
 }
 
+// Volume of the measurement space the clutter is uniform over (kappa =
+// lambda / volume): the region (linear sensor) or [0, r_max] x bearing span.
+double meas_volume(const phd_config& c) {
+  const double kPi = 3.14159265358979323846;
+  if (c.meas_model == PHD_MEAS_LINEAR) return (c.region[1] - c.region[0]) * (c.region[3] - c.region[2]);
+  return c.r_max * (c.theta_span > 0 ? c.theta_span : 2.0 * kPi);
+}
+
 Model make_model(const phd_config& c) {
   Model m{};
   const double kPi = 3.14159265358979323846;
@@ -182,6 +195,15 @@ Model make_model(const phd_config& c) {
   m.ck_global = c.ck_mode == PHD_CK_GLOBAL;
   m.dt = c.dt;
   m.sigma_a = c.sigma_a;
+  m.sigma_ay = c.sigma_a_y > 0 ? c.sigma_a_y : c.sigma_a;
+  m.birth_gauss = c.birth_model == PHD_BIRTH_GAUSSIAN;
+  for (int k = 0; k < 4; ++k) {
+    m.bmean[k] = c.birth_mean[k];
+    m.bstd[k] = c.birth_std[k];
+    m.f_bmean[k] = (float)c.birth_mean[k];
+    m.f_bstd[k] = (float)c.birth_std[k];
+  }
+  m.f_sigma_ay = (float)m.sigma_ay;
   m.sz0 = c.sigma_z[0];
   m.sz1 = c.sigma_z[1];
   m.sx = c.sensor[0];
@@ -192,9 +214,7 @@ Model make_model(const phd_config& c) {
   m.ry1 = c.region[3];
   m.p_s = c.p_s;
   m.p_d = c.p_d;
-  const double vol = c.meas_model == PHD_MEAS_LINEAR ? (c.region[1] - c.region[0]) * (c.region[3] - c.region[2])
-                                                     : c.r_max * 2.0 * kPi;
-  m.kappa = c.clutter_rate / vol;
+  m.kappa = c.clutter_rate / meas_volume(c);
   m.birth_mass = c.birth_mass;
   m.birth_vel_sigma = c.birth_vel_sigma;
   m.rho_pe = c.particles_per_target / (double)c.num_pe;
@@ -273,12 +293,9 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
   std::vector<double> kap(K), rho(K), bwd(K);
   std::vector<float> bwf(K);
   std::vector<int> Jb(K), lmax(K), zero(K, 0);
-  const double kPi = 3.14159265358979323846;
   for (int j = 0; j < K; ++j) {
     const phd_config& c = cf[j];
-    const double vol = c.meas_model == PHD_MEAS_LINEAR ? (c.region[1] - c.region[0]) * (c.region[3] - c.region[2])
-                                                       : c.r_max * 2.0 * kPi;
-    kap[j] = c.clutter_rate / vol;
+    kap[j] = c.clutter_rate / meas_volume(c);
     if (batch) {
       rho[j] = c.particles_per_target;
       Jb[j] = c.birth_count;
@@ -740,6 +757,8 @@ phd_status phd_set_birth_proposal(phd_handle* h, const float* d_params, double a
   }
   if (is_fp64(h) || h->batch_runs)
     return fail(h, PHD_ERR_STATE, "phd_set_birth_proposal: FP32 one-filter handles only");
+  if (h->m.birth_gauss)
+    return fail(h, PHD_ERR_STATE, "phd_set_birth_proposal: the defensive mixture needs the uniform birth density");
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(h, PHD_ERR_INVALID_ARG, "alpha must be in (0, 1]");
   PHD_CUDA(h, phd::prepare_birth(h->m));
   PHD_CUDA(h, phd::launch_params_bf16(h->d.mlp_w, d_params, h->stream));
@@ -1168,7 +1187,10 @@ const char* batch_problem(const phd_config* c, int runs) {
         b.sigma_z[1] != a.sigma_z[1] || b.sensor[0] != a.sensor[0] || b.sensor[1] != a.sensor[1] ||
         b.region[0] != a.region[0] || b.region[1] != a.region[1] || b.region[2] != a.region[2] ||
         b.region[3] != a.region[3] || b.r_max != a.r_max || b.dt != a.dt || b.sigma_a != a.sigma_a ||
-        b.p_s != a.p_s || b.p_d != a.p_d || b.birth_vel_sigma != a.birth_vel_sigma || b.seed != a.seed)
+        b.p_s != a.p_s || b.p_d != a.p_d || b.birth_vel_sigma != a.birth_vel_sigma || b.seed != a.seed ||
+        b.sigma_a_y != a.sigma_a_y || b.birth_model != a.birth_model || b.theta_span != a.theta_span ||
+        std::memcmp(b.birth_mean, a.birth_mean, sizeof(a.birth_mean)) != 0 ||
+        std::memcmp(b.birth_std, a.birth_std, sizeof(a.birth_std)) != 0)
       return "runs of a batch differ in a shared model field";
   }
   return nullptr;

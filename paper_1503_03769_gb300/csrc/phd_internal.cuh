@@ -48,11 +48,13 @@ struct Model {
   int m_max;
   int J;                 // births per step, all PEs
   int ck_global;         // 1: every PE uses the PE-mean C
-  double dt, sigma_a;
+  double dt, sigma_a, sigma_ay;   // acceleration noise std per axis
   double sz0, sz1;       // measurement noise std per coordinate
   double sx, sy;         // sensor
   double rx0, rx1, ry0, ry1;
   double p_s, p_d, kappa, birth_mass, birth_vel_sigma;
+  int birth_gauss;       // 1: births from N(bmean, diag(bstd^2)); 0: uniform position
+  double bmean[4], bstd[4];
   double rho_pe;         // particles per target per PE
   double exchange_frac;
   // likelihood in exp2 form: g = cnorm * 2^-(a0^2 d0^2 + a1^2 d1^2)
@@ -62,6 +64,7 @@ struct Model {
   // FP32 copies of the per-particle constants (FP64 is ~1/60 of the FP32 rate
   // on this part: no conversion in the FP32 kernels' inner code)
   float f_dt, f_sigma_a, f_ps, f_rx0, f_rw, f_ry0, f_rh, f_bv, f_sx, f_sy, f_miss;
+  float f_sigma_ay, f_bmean[4], f_bstd[4];
   float f_bw_lo, f_bw_hi;  // birth weight nu_b / J_j for J_j = J / K and J / K + 1
   double bw_lo, bw_hi;
   Tune tune;
@@ -77,15 +80,24 @@ struct Model {
 };
 
 // Per-particle model constants in the kernel's precision.
-template <class R> struct Cst { R dt, sa, ps, rx0, rw, ry0, rh, bv, sx, sy, miss, bw_lo, bw_hi; };
+template <class R> struct Cst {
+  R dt, sa, ps, rx0, rw, ry0, rh, bv, sx, sy, miss, bw_lo, bw_hi;
+  R say;              // y-axis acceleration noise std
+  int gauss;          // Gaussian birth density
+  R bm[4], bs[4];     // its mean and std per state component
+};
 template <class R> __device__ __forceinline__ Cst<R> consts(const Model& m);
 template <> __device__ __forceinline__ Cst<float> consts<float>(const Model& m) {
   return Cst<float>{m.f_dt, m.f_sigma_a, m.f_ps, m.f_rx0, m.f_rw, m.f_ry0, m.f_rh, m.f_bv, m.f_sx, m.f_sy,
-                    m.f_miss, m.f_bw_lo, m.f_bw_hi};
+                    m.f_miss, m.f_bw_lo, m.f_bw_hi, m.f_sigma_ay, m.birth_gauss,
+                    {m.f_bmean[0], m.f_bmean[1], m.f_bmean[2], m.f_bmean[3]},
+                    {m.f_bstd[0], m.f_bstd[1], m.f_bstd[2], m.f_bstd[3]}};
 }
 template <> __device__ __forceinline__ Cst<double> consts<double>(const Model& m) {
   return Cst<double>{m.dt, m.sigma_a, m.p_s, m.rx0, m.rx1 - m.rx0, m.ry0, m.ry1 - m.ry0, m.birth_vel_sigma, m.sx,
-                     m.sy, 1.0 - m.p_d, m.bw_lo, m.bw_hi};
+                     m.sy, 1.0 - m.p_d, m.bw_lo, m.bw_hi, m.sigma_ay, m.birth_gauss,
+                     {m.bmean[0], m.bmean[1], m.bmean[2], m.bmean[3]},
+                     {m.bstd[0], m.bstd[1], m.bstd[2], m.bstd[3]}};
 }
 
 // Workspace carve (device pointers).  Real-typed arrays are void* and cast by
@@ -596,12 +608,23 @@ __device__ __forceinline__ void predict_slot(const Cst<R>& c, bool survivor, con
                                              R u1, R u2, St4<R>& o, R& wo) {
   if (survivor) {
     const R T = c.dt;
-    const R ax = c.sa * n1, ay = c.sa * n2;
+    const R ax = c.sa * n1, ay = c.say * n2;
     o.x = s.x + T * s.vx + (R)0.5 * T * T * ax;
     o.vx = s.vx + T * ax;
     o.y = s.y + T * s.vy + (R)0.5 * T * T * ay;
     o.vy = s.vy + T * ay;
     wo = c.ps * w;
+  } else if (c.gauss) {
+    // Gaussian birth density: velocity normals (n1, n2), position normals by
+    // Box-Muller from (u1, u2): r = sqrt(-2 ln(1 - u1)), angle 2 pi u2
+    const R rad = sqrt((R)-2 * log1p(-u1));
+    R sn, cs;
+    sincospi((R)2 * u2, &sn, &cs);
+    o.x = c.bm[0] + c.bs[0] * (rad * cs);
+    o.vx = c.bm[1] + c.bs[1] * n1;
+    o.y = c.bm[2] + c.bs[2] * (rad * sn);
+    o.vy = c.bm[3] + c.bs[3] * n2;
+    wo = bw;
   } else {
     o.x = c.rx0 + u1 * c.rw;
     o.vx = c.bv * n1;

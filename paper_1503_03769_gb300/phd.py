@@ -23,6 +23,7 @@ PHD_MEAS_LINEAR, PHD_MEAS_RANGE_BEARING = 0, 1
 PHD_FP32, PHD_FP64 = 0, 1
 PHD_CK_LOCAL, PHD_CK_GLOBAL = 0, 1
 PHD_PATH_AUTO, PHD_PATH_STAGED, PHD_PATH_FUSED = 0, 1, 2
+PHD_BIRTH_UNIFORM, PHD_BIRTH_GAUSSIAN = 0, 1
 _PATHS = {"auto": PHD_PATH_AUTO, "staged": PHD_PATH_STAGED, "fused": PHD_PATH_FUSED}
 
 
@@ -38,7 +39,7 @@ class phd_config(ctypes.Structure):
         ("meas_model", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("num_pe", ctypes.c_int32), ("ck_mode", ctypes.c_int32),
         ("pe_cap", ctypes.c_int32), ("m_max", ctypes.c_int32),
-        ("birth_count", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("birth_count", ctypes.c_int32), ("birth_model", ctypes.c_int32),
         ("dt", ctypes.c_double), ("sigma_a", ctypes.c_double),
         ("sigma_z", ctypes.c_double * 2), ("sensor", ctypes.c_double * 2),
         ("region", ctypes.c_double * 4), ("r_max", ctypes.c_double),
@@ -46,6 +47,8 @@ class phd_config(ctypes.Structure):
         ("clutter_rate", ctypes.c_double), ("birth_mass", ctypes.c_double),
         ("birth_vel_sigma", ctypes.c_double), ("particles_per_target", ctypes.c_double),
         ("exchange_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("sigma_a_y", ctypes.c_double), ("theta_span", ctypes.c_double),
+        ("birth_mean", ctypes.c_double * 4), ("birth_std", ctypes.c_double * 4),
     ]
 
 
@@ -168,6 +171,13 @@ def make_config(w, seed: int = 0) -> phd_config:
     c.particles_per_target = float(w.particles_per_target)
     c.exchange_frac = float(w.exchange_frac)
     c.seed = int(seed) & (2 ** 64 - 1)
+    c.sigma_a_y = float(getattr(w, "sigma_a_y", 0.0))
+    c.theta_span = float(getattr(w, "theta_span", 0.0))
+    c.birth_model = PHD_BIRTH_GAUSSIAN if getattr(w, "birth_model", "uniform") == "gaussian" else PHD_BIRTH_UNIFORM
+    for k, v in enumerate(getattr(w, "birth_mean", (0.0,) * 4)):
+        c.birth_mean[k] = float(v)
+    for k, v in enumerate(getattr(w, "birth_std", (0.0,) * 4)):
+        c.birth_std[k] = float(v)
     return c
 
 

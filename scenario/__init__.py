@@ -20,7 +20,8 @@ Noise layout consumed by both implementations (one row of four per particle
 slot, survivors first then births, per processing element (PE) slot range):
   row = (n1, n2, u1, u2); survivors use n1, n2 as the standard normal
   acceleration draws; births use n1, n2 as standard normal velocity draws and
-  u1, u2 in [0, 1) as the position fractions across the region.
+  u1, u2 in [0, 1) as the position fractions across the region (uniform
+  birth) or as the Box-Muller pair of the position normals (Gaussian birth).
 Resampling takes one uint32 per PE per step; the ring exchange takes one
 uint32 per selected slot (a partial Fisher-Yates draw), up to pe_cap per PE.
 """
@@ -66,6 +67,11 @@ class Workload:
     truth_vel_sigma: float = 20.0
     pe_cap: int = 0                         # particle slots per PE (0: derived)
     m_max: int = 0                          # measurement capacity (0: derived)
+    sigma_a_y: float = 0.0                  # y-axis acceleration noise std (0: sigma_a)
+    theta_span: float = 0.0                 # range-bearing clutter bearing extent (0: 2 pi)
+    birth_model: str = "uniform"            # "uniform" or "gaussian" (N(birth_mean, diag birth_std^2))
+    birth_mean: tuple = (0.0, 0.0, 0.0, 0.0)
+    birth_std: tuple = (0.0, 0.0, 0.0, 0.0)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -112,6 +118,18 @@ def workload(name: str, **overrides) -> Workload:
             name="rb_50t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=100.0, n_targets=50, particles_per_target=1000,
             birth_count=5000, steps=100, precision="fp32"),
+        # The paper's own simulation shape (Sec. 4): bearing-range sensor with
+        # a half-plane field of view over 200 m, p_S 0.9, p_D 1, Gaussian
+        # birth N(x_bar, Q) near the sensor, 4 PEs with 200 particles per
+        # target each, 5 tracks over 50 scans; process noise std as printed
+        # (0.025 and 4 per axis; the printed values are garbled).
+        "paper_bot": Workload(
+            name="paper_bot", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.05),
+            sigma_a=0.025, sigma_a_y=4.0, region=(0.0, 200.0, -200.0, 200.0), r_max=200.0,
+            theta_span=math.pi, p_s=0.9, p_d=1.0, clutter_rate=10.0, n_targets=5,
+            particles_per_target=800, birth_count=800, num_pe=4, exchange_frac=0.1, steps=50,
+            birth_model="gaussian", birth_mean=(0.0, 3.0, 0.0, -3.0),
+            birth_std=(math.sqrt(10.0), 1.0, math.sqrt(10.0), 1.0), precision="fp32", pe_cap=2048),
     }
     if name not in base:
         raise KeyError(f"unknown workload {name!r}; known: {sorted(base)}")
@@ -194,6 +212,9 @@ def _clutter(w: Workload, rng: np.random.Generator, n: int) -> np.ndarray:
     if w.meas_model == LINEAR:
         x0, x1, y0, y1 = w.region
         return np.stack([x0 + u[:, 0] * (x1 - x0), y0 + u[:, 1] * (y1 - y0)], axis=1)
+    if w.theta_span > 0:
+        # bearing uniform over [-span / 2, span / 2] (the sensor's field of view)
+        return np.stack([u[:, 0] * w.r_max, 0.5 * w.theta_span - u[:, 1] * w.theta_span], axis=1)
     return np.stack([u[:, 0] * w.r_max, math.pi - u[:, 1] * 2 * math.pi], axis=1)
 
 
@@ -208,20 +229,31 @@ def simulate(w: Workload, seed: int, steps: Optional[int] = None) -> Scenario:
     else:
         hi = max(1, int(0.4 * w.steps))
         bsteps = sorted(int(s) for s in rng.integers(1, hi + 1, size=w.n_targets))
-    # initial states: positions in the inner 80 % of the region
-    cx, cy, hx, hy = 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.4 * (x1 - x0), 0.4 * (y1 - y0)
-    init = np.stack([cx + hx * (2 * rng.random(w.n_targets) - 1),
-                     w.truth_vel_sigma * rng.standard_normal(w.n_targets),
-                     cy + hy * (2 * rng.random(w.n_targets) - 1),
-                     w.truth_vel_sigma * rng.standard_normal(w.n_targets)], axis=1)
+    if w.birth_model == "gaussian":
+        # initial states from the birth density N(x_bar, Q) itself
+        init = (np.asarray(w.birth_mean, np.float64)
+                + np.asarray(w.birth_std, np.float64) * rng.standard_normal((w.n_targets, 4)))
+    else:
+        # initial states: positions in the inner 80 % of the region
+        cx, cy, hx, hy = 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.4 * (x1 - x0), 0.4 * (y1 - y0)
+        init = np.stack([cx + hx * (2 * rng.random(w.n_targets) - 1),
+                         w.truth_vel_sigma * rng.standard_normal(w.n_targets),
+                         cy + hy * (2 * rng.random(w.n_targets) - 1),
+                         w.truth_vel_sigma * rng.standard_normal(w.n_targets)], axis=1)
+    acc_std = np.array([w.sigma_a, w.sigma_a_y if w.sigma_a_y > 0 else w.sigma_a])
     sc = Scenario(workload=w)
     live = np.zeros((0, 4))
     ids = np.zeros((0,), dtype=np.int64)
     for k in range(1, steps + 1):
         if len(live):
-            live = _cv_move(live, w.dt, w.sigma_a * rng.standard_normal((len(live), 2)))
+            live = _cv_move(live, w.dt, rng.standard_normal((len(live), 2)) * acc_std)
             inside = ((live[:, 0] >= x0) & (live[:, 0] <= x1) &
                       (live[:, 2] >= y0) & (live[:, 2] <= y1))
+            if w.meas_model == RANGE_BEARING and w.theta_span > 0:
+                # a sensor with a field of view: tracks leave it past r_max
+                # or outside the bearing span
+                px, py = live[:, 0] - w.sensor[0], live[:, 2] - w.sensor[1]
+                inside &= (np.hypot(px, py) <= w.r_max) & (np.abs(np.arctan2(py, px)) <= 0.5 * w.theta_span)
             live, ids = live[inside], ids[inside]
         born = [t for t in range(w.n_targets) if bsteps[t] == k]
         if born:

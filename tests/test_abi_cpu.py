@@ -57,10 +57,17 @@ def test_workspace_size_and_config_validation_without_gpu():
     assert L.phd_workspace_size(ctypes.byref(c), ctypes.byref(n)) == phd.PHD_OK
     assert n.value > 0 and n.value % 256 == 0
     for field, bad in [("num_pe", 0), ("num_pe", 300), ("m_max", 5000), ("pe_cap", 0),
-                       ("p_d", 1.5), ("exchange_frac", 0.6), ("precision", 7), ("reserved0", 1)]:
+                       ("p_d", 1.5), ("exchange_frac", 0.6), ("precision", 7), ("birth_model", 2),
+                       ("sigma_a_y", -1.0), ("theta_span", 7.0)]:
         c2 = phd.make_config(w)
         setattr(c2, field, bad)
         assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_ERR_INVALID_ARG, field
+    c2 = phd.make_config(w)
+    c2.birth_model = phd.PHD_BIRTH_GAUSSIAN
+    c2.birth_std[1] = -1.0
+    assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_ERR_INVALID_ARG
+    c2.birth_std[1] = 1.0
+    assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_OK
     assert L.phd_init(None, ctypes.byref(c), None, 0, None) == phd.PHD_ERR_INVALID_ARG
     assert L.phd_status_string(phd.PHD_ERR_CAPACITY) == b"capacity exceeded"
 

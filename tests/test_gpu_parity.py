@@ -87,6 +87,30 @@ def test_distributed_linear_stages(ck_mode, path):
     assert rep.compared_labels > 0
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("path", ["staged", "fused"])
+def test_paper_scenario_stages(precision, path):
+    """The paper's own simulation shape (Sec. 4): Gaussian birth N(x_bar, Q),
+    per-axis process noise, a bearing field of view (kappa over [0, r_max] x
+    [-pi/2, pi/2]), p_S 0.9, p_D 1, 4 PEs with exchange; 8 free-running
+    scans, then 3 scans compared stage by stage."""
+    w = scenario.workload("paper_bot", precision=precision, clutter_rate=20.0)
+    truth = scenario.simulate(w, 21, steps=11)
+    rep = _run_stages(w, 21, 3, sc=truth, warm=8, path=path)
+    assert rep.compared_labels > 0
+
+
+def test_learned_proposal_needs_the_uniform_birth():
+    """The defensive mixture's plain part is the uniform birth: a Gaussian-birth
+    handle refuses a network."""
+    from paper_1503_03769_gb300 import PhdError, proposal
+    w = scenario.workload("paper_bot")
+    f = _filter(w, 1)
+    with pytest.raises(PhdError):
+        f.set_birth_proposal(torch.as_tensor(proposal.init_params(0), device="cuda:0"))
+    f.close()
+
+
 @pytest.mark.parametrize("pe_cap", [64, 128])
 def test_fused_many_pes_small_slices(pe_cap):
     """64 PEs with slices of a few dozen particles on the fused path: CU

@@ -123,6 +123,79 @@ def test_birth_distribution_and_mass():
     assert np.all(wo == wo[0])
 
 
+PAPER = scenario.workload("paper_bot")
+
+
+def test_kappa_with_a_bearing_field_of_view():
+    """kappa = lambda V_u (Sec. 4): the uniform clutter density over [0, r_max]
+    x the bearing span, in closed form and against the scenario's clutter
+    generator (independent code): the count in a sub-box of measurement space
+    over many scans is kappa x the sub-box area per scan."""
+    m = oracle.model(PAPER.with_(clutter_rate=20.0))
+    assert oracle.kappa(m) == pytest.approx(20.0 / (200.0 * math.pi), rel=1e-15)
+    w = PAPER.with_(clutter_rate=20.0, n_targets=0, steps=4000)
+    sc = scenario.simulate(w, 3)
+    Z = np.concatenate(sc.meas)
+    assert np.all(np.abs(Z[:, 1]) <= math.pi / 2 + 1e-6) and np.all((Z[:, 0] >= 0) & (Z[:, 0] <= 200))
+    box = (Z[:, 0] > 40) & (Z[:, 0] < 90) & (Z[:, 1] > -0.3) & (Z[:, 1] < 0.5)
+    expect = oracle.kappa(m) * 50.0 * 0.8 * w.steps
+    assert abs(box.sum() - expect) < 5 * math.sqrt(expect)
+
+
+def test_gaussian_birth_box_muller_worked_values():
+    """Gaussian birth (Sec. 4's N(x_bar, Q)): velocity from the normals, the
+    position normals by the Box-Muller map of (u1, u2); u1 = 1 - e^{-1/2}
+    gives radius 1, so the angle 2 pi u2 = 0 or pi/2 puts the draw one std
+    along x or y; u1 = 0 gives the mean."""
+    w = PAPER.with_(birth_mean=(1.0, 2.0, 3.0, 4.0), birth_std=(2.0, 0.5, 3.0, 0.25), birth_mass=0.3)
+    m = oracle.model(w)
+    u1 = 1.0 - math.exp(-0.5)
+    noise = np.array([[0.5, -1.0, u1, 0.0],
+                      [0.0, 2.0, u1, 0.25],
+                      [1.0, 1.0, 0.0, 0.7]])
+    xo, wo = oracle.predict(m, np.zeros((0, 4)), np.zeros(0), 3, noise)
+    np.testing.assert_allclose(xo[0], [1.0 + 2.0, 2.0 + 0.25, 3.0, 4.0 - 0.25], atol=1e-12)
+    np.testing.assert_allclose(xo[1], [1.0, 2.0, 3.0 + 3.0, 4.0 + 0.5], atol=1e-12)
+    np.testing.assert_allclose(xo[2], [1.0, 2.5, 3.0, 4.25], atol=1e-12)
+    np.testing.assert_allclose(wo, 0.1, rtol=1e-15)
+
+
+def test_gaussian_birth_moments():
+    """Draws with uniform (u1, u2) and normal (n1, n2) have the birth density's
+    mean and std per component and uncorrelated components."""
+    m = oracle.model(PAPER)
+    J = 200_000
+    rng = np.random.default_rng(11)
+    noise = np.concatenate([rng.standard_normal((J, 2)), rng.random((J, 2))], axis=1)
+    xo, wo = oracle.predict(m, np.zeros((0, 4)), np.zeros(0), J, noise)
+    mean, std = np.asarray(PAPER.birth_mean), np.asarray(PAPER.birth_std)
+    assert np.all(np.abs(xo.mean(0) - mean) < 5 * std / math.sqrt(J))
+    np.testing.assert_allclose(xo.std(0), std, rtol=0.01)
+    c = np.corrcoef(xo.T)
+    assert np.all(np.abs(c - np.eye(4)) < 5 / math.sqrt(J))
+    # a 4-D normal: the squared standardised radius is chi-square with 4 dof
+    q = (((xo - mean) / std) ** 2).sum(1)
+    assert q.mean() == pytest.approx(4.0, abs=5 * math.sqrt(8.0 / J))
+    assert wo.sum() == pytest.approx(PAPER.birth_mass, rel=1e-12)
+
+
+def test_predict_per_axis_process_noise():
+    """Per-axis acceleration noise: each axis follows the CV covariance with
+    its own sigma (T = 2 so a wrong power of T shows), no cross-axis terms."""
+    dt, sx, sy = 2.0, 0.7, 3.0
+    m = oracle.model(PAPER.with_(dt=dt, sigma_a=sx, sigma_a_y=sy))
+    n = 200_000
+    rng = np.random.default_rng(5)
+    noise = np.zeros((n, 4))
+    noise[:, :2] = rng.standard_normal((n, 2))
+    xo, _ = oracle.predict(m, np.tile([0.0, 1.0, 0.0, -1.0], (n, 1)), np.full(n, 1.0), 0, noise)
+    cov = np.cov(xo.T)
+    for s, sl in ((sx, slice(0, 2)), (sy, slice(2, 4))):
+        ref = s * s * np.array([[dt ** 4 / 4, dt ** 3 / 2], [dt ** 3 / 2, dt ** 2]])
+        np.testing.assert_allclose(cov[sl, sl], ref, rtol=0.02)
+    assert np.all(np.abs(cov[:2, 2:]) < 0.02 * sx * sy * dt ** 2)
+
+
 # ----------------------------------------------------------------------------
 # Update, Eq. 7-8
 # ----------------------------------------------------------------------------
