@@ -728,20 +728,22 @@ def run_gpu_learned(args, rank, world, local_rank):
     return 0
 
 
-def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p):
+def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p, extra=()):
     """The paper's three filters on the same scenarios of workload wd: the
     global filter (PHD, all particles), the distributed scheme (DCPFPHD, wd's
     PEs, ring exchange, CU fusion) and the global filter on 1/K of the
-    particles (partPHD); steps/s and OSPA (c = 100 m, order ospa_p) each."""
+    particles (partPHD), plus any `extra` (name, workload) variants; steps/s
+    and OSPA (c = 100 m, order ospa_p) each."""
     import torch
     from paper_1503_03769_gb300 import ParticlePHD
 
     K = wd.num_pe
-    variants = [("PHD", wd.with_(num_pe=1, exchange_frac=0.0)),
+    # equal capacity: the global filter gets the K slices' slots, partPHD one slice's
+    variants = [("PHD", wd.with_(num_pe=1, exchange_frac=0.0, pe_cap=K * wd.pe_cap)),
                 ("DCPFPHD", wd),
                 ("partPHD", wd.with_(num_pe=1, exchange_frac=0.0,
                                      particles_per_target=wd.particles_per_target // K,
-                                     birth_count=wd.birth_count // K))]
+                                     birth_count=wd.birth_count // K))] + list(extra)
     scen = {s_: scenario.simulate(wd, s_) for s_ in seeds}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     res = {}
@@ -791,7 +793,11 @@ def run_gpu_compare(args, rank, world, local_rank):
     wd = scenario.workload("dist16_10t")
     runs = max(1, -(-args.steps // wd.steps))
     seeds = [args.seed + r + 7919 * rank for r in range(runs)]
-    res = _three_way(args, wd, seeds, dev, rank, local_rank, 2.0)
+    # exchange variants (Step 6): all-to-all, and the ring only when a PE has
+    # degenerated (its mass below half the PE mean)
+    extra = [("DCPFPHD_all_to_all", wd.with_(exchange_mode="all")),
+             ("DCPFPHD_adaptive_0.5", wd.with_(exchange_threshold=0.5))]
+    res = _three_way(args, wd, seeds, dev, rank, local_rank, 2.0, extra)
     if rank != 0:
         return 0
     D = res["DCPFPHD"]

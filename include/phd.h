@@ -51,6 +51,7 @@ enum { PHD_FP32 = 0, PHD_FP64 = 1 };
 enum { PHD_CK_LOCAL = 0, PHD_CK_GLOBAL = 1 };
 enum { PHD_PATH_AUTO = 0, PHD_PATH_STAGED = 1, PHD_PATH_FUSED = 2 };
 enum { PHD_BIRTH_UNIFORM = 0, PHD_BIRTH_GAUSSIAN = 1 };
+enum { PHD_XCHG_RING = 0, PHD_XCHG_ALL = 1 };
 
 /* Filter configuration (plain data, copied by phd_init). */
 typedef struct phd_config {
@@ -85,6 +86,13 @@ typedef struct phd_config {
                                (kappa = lambda / (r_max theta_span)) */
     double birth_mean[4];   /* PHD_BIRTH_GAUSSIAN: mean state [x, vx, y, vy] */
     double birth_std[4];    /* PHD_BIRTH_GAUSSIAN: std per state component (diagonal Q) */
+    int32_t exchange_mode;  /* Step 6 pattern: PHD_XCHG_RING: PE j's t-th outgoing particle goes
+                               to PE j+1 (the paper's); PHD_XCHG_ALL: to PE j + 1 + (t mod (K-1))
+                               (mod K), so every PE receives from all others; either way the
+                               receiver's t-th vacated slot takes it */
+    int32_t reserved1;      /* must be 0 */
+    double exchange_threshold; /* 0: exchange every step (the paper's); > 0: only in steps where
+                               some PE has degenerated, min_j N^j < threshold * mean_j N^j */
 } phd_config;
 
 typedef struct phd_handle phd_handle;

@@ -89,6 +89,9 @@ def lib():
             L.orc_resample.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_uint32, _D, _D, _I]
             L.orc_exchange_slots.argtypes = [ctypes.c_int, ctypes.c_int, _U, _I]
+            L.orc_exchange_ex.restype = ctypes.c_int
+            L.orc_exchange_ex.argtypes = [ctypes.c_int, _D, _D, _I, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_double, _D, _U, _I]
             L.orc_exchange.argtypes = [ctypes.c_int, _D, _D, _I, ctypes.c_int, ctypes.c_double,
                                        _U, _I]
             L.orc_fuse.restype = ctypes.c_int
@@ -246,8 +249,11 @@ def exchange_slots(n: int, count: int, u) -> np.ndarray:
     return slots[:count].copy()
 
 
-def exchange(xs: List[np.ndarray], ws: List[np.ndarray], frac: float, u) -> tuple:
-    """Step 6 ring exchange over K slices; returns new (xs, ws, slots)."""
+def exchange(xs: List[np.ndarray], ws: List[np.ndarray], frac: float, u, mode: str = "ring",
+             threshold: float = 0.0, masses=None) -> tuple:
+    """Step 6 exchange over K slices (ring, or "all" to all; with threshold > 0
+    only when min_j N_j < threshold * mean_j N_j for the PE masses N_j);
+    returns new (xs, ws, slots), slots [K][L_x] (L_x = 0 when it did not run)."""
     K = len(xs)
     counts = np.asarray([len(a) for a in xs], dtype=np.int32)
     u = np.ascontiguousarray(np.asarray(u, dtype=np.uint32))
@@ -259,9 +265,11 @@ def exchange(xs: List[np.ndarray], ws: List[np.ndarray], frac: float, u) -> tupl
         X[j, :counts[j]] = xs[j]
         W[j, :counts[j]] = ws[j]
     nmin = int(counts.min()) if K else 0
-    Lx = int(np.floor(frac * nmin)) if K > 1 else 0
-    slots = np.zeros((K, max(Lx, 1)), dtype=np.int32)
-    lib().orc_exchange(K, _d(X), _d(W), _i(counts), stride, float(frac), _u(u), _i(slots))
+    cap = int(np.floor(frac * nmin)) if K > 1 else 0
+    slots = np.zeros((K, max(cap, 1)), dtype=np.int32)
+    mass = _f64(masses if masses is not None else np.zeros(max(K, 1)), (-1,))
+    Lx = lib().orc_exchange_ex(K, _d(X), _d(W), _i(counts), stride, float(frac), 1 if mode == "all" else 0,
+                               float(threshold), _d(mass), _u(u), _i(slots))
     return ([X[j, :counts[j]].copy() for j in range(K)],
             [W[j, :counts[j]].copy() for j in range(K)], slots[:, :Lx].copy())
 
@@ -437,7 +445,8 @@ class OracleFilter:
         # Step 6: ring exchange
         slots = None
         if K > 1 and self.w.exchange_frac > 0:
-            xr, wr, slots = exchange(xr, wr, self.w.exchange_frac, xu)
+            xr, wr, slots = exchange(xr, wr, self.w.exchange_frac, xu, getattr(self.w, "exchange_mode", "ring"),
+                                     getattr(self.w, "exchange_threshold", 0.0), Nk)
         self.x, self.wt = xr, wr
         self.last = dict(x_pred=xp, w_pred=wp, C_local=C_loc, C_used=C_used, w_upd=wu,
                          Nk=Nk, extract=ex, parents=par, slots=slots)

@@ -279,20 +279,35 @@ void orc_exchange_slots(int n, int count, const uint32_t *u, int *slots)
     free(perm);
 }
 
-/* Step 6 "Local exchange" on a ring (PE j sends to PE j+1, PE K-1 to PE 0).
- * Each PE j picks L_x random slots s_j; the particle-weight couples in s_j
- * move to PE j+1 and land in the slots s_{j+1} that PE j+1 vacated.  With
- * L_x = floor(frac * min_j n_j) every PE sends and receives the same number,
- * so slice sizes and the union of all particles are unchanged.
+/* Step 6 "Local exchange".  Each PE j picks L_x random slots s_j; its t-th
+ * chosen particle-weight couple moves to PE d = j + shift_t (mod K) and lands
+ * in the t-th slot s_d that PE d vacated.  The paper's ring has shift_t = 1
+ * (PE j sends to PE j+1, PE K-1 to PE 0); the all-to-all pattern (mode 1, a
+ * variant the paper leaves to future work) has shift_t = 1 + (t mod (K-1)),
+ * so a PE's outgoing particles spread over all other PEs.  For each t the
+ * shift is the same for every PE, so every PE sends and receives one
+ * particle per t: with L_x = floor(frac * min_j n_j) slice sizes and the
+ * union of all particles are unchanged.  Adaptive trigger (threshold > 0):
+ * the exchange runs only when some PE has degenerated, i.e. its mass is
+ * negligible next to the others': min_j N_j < threshold * (sum_j N_j) / K
+ * (the PE masses N_j of this step's update).
  * x, w: K slices of stride `stride` particles; counts: n_j; u: [K][stride]. */
-void orc_exchange(int K, double *x, double *w, const int *counts, int stride, double frac,
-                  const uint32_t *u, int *slots_out)
+int orc_exchange_ex(int K, double *x, double *w, const int *counts, int stride, double frac, int mode,
+                    double threshold, const double *mass, const uint32_t *u, int *slots_out)
 {
-    if (K <= 1) return;
+    if (K <= 1) return 0;
+    if (threshold > 0.0) {
+        double sum = 0.0, mn = mass[0];
+        for (int j = 0; j < K; ++j) {
+            sum += mass[j];
+            if (mass[j] < mn) mn = mass[j];
+        }
+        if (!(mn < threshold * (sum / (double)K))) return 0;
+    }
     int nmin = counts[0];
     for (int j = 1; j < K; ++j) if (counts[j] < nmin) nmin = counts[j];
     int Lx = (int)floor(frac * (double)nmin);
-    if (Lx <= 0) return;
+    if (Lx <= 0) return 0;
     int *slots = (int *)malloc(sizeof(int) * (size_t)K * (size_t)Lx);
     for (int j = 0; j < K; ++j)
         orc_exchange_slots(counts[j], Lx, u + (size_t)j * stride, slots + (size_t)j * Lx);
@@ -305,8 +320,9 @@ void orc_exchange(int K, double *x, double *w, const int *counts, int stride, do
             ws[(size_t)j * Lx + t] = w[src];
         }
     for (int j = 0; j < K; ++j) {
-        int k = (j + 1) % K;
         for (int t = 0; t < Lx; ++t) {
+            int shift = (mode == 1 && K > 2) ? 1 + t % (K - 1) : 1;
+            int k = (j + shift) % K;
             size_t dst = (size_t)k * stride + (size_t)slots[(size_t)k * Lx + t];
             for (int d = 0; d < 4; ++d) x[4 * dst + d] = xs[4 * ((size_t)j * Lx + t) + d];
             w[dst] = ws[(size_t)j * Lx + t];
@@ -316,6 +332,14 @@ void orc_exchange(int K, double *x, double *w, const int *counts, int stride, do
     free(slots);
     free(xs);
     free(ws);
+    return Lx;
+}
+
+/* The paper's ring exchange, every step. */
+void orc_exchange(int K, double *x, double *w, const int *counts, int stride, double frac,
+                  const uint32_t *u, int *slots_out)
+{
+    orc_exchange_ex(K, x, w, counts, stride, frac, 0, 0.0, NULL, u, slots_out);
 }
 
 /* Step 4 "Global Estimation" at the central unit: a label (measurement index)

@@ -750,11 +750,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       if (!grid_sync(d)) return;
       int lx = 0;
       if (xchg) {
-        // smallest resample count over the PEs: the K counts loaded at once
-        int nmin = INT_MAX;
-        for (int k = lane; k < m.K; k += 32) nmin = min(nmin, __ldcg(d.rs_L + k));
-        nmin = __reduce_min_sync(0xffffffffu, nmin);
-        lx = (int)floor(m.exchange_frac * (double)nmin);
+        // exchange count from all PEs' counts (and masses), by warp 0
+        __shared__ int lx_s;
+        if (tid < 32) {
+          const int c = exchange_count_warp(d, m, reinterpret_cast<double*>(smem + SL.red));
+          if (tid == 0) lx_s = c;
+        }
+        __syncthreads();
+        lx = lx_s;
         if (j == 0 && tid == 0) *d.lx = lx;
       }
       // the exchange draws are independent: made in parallel; the swaps are
@@ -796,10 +799,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
       if (!grid_sync(d)) return;
       if (xchg && lx > 0) {
-        const int from = (j + m.K - 1) % m.K;
         const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
         const R* wo = static_cast<const R*>(d.w_out);
         for (int t = tid; t < lx; t += T) {
+          const int from = exchange_source(m, j, t);
           const long dst = base + perm[t];
           gx[dst] = xo[(long)from * m.pe_cap + t];
           gw[dst] = wo[(long)from * m.pe_cap + t];

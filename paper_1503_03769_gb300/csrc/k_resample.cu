@@ -180,12 +180,16 @@ __global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
 __global__ void k_xplan(Dev d, Model m, const uint32_t* __restrict__ xu) {
   pdl_enter();
   extern __shared__ int perm[];
+  __shared__ double msm[kMaxPE];
+  __shared__ int lx_s;
   const int j = blockIdx.x;
-  const int K = m.K;
   const int n = d.rs_L[j];
-  int nmin = d.rs_L[0];
-  for (int k = 1; k < K; ++k) nmin = min(nmin, d.rs_L[k]);
-  const int lx = (int)floor(m.exchange_frac * (double)nmin);
+  if (threadIdx.x < 32) {
+    const int c = exchange_count_warp(d, m, msm);
+    if (threadIdx.x == 0) lx_s = c;
+  }
+  __syncthreads();
+  const int lx = lx_s;
   if (j == 0 && threadIdx.x == 0) *d.lx = lx;
   if (lx <= 0) return;
   // perm in the first n ints, the (independent) draws after it; swaps serial
@@ -226,7 +230,7 @@ __global__ void k_xout(Dev d, Model m) {
   }
 }
 
-// PE j's chosen slots receive PE j-1's outbox (ring).
+// PE j's chosen slots receive the outboxes of its sources (exchange_source).
 template <class R>
 __global__ void k_xin(Dev d, Model m) {
   pdl_enter();
@@ -239,7 +243,7 @@ __global__ void k_xin(Dev d, Model m) {
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
     const int j = (int)(g / lx);
     const int t = (int)(g - (long)j * lx);
-    const int from = (j + m.K - 1) % m.K;
+    const int from = exchange_source(m, j, t);
     const long dst = (long)j * m.pe_cap + d.xslots[(long)j * m.pe_cap + t];
     x[dst] = xo[(long)from * m.pe_cap + t];
     w[dst] = wo[(long)from * m.pe_cap + t];

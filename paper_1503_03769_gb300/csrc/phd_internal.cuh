@@ -57,6 +57,8 @@ struct Model {
   double bmean[4], bstd[4];
   double rho_pe;         // particles per target per PE
   double exchange_frac;
+  int xmode;             // 0 ring, 1 all-to-all
+  double xthresh;        // adaptive trigger (0: every step)
   // likelihood in exp2 form: g = cnorm * 2^-(a0^2 d0^2 + a1^2 d1^2)
   double a0, a1;         // sqrt(log2(e) / 2) / sigma per measurement coordinate
   double cnorm;          // 1 / (2 pi s0 s1)
@@ -632,6 +634,44 @@ __device__ __forceinline__ void predict_slot(const Cst<R>& c, bool survivor, con
     o.vy = c.bv * n2;
     wo = bw;
   }
+}
+
+// Step 6: the source PE of receiver j's t-th exchanged particle (ring: j - 1;
+// all-to-all: j - 1 - (t mod (K - 1)), so for each t the sources are a
+// rotation of the PEs and every PE sends and receives one particle).
+__device__ __forceinline__ int exchange_source(const Model& m, int j, int t) {
+  const int s = m.xmode && m.K > 2 ? 1 + t % (m.K - 1) : 1;
+  return (j + m.K - s) % m.K;
+}
+
+// Particles each PE sends in this step's exchange, by one whole warp: L_x =
+// floor(frac * min_j L_j) over the PEs' resample counts, or 0 when the
+// adaptive trigger is on and no PE has degenerated, i.e. unless
+// min_j N^j < threshold * (sum_j N^j) / K (N^j the PEs' masses after the
+// update, summed in PE order in FP64).  The lanes load the K counts and
+// masses at once (sm: K doubles of scratch); every lane returns L_x.
+__device__ __forceinline__ int exchange_count_warp(const Dev& d, const Model& m, double* sm) {
+  const int lane = threadIdx.x & 31;
+  int nmin = INT_MAX;
+  for (int k = lane; k < m.K; k += 32) {
+    nmin = min(nmin, __ldcg(d.rs_L + k));
+    if (m.xthresh > 0.0) sm[k] = __ldcg(d.rs_mass + k);
+  }
+  nmin = __reduce_min_sync(0xffffffffu, nmin);
+  __syncwarp();
+  int due = 1;
+  if (m.xthresh > 0.0) {
+    if (lane == 0) {
+      double sum = 0.0, mn = INFINITY;
+      for (int k = 0; k < m.K; ++k) {
+        sum += sm[k];
+        mn = fmin(mn, sm[k]);
+      }
+      due = mn < m.xthresh * (sum / (double)m.K) ? 1 : 0;
+    }
+    due = __shfl_sync(0xffffffffu, due, 0);
+  }
+  return due ? (int)floor(m.exchange_frac * (double)nmin) : 0;
 }
 
 // Birth weight nu_b / J_j of PE j.

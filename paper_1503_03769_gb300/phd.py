@@ -24,6 +24,7 @@ PHD_FP32, PHD_FP64 = 0, 1
 PHD_CK_LOCAL, PHD_CK_GLOBAL = 0, 1
 PHD_PATH_AUTO, PHD_PATH_STAGED, PHD_PATH_FUSED = 0, 1, 2
 PHD_BIRTH_UNIFORM, PHD_BIRTH_GAUSSIAN = 0, 1
+PHD_XCHG_RING, PHD_XCHG_ALL = 0, 1
 _PATHS = {"auto": PHD_PATH_AUTO, "staged": PHD_PATH_STAGED, "fused": PHD_PATH_FUSED}
 
 
@@ -49,6 +50,8 @@ class phd_config(ctypes.Structure):
         ("exchange_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("sigma_a_y", ctypes.c_double), ("theta_span", ctypes.c_double),
         ("birth_mean", ctypes.c_double * 4), ("birth_std", ctypes.c_double * 4),
+        ("exchange_mode", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("exchange_threshold", ctypes.c_double),
     ]
 
 
@@ -178,6 +181,8 @@ def make_config(w, seed: int = 0) -> phd_config:
         c.birth_mean[k] = float(v)
     for k, v in enumerate(getattr(w, "birth_std", (0.0,) * 4)):
         c.birth_std[k] = float(v)
+    c.exchange_mode = PHD_XCHG_ALL if getattr(w, "exchange_mode", "ring") == "all" else PHD_XCHG_RING
+    c.exchange_threshold = float(getattr(w, "exchange_threshold", 0.0))
     return c
 
 

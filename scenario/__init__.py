@@ -72,6 +72,8 @@ class Workload:
     birth_model: str = "uniform"            # "uniform" or "gaussian" (N(birth_mean, diag birth_std^2))
     birth_mean: tuple = (0.0, 0.0, 0.0, 0.0)
     birth_std: tuple = (0.0, 0.0, 0.0, 0.0)
+    exchange_mode: str = "ring"             # Step 6 pattern: "ring" (the paper's) or "all" (all-to-all)
+    exchange_threshold: float = 0.0         # > 0: exchange only when min_j N_j < threshold * mean_j N_j
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)

@@ -175,7 +175,10 @@ def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
         rxs.append(xo)
         rws.append(wo)
     if K > 1 and w.exchange_frac > 0:
-        rxs, rws, slots = oracle.exchange(rxs, rws, w.exchange_frac, xu)
+        # the exchange stage's input: the resampled slices and, for the
+        # adaptive trigger, the PE masses the GPU's update produced
+        rxs, rws, slots = oracle.exchange(rxs, rws, w.exchange_frac, xu, w.exchange_mode,
+                                          w.exchange_threshold, np.asarray(mass, np.float64)[:K])
         assert lx == slots.shape[1]
     for j in range(K):
         assert len(xr[j]) == len(rxs[j])

@@ -130,6 +130,22 @@ def test_fused_many_pes_small_slices(pe_cap):
     assert rep.compared_labels > 0
 
 
+@pytest.mark.parametrize("mode,threshold", [("all", 0.0), ("ring", 1e-9), ("all", 1e9), ("all", 0.97)])
+@pytest.mark.parametrize("path", ["staged", "fused"])
+def test_exchange_variants_stages(mode, threshold, path):
+    """Step 6 variants on 16 PEs: all-to-all every step; the adaptive trigger
+    never firing (threshold 1e-9), always firing (1e9) and deciding from the
+    step's PE masses (0.97); the GPU's exchange count must be the oracle's."""
+    w = scenario.workload("dist16_10t", n_targets=6, clutter_rate=30.0, particles_per_target=800,
+                          birth_count=1000, birth_steps=(1,) * 6, exchange_mode=mode,
+                          exchange_threshold=threshold)
+    truth = scenario.simulate(w, 9, steps=3)
+    centres = np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)])[:6]
+    counts = [300 + 37 * j for j in range(16)]
+    rep = _run_stages(w, 9, 3, sc=truth, n_seed=counts, centres=centres, path=path)
+    assert rep.compared_labels > 0
+
+
 @pytest.mark.parametrize("path", ["staged", "fused"])
 def test_range_bearing_stages_many_measurements(path):
     """Range-bearing sensor, M ~ 330 (> one 256-thread round), 4 PEs, FP32."""

@@ -443,6 +443,76 @@ def test_exchange_is_a_ring_move():
     assert sum(a.sum() for a in nw) == pytest.approx(sum(a.sum() for a in ws), rel=1e-15)
 
 
+def _tagged_slices(rng, counts, stride):
+    """Slices whose particles carry their PE and slot in the state (x = PE,
+    vx = slot) so a move's source can be read off the destination."""
+    xs, ws = [], []
+    for j, n in enumerate(counts):
+        x = rng.standard_normal((n, 4))
+        x[:, 0], x[:, 1] = j, np.arange(n)
+        xs.append(x)
+        ws.append(rng.random(n))
+    u = rng.integers(0, 2 ** 32, size=(len(counts), stride), dtype=np.uint64).astype(np.uint32)
+    return xs, ws, u
+
+
+def test_all_to_all_exchange_reaches_every_pe():
+    """The all-to-all variant: PE j's t-th chosen particle lands in the t-th
+    vacated slot of PE j + 1 + (t mod (K-1)); every PE then holds particles of
+    all K-1 others, keeps its count, and the union and the mass are unchanged."""
+    rng = np.random.default_rng(21)
+    K, stride = 5, 128
+    counts = [90, 84, 101, 95, 88]
+    xs, ws, u = _tagged_slices(rng, counts, stride)
+    nx, nw, slots = oracle.exchange(xs, ws, 0.1, u, "all")
+    Lx = int(math.floor(0.1 * min(counts)))
+    assert slots.shape == (K, Lx) and Lx == 8
+    assert [len(a) for a in nx] == counts
+    for d in range(K):
+        got = nx[d][slots[d]]
+        for t in range(Lx):
+            src = (d - 1 - t % (K - 1)) % K
+            assert got[t, 0] == src and got[t, 1] == slots[src][t]
+            assert nw[d][slots[d][t]] == ws[src][slots[src][t]]
+        assert set(got[:, 0].astype(int)) == set(range(K)) - {d}
+        keep = np.setdiff1d(np.arange(counts[d]), slots[d])
+        np.testing.assert_array_equal(nx[d][keep], xs[d][keep])
+    before = np.sort(np.concatenate([np.c_[a, b] for a, b in zip(xs, ws)]).view("u8"), axis=0)
+    after = np.sort(np.concatenate([np.c_[a, b] for a, b in zip(nx, nw)]).view("u8"), axis=0)
+    np.testing.assert_array_equal(before, after)
+    # with two PEs all-to-all is the ring
+    a = oracle.exchange(xs[:2], ws[:2], 0.1, u[:2], "all")
+    b = oracle.exchange(xs[:2], ws[:2], 0.1, u[:2], "ring")
+    for p, q in zip(a[0] + a[1], b[0] + b[1]):
+        np.testing.assert_array_equal(p, q)
+
+
+@pytest.mark.parametrize("mode", ["ring", "all"])
+def test_adaptive_exchange_trigger(mode):
+    """Adaptive trigger (threshold > 0): nothing moves while every PE's mass
+    is at least threshold x the mean; once one PE's mass drops below it the
+    exchange is exactly the unconditional one."""
+    rng = np.random.default_rng(4)
+    K, stride = 4, 64
+    counts = [40, 44, 41, 50]
+    xs, ws, u = _tagged_slices(rng, counts, stride)
+    even = np.array([2.0, 2.1, 1.9, 2.0])
+    nx, nw, slots = oracle.exchange(xs, ws, 0.1, u, mode, 0.5, even)
+    assert slots.shape == (K, 0)
+    for a, b in zip(nx + nw, xs + ws):
+        np.testing.assert_array_equal(a, b)
+    # mean 1.525, threshold 0.5: 0.76 > 0.1, the exchange runs
+    starved = np.array([2.0, 2.1, 0.1, 1.9])
+    got = oracle.exchange(xs, ws, 0.1, u, mode, 0.5, starved)
+    ref = oracle.exchange(xs, ws, 0.1, u, mode)
+    assert got[2].shape == (K, 4)
+    for a, b in zip(got[0] + got[1], ref[0] + ref[1]):
+        np.testing.assert_array_equal(a, b)
+    # the boundary is strict: min == threshold x mean does not trigger
+    edge = np.array([1.0, 3.0, 3.0, 1.0])          # mean 2, threshold 0.5 -> 1.0
+    assert oracle.exchange(xs, ws, 0.1, u, mode, 0.5, edge)[2].shape == (K, 0)
+
+
 def test_exchange_slots_are_uniform():
     rng = np.random.default_rng(1)
     n, cnt, R = 10, 3, 20000
