@@ -301,10 +301,14 @@ phd_status phd_run(phd_handle *h, const void *d_Z, const int32_t *d_offsets, int
 phd_status phd_set_path(phd_handle *h, int32_t path);
 phd_status phd_get_path(phd_handle *h, int32_t *path);
 
-/* phd_step from host memory: copies h_Z [M][2] to the device, runs the step,
- * copies the estimates back to h_states [cap][4] / h_labels [cap] and their
- * true count to *h_count.  Host buffers may be pageable; pinned is faster.
- * Synchronises.  Errors as phd_step; PHD_ERR_INVALID_ARG for non-finite h_Z. */
+/* phd_step from host memory: h_Z [M][2] in, the estimates out to h_states
+ * [cap][4] / h_labels [cap] and their true count to *h_count.  When h_Z and
+ * the two output buffers are pinned and mapped (cudaHostAlloc or
+ * cudaHostRegister memory) the step's kernels read h_Z and write the outputs
+ * in host memory themselves (zero copy; over NVLink-C2C on Grace systems)
+ * and the call synchronises once; otherwise (pageable buffers) it copies
+ * through the workspace.  Synchronises.  Errors as phd_step;
+ * PHD_ERR_INVALID_ARG for non-finite h_Z. */
 phd_status phd_step_host(phd_handle *h, const void *h_Z, int32_t M, void *h_states,
                          int32_t *h_labels, int32_t cap, int32_t *h_count);
 

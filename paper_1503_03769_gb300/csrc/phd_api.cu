@@ -46,6 +46,7 @@ struct phd_handle {
   bool have_update = false;
   int batch_runs = 0;      // > 0: a batch of independent one-PE filters
   std::vector<int> slice_J;  // births per step of each slice (host copy)
+  int* pin = nullptr;        // pinned mapped host ints of phd_step_host: [0] count, [1] error word
 };
 
 namespace {
@@ -590,6 +591,18 @@ phd_status run_fused(phd_handle* h, const void* Z, const int* zoff, int M, int S
 
 // The output contract of phd_step: estimates into the caller's buffers (or
 // the workspace's), the true count on the device.
+// Device address of a host buffer the GPU can read and write in place
+// (pinned and mapped: cudaHostAlloc / cudaHostRegister memory), else NULL.
+void* mapped_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u,
                        const uint32_t* xu, void* d_states, int* d_labels, int cap, int* d_count) {
   phd_status st;
@@ -615,9 +628,8 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
     if (st == PHD_OK && cap > 0) {
       const size_t rs = real_size(h->cfg);
       const int ncp = cap < h->cfg.m_max ? cap : h->cfg.m_max;
-      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
-      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDeviceToDevice,
-                                  h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDefault, h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDefault, h->stream));
     }
   } else {
     st = stage_z_only(h, Z, M);
@@ -625,15 +637,14 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
     if (st == PHD_OK && cap > 0) {
       const size_t rs = real_size(h->cfg);
       const int ncp = cap < h->cfg.m_max ? cap : h->cfg.m_max;
-      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDeviceToDevice, h->stream));
-      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDeviceToDevice,
-                                  h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_states, h->out_states, (size_t)ncp * 4 * rs, cudaMemcpyDefault, h->stream));
+      PHD_CUDA(h, cudaMemcpyAsync(d_labels, h->out_labels, (size_t)ncp * sizeof(int), cudaMemcpyDefault, h->stream));
     }
   }
   if (st != PHD_OK) return st;
   h->have_update = true;
   if (d_count && !fused)
-    PHD_CUDA(h, cudaMemcpyAsync(d_count, h->d.out_count, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    PHD_CUDA(h, cudaMemcpyAsync(d_count, h->d.out_count, sizeof(int), cudaMemcpyDefault, h->stream));
   return PHD_OK;
 }
 
@@ -737,6 +748,7 @@ phd_status phd_destroy(phd_handle* h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->pin) cudaFreeHost(h->pin);
   delete h;
   return e == cudaSuccess ? PHD_OK : PHD_ERR_CUDA;
 }
@@ -853,6 +865,29 @@ phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_stat
   for (int i = 0; i < 2 * M; ++i) {
     const double v = rs == 8 ? static_cast<const double*>(h_Z)[i] : (double)static_cast<const float*>(h_Z)[i];
     if (!std::isfinite(v)) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
+  }
+  // Pinned (mapped) host buffers: the step reads Z and writes the estimates
+  // and the count in host memory itself (over NVLink-C2C on Grace systems),
+  // with one synchronisation; otherwise staged copies.
+  void* zd = M > 0 ? mapped_ptr(h_Z) : nullptr;
+  void* sd = cap > 0 ? mapped_ptr(h_states) : nullptr;
+  void* ld = cap > 0 ? mapped_ptr(h_labels) : nullptr;
+  if ((M == 0 || zd) && (cap == 0 || (sd && ld))) {
+    if (!h->pin) PHD_CUDA(h, cudaHostAlloc(reinterpret_cast<void**>(&h->pin), 2 * sizeof(int), cudaHostAllocMapped));
+    int* pin_d = static_cast<int*>(mapped_ptr(h->pin));
+    if (!pin_d) return fail(h, PHD_ERR_CUDA, "phd_step_host: no device address for the pinned count");
+    phd_status st = step_common(h, M > 0 ? zd : h->d.Z, M, nullptr, nullptr, nullptr, sd, static_cast<int*>(ld), cap,
+                                pin_d);
+    if (st != PHD_OK) return st;
+    PHD_CUDA(h, cudaMemcpyAsync(h->pin + 1, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int n = h->pin[0];
+    *h_count = n;
+    if (h->pin[1] != 0) {
+      phd_status es = read_device_error(h);
+      if (es != PHD_OK) return es;
+    }
+    return n > cap ? fail(h, PHD_ERR_CAPACITY, "more estimates than cap") : PHD_OK;
   }
   if (M > 0) PHD_CUDA(h, cudaMemcpyAsync(h->d.Z, h_Z, (size_t)M * 2 * rs, cudaMemcpyHostToDevice, h->stream));
   phd_status st = step_common(h, h->d.Z, M, nullptr, nullptr, nullptr, h->out_states, h->out_labels, h->cfg.m_max,

@@ -386,20 +386,42 @@ def test_checkpoint_resume_is_bit_identical(path):
         np.testing.assert_array_equal(wa[j], wb[j])
 
 
+@pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("path", ["staged", "fused"])
-def test_step_host_matches_device_step(path):
+def test_step_host_matches_device_step(path, pinned):
+    """Host-memory steps equal device steps: pageable buffers (copies through
+    the workspace) and pinned ones (the kernels read Z and write the
+    estimates and count in host memory), then a too-small cap."""
+    from paper_1503_03769_gb300 import PhdError
     w = scenario.workload("dist16_10t", num_pe=4, n_targets=4, clutter_rate=20.0,
                           particles_per_target=300, birth_count=400)
-    sc = scenario.simulate(w, 8, steps=5)
+    sc = scenario.simulate(w, 8, steps=6)
     a, b = _filter(w, 8, path), _filter(w, 8, path)
-    out_s = np.zeros((w.m_max, 4), np.float32)
-    out_l = np.zeros(w.m_max, np.int32)
-    for Z in sc.meas:
+
+    def host(shape, dt):
+        t = torch.zeros(shape, dtype=dt)
+        return (t.pin_memory() if pinned else t).numpy()
+
+    out_s = host((w.m_max, 4), torch.float32)
+    out_l = host(w.m_max, torch.int32)
+    for Z in sc.meas[:5]:
+        Zh = host(Z.shape, torch.float32)
+        Zh[:] = Z
         sa, la = a.step(Z)
-        n = b.step_host(Z, out_s, out_l)
+        n = b.step_host(Zh, out_s, out_l)
         assert n == len(la)
         np.testing.assert_array_equal(out_l[:n], la.cpu().numpy())
         np.testing.assert_array_equal(out_s[:n], sa.cpu().numpy())
+    Z = sc.meas[5]
+    Zh = host(Z.shape, torch.float32)
+    Zh[:] = Z
+    sa, la = a.step(Z)
+    if len(la) > 0:
+        with pytest.raises(PhdError) as ei:
+            b.step_host(Zh, out_s[:0], out_l[:0])
+        assert ei.value.count == len(la)
+    a.close()
+    b.close()
 
 
 def test_fused_run_matches_fused_steps():
