@@ -279,7 +279,7 @@ def run_gpu(args, w, rank, world, local_rank):
     steps_per_run = w.steps
     # steady-state window: scans before `steady` of every run are replayed
     # untimed (all truth targets exist from 40 % of the run on)
-    steady = args.steady_from if args.steady_from is not None else (50 if w.name == "dense_rb_100t" else 0)
+    steady = args.steady_from if args.steady_from is not None else (50 if w.name.startswith("dense_rb_100t") else 0)
     per_run = steps_per_run - steady
     runs = max(1, math.ceil((args.warmup + args.steps) / per_run))
     base_seed = args.seed + 1000 * rank

@@ -286,6 +286,51 @@ def test_dense_workload_sampled():
     f.close()
 
 
+def test_dense_workload_64_pes_sampled():
+    """The dense workload's 64-PE distributed form (config 3) at full size on
+    the staged path, autotuned: after 20 free-running scans, one step with
+    injected noise is checked per PE on samples (C of 12 measurements and
+    the updated weights of 400 particles on 6 PEs), the Eq. 8 mass closed
+    form on every PE, and the CU fusion of the GPU's own local estimates."""
+    w = scenario.workload("dense_rb_100t", num_pe=64)
+    sc = scenario.simulate(w, 6, steps=21)
+    f = _filter(w, 6)
+    m = oracle.model(w)
+    kap = oracle.kappa(m)
+    for k in range(20):
+        f.step(sc.meas[k])
+    f.autotune(2)
+    noise = scenario.step_noise(6, 20, w.num_pe, w.pe_cap, np.float32)
+    f.predict(torch.as_tensor(noise).cuda())
+    xp, wp = f.get_state()
+    Z = sc.meas[20]
+    M = len(Z)
+    # each PE keeps rho / 64 ~ 31 particles per target it believes in: ~2.8e4 here
+    assert M > 450 and sum(len(a) for a in xp) > 20_000
+    f.update(torch.as_tensor(Z).cuda())
+    C, mass = f.get_update()
+    _, wu = f.get_state()
+    rng = np.random.default_rng(6)
+    for j in rng.choice(64, 6, replace=False):
+        sel_p = rng.choice(M, 12, replace=False)
+        Co = oracle.colsum(m, xp[j], wp[j], Z[sel_p].astype(np.float64))
+        assert np.all(np.abs(C[j, sel_p] - Co) <= 1e-4 * Co + 1e-7 * kap), j
+        sel_i = rng.choice(len(xp[j]), min(400, len(xp[j])), replace=False)
+        wo = oracle.weight_update(m, xp[j][sel_i], wp[j][sel_i], Z.astype(np.float64), C[j, :M])
+        check_weights(wu[j][sel_i], wo, dict(w_rel=1e-4), f"sampled weights PE {j}")
+    for j in range(64):
+        ref = (1 - w.p_d) * wp[j].astype(np.float64).sum() + np.sum(C[j, :M] / (kap + C[j, :M]))
+        assert abs(mass[j] - ref) <= 1e-5 * max(ref, 1e-12), j
+    states, labels = f.extract()
+    loc_s, loc_l = f.get_local_estimates()
+    per_pe = [oracle.Extraction(np.asarray(loc_l[j], np.int32), np.asarray(loc_s[j], np.float64), np.zeros(M), 0.0,
+                                len(loc_l[j])) for j in range(64)]
+    fl, fz = oracle.fuse(per_pe, M)
+    assert list(labels.cpu().numpy()) == list(fl)
+    np.testing.assert_allclose(states.cpu().numpy().astype(np.float64), fz, rtol=0, atol=1e-3)
+    f.close()
+
+
 def test_edge_cases_and_errors():
     from paper_1503_03769_gb300 import PhdError
     from paper_1503_03769_gb300 import phd as P
