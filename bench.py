@@ -538,6 +538,7 @@ def run_gpu_batch(args, rank, world, local_rank):
     clk = ClockSampler(gpu_id)
     clk.begin()
     evs = []
+    logs = []   # (scan, states, counts) of every 4th scan of the runs begun in the warm-up
     nvtx_push("timed")
     for k in range(args.warmup, total):
         if k % steps_per_run == 0:
@@ -546,9 +547,11 @@ def run_gpu_batch(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.batch_step(packed=packed[k % steps_per_run], cap=cap, sync=False)
+        s_, l_, c_ = b.batch_step(packed=packed[k % steps_per_run], cap=cap, sync=False)
         e1.record()
         evs.append((e0, e1))
+        if k < steps_per_run and k % 4 == 0:
+            logs.append((k, s_, c_))
     nvtx_pop()
     torch.cuda.synchronize()
     if world > 1:
@@ -561,6 +564,48 @@ def run_gpu_batch(args, rank, world, local_rank):
     pairs, ms = job_totals(pairs, ms, world, dev)
     upd_ms = st["update_ms"]
     b.close()
+    # the same runs one at a time through the one-filter API (fused path where
+    # a run fits, else staged): a sample of every 8th run over its whole 60
+    # scans, L2 flushed between steps as above; OSPA of both on those runs
+    from paper_1503_03769_gb300 import ParticlePHD
+    sample = list(range(0, R, 8))
+    one_ms, one_steps, one_ospa, paths = 0.0, 0, [], set()
+    for r in sample:
+        f = ParticlePHD(ws[r], seed=5000 + r + rank, device=f"cuda:{local_rank}")
+        paths.add(f.get_path())
+        Zr = [torch.as_tensor(z, dtype=torch.float32, device=dev) for z in scen[r].meas]
+        evr, lg = [], []
+        for k in range(steps_per_run):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s1, l1, c1 = f.step(Zr[k], cap=cap, sync=False)
+            e1.record()
+            evr.append((e0, e1))
+            if k >= args.warmup and k % 4 == 0:
+                lg.append((k, s1.clone(), c1.clone()))
+        torch.cuda.synchronize()
+        one_ms += sum(a.elapsed_time(c) for a, c in evr)
+        one_steps += len(evr)
+        for k, s1, c1 in lg:
+            n = int(c1.item())
+            tr = scen[r].truth[k]
+            one_ospa.append(ospa_metric(s1[:n].double().cpu().numpy()[:, [0, 2]] if n else np.zeros((0, 2)),
+                                        tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+        f.close()
+    batch_ospa = []
+    for k, s_, c_ in logs:
+        if k < args.warmup:
+            continue
+        cn = c_.cpu().numpy()
+        sn = s_.double().cpu().numpy()
+        for r in sample:
+            n = min(int(cn[r]), cap)
+            tr = scen[r].truth[k]
+            batch_ospa.append(ospa_metric(sn[r, :n][:, [0, 2]] if n else np.zeros((0, 2)),
+                                          tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+    one_rs = one_steps / (one_ms * 1e-3) if one_ms > 0 else None
     if rank != 0:
         return 0
     achieved = (st["pairs"] / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
@@ -574,6 +619,13 @@ def run_gpu_batch(args, rank, world, local_rank):
                    "l2": "flushed between timed batched steps (512 MiB write, outside the events)",
                    "global_batch": R, "seq_len": steps_per_run, "parallelism": "replicas"},
         "run_steps_per_s": world * R * args.steps / (ms * 1e-3),
+        "vs_one_filter_at_a_time": {
+            "runs_sampled": len(sample), "paths": sorted(paths), "run_steps_per_s": one_rs,
+            "speedup": (R * args.steps / (ms * 1e-3)) / one_rs if one_rs else None,
+            "ospa_batch": float(np.mean(batch_ospa)) if batch_ospa else None,
+            "ospa_one_at_a_time": float(np.mean(one_ospa)) if one_ospa else None,
+            "note": "every 8th run of the batch stepped alone over its 60 scans; OSPA (c = 100 m, p = 2) "
+                    "on every 4th scan of those runs, batch vs alone"},
         "per_run_latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "roofline": {"bound": "alu", "kernel": UPDATE_KERNELS,
                      "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
