@@ -122,48 +122,42 @@ __device__ __forceinline__ int pow2_floor(int v) {
   return p;
 }
 
-// Block reduction of per-thread values in the kernel's precision: within each
-// warp in R, the 32 warp totals in FP64 by warp 0 (fixed order), result
-// broadcast to every thread.  In FP32 mode the FP64 work is 5 shuffle-adds
-// in one warp; in FP64 mode everything is FP64.
+// The three block reductions after pass 2 with two barriers: the mass N^j
+// (within each warp in R, the 32 warp totals in FP64 by warp 0 in a fixed
+// order; in FP32 mode the FP64 work is 5 shuffle-adds in one warp), the
+// largest weight, and the count of measurements with dW > 0.  wred: 64 reals,
+// ired: 32 ints (distinct shared scratch); every thread gets all three.
 template <class R>
-__device__ __forceinline__ double block_sum_r(R v, R* wred, double* out) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
+__device__ __forceinline__ void block_mass_stats(R sum, R mx, int cnt, R* wred, int* ired, double* bN, double& N,
+                                                 R& wmax, int& npos) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_down_sync(0xffffffffu, sum, o);
+    const R u = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = u > mx ? u : mx;
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0) {
+    wred[wid] = sum;
+    wred[32 + wid] = mx;
+    ired[wid] = cnt;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? (double)wred[threadIdx.x] : 0.0;
+    double t = threadIdx.x < nw ? (double)wred[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) *out = t;
+    if (threadIdx.x == 0) *bN = t;
+  }
+  R m = 0;
+  int c = 0;
+  for (int k = 0; k < nw; ++k) {
+    m = wred[32 + k] > m ? wred[32 + k] : m;
+    c += ired[k];
   }
   __syncthreads();
-  return *out;
-}
-
-template <class R>
-__device__ __forceinline__ R block_max_r(R v, R* wred) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const R u = __shfl_down_sync(0xffffffffu, v, o);
-    v = u > v ? u : v;
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
-  __syncthreads();
-  R r = 0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = wred[k] > r ? wred[k] : r;
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ int block_sum_i(int v, int* ired) {
-  v = __reduce_add_sync(0xffffffffu, v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) ired[threadIdx.x >> 5] = v;
-  __syncthreads();
-  int r = 0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += ired[k];
-  __syncthreads();
-  return r;
+  N = *bN;
+  wmax = m;
+  npos = c;
 }
 
 // Cartesian point of a measurement (offset origin of the labelled sums).
@@ -581,13 +575,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       msum += wv;
       mmax = wv > mmax ? wv : mmax;
     }
-    const double N = block_sum_r<R>(msum, wred, &bN);
-    const R wmaxr = block_max_r<R>(mmax, wred);
-    if (tid == 0) d.mass[j] = N;
-    // ---- selection (Step 3): rank of dW by integer compares of the keys
+    // mass, largest weight and the count of labels with dW > 0 in one pass
     int npos_t = 0;
     for (int p = tid; p < M; p += T) npos_t += key[p] > 0ull ? 1 : 0;
-    const int npos = block_sum_i(npos_t, ired);
+    double N;
+    R wmaxr;
+    int npos;
+    block_mass_stats<R>(msum, mmax, npos_t, wred, reinterpret_cast<int*>(smem + SL.red + 64 * sizeof(double)), &bN,
+                        N, wmaxr, npos);
+    if (tid == 0) d.mass[j] = N;
+    // resampling plan (Step 5) by the last warp's lane 0, beside the selection
+    // (the last warp ranks the fewest labels); read after pass 3's barrier
+    if (tid == T - 32) {
+      int Lp, sp_;
+      resample_plan(m.rho_pe, m.pe_cap - Jj, np, N, (double)wmaxr, Lp, sp_);
+      bL = Lp;
+      bS = sp_;
+      bW = Lp > 0 ? (R)(N / (double)Lp) : (R)0;
+    }
+    // ---- selection (Step 3): rank of dW by integer compares of the keys
     long long LTl = llround(N);
     if (LTl > npos) LTl = npos;
     if (LTl < 0) LTl = 0;
@@ -668,13 +674,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
     }
     // ---- resampling (Step 5): exact integer CDF, offspring counts, gather
-    if (tid == 0) {
-      int Lc, sc;
-      resample_plan(m.rho_pe, m.pe_cap - Jj, np, N, (double)wmaxr, Lc, sc);
-      bL = Lc;
-      bS = sc;
-      bW = Lc > 0 ? (R)(N / (double)Lc) : (R)0;
-    }
     __syncthreads();
     const int Lc = bL, sc = bS;
     {
