@@ -71,7 +71,9 @@ def workload_config(w, runs, l2_note):
             "particles_per_target": w.particles_per_target, "births_per_step": w.birth_count,
             "num_pe": w.num_pe, "exchange_frac": w.exchange_frac, "ck_mode": w.ck_mode,
             "scans_per_run": w.steps, "runs": runs, "precision": w.precision, "l2": l2_note,
-            "birth_mass": w.birth_mass, "global_batch": 1, "seq_len": w.steps, "parallelism": "replicas"}
+            "birth_mass": w.birth_mass, "global_batch": 1, "seq_len": w.steps, "parallelism": "replicas",
+            **({"gate_sigma": w.gate_sigma, "likelihood": "truncated beyond gate_sigma std (a variant)"}
+               if w.gate_sigma > 0 else {})}
 
 
 # ----------------------------------------------------------------------------
@@ -948,6 +950,9 @@ def main():
                     help="time scans from this index of every run (earlier ones replayed untimed); "
                          "default 50 for dense_rb_100t, else 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gate-sigma", type=float, default=0.0,
+                    help="likelihood truncation beyond this many standard deviations (a variant that "
+                         "changes results; 0 = the exact likelihood)")
     ap.add_argument("--tuning", type=_parse_tuning, default=None,
                     help="fixed launch shape of the pair passes instead of autotuning, "
                          "e.g. c_tile=512,c_mb=4,r_pb=1,r_g=1,grid1=1216,grid2=608,gate=1,order=1")
@@ -1011,6 +1016,8 @@ def main():
                 dist.destroy_process_group()
     w = scenario.workload({"batch256": "linear4_fp64", "rb_50t_learned": "rb_50t",
                            "dist16_compare": "dist16_10t"}.get(args.workload, args.workload))
+    if args.gate_sigma > 0:
+        w = w.with_(gate_sigma=args.gate_sigma)
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     local_rank = _env_int("LOCAL_RANK", 0)

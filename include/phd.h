@@ -93,6 +93,10 @@ typedef struct phd_config {
     int32_t reserved1;      /* must be 0 */
     double exchange_threshold; /* 0: exchange every step (the paper's); > 0: only in steps where
                                some PE has degenerated, min_j N^j < threshold * mean_j N^j */
+    double gate_sigma;      /* 0: the exact likelihood; k > 0: a variant (it changes results) that
+                               truncates g(z|x) to 0 beyond k standard deviations, i.e. where
+                               (d0/s0)^2 + (d1/s1)^2 >= k^2 (the paper's "simplify the update
+                               step"); every pass uses the truncated g */
 } phd_config;
 
 typedef struct phd_handle phd_handle;

@@ -60,6 +60,7 @@ class _Model(ctypes.Structure):
         ("birth_vel_sigma", ctypes.c_double),
         ("sigma_a_y", ctypes.c_double), ("theta_span", ctypes.c_double),
         ("birth_mean", ctypes.c_double * 4), ("birth_std", ctypes.c_double * 4),
+        ("gate_sigma", ctypes.c_double),
     ]
 
 
@@ -151,6 +152,7 @@ def model(w) -> _Model:
         m.birth_mean[k] = float(v)
     for k, v in enumerate(getattr(w, "birth_std", (0.0,) * 4)):
         m.birth_std[k] = float(v)
+    m.gate_sigma = float(getattr(w, "gate_sigma", 0.0))
     return m
 
 

@@ -28,6 +28,7 @@ typedef struct {
     double theta_span;    /* range-bearing clutter bearing extent (0: 2 pi) */
     double birth_mean[4]; /* Gaussian birth N(x_bar, Q) of Sec. 4: mean [x, vx, y, vy] */
     double birth_std[4];  /* and the square roots of Q's diagonal */
+    double gate_sigma;    /* > 0: g truncated to 0 at Mahalanobis distance >= gate_sigma */
 } orc_model;
 
 #endif /* ORC_MODEL_H */

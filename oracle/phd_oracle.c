@@ -31,7 +31,8 @@ static const double ORC_PI = 3.14159265358979323846;
 
 /* Clutter intensity kappa(z) = lambda * c(z) with c uniform over the
  * measurement space (Sec. 4, clutter model): the region's area for the linear
- * sensor; [0, r_max] x (-pi, pi] for the range-bearing sensor. */
+ * sensor; [0, r_max] x the bearing span (2 pi unless given) for the
+ * range-bearing sensor. */
 double orc_kappa(const orc_model *m)
 {
     /* kappa = lambda V_u(z) (Sec. 4): the uniform density over the
@@ -67,7 +68,9 @@ void orc_measure(const orc_model *m, const double *x, double *h)
 
 /* Single-target likelihood g(z|x): Gaussian in the sensor's coordinates with
  * its normalising constant kept, since kappa is a density over the same space
- * (Eq. 4 with psi_z = p_D g, Sec. 4 sensor model). */
+ * (Eq. 4 with psi_z = p_D g, Sec. 4 sensor model).  The truncation variant
+ * (gate_sigma = k > 0; the paper's "simplify the update step") sets g to 0
+ * at Mahalanobis distance k and beyond. */
 double orc_likelihood(const orc_model *m, const double *z, const double *x)
 {
     double h[2], d0, d1;
@@ -77,6 +80,7 @@ double orc_likelihood(const orc_model *m, const double *z, const double *x)
     if (m->meas_model == ORC_RANGE_BEARING) d1 = wrap_angle(d1);
     d0 /= m->sigma_z[0];
     d1 /= m->sigma_z[1];
+    if (m->gate_sigma > 0.0 && d0 * d0 + d1 * d1 >= m->gate_sigma * m->gate_sigma) return 0.0;
     return exp(-0.5 * (d0 * d0 + d1 * d1)) / (2.0 * ORC_PI * m->sigma_z[0] * m->sigma_z[1]);
 }
 

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
         bool keep = false;
         if (r < ns) {
           const V2<R> z = Z[d.sel[j * m.m_max + r]];
-          keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>();
+          keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_limit<R>(m);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wcnt[wid] = __popc(bal);

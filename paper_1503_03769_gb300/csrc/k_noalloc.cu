@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum_flat(Model m, const St4<R>*
   __shared__ R sh0[kTile], sh1[kTile], shl[kTile], sw[kTile];
   __shared__ double red[kThreads];
   const Lik<R> L = make_lik<R>(m);
+  const R qk = (R)m.qk;
   const int tiles = (n + kTile - 1) / kTile;
   const int mper = M < kThreads ? M : kThreads;
   const int nsplit = kThreads / mper;
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) k_colsum_flat(Model m, const St4<R>*
         R part_ = 0;
         int k = 0;
         for (int i = split; i < cnt; i += nsplit) {
-          part_ = fma(exp2_neg(qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i])), sw[i], part_);
+          const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
+          part_ = fma(exp2_neg(q < qk ? q : (R)INFINITY), sw[i], part_);   // k-sigma truncation
           if (++k == 32) { acc += part_; part_ = 0; k = 0; }
         }
         acc += part_;

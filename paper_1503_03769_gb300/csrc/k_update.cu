@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       bool keep = false;
       if ((int)threadIdx.x < Mc) {
         const V2<R> z = Z[pbeg + threadIdx.x];
-        keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_q<R>();
+        keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_limit<R>(m);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) wcnt[wid] = __popc(bal);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       int base_w = 0;
       for (int p0 = 0; p0 < M; p0 += kThreads) {
         const int p = p0 + (int)threadIdx.x;
-        const bool keep = p < M && box_qmin<R, RB>(box, LB.b0, LB.b1, zs[p].z0, zs[p].z1) < gate_q<R>();
+        const bool keep = p < M && box_qmin<R, RB>(box, LB.b0, LB.b1, zs[p].z0, zs[p].z1) < gate_limit<R>(m);
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wcnt[wid] = __popc(bal);
         __syncthreads();

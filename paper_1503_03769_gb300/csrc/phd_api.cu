@@ -160,6 +160,7 @@ const char* check_config(const phd_config& c) {
   if (c.exchange_mode != PHD_XCHG_RING && c.exchange_mode != PHD_XCHG_ALL) return "exchange_mode";
   if (c.reserved1 != 0) return "reserved1 must be 0";
   if (!(c.exchange_threshold >= 0) || !std::isfinite(c.exchange_threshold)) return "exchange_threshold";
+  if (!(c.gate_sigma >= 0) || !std::isfinite(c.gate_sigma)) return "gate_sigma";
   if (!(c.theta_span >= 0 && c.theta_span <= 2.0 * 3.14159265358979323846)) return "theta_span must be in [0, 2 pi]";
   if (!(c.dt > 0) || !std::isfinite(c.dt)) return "dt";
   if (!(c.sigma_a >= 0) || !std::isfinite(c.sigma_a)) return "sigma_a";
@@ -225,6 +226,8 @@ Model make_model(const phd_config& c) {
   m.exchange_frac = c.exchange_frac;
   m.xmode = c.exchange_mode;
   m.xthresh = c.exchange_threshold;
+  m.qk = c.gate_sigma > 0 ? 0.5 * kLog2e * c.gate_sigma * c.gate_sigma : (double)INFINITY;
+  m.f_qk = (float)m.qk;
   m.a0 = std::sqrt(0.5 * kLog2e) / c.sigma_z[0];
   m.a1 = std::sqrt(0.5 * kLog2e) / c.sigma_z[1];
   m.cnorm = 1.0 / (2.0 * kPi * c.sigma_z[0] * c.sigma_z[1]);

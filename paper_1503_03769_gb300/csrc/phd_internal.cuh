@@ -59,6 +59,8 @@ struct Model {
   double exchange_frac;
   int xmode;             // 0 ring, 1 all-to-all
   double xthresh;        // adaptive trigger (0: every step)
+  double qk;             // likelihood truncation: pairs with exponent q >= qk are 0 (inf: exact)
+  float f_qk;
   // likelihood in exp2 form: g = cnorm * 2^-(a0^2 d0^2 + a1^2 d1^2)
   double a0, a1;         // sqrt(log2(e) / 2) / sigma per measurement coordinate
   double cnorm;          // 1 / (2 pi s0 s1)
@@ -350,6 +352,7 @@ __device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R 
 struct LikP {
   unsigned long long a01;   // packed (a0, a1)
   float per_hi, per_lo;
+  float qk;                 // truncation (inf: none)
 };
 __device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
   unsigned long long r;
@@ -375,6 +378,7 @@ __device__ __forceinline__ LikP make_likp(const Model& m) {
   L.a01 = f2_pack((float)m.a0, (float)m.a1);
   L.per_hi = (float)two_pi;
   L.per_lo = (float)(two_pi - (double)L.per_hi);
+  L.qk = m.f_qk;
   return L;
 }
 template <int RB>
@@ -462,22 +466,33 @@ __device__ __forceinline__ Box<R> block_box(R lo0, R hi0, R lo1, R hi1, R* sh) {
   return B;
 }
 
-// Pair exponent in the kernels' precision: packed FP32, or plain FP64.
+// Pair exponent in the kernels' precision: packed FP32, or plain FP64.  With
+// the k-sigma truncation on, an exponent at or past qk = k^2 log2(e) / 2 is
+// returned as +inf, whose exp2 is exactly 0.
 template <class R, int RB> struct PairQ;
 template <int RB> struct PairQ<float, RB> {
   LikP L;
   __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_likp(m)) {}
   __device__ __forceinline__ float operator()(float z0, float z1, float h0, float h1, float h1lo) const {
-    return qform_p<RB>(L, f2_pack(z0, z1), f2_pack(h0, h1), h1lo);
+    const float q = qform_p<RB>(L, f2_pack(z0, z1), f2_pack(h0, h1), h1lo);
+    return q < L.qk ? q : INFINITY;
   }
 };
 template <int RB> struct PairQ<double, RB> {
   Lik<double> L;
-  __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_lik<double>(m)) {}
+  double qk;
+  __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_lik<double>(m)), qk(m.qk) {}
   __device__ __forceinline__ double operator()(double z0, double z1, double h0, double h1, double h1lo) const {
-    return qform_t<double, RB>(L, z0, z1, h0, h1, h1lo);
+    const double q = qform_t<double, RB>(L, z0, z1, h0, h1, h1lo);
+    return q < qk ? q : (double)INFINITY;
   }
 };
+
+// Exponent beyond which a measurement cannot reach a work item's particles:
+// the exp2 flush (gate_q) or the truncation, whichever is lower.
+template <class R> __device__ __forceinline__ R gate_limit(const Model& m) {
+  return fmin(gate_q<R>(), (R)m.qk);
+}
 
 // Quotient in the kernel's precision: the FP32 kernels round the operands to
 // FP32 and divide in FP32 (the FP64 divide is a long sequence on the ~2

@@ -51,7 +51,7 @@ class phd_config(ctypes.Structure):
         ("sigma_a_y", ctypes.c_double), ("theta_span", ctypes.c_double),
         ("birth_mean", ctypes.c_double * 4), ("birth_std", ctypes.c_double * 4),
         ("exchange_mode", ctypes.c_int32), ("reserved1", ctypes.c_int32),
-        ("exchange_threshold", ctypes.c_double),
+        ("exchange_threshold", ctypes.c_double), ("gate_sigma", ctypes.c_double),
     ]
 
 
@@ -183,6 +183,7 @@ def make_config(w, seed: int = 0) -> phd_config:
         c.birth_std[k] = float(v)
     c.exchange_mode = PHD_XCHG_ALL if getattr(w, "exchange_mode", "ring") == "all" else PHD_XCHG_RING
     c.exchange_threshold = float(getattr(w, "exchange_threshold", 0.0))
+    c.gate_sigma = float(getattr(w, "gate_sigma", 0.0))
     return c
 
 

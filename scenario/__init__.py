@@ -74,6 +74,7 @@ class Workload:
     birth_std: tuple = (0.0, 0.0, 0.0, 0.0)
     exchange_mode: str = "ring"             # Step 6 pattern: "ring" (the paper's) or "all" (all-to-all)
     exchange_threshold: float = 0.0         # > 0: exchange only when min_j N_j < threshold * mean_j N_j
+    gate_sigma: float = 0.0                 # > 0: likelihood truncated beyond this many std (a variant)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)

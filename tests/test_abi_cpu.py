@@ -59,7 +59,7 @@ def test_workspace_size_and_config_validation_without_gpu():
     for field, bad in [("num_pe", 0), ("num_pe", 300), ("m_max", 5000), ("pe_cap", 0),
                        ("p_d", 1.5), ("exchange_frac", 0.6), ("precision", 7), ("birth_model", 2),
                        ("sigma_a_y", -1.0), ("theta_span", 7.0), ("exchange_mode", 2), ("reserved1", 1),
-                       ("exchange_threshold", -0.5)]:
+                       ("exchange_threshold", -0.5), ("gate_sigma", -1.0)]:
         c2 = phd.make_config(w)
         setattr(c2, field, bad)
         assert L.phd_workspace_size(ctypes.byref(c2), ctypes.byref(n)) == phd.PHD_ERR_INVALID_ARG, field

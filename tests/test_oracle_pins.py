@@ -72,6 +72,30 @@ def test_range_bearing_likelihood_integrates_to_one_across_the_cut(theta0):
     assert C.sum() * (rr[1] - rr[0]) * (tt[1] - tt[0]) == pytest.approx(1.0, abs=2e-6)
 
 
+@pytest.mark.parametrize("k", [1.5, 3.0])
+def test_truncated_likelihood_mass(k):
+    """The k-sigma truncation variant: the integral of g(z|x) over z is the
+    chi-square (2 dof) CDF at k^2, 1 - exp(-k^2 / 2) (midpoint rule on a
+    fine grid around the particle, anisotropic noise); g is 0 just past the
+    radius and the full Gaussian's value just inside it."""
+    w = LIN.with_(sigma_z=(7.0, 13.0), gate_sigma=k)
+    m = oracle.model(w)
+    x = np.array([30.0, 0.0, -20.0, 0.0])
+    h = 0.05
+    gx = np.arange(-7.0 * k, 7.0 * k, h) + h / 2
+    gy = np.arange(-13.0 * k, 13.0 * k, h * 13 / 7) + h * 13 / 14
+    tot = 0.0
+    for dy in gy[::1]:
+        row = [oracle.likelihood(m, np.array([30.0 + dx, -20.0 + dy]), x) for dx in gx[::4]]
+        tot += sum(row) * (4 * h) * (h * 13 / 7)
+    assert tot == pytest.approx(1.0 - math.exp(-0.5 * k * k), rel=2e-3)
+    full = oracle.model(LIN.with_(sigma_z=(7.0, 13.0)))
+    inside = np.array([30.0 + 7.0 * k * 0.999, -20.0])
+    outside = np.array([30.0 + 7.0 * k * 1.001, -20.0])
+    assert oracle.likelihood(m, outside, x) == 0.0
+    assert oracle.likelihood(m, inside, x) == oracle.likelihood(full, inside, x) > 0.0
+
+
 def test_kappa_units():
     assert oracle.kappa(_m(LIN, clutter_rate=10.0)) == pytest.approx(10.0 / 4e6, rel=1e-15)
     assert oracle.kappa(_m(RB, clutter_rate=500.0, r_max=1000.0)) == pytest.approx(
