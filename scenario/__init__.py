@@ -116,11 +116,13 @@ def workload(name: str, **overrides) -> Workload:
             name="dense_rb_100t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=500.0, n_targets=100, particles_per_target=2000,
             birth_count=20000, steps=100, precision="fp32"),
-        # The dense workload's distributed form: 64 PEs.
+        # The dense workload's distributed form: 64 PEs.  A PE keeps rho/64 =
+        # 31 particles per target it holds plus 312 births: 4096 slots cover
+        # ~120 targets per PE, and a slice fits one SM's shared memory.
         "dense_rb_100t_pe64": Workload(
             name="dense_rb_100t_pe64", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=500.0, n_targets=100, particles_per_target=2000,
-            birth_count=20000, steps=100, num_pe=64, exchange_frac=0.1, precision="fp32"),
+            birth_count=20000, steps=100, num_pe=64, exchange_frac=0.1, precision="fp32", pe_cap=4096),
         # Learned-birth evaluation scenario (range-bearing, 50 targets).
         "rb_50t": Workload(
             name="rb_50t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
