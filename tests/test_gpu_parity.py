@@ -286,30 +286,37 @@ def test_dense_workload_sampled():
     f.close()
 
 
-def test_dense_workload_64_pes_sampled():
-    """The dense workload's 64-PE distributed form (config 3) at full size on
-    the staged path, autotuned: after 20 free-running scans, one step with
-    injected noise is checked per PE on samples (C of 12 measurements and
-    the updated weights of 400 particles on 6 PEs), the Eq. 8 mass closed
-    form on every PE, and the CU fusion of the GPU's own local estimates."""
-    w = scenario.workload("dense_rb_100t", num_pe=64)
+@pytest.mark.parametrize("path", ["staged", "fused"])
+def test_dense_workload_64_pes_sampled(path):
+    """The dense workload's 64-PE distributed form (config 3) at full size
+    (staged path autotuned; fused path: one CTA per PE, as the benchmark runs
+    it): after 20 free-running scans, one step with injected noise is checked
+    per PE on samples (C of 12 measurements and the updated weights of 400
+    particles on 6 PEs), the Eq. 8 mass closed form on every PE, and the CU
+    fusion of the GPU's own local estimates."""
+    w = scenario.workload("dense_rb_100t_pe64")
     sc = scenario.simulate(w, 6, steps=21)
-    f = _filter(w, 6)
+    f = _filter(w, 6, path)
     m = oracle.model(w)
     kap = oracle.kappa(m)
     for k in range(20):
         f.step(sc.meas[k])
-    f.autotune(2)
     noise = scenario.step_noise(6, 20, w.num_pe, w.pe_cap, np.float32)
-    f.predict(torch.as_tensor(noise).cuda())
-    xp, wp = f.get_state()
     Z = sc.meas[20]
     M = len(Z)
+    if path == "staged":
+        f.autotune(2)
+        f.predict(torch.as_tensor(noise).cuda())
+        xp, wp = f.get_state()
+        f.update(torch.as_tensor(Z).cuda())
+        _, wu = f.get_state()
+    else:
+        states, labels = f.step_inject(np.asarray(Z, np.float32), noise, scenario.resample_u32(6, 20, 64),
+                                       scenario.exchange_u32(6, 20, 64, w.pe_cap))
+        xp, wp, wu = f.get_predicted()
+    C, mass = f.get_update()
     # each PE keeps rho / 64 ~ 31 particles per target it believes in: ~2.8e4 here
     assert M > 450 and sum(len(a) for a in xp) > 20_000
-    f.update(torch.as_tensor(Z).cuda())
-    C, mass = f.get_update()
-    _, wu = f.get_state()
     rng = np.random.default_rng(6)
     for j in rng.choice(64, 6, replace=False):
         sel_p = rng.choice(M, 12, replace=False)
@@ -321,7 +328,8 @@ def test_dense_workload_64_pes_sampled():
     for j in range(64):
         ref = (1 - w.p_d) * wp[j].astype(np.float64).sum() + np.sum(C[j, :M] / (kap + C[j, :M]))
         assert abs(mass[j] - ref) <= 1e-5 * max(ref, 1e-12), j
-    states, labels = f.extract()
+    if path == "staged":
+        states, labels = f.extract()
     loc_s, loc_l = f.get_local_estimates()
     per_pe = [oracle.Extraction(np.asarray(loc_l[j], np.int32), np.asarray(loc_s[j], np.float64), np.zeros(M), 0.0,
                                 len(loc_l[j])) for j in range(64)]
