@@ -11,12 +11,14 @@
 //   selection (Step 3)      LT_j = round(N^j), rank counting over dW^{j,p}
 //   pass 3 (Eq. 18)         labelled sums for the selected labels -> zeta
 //   resampling (Step 5)     exact integer CDF scan, offspring counts, gather
-//   grid barrier            all L_j, local estimates visible
-//   exchange plan (Step 6)  L_x = floor(frac min L_j), Fisher-Yates slots,
-//                           outgoing couples to the outbox; CTA 0 fuses the
-//                           local estimates (Step 4) into the step's output
+//   grid barrier            all L_j, masses and local estimates visible
+//   exchange plan (Step 6)  L_x (or 0 when the adaptive trigger holds off),
+//                           Fisher-Yates slots by one lane while the other
+//                           warps fuse their share of the labels (Step 4),
+//                           outgoing couples to the outbox
 //   grid barrier
-//   exchange in             PE j's slots take PE j-1's outbox
+//   exchange in             PE j's slots take their sources' outboxes (ring:
+//                           PE j-1; all-to-all: a rotation per slot)
 // The only cross-PE waits are the two (three) grid barriers the scheme needs:
 // the exchange count and the CU fusion depend on every PE.  Barriers spin
 // with an iteration limit; on expiry the kernel records kErrTimeout and every
@@ -27,7 +29,6 @@
 namespace phd {
 
 constexpr int kFusedThreads = 1024;
-constexpr long kSpinLimit = 20000000;   // ~2 s with 100 ns sleeps
 
 struct FusedArgs {
   const void* Z;            // packed measurements of S steps
@@ -43,10 +44,10 @@ struct FusedArgs {
   int S;
 };
 
-// Grid-wide barrier over gridDim.x CTAs with a bounded wait.  Returns false
-// (in every thread of the CTA) when the wait gave up or another CTA recorded
-// an error; the caller then returns from the kernel.
-__device__ __forceinline__ bool grid_sync(const Dev& d) {
+// Grid-wide barrier over gridDim.x CTAs with a bounded wait (`limit`
+// polls).  Returns false (in every thread of the CTA) when the wait gave up
+// or another CTA recorded an error; the caller then returns from the kernel.
+__device__ __forceinline__ bool grid_sync(const Dev& d, long long limit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -61,10 +62,10 @@ __device__ __forceinline__ bool grid_sync(const Dev& d) {
       __threadfence();
       atomicAdd(d.bar + 1, 1u);
     } else {
-      long it = 0;
+      long long it = 0;
       while (*gen == g) {
         if (*err != 0) { ok = 0; break; }
-        if (++it > kSpinLimit) {
+        if (++it > limit) {
           atomicOr(d.err, kErrTimeout);
           ok = 0;
           break;
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
     }
     if (m.ck_global && m.K > 1) {
-      if (!grid_sync(d)) return;
+      if (!grid_sync(d, m.spin_limit)) return;
       for (int p = tid; p < M; p += T) {
         double mean = 0.0;
         for (int k = 0; k < m.K; ++k) mean += d.C[k * m.m_max + p];
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     St4<R>* out_s = static_cast<St4<R>*>(a.out_states) + (long)s * a.cap;
     int* out_l = a.out_labels + (long)s * a.cap;
     if (m.K > 1) {
-      if (!grid_sync(d)) return;
+      if (!grid_sync(d, m.spin_limit)) return;
       int lx = 0;
       if (xchg) {
         // exchange count from all PEs' counts (and masses), by warp 0
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           wo[base + t] = gw[base + slot];
         }
       }
-      if (!grid_sync(d)) return;
+      if (!grid_sync(d, m.spin_limit)) return;
       if (xchg && lx > 0) {
         const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
         const R* wo = static_cast<const R*>(d.w_out);

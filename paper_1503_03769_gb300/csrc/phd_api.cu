@@ -228,6 +228,7 @@ Model make_model(const phd_config& c) {
   m.xthresh = c.exchange_threshold;
   m.qk = c.gate_sigma > 0 ? 0.5 * kLog2e * c.gate_sigma * c.gate_sigma : (double)INFINITY;
   m.f_qk = (float)m.qk;
+  m.spin_limit = phd::kDefaultSpinLimit;
   m.a0 = std::sqrt(0.5 * kLog2e) / c.sigma_z[0];
   m.a1 = std::sqrt(0.5 * kLog2e) / c.sigma_z[1];
   m.cnorm = 1.0 / (2.0 * kPi * c.sigma_z[0] * c.sigma_z[1]);
@@ -1060,6 +1061,23 @@ phd_status phd_set_step(phd_handle* h, uint64_t step) {
 phd_status phd_set_stage_timer(phd_handle* h, int32_t on) {
   if (!h) return PHD_ERR_INVALID_ARG;
   h->timer = on != 0;
+  return PHD_OK;
+}
+
+phd_status phd_set_wait_limit(phd_handle* h, int64_t iterations) {
+  if (!h || iterations < 1 || iterations > 1000000000LL) return PHD_ERR_INVALID_ARG;
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->m.spin_limit = iterations;
+  destroy_graphs(h);
+  return PHD_OK;
+}
+
+phd_status phd_inject_barrier_fault(phd_handle* h) {
+  if (!h) return PHD_ERR_INVALID_ARG;
+  // an arrival count far past any grid: the last arrival is never seen
+  const unsigned int poison[2] = {0x40000000u, 0u};
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.bar, poison, sizeof(poison), cudaMemcpyHostToDevice, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   return PHD_OK;
 }
 

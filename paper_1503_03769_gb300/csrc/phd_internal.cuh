@@ -61,6 +61,7 @@ struct Model {
   double xthresh;        // adaptive trigger (0: every step)
   double qk;             // likelihood truncation: pairs with exponent q >= qk are 0 (inf: exact)
   float f_qk;
+  long long spin_limit;  // polls of a bounded wait on other CTAs before it gives up
   // likelihood in exp2 form: g = cnorm * 2^-(a0^2 d0^2 + a1^2 d1^2)
   double a0, a1;         // sqrt(log2(e) / 2) / sigma per measurement coordinate
   double cnorm;          // 1 / (2 pi s0 s1)
@@ -176,6 +177,7 @@ struct Dev {
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
+constexpr long long kDefaultSpinLimit = 20000000;   // a few seconds of 100 ns polls
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based RNG.

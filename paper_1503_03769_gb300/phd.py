@@ -97,6 +97,8 @@ ABI = {
     "phd_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(phd_stats)]),
     "phd_reset_stats": (ctypes.c_int, [_H]),
     "phd_set_stage_timer": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "phd_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "phd_inject_barrier_fault": (ctypes.c_int, [_H]),
     "phd_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(phd_tuning)]),
     "phd_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(phd_tuning)]),
     "phd_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(phd_tuning)]),
@@ -542,6 +544,15 @@ class ParticlePHD:
 
     def set_stage_timer(self, on: bool):
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
+
+    def set_wait_limit(self, iterations: int):
+        """Polls of a bounded wait on other CTAs before it reports a timeout."""
+        self._check(self.L.phd_set_wait_limit(self.h, int(iterations)), "phd_set_wait_limit")
+
+    def inject_barrier_fault(self):
+        """Failure injection for tests: the next fused step's grid barrier
+        cannot complete and its bounded wait reports PHD_ERR_TIMEOUT."""
+        self._check(self.L.phd_inject_barrier_fault(self.h), "phd_inject_barrier_fault")
 
     def get_tuning(self) -> dict:
         t = phd_tuning()

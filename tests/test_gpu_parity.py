@@ -339,6 +339,41 @@ def test_dense_workload_64_pes_sampled(path):
     f.close()
 
 
+def test_barrier_timeout_is_reported_and_recoverable():
+    """Failure detection without a GPU fault: the host sets the fused step's
+    grid-barrier counter where it cannot complete, the bounded wait (limit
+    lowered to 2e4 polls) gives up, the step reports PHD_ERR_TIMEOUT, and the
+    same handle then steps normally again (barrier and error word reset)."""
+    from paper_1503_03769_gb300 import PhdError, phd
+    w = scenario.workload("dist16_10t", num_pe=4, n_targets=3, clutter_rate=10.0, particles_per_target=200,
+                          birth_count=200)
+    sc = scenario.simulate(w, 2, steps=6)
+    f = _filter(w, 2, "fused")
+    ref = _filter(w, 2, "fused")
+    for k in range(2):
+        f.step(sc.meas[k])
+        ref.step(sc.meas[k])
+    xs, ws = f.get_state()
+    step = f.get_step()
+    f.set_wait_limit(20_000)
+    f.inject_barrier_fault()
+    with pytest.raises(PhdError) as ei:
+        f.step(sc.meas[2])
+    assert ei.value.status == phd.PHD_ERR_TIMEOUT
+    # the context is usable: restore the checkpoint (state and step counter)
+    # and the default limit; the next steps equal an uninterrupted filter's
+    f.set_wait_limit(20_000_000)
+    f.set_state(xs, ws)
+    f.set_step(step)
+    for k in range(2, 6):
+        s_f, l_f = f.step(sc.meas[k])
+        s_r, l_r = ref.step(sc.meas[k])
+        np.testing.assert_array_equal(l_f.cpu().numpy(), l_r.cpu().numpy())
+        np.testing.assert_array_equal(s_f.cpu().numpy(), s_r.cpu().numpy())
+    f.close()
+    ref.close()
+
+
 def test_edge_cases_and_errors():
     from paper_1503_03769_gb300 import PhdError
     from paper_1503_03769_gb300 import phd as P
