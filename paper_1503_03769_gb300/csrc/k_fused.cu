@@ -620,21 +620,43 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     }
     if (tid == 0) d.nsel[j] = LT;
     __syncthreads();
-    // ---- pass 3: labelled sums for the selected labels (Eq. 18); groups of
-    // nsplit lanes per label, FP32 sums of offsets from the label's point,
-    // shuffle-reduced in FP32, zeta formed in FP64 by the group's lane 0
+    // ---- pass 3: labelled sums for the selected labels (Eq. 18), FP32 sums
+    // of offsets from the label's point, zeta formed by one thread per label.
+    // Up to one label per warp: wpl = (warps / LT) warps per label split the
+    // particles, warp totals by shuffles, the wpl totals summed in warp order
+    // through shared memory; more labels: groups of nsplit lanes per label.
     if (LT > 0) {
-      const int nsplit = pow2_floor(min(32, max(1, T / LT)));
-      const int mper = T / nsplit;
-      const int rl = tid / nsplit, split = tid % nsplit;
-      for (int r0 = 0; r0 < LT; r0 += mper) {
-        const int r = r0 + rl;
+      const int nw = T >> 5, wid = tid >> 5;
+      auto zeta_out = [&](int r, R s0, R s1, R s2, R s3, R s4, R px, R py) {
+        St4<R> o;
+        if (s0 > (R)0) {
+          if constexpr (sizeof(R) == 4) {
+            const R inv = (R)1 / s0;
+            o.x = px + s1 * inv;
+            o.vx = s2 * inv;
+            o.y = py + s3 * inv;
+            o.vy = s4 * inv;
+          } else {
+            o.x = px + s1 / s0;
+            o.vx = s2 / s0;
+            o.y = py + s3 / s0;
+            o.vy = s4 / s0;
+          }
+        } else {
+          o = St4<R>{px, (R)0, py, (R)0};
+        }
+        gest[j * m.m_max + r] = o;
+      };
+      if (LT <= nw) {
+        const int wpl = nw / LT;
+        const int r = wid / wpl, part = wid - r * wpl;
+        R* pbuf = reinterpret_cast<R*>(smem + SL.red);   // [LT][wpl][5]
         R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-        R px = 0, py = 0;
         if (r < LT) {
           const V2<R> z = zs[sel[r]];
+          R px, py;
           meas_point_f<R>(cc, m.meas_model, z, px, py);
-          for (int i = split; i < np; i += nsplit) {
+          for (int i = part * 32 + lane; i < np; i += wpl * 32) {
             const P4<R> q = sp[i];
             const R ew = exp2_neg(PQ(z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
             const St4<R> st = sx[i];
@@ -644,33 +666,62 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
             s3 = fma(ew, st.y - py, s3);
             s4 = fma(ew, st.vy, s4);
           }
-        }
-        for (int o = nsplit >> 1; o > 0; o >>= 1) {
-          s0 += __shfl_down_sync(0xffffffffu, s0, o, nsplit);
-          s1 += __shfl_down_sync(0xffffffffu, s1, o, nsplit);
-          s2 += __shfl_down_sync(0xffffffffu, s2, o, nsplit);
-          s3 += __shfl_down_sync(0xffffffffu, s3, o, nsplit);
-          s4 += __shfl_down_sync(0xffffffffu, s4, o, nsplit);
-        }
-        if (split == 0 && r < LT) {
-          St4<R> o;
-          if (s0 > (R)0) {
-            if constexpr (sizeof(R) == 4) {
-              const R inv = (R)1 / s0;
-              o.x = px + s1 * inv;
-              o.vx = s2 * inv;
-              o.y = py + s3 * inv;
-              o.vy = s4 * inv;
-            } else {
-              o.x = px + s1 / s0;
-              o.vx = s2 / s0;
-              o.y = py + s3 / s0;
-              o.vy = s4 / s0;
-            }
-          } else {
-            o = St4<R>{px, (R)0, py, (R)0};
+          for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            s2 += __shfl_down_sync(0xffffffffu, s2, o);
+            s3 += __shfl_down_sync(0xffffffffu, s3, o);
+            s4 += __shfl_down_sync(0xffffffffu, s4, o);
           }
-          gest[j * m.m_max + r] = o;
+          if (lane == 0) {
+            R* b = pbuf + (r * wpl + part) * 5;
+            b[0] = s0;
+            b[1] = s1;
+            b[2] = s2;
+            b[3] = s3;
+            b[4] = s4;
+          }
+        }
+        __syncthreads();
+        if (tid < LT) {
+          const V2<R> z = zs[sel[tid]];
+          R px, py;
+          meas_point_f<R>(cc, m.meas_model, z, px, py);
+          R t[5] = {0, 0, 0, 0, 0};
+          for (int k = 0; k < wpl; ++k)
+            for (int c = 0; c < 5; ++c) t[c] += pbuf[(tid * wpl + k) * 5 + c];
+          zeta_out(tid, t[0], t[1], t[2], t[3], t[4], px, py);
+        }
+      } else {
+        const int nsplit = pow2_floor(min(32, max(1, T / LT)));
+        const int mper = T / nsplit;
+        const int rl = tid / nsplit, split = tid % nsplit;
+        for (int r0 = 0; r0 < LT; r0 += mper) {
+          const int r = r0 + rl;
+          R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+          R px = 0, py = 0;
+          if (r < LT) {
+            const V2<R> z = zs[sel[r]];
+            meas_point_f<R>(cc, m.meas_model, z, px, py);
+            for (int i = split; i < np; i += nsplit) {
+              const P4<R> q = sp[i];
+              const R ew = exp2_neg(PQ(z.a, z.b, q.h0, q.h1, q.h1lo)) * q.w;
+              const St4<R> st = sx[i];
+              s0 += ew;
+              s1 = fma(ew, st.x - px, s1);
+              s2 = fma(ew, st.vx, s2);
+              s3 = fma(ew, st.y - py, s3);
+              s4 = fma(ew, st.vy, s4);
+            }
+          }
+          for (int o = nsplit >> 1; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o, nsplit);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o, nsplit);
+            s2 += __shfl_down_sync(0xffffffffu, s2, o, nsplit);
+            s3 += __shfl_down_sync(0xffffffffu, s3, o, nsplit);
+            s4 += __shfl_down_sync(0xffffffffu, s4, o, nsplit);
+          }
+          if (split == 0 && r < LT) zeta_out(r, s0, s1, s2, s3, s4, px, py);
         }
       }
     }
