@@ -541,7 +541,7 @@ def run_gpu_batch(args, rank, world, local_rank):
         b.set_tuning(**args.tuning)
         tuning = b.get_tuning()
     else:
-        tuning = b.autotune(3) if not args.no_autotune else b.get_tuning()
+        tuning = b.autotune(5) if not args.no_autotune else b.get_tuning()
     t_tune = time.perf_counter() - t_tune
     b.set_state(empty_x, empty_w)
     b.set_stage_timer(True)

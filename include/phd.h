@@ -481,7 +481,8 @@ phd_status phd_set_tuning(phd_handle *h, const phd_tuning *t);
 /* Autotuner: times every supported shape of pass 1 (c_tile x c_mb x grid1 in
  * {608, 1216, 2432}) and then of pass 2 ((r_pb, r_g) x grid2), each as the
  * mean of `reps` launches (1 .. 1000) after one untimed launch, then the whole
- * update with the spatial order on and off (the gate setting is kept), on the
+ * update and the extraction with the spatial order on and off (the gate
+ * setting is kept), on the
  * handle's current predicted set and measurements, i.e. the input of the last
  * update (call it after a representative step: the best shape depends on the
  * slices' particle and measurement counts).  Keeps the fastest shape of each

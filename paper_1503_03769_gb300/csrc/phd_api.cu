@@ -1198,19 +1198,25 @@ phd_status phd_autotune(phd_handle* h, int32_t reps, phd_tuning* out) {
         best.grid2 = m.tune.grid2;
       }
     }
-  // spatial order on or off: the whole update timed both ways
+  // spatial order on or off: the whole update and the extraction (whose label
+  // sums walk the same order) timed both ways
   if (e == cudaSuccess) {
     float t_on = 0.0f, t_off = 0.0f;
     m.tune = best;
+    auto upd_ext = [&] {
+      cudaError_t r = fp64 ? phd::launch_update<double>(h->d, m, h->stream)
+                           : phd::launch_update<float>(h->d, m, h->stream);
+      if (r == cudaSuccess)
+        r = fp64 ? phd::launch_extract<double>(h->d, m, static_cast<double*>(h->out_states), h->out_labels,
+                                               h->cfg.m_max, nullptr, h->stream)
+                 : phd::launch_extract<float>(h->d, m, static_cast<float*>(h->out_states), h->out_labels,
+                                              h->cfg.m_max, nullptr, h->stream);
+      return r;
+    };
     m.tune.order = 1;
-    e = time_pass(h, reps, [&] {
-      return fp64 ? phd::launch_update<double>(h->d, m, h->stream) : phd::launch_update<float>(h->d, m, h->stream);
-    }, &t_on);
+    e = time_pass(h, reps, upd_ext, &t_on);
     m.tune.order = 0;
-    if (e == cudaSuccess)
-      e = time_pass(h, reps, [&] {
-        return fp64 ? phd::launch_update<double>(h->d, m, h->stream) : phd::launch_update<float>(h->d, m, h->stream);
-      }, &t_off);
+    if (e == cudaSuccess) e = time_pass(h, reps, upd_ext, &t_off);
     if (e == cudaSuccess) best.order = t_on < t_off ? 1 : 0;
   }
   // leave the update's outputs as the chosen shapes compute them, and the
