@@ -98,3 +98,13 @@ def test_bench_ospa_metric_matches_permutation_brute_force():
                        for perm in itertools.permutations(range(b), a))
             want = ((best + c ** p * (b - a)) / b) ** (1 / p)
         assert math.isclose(bench.ospa_metric(X, Y, c, p), want, rel_tol=1e-12, abs_tol=1e-12)
+
+
+def test_c_program_builds_against_the_header(tmp_path):
+    """tests/c_abi_track.c (the C-ABI example the GPU tests run) compiles as
+    C99 with -Wall -Werror and links against libphd.so here, without a GPU."""
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import test_gpu_c_abi
+    test_gpu_c_abi.build_c_program(str(tmp_path / "track"))
+    assert os.path.exists(tmp_path / "track")
