@@ -236,9 +236,9 @@ def run_reference(args, w, rank, world):
 _TRAFFIC_PROFILES = {
     ("fused", "dist16_10t"): ("k_step_fused_dist16_ncu.md", ("k_fused.cu", "phd_internal.cuh")),
     ("staged", "dense_rb_100t"): ("update_dense_rb_100t_ncu.md",
-                                  ("k_update.cu", "k_order.cu", "phd_internal.cuh")),
+                                  ("k_update.cu", "k_order.cu", "k_extract.cu", "phd_internal.cuh")),
 }
-UPDATE_KERNELS = "update stage (k_cell_hist, k_cell_scan, k_cell_scatter, k_colsum, k_finalize, k_rowsum, k_mass)"
+UPDATE_KERNELS = "update stage (k_cell_hist, k_cell_scatter, k_colsum, k_finalize, k_rowsum, k_select)"
 
 
 def kernel_sources_sha256(files):

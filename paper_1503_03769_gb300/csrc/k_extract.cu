@@ -1,7 +1,9 @@
 // Measurement-labelled state extraction (Eq. 10-18, Step 3) and CU fusion
 // (Step 4).
 //
-// k_select (one CTA per PE): LT_j = round(N^j) with the updated mass N^j,
+// k_select (one CTA per PE and chunk of measurements; the last kernel of the
+//   update stage): N^j from the pass-2 tile sums (and, in the first CTA of
+//   the slice, the resampling plan), LT_j = round(N^j),
 //   dW^{j,p} = C^j_p / (kappa + C_p) (Eq. 16 in closed
 //   form), and the LT_j largest dW by rank counting: rank_p = #{q : dW_q > dW_p
 //   or (dW_q = dW_p and q < p)}; label p is taken when dW_p > 0 and
@@ -31,8 +33,12 @@ __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   __shared__ int npos_s;
+  __shared__ int pref[kMaxPE + 1];
+  __shared__ double red[8], redm[8], mass_s;
   const int j = blockIdx.x;
   const int M = slice_M(d, j);
+  item_prefix(d.n_pred, m.K, pref, row_tile(m.tune));
+  const double N = slice_mass(d, m, j, pref, blockIdx.y == 0, red, redm, &mass_s);
   if (threadIdx.x == 0) npos_s = 0;
   for (int p = threadIdx.x; p < M; p += blockDim.x) key[p] = d.dwkey[j * m.m_max + p];
   __syncthreads();
@@ -41,7 +47,7 @@ __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
   npos_t = __reduce_add_sync(0xffffffffu, npos_t);
   if ((threadIdx.x & 31) == 0) atomicAdd(&npos_s, npos_t);
   __syncthreads();
-  long long LT = llround(d.mass[j]);
+  long long LT = llround(N);
   if (LT > npos_s) LT = npos_s;
   if (LT < 0) LT = 0;
   // one warp per measurement, lanes split the comparisons
@@ -420,7 +426,6 @@ cudaError_t launch_batch_out(const Dev& d, const Model& m, R* out_states, int* o
 template <class R>
 cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap,
                            int* d_count, cudaStream_t s) {
-  launch_k(k_select<R>, dim3(dim3(m.K, (m.m_max + 63) / 64)), dim3(256), sizeof(unsigned long long) * (size_t)m.m_max, s, d, m);
   {
     const long items = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
     const int g = (int)(items < 152L * 8 ? (items > 0 ? items : 1) : 152L * 8);
@@ -438,6 +443,15 @@ cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out
 
 template cudaError_t launch_batch_out<float>(const Dev&, const Model&, float*, int*, int*, int, cudaStream_t);
 template cudaError_t launch_batch_out<double>(const Dev&, const Model&, double*, int*, int*, int, cudaStream_t);
+template <class R>
+cudaError_t launch_select(const Dev& d, const Model& m, cudaStream_t s) {
+  launch_k(k_select<R>, dim3(m.K, (m.m_max + 63) / 64), dim3(256), sizeof(unsigned long long) * (size_t)m.m_max, s,
+           d, m);
+  return cudaGetLastError();
+}
+template cudaError_t launch_select<float>(const Dev&, const Model&, cudaStream_t);
+template cudaError_t launch_select<double>(const Dev&, const Model&, cudaStream_t);
+
 template cudaError_t launch_extract<float>(const Dev&, const Model&, float*, int*, int, int*, cudaStream_t);
 template cudaError_t launch_extract<double>(const Dev&, const Model&, double*, int*, int, int*, cudaStream_t);
 

@@ -2,7 +2,7 @@
 // exchange (Step 6).
 //
 // Systematic resampling on an exact integer-valued CDF, per PE j:
-//   plan (k_mass, after the update): N^j = sum_i w_i (FP64, fixed order),
+//   plan (k_select, the update's last kernel): N^j = sum_i w_i (FP64, fixed order),
 //               e with max w < 2^e, c = ceil(log2 n), s = 52 - c - e,
 //               L_j = min(pe_cap - J_j, round((rho / K) max(1, N^j))).
 //   k_rs_q / k_rs_off: q_i = floor(w_i 2^s) (exact, from the float's bits),

@@ -21,8 +21,9 @@
 //   holds r_pb particles in registers and r_g lanes share them, splitting the
 //   measurements (combined by shuffles); Z_k and ginv are staged in shared
 //   memory.  Per-tile FP64 sums and maxima of the updated weights feed N^j and
-//   the resampling plan (k_mass).  The updated weights go to their own
-//   buffer: the extraction (Eq. 13, 18) still needs the predicted ones.
+//   the resampling plan, formed by k_select (slice_mass), the update stage's
+//   last kernel.  The updated weights go to their own buffer: the extraction
+//   (Eq. 13, 18) still needs the predicted ones.
 //
 // Algorithmic work per pair and pass: one ex2 and 7 FP32 operations (linear
 // sensor; 10 with the bearing wrap); bytes per particle and pass: 16 B state
@@ -424,44 +425,6 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   }
 }
 
-// Per slice: N^j = sum of the pass-2 tile sums (fixed order), the largest
-// updated weight, and the resampling plan (L_j and the CDF scale).
-__global__ void __launch_bounds__(256) k_mass(Dev d, Model m) {
-  pdl_enter();
-  __shared__ int pref[kMaxPE + 1];
-  __shared__ double red[8], redm[8];
-  const int j = blockIdx.x;
-  item_prefix(d.n_pred, m.K, pref, row_tile(m.tune));
-  double s = 0.0, mx = 0.0;
-  for (int it = pref[j] + threadIdx.x; it < pref[j + 1]; it += blockDim.x) {
-    s += d.rowpart[it];
-    mx = fmax(mx, d.rowmax[it]);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_down_sync(0xffffffffu, s, o);
-    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = s;
-    redm[threadIdx.x >> 5] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0, tm = 0.0;
-    for (int k = 0; k < 8; ++k) {
-      t += red[k];
-      tm = fmax(tm, redm[k]);
-    }
-    d.mass[j] = t;
-    int L, sc;
-    resample_plan(d.rho[j], d.lmax[j], d.n_pred[j], t, tm, L, sc);
-    d.rs_mass[j] = t;
-    d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
-    d.rs_s[j] = sc;
-    d.rs_L[j] = L;
-  }
-}
-
 int grid_items(const Model& m) {
   long items = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
   long g = 152L * 4;
@@ -583,11 +546,6 @@ cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s) {
   return m.meas_model ? rowsum_model<R, 1>(d, m, s) : rowsum_model<R, 0>(d, m, s);
 }
 
-cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s) {
-  launch_k(k_mass, dim3(m.K), dim3(256), 0, s, d, m);
-  return cudaGetLastError();
-}
-
 int n_update_launches(const Model& m) { return (m.tune.order ? n_order_launches() : 0) + 4; }
 
 template <class R>
@@ -596,7 +554,7 @@ cudaError_t launch_update(const Dev& d, const Model& m, cudaStream_t s) {
   if (e == cudaSuccess) e = launch_colsum<R>(d, m, s);
   if (e == cudaSuccess) e = launch_finalize<R>(d, m, s);
   if (e == cudaSuccess) e = launch_rowsum<R>(d, m, s);
-  if (e == cudaSuccess) e = launch_mass(d, m, s);
+  if (e == cudaSuccess) e = launch_select<R>(d, m, s);   // N^j, the resampling plan, the LT_j labels
   return e;
 }
 

@@ -333,7 +333,7 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
 }
 
 // kernels each stage launches (for the launch counter)
-constexpr int kNPredict = 1, kNStageZ = 1, kNExtract = 4, kNAdvance = 1, kNBirth = 2;
+constexpr int kNPredict = 1, kNStageZ = 1, kNExtract = 3, kNAdvance = 1, kNBirth = 2;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
 
 phd_status read_device_error(phd_handle* h) {

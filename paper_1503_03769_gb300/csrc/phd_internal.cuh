@@ -810,6 +810,48 @@ __device__ __forceinline__ void resample_plan(double rho, int lmax, int n, doubl
   }
 }
 
+// N^j = sum of slice j's pass-2 tile sums (the row-tile prefix `pref`) and its
+// largest updated weight, by one CTA of exactly 256 threads in a fixed order
+// (each thread a stride of 256 tiles, shuffles within the warps, the 8 warp
+// totals in warp order); with `plan` the CTA also writes N^j and the
+// resampling plan (L_j and the CDF scale).  Every thread gets N^j.
+__device__ __forceinline__ double slice_mass(const Dev& d, const Model& m, int j, const int* pref, bool plan,
+                                             double* red, double* redm, double* sh) {
+  double s = 0.0, mx = 0.0;
+  for (int it = pref[j] + threadIdx.x; it < pref[j + 1]; it += 256) {
+    s += d.rowpart[it];
+    mx = fmax(mx, d.rowmax[it]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = s;
+    redm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, tm = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      t += red[k];
+      tm = fmax(tm, redm[k]);
+    }
+    *sh = t;
+    if (plan) {
+      d.mass[j] = t;
+      int L, sc;
+      resample_plan(d.rho[j], d.lmax[j], d.n_pred[j], t, tm, L, sc);
+      d.rs_mass[j] = t;
+      d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
+      d.rs_s[j] = sc;
+      d.rs_L[j] = L;
+    }
+  }
+  __syncthreads();
+  return *sh;
+}
+
 // Measurements of slice j.
 __device__ __forceinline__ int slice_M(const Dev& d, int j) { return d.zshared ? *d.M : d.Mj[j]; }
 template <class R> __device__ __forceinline__ const V2<R>* slice_Z(const Dev& d, int j) {
@@ -839,7 +881,7 @@ int n_order_launches();                  // kernels one launch_order enqueues
 template <class R> cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s);
 template <class R> cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s);
-cudaError_t launch_mass(const Dev& d, const Model& m, cudaStream_t s);
+template <class R> cudaError_t launch_select(const Dev& d, const Model& m, cudaStream_t s);
 Tune default_tune(bool fp64);
 // measurement-driven birth (FP32): network head per measurement (unless the
 // head was supplied), mixture table, births drawn over the plain ones
