@@ -430,8 +430,12 @@ cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out
     const long items = (long)m.K * ((m.pe_cap + m.tune.c_tile - 1) / m.tune.c_tile);
     const int g = (int)(items < 152L * 8 ? (items > 0 ? items : 1) : 152L * 8);
     const size_t smem = (sizeof(P4<R>) + sizeof(St4<R>)) * (size_t)m.tune.c_tile + sizeof(int) * (size_t)m.m_max;
-    if (m.meas_model) launch_k(k_selsum<R, 1>, dim3(g), dim3(kThreads), smem, s, d, m);
-    else launch_k(k_selsum<R, 0>, dim3(g), dim3(kThreads), smem, s, d, m);
+    switch (model_flag(m)) {
+      case 1: launch_k(k_selsum<R, 1>, dim3(g), dim3(kThreads), smem, s, d, m); break;
+      case 2: launch_k(k_selsum<R, 2>, dim3(g), dim3(kThreads), smem, s, d, m); break;
+      case 3: launch_k(k_selsum<R, 3>, dim3(g), dim3(kThreads), smem, s, d, m); break;
+      default: launch_k(k_selsum<R, 0>, dim3(g), dim3(kThreads), smem, s, d, m); break;
+    }
   }
   long warps = (long)m.K * m.m_max;
   int b = (int)((warps + 7) / 8);
@@ -463,6 +467,8 @@ cudaError_t prepare_extract() {
   const int sm = (int)((sizeof(P4<R>) + sizeof(St4<R>)) * 1024 + sizeof(int) * kMaxM);
   cudaError_t e = cudaFuncSetAttribute(k_selsum<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selsum<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selsum<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selsum<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 template cudaError_t prepare_extract<float>();

@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   const int Jj = births_of(m.J, m.K, j);
   const unsigned long long step0 = *d.step;
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const PairQ<R, RB> PQ(m);   // pair exponent, sensor model fixed at compile time
+  const PairQ<R, RB> PQ(m);   // pair exponent, sensor model and truncation fixed at compile time
   const Cst<R> cc = consts<R>(m);
   const R bw = birth_weight<R>(cc, m, j);
   const double cs = m.p_d * m.cnorm;
@@ -871,7 +871,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
 
 template <class R>
 static const void* fused_fn(const Model& m) {
-  return m.meas_model ? (const void*)k_step_fused<R, 1> : (const void*)k_step_fused<R, 0>;
+  switch (model_flag(m)) {
+    case 1: return (const void*)k_step_fused<R, 1>;
+    case 2: return (const void*)k_step_fused<R, 2>;
+    case 3: return (const void*)k_step_fused<R, 3>;
+    default: return (const void*)k_step_fused<R, 0>;
+  }
 }
 
 template <class R>

@@ -494,6 +494,8 @@ cudaError_t prepare_kernels(const Model& m) {
   const size_t sm = (sizeof(Z4<R>) + sizeof(int)) * (size_t)m.m_max;
   cudaError_t e = prepare_rowsum<R, 0>(sm);
   if (e == cudaSuccess) e = prepare_rowsum<R, 1>(sm);
+  if (e == cudaSuccess) e = prepare_rowsum<R, 2>(sm);
+  if (e == cudaSuccess) e = prepare_rowsum<R, 3>(sm);
   if (e == cudaSuccess) e = prepare_extract<R>();
   return e;
 }
@@ -532,7 +534,12 @@ static cudaError_t rowsum_model(const Dev& d, const Model& m, cudaStream_t s) {
 
 template <class R>
 cudaError_t launch_colsum(const Dev& d, const Model& m, cudaStream_t s) {
-  return m.meas_model ? colsum_model<R, 1>(d, m, s) : colsum_model<R, 0>(d, m, s);
+  switch (model_flag(m)) {
+    case 1: return colsum_model<R, 1>(d, m, s);
+    case 2: return colsum_model<R, 2>(d, m, s);
+    case 3: return colsum_model<R, 3>(d, m, s);
+    default: return colsum_model<R, 0>(d, m, s);
+  }
 }
 
 template <class R>
@@ -543,7 +550,12 @@ cudaError_t launch_finalize(const Dev& d, const Model& m, cudaStream_t s) {
 
 template <class R>
 cudaError_t launch_rowsum(const Dev& d, const Model& m, cudaStream_t s) {
-  return m.meas_model ? rowsum_model<R, 1>(d, m, s) : rowsum_model<R, 0>(d, m, s);
+  switch (model_flag(m)) {
+    case 1: return rowsum_model<R, 1>(d, m, s);
+    case 2: return rowsum_model<R, 2>(d, m, s);
+    case 3: return rowsum_model<R, 3>(d, m, s);
+    default: return rowsum_model<R, 0>(d, m, s);
+  }
 }
 
 int n_update_launches(const Model& m) { return (m.tune.order ? n_order_launches() : 0) + 4; }

@@ -339,7 +339,7 @@ template <class R, int RB>
 __device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
   const R d0 = z0 - h0;
   R d1 = z1 - h1;
-  if (RB) {
+  if (RB & 1) {
     d1 = d1 - h1lo;
     const R a = fabs(d1);
     d1 = fmin(a, (L.per_hi - a) + L.per_lo);
@@ -387,7 +387,7 @@ template <int RB>
 __device__ __forceinline__ float qform_p(const LikP& L, unsigned long long z, unsigned long long h, float h1lo) {
   float d0, d1;
   f2_unpack(f2_sub(z, h), d0, d1);
-  if (RB) {
+  if (RB & 1) {
     d1 = d1 - h1lo;
     const float a = fabsf(d1);
     d1 = fminf(a, (L.per_hi - a) + L.per_lo);
@@ -422,7 +422,7 @@ template <class R, int RB>
 __device__ __forceinline__ R box_qmin(const Box<R>& B, R b0, R b1, R z0, R z1) {
   const R d0 = fmax(fmax(B.lo0 - z0, z0 - B.hi0), (R)0);
   R d1;
-  if (RB) {
+  if (RB & 1) {
     const R c = (R)0.5 * (B.lo1 + B.hi1), hw = (R)0.5 * (B.hi1 - B.lo1);
     if (hw > (R)1.5707963267948966) {
       d1 = 0;
@@ -468,16 +468,19 @@ __device__ __forceinline__ Box<R> block_box(R lo0, R hi0, R lo1, R hi1, R* sh) {
   return B;
 }
 
-// Pair exponent in the kernels' precision: packed FP32, or plain FP64.  With
-// the k-sigma truncation on, an exponent at or past qk = k^2 log2(e) / 2 is
-// returned as +inf, whose exp2 is exactly 0.
+// Pair exponent in the kernels' precision: packed FP32, or plain FP64.  The
+// kernels' compile-time model flag RB carries the sensor (bit 0: range-
+// bearing) and the k-sigma truncation (bit 1): with it, an exponent at or
+// past qk = k^2 log2(e) / 2 is returned as +inf, whose exp2 is exactly 0;
+// without it no per-pair test is compiled in.
 template <class R, int RB> struct PairQ;
 template <int RB> struct PairQ<float, RB> {
   LikP L;
   __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_likp(m)) {}
   __device__ __forceinline__ float operator()(float z0, float z1, float h0, float h1, float h1lo) const {
     const float q = qform_p<RB>(L, f2_pack(z0, z1), f2_pack(h0, h1), h1lo);
-    return q < L.qk ? q : INFINITY;
+    if constexpr ((RB & 2) != 0) return q < L.qk ? q : INFINITY;
+    return q;
   }
 };
 template <int RB> struct PairQ<double, RB> {
@@ -486,9 +489,15 @@ template <int RB> struct PairQ<double, RB> {
   __device__ __forceinline__ explicit PairQ(const Model& m) : L(make_lik<double>(m)), qk(m.qk) {}
   __device__ __forceinline__ double operator()(double z0, double z1, double h0, double h1, double h1lo) const {
     const double q = qform_t<double, RB>(L, z0, z1, h0, h1, h1lo);
-    return q < qk ? q : (double)INFINITY;
+    if constexpr ((RB & 2) != 0) return q < qk ? q : (double)INFINITY;
+    return q;
   }
 };
+
+// The compile-time model flag of a handle: sensor bit | truncation bit.
+__host__ __device__ __forceinline__ int model_flag(const Model& m) {
+  return (m.meas_model ? 1 : 0) | (m.qk < (double)INFINITY ? 2 : 0);
+}
 
 // Exponent beyond which a measurement cannot reach a work item's particles:
 // the exp2 flush (gate_q) or the truncation, whichever is lower.
