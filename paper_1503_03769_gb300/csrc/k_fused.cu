@@ -799,43 +799,38 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     int* out_l = a.out_labels + (long)s * a.cap;
     if (m.K > 1) {
       if (!grid_sync(d, m.spin_limit)) return;
-      int lx = 0;
-      if (xchg) {
-        // exchange count from all PEs' counts (and masses), by warp 0
-        __shared__ int lx_s;
-        if (tid < 32) {
-          const int c = exchange_count_warp(d, m, reinterpret_cast<double*>(smem + SL.red));
-          if (tid == 0) lx_s = c;
-        }
-        __syncthreads();
-        lx = lx_s;
-        if (j == 0 && tid == 0) *d.lx = lx;
-      }
-      // the exchange draws are independent: made in parallel; the swaps are
-      // serial (lane 0 of warp 0) while the other warps do this CTA's share
-      // of the CU fusion
+      // warp 0: the exchange count, its draws (independent) and the serial
+      // Fisher-Yates swaps; the other warps, at the same time: this CTA's
+      // share of the CU fusion (the predicted states' block, free after the
+      // gather, is its scratch)
+      __shared__ int lx_s;
       unsigned int* ud = reinterpret_cast<unsigned int*>(cend);
-      if (lx > 0) {
-        for (int i = tid; i < Lc; i += T) perm[i] = i;
-        for (int t = tid; t < lx; t += T)
-          ud[t] = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
-      }
-      __syncthreads();
-      // (the predicted states' block, free after the gather, is the scratch)
       const int fchunk = share_chunk<R>(m.K, sizeof(St4<R>) * (size_t)m.pe_cap, T - 32);
       if (tid < 32) {
-        if (tid == 0) {
-          for (int t = 0; t < lx; ++t) {
-            const int r = t + (int)(((unsigned long long)ud[t] * (unsigned long long)(Lc - t)) >> 32);
-            const int tmp = perm[t];
-            perm[t] = perm[r];
-            perm[r] = tmp;
+        const int c = xchg ? exchange_count_warp(d, m, reinterpret_cast<double*>(smem + SL.red + 1024)) : 0;
+        if (c > 0) {
+          for (int i = lane; i < Lc; i += 32) perm[i] = i;
+          for (int t = lane; t < c; t += 32)
+            ud[t] = a.xu ? a.xu[base + t] : philox_u32(m, (uint32_t)(base + t), step, kTagExchange);
+          __syncwarp();
+          if (lane == 0) {
+            for (int t = 0; t < c; ++t) {
+              const int r = t + (int)(((unsigned long long)ud[t] * (unsigned long long)(Lc - t)) >> 32);
+              const int tmp = perm[t];
+              perm[t] = perm[r];
+              perm[r] = tmp;
+            }
           }
+        }
+        if (lane == 0) {
+          lx_s = c;
+          if (j == 0) *d.lx = c;
         }
       } else if (fchunk > 0) {
         cu_fuse_share<R>(d, m, j, M, out_s, out_l, a.cap, a.out_count + s, ired, smem + SL.sx, fchunk, zs, cc, 32);
       }
       __syncthreads();
+      const int lx = lx_s;
       // scratch too small for a share (many PEs, tiny slices): CTA 0 fuses alone
       if (fchunk <= 0 && j == 0) cu_fuse<R>(d, m, M, out_s, out_l, a.cap, a.out_count + s, ired, srank, srank_cap, zs, cc);
       if (lx > 0) {
