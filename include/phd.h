@@ -422,17 +422,18 @@ phd_status phd_set_stage_timer(phd_handle *h, int32_t on);
 /* ---- failure detection ------------------------------------------------------ */
 
 /* Every wait of a CTA on other CTAs (the fused step's grid barriers) polls at
- * most `iterations` times (each poll a ~100 ns sleep and an L2 load; the
- * default 2e7 is a few seconds), then records a timeout in the device error
+ * most `iterations` times (each poll a ~32 ns sleep and an L2 load; the
+ * default 2e7 is several seconds), then records a timeout in the device error
  * word and every CTA of the launch returns: the GPU context stays usable and
  * the next synchronising call returns PHD_ERR_TIMEOUT (and resets the barrier
  * and the error word).  iterations in 1 .. 1e9.  Synchronises. */
 phd_status phd_set_wait_limit(phd_handle *h, int64_t iterations);
 
-/* Failure injection for tests (host side; nothing on the GPU faults): sets
- * the fused step's grid-barrier arrival counter where it can never complete,
- * so the next fused step of a K > 1 filter waits out its limit at the first
- * grid barrier and reports PHD_ERR_TIMEOUT.  Synchronises. */
+/* Failure injection for tests (host side; nothing on the GPU faults): sets a
+ * flag that makes PE 0 leave the next fused step of a K > 1 filter at its
+ * first grid barrier without arriving, as a PE that died would; the other PEs
+ * wait out their limit there and the step reports PHD_ERR_TIMEOUT (which
+ * clears the flag).  Synchronises. */
 phd_status phd_inject_barrier_fault(phd_handle *h);
 
 /* ---- launch shapes of the update's pair passes, and their autotuner -------- */

@@ -20,7 +20,7 @@
 //   exchange in             PE j's slots take their sources' outboxes (ring:
 //                           PE j-1; all-to-all: a rotation per slot)
 // The only cross-PE waits are the two (three) grid barriers the scheme needs:
-// the exchange count and the CU fusion depend on every PE.  Barriers spin
+// the exchange count and the CU fusion depend on every PE.  Barriers poll
 // with an iteration limit; on expiry the kernel records kErrTimeout and every
 // CTA returns.  All arithmetic matches the staged kernels (same helpers), but
 // reductions run in a different fixed order.
@@ -45,36 +45,44 @@ struct FusedArgs {
 };
 
 // Grid-wide barrier over gridDim.x CTAs with a bounded wait (`limit`
-// polls).  Returns false (in every thread of the CTA) when the wait gave up
-// or another CTA recorded an error; the caller then returns from the kernel.
-__device__ __forceinline__ bool grid_sync(const Dev& d, long long limit) {
+// polls).  Every CTA adds one to a 64-bit arrival count that only grows, so
+// barrier b of a launch completes when the count reaches b * gridDim.x: one
+// release atomic and the acquire polls are the whole cost (no reset, no
+// generation word).  The count is a multiple of gridDim.x between launches; a
+// launch that gave up leaves an error word behind and the host clears both
+// before the next.  Returns false (in every thread of the CTA) when the wait
+// gave up or an error was recorded; the caller then returns from the kernel.
+// `lost` (read by thread 0) makes the CTA leave without arriving, as a PE that
+// died would: the host's failure injection.
+__device__ __forceinline__ bool grid_sync(const Dev& d, long long limit, bool lost) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = d.bar + 1;
-    volatile int* err = d.err;
-    const unsigned int g = *gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(d.bar, 1u);
-    int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(d.bar, 0u);
-      __threadfence();
-      atomicAdd(d.bar + 1, 1u);
-    } else {
+    int ok = 0;
+    if (!lost) {
+      unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.bar);
+      const unsigned long long G = gridDim.x;
+      unsigned long long old;
+      asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(cnt) : "memory");
+      const unsigned long long target = (old / G + 1ull) * G;
       long long it = 0;
-      while (*gen == g) {
-        if (*err != 0) { ok = 0; break; }
-        if (++it > limit) {
-          atomicOr(d.err, kErrTimeout);
-          ok = 0;
+      for (;;) {
+        unsigned long long c;
+        int e;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
+        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(d.err) : "memory");
+        if (e != 0) break;
+        if (c >= target) {
+          ok = 1;
           break;
         }
-        __nanosleep(100);
+        if (++it > limit) {
+          atomicOr(d.err, kErrTimeout);
+          break;
+        }
+        __nanosleep(32);
       }
     }
-    __threadfence();
-    if (*err != 0) ok = 0;
     ok_s = ok;
   }
   __syncthreads();
@@ -439,6 +447,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
   St4<R>* gest = static_cast<St4<R>*>(d.est_local);
   const bool xchg = m.K > 1 && m.exchange_frac > 0.0;
   int n = d.n_cur[j];
+  // host-injected failure: PE 0 leaves at its first grid barrier
+  const bool lost = j == 0 && tid == 0 && reinterpret_cast<volatile unsigned int*>(d.bar)[2] != 0u;
 
   for (int s = 0; s < a.S; ++s) {
     const unsigned long long step = step0 + (unsigned long long)s;
@@ -527,7 +537,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
       }
     }
     if (m.ck_global && m.K > 1) {
-      if (!grid_sync(d, m.spin_limit)) return;
+      if (!grid_sync(d, m.spin_limit, lost)) return;
       for (int p = tid; p < M; p += T) {
         double mean = 0.0;
         for (int k = 0; k < m.K; ++k) mean += d.C[k * m.m_max + p];
@@ -798,7 +808,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     St4<R>* out_s = static_cast<St4<R>*>(a.out_states) + (long)s * a.cap;
     int* out_l = a.out_labels + (long)s * a.cap;
     if (m.K > 1) {
-      if (!grid_sync(d, m.spin_limit)) return;
+      if (!grid_sync(d, m.spin_limit, lost)) return;
       // warp 0: the exchange count, its draws (independent) and the serial
       // Fisher-Yates swaps; the other warps, at the same time: this CTA's
       // share of the CU fusion (the predicted states' block, free after the
@@ -843,7 +853,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
           wo[base + t] = gw[base + slot];
         }
       }
-      if (!grid_sync(d, m.spin_limit)) return;
+      if (!grid_sync(d, m.spin_limit, lost)) return;
       if (xchg && lx > 0) {
         const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
         const R* wo = static_cast<const R*>(d.w_out);

@@ -121,7 +121,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.parent = cv.take<int>(K * P);
   t.xslots = cv.take<int>(K * P);
   t.lx = cv.take<int>(1);
-  t.bar = cv.take<unsigned int>(2);
+  t.bar = cv.take<unsigned int>(4);
   t.step = cv.take<unsigned long long>(1);
   t.stats = cv.take<unsigned long long>(5);
   t.err = cv.take<int>(1);
@@ -342,8 +342,9 @@ phd_status read_device_error(phd_handle* h) {
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err == 0) return PHD_OK;
   PHD_CUDA(h, cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
-  // a wait that gave up may have left the grid barrier mid-count
-  PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 2 * sizeof(unsigned int), h->stream));
+  // a wait that gave up may have left the grid barrier mid-count (and an
+  // injected fault its flag)
+  PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 4 * sizeof(unsigned int), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (err & phd::kErrNonFinite) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
@@ -1074,9 +1075,10 @@ phd_status phd_set_wait_limit(phd_handle* h, int64_t iterations) {
 
 phd_status phd_inject_barrier_fault(phd_handle* h) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  // an arrival count far past any grid: the last arrival is never seen
-  const unsigned int poison[2] = {0x40000000u, 0u};
-  PHD_CUDA(h, cudaMemcpyAsync(h->d.bar, poison, sizeof(poison), cudaMemcpyHostToDevice, h->stream));
+  // the lost-PE flag: PE 0 leaves the next fused step at its first grid
+  // barrier without arriving
+  const unsigned int flag = 1u;
+  PHD_CUDA(h, cudaMemcpyAsync(h->d.bar + 2, &flag, sizeof(flag), cudaMemcpyHostToDevice, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   return PHD_OK;
 }

@@ -146,7 +146,7 @@ struct Dev {
   int* parent;           // [K*pe_cap]
   int* xslots;           // [K][pe_cap] exchange slots
   int* lx;               // [1] particles moved per PE
-  unsigned int* bar;     // [2] grid barrier: arrival count, generation
+  unsigned int* bar;     // [4] grid barrier: [0..1] 64-bit arrival count, [2] injected lost-PE flag
   // per-slice descriptors (a slice is a PE of one filter, or one run of a
   // batch of independent filters); slot j*pe_cap .. of every [K][pe_cap] array
   int zshared;           // 1: every slice uses Z rows 0 .. *M-1 (one filter)
@@ -177,7 +177,7 @@ struct Dev {
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
-constexpr long long kDefaultSpinLimit = 20000000;   // a few seconds of 100 ns polls
+constexpr long long kDefaultSpinLimit = 20000000;   // several seconds of polls (32 ns sleep + an L2 read)
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based RNG.

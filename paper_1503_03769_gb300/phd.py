@@ -550,8 +550,9 @@ class ParticlePHD:
         self._check(self.L.phd_set_wait_limit(self.h, int(iterations)), "phd_set_wait_limit")
 
     def inject_barrier_fault(self):
-        """Failure injection for tests: the next fused step's grid barrier
-        cannot complete and its bounded wait reports PHD_ERR_TIMEOUT."""
+        """Failure injection for tests: PE 0 leaves the next fused step at its
+        first grid barrier without arriving; the other PEs' bounded waits
+        report PHD_ERR_TIMEOUT."""
         self._check(self.L.phd_inject_barrier_fault(self.h), "phd_inject_barrier_fault")
 
     def get_tuning(self) -> dict:

@@ -340,10 +340,11 @@ def test_dense_workload_64_pes_sampled(path):
 
 
 def test_barrier_timeout_is_reported_and_recoverable():
-    """Failure detection without a GPU fault: the host sets the fused step's
-    grid-barrier counter where it cannot complete, the bounded wait (limit
-    lowered to 2e4 polls) gives up, the step reports PHD_ERR_TIMEOUT, and the
-    same handle then steps normally again (barrier and error word reset)."""
+    """Failure detection without a GPU fault: the host flags PE 0 as lost, so
+    it leaves the fused step at the first grid barrier without arriving; the
+    other PEs' bounded waits (limit lowered to 2e4 polls) give up, the step
+    reports PHD_ERR_TIMEOUT, and the same handle then steps normally again
+    (barrier words, flag and error word reset)."""
     from paper_1503_03769_gb300 import PhdError, phd
     w = scenario.workload("dist16_10t", num_pe=4, n_targets=3, clutter_rate=10.0, particles_per_target=200,
                           birth_count=200)
