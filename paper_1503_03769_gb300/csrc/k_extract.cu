@@ -16,8 +16,9 @@
 //   Cartesian point; the offsets keep the FP32 sums small.  Eq. 18's
 //   zeta_p = sum_i dw^{i,p} x_i / dW^p does not depend on the per-label
 //   factor p_D cnorm / (kappa + C_p), which cancels.
-// k_est_local: per (PE, rank) FP64 reduction of the pass-3 partials to zeta.
-// k_fuse (one CTA): for every label the PEs that took it vote; a label is
+// k_est_local: per (PE, rank) FP64 reduction of the pass-3 partials to zeta
+//   (one filter on one PE: also the output, in ascending label order).
+// k_fuse (one CTA, K > 1): for every label the PEs that took it vote; a label is
 //   valid with more than K/2 votes, and its state is the mean of the voters'
 //   local states in PE order (FP32 kernels: positions as offsets from the
 //   label's measurement point, summed and scaled in FP32; FP64 kernels: FP64
@@ -223,9 +224,13 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
 
 // One warp per (PE, rank): lanes take the PE's pass-3 tile partials in a
 // strided order, an FP64 shuffle tree combines them (fixed order), then
-// zeta = r + S / C (Eq. 18).
+// zeta = r + S / C (Eq. 18).  With one filter on one PE (`direct`) the fusion
+// rule has a single voter, so the output is the local estimates themselves in
+// ascending label order: each warp places its label after the selected labels
+// below it, and the count is the selection's size.
 template <class R>
-__global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_est_local(Dev d, Model m, bool direct, R* out_states, int* out_labels,
+                                                   int cap, int* d_count) {
   pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
@@ -237,9 +242,19 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
   for (long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < total; gw += nwarps) {
     const int j = (int)(gw / m.m_max);
     const int r = (int)(gw - (long)j * m.m_max);
-    if (r >= d.nsel[j]) continue;   // uniform over the warp
+    const int nsel = d.nsel[j];
+    if (direct && r == 0 && lane == 0) {
+      *d.out_count = nsel;
+      if (d_count) *d_count = nsel;
+    }
+    if (r >= nsel) continue;   // uniform over the warp
     // the label's measurement, fetched ahead of the partials
     const int p = d.sel[j * m.m_max + r];
+    int below = 0;
+    if (direct) {
+      for (int t = lane; t < nsel; t += 32) below += d.sel[j * m.m_max + t] < p ? 1 : 0;
+      below = __reduce_add_sync(0xffffffffu, below);
+    }
     const V2<R> z = slice_Z<R>(d, j)[p];
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
 #pragma unroll 4
@@ -280,6 +295,10 @@ __global__ void __launch_bounds__(256) k_est_local(Dev d, Model m) {
         o = St4<R>{px, (R)0, py, (R)0};
       }
       est[gw] = o;
+      if (direct && below < cap) {
+        reinterpret_cast<St4<R>*>(out_states)[below] = o;
+        out_labels[below] = p;
+      }
     }
   }
 }
@@ -440,8 +459,10 @@ cudaError_t launch_extract(const Dev& d, const Model& m, R* out_states, int* out
   long warps = (long)m.K * m.m_max;
   int b = (int)((warps + 7) / 8);
   if (b > 152 * 8) b = 152 * 8;
-  launch_k(k_est_local<R>, dim3(b), dim3(256), 0, s, d, m);
-  if (d.zshared) launch_k(k_fuse<R>, dim3(1), dim3(1024), 0, s, d, m, out_states, out_labels, cap, d_count);
+  const bool direct = d.zshared && m.K == 1;
+  launch_k(k_est_local<R>, dim3(b), dim3(256), 0, s, d, m, direct, out_states, out_labels, cap, d_count);
+  if (d.zshared && !direct)
+    launch_k(k_fuse<R>, dim3(1), dim3(1024), 0, s, d, m, out_states, out_labels, cap, d_count);
   return cudaGetLastError();
 }
 

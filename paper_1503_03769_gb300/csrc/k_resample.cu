@@ -129,13 +129,16 @@ __global__ void __launch_bounds__(kChunk) k_rs_count(Dev d, Model m, const uint3
 // parent's lane) and the weight N^j / L_j.  Work items: 256-particle tiles
 // of each slice.
 template <class R>
-__global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m) {
+__global__ void __launch_bounds__(256) k_rs_gather(Dev d, Model m, bool last) {
   pdl_enter();
   __shared__ int pref[kMaxPE + 1];
   const int K = m.K;
   item_prefix(d.n_pred, K, pref);
   if (blockIdx.x == 0)
     for (int j = threadIdx.x; j < K; j += blockDim.x) d.n_cur[j] = d.rs_L[j];
+  // the step's last kernel advances the step counter (every reader of this
+  // step's counter has completed: each kernel waits for its predecessor)
+  if (last && blockIdx.x == 0 && threadIdx.x == 0) *d.step += 1ull;
   const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
   St4<R>* x = static_cast<St4<R>*>(d.x);
   R* w = static_cast<R*>(d.w);
@@ -234,6 +237,7 @@ __global__ void k_xout(Dev d, Model m) {
 template <class R>
 __global__ void k_xin(Dev d, Model m) {
   pdl_enter();
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d.step += 1ull;   // the step's last kernel
   St4<R>* x = static_cast<St4<R>*>(d.x);
   R* w = static_cast<R*>(d.w);
   const St4<R>* xo = static_cast<const St4<R>*>(d.x_out);
@@ -250,9 +254,6 @@ __global__ void k_xin(Dev d, Model m) {
   }
 }
 
-__global__ void k_advance(Dev d) {
-  pdl_enter(); *d.step += 1ull; }
-
 template <class R>
 cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, const uint32_t* xu,
                             cudaStream_t s) {
@@ -265,8 +266,10 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   launch_k(k_rs_off, dim3(m.K), dim3(1024), 0, s, d, m);
   launch_k(k_rs_count<R>, dim3(gc), dim3(kChunk), 0, s, d, m, u);
   const long gitems = (long)m.K * ((m.pe_cap + kTile - 1) / kTile);
-  launch_k(k_rs_gather<R>, dim3((int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16)), dim3(256), 0, s, d, m);
-  if (m.K > 1 && m.exchange_frac > 0.0) {
+  const bool xchg = m.K > 1 && m.exchange_frac > 0.0;
+  launch_k(k_rs_gather<R>, dim3((int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16)), dim3(256), 0, s, d, m,
+           !xchg);
+  if (xchg) {
     int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
     if (bx < 1) bx = 1;
     if (bx > 152 * 8) bx = 152 * 8;
@@ -274,11 +277,6 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
     launch_k(k_xout<R>, dim3(bx), dim3(256), 0, s, d, m);
     launch_k(k_xin<R>, dim3(bx), dim3(256), 0, s, d, m);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_advance_step(const Dev& d, cudaStream_t s) {
-  launch_k(k_advance, dim3(1), dim3(1), 0, s, d);
   return cudaGetLastError();
 }
 

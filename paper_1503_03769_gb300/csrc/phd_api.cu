@@ -333,8 +333,10 @@ cudaError_t upload_slices(phd_handle* h, const std::vector<phd_config>& cf) {
 }
 
 // kernels each stage launches (for the launch counter)
-constexpr int kNPredict = 1, kNStageZ = 1, kNExtract = 3, kNAdvance = 1, kNBirth = 2;
+constexpr int kNPredict = 1, kNStageZ = 1, kNBirth = 2;
 int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 : 4; }
+// label sums and local estimates; the fusion kernel only for K > 1 PEs of one filter
+int n_extract(const phd_handle* h) { return (h->batch_runs == 0 && h->m.K > 1) ? 3 : 2; }
 
 phd_status read_device_error(phd_handle* h) {
   int err = 0;
@@ -405,7 +407,7 @@ phd_status do_extract(phd_handle* h, void* states, int* labels, int cap, int* d_
       ? phd::launch_extract<double>(h->d, h->m, static_cast<double*>(states), labels, cap, d_count, h->stream)
       : phd::launch_extract<float>(h->d, h->m, static_cast<float*>(states), labels, cap, d_count, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "extract");
-  h->launches += kNExtract;
+  h->launches += n_extract(h);
   if (h_count) {
     phd_status st = read_device_error(h);
     if (st != PHD_OK) return st;
@@ -421,9 +423,7 @@ phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
   cudaError_t e = is_fp64(h) ? phd::launch_resample<double>(h->d, h->m, u, xu, h->stream)
                              : phd::launch_resample<float>(h->d, h->m, u, xu, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "resample");
-  e = phd::launch_advance_step(h->d, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "advance_step");
-  h->launches += n_resample(h->m) + kNAdvance;
+  h->launches += n_resample(h->m);
   h->stage = kReady;
   return PHD_OK;
 }
@@ -460,7 +460,6 @@ cudaError_t enq_post(phd_handle* h, cudaStream_t s) {
   if (e == cudaSuccess)
     e = is_fp64(h) ? phd::launch_resample<double>(h->d, h->m, nullptr, nullptr, s)
                    : phd::launch_resample<float>(h->d, h->m, nullptr, nullptr, s);
-  if (e == cudaSuccess) e = phd::launch_advance_step(h->d, s);
   return e;
 }
 cudaError_t enq_all(phd_handle* h, cudaStream_t s) {
@@ -556,8 +555,8 @@ phd_status run_step_body(phd_handle* h) {
     if (e == cudaSuccess) e = cudaGraphLaunch(h->g_post, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
-  h->launches += kNPredict + phd::n_update_launches(h->m) + kNExtract - (h->batch_runs ? 1 : 0) + n_resample(h->m) +
-                 kNAdvance + (h->m.learned ? kNBirth : 0);
+  h->launches += kNPredict + phd::n_update_launches(h->m) + n_extract(h) + n_resample(h->m) +
+                 (h->m.learned ? kNBirth : 0);
   return PHD_OK;
 }
 
@@ -1356,7 +1355,7 @@ phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* 
       e = is_fp64(h) ? phd::launch_extract<double>(h->d, h->m, nullptr, nullptr, 0, nullptr, h->stream)
                      : phd::launch_extract<float>(h->d, h->m, nullptr, nullptr, 0, nullptr, h->stream);
       if (e != cudaSuccess) st = cuda_fail(h, e, "extract");
-      h->launches += kNExtract - 1;
+      h->launches += n_extract(h);
     }
     if (st == PHD_OK) st = do_resample(h, d_u, nullptr);
     if (st != PHD_OK) {

@@ -904,7 +904,6 @@ template <class R> cudaError_t launch_extract(const Dev& d, const Model& m, R* o
                                               int cap, int* d_count, cudaStream_t s);
 template <class R> cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u,
                                                const uint32_t* xu, cudaStream_t s);
-cudaError_t launch_advance_step(const Dev& d, cudaStream_t s);
 template <class R> cudaError_t prepare_kernels(const Model& m);
 template <class R> cudaError_t prepare_extract();
 cudaError_t prepare_exchange(const Model& m);
