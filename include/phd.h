@@ -23,6 +23,14 @@
  *    Z_k is its label p (Sec. 3, Step 3).
  *  - Particle slices are laid out [K][pe_cap]: PE j owns slots
  *    j*pe_cap .. j*pe_cap + n_j - 1.
+ *  - Alignment: the kernels access caller buffers as vectors, so a
+ *    measurement array (Z) must be aligned to one row of 2 reals (8 bytes
+ *    FP32, 16 FP64); an estimate, state-row or injected-draw array to one row
+ *    of 4 reals (16 bytes FP32, 32 FP64); int32 / uint32 arrays to 4 bytes.
+ *    Allocations from cudaMalloc, cudaHostAlloc or PyTorch qualify; a view at
+ *    an odd element offset may not.  A misaligned buffer is refused with
+ *    PHD_ERR_INVALID_ARG before anything is launched (phd_step_host instead
+ *    copies through the workspace).
  *  - Calls are asynchronous on the stream given to phd_init unless marked
  *    "synchronises"; those wait for the stream before returning.
  *  - A handle is not thread-safe; use one handle per host thread.

@@ -27,6 +27,7 @@
 // Random numbers: the plain rows (n1, n2, u1, u2) of k_predict's slot, and
 // (u_c, nz1, nz2) from the caller's extra rows [K][jmax] after the K x pe_cap
 // plain rows, or from Philox-4x32-10 with the birth tag.
+#include <cstdint>
 #include <cuda_bf16.h>
 
 #include "mlp_device.cuh"
@@ -329,6 +330,7 @@ cudaError_t launch_params_bf16(void* dst, const float* src, cudaStream_t s) {
 extern "C" phd_status phd_birth_features(const phd_config* cfg, const float* d_Z, int32_t M, float* d_X,
                                          void* stream) {
   if (!cfg || M < 0 || (M > 0 && (!d_Z || !d_X))) return PHD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_Z) % 8 != 0) return PHD_ERR_INVALID_ARG;   // rows read as float pairs
   if (phd::config_problem(*cfg)) return PHD_ERR_INVALID_ARG;
   if (M == 0) return PHD_OK;
   const phd::Model m = phd::model_from_config(*cfg);

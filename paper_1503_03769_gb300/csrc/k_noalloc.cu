@@ -11,6 +11,7 @@
 // symbol's host-side name is not a device pointer); on the first call made
 // with a device current, the addresses are looked up and the anchor table is
 // copied in (a synchronous copy), and both are cached for that device.
+#include <cstdint>
 #include <mutex>
 
 #include "phd.h"
@@ -143,6 +144,13 @@ extern "C" phd_status phd_colsum_static(const phd_config* cfg, const void* d_x, 
   if (!cfg || n < 0 || M < 0) return PHD_ERR_INVALID_ARG;
   if (phd::config_problem(*cfg)) return PHD_ERR_INVALID_ARG;
   if ((n > 0 && (!d_x || !d_w)) || (M > 0 && (!d_Z || !d_C))) return PHD_ERR_INVALID_ARG;
+  {
+    // state rows and Z rows are read as vectors (four and two reals)
+    const uintptr_t rs = cfg->precision == PHD_FP64 ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(d_x) % (4 * rs) != 0 || reinterpret_cast<uintptr_t>(d_w) % rs != 0 ||
+        reinterpret_cast<uintptr_t>(d_Z) % (2 * rs) != 0 || reinterpret_cast<uintptr_t>(d_C) % 8 != 0)
+      return PHD_ERR_INVALID_ARG;
+  }
   const size_t tiles = ((size_t)n + phd::kTile - 1) / phd::kTile;
   if (tiles * (size_t)M > phd::kStaticScratchDoubles) return PHD_ERR_CAPACITY;
   void* scratch = nullptr;

@@ -1,8 +1,10 @@
 // Host side of the C ABI declared in include/phd.h: configuration checks,
 // workspace carve, stage ordering, and stream-ordered launches.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -52,6 +54,13 @@ struct phd_handle {
 namespace {
 
 size_t real_size(const phd_config& c) { return c.precision == PHD_FP64 ? 8 : 4; }
+
+// The kernels access caller buffers as vectors: measurement rows (two reals),
+// state and estimate rows and injected predict draws (four reals), and 32-bit
+// words.  Arrays from cudaMalloc, cudaHostAlloc or PyTorch meet these
+// alignments; a view at an odd element offset may not, and is refused before
+// any launch instead of faulting.
+bool misaligned(const void* p, size_t a) { return p && reinterpret_cast<uintptr_t>(p) % a != 0; }
 
 struct Carver {
   char* base;
@@ -338,6 +347,17 @@ int n_resample(const Model& m) { return (m.K > 1 && m.exchange_frac > 0.0) ? 7 :
 // label sums and local estimates; the fusion kernel only for K > 1 PEs of one filter
 int n_extract(const phd_handle* h) { return (h->batch_runs == 0 && h->m.K > 1) ? 3 : 2; }
 
+phd_status check_align(phd_handle* h, const void* Z, const void* rows4a, const void* rows4b,
+                       std::initializer_list<const void*> words) {
+  const size_t rs = real_size(h->cfg);
+  if (misaligned(Z, 2 * rs)) return fail(h, PHD_ERR_INVALID_ARG, "Z is not aligned to a row of two reals");
+  if (misaligned(rows4a, 4 * rs) || misaligned(rows4b, 4 * rs))
+    return fail(h, PHD_ERR_INVALID_ARG, "a state, estimate or draw buffer is not aligned to a row of four reals");
+  for (const void* p : words)
+    if (misaligned(p, 4)) return fail(h, PHD_ERR_INVALID_ARG, "a 32-bit buffer is not 4-byte aligned");
+  return PHD_OK;
+}
+
 phd_status read_device_error(phd_handle* h) {
   int err = 0;
   PHD_CUDA(h, cudaMemcpyAsync(&err, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -361,6 +381,7 @@ phd_status do_predict(phd_handle* h, const void* noise, bool z_staged = false, c
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_predict: a step is already in progress");
   if (h->m.learned && !z_staged)
     return fail(h, PHD_ERR_STATE, "phd_predict: a birth network is loaded; births need the scan (phd_predict_z)");
+  if (phd_status st = check_align(h, nullptr, noise, nullptr, {})) return st;
   cudaError_t e = is_fp64(h) ? phd::launch_predict<double>(h->d, h->m, static_cast<const double*>(noise), h->stream)
                              : phd::launch_predict<float>(h->d, h->m, static_cast<const float*>(noise), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "predict");
@@ -387,6 +408,8 @@ phd_status do_update(phd_handle* h, const void* Z, int M, bool z_in_workspace) {
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
   if (M > 0 && !Z && !z_in_workspace) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  if (!z_in_workspace)
+    if (phd_status st = check_align(h, Z, nullptr, nullptr, {})) return st;
   const void* src = z_in_workspace ? h->d.Z : Z;
   cudaError_t e = is_fp64(h) ? phd::launch_stage_z<double>(h->d, h->m, static_cast<const double*>(src), M, h->stream)
                              : phd::launch_stage_z<float>(h->d, h->m, static_cast<const float*>(src), M, h->stream);
@@ -403,6 +426,7 @@ phd_status do_extract(phd_handle* h, void* states, int* labels, int cap, int* d_
   if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_extract: call phd_update first");
   if (cap < 0) return fail(h, PHD_ERR_INVALID_ARG, "cap < 0");
   if (cap > 0 && (!states || !labels)) return fail(h, PHD_ERR_INVALID_ARG, "NULL output buffer");
+  if (phd_status st = check_align(h, nullptr, states, nullptr, {labels, d_count})) return st;
   cudaError_t e = is_fp64(h)
       ? phd::launch_extract<double>(h->d, h->m, static_cast<double*>(states), labels, cap, d_count, h->stream)
       : phd::launch_extract<float>(h->d, h->m, static_cast<float*>(states), labels, cap, d_count, h->stream);
@@ -420,6 +444,7 @@ phd_status do_extract(phd_handle* h, void* states, int* labels, int cap, int* d_
 
 phd_status do_resample(phd_handle* h, const uint32_t* u, const uint32_t* xu) {
   if (h->stage != kUpdated) return fail(h, PHD_ERR_STATE, "phd_resample: call phd_update first");
+  if (phd_status st = check_align(h, nullptr, nullptr, nullptr, {u, xu})) return st;
   cudaError_t e = is_fp64(h) ? phd::launch_resample<double>(h->d, h->m, u, xu, h->stream)
                              : phd::launch_resample<float>(h->d, h->m, u, xu, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "resample");
@@ -797,6 +822,7 @@ phd_status phd_predict_z(phd_handle* h, const void* d_Z, int32_t M, const float*
   if (M < 0) return fail(h, PHD_ERR_INVALID_ARG, "M < 0");
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
   if (M > 0 && !d_Z) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
+  if (phd_status sa = check_align(h, d_Z, d_noise, nullptr, {})) return sa;
   phd_status st = stage_z_only(h, d_Z, M);
   if (st != PHD_OK) return st;
   return do_predict(h, d_noise, true, d_head, M);
@@ -844,6 +870,7 @@ phd_status phd_step_inject(phd_handle* h, const void* d_Z, int32_t M, const void
   if (M > h->cfg.m_max) return fail(h, PHD_ERR_CAPACITY, "M > m_max");
   if (M > 0 && !d_Z) return fail(h, PHD_ERR_INVALID_ARG, "Z is NULL");
   if (cap < 0 || (cap > 0 && (!d_states || !d_labels))) return fail(h, PHD_ERR_INVALID_ARG, "bad output buffer");
+  if (phd_status sa = check_align(h, d_Z, d_states, d_noise, {d_labels, d_count, d_u, d_xu})) return sa;
   phd_status st = step_common(h, d_Z, M, d_noise, d_u, d_xu, d_states, d_labels, cap, d_count);
   if (st != PHD_OK) return st;
   if (h_count) {
@@ -876,7 +903,9 @@ phd_status phd_step_host(phd_handle* h, const void* h_Z, int32_t M, void* h_stat
   void* zd = M > 0 ? mapped_ptr(h_Z) : nullptr;
   void* sd = cap > 0 ? mapped_ptr(h_states) : nullptr;
   void* ld = cap > 0 ? mapped_ptr(h_labels) : nullptr;
-  if ((M == 0 || zd) && (cap == 0 || (sd && ld))) {
+  // (buffers the kernels cannot access as vectors take the copying path)
+  const bool vec_ok = !misaligned(zd, 2 * rs) && !misaligned(sd, 4 * rs) && !misaligned(ld, 4);
+  if ((M == 0 || zd) && (cap == 0 || (sd && ld)) && vec_ok) {
     if (!h->pin) PHD_CUDA(h, cudaHostAlloc(reinterpret_cast<void**>(&h->pin), 2 * sizeof(int), cudaHostAllocMapped));
     int* pin_d = static_cast<int*>(mapped_ptr(h->pin));
     if (!pin_d) return fail(h, PHD_ERR_CUDA, "phd_step_host: no device address for the pinned count");
@@ -919,6 +948,7 @@ phd_status phd_run(phd_handle* h, const void* d_Z, const int32_t* d_offsets, int
   if (S < 0 || !d_offsets || (S > 0 && (!d_counts || cap < 1 || !d_states || !d_labels)))
     return fail(h, PHD_ERR_INVALID_ARG, "bad phd_run arguments");
   if (S == 0) return PHD_OK;
+  if (phd_status sa = check_align(h, d_Z, d_states, nullptr, {d_offsets, d_labels, d_counts})) return sa;
   const size_t rs = real_size(h->cfg);
   if (use_fused(h)) return run_fused(h, d_Z, d_offsets, 0, S, nullptr, nullptr, nullptr, d_states, d_labels, d_counts, cap);
   // staged path: one graph-launched step per scan
@@ -1335,6 +1365,7 @@ phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* 
   if (h->stage != kReady) return fail(h, PHD_ERR_STATE, "phd_batch_step: a step is already in progress");
   if (!d_Z || !d_offsets || !d_counts || cap < 0 || (cap > 0 && (!d_states || !d_labels)))
     return fail(h, PHD_ERR_INVALID_ARG, "bad phd_batch_step arguments");
+  if (phd_status sa = check_align(h, d_Z, d_states, d_noise, {d_offsets, d_labels, d_counts, d_u})) return sa;
   cudaError_t e = is_fp64(h)
       ? phd::launch_stage_zb<double>(h->d, h->m, static_cast<const double*>(d_Z), d_offsets, h->stream)
       : phd::launch_stage_zb<float>(h->d, h->m, static_cast<const float*>(d_Z), d_offsets, h->stream);

@@ -547,3 +547,61 @@ def test_fused_and_staged_track_each_other():
             if len(la):
                 assert float((sa.double() - sb.double()).abs().max()) < 1e-2
     assert same >= 30
+
+
+@pytest.mark.parametrize("path", ["staged", "fused"])
+def test_misaligned_buffers_are_refused(path):
+    """The kernels access caller buffers as vectors (a measurement row of two
+    reals, an estimate row of four).  Views at an odd float offset are refused
+    with PHD_ERR_INVALID_ARG before anything is launched, the handle keeps
+    stepping exactly like an untouched one, and phd_step_host takes the
+    copying path for misaligned pinned host arrays."""
+    import ctypes
+    from paper_1503_03769_gb300 import phd as P
+    w = scenario.workload("dist16_10t", num_pe=4, n_targets=3, clutter_rate=10.0, particles_per_target=200,
+                          birth_count=200)
+    sc = scenario.simulate(w, 5, steps=3)
+    f, ref = _filter(w, 5, path), _filter(w, 5, path)
+    Z = torch.as_tensor(sc.meas[0], dtype=torch.float32, device="cuda").contiguous()
+    M, cap = Z.shape[0], w.m_max
+    zbuf = torch.zeros(2 * M + 1, dtype=torch.float32, device="cuda")
+    zbuf[1:] = Z.reshape(-1)
+    sbuf = torch.zeros(4 * cap + 1, dtype=torch.float32, device="cuda")
+    lab = torch.zeros(cap + 1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
+    off = torch.tensor([0, M], dtype=torch.int32, device="cuda")
+    vp = ctypes.c_void_p
+    hc = ctypes.c_int32(0)
+    z_ok, z_bad = vp(Z.data_ptr()), vp(zbuf.data_ptr() + 4)
+    s_ok, s_bad = vp(sbuf.data_ptr()), vp(sbuf.data_ptr() + 4)
+    l_ok, l_bad = vp(lab.data_ptr()), vp(lab.data_ptr() + 2)
+    c_ok = vp(cnt.data_ptr())
+    for args in [(z_bad, s_ok, l_ok), (z_ok, s_bad, l_ok), (z_ok, s_ok, l_bad)]:
+        st = f.L.phd_step(f.h, args[0], M, args[1], args[2], cap, c_ok, ctypes.byref(hc))
+        assert st == P.PHD_ERR_INVALID_ARG
+    assert f.L.phd_run(f.h, z_bad, vp(off.data_ptr()), 1, s_ok, l_ok, c_ok, cap) == P.PHD_ERR_INVALID_ARG
+    # nothing ran: the next steps equal an untouched filter's
+    for k in range(2):
+        s_f, l_f = f.step(sc.meas[k])
+        s_r, l_r = ref.step(sc.meas[k])
+        assert torch.equal(l_f, l_r) and torch.equal(s_f, s_r)
+    # stage API: a refused update leaves the predicted stage in place
+    f.predict()
+    assert f.L.phd_update(f.h, z_bad, M) == P.PHD_ERR_INVALID_ARG
+    f.update(sc.meas[2])
+    assert f.L.phd_extract(f.h, s_bad, l_ok, cap, None, ctypes.byref(hc)) == P.PHD_ERR_INVALID_ARG
+    f.extract()
+    f.resample()
+    # misaligned pinned host arrays: copied through the workspace instead
+    g, gref = _filter(w, 6, path), _filter(w, 6, path)
+    zh = torch.zeros(2 * M + 1, dtype=torch.float32).pin_memory().numpy()
+    zh[1:] = np.asarray(sc.meas[0], np.float32).reshape(-1)
+    sh = torch.zeros(4 * cap + 1, dtype=torch.float32).pin_memory().numpy()
+    lh = torch.zeros(cap, dtype=torch.int32).pin_memory().numpy()
+    n = g.step_host(zh[1:].reshape(M, 2), sh[1:].reshape(cap, 4), lh)
+    s_r, l_r = gref.step(sc.meas[0])
+    assert n == len(l_r)
+    np.testing.assert_array_equal(lh[:n], l_r.cpu().numpy())
+    np.testing.assert_array_equal(sh[1:].reshape(cap, 4)[:n], s_r.cpu().numpy())
+    for x in (f, ref, g, gref):
+        x.close()
