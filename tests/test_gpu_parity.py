@@ -130,6 +130,26 @@ def test_fused_many_pes_small_slices(pe_cap):
     assert rep.compared_labels > 0
 
 
+def test_maximum_pe_count_staged():
+    """K = 256 PEs, the most a handle takes: more PEs than SMs, so the fused
+    kernel (one co-resident CTA per PE) cannot hold them; AUTO runs the staged
+    path, a forced fused path is refused, and every stage (ring exchange and
+    CU fusion over 256 voters included) matches the oracle."""
+    from paper_1503_03769_gb300 import PhdError
+    w = scenario.workload("dist16_10t", num_pe=256, n_targets=3, clutter_rate=20.0,
+                          particles_per_target=2560, birth_count=2560, birth_steps=(1, 1, 1),
+                          pe_cap=64, exchange_frac=0.1)
+    truth = scenario.simulate(w, 17, steps=2)
+    centres = np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)])
+    f = _filter(w, 17, "auto")
+    assert f.get_path() == "staged"
+    with pytest.raises(PhdError):
+        f.set_path("fused")
+    f.close()
+    rep = _run_stages(w, 17, 2, sc=truth, n_seed=[20 + (j % 9) for j in range(256)], centres=centres)
+    assert rep.compared_labels > 0
+
+
 @pytest.mark.parametrize("mode,threshold", [("all", 0.0), ("ring", 1e-9), ("all", 1e9), ("all", 0.97)])
 @pytest.mark.parametrize("path", ["staged", "fused"])
 def test_exchange_variants_stages(mode, threshold, path):
