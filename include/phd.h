@@ -207,8 +207,8 @@ phd_status phd_get_birth_head(phd_handle *h, float *d_out, int32_t cap, int32_t 
  * n the number of other measurements q with |z_q0 - z_p0| <= 3 sigma_z[0]
  * and |wrap(z_q1 - z_p1)| <= 3 sigma_z[1] (bearing wrapped to [-pi, pi]).
  * d_Z FP32 [M][2], device; stream a cudaStream_t or NULL.  Asynchronous.
- * PHD_ERR_INVALID_ARG for a bad cfg (phd_init's checks), M < 0 or NULL
- * buffers. */
+ * PHD_ERR_INVALID_ARG for a bad cfg (phd_init's checks), M < 0, NULL
+ * buffers or a d_Z not aligned to 8 bytes. */
 phd_status phd_birth_features(const phd_config *cfg, const float *d_Z, int32_t M, float *d_X, void *stream);
 
 /* Number of parameters (4741): W1[64][3], b1[64], W2[64][64], b2[64],
@@ -526,7 +526,8 @@ phd_status phd_autotune(phd_handle *h, int32_t reps, phd_tuning *out);
  * Every call uses the same array; each call writes every partial it reads,
  * so nothing needs clearing, but calls that overlap on the GPU (concurrent
  * streams, several host threads) race on it: order them on one stream.
- * Errors: PHD_ERR_INVALID_ARG for a bad cfg, negative sizes or NULL buffers;
+ * Errors: PHD_ERR_INVALID_ARG for a bad cfg, negative sizes, NULL buffers or
+ * buffers off their row alignment (d_x 4 reals, d_w 1, d_Z 2, d_C 8 bytes);
  * PHD_ERR_CUDA if the set-up or a launch fails. */
 phd_status phd_colsum_static(const phd_config *cfg, const void *d_x, const void *d_w, int32_t n,
                              const void *d_Z, int32_t M, double *d_C, void *stream);
