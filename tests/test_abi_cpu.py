@@ -108,3 +108,16 @@ def test_c_program_builds_against_the_header(tmp_path):
     import test_gpu_c_abi
     test_gpu_c_abi.build_c_program(str(tmp_path / "track"))
     assert os.path.exists(tmp_path / "track")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libphd.so the binding raises before it computes
+    anything, for the library loader and for a filter handle alike."""
+    import scenario
+    from paper_1503_03769_gb300 import phd
+    monkeypatch.setattr(phd, "LIB_PATH", str(tmp_path / "libphd.so"))
+    monkeypatch.setattr(phd, "_lib", None)
+    with pytest.raises(ImportError):
+        phd.lib()
+    with pytest.raises(ImportError):
+        phd.ParticlePHD(scenario.workload("linear4_fp64"), device="cpu")
