@@ -42,6 +42,8 @@ class StageReport:
     max_w_rel: float = 0.0
     max_mass_rel: float = 0.0
     max_state_err: float = 0.0
+    max_c_rel: float = 0.0
+    max_pred_abs: float = 0.0
     notes: List[str] = field(default_factory=list)
 
 
@@ -108,6 +110,8 @@ def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
         # FP32 rounding of x + T vx + T^2/2 a: a few ulp of |x| <= 2e3 m
         atol = 1e-3 if dt == np.float32 else 1e-9
         np.testing.assert_allclose(xp[j], xo, rtol=0, atol=atol)
+        if len(xo):
+            rep.max_pred_abs = max(rep.max_pred_abs, float(np.abs(np.asarray(xp[j], np.float64) - xo).max()))
         check_weights(wp[j], wo, tol, f"predict PE {j}")
     # --- update (Eq. 7-8)
     C, mass = g["C"], g["mass"]
@@ -123,6 +127,9 @@ def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
             # C matters to the filter through C / (kappa + C): an absolute slack of
             # 1e-7 kappa per measurement moves the mass by at most 1e-7 per label
             err = np.abs(C[j, :M] - Cloc[j])
+            big = Cloc[j] > 1e-3 * kap   # relative error where C is not negligible against kappa
+            if big.any():
+                rep.max_c_rel = max(rep.max_c_rel, float((err[big] / Cloc[j][big]).max()))
             bad = err > tol["c_rel"] * Cloc[j] + 1e-7 * kap
             assert not bad.any(), (j, int(bad.sum()), err[bad][:3], Cloc[j][bad][:3], kap)
         wo = oracle.weight_update(m, xp[j], wp[j], Zd, Cu[j])

@@ -8,6 +8,7 @@ with unequal counts, M below and above the 256-thread measurement rounds,
 both sensors, both precisions and both normaliser modes.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -55,7 +56,23 @@ def _run_stages(w, seed, steps, sc=None, warm=0, n_seed=None, centres=None, path
         xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap)
         stage_step(f, w, m, sc.meas[k], noise, u, xu, rep, path=path)
     f.close()
+    _log_errors(w, path, rep)
     return rep
+
+
+def _log_errors(w, path, rep):
+    """With PHD_PARITY_LOG set, append the largest errors this test saw
+    against the oracle (one JSON line per test) to that file."""
+    out = os.environ.get("PHD_PARITY_LOG")
+    if not out:
+        return
+    import json
+    rec = {"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "workload": w.name,
+           "precision": w.precision, "path": path, "K": w.num_pe, "C_rel": rep.max_c_rel,
+           "w_rel": rep.max_w_rel, "mass_rel": rep.max_mass_rel, "state_abs_m": rep.max_state_err,
+           "predict_abs_m": rep.max_pred_abs, "labels": rep.compared_labels}
+    with open(out, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
