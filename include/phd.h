@@ -521,11 +521,19 @@ phd_status phd_autotune(phd_handle *h, int32_t reps, phd_tuning *out);
  * exits: ceil(n / 256) * M must not exceed 524288, else PHD_ERR_CAPACITY and
  * nothing runs.  No cudaMalloc, cudaFree or allocating library call is made.
  * The first call on a device, with that device current, looks up the array's
- * device address and copies in a 4 KB lookup table (a synchronous copy): make
- * that first call before any stream capture.  Later calls are asynchronous.
+ * device address and copies in a 4 KB lookup table on `stream`, then waits
+ * for `stream` (with stream NULL, the legacy default stream, that wait also
+ * covers the work of every blocking stream on the device): make that first
+ * call before any stream capture.  Later calls are asynchronous.  The looked-up
+ * addresses are kept for the life of the process: after cudaDeviceReset the
+ * library's device arrays are gone, and this entry point must not be called
+ * again in that process.
  * Every call uses the same array; each call writes every partial it reads,
  * so nothing needs clearing, but calls that overlap on the GPU (concurrent
  * streams, several host threads) race on it: order them on one stream.
+ * Non-finite states, weights or measurements give NaN column sums (as in
+ * phd_update), except that with the gate_sigma truncation on, a pair whose
+ * exponent is NaN counts as truncated (0).
  * Errors: PHD_ERR_INVALID_ARG for a bad cfg, negative sizes, NULL buffers or
  * buffers off their row alignment (d_x 4 reals, d_w 1, d_Z 2, d_C 8 bytes);
  * PHD_ERR_CUDA if the set-up or a launch fails. */

@@ -10,7 +10,10 @@
 // arrays only through the device addresses cudaGetSymbolAddress returns (a
 // symbol's host-side name is not a device pointer); on the first call made
 // with a device current, the addresses are looked up and the anchor table is
-// copied in (a synchronous copy), and both are cached for that device.
+// copied in (on the caller's stream, which the call then waits for), and both
+// are cached for that device.  The cache is not invalidated by a device reset:
+// after cudaDeviceReset the library's device arrays are gone and this entry
+// point must not be called again in the process.
 #include <cstdint>
 #include <mutex>
 
@@ -39,6 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum_flat(Model m, const St4<R>*
   __shared__ double red[kThreads];
   const Lik<R> L = make_lik<R>(m);
   const R qk = (R)m.qk;
+  const bool trunc = m.qk < (double)INFINITY;   // k-sigma truncation variant on
   const int tiles = (n + kTile - 1) / kTile;
   const int mper = M < kThreads ? M : kThreads;
   const int nsplit = kThreads / mper;
@@ -70,7 +74,10 @@ __global__ void __launch_bounds__(kThreads) k_colsum_flat(Model m, const St4<R>*
         int k = 0;
         for (int i = split; i < cnt; i += nsplit) {
           const R q = qform<R>(L, z.a, z.b, sh0[i], sh1[i], shl[i]);
-          part_ = fma(exp2_neg(q < qk ? q : (R)INFINITY), sw[i], part_);   // k-sigma truncation
+          // truncation only when the variant is on, so a NaN exponent (non-finite
+          // state or measurement) propagates into C as on the staged path
+          const R qq = (trunc && !(q < qk)) ? (R)INFINITY : q;
+          part_ = fma(exp2_neg(qq), sw[i], part_);
           if (++k == 32) { acc += part_; part_ = 0; k = 0; }
         }
         acc += part_;
@@ -97,8 +104,9 @@ __global__ void k_colsum_flat_sum(const double* __restrict__ part, int tiles, in
 }
 
 // Device addresses of the scratch array and the anchor table for the current
-// device; the first call per device looks them up and fills the table.
-static cudaError_t static_arrays_for_current_device(void** scratch, void** anchors) {
+// device; the first call per device looks them up and fills the table with a
+// copy on the caller's stream, then waits for that stream alone.
+static cudaError_t static_arrays_for_current_device(cudaStream_t s, void** scratch, void** anchors) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -113,7 +121,9 @@ static cudaError_t static_arrays_for_current_device(void** scratch, void** ancho
     if (e != cudaSuccess) return e;
     Anchor tab[kAnchors];
     fill_anchor_table(tab);
-    e = cudaMemcpy(q, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(q, tab, sizeof(tab), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);   // tab is on this stack frame
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = p;
     g_anchor_ptr[dev] = q;
@@ -153,12 +163,12 @@ extern "C" phd_status phd_colsum_static(const phd_config* cfg, const void* d_x, 
   }
   const size_t tiles = ((size_t)n + phd::kTile - 1) / phd::kTile;
   if (tiles * (size_t)M > phd::kStaticScratchDoubles) return PHD_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* scratch = nullptr;
   void* anchors = nullptr;
-  if (phd::static_arrays_for_current_device(&scratch, &anchors) != cudaSuccess) return PHD_ERR_CUDA;
+  if (phd::static_arrays_for_current_device(s, &scratch, &anchors) != cudaSuccess) return PHD_ERR_CUDA;
   const phd::Anchor* tab = static_cast<const phd::Anchor*>(anchors);
   const phd::Model m = phd::model_from_config(*cfg);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cfg->precision == PHD_FP64
       ? phd::launch_colsum_static<double>(m, d_x, d_w, n, d_Z, M, d_C, static_cast<double*>(scratch), tab, s)
       : phd::launch_colsum_static<float>(m, d_x, d_w, n, d_Z, M, d_C, static_cast<double*>(scratch), tab, s);

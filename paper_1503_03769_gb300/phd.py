@@ -189,13 +189,47 @@ def make_config(w, seed: int = 0) -> phd_config:
     return c
 
 
+def _check_colsum_static_args(cfg: phd_config, x, w, Z, C):
+    """Shapes, dtypes and device of phd_colsum_static's buffers; returns (n, M)."""
+    real = torch.float64 if cfg.precision == PHD_FP64 else torch.float32
+    for name, t in (("x", x), ("w", w), ("Z", Z), ("C", C)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+    for name, t in (("x", x), ("w", w), ("Z", Z)):
+        if t.dtype != real:
+            raise ValueError(f"{name} is {t.dtype}; the config's precision needs {real}")
+    if C.dtype != torch.float64:
+        raise ValueError(f"C is {C.dtype}; it must be torch.float64")
+    if x.dim() != 2 or x.shape[1] != 4:
+        raise ValueError(f"x must be (n, 4), got {tuple(x.shape)}")
+    if w.dim() != 1 or w.shape[0] != x.shape[0]:
+        raise ValueError(f"w must be ({x.shape[0]},), got {tuple(w.shape)}")
+    if Z.dim() != 2 or Z.shape[1] != 2:
+        raise ValueError(f"Z must be (M, 2), got {tuple(Z.shape)}")
+    n, M = int(x.shape[0]), int(Z.shape[0])
+    if C.numel() < M:
+        raise ValueError(f"C holds {C.numel()} values, fewer than M = {M}")
+    devs = {t.device for t in (x, w, Z, C)}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError(f"x, w, Z and C must be on one CUDA device, got {sorted(map(str, devs))}")
+    for name, t in (("x", x), ("w", w), ("Z", Z), ("C", C)):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    return n, M
+
+
 def colsum_static(cfg: phd_config, x: torch.Tensor, w: torch.Tensor, Z: torch.Tensor, C: torch.Tensor,
                   stream: Optional[torch.cuda.Stream] = None) -> int:
     """phd_colsum_static: Eq. 7 column sums into C (double [M]) with no device
-    allocation; returns the phd status."""
+    allocation; returns the phd status.
+
+    The library reads x, w and Z as the config's real type and writes M
+    doubles into C, so every tensor is checked here first (ValueError, nothing
+    launched): x (n, 4), w (n,), Z (M, 2) in float32 (PHD_FP32) or float64
+    (PHD_FP64), C float64 with at least M elements, all contiguous on one CUDA
+    device."""
+    n, M = _check_colsum_static_args(cfg, x, w, Z, C)
     st = stream if stream is not None else torch.cuda.current_stream()
-    n = int(w.shape[0])
-    M = int(Z.shape[0])
     return lib().phd_colsum_static(ctypes.byref(cfg), _ptr(x) if n else None, _ptr(w) if n else None, n,
                                    _ptr(Z) if M else None, M, _ptr(C) if M else None,
                                    ctypes.c_void_p(st.cuda_stream))

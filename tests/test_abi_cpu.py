@@ -121,3 +121,33 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         phd.lib()
     with pytest.raises(ImportError):
         phd.ParticlePHD(scenario.workload("linear4_fp64"), device="cpu")
+
+
+def test_colsum_static_binding_refuses_wrong_buffers_before_any_launch():
+    """The binding checks dtype, shape and device of phd_colsum_static's
+    buffers against the config before the library is called: a float32
+    state array under a PHD_FP64 config (the kernel would read twice its
+    bytes), a float32 or short C (the kernel would write past it), a wrong
+    row width, or host tensors are refused with ValueError."""
+    import torch
+    import scenario
+    from paper_1503_03769_gb300 import phd
+    w64 = scenario.workload("linear4_fp64")
+    w32 = scenario.workload("dist16_10t")
+    c64, c32 = phd.make_config(w64), phd.make_config(w32)
+    n, M = 10, 4
+    f32 = lambda *s: torch.zeros(*s, dtype=torch.float32)
+    f64 = lambda *s: torch.zeros(*s, dtype=torch.float64)
+    cases = [
+        (c64, f32(n, 4), f64(n), f64(M, 2), f64(M), "x is"),
+        (c64, f64(n, 4), f64(n), f32(M, 2), f64(M), "Z is"),
+        (c32, f32(n, 4), f32(n), f32(M, 2), f32(M), "C is"),
+        (c32, f32(n, 4), f32(n), f32(M, 2), f64(M - 1), "fewer than M"),
+        (c32, f32(n, 3), f32(n), f32(M, 2), f64(M), "x must be"),
+        (c32, f32(n, 4), f32(n + 1), f32(M, 2), f64(M), "w must be"),
+        (c32, f32(n, 4), f32(n), f32(M, 3), f64(M), "Z must be"),
+        (c32, f32(n, 4), f32(n), f32(M, 2), f64(M), "one CUDA device"),
+    ]
+    for cfg, x, wt, Z, C, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            phd.colsum_static(cfg, x, wt, Z, C)
