@@ -3,20 +3,32 @@
 
 Metric: particle x measurement pairs per second per PHD update (the update's
 pairs, N_k x M_k summed over the timed steps, divided by the timed device
-time of the whole steps), plus steps/s.  A step is one full filter step:
-predict + birth, update, labelled extraction + CU fusion, resampling + ring
-exchange, through libphd.so's phd_step (a CUDA graph of the step's kernels).
+time of the whole steps), plus steps/s, at matched OSPA.  A step is one full
+filter step: predict + birth, update, labelled extraction (+ CU fusion),
+resampling (+ ring exchange), through libphd.so's phd_step (a CUDA graph of
+the step's kernels, or the fused step kernel where a PE's slice fits one SM).
 
-Default workload: the 16-PE distributed scheme (10 targets, clutter rate 50,
-1000 particles per target, 1000 births per step, 10 % ring exchange, FP32
-bulk / FP64 normalisers and CDF).  A run of that workload is 100 scans; K
-timed steps are K / 100 independent runs back to back (fresh filter state
-and scenario seed per run, reset between timed steps).  All measurement sets
-are resident in device memory before timing; L2 is flushed (512 MiB write)
-between timed steps, outside the timed events.
+Default workload: the dense range-bearing configuration (100 targets, clutter
+rate 500, ~600 measurements per scan, 2000 particles per target, 20000 births
+per step, ~2.2e5 particles and ~1.3e8 pairs per update at steady state; FP32
+bulk, FP64 normalisers and CDF), the largest single-GPU configuration.  A run
+is 100 scans; the timed steps are scans 50.. of consecutive runs (all truth
+targets exist from 40 % of a run on; the earlier scans are replayed untimed).
+Measurement sets are resident in device memory before timing; L2 is flushed
+(512 MiB write) between timed steps, outside the timed events.
 
---impl reference times the FP64 CPU oracle (tests' reference implementation)
-on the same workload; the driver divides the two.
+OSPA (c = 100 m, p = 2) is computed on every timed scan and compared with the
+FP64 oracle's on the same seeds and scans (a stored record written by
+tests/golden/make_oracle_ospa.py, which calls only the oracle): once for the
+timed run (in-kernel random numbers) and once for an untimed run that
+injects the oracle's own random numbers; "matched" means within 5 %.
+
+The line also carries compact sub-blocks for the 16-PE distributed workload,
+the 256-run batch and the learned birth proposal (--no-subblocks drops them;
+--workload NAME runs one workload alone).
+
+--impl reference times the FP64 CPU oracle (the tests' reference
+implementation) on the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -40,8 +52,38 @@ import scenario
 
 METRIC = "particle×measurement pairs/s per PHD update and steps/s on 1 GB300 at matched OSPA"
 UNIT = "pairs/s"
-# MUFU ex2 peak: 152 SMs x 32 ex2/clk/SM x 2.07 GHz (max SM clock); one ex2 per pair
-EX2_PEAK_TEXP = 152 * 32 * 2.070e9 / 1e12
+# nominal MUFU ex2 rate, context only: 152 SMs x 32 ex2/clk/SM x 2.07 GHz; the
+# roofline divides by the rate phd_measure_ex2_rate measures on the device
+EX2_NOMINAL_TEXP = 152 * 32 * 2.070e9 / 1e12
+DEFAULT_WORKLOAD = "dense_rb_100t"
+MATCH_TOL = 0.05
+
+
+def cpu_info():
+    """Host cores and CPU model (from /proc/cpuinfo, where the kernel reports one)."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            k, _, v = ln.partition(":")
+            if k.strip().lower() in ("model name", "cpu model", "hardware") and v.strip():
+                model = v.strip()
+                break
+            if k.strip() == "CPU part" and model is None:
+                model = f"CPU part {v.strip()}"
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def oracle_record(wname):
+    """The stored oracle OSPA record of a workload, {seed: {scan: row}}, or None."""
+    p = os.path.join(ROOT, "tests", "golden", f"oracle_ospa_{wname}.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    return {r["seed"]: {row["scan"]: row for row in r["scans"]} for r in d["runs"]}
 
 
 def job_totals(amount, seconds, world, device="cpu"):
@@ -167,33 +209,40 @@ def _bad_clocks(c):
 # the CPU oracle (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
 
-def oracle_run(w, seeds, max_steps, budget_s, skip=0):
-    """Run the FP64 oracle filter over the scenarios of `seeds` (100 scans each);
-    returns (pairs, seconds, steps, ospa_list) for the timed steps after `skip`."""
+def oracle_run(w, seeds, max_steps, budget_s, skip=0, threads=1):
+    """Run the FP64 oracle filter over whole runs of the scenarios of `seeds`
+    with the scenario's injected random numbers (FP32-rounded, as the GPU
+    path receives them); returns (pairs, seconds, steps, ospa_list) for the
+    timed steps after `skip`, on `threads` host threads (the oracle's OpenMP
+    build, bit-identical to the single-threaded one)."""
     import oracle
+    oracle.set_threads(threads)
     pairs, secs, steps, ospas = 0, 0.0, 0, []
     done = 0
-    for seed in seeds:
-        sc = scenario.simulate(w, seed)
-        f = oracle.OracleFilter(w)
-        for k, Z in enumerate(sc.meas):
-            noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap)
-            u = scenario.resample_u32(seed, k, w.num_pe)
-            xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap) if w.num_pe > 1 else None
-            n_before = sum(len(a) for a in f.x) + w.birth_count
-            t0 = time.perf_counter()
-            lab, zet = f.step(Z, noise, u, xu)
-            dt = time.perf_counter() - t0
-            done += 1
-            if done <= skip:
-                continue
-            pairs += n_before * len(Z)
-            secs += dt
-            steps += 1
-            ospas.append(_ospa(zet, sc.truth[k]))
-            if steps >= max_steps or secs >= budget_s:
-                return pairs, secs, steps, ospas
-    return pairs, secs, steps, ospas
+    try:
+        for seed in seeds:
+            sc = scenario.simulate(w, seed)
+            f = oracle.OracleFilter(w)
+            for k, Z in enumerate(sc.meas):
+                noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap, np.float32)
+                u = scenario.resample_u32(seed, k, w.num_pe)
+                xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap) if w.num_pe > 1 else None
+                n_before = sum(len(a) for a in f.x) + w.birth_count
+                t0 = time.perf_counter()
+                lab, zet = f.step(Z, noise, u, xu)
+                dt = time.perf_counter() - t0
+                done += 1
+                if done <= skip:
+                    continue
+                pairs += n_before * len(Z)
+                secs += dt
+                steps += 1
+                ospas.append(_ospa(zet, sc.truth[k]))
+                if steps >= max_steps or secs >= budget_s:
+                    return pairs, secs, steps, ospas
+        return pairs, secs, steps, ospas
+    finally:
+        oracle.set_threads(1)
 
 
 def _ospa(zet, truth):
@@ -203,12 +252,33 @@ def _ospa(zet, truth):
     return oracle.ospa(X, Y, 100.0, 2.0)
 
 
+def cpu_baseline(w, seed, budget_s):
+    """The oracle on whole filter steps of the workload, scans 0.. of run `seed`:
+    single-threaded until ~budget_s, then the same steps on all host cores."""
+    nproc = os.cpu_count() or 1
+    p1, s1, n1, _ = oracle_run(w, [seed], 10 ** 9, budget_s, threads=1)
+    pn, sn, nn, _ = oracle_run(w, [seed], n1, 10 ** 9, threads=nproc)
+    import oracle
+    info = cpu_info()
+    return {"value": pn / sn if sn > 0 else None, "unit": UNIT, "cores": oracle.threads() if nproc > 1 else 1,
+            "kind": "oracle",
+            "sample": f"filter steps on scans 0..{n1 - 1} of {w.name} run {seed} ({p1:.3g} pairs; whole steps: "
+                      f"predict, update, extraction, resampling), FP64 C oracle, OpenMP build on all host cores "
+                      f"({sn:.1f} s)",
+            **info,
+            "single_thread": {"value": p1 / s1 if s1 > 0 else None, "unit": UNIT, "cores": 1, "seconds": round(s1, 2),
+                              "sample": "the same steps, single-threaded build"},
+            "openmp_seconds": round(sn, 2), "openmp_available": oracle.openmp_available()}
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
     budget = float(os.environ.get("PHD_REF_BUDGET_S", "150"))
     seeds = [args.seed + r for r in range(64)]
-    pairs, secs, steps, ospas = oracle_run(w, seeds, args.steps, budget, skip=args.warmup)
+    nproc = os.cpu_count() or 1
+    pairs, secs, steps, ospas = oracle_run(w, seeds, args.steps, budget, skip=args.warmup, threads=nproc)
+    import oracle
     value = pairs / secs if secs > 0 else 0.0
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -217,9 +287,11 @@ def run_reference(args, w, rank, world):
         "data": "synthetic", "config": workload_config(w, None, "n/a (CPU)"),
         "steps_per_s": steps / secs if secs > 0 else 0.0,
         "ospa_mean": float(np.mean(ospas)) if ospas else None,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} filter steps of {w.name} (seeds from {args.seed}), "
-                                   f"after {args.warmup} untimed, single-threaded FP64 C oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc if oracle.openmp_available() else 1,
+                         "kind": "oracle", **cpu_info(),
+                         "sample": f"{steps} whole filter steps of {w.name} (runs from seed {args.seed}, scans "
+                                   f"from 0, after {args.warmup} untimed), FP64 C oracle on all host cores "
+                                   f"(OpenMP build, bit-identical to the single-threaded one)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -272,7 +344,91 @@ def _traffic_from_profile(path, workload):
     return traffic if want == kernel_sources_sha256(files) else None
 
 
-def run_gpu(args, w, rank, world, local_rank):
+def ex2_peak(local_rank):
+    """The device's measured ex2 rate (phd_measure_ex2_rate: fastest of 20
+    launches of ~6 ms), with the SM clock sampled while it ran."""
+    import torch
+    from paper_1503_03769_gb300 import phd
+    clk = ClockSampler(_gpu_id(local_rank))
+    clk.begin()
+    rate, ms = phd.measure_ex2_rate(20)
+    rate2, ms2 = phd.measure_ex2_rate(60)
+    c = clk.end()
+    best = max(rate, rate2)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    out = {"ex2_per_s": best, "Texp_per_s": best / 1e12, "best_launch_ms": min(ms, ms2), "sms": sms,
+           "sm_mhz_median": c.get("sm_mhz"), "clock_samples": c.get("samples"),
+           "nominal_Texp_per_s": EX2_NOMINAL_TEXP,
+           "how": "phd_measure_ex2_rate: 8 CTAs x 256 threads per SM, 8 independent chains of 4096 dependent "
+                  "ex2.approx.ftz.f32 per thread; fastest launch (CUDA events)"}
+    if c.get("sm_mhz"):
+        out["ex2_per_clk_per_sm"] = best / (sms * c["sm_mhz"] * 1e6)
+    return out
+
+
+def _gpu_id(local_rank):
+    import torch
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        return str(local_rank)
+
+
+def _ospa_of(states, count, truth):
+    n = int(count)
+    est = states[:n].double().cpu().numpy() if n else np.zeros((0, 4))
+    return ospa_metric(est[:, [0, 2]] if n else np.zeros((0, 2)),
+                       truth[:, [0, 2]] if len(truth) else np.zeros((0, 2)), 100.0, 2.0)
+
+
+def injected_ospa(f, w, seeds, scen, dev):
+    """Untimed whole runs of `seeds` that inject the oracle's random numbers
+    (the FP32-rounded draws tests/golden/make_oracle_ospa.py gives the oracle):
+    OSPA (c = 100, p = 2) per (seed, scan)."""
+    import torch
+    out = {}
+    K = w.num_pe
+    for seed in seeds:
+        sc = scen(seed)
+        f.set_state([np.zeros((0, 4))] * K, [np.zeros(0)] * K)
+        for k, Z in enumerate(sc.meas):
+            noise = scenario.step_noise(seed, k, K, w.pe_cap, np.float32)
+            u = scenario.resample_u32(seed, k, K)
+            xu = scenario.exchange_u32(seed, k, K, w.pe_cap) if K > 1 else None
+            st, lb = f.step_inject(Z, noise, u, xu)
+            out[(seed, k)] = _ospa_of(st, len(lb), sc.truth[k])
+    return out
+
+
+def matched_ospa(w, timed_ospa, inj_ospa, rec, steady):
+    """GPU OSPA against the oracle record on the same seeds and scans."""
+    def mean_over(d, keys):
+        v = [d[k] for k in keys if k in d]
+        return float(np.mean(v)) if v else None
+
+    keys_timed = [k for k in timed_ospa if k[0] in rec]
+    orc = {(sd, sc): row["ospa2"] for sd, rows in rec.items() for sc, row in rows.items()}
+    keys_steady = sorted({(sd, k) for sd, _ in keys_timed for k in range(steady, w.steps)})
+    o_t, g_t, i_t = mean_over(orc, keys_timed), mean_over(timed_ospa, keys_timed), mean_over(inj_ospa, keys_timed)
+    o_s, i_s = mean_over(orc, keys_steady), mean_over(inj_ospa, keys_steady)
+    rel = lambda a, b: (a - b) / b if (a is not None and b) else None
+    res = {"oracle_timed_scans": o_t, "gpu_timed": g_t, "gpu_injected_timed_scans": i_t,
+           "rel_gpu_timed": rel(g_t, o_t), "rel_injected": rel(i_t, o_t),
+           "oracle_scans_from_steady": o_s, "gpu_injected_scans_from_steady": i_s,
+           "rel_injected_from_steady": rel(i_s, o_s),
+           "scans_compared": len(keys_timed), "seeds": sorted({k[0] for k in keys_timed}),
+           "tolerance": MATCH_TOL}
+    ok = [abs(r) <= MATCH_TOL for r in (res["rel_injected"], res["rel_injected_from_steady"]) if r is not None]
+    res["matched"] = bool(ok) and all(ok)
+    res["note"] = ("matched: the GPU run injecting the oracle's random numbers has mean OSPA within 5 % of the "
+                   "FP64 oracle's on the timed scans and on every scan from the steady window on; the timed run "
+                   "(in-kernel Philox draws) is compared on the same scans for context")
+    return res
+
+
+def run_gpu(args, w, rank, world, local_rank, sub=False):
+    """One-filter workloads through phd_step; returns the JSON line (rank 0) or None."""
     import torch
     from paper_1503_03769_gb300 import ParticlePHD
 
@@ -285,7 +441,14 @@ def run_gpu(args, w, rank, world, local_rank):
     per_run = steps_per_run - steady
     runs = max(1, math.ceil((args.warmup + args.steps) / per_run))
     base_seed = args.seed + 1000 * rank
-    scen = [scenario.simulate(w, base_seed + r) for r in range(runs)]
+    scen_cache = {}
+
+    def scen_of(seed):
+        if seed not in scen_cache:
+            scen_cache[seed] = scenario.simulate(w, seed)
+        return scen_cache[seed]
+
+    scen = [scen_of(base_seed + r) for r in range(runs)]
     seq = [(r, k) for r in range(runs) for k in range(steady, steps_per_run)][: args.warmup + args.steps]
     dtype = torch.float64 if w.precision == "fp64" else torch.float32
     Zdev = {(r, k): torch.as_tensor(scen[r].meas[k], dtype=dtype, device=dev) for r, k in seq}
@@ -295,8 +458,6 @@ def run_gpu(args, w, rank, world, local_rank):
     empty_w = [np.zeros(0)] * w.num_pe
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     cap = w.m_max
-    out_s = torch.empty((cap, 4), dtype=dtype, device=dev)
-    out_l = torch.empty(cap, dtype=torch.int32, device=dev)
 
     # work of the untimed run heads, taken out of the counters (the stage
     # timer is off during them)
@@ -344,12 +505,7 @@ def run_gpu(args, w, rank, world, local_rank):
         begin_run_if_needed(r, k)
         f.step(Zdev[(r, k)], cap=cap, sync=False)
     torch.cuda.synchronize()
-
-    try:
-        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
-        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        gpu_id = str(local_rank)
+    gpu_id = _gpu_id(local_rank)
 
     def timed_loop():
         f.reset_stats()
@@ -372,8 +528,7 @@ def run_gpu(args, w, rank, world, local_rank):
             s, l, c = f.step(Zdev[(r, k)], cap=cap, sync=False)
             e1.record()
             evs.append((e0, e1))
-            if k % 10 == 0:
-                est_log.append((r, k, s.clone(), c.clone()))
+            est_log.append((r, k, s.clone(), c.clone()))
         nvtx_pop()
         torch.cuda.synchronize()
         if world > 1:
@@ -397,30 +552,32 @@ def run_gpu(args, w, rank, world, local_rank):
     value = pairs_all / (ms_max * 1e-3)
     steps_per_s = world * K / (ms_max * 1e-3)
 
-    # OSPA of the logged estimates against the truth (c = 100, p = 2)
-    ospa_vals = []
+    # OSPA (c = 100, p = 2) of every timed scan against the truth
+    timed_ospa = {}
     for r, k, s, c in est_log:
-        n = int(c.item())
-        est = s[:n].double().cpu().numpy()
-        tr = scen[r].truth[k]
-        ospa_vals.append(ospa_metric(est[:, [0, 2]] if n else np.zeros((0, 2)),
-                                     tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
+        timed_ospa[(base_seed + r, k)] = _ospa_of(s, c.item(), scen[r].truth[k])
 
-    # roofline of the timed kernel: the fused step kernel (fused path) or the
-    # update stage's kernels (staged path); one ex2 per pair is the unit
+    # roofline of the timed kernels: the fused step kernel (fused path) or the
+    # update stage's kernels (staged path); one ex2 per pair, against the
+    # device's measured ex2 rate
     path = f.get_path()
+    peak = ex2_peak(local_rank)
     upd_ms = st["update_ms"]
     achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
+    ev_frac = st["pairs_evaluated"] / pairs if pairs else None
     kname = "k_step_fused (whole step, one CTA per PE)" if path == "fused" else UPDATE_KERNELS
     roofline = {"bound": "alu", "kernel": kname,
-                "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
-                "frac": achieved / EX2_PEAK_TEXP, "traffic": _traffic_from_profile(path, w.name),
-                "peak_source": "derived: 152 SMs x 32 MUFU ex2/clk x 2.07 GHz (one ex2 per pair)",
+                "achieved": achieved, "peak": peak["Texp_per_s"], "unit": "Texp/s",
+                "frac": achieved / peak["Texp_per_s"], "traffic": _traffic_from_profile(path, w.name),
+                "peak_source": "measured on this device: phd_measure_ex2_rate (burst; the kernel is timed alone)",
+                "frac_evaluated": (achieved * ev_frac / peak["Texp_per_s"]) if ev_frac is not None else None,
+                "frac_of_nominal": achieved / EX2_NOMINAL_TEXP,
                 "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                 "pairs_per_update": pairs / max(st["updates"], 1),
-                "pairs_evaluated_frac": st["pairs_evaluated"] / pairs if pairs else None,
+                "pairs_evaluated_frac": ev_frac,
                 "note": "achieved counts every particle x measurement pair (the metric's unit); pairs past "
-                        "the exact likelihood gate contribute exactly 0 and are skipped"}
+                        "the exact likelihood gate contribute exactly 0 and are skipped (frac_evaluated counts "
+                        "only the evaluated ones)"}
 
     # whole runs in one launch each (phd_run): S scans per call, L2 flushed
     # between runs (outside the events)
@@ -449,7 +606,6 @@ def run_gpu(args, w, rank, world, local_rank):
 
     # end to end through the public host-buffer call (pinned host memory)
     set_timer(False)
-    npdt = np.float64 if w.precision == "fp64" else np.float32
     Zhost = {key: torch.as_tensor(scen[key[0]].meas[key[1]], dtype=dtype).pin_memory().numpy()
              for key in seq}
     hs = torch.empty((cap, 4), dtype=dtype).pin_memory().numpy()
@@ -474,10 +630,20 @@ def run_gpu(args, w, rank, world, local_rank):
     st2 = f.stats()
     e2e_pairs, e2e_max = job_totals(st2["pairs"] - head["pairs"], e2e_s, world, dev)
     e2e_val = e2e_pairs / e2e_max
+
+    # matched OSPA: the oracle's stored record on the same seeds and scans,
+    # and an untimed run with the oracle's own random numbers
+    rec = oracle_record(w.name) if (w.gate_sigma == 0 and not args.no_matched) else None
+    matched = None
+    if rec is not None:
+        seeds = sorted({sd for sd, _ in timed_ospa if sd in rec})
+        if seeds:
+            inj = injected_ospa(f, w, seeds, scen_of, dev)
+            matched = matched_ospa(w, timed_ospa, inj, rec, steady)
     f.close()
 
     if rank != 0:
-        return 0
+        return None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
@@ -490,8 +656,11 @@ def run_gpu(args, w, rank, world, local_rank):
         "run_mode": {"api": "phd_run (one launch per run of scans)",
                      "value": run_pairs / (run_ms * 1e-3) if run_ms > 0 else None, "unit": UNIT,
                      "ms_per_step": run_ms / max(run_steps, 1), "steps": run_steps},
-        "ospa_mean": float(np.mean(ospa_vals)) if ospa_vals else None,
+        "ospa_mean": float(np.mean(list(timed_ospa.values()))) if timed_ospa else None,
+        "ospa_scans": len(timed_ospa),
+        "matched_ospa": matched,
         "roofline": roofline,
+        "ex2_peak": peak,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K,
                 "note": "phd_step_host: pinned host Z in, estimates + count out, synchronous per step"},
@@ -500,17 +669,10 @@ def run_gpu(args, w, rank, world, local_rank):
     }
     if tuning is not None:
         line["tuning"] = tuning
-    if world == 1 and not args.no_cpu_baseline:
-        # whole runs of the same workload (consecutive seeds, like the timed
-        # region) until the time budget is spent
+    if world == 1 and not args.no_cpu_baseline and not sub:
         budget = float(os.environ.get("PHD_CPU_BASELINE_S", "12"))
-        cp, cs, cn, _ = oracle_run(w, [args.seed + r for r in range(256)], 10 ** 9, budget)
-        line["cpu_baseline"] = {"value": cp / cs if cs > 0 else None, "unit": UNIT, "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"first {cn} filter steps of {w.name} runs from seed {args.seed} "
-                                          f"({w.steps} scans each; {cs:.1f} s), single-threaded FP64 C oracle"}
-    print(json.dumps(line), flush=True)
-    return 0
+        line["cpu_baseline"] = cpu_baseline(w, args.seed, budget)
+    return line
 
 
 def run_gpu_batch(args, rank, world, local_rank):
@@ -633,8 +795,9 @@ def run_gpu_batch(args, rank, world, local_rank):
                                           tr[:, [0, 2]] if len(tr) else np.zeros((0, 2)), 100.0, 2.0))
     one_rs = one_steps / (one_ms * 1e-3) if one_ms > 0 else None
     if rank != 0:
-        return 0
+        return None
     achieved = (st["pairs"] / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
+    peak = ex2_peak(local_rank)["Texp_per_s"]
     line = {
         "metric": METRIC, "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -654,8 +817,9 @@ def run_gpu_batch(args, rank, world, local_rank):
                     "on every 4th scan of those runs, batch vs alone"},
         "per_run_latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "roofline": {"bound": "alu", "kernel": UPDATE_KERNELS,
-                     "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
-                     "frac": achieved / EX2_PEAK_TEXP, "traffic": None,
+                     "achieved": achieved, "peak": peak, "unit": "Texp/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured on this device: phd_measure_ex2_rate",
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                      "pairs_per_update": st["pairs"] / max(st["updates"], 1),
                      "pairs_evaluated_frac": st["pairs_evaluated"] / st["pairs"] if st["pairs"] else None},
@@ -664,8 +828,7 @@ def run_gpu_batch(args, rank, world, local_rank):
                    "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
                    "autotuned": not (args.no_autotune or args.tuning), "setup_s": round(t_tune, 3)},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_gpu_learned(args, rank, world, local_rank):
@@ -766,7 +929,7 @@ def run_gpu_learned(args, rank, world, local_rank):
         f.close()
     job_pairs, job_ms = job_totals(res["learned_J5000"]["pairs"], res["learned_J5000"]["ms"], world, dev)
     if rank != 0:
-        return 0
+        return None
     L, P4 = res["learned_J5000"], res["plain_J20000"]
     matched = L["ospa_mean"] <= 1.05 * P4["ospa_mean"]
     # the cheapest plain-birth variant whose OSPA is within 5 % of the learned one's
@@ -774,6 +937,7 @@ def run_gpu_learned(args, rank, world, local_rank):
     eq_best = max(eq, key=lambda k: res[k]["steps_per_s"]) if eq else None
     upd_s = L["update_ms_per_step"] * 1e-3
     achieved = (L["pairs"] / L["steps"]) / upd_s / 1e12 if upd_s > 0 else 0.0
+    peak = ex2_peak(local_rank)["Texp_per_s"]
     line = {
         "metric": METRIC, "value": job_pairs / (job_ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": L["steps"],
         "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -793,12 +957,12 @@ def run_gpu_learned(args, rank, world, local_rank):
         "training": {"pairs": int(X.shape[0]), "extracted_frac": float(T[:, 0].mean()), "adam_steps": 1500,
                      "loss": loss, "setup_s": round(t_train, 2)},
         "roofline": {"bound": "alu", "kernel": UPDATE_KERNELS,
-                     "achieved": achieved, "peak": EX2_PEAK_TEXP, "unit": "Texp/s",
-                     "frac": achieved / EX2_PEAK_TEXP, "traffic": None},
+                     "achieved": achieved, "peak": peak, "unit": "Texp/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured on this device: phd_measure_ex2_rate"},
         "gpu_launches": int(L["launches"]), "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p, extra=()):
@@ -874,7 +1038,7 @@ def run_gpu_compare(args, rank, world, local_rank):
     res = _three_way(args, wd, seeds, dev, rank, local_rank, 2.0, extra)
     job_pairs, job_ms = job_totals(res["DCPFPHD"]["pairs"], res["DCPFPHD"]["ms"], world, dev)
     if rank != 0:
-        return 0
+        return None
     D = res["DCPFPHD"]
     line = {
         "metric": METRIC, "value": job_pairs / (job_ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": D["steps"],
@@ -888,8 +1052,7 @@ def run_gpu_compare(args, rank, world, local_rank):
         "speedup_vs_PHD": {k: res[k]["steps_per_s"] / res["PHD"]["steps_per_s"] for k in res},
         "gpu_launches": int(D["launches"]),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_gpu_table1(args, rank, world, local_rank):
@@ -911,7 +1074,7 @@ def run_gpu_table1(args, rank, world, local_rank):
         table[str(int(lam))] = _three_way(args, wd, seeds, dev, rank, local_rank, 1.0)
     job_pairs, job_ms = job_totals(table["10"]["DCPFPHD"]["pairs"], table["10"]["DCPFPHD"]["ms"], world, dev)
     if rank != 0:
-        return 0
+        return None
     D = table["10"]["DCPFPHD"]
     line = {
         "metric": METRIC, "value": job_pairs / (job_ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": D["steps"],
@@ -928,8 +1091,7 @@ def run_gpu_table1(args, rank, world, local_rank):
                         for k, v in arms.items()} for lam, arms in table.items()},
         "gpu_launches": int(D["launches"]),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def _parse_tuning(text):
@@ -960,13 +1122,55 @@ def nvtx_pop():
         pass
 
 
+def _compact(line, keys):
+    return {k: line[k] for k in keys if k in line}
+
+
+def compact_one(line):
+    """Sub-block of a one-filter workload's line."""
+    out = _compact(line, ("value", "unit", "steps", "ms_per_step", "steps_per_s", "path", "ospa_mean", "gpu_launches"))
+    out["workload"] = line["config"]["workload"]
+    out["roofline"] = _compact(line["roofline"], ("frac", "achieved", "peak", "unit", "frac_evaluated",
+                                                  "kernel_ms_per_step", "pairs_per_update", "traffic"))
+    out["e2e"] = _compact(line["e2e"], ("value", "unit"))
+    out["run_mode"] = _compact(line["run_mode"], ("value", "ms_per_step"))
+    if line.get("matched_ospa"):
+        out["matched_ospa"] = _compact(line["matched_ospa"], ("matched", "oracle_timed_scans", "gpu_timed",
+                                                              "gpu_injected_timed_scans", "rel_injected",
+                                                              "rel_injected_from_steady", "rel_gpu_timed"))
+    out["clocks"] = _compact(line["clocks"], ("sm_mhz", "reasons"))
+    return out
+
+
+def compact_batch(line):
+    out = _compact(line, ("value", "unit", "steps", "ms_per_step", "run_steps_per_s", "per_run_latency_ms",
+                          "vs_one_filter_at_a_time", "gpu_launches"))
+    out["workload"] = line["config"]["workload"]
+    out["roofline"] = _compact(line["roofline"], ("frac", "achieved", "peak", "unit", "kernel_ms_per_step",
+                                                  "pairs_evaluated_frac"))
+    out["tuning"] = line.get("tuning")
+    out["clocks"] = _compact(line["clocks"], ("sm_mhz", "reasons"))
+    return out
+
+
+def compact_learned(line):
+    out = _compact(line, ("value", "unit", "steps", "ms_per_step", "steps_per_s", "learned_vs_plain_J20000",
+                          "at_equal_ospa", "gpu_launches"))
+    out["workload"] = line["config"]["workload"]
+    out["variants"] = {k: _compact(v, ("steps_per_s", "ospa_mean", "card_err_mean", "birth_count"))
+                       for k, v in line["variants"].items()}
+    out["training"] = _compact(line["training"], ("pairs", "loss", "adam_steps", "setup_s"))
+    out["roofline"] = _compact(line["roofline"], ("frac", "achieved", "peak", "unit"))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dist16_10t")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--runs", type=int, default=256, help="filters in the batched workload (batch256)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of the pair passes")
@@ -974,6 +1178,9 @@ def main():
                     help="time scans from this index of every run (earlier ones replayed untimed); "
                          "default 50 for dense_rb_100t, else 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subblocks", action="store_true",
+                    help="default workload only: leave out the 16-PE, batch and learned-birth sub-blocks")
+    ap.add_argument("--no-matched", action="store_true", help="skip the matched-OSPA run against the oracle record")
     ap.add_argument("--gate-sigma", type=float, default=0.0,
                     help="likelihood truncation beyond this many standard deviations (a variant that "
                          "changes results; 0 = the exact likelihood)")
@@ -982,80 +1189,53 @@ def main():
                          "e.g. c_tile=512,c_mb=4,r_pb=1,r_g=1,grid1=1216,grid2=608,gate=1,order=1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
-    if args.workload == "paper_table1" and args.impl == "ours":
-        world = _env_int("WORLD_SIZE", 1)
-        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            torch.cuda.set_device(local_rank)
-            dist.init_process_group(backend="nccl")
-        try:
-            return run_gpu_table1(args, rank, world, local_rank)
-        finally:
-            if world > 1:
-                import torch.distributed as dist
-                dist.destroy_process_group()
-    if args.workload == "dist16_compare" and args.impl == "ours":
-        world = _env_int("WORLD_SIZE", 1)
-        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            torch.cuda.set_device(local_rank)
-            dist.init_process_group(backend="nccl")
-        try:
-            return run_gpu_compare(args, rank, world, local_rank)
-        finally:
-            if world > 1:
-                import torch.distributed as dist
-                dist.destroy_process_group()
-    if args.workload == "rb_50t_learned" and args.impl == "ours":
-        world = _env_int("WORLD_SIZE", 1)
-        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            torch.cuda.set_device(local_rank)
-            dist.init_process_group(backend="nccl")
-        try:
-            return run_gpu_learned(args, rank, world, local_rank)
-        finally:
-            if world > 1:
-                import torch.distributed as dist
-                dist.destroy_process_group()
-    if args.workload == "batch256" and args.impl == "ours":
-        world = _env_int("WORLD_SIZE", 1)
-        rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            torch.cuda.set_device(local_rank)
-            dist.init_process_group(backend="nccl")
-        try:
-            return run_gpu_batch(args, rank, world, local_rank)
-        finally:
-            if world > 1:
-                import torch.distributed as dist
-                dist.destroy_process_group()
-    w = scenario.workload({"batch256": "linear4_fp64", "rb_50t_learned": "rb_50t",
-                           "dist16_compare": "dist16_10t"}.get(args.workload, args.workload))
-    if args.gate_sigma > 0:
-        w = w.with_(gate_sigma=args.gate_sigma)
     world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local_rank = _env_int("LOCAL_RANK", 0)
-    if world > 1:
-        import torch.distributed as dist
-        backend = "gloo" if args.impl == "reference" else "nccl"
-        if backend == "nccl":
-            import torch
-            torch.cuda.set_device(local_rank)
-        dist.init_process_group(backend=backend)
-    try:
-        if args.impl == "reference":
+    rank, local_rank = _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
+    special = {"paper_table1": run_gpu_table1, "dist16_compare": run_gpu_compare,
+               "rb_50t_learned": run_gpu_learned, "batch256": run_gpu_batch}
+    if args.impl == "reference":
+        w = scenario.workload({"batch256": "linear4_fp64", "rb_50t_learned": "rb_50t", "paper_table1": "paper_bot",
+                               "dist16_compare": "dist16_10t"}.get(args.workload, args.workload))
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend="gloo")
+        try:
             return run_reference(args, w, rank, world)
-        return run_gpu(args, w, rank, world, local_rank)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend="nccl")
+    try:
+        if args.workload in special:
+            line = special[args.workload](args, rank, world, local_rank)
+        else:
+            w = scenario.workload(args.workload)
+            if args.gate_sigma > 0:
+                w = w.with_(gate_sigma=args.gate_sigma)
+            line = run_gpu(args, w, rank, world, local_rank)
+            if args.workload == DEFAULT_WORKLOAD and not args.no_subblocks:
+                sub_args = argparse.Namespace(**{**vars(args), "steady_from": None, "tuning": None})
+                subs = {}
+                t0 = time.perf_counter()
+                l2 = run_gpu(sub_args, scenario.workload("dist16_10t"), rank, world, local_rank, sub=True)
+                lb = run_gpu_batch(sub_args, rank, world, local_rank)
+                ll = run_gpu_learned(sub_args, rank, world, local_rank)
+                if rank == 0:
+                    subs["dist16_10t"] = compact_one(l2)
+                    subs["batch256"] = compact_batch(lb)
+                    subs["rb_50t_learned"] = compact_learned(ll)
+                    line["subblocks"] = {**subs, "seconds": round(time.perf_counter() - t0, 1),
+                                         "note": "the 16-PE distributed workload, the 256-run batch and the "
+                                                 "learned birth proposal, each measured as its own --workload "
+                                                 "run measures it; compact"}
+        if rank == 0 and line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
     finally:
         if world > 1:
             import torch.distributed as dist

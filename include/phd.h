@@ -540,6 +540,21 @@ phd_status phd_autotune(phd_handle *h, int32_t reps, phd_tuning *out);
 phd_status phd_colsum_static(const phd_config *cfg, const void *d_x, const void *d_w, int32_t n,
                              const void *d_Z, int32_t M, double *d_C, void *stream);
 
+/* ---- roofline denominator ------------------------------------------------- */
+
+/* Measured issue rate of the ex2 instruction the pair passes evaluate once per
+ * particle x measurement pair (Eq. 7 and Eq. 8 each take g(z|x) through one
+ * FP32 exp2 of its exponent): a full-occupancy grid on the current device (8
+ * CTAs of 256 threads per SM), each thread running 8 independent chains of
+ * 4096 dependent ex2 instructions.  Times `reps` launches (1 .. 10000) with
+ * CUDA events on `stream` (a cudaStream_t or NULL) after one untimed launch
+ * and returns the fastest as *h_per_s (ex2 instructions per second, the
+ * whole device) and *h_best_ms (may be NULL).  The paper has no counterpart;
+ * this is the denominator the benchmark's roofline fraction uses.
+ * Synchronises.  Errors: PHD_ERR_INVALID_ARG for reps out of range or a NULL
+ * h_per_s; PHD_ERR_CUDA if a launch fails. */
+phd_status phd_measure_ex2_rate(int32_t reps, double *h_per_s, double *h_best_ms, void *stream);
+
 /* Wait for the stream and report a device-side error (non-finite input,
  * bounded-wait timeout) recorded since the last check.  Synchronises. */
 phd_status phd_sync(phd_handle *h);

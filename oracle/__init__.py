@@ -33,20 +33,60 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "phd_oracle.c"), os.path.join(_HERE, "birth_oracle.c")]
 _DEPS = _SRCS + [os.path.join(_HERE, "orc_model.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threads = 1
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's C sources into liboracle.so beside them (gcc, no CUDA)."""
-    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in _DEPS)
+def _build_one(path: str, extra, force: bool) -> str:
+    stale = not os.path.exists(path) or any(os.path.getmtime(path) < os.path.getmtime(p) for p in _DEPS)
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-I", _HERE, *_SRCS, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, *extra, "-I", _HERE, *_SRCS, "-o", tmp, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C sources into liboracle.so beside them (gcc, no
+    CUDA), and the same sources with OpenMP into liboracle_omp.so when the
+    compiler supports it (see set_threads)."""
+    _build_one(_LIB, [], force)
+    try:
+        _build_one(_LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB
+
+
+def openmp_available() -> bool:
+    try:
+        _build_one(_LIB_OMP, ["-fopenmp"], False)
+        return True
+    except (subprocess.CalledProcessError, OSError):
+        return False
+
+
+def set_threads(n: int) -> int:
+    """Run the oracle's stage loops on n host threads (the OpenMP build, whose
+    results are bit-identical to the single-threaded build's); n <= 1 selects
+    the single-threaded build.  Returns the thread count in effect."""
+    global _threads
+    n = int(n)
+    if n > 1 and openmp_available():
+        L = _load(_LIB_OMP)
+        L.orc_set_threads(n)
+        _threads = n
+    else:
+        _threads = 1
+    return _threads
+
+
+def threads() -> int:
+    return _threads
 
 
 class _Model(ctypes.Structure):
@@ -71,10 +111,20 @@ _M = ctypes.POINTER(_Model)
 
 
 def lib():
-    global _lib
+    """The oracle library in use: single-threaded unless set_threads(n > 1)."""
+    if _threads > 1:
+        return _load(_LIB_OMP)
+    if _LIB not in _libs:
+        build()
+    return _load(_LIB)
+
+
+def _load(path):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if path not in _libs:
+            L = ctypes.CDLL(path)
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_is_parallel.restype = ctypes.c_int
             L.orc_kappa.restype = ctypes.c_double
             L.orc_kappa.argtypes = [_M]
             L.orc_measure.argtypes = [_M, _D, _D]
@@ -109,8 +159,8 @@ def lib():
             L.orc_birth_learned.argtypes = [_M, _D, ctypes.c_int, _D, ctypes.c_double, ctypes.c_int,
                                             _D, _D, _D, _D, _I]
             L.orc_birth_cdf.argtypes = [_M, _D, ctypes.c_int, _D]
-            _lib = L
-    return _lib
+            _libs[path] = L
+    return _libs[path]
 
 
 def _d(a):
@@ -456,7 +506,7 @@ class OracleFilter:
 
 
 __all__ = [
-    "build", "lib", "model", "kappa", "measure", "likelihood", "predict", "colsum",
+    "build", "lib", "set_threads", "threads", "openmp_available", "model", "kappa", "measure", "likelihood", "predict", "colsum",
     "weight_update", "extract", "Extraction", "resample", "exchange_slots", "exchange",
     "fuse", "ospa", "OracleFilter",
 ]

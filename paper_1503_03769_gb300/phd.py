@@ -125,6 +125,8 @@ ABI = {
     "phd_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),
     "phd_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, _P]),
+    "phd_measure_ex2_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 _lib = None
@@ -233,6 +235,15 @@ def colsum_static(cfg: phd_config, x: torch.Tensor, w: torch.Tensor, Z: torch.Te
     return lib().phd_colsum_static(ctypes.byref(cfg), _ptr(x) if n else None, _ptr(w) if n else None, n,
                                    _ptr(Z) if M else None, M, _ptr(C) if M else None,
                                    ctypes.c_void_p(st.cuda_stream))
+
+
+def measure_ex2_rate(reps: int = 20, stream: Optional[torch.cuda.Stream] = None):
+    """phd_measure_ex2_rate: (ex2 instructions per second on the current
+    device, fastest launch in ms)."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().phd_measure_ex2_rate(int(reps), ctypes.byref(rate), ctypes.byref(ms), _stream_ptr(stream))
+    _check_status(st, "phd_measure_ex2_rate")
+    return rate.value, ms.value
 
 
 def _stream_ptr(stream: Optional[torch.cuda.Stream]):

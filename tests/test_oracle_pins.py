@@ -625,3 +625,31 @@ def test_ospa():
     assert oracle.ospa([[0.0, 0.0]], [[3.0, 4.0]]) == pytest.approx(5.0)
     assert oracle.ospa([[0.0, 0.0]], [[0.0, 0.0], [1000.0, 0.0]], 100.0, 2.0) == pytest.approx(
         math.sqrt(100.0 ** 2 / 2))
+
+
+def test_openmp_build_is_bit_identical():
+    """The OpenMP build of the oracle (used to time it on all host cores)
+    splits only loops whose iterations write their own outputs, so every
+    stage's result equals the single-threaded build's bit for bit."""
+    if not oracle.openmp_available():
+        pytest.skip("no OpenMP in this compiler")
+    for w in (RB, LIN):
+        m = oracle.model(w)
+        x, wt, Z = _cloud(w, 3000, 8, M=40)
+        if w is RB:
+            Z = _rb_meas(Z)
+        noise = scenario.step_noise(8, 0, 1, 3000 + 500)
+        out = {}
+        try:
+            for th in (1, 4):
+                oracle.set_threads(th)
+                C = oracle.colsum(m, x, wt, Z)
+                wu = oracle.weight_update(m, x, wt, Z, C)
+                ex = oracle.extract(m, x, wt, Z, C, wu.sum())
+                xp, wp = oracle.predict(m, x, wt, 500, noise)
+                out[th] = (C, wu, ex.labels, ex.zeta, ex.dW, xp, wp)
+        finally:
+            oracle.set_threads(1)
+        for a, b in zip(out[1], out[4]):
+            assert np.array_equal(a, b)
+        assert len(out[1][2]) > 0
