@@ -216,7 +216,8 @@ def oracle_run(w, seeds, max_steps, budget_s, skip=0, threads=1):
     timed steps after `skip`, on `threads` host threads (the oracle's OpenMP
     build, bit-identical to the single-threaded one)."""
     import oracle
-    oracle.set_threads(threads)
+    used = oracle.set_threads(threads)
+    oracle_run.threads_used = used
     pairs, secs, steps, ospas = 0, 0.0, 0, []
     done = 0
     try:
@@ -260,7 +261,7 @@ def cpu_baseline(w, seed, budget_s):
     pn, sn, nn, _ = oracle_run(w, [seed], n1, 10 ** 9, threads=nproc)
     import oracle
     info = cpu_info()
-    return {"value": pn / sn if sn > 0 else None, "unit": UNIT, "cores": oracle.threads() if nproc > 1 else 1,
+    return {"value": pn / sn if sn > 0 else None, "unit": UNIT, "cores": oracle_run.threads_used,
             "kind": "oracle",
             "sample": f"filter steps on scans 0..{n1 - 1} of {w.name} run {seed} ({p1:.3g} pairs; whole steps: "
                       f"predict, update, extraction, resampling), FP64 C oracle, OpenMP build on all host cores "
@@ -287,7 +288,7 @@ def run_reference(args, w, rank, world):
         "data": "synthetic", "config": workload_config(w, None, "n/a (CPU)"),
         "steps_per_s": steps / secs if secs > 0 else 0.0,
         "ospa_mean": float(np.mean(ospas)) if ospas else None,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc if oracle.openmp_available() else 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_run.threads_used,
                          "kind": "oracle", **cpu_info(),
                          "sample": f"{steps} whole filter steps of {w.name} (runs from seed {args.seed}, scans "
                                    f"from 0, after {args.warmup} untimed), FP64 C oracle on all host cores "

@@ -198,3 +198,158 @@ def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True, 
     g = gpu_stages(f, w, Z, noise, u, xu, path)
     check_step(w, m, Z, noise, u, xu, g, rep, check_resample)
     return g
+
+
+# ----------------------------------------------------------------------------
+# One step from generator inputs on both sides
+#
+# The oracle never sees a GPU intermediate here: both implementations start
+# from the same generator-made particle set and draws, and the oracle runs
+# its own chain (predict -> update -> extraction -> resampling).  The inputs
+# are dyadic (states on a 2^-8 m grid, normals on 2^-8, uniforms on 2^-12),
+# for which the CV prediction and the uniform birth are exact in FP32, so the
+# GPU's predicted set must equal the oracle's bit for bit and every later
+# stage of both sides starts from the same numbers.  Resampling is compared
+# by what is unique (the particle count, within the rounding of rho * N_k)
+# and by validity (each parent's offspring count is floor or ceil of
+# L w_i / W under the oracle's weights, to their tolerance; children are
+# gathered copies; new weights N_k / L).
+# ----------------------------------------------------------------------------
+
+def dyadic(a, frac_bits):
+    s = float(2 ** frac_bits)
+    return np.round(np.asarray(a, np.float64) * s) / s
+
+
+def exact_particles(rng, w, n, centres=None, spread=30.0, mass=1.0):
+    x, wt = scenario.random_particles(rng, w, n, centres=centres, spread=spread, mass=mass)
+    x = dyadic(x, 8)
+    x[:, [1, 3]] = np.clip(x[:, [1, 3]], -127.0, 127.0)
+    dt = npdtype(w)
+    return x.astype(dt), wt.astype(dt)
+
+
+def exact_noise(seed, step, K, pe_cap, dtype):
+    nz = scenario.step_noise(seed, step, K, pe_cap, np.float64)
+    nz[:, :2] = dyadic(np.clip(nz[:, :2], -7.99, 7.99), 8)
+    nz[:, 2:] = np.minimum(dyadic(nz[:, 2:], 12), 1.0 - 2.0 ** -12)
+    return nz.astype(dtype)
+
+
+def check_offspring(par, L, w_ref, what=""):
+    """Systematic resampling's unique property under the reference weights:
+    every parent's offspring count is floor or ceil of L w_i / W (slack for
+    the compared weights' tolerance); parents are non-decreasing."""
+    par = np.asarray(par[:L])
+    w_ref = np.asarray(w_ref, np.float64)
+    assert L == 0 or (np.all(np.diff(par) >= 0) and par[0] >= 0 and par[-1] < len(w_ref)), what
+    if L == 0:
+        return
+    o = np.bincount(par, minlength=len(w_ref))
+    xexp = L * w_ref / w_ref.sum()
+    lo = np.floor(xexp * (1 - 3e-4) - 1e-6)
+    hi = np.ceil(xexp * (1 + 3e-4) + 1e-6)
+    bad = (o < lo) | (o > hi)
+    assert not bad.any(), (what, int(bad.sum()), np.flatnonzero(bad)[:5], o[bad][:5], xexp[bad][:5])
+
+
+def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, exact_predict=True,
+                           check_resample=True):
+    """Compare one GPU step (gpu_stages output g) with the oracle's own chain
+    from the generator inputs x0, w0 (per PE) and the same draws."""
+    tol = tol_for(w)
+    K = w.num_pe
+    dt = npdtype(w)
+    kap = oracle.kappa(m)
+    Zd = np.asarray(Z, np.float64)
+    M = len(Zd)
+    nz = np.asarray(noise, np.float64).reshape(K, w.pe_cap, 4)
+    J = scenario.births_per_pe(w)
+    # --- predict (Eq. 5-6)
+    xo, wo = [], []
+    for j in range(K):
+        a, b = oracle.predict(m, np.asarray(x0[j], np.float64), np.asarray(w0[j], np.float64), J[j], nz[j])
+        xo.append(a)
+        wo.append(b)
+        assert len(g["xp"][j]) == len(a), ("predicted count", j)
+        if exact_predict:
+            assert np.array_equal(np.asarray(g["xp"][j], np.float64), a), ("predicted states", j)
+        else:
+            np.testing.assert_allclose(g["xp"][j], a, rtol=0, atol=1e-3 if dt == np.float32 else 1e-9)
+        check_weights(g["wp"][j], b, dict(w_rel=1e-6 if dt == np.float32 else 1e-14), f"predicted weights {j}")
+    # --- update (Eq. 7-8)
+    Cloc = [oracle.colsum(m, xo[j], wo[j], Zd) for j in range(K)]
+    Cu = [np.mean(np.stack(Cloc), axis=0)] * K if (w.ck_mode == "global" and M) else Cloc
+    wuo, Nko = [], []
+    for j in range(K):
+        if M:
+            err = np.abs(g["C"][j, :M] - Cloc[j])
+            big = Cloc[j] > 1e-3 * kap
+            if big.any():
+                rep.max_c_rel = max(rep.max_c_rel, float((err[big] / Cloc[j][big]).max()))
+            bad = err > tol["c_rel"] * Cloc[j] + 1e-7 * kap
+            assert not bad.any(), ("C", j, int(bad.sum()), err[bad][:3], Cloc[j][bad][:3])
+        a = oracle.weight_update(m, xo[j], wo[j], Zd, Cu[j])
+        wuo.append(a)
+        rep.max_w_rel = max(rep.max_w_rel, check_weights(g["wu"][j], a, tol, f"updated weights {j}"))
+        Nko.append(float(a.sum()))
+        if Nko[j] > 0:
+            rel = abs(g["mass"][j] - Nko[j]) / Nko[j]
+            rep.max_mass_rel = max(rep.max_mass_rel, rel)
+            assert rel <= tol["mass_rel"], ("mass", j, g["mass"][j], Nko[j])
+    # --- local estimation (Step 3, Eq. 10-18) and fusion (Step 4)
+    exs, ambiguous = [], False
+    for j in range(K):
+        ex = oracle.extract(m, xo[j], wo[j], Zd, Cu[j], Nko[j])
+        exs.append(ex)
+        got, want = list(g["loc_l"][j]), list(ex.labels)
+        if got != want:
+            dW = np.sort(ex.dW)[::-1]
+            lt = max(len(got), len(want))
+            Nk = Nko[j]
+            near_half = abs(Nk - math.floor(Nk) - 0.5) < 1e-5 * max(1.0, Nk)
+            near_tie = 0 < lt < len(dW) and abs(dW[lt - 1] - dW[lt]) <= 1e-6 * dW[lt - 1]
+            assert near_half or near_tie, ("labels", j, got, want, Nk)
+            rep.ambiguous_selection += 1
+            ambiguous = True
+        for r, p in enumerate(got):
+            if p in want:
+                e = np.abs(np.asarray(g["loc_s"][j][r], np.float64) - ex.zeta[want.index(p)]).max()
+                rep.max_state_err = max(rep.max_state_err, float(e))
+                assert e <= tol["state_abs"], ("state", j, p, g["loc_s"][j][r], ex.zeta[want.index(p)])
+                rep.compared_labels += 1
+    fl, fz = oracle.fuse(exs, M)
+    gl = list(np.asarray(g["labels"].cpu()))
+    if not ambiguous:
+        assert gl == list(fl), (gl, list(fl))
+        np.testing.assert_allclose(np.asarray(g["states"].cpu(), np.float64), fz, rtol=0,
+                                   atol=tol["state_abs"])
+    # --- resampling (Sec. 2.2 step 3; Step 5) and exchange (Step 6): by what
+    # is unique (counts) and validity (offspring, gather, weights, union)
+    if not check_resample:
+        return
+    par, lx, xr, wr = g["par"], g["lx"], g["xr"], g["wr"]
+    pre = []
+    for j in range(K):
+        L = len(xr[j])
+        lmax = w.pe_cap - J[j]
+        Lo = min(lmax, int(math.floor(w.particles_per_target / K * max(1.0, Nko[j]) + 0.5)))
+        Lg = min(lmax, int(math.floor(w.particles_per_target / K * max(1.0, float(g["mass"][j])) + 0.5)))
+        assert L == Lg and abs(L - Lo) <= 1, ("resample count", j, L, Lg, Lo)
+        check_offspring(par[j], L, wuo[j], f"PE {j}")
+        xg = np.asarray(g["xp"][j])[par[j][:L]]
+        pre.append(xg)
+        nw = float(g["mass"][j]) / L if L else 0.0
+        if L:
+            np.testing.assert_allclose(np.asarray(wr[j], np.float64), nw, rtol=1e-6 if dt == np.float32 else 1e-14)
+    if K > 1 and w.exchange_frac > 0:
+        moved = 0
+        for j in range(K):
+            moved += int((np.asarray(xr[j]) != pre[j]).any(axis=1).sum())
+        assert lx == int(math.floor(w.exchange_frac * min(len(a) for a in xr))) or lx == 0
+        assert moved <= K * lx
+        key = lambda arrs: np.sort(np.concatenate(arrs).view(np.dtype((np.void, np.dtype(dt).itemsize * 4))).ravel())
+        assert np.array_equal(key([np.ascontiguousarray(a) for a in xr]), key([np.ascontiguousarray(a) for a in pre]))
+    else:
+        for j in range(K):
+            assert np.array_equal(np.asarray(xr[j]), pre[j])

@@ -2,9 +2,10 @@
 device memory (fixed-memory real-time trackers, plug-ins inside a host
 application that owns every allocation).  Its scratch is the library's own
 file-scope device array, shared by every call, so the tests make two calls in
-a row through the C ABI and check each against the FP64 oracle's column sums
-and against the normaliser phd_update computes on the same particle set
-(within the C tolerance of the parity tests); they also cover the k-sigma
+a row through the C ABI and check each against the normaliser phd_update
+computes on the same particle set and, on the generator's particle set,
+against the FP64 oracle's column sums (within the C tolerance of the parity
+tests); they also cover the k-sigma
 truncation variant (between oracle brackets), an empty particle set, a scan
 with fewer measurements than a CTA has threads, and sizes beyond the array.
 This file is collected last on purpose."""
@@ -70,9 +71,11 @@ def test_colsum_static_matches_oracle_and_update_on_two_calls(wname, precision):
         assert st == phd.PHD_OK
         ref = C_upd[0, :len(Z)]
         assert np.all(np.abs(got - ref) <= rel * np.abs(ref) + kap), (call, np.abs(got - ref).max())
-        # the FP64 oracle on the same (rounded) inputs
-        Co = oracle.colsum(m, np.asarray(xp[0], np.float64), np.asarray(wp[0], np.float64),
-                           np.asarray(Z, np.float64))
+        # the FP64 oracle, both sides on the generator's particle set
+        xg, wg = x.astype(dt), wt.astype(dt)
+        st, got = _static(w, f.cfg, xg, wg, Z)
+        assert st == phd.PHD_OK
+        Co = oracle.colsum(m, xg.astype(np.float64), wg.astype(np.float64), np.asarray(Z, np.float64))
         assert np.all(np.abs(got - Co) <= rel * np.abs(Co) + kap), (call, np.abs(got - Co).max())
     f.close()
 
@@ -106,7 +109,7 @@ def test_colsum_static_empty_set_and_few_measurements():
     a CTA's threads, so each measurement's particles are split over many
     threads) matches the oracle; both twice in a row."""
     from paper_1503_03769_gb300 import phd
-    w = scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0)
+    w = scenario.workload("dist16_10t", num_pe=1, exchange_frac=0.0, birth_steps=(1,) * 10)
     cfg = phd.make_config(w)
     sc, x, wt = _particles(w, 13, 1777)
     x32, w32 = x.astype(np.float32), wt.astype(np.float32)
