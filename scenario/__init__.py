@@ -65,6 +65,8 @@ class Workload:
     birth_steps: Optional[tuple] = None     # explicit truth birth steps (1-based)
     steps: int = 50
     truth_vel_sigma: float = 20.0
+    truth_bounded: bool = False             # truth tracks reflect at the region boundary (the
+                                            # configured target count stays present) instead of leaving
     pe_cap: int = 0                         # particle slots per PE (0: derived)
     m_max: int = 0                          # measurement capacity (0: derived)
     sigma_a_y: float = 0.0                  # y-axis acceleration noise std (0: sigma_a)
@@ -107,25 +109,25 @@ def workload(name: str, **overrides) -> Workload:
             particles_per_target=500, birth_count=500, steps=50, precision="fp64"),
         # Paper's distributed scheme: 16 PEs, 10 % ring exchange, CU fusion.
         "dist16_10t": Workload(
-            name="dist16_10t", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+            name="dist16_10t", truth_bounded=True, meas_model=LINEAR, sigma_z=(10.0, 10.0),
             clutter_rate=50.0, n_targets=10, particles_per_target=1000,
             birth_count=1000, steps=100, num_pe=16, exchange_frac=0.1,
             precision="fp32"),
         # Dense scale, range-bearing sensor at the origin.
         "dense_rb_100t": Workload(
-            name="dense_rb_100t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
+            name="dense_rb_100t", truth_bounded=True, meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=500.0, n_targets=100, particles_per_target=2000,
             birth_count=20000, steps=100, precision="fp32"),
         # The dense workload's distributed form: 64 PEs.  A PE keeps rho/64 =
         # 31 particles per target it holds plus 312 births: 4096 slots cover
         # ~120 targets per PE, and a slice fits one SM's shared memory.
         "dense_rb_100t_pe64": Workload(
-            name="dense_rb_100t_pe64", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
+            name="dense_rb_100t_pe64", truth_bounded=True, meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=500.0, n_targets=100, particles_per_target=2000,
             birth_count=20000, steps=100, num_pe=64, exchange_frac=0.1, precision="fp32", pe_cap=4096),
         # Learned-birth evaluation scenario (range-bearing, 50 targets).
         "rb_50t": Workload(
-            name="rb_50t", meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
+            name="rb_50t", truth_bounded=True, meas_model=RANGE_BEARING, sigma_z=(5.0, 0.5 * DEG),
             clutter_rate=100.0, n_targets=50, particles_per_target=1000,
             birth_count=5000, steps=100, precision="fp32"),
         # The paper's own simulation shape (Sec. 4): bearing-range sensor with
@@ -168,7 +170,7 @@ def batch_workloads(seed: int = 1000, runs: int = 256, steps: int = 60) -> List[
         nt = int(rng.integers(1, 51))
         lam = float(rng.uniform(5.0, 200.0))
         rho = int(rng.integers(256, 4097))
-        wr = Workload(name=f"batch_run{r}", meas_model=LINEAR, sigma_z=(10.0, 10.0),
+        wr = Workload(name=f"batch_run{r}", meas_model=LINEAR, sigma_z=(10.0, 10.0), truth_bounded=True,
                       clutter_rate=lam, n_targets=nt, particles_per_target=rho,
                       birth_count=rho, steps=steps, precision="fp32")
         out.append(wr.with_(birth_mass=matched_birth_mass(wr)))
@@ -192,6 +194,18 @@ class Scenario:
     truth_ids: List[np.ndarray] = field(default_factory=list)
     meas: List[np.ndarray] = field(default_factory=list)    # per step: (M_k, 2) float32
     meas_is_target: List[np.ndarray] = field(default_factory=list)
+
+
+def _reflect(x: np.ndarray, region) -> np.ndarray:
+    """Specular reflection of truth tracks at the region boundary: a position
+    past an edge is mirrored back inside and that velocity component negated."""
+    out = x.copy()
+    for pc, vc, lo, hi in ((0, 1, region[0], region[1]), (2, 3, region[2], region[3])):
+        below, above = out[:, pc] < lo, out[:, pc] > hi
+        out[below, pc] = 2 * lo - out[below, pc]
+        out[above, pc] = 2 * hi - out[above, pc]
+        out[below | above, vc] = -out[below | above, vc]
+    return out
 
 
 def _cv_move(x: np.ndarray, dt: float, acc: np.ndarray) -> np.ndarray:
@@ -257,6 +271,8 @@ def simulate(w: Workload, seed: int, steps: Optional[int] = None) -> Scenario:
     for k in range(1, steps + 1):
         if len(live):
             live = _cv_move(live, w.dt, rng.standard_normal((len(live), 2)) * acc_std)
+            if w.truth_bounded:
+                live = _reflect(live, w.region)
             inside = ((live[:, 0] >= x0) & (live[:, 0] <= x1) &
                       (live[:, 2] >= y0) & (live[:, 2] <= y1))
             if w.meas_model == RANGE_BEARING and w.theta_span > 0:

@@ -1,12 +1,14 @@
 """Helpers for the GPU parity tests: stage-by-stage comparison of libphd.so
-against the FP64 oracle on the same injected random numbers.
+against the FP64 oracle on the same generator inputs and injected random
+numbers.
 
-At every stage the oracle is fed the GPU's own input state (the GPU's
-predicted set for the update, the GPU's updated weights for resampling), so
-each comparison isolates one stage; tolerances are the ones the filter is
+Both sides start every compared step from the same generator-made particle
+set, and the oracle runs its own chain through the step's stages; no oracle
+input is ever taken from the GPU.  Tolerances are the ones the filter is
 specified to: weights 1e-4 relative (plus a 1e-9 * mean-weight floor for
 weights that FP32's exp2 flushes to zero), masses 1e-5 relative, extracted
-states 1e-3 m, resampling parents and exchange moves bit-exact.
+states 1e-3 m; resampling by its count and offspring validity, the exchange
+bit-exact given the resampled slices.
 """
 from __future__ import annotations
 
@@ -90,113 +92,6 @@ def gpu_stages(f, w, Z, noise, u, xu, path):
         g["loc_s"], g["loc_l"] = f.get_local_estimates()
     g["par"], g["lx"] = f.get_resample()
     g["xr"], g["wr"] = f.get_state()
-    return g
-
-
-def check_step(w, m, Z, noise, u, xu, g, rep: StageReport, check_resample=True):
-    """Compare one step's GPU intermediates with the oracle, stage by stage,
-    the oracle always starting from the GPU's own input to that stage."""
-    tol = tol_for(w)
-    K = w.num_pe
-    dt = npdtype(w)
-    kap = oracle.kappa(m)
-    xs0, ws0, xp, wp, wu = g["xs0"], g["ws0"], g["xp"], g["wp"], g["wu"]
-    # --- predict (Eq. 5-6)
-    nz = np.asarray(noise, np.float64).reshape(K, w.pe_cap, 4)
-    for j in range(K):
-        Jj = scenario.births_per_pe(w)[j]
-        xo, wo = oracle.predict(m, xs0[j], ws0[j], Jj, nz[j])
-        assert len(xp[j]) == len(xo), ("predicted count", j, len(xs0[j]), Jj, len(xp[j]), len(xo))
-        # FP32 rounding of x + T vx + T^2/2 a: a few ulp of |x| <= 2e3 m
-        atol = 1e-3 if dt == np.float32 else 1e-9
-        np.testing.assert_allclose(xp[j], xo, rtol=0, atol=atol)
-        if len(xo):
-            rep.max_pred_abs = max(rep.max_pred_abs, float(np.abs(np.asarray(xp[j], np.float64) - xo).max()))
-        check_weights(wp[j], wo, tol, f"predict PE {j}")
-    # --- update (Eq. 7-8)
-    C, mass = g["C"], g["mass"]
-    M = len(Z)
-    Zd = np.asarray(Z, np.float64)
-    Cloc = [oracle.colsum(m, xp[j], wp[j], Zd) for j in range(K)]
-    if getattr(w, "ck_mode", "local") == "global" and M:
-        Cu = [np.mean(np.stack(Cloc), axis=0)] * K
-    else:
-        Cu = Cloc
-    for j in range(K):
-        if M:
-            # C matters to the filter through C / (kappa + C): an absolute slack of
-            # 1e-7 kappa per measurement moves the mass by at most 1e-7 per label
-            err = np.abs(C[j, :M] - Cloc[j])
-            big = Cloc[j] > 1e-3 * kap   # relative error where C is not negligible against kappa
-            if big.any():
-                rep.max_c_rel = max(rep.max_c_rel, float((err[big] / Cloc[j][big]).max()))
-            bad = err > tol["c_rel"] * Cloc[j] + 1e-7 * kap
-            assert not bad.any(), (j, int(bad.sum()), err[bad][:3], Cloc[j][bad][:3], kap)
-        wo = oracle.weight_update(m, xp[j], wp[j], Zd, Cu[j])
-        rep.max_w_rel = max(rep.max_w_rel, check_weights(wu[j], wo, tol, f"update PE {j}"))
-        Nref = wo.sum()
-        if Nref > 0:
-            rel = abs(mass[j] - Nref) / Nref
-            rep.max_mass_rel = max(rep.max_mass_rel, rel)
-            assert rel <= tol["mass_rel"], (j, mass[j], Nref)
-    # --- extraction (Eq. 10-18) and fusion (Step 4)
-    loc_s, loc_l = g["loc_s"], g["loc_l"]
-    for j in range(K):
-        Nk = float(wu[j].astype(np.float64).sum())
-        ex = oracle.extract(m, xp[j], wp[j], Zd, Cu[j], Nk)
-        got = list(loc_l[j])
-        want = list(ex.labels)
-        if got != want:
-            # acceptable only at a genuine tie: LT near a .5 boundary or the
-            # boundary dW values within 1e-6 relative
-            dW = np.sort(ex.dW)[::-1]
-            lt = max(len(got), len(want))
-            near_half = abs(Nk - math.floor(Nk) - 0.5) < 1e-5 * max(1.0, Nk)
-            near_tie = 0 < lt < len(dW) and abs(dW[lt - 1] - dW[lt]) <= 1e-6 * dW[lt - 1]
-            assert near_half or near_tie, (j, got, want, Nk)
-            rep.ambiguous_selection += 1
-        for r, p in enumerate(got):
-            if p in want:
-                zi = ex.zeta[want.index(p)]
-                e = np.abs(loc_s[j][r].astype(np.float64) - zi).max()
-                rep.max_state_err = max(rep.max_state_err, float(e))
-                assert e <= tol["state_abs"], (j, p, loc_s[j][r], zi)
-                rep.compared_labels += 1
-    # fusion of the GPU's own local estimates (identical inputs)
-    gl = [oracle.Extraction(np.asarray(loc_l[j], np.int32), np.asarray(loc_s[j], np.float64),
-                            np.zeros(M), 0.0, len(loc_l[j])) for j in range(K)]
-    fl, fz = oracle.fuse(gl, M)
-    assert list(g["labels"].cpu().numpy()) == list(fl), (g["labels"], fl)
-    np.testing.assert_allclose(g["states"].cpu().numpy().astype(np.float64), fz,
-                               rtol=0, atol=1e-4 if dt == np.float32 else 1e-9)
-    # --- resampling (exact CDF) + ring exchange
-    if not check_resample:
-        return
-    par, lx, xr, wr = g["par"], g["lx"], g["xr"], g["wr"]
-    rxs, rws = [], []
-    for j in range(K):
-        rho = w.particles_per_target / K
-        lmax = w.pe_cap - scenario.births_per_pe(w)[j]
-        xo, wo, po = oracle.resample(xp[j], wu[j].astype(np.float64), rho, lmax, int(u[j]))
-        assert np.array_equal(par[j, :len(po)], po), f"resample parents differ on PE {j}"
-        rxs.append(xo)
-        rws.append(wo)
-    if K > 1 and w.exchange_frac > 0:
-        # the exchange stage's input: the resampled slices and, for the
-        # adaptive trigger, the PE masses the GPU's update produced
-        rxs, rws, slots = oracle.exchange(rxs, rws, w.exchange_frac, xu, w.exchange_mode,
-                                          w.exchange_threshold, np.asarray(mass, np.float64)[:K])
-        assert lx == slots.shape[1]
-    for j in range(K):
-        assert len(xr[j]) == len(rxs[j])
-        np.testing.assert_array_equal(xr[j].astype(np.float64), rxs[j].astype(dt).astype(np.float64))
-        check_weights(wr[j], rws[j], tol, f"resampled weights PE {j}")
-
-
-def stage_step(f, w, m, Z, noise, u, xu, rep: StageReport, check_resample=True, path="staged"):
-    """One filter step on the GPU with every stage compared to the oracle."""
-    g = gpu_stages(f, w, Z, noise, u, xu, path)
-    check_step(w, m, Z, noise, u, xu, g, rep, check_resample)
     return g
 
 
@@ -329,13 +224,16 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
     if not check_resample:
         return
     par, lx, xr, wr = g["par"], g["lx"], g["xr"], g["wr"]
-    pre = []
+    pre, Lo_all = [], []
     for j in range(K):
         L = len(xr[j])
         lmax = w.pe_cap - J[j]
         Lo = min(lmax, int(math.floor(w.particles_per_target / K * max(1.0, Nko[j]) + 0.5)))
         Lg = min(lmax, int(math.floor(w.particles_per_target / K * max(1.0, float(g["mass"][j])) + 0.5)))
         assert L == Lg and abs(L - Lo) <= 1, ("resample count", j, L, Lg, Lo)
+        Lo_all.append(Lo)
+        if L != Lo:
+            rep.notes.append(f"PE {j}: rho N_k within rounding of a .5 boundary ({L} vs {Lo})")
         check_offspring(par[j], L, wuo[j], f"PE {j}")
         xg = np.asarray(g["xp"][j])[par[j][:L]]
         pre.append(xg)
@@ -343,13 +241,65 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
         if L:
             np.testing.assert_allclose(np.asarray(wr[j], np.float64), nw, rtol=1e-6 if dt == np.float32 else 1e-14)
     if K > 1 and w.exchange_frac > 0:
-        moved = 0
+        # Step 6: the count and the trigger from the oracle's own masses and
+        # counts, the slots from the oracle's slot function on the injected
+        # draws; PE j's t-th chosen particle lands in the receiver's t-th slot
+        counts = Lo_all
+        if [len(a) for a in xr] != counts:
+            # a count at a rounding boundary: the exchange is checked by its
+            # invariants (slice sizes, the union of all particles)
+            key = lambda arrs: np.sort(np.concatenate(arrs).view(
+                np.dtype((np.void, np.dtype(dt).itemsize * 4))).ravel())
+            assert np.array_equal(key([np.ascontiguousarray(a) for a in xr]),
+                                  key([np.ascontiguousarray(a) for a in pre]))
+            return
+        due = True
+        if w.exchange_threshold > 0:
+            mn, mean = min(Nko), sum(Nko) / K
+            near = abs(mn - w.exchange_threshold * mean) <= 1e-4 * max(mean, 1e-300)
+            due = mn < w.exchange_threshold * mean
+            if near:
+                due = lx > 0
+        Lx = int(math.floor(w.exchange_frac * min(counts))) if due else 0
+        assert lx == Lx, ("exchange count", lx, Lx)
+        slots = [oracle.exchange_slots(counts[j], Lx, np.asarray(xu, np.uint32).reshape(K, -1)[j]) for j in range(K)]
+        want = [np.array(a, copy=True) for a in pre]
         for j in range(K):
-            moved += int((np.asarray(xr[j]) != pre[j]).any(axis=1).sum())
-        assert lx == int(math.floor(w.exchange_frac * min(len(a) for a in xr))) or lx == 0
-        assert moved <= K * lx
-        key = lambda arrs: np.sort(np.concatenate(arrs).view(np.dtype((np.void, np.dtype(dt).itemsize * 4))).ravel())
-        assert np.array_equal(key([np.ascontiguousarray(a) for a in xr]), key([np.ascontiguousarray(a) for a in pre]))
+            for t in range(Lx):
+                shift = 1 + t % (K - 1) if (w.exchange_mode == "all" and K > 2) else 1
+                k = (j + shift) % K
+                want[k][slots[k][t]] = pre[j][slots[j][t]]
+        for j in range(K):
+            assert np.array_equal(np.asarray(xr[j]), want[j]), ("exchange", j)
     else:
         for j in range(K):
             assert np.array_equal(np.asarray(xr[j]), pre[j])
+
+
+def exact_state(w, seed, n_per_pe, centres=None, spread=25.0, mass=3.0, resampled=False):
+    """Generator particle slices for K PEs (dyadic, see exact_particles); with
+    `resampled` each slice looks like a resampling output: equal weights and
+    runs of duplicated states."""
+    rng = np.random.default_rng(seed)
+    xs, ws = [], []
+    for j in range(w.num_pe):
+        n = n_per_pe[j] if isinstance(n_per_pe, (list, tuple)) else n_per_pe
+        x, wt = exact_particles(rng, w, n, centres=centres, spread=spread, mass=mass)
+        if resampled and n > 1:
+            src = np.sort(rng.integers(0, max(1, n // 3), size=n))
+            x = x[src]
+            wt = np.full(n, mass / n, dtype=wt.dtype)
+        xs.append(x)
+        ws.append(wt)
+    return xs, ws
+
+
+def stage_step(f, w, m, x0, w0, Z, noise, u, xu, rep: StageReport, path="staged", exact_predict=True,
+               check_resample=True):
+    """Load the generator state (x0, w0) into the GPU filter, run one step with
+    the injected draws, and compare every stage with the oracle's own chain
+    from the same state."""
+    f.set_state(x0, w0)
+    g = gpu_stages(f, w, Z, noise, u, xu, path)
+    check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep, exact_predict, check_resample)
+    return g

@@ -3,15 +3,15 @@
 Five runs with different clutter rates, birth counts, particles per target
 and measurement capacities, uneven particle sets, stepped together; every
 run is checked stage by stage against the FP64 oracle of its own
-configuration (the same harness as the one-filter tests), on injected random
-numbers."""
+configuration (the harness of the one-filter tests: both sides from the same
+generator slices), on injected random numbers."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import scenario
-from gpu_harness import StageReport, check_step, npdtype
+from gpu_harness import StageReport, check_step_from_inputs, exact_noise, exact_state
 
 pytestmark = pytest.mark.gpu
 
@@ -31,28 +31,28 @@ def _runs():
 
 @pytest.mark.parametrize("autotune", [False, True])
 def test_batch_runs_match_their_oracles(autotune):
-    """With autotune, the pair passes' launch shape is re-chosen after the
-    first step (timed on the batch's own slices) and the runs stay on their
-    oracles."""
+    """Three batched steps, each from generator slices (every run's own size;
+    the second shaped like a resampling output); with autotune, the pair
+    passes' launch shape is re-chosen after the first step (timed on the
+    batch's own slices) and the runs stay on their oracles."""
     from paper_1503_03769_gb300 import ParticlePHDBatch
     ws = _runs()
     R = len(ws)
     b = ParticlePHDBatch(ws, seed=2)
-    rng = np.random.default_rng(2)
     scs = [scenario.simulate(w, 40 + j, steps=3) for j, w in enumerate(ws)]
-    xs, wts = [], []
-    for j, w in enumerate(ws):
-        cen = np.concatenate([t[:, [0, 2]] for t in scs[j].truth if len(t)])
-        x, wt = scenario.random_particles(rng, w, 700 + 333 * j, centres=cen, spread=25.0, mass=2.0 + j)
-        xs.append(x.astype(np.float32))
-        wts.append(wt.astype(np.float32))
-    b.set_state(xs, wts)
     rep = StageReport()
     for k in range(3):
+        xs, wts = [], []
+        for j, w in enumerate(ws):
+            cen = np.concatenate([t[:, [0, 2]] for t in scs[j].truth if len(t)])
+            x, wt = exact_state(w, 100 * k + j, [700 + 333 * j], centres=cen, mass=2.0 + j,
+                                resampled=(k == 1))
+            xs.append(x[0])
+            wts.append(wt[0])
+        b.set_state(xs, wts)
         Zs = [scs[j].meas[k] for j in range(R)]
-        noise = scenario.step_noise(9, k, R, b.pe_cap, np.float32)
+        noise = exact_noise(9, k, R, b.pe_cap, np.float32)
         u = scenario.resample_u32(9, k, R)
-        pre_x, pre_w = b.get_state()
         outs = b.batch_step(Zs, noise=noise, u=u)
         xp, wp, wu = b.get_predicted()
         C, mass = b.get_update()
@@ -61,11 +61,10 @@ def test_batch_runs_match_their_oracles(autotune):
         xr, wr = b.get_state()
         nz = np.asarray(noise).reshape(R, b.pe_cap, 4)
         for j, w in enumerate(ws):
-            g = dict(xs0=[pre_x[j]], ws0=[pre_w[j]], xp=[xp[j]], wp=[wp[j]], wu=[wu[j]],
-                     C=C[j:j + 1], mass=mass[j:j + 1], loc_s=[loc_s[j]], loc_l=[loc_l[j]],
-                     states=outs[j][0], labels=outs[j][1], par=par[j:j + 1], lx=0,
+            g = dict(xp=[xp[j]], wp=[wp[j]], wu=[wu[j]], C=C[j:j + 1], mass=mass[j:j + 1], loc_s=[loc_s[j]],
+                     loc_l=[loc_l[j]], states=outs[j][0], labels=outs[j][1], par=par[j:j + 1], lx=0,
                      xr=[xr[j]], wr=[wr[j]])
-            check_step(w, oracle.model(w), Zs[j], nz[j], u[j:j + 1], None, g, rep)
+            check_step_from_inputs(w, oracle.model(w), [xs[j]], [wts[j]], Zs[j], nz[j], u[j:j + 1], None, g, rep)
         if autotune and k == 0:
             t = b.autotune(2)
             assert t["pass1_us"] > 0 and t["pass2_us"] > 0

@@ -50,7 +50,7 @@ def _dense_inputs():
 def test_dense_full_size_step(shape):
     from paper_1503_03769_gb300 import ParticlePHD
     w, Z, x, wt, noise, u = _dense_inputs()
-    assert len(Z) > 550 and len(x) > 1.8e5
+    assert len(Z) > 450 and len(x) > 1.5e5
     f = ParticlePHD(w, seed=3, device="cuda:0")
     assert f.get_path() == "staged"
     if shape == "autotuned":

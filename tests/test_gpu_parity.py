@@ -1,11 +1,15 @@
 """GPU parity: libphd.so (through its C ABI) against the FP64 oracle.
 
-Every test injects the same random numbers into both sides and compares
-stage by stage (see gpu_harness.stage_step): predict and update elementwise,
-extraction per PE and after fusion, resampling parents and the ring exchange
-bit-exactly.  Sizes span several 256-particle tiles with ragged tails, PEs
-with unequal counts, M below and above the 256-thread measurement rounds,
-both sensors, both precisions and both normaliser modes.
+Every compared step starts both sides from the same generator-made particle
+set (dyadic values, so FP32 prediction is exact; see gpu_harness) with the
+same injected random numbers, and the oracle runs its own chain through the
+stages: predict and update elementwise, extraction per PE and after fusion,
+resampling by count and offspring validity, the ring exchange bit-exactly
+given the resampled slices.  Sizes span several 256-particle tiles with
+ragged tails, PEs with unequal counts, M below and above the 256-thread
+measurement rounds, both sensors, both precisions and both normaliser modes;
+every other compared step starts from a set shaped like a resampling output
+(equal weights, duplicated states).
 """
 import math
 import os
@@ -16,7 +20,7 @@ import torch
 
 import oracle
 import scenario
-from gpu_harness import StageReport, stage_step, check_weights, npdtype
+from gpu_harness import StageReport, stage_step, check_weights, npdtype, exact_noise, exact_state
 
 pytestmark = pytest.mark.gpu
 
@@ -28,33 +32,30 @@ def _filter(w, seed=0, path="staged"):
     return f
 
 
-def _seed_state(f, w, seed, n_per_pe, centres=None, mass=3.0):
-    rng = np.random.default_rng(seed)
-    xs, ws = [], []
-    for j in range(w.num_pe):
-        n = n_per_pe[j] if isinstance(n_per_pe, (list, tuple)) else n_per_pe
-        x, wt = scenario.random_particles(rng, w, n, centres=centres, spread=25.0, mass=mass)
-        dt = npdtype(w)
-        xs.append(x.astype(dt))
-        ws.append(wt.astype(dt))
-    f.set_state(xs, ws)
-
-
 def _run_stages(w, seed, steps, sc=None, warm=0, n_seed=None, centres=None, path="staged"):
+    """`steps` compared steps on scans warm .. warm + steps - 1; each starts
+    both sides from a generator state around that scan's truth (or around
+    `centres`) with n_seed particles per PE (default: rho / K per live
+    target)."""
     f = _filter(w, seed, path)
     m = oracle.model(w)
     if sc is None:
         sc = scenario.simulate(w, seed, steps=warm + steps)
-    if n_seed is not None:
-        _seed_state(f, w, seed, n_seed, centres=centres)
-    for k in range(warm):
-        f.step(sc.meas[k])
+    exact = w.birth_model != "gaussian" or w.precision == "fp64"
     rep = StageReport()
-    for k in range(warm, warm + steps):
-        noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap, npdtype(w))
-        u = scenario.resample_u32(seed, k, w.num_pe)
-        xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap)
-        stage_step(f, w, m, sc.meas[k], noise, u, xu, rep, path=path)
+    K = w.num_pe
+    for s in range(steps):
+        k = warm + s
+        tr = sc.truth[k]
+        cen = centres if centres is not None else (tr[:, [0, 2]] if len(tr) else None)
+        counts = n_seed if n_seed is not None else \
+            int(round(w.particles_per_target / K * max(1, len(tr))))
+        x0, w0 = exact_state(w, 1000 * seed + s, counts, centres=cen, mass=float(max(1, len(tr))),
+                             resampled=(s % 2 == 1))
+        noise = exact_noise(seed, k, K, w.pe_cap, npdtype(w))
+        u = scenario.resample_u32(seed, k, K)
+        xu = scenario.exchange_u32(seed, k, K, w.pe_cap)
+        stage_step(f, w, m, x0, w0, sc.meas[k], noise, u, xu, rep, path=path, exact_predict=exact)
     f.close()
     _log_errors(w, path, rep)
     return rep
@@ -210,12 +211,11 @@ def test_bearing_branch_cut():
     r = 800 + 5 * rng.standard_normal(n)
     x = np.stack([r * np.cos(th), np.zeros(n), r * np.sin(th), np.zeros(n)], 1).astype(np.float32)
     wt = np.full(n, 1.0 / n, np.float32)
-    f.set_state([x], [wt])
     Z = np.array([[800.0, math.pi - 0.002], [800.0, -math.pi + 0.003], [810.0, 3.1]], np.float32)
     noise = np.zeros((w.pe_cap, 4), np.float32)
     noise[:, 2:] = 0.5
     rep = StageReport()
-    stage_step(f, w, m, Z, noise, np.array([12345], np.uint32), None, rep)
+    stage_step(f, w, m, [x], [wt], Z, noise, np.array([12345], np.uint32), None, rep)
     assert rep.compared_labels >= 1
 
 
@@ -242,10 +242,12 @@ def test_resample_bit_exact_on_injected_weights(precision):
             f.resample(np.array([U], np.uint32))
             par, _ = f.get_resample()
             xr, wr = f.get_state()
-            xo, wo, po = oracle.resample(xp[0].astype(np.float64), wt.astype(np.float64),
-                                         w.particles_per_target, w.pe_cap, U)
+            x_or, _ = oracle.predict(oracle.model(w), x.astype(np.float64), wt.astype(np.float64), 0,
+                                     np.zeros((n, 4)))
+            xo, wo, po = oracle.resample(x_or, wt.astype(np.float64), w.particles_per_target, w.pe_cap, U)
             assert np.array_equal(par[0, :len(po)], po), (n, U)
-            np.testing.assert_array_equal(xr[0].astype(np.float64), xo)
+            np.testing.assert_allclose(xr[0].astype(np.float64), xo, rtol=0,
+                                       atol=1e-14 if dt == np.float64 else 2e-6)
             check_weights(wr[0], wo, dict(w_rel=1e-15 if dt == np.float64 else 1e-7), "new weights")
         f.close()
 
@@ -281,99 +283,48 @@ def test_free_running_fp64_matches_oracle_over_many_steps():
 def test_published_distributed_workload_sizes(path):
     """The 16-PE workload at its published sizes (10 targets, lambda = 50,
     1000 particles per target, 1000 births) in the launch configuration the
-    benchmark times: stage parity after a free-running warm-up on the GPU's
-    own random numbers."""
+    benchmark times: stage parity on scans 12 and 13 (all ten targets live),
+    from generator slices of rho / K particles per target."""
     w = scenario.workload("dist16_10t")
     rep = _run_stages(w, 2, 2, warm=12, path=path)
     assert rep.max_mass_rel <= 1e-5
 
 
-def test_dense_workload_sampled():
-    """The dense range-bearing workload at full size (~2.2e5 particles, ~600
-    measurements): C on a sample of measurements and the updated weights on a
-    sample of particles against the oracle; the mass closed form of Eq. 8 at
-    full size."""
-    w = scenario.workload("dense_rb_100t")
-    sc = scenario.simulate(w, 3, steps=1)
-    f = _filter(w, 3)
-    rng = np.random.default_rng(3)
-    centres = sc.truth[0][:, [0, 2]]
-    n = 200_000
-    x, wt = scenario.random_particles(rng, w, n, centres=centres, spread=20.0, mass=100.0)
-    f.set_state([x.astype(np.float32)], [wt.astype(np.float32)])
-    m = oracle.model(w)
-    noise = scenario.step_noise(3, 0, 1, w.pe_cap, np.float32)
-    f.predict(torch.as_tensor(noise).cuda())
-    xp, wp = f.get_state()
-    Z = sc.meas[0]
-    M = len(Z)
-    assert M > 450
-    f.update(torch.as_tensor(Z).cuda())
-    C, mass = f.get_update()
-    xu_, wu = f.get_state()
-    sel_p = rng.choice(M, 24, replace=False)
-    Co = oracle.colsum(m, xp[0], wp[0], Z[sel_p].astype(np.float64))
-    kap = oracle.kappa(m)
-    assert np.all(np.abs(C[0, sel_p] - Co) <= 1e-5 * Co + 1e-9 * kap)
-    sel_i = rng.choice(len(xp[0]), 3000, replace=False)
-    wo = oracle.weight_update(m, xp[0][sel_i], wp[0][sel_i], Z.astype(np.float64), C[0, :M])
-    check_weights(wu[0][sel_i], wo, dict(w_rel=1e-4), "sampled weights")
-    ref = (1 - w.p_d) * wp[0].astype(np.float64).sum() + np.sum(C[0, :M] / (kap + C[0, :M]))
-    assert abs(mass[0] - ref) <= 1e-5 * ref
-    f.close()
-
-
 @pytest.mark.parametrize("path", ["staged", "fused"])
-def test_dense_workload_64_pes_sampled(path):
-    """The dense workload's 64-PE distributed form (config 3) at full size
-    (staged path autotuned; fused path: one CTA per PE, as the benchmark runs
-    it): after 20 free-running scans, one step with injected noise is checked
-    per PE on samples (C of 12 measurements and the updated weights of 400
-    particles on 6 PEs), the Eq. 8 mass closed form on every PE, and the CU
-    fusion of the GPU's own local estimates."""
+def test_dense_workload_64_pes_full_size(path):
+    """The dense workload's 64-PE distributed form (config 3) at full size:
+    64 generator slices of rho / 64 particles per live target (~3.1e3 each,
+    ~2.2e5 in all) against ~600 measurements, one step in the launch
+    configuration the benchmark times (staged path autotuned on these
+    slices; fused path one CTA per PE), every stage of every PE against the
+    oracle (which runs on all host cores)."""
     w = scenario.workload("dense_rb_100t_pe64")
-    sc = scenario.simulate(w, 6, steps=21)
+    sc = scenario.simulate(w, 6, steps=61)
+    tr = sc.truth[60]
+    Z = sc.meas[60]
+    counts = int(round(w.particles_per_target / w.num_pe * len(tr)))
+    x0, w0 = exact_state(w, 66, counts, centres=tr[:, [0, 2]], mass=float(len(tr)))
+    noise = exact_noise(6, 60, w.num_pe, w.pe_cap, np.float32)
+    u = scenario.resample_u32(6, 60, w.num_pe)
+    xu = scenario.exchange_u32(6, 60, w.num_pe, w.pe_cap)
+    assert len(Z) > 450 and counts * w.num_pe > 1.5e5
     f = _filter(w, 6, path)
-    m = oracle.model(w)
-    kap = oracle.kappa(m)
-    for k in range(20):
-        f.step(sc.meas[k])
-    noise = scenario.step_noise(6, 20, w.num_pe, w.pe_cap, np.float32)
-    Z = sc.meas[20]
-    M = len(Z)
     if path == "staged":
-        f.autotune(2)
+        f.set_state(x0, w0)
         f.predict(torch.as_tensor(noise).cuda())
-        xp, wp = f.get_state()
         f.update(torch.as_tensor(Z).cuda())
-        _, wu = f.get_state()
-    else:
-        states, labels = f.step_inject(np.asarray(Z, np.float32), noise, scenario.resample_u32(6, 20, 64),
-                                       scenario.exchange_u32(6, 20, 64, w.pe_cap))
-        xp, wp, wu = f.get_predicted()
-    C, mass = f.get_update()
-    # each PE keeps rho / 64 ~ 31 particles per target it believes in: ~2.8e4 here
-    assert M > 450 and sum(len(a) for a in xp) > 20_000
-    rng = np.random.default_rng(6)
-    for j in rng.choice(64, 6, replace=False):
-        sel_p = rng.choice(M, 12, replace=False)
-        Co = oracle.colsum(m, xp[j], wp[j], Z[sel_p].astype(np.float64))
-        assert np.all(np.abs(C[j, sel_p] - Co) <= 1e-4 * Co + 1e-7 * kap), j
-        sel_i = rng.choice(len(xp[j]), min(400, len(xp[j])), replace=False)
-        wo = oracle.weight_update(m, xp[j][sel_i], wp[j][sel_i], Z.astype(np.float64), C[j, :M])
-        check_weights(wu[j][sel_i], wo, dict(w_rel=1e-4), f"sampled weights PE {j}")
-    for j in range(64):
-        ref = (1 - w.p_d) * wp[j].astype(np.float64).sum() + np.sum(C[j, :M] / (kap + C[j, :M]))
-        assert abs(mass[j] - ref) <= 1e-5 * max(ref, 1e-12), j
-    if path == "staged":
-        states, labels = f.extract()
-    loc_s, loc_l = f.get_local_estimates()
-    per_pe = [oracle.Extraction(np.asarray(loc_l[j], np.int32), np.asarray(loc_s[j], np.float64), np.zeros(M), 0.0,
-                                len(loc_l[j])) for j in range(64)]
-    fl, fz = oracle.fuse(per_pe, M)
-    assert list(labels.cpu().numpy()) == list(fl)
-    np.testing.assert_allclose(states.cpu().numpy().astype(np.float64), fz, rtol=0, atol=1e-3)
+        f.autotune(2)
+        f.extract()
+        f.resample(u, xu)
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        rep = StageReport()
+        stage_step(f, w, oracle.model(w), x0, w0, Z, noise, u, xu, rep, path=path)
+    finally:
+        oracle.set_threads(1)
     f.close()
+    _log_errors(w, path, rep)
+    assert rep.compared_labels > 100
 
 
 def test_barrier_timeout_is_reported_and_recoverable():

@@ -6,7 +6,8 @@ and dropped on the other, so the oracle brackets the GPU: with the radius
 shrunk and grown by 1e-5 relative (far wider than FP32's error on the
 exponent, ~1e-7) it gives a lower and an upper bound for every column sum
 C_p and every updated weight, and the GPU must lie between them (to the
-usual FP32 tolerance).  Staged passes and the fused step kernel, both
+usual FP32 tolerance).  Both sides start from the same generator slices
+(dyadic, so the GPU's prediction equals the oracle's exactly).  Staged passes and the fused step kernel, both
 sensors."""
 import numpy as np
 import pytest
@@ -14,6 +15,7 @@ import torch
 
 import oracle
 import scenario
+from gpu_harness import exact_noise, exact_state
 
 pytestmark = pytest.mark.gpu
 
@@ -40,17 +42,12 @@ def test_truncated_update_between_oracle_brackets(case, path):
     w, seed = _case(case)
     sc = scenario.simulate(w, seed, steps=1)
     Z = np.asarray(sc.meas[0], np.float32)
-    rng = np.random.default_rng(seed)
     centres = sc.truth[0][:, [0, 2]]
-    xs, ws = [], []
-    for j in range(w.num_pe):
-        x, wt = scenario.random_particles(rng, w, 700 + 90 * j, centres=centres, spread=25.0, mass=3.0)
-        xs.append(x.astype(np.float32))
-        ws.append(wt.astype(np.float32))
+    xs, ws = exact_state(w, seed, [700 + 90 * j for j in range(w.num_pe)], centres=centres)
     f = ParticlePHD(w, seed=seed, device="cuda:0")
     f.set_path(path)
     f.set_state(xs, ws)
-    noise = scenario.step_noise(seed, 0, w.num_pe, w.pe_cap, np.float32)
+    noise = exact_noise(seed, 0, w.num_pe, w.pe_cap, np.float32)
     if path == "staged":
         f.predict(torch.as_tensor(noise).cuda())
         xp, wp = f.get_state()
@@ -69,16 +66,24 @@ def test_truncated_update_between_oracle_brackets(case, path):
     Zd = Z.astype(np.float64)
     M = len(Z)
     bites = 0.0
+    nz = noise.astype(np.float64).reshape(w.num_pe, w.pe_cap, 4)
+    J = scenario.births_per_pe(w)
     for j in range(w.num_pe):
-        c_lo = oracle.colsum(lo, xp[j], wp[j], Zd)
-        c_hi = oracle.colsum(hi, xp[j], wp[j], Zd)
-        c_full = oracle.colsum(full, xp[j], wp[j], Zd)
+        # the oracle's own prediction of the same generator slice (exact in FP32)
+        xo, wo = oracle.predict(full, xs[j].astype(np.float64), ws[j].astype(np.float64), J[j], nz[j])
+        assert np.array_equal(np.asarray(xp[j], np.float64), xo), j
+        c_lo = oracle.colsum(lo, xo, wo, Zd)
+        c_hi = oracle.colsum(hi, xo, wo, Zd)
+        c_full = oracle.colsum(full, xo, wo, Zd)
         Cg = C[j, :M]
         assert np.all(Cg >= c_lo * (1 - 1e-4) - 1e-7 * kap), j
         assert np.all(Cg <= c_hi * (1 + 1e-4) + 1e-7 * kap), j
         bites = max(bites, float(np.max((c_full - c_hi) / np.maximum(c_full, 1e-300))))
-        w_lo = oracle.weight_update(lo, xp[j], wp[j], Zd, Cg)
-        w_hi = oracle.weight_update(hi, xp[j], wp[j], Zd, Cg)
+        # Eq. 8 grows with every g and shrinks with every C: the narrow
+        # likelihood over the wide normaliser bounds the weights from below,
+        # the wide over the narrow from above
+        w_lo = oracle.weight_update(lo, xo, wo, Zd, c_hi)
+        w_hi = oracle.weight_update(hi, xo, wo, Zd, c_lo)
         floor = 1e-9 * max(w_hi.sum(), 1e-300) / max(len(w_hi), 1)
         g = np.asarray(wu[j], np.float64)
         assert np.all(g >= w_lo * (1 - 1e-4) - floor), j

@@ -2,7 +2,7 @@
 sums, Eq. 8 row sums), and of the autotuner that picks among them.
 
 Each shape is checked stage by stage against the FP64 oracle (the harness of
-the one-filter tests) on a configuration whose slices span several work
+the one-filter tests: both sides from the same generator state) on a configuration whose slices span several work
 items with ragged tails and whose measurement count crosses the pass-1 chunk
 of every shape, with CTA caps small enough that every CTA walks several work
 items (and restages particles and measurements between slices)."""
@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import scenario
-from gpu_harness import StageReport, stage_step, npdtype
+from gpu_harness import StageReport, exact_noise, exact_state, npdtype, stage_step
 
 pytestmark = pytest.mark.gpu
 
@@ -25,21 +25,21 @@ def _filter(w, seed, counts, centres, **shape):
     f.set_path("staged")
     if shape:
         f.set_tuning(**shape)
-    rng = np.random.default_rng(seed)
-    xs, ws = [], []
-    for j in range(w.num_pe):
-        x, wt = scenario.random_particles(rng, w, counts[j], centres=centres, spread=25.0, mass=3.0)
-        xs.append(x.astype(npdtype(w)))
-        ws.append(wt.astype(npdtype(w)))
+    f.gen = (seed, counts, centres)
+    xs, ws = exact_state(w, seed, counts, centres=centres)
     f.set_state(xs, ws)
     return f
 
 
 def _step(f, w, sc, seed, k, rep):
-    noise = scenario.step_noise(seed, k, w.num_pe, w.pe_cap, npdtype(w))
+    """One step from a generator state (every other one shaped like a
+    resampling output), compared stage by stage with the oracle's chain."""
+    s0, counts, centres = f.gen
+    xs, ws = exact_state(w, 100 * s0 + k, counts, centres=centres, resampled=(k % 2 == 1))
+    noise = exact_noise(seed, k, w.num_pe, w.pe_cap, npdtype(w))
     u = scenario.resample_u32(seed, k, w.num_pe)
     xu = scenario.exchange_u32(seed, k, w.num_pe, w.pe_cap)
-    return stage_step(f, w, oracle.model(w), sc.meas[k], noise, u, xu, rep)
+    return stage_step(f, w, oracle.model(w), xs, ws, sc.meas[k], noise, u, xu, rep)
 
 
 def _rb_case():
