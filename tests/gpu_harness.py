@@ -224,7 +224,7 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
     if not check_resample:
         return
     par, lx, xr, wr = g["par"], g["lx"], g["xr"], g["wr"]
-    pre, Lo_all = [], []
+    pre, pre_w, Lo_all = [], [], []
     for j in range(K):
         L = len(xr[j])
         lmax = w.pe_cap - J[j]
@@ -237,9 +237,14 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
         check_offspring(par[j], L, wuo[j], f"PE {j}")
         xg = np.asarray(g["xp"][j])[par[j][:L]]
         pre.append(xg)
-        nw = float(g["mass"][j]) / L if L else 0.0
-        if L:
-            np.testing.assert_allclose(np.asarray(wr[j], np.float64), nw, rtol=1e-6 if dt == np.float32 else 1e-14)
+        # new weights N_j / L_j before the exchange moves some of them
+        pre_w.append(np.full(L, float(g["mass"][j]) / L if L else 0.0))
+
+    def check_new_weights(want_w):
+        for j in range(K):
+            if len(want_w[j]):
+                np.testing.assert_allclose(np.asarray(wr[j], np.float64), want_w[j],
+                                           rtol=1e-6 if dt == np.float32 else 1e-14)
     if K > 1 and w.exchange_frac > 0:
         # Step 6: the count and the trigger from the oracle's own masses and
         # counts, the slots from the oracle's slot function on the injected
@@ -252,6 +257,8 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
                 np.dtype((np.void, np.dtype(dt).itemsize * 4))).ravel())
             assert np.array_equal(key([np.ascontiguousarray(a) for a in xr]),
                                   key([np.ascontiguousarray(a) for a in pre]))
+            tot = lambda arrs: sum(float(np.sum(np.asarray(a, np.float64))) for a in arrs)
+            assert abs(tot(wr) - tot(pre_w)) <= 1e-5 * max(tot(pre_w), 1e-300)
             return
         due = True
         if w.exchange_threshold > 0:
@@ -264,16 +271,20 @@ def check_step_from_inputs(w, m, x0, w0, Z, noise, u, xu, g, rep: StageReport, e
         assert lx == Lx, ("exchange count", lx, Lx)
         slots = [oracle.exchange_slots(counts[j], Lx, np.asarray(xu, np.uint32).reshape(K, -1)[j]) for j in range(K)]
         want = [np.array(a, copy=True) for a in pre]
+        want_w = [np.array(a, copy=True) for a in pre_w]
         for j in range(K):
             for t in range(Lx):
                 shift = 1 + t % (K - 1) if (w.exchange_mode == "all" and K > 2) else 1
                 k = (j + shift) % K
                 want[k][slots[k][t]] = pre[j][slots[j][t]]
+                want_w[k][slots[k][t]] = pre_w[j][slots[j][t]]
         for j in range(K):
             assert np.array_equal(np.asarray(xr[j]), want[j]), ("exchange", j)
+        check_new_weights(want_w)
     else:
         for j in range(K):
             assert np.array_equal(np.asarray(xr[j]), pre[j])
+        check_new_weights(pre_w)
 
 
 def exact_state(w, seed, n_per_pe, centres=None, spread=25.0, mass=3.0, resampled=False):
