@@ -335,16 +335,34 @@ __device__ __forceinline__ H3<double> meas_h<double>(const Model& m, const St4<d
   return h;
 }
 
+// Bearing residual |z1 - (h1 + h1lo)| wrapped to [0, pi] (the exponent only
+// squares it); d1 = z1 - h1 as rounded.  Bearings lie in (-pi, pi]: on the
+// same side of the +-pi cut, z1 - h1 is exact for every pair that can matter
+// (Sterbenz), and the wrap is not needed.  Across the cut the raw difference
+// is near +-2 pi, where FP32 rounds it to 2.4e-7 rad (~1e-4 of the likelihood
+// at 3 sigma for 0.5 deg noise); that rare case recovers the rounding error
+// (TwoSum) and wraps with 2 pi as a double-float.
+__device__ __forceinline__ float bearing_resid(float z1, float h1, float h1lo, float d1, float per_hi,
+                                               float per_lo) {
+  const float a = fabsf(d1 - h1lo);
+  if (a <= 3.14159265f) return a;
+  const float bb = d1 - z1;
+  const float err = (z1 - (d1 - bb)) + (-h1 - bb);        // z1 - h1 = d1 + err exactly
+  const float sg = d1 > 0.0f ? 1.0f : -1.0f;
+  return fabsf((per_hi - sg * d1) + (per_lo - sg * (err - h1lo)));
+}
+__device__ __forceinline__ double bearing_resid(double, double, double h1lo, double d1, double per_hi,
+                                                double per_lo) {
+  const double a = fabs(d1 - h1lo);
+  return fmin(a, (per_hi - a) + per_lo);
+}
+
 // Exponent q of the likelihood 2^-q for measurement (z0, z1) and particle h.
 template <class R>
 __device__ __forceinline__ R qform(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
   const R d0 = z0 - h0;
   R d1 = z1 - h1;
-  if (L.rb) {
-    d1 = d1 - h1lo;
-    const R a = fabs(d1);
-    d1 = fmin(a, (L.per_hi - a) + L.per_lo);   // wrap to [0, pi]
-  }
+  if (L.rb) d1 = bearing_resid(z1, h1, h1lo, d1, L.per_hi, L.per_lo);
   return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
 }
 
@@ -354,11 +372,7 @@ template <class R, int RB>
 __device__ __forceinline__ R qform_t(const Lik<R>& L, R z0, R z1, R h0, R h1, R h1lo) {
   const R d0 = z0 - h0;
   R d1 = z1 - h1;
-  if (RB & 1) {
-    d1 = d1 - h1lo;
-    const R a = fabs(d1);
-    d1 = fmin(a, (L.per_hi - a) + L.per_lo);
-  }
+  if (RB & 1) d1 = bearing_resid(z1, h1, h1lo, d1, L.per_hi, L.per_lo);
   return fma(L.b1 * d1, d1, (L.b0 * d0) * d0);
 }
 
@@ -403,9 +417,10 @@ __device__ __forceinline__ float qform_p(const LikP& L, unsigned long long z, un
   float d0, d1;
   f2_unpack(f2_sub(z, h), d0, d1);
   if (RB & 1) {
-    d1 = d1 - h1lo;
-    const float a = fabsf(d1);
-    d1 = fminf(a, (L.per_hi - a) + L.per_lo);
+    float z0, z1, h0, h1;
+    f2_unpack(z, z0, z1);
+    f2_unpack(h, h0, h1);
+    d1 = bearing_resid(z1, h1, h1lo, d1, L.per_hi, L.per_lo);
   }
   float e0, e1;
   f2_unpack(f2_mul(f2_pack(d0, d1), L.a01), e0, e1);
