@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
   const int total = pref[K];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
+  const P4<R>* __restrict__ geo = static_cast<const P4<R>*>(d.geo);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
@@ -127,15 +128,20 @@ __global__ void __launch_bounds__(kThreads) k_selsum(Dev d, Model m) {
       P4<R> q = {0, 0, 0, 0};
       St4<R> st = {0, 0, 0, 0};
       if (i < cnt) {
-        // the pass-1 tiles: the spatial order when the update built it
-        const long src = m.tune.order ? (long)j * m.pe_cap + d.perm[base + i] : base + i;
-        st = x[src];
-        const H3<R> h = meas_h<R>(m, st, tab);
-        q = P4<R>{h.h0, h.h1, h.h1lo, w[src]};
-        lo0 = fmin(lo0, h.h0);
-        hi0 = fmax(hi0, h.h0);
-        lo1 = fmin(lo1, h.h1);
-        hi1 = fmax(hi1, h.h1);
+        // the pass-1 tiles: the spatial order (and its geometry records) when
+        // the update built it
+        if (m.tune.order) {
+          q = geo[base + i];
+          st = x[(long)j * m.pe_cap + d.perm[base + i]];
+        } else {
+          st = x[base + i];
+          const H3<R> h = meas_h<R>(m, st, tab);
+          q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
+        }
+        lo0 = fmin(lo0, q.h0);
+        hi0 = fmax(hi0, q.h0);
+        lo1 = fmin(lo1, q.h1);
+        hi1 = fmax(hi1, q.h1);
       }
       sp[i] = q;
       sx[i] = st;

@@ -493,20 +493,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
     }
     __syncthreads();
     // ---- pass 1: C^j_p (Eq. 7).  Groups of nsplit consecutive lanes share a
-    // measurement and split the particles; FP32 runs of <= 256 pairs per
-    // thread, FP64 across runs and across the group (shuffle tree).
+    // measurement and split the particles.  Accumulation: FP32 runs of at
+    // most 256 pairs per thread, the runs summed in FP64, and the nsplit
+    // lanes' FP64 sums added in lane order by one thread per measurement.
     if (M > 0) {
       const int nsplit = pow2_floor(min(32, max(1, T / M)));
       const int mper = T / nsplit;
       const int pl = tid / nsplit, split = tid % nsplit;
+      double* dred = reinterpret_cast<double*>(smem + SL.red);
       for (int p0 = 0; p0 < M; p0 += mper) {
         const int p = p0 + pl;
-        R acc = 0;
+        double acc = 0.0;
         if (p < M) {
-          // four independent partial sums (ILP), folded every 256 pairs; the
-          // slice is one tile: its sums stay in the kernel's precision and
-          // the measurement's total goes to FP64 once (the FP64 pipe runs
-          // ~2 lanes/clk/SM)
+          // four independent partial sums (ILP), a run of 4 x 64 pairs each
+          // time they are folded into the FP64 sum (the FP64 pipe runs ~2
+          // lanes/clk/SM: one add per run)
           const V2<R> z = zs[p];
           R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
           int i = split, k = 0;
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
             a2 = fma(exp2_neg(PQ(z.a, z.b, q2.h0, q2.h1, q2.h1lo)), q2.w, a2);
             a3 = fma(exp2_neg(PQ(z.a, z.b, q3.h0, q3.h1, q3.h1lo)), q3.w, a3);
             if (++k == 64) {
-              acc += (a0 + a1) + (a2 + a3);
+              acc += (double)((a0 + a1) + (a2 + a3));
               a0 = a1 = a2 = a3 = 0;
               k = 0;
             }
@@ -526,14 +527,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_step_fused(Dev d, Model m,
             const P4<R> q0 = sp[i];
             a0 = fma(exp2_neg(PQ(z.a, z.b, q0.h0, q0.h1, q0.h1lo)), q0.w, a0);
           }
-          acc += (a0 + a1) + (a2 + a3);
+          acc += (double)((a0 + a1) + (a2 + a3));
         }
-        for (int o = nsplit >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, nsplit);
+        dred[tid] = acc;
+        __syncthreads();
         if (split == 0 && p < M) {
-          const double c = (double)acc * cs;
+          double c = dred[tid];
+          for (int o = 1; o < nsplit; ++o) c += dred[tid + o];
+          c *= cs;
           Cd[p] = c;
           d.C[j * m.m_max + p] = c;
         }
+        __syncthreads();
       }
     }
     if (m.ck_global && m.K > 1) {

@@ -21,6 +21,11 @@
 // k_cell_scatter: per chunk: each particle's stable rank among the chunk's
 //   particles with its key (a warp's peers by match, earlier warps by their
 //   per-bin counts) gives its sorted position.
+// The histogram kernel keeps each particle's sensor-space geometry and
+// predicted weight, (h0, h1, h1lo, w) as computed for its key, and the scatter
+// moves that record to the particle's sorted position: passes 1-3 then load
+// one coalesced 16-byte record per particle instead of gathering the state
+// through the permutation and recomputing the range and the bearing.
 #include "phd_internal.cuh"
 
 namespace phd {
@@ -100,6 +105,8 @@ __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
   __shared__ int last_chunk;
   item_prefix(d.n_pred, m.K, pref, kChunk);
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
+  const R* __restrict__ w = static_cast<const R*>(d.w_alt);
+  P4<R>* __restrict__ geo_s = static_cast<P4<R>*>(d.geo_s);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   for (int c = blockIdx.x; c < pref[m.K]; c += gridDim.x) {
     const int j = item_pe(pref, m.K, c);
@@ -109,6 +116,7 @@ __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
     if (i < d.n_pred[j]) {
       const long g = (long)j * m.pe_cap + i;
       const H3<R> h = meas_h<R>(m, x[g], tab);
+      geo_s[g] = P4<R>{h.h0, h.h1, h.h1lo, w[g]};
       const int k = cell_key(m, (float)h.h0, (float)h.h1);
       d.ckey[g] = (unsigned char)k;
       atomicAdd(&hist[k], 1);
@@ -130,8 +138,11 @@ __global__ void __launch_bounds__(kChunk) k_cell_hist(Dev d, Model m) {
   }
 }
 
+template <class R>
 __global__ void __launch_bounds__(kChunk) k_cell_scatter(Dev d, Model m) {
   pdl_enter();
+  const P4<R>* __restrict__ geo_s = static_cast<const P4<R>*>(d.geo_s);
+  P4<R>* __restrict__ geo = static_cast<P4<R>*>(d.geo);
   __shared__ int pref[kMaxPE + 1];
   __shared__ int wc[kChunk / 32][kCells];   // per-warp key counts, then their exclusive prefix over warps
   item_prefix(d.n_pred, m.K, pref, kChunk);
@@ -161,6 +172,7 @@ __global__ void __launch_bounds__(kChunk) k_cell_scatter(Dev d, Model m) {
     if (live) {
       const int dst = d.chist[(long)c * kCells + key] + wc[wid][key] + rank_w;
       d.perm[(long)j * m.pe_cap + dst] = i;
+      geo[(long)j * m.pe_cap + dst] = geo_s[g];
     }
     __syncthreads();
   }
@@ -171,7 +183,7 @@ cudaError_t launch_order(const Dev& d, const Model& m, cudaStream_t s) {
   const long chunks = (long)m.K * ((m.pe_cap + kChunk - 1) / kChunk);
   const int gc = (int)(chunks < 152 * 4 ? (chunks > 0 ? chunks : 1) : 152 * 4);
   launch_k(k_cell_hist<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
-  launch_k(k_cell_scatter, dim3(gc), dim3(kChunk), 0, s, d, m);
+  launch_k(k_cell_scatter<R>, dim3(gc), dim3(kChunk), 0, s, d, m);
   return cudaGetLastError();
 }
 

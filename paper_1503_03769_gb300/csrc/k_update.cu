@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
   const int total = ipref[K];
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
+  const P4<R>* __restrict__ geo = static_cast<const P4<R>*>(d.geo);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
@@ -77,13 +78,16 @@ __global__ void __launch_bounds__(kThreads) k_colsum(Dev d, Model m) {
       for (int i = threadIdx.x; i < TP; i += kThreads) {
         P4<R> q = {0, 0, 0, 0};
         if (i < cnt) {
-          const long src = m.tune.order ? (long)j * m.pe_cap + d.perm[base + i] : base + i;
-          const H3<R> h = meas_h<R>(m, x[src], tab);
-          q = P4<R>{h.h0, h.h1, h.h1lo, w[src]};
-          lo0 = fmin(lo0, h.h0);
-          hi0 = fmax(hi0, h.h0);
-          lo1 = fmin(lo1, h.h1);
-          hi1 = fmax(hi1, h.h1);
+          if (m.tune.order) {
+            q = geo[base + i];   // the spatial order's record: geometry and weight
+          } else {
+            const H3<R> h = meas_h<R>(m, x[base + i], tab);
+            q = P4<R>{h.h0, h.h1, h.h1lo, w[base + i]};
+          }
+          lo0 = fmin(lo0, q.h0);
+          hi0 = fmax(hi0, q.h0);
+          lo1 = fmin(lo1, q.h1);
+          hi1 = fmax(hi1, q.h1);
         }
         sp[i] = q;
       }
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
   const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x_alt);
   const R* __restrict__ w = static_cast<const R*>(d.w_alt);
   R* __restrict__ wu = static_cast<R*>(d.wu);
+  const P4<R>* __restrict__ geo = static_cast<const P4<R>*>(d.geo);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
@@ -302,16 +307,24 @@ __global__ void __launch_bounds__(kThreads) k_rowsum(Dev d, Model m) {
       const int i = tile * TPR + k * GR + il;
       h0[k] = h1[k] = hl[k] = wi[k] = 0;
       if (i < n) {
-        const long gi = (long)j * m.pe_cap + (m.tune.order ? d.perm[(long)j * m.pe_cap + i] : i);
-        const H3<R> h = meas_h<R>(m, x[gi], tab);
-        h0[k] = h.h0;
-        h1[k] = h.h1;
-        hl[k] = h.h1lo;
-        wi[k] = w[gi];
-        lo0 = fmin(lo0, h.h0);
-        hi0 = fmax(hi0, h.h0);
-        lo1 = fmin(lo1, h.h1);
-        hi1 = fmax(hi1, h.h1);
+        if (m.tune.order) {
+          const P4<R> q = geo[(long)j * m.pe_cap + i];   // sorted position i
+          h0[k] = q.h0;
+          h1[k] = q.h1;
+          hl[k] = q.h1lo;
+          wi[k] = q.w;
+        } else {
+          const long gi = (long)j * m.pe_cap + i;
+          const H3<R> h = meas_h<R>(m, x[gi], tab);
+          h0[k] = h.h0;
+          h1[k] = h.h1;
+          hl[k] = h.h1lo;
+          wi[k] = w[gi];
+        }
+        lo0 = fmin(lo0, h0[k]);
+        hi0 = fmax(hi0, h0[k]);
+        lo1 = fmin(lo1, h1[k]);
+        hi1 = fmax(hi1, h1[k]);
       }
     }
     if (j != staged) {

@@ -143,6 +143,8 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.chist = cv.take<int>(chunks * 256);
   t.perm = cv.take<int>(K * P);
   t.hdone = cv.take<unsigned int>(K);
+  t.geo_s = cv.take<char>(K * P, 4 * rs);
+  t.geo = cv.take<char>(K * P, 4 * rs);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;

@@ -174,6 +174,8 @@ struct Dev {
   int* chist;            // [chunks][256] per-chunk cell counts, then their starts
   int* perm;             // [K][pe_cap] slot of the particle at each sorted position
   unsigned int* hdone;   // [K] cell-histogram chunks finished per slice (the last scans the slice)
+  void* geo_s;           // P4<R> [K*pe_cap] sensor-space geometry and predicted weight, slot order
+  void* geo;             // P4<R> [K*pe_cap] the same at each sorted position (read by passes 1-3)
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
