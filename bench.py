@@ -463,6 +463,7 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
     # work of the untimed run heads, taken out of the counters (the stage
     # timer is off during them)
     head = {"pairs": 0, "pairs_evaluated": 0, "updates": 0, "launches": 0}
+    head_phases = {}
     timer = {"on": False}
 
     def set_timer(on):
@@ -475,12 +476,16 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
             f.set_state(empty_x, empty_w)
             if steady:
                 s0 = f.stats()
+                p0 = f.phase_times()
                 f.set_stage_timer(False)
                 f.run([scen[r].meas[q] for q in range(steady)], sync=False)
                 s1 = f.stats()
+                p1 = f.phase_times()
                 f.set_stage_timer(timer["on"])
                 for key in head:
                     head[key] += s1[key] - s0[key]
+                for key in p1:
+                    head_phases[key] = head_phases.get(key, 0.0) + p1[key] - p0[key]
 
     # set-up on the staged path: the pair passes' launch shape is autotuned
     # half-way through a run of the same workload, then the state is reset
@@ -512,6 +517,7 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
         f.reset_stats()
         for key in head:
             head[key] = 0
+        head_phases.clear()
         evs = []
         est_log = []
         if world > 1:
@@ -564,9 +570,18 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
     path = f.get_path()
     peak = ex2_peak(local_rank)
     upd_ms = st["update_ms"]
+    phases = None
+    if path == "grid":
+        # the step kernel's phase clock: the update is its spatial-order, pass-1,
+        # normaliser and pass-2 phases (Eq. 7-8 with the order the passes walk)
+        phases = {k: v - head_phases.get(k, 0.0) for k, v in f.phase_times().items()}
+        step_ms = upd_ms
+        upd_ms = sum(phases[k] for k in ("cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2"))
     achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
     ev_frac = st["pairs_evaluated"] / pairs if pairs else None
-    kname = "k_step_fused (whole step, one CTA per PE)" if path == "fused" else UPDATE_KERNELS
+    kname = {"fused": "k_step_fused (whole step, one CTA per PE)",
+             "grid": "k_step_grid update phases (cell totals, cell starts, scatter, pass 1, normalisers, pass 2)"
+             }.get(path, UPDATE_KERNELS)
     roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": peak["Texp_per_s"], "unit": "Texp/s",
                 "frac": achieved / peak["Texp_per_s"], "traffic": _traffic_from_profile(path, w.name),
@@ -579,6 +594,10 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
                 "note": "achieved counts every particle x measurement pair (the metric's unit); pairs past "
                         "the exact likelihood gate contribute exactly 0 and are skipped (frac_evaluated counts "
                         "only the evaluated ones)"}
+    if phases is not None:
+        nt = max(st["timed_updates"], 1)
+        roofline["step_kernel_ms_per_step"] = step_ms / nt
+        roofline["phase_ms_per_step"] = {k: v / nt for k, v in phases.items()}
 
     # whole runs in one launch each (phd_run): S scans per call, L2 flushed
     # between runs (outside the events)

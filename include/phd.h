@@ -57,7 +57,7 @@ typedef enum {
 enum { PHD_MEAS_LINEAR = 0, PHD_MEAS_RANGE_BEARING = 1 };
 enum { PHD_FP32 = 0, PHD_FP64 = 1 };
 enum { PHD_CK_LOCAL = 0, PHD_CK_GLOBAL = 1 };
-enum { PHD_PATH_AUTO = 0, PHD_PATH_STAGED = 1, PHD_PATH_FUSED = 2 };
+enum { PHD_PATH_AUTO = 0, PHD_PATH_STAGED = 1, PHD_PATH_FUSED = 2, PHD_PATH_GRID = 3 };
 enum { PHD_BIRTH_UNIFORM = 0, PHD_BIRTH_GAUSSIAN = 1 };
 enum { PHD_XCHG_RING = 0, PHD_XCHG_ALL = 1 };
 
@@ -302,14 +302,22 @@ phd_status phd_step_inject(phd_handle *h, const void *d_Z, int32_t M, const void
 phd_status phd_run(phd_handle *h, const void *d_Z, const int32_t *d_offsets, int32_t S, void *d_states,
                    int32_t *d_labels, int32_t *d_counts, int32_t cap);
 
-/* Kernel path of phd_step / phd_step_host / phd_step_inject / phd_run.
+/* Kernel path of phd_step / phd_step_host / phd_step_inject / phd_run (and,
+ * for batch handles, phd_batch_step).
  * PHD_PATH_FUSED: one cooperative kernel per call, one CTA per PE with the PE's
  * slice in shared memory (available when the slice of pe_cap particles and
  * m_max measurements fits an SM's shared memory and all K CTAs can be
- * co-resident); PHD_PATH_STAGED: the stage kernels of phd_predict ..
- * phd_resample as a CUDA graph; PHD_PATH_AUTO (default): fused when
- * available.  phd_set_path returns PHD_ERR_INVALID_ARG for an unavailable
- * path; phd_get_path reports the path in use. */
+ * co-resident); PHD_PATH_GRID: one cooperative kernel per step over the
+ * whole GPU, its phases (prediction, spatial order, the two pair passes,
+ * selection, label sums, resampling) separated by grid-wide barriers with
+ * bounded waits (available for one-PE filters and batches of independent
+ * runs, without a birth network; the pair passes always walk the spatial
+ * order, the gate setting of phd_set_tuning applies); PHD_PATH_STAGED: the
+ * stage kernels of phd_predict .. phd_resample as a CUDA graph;
+ * PHD_PATH_AUTO (default): fused when available, else grid when available,
+ * else staged.  phd_set_path returns PHD_ERR_INVALID_ARG for an unavailable
+ * path; phd_get_path reports the path in use.  The stage calls (phd_predict,
+ * phd_update, phd_extract, phd_resample) always run the staged kernels. */
 phd_status phd_set_path(phd_handle *h, int32_t path);
 phd_status phd_get_path(phd_handle *h, int32_t *path);
 
@@ -420,6 +428,17 @@ typedef struct phd_stats {
 /* Read the counters accumulated since phd_init / phd_reset_stats.  Synchronises. */
 phd_status phd_get_stats(phd_handle *h, phd_stats *out);
 phd_status phd_reset_stats(phd_handle *h);
+
+/* Time spent in each phase of the grid path's step kernel, summed over its
+ * launches since phd_init / phd_reset_stats (device clock at the phases'
+ * barriers, read by one thread): h_ms[0..n-1] (n <= 12) in milliseconds for
+ * the phases prediction + spatial keys, cell totals, cell starts, scatter,
+ * pass 1 (Eq. 7), normalisers (Eq. 12), pass 2 (Eq. 8), mass and plan,
+ * selection ranks + CDF chunk sums, label sums (Eq. 18) + CDF offsets,
+ * estimates + offspring ends, gather.  Each figure runs from the previous
+ * barrier to the phase's own (it includes the wait for the slowest CTA).
+ * Zeros on the other paths.  Synchronises. */
+phd_status phd_get_phase_times(phd_handle *h, double *h_ms, int32_t n);
 
 /* on != 0: phd_step / phd_step_host bracket the update stage (Eq. 7-8 pair
  * passes) with CUDA events on the handle's stream; the times add up in

@@ -71,19 +71,6 @@ __global__ void __launch_bounds__(256) k_select(Dev d, Model m) {
   if (blockIdx.y == 0 && threadIdx.x == 0) d.nsel[j] = (int)LT;
 }
 
-// Cartesian point of a measurement, the offset origin of the labelled sums.
-template <class R>
-__device__ __forceinline__ void meas_point(const Model& m, V2<R> z, R& rx, R& ry) {
-  if (m.meas_model == 0) {
-    rx = z.a;
-    ry = z.b;
-  } else {
-    R sn, cs;
-    sincos(z.b, &sn, &cs);
-    rx = (R)m.sx + z.a * cs;
-    ry = (R)m.sy + z.a * sn;
-  }
-}
 
 // Pass 3: a work item is a tile of c_tile particles of one slice (the pass-1
 // tile), staged as packed geometry + weight and state; groups of nsplit

@@ -44,51 +44,6 @@ struct FusedArgs {
   int S;
 };
 
-// Grid-wide barrier over gridDim.x CTAs with a bounded wait (`limit`
-// polls).  Every CTA adds one to a 64-bit arrival count that only grows, so
-// barrier b of a launch completes when the count reaches b * gridDim.x: one
-// release atomic and the acquire polls are the whole cost (no reset, no
-// generation word).  The count is a multiple of gridDim.x between launches; a
-// launch that gave up leaves an error word behind and the host clears both
-// before the next.  Returns false (in every thread of the CTA) when the wait
-// gave up or an error was recorded; the caller then returns from the kernel.
-// `lost` (read by thread 0) makes the CTA leave without arriving, as a PE that
-// died would: the host's failure injection.
-__device__ __forceinline__ bool grid_sync(const Dev& d, long long limit, bool lost) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 0;
-    if (!lost) {
-      unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.bar);
-      const unsigned long long G = gridDim.x;
-      unsigned long long old;
-      asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(cnt) : "memory");
-      const unsigned long long target = (old / G + 1ull) * G;
-      long long it = 0;
-      for (;;) {
-        unsigned long long c;
-        int e;
-        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
-        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(d.err) : "memory");
-        if (e != 0) break;
-        if (c >= target) {
-          ok = 1;
-          break;
-        }
-        if (++it > limit) {
-          atomicOr(d.err, kErrTimeout);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
-
 // Shared-memory layout of the fused kernel (bytes), for pe_cap P and m_max Mm.
 struct FusedSmem {
   size_t sx, sh0, sh1, shl, sw, swu, zs, ginv, Cd, Cu, dW, sel, selrank, red, total;

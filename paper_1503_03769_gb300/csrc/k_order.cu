@@ -30,18 +30,6 @@
 
 namespace phd {
 
-constexpr int kCells = 256;   // 16 x 16, Morton order
-
-__device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
-  int cx = (int)floorf((h0 - m.f_cell_o0) * m.f_cell_s0);
-  int cy = (int)floorf((h1 - m.f_cell_o1) * m.f_cell_s1);
-  cx = min(max(cx, 0), 15);
-  cy = min(max(cy, 0), 15);
-  int k = 0;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) k |= (((cx >> b) & 1) << (2 * b)) | (((cy >> b) & 1) << (2 * b + 1));
-  return k;
-}
 
 static_assert(kChunk == 4 * kCells, "the slice scan uses four threads per bin");
 

@@ -1,0 +1,952 @@
+// Persistent step kernel: one cooperative launch runs a whole filter step
+// (predict, update, labelled extraction, resampling) for every slice of a
+// handle, its phases separated by grid-wide barriers with bounded waits.
+//
+// It computes what the staged kernels compute (the same helpers, the same
+// per-pair arithmetic), for handles without particle exchange or CU fusion:
+// one filter (one PE) or a batch of independent runs.  What changes is the
+// organisation of the work, which on the gated dense workloads is what the
+// staged step's time goes to (a dozen launches of latency-bound kernels):
+//  - every phase is one sweep of the grid over work items of 256 particles
+//    (or over measurements / labels), with no launch between phases;
+//  - the spatial order of the pair passes (a stable counting sort on a 16 x 16
+//    grid over measurement space) is built in three phases (chunk histograms
+//    with the prediction, per-bin totals, per-bin starts) and its records
+//    (sensor-space geometry and predicted weight) are moved once;
+//  - pass 1 records, per sorted tile, which measurements can reach the tile
+//    (the exact likelihood gate, a bit per measurement).  Pass 1 writes only
+//    those partial sums, the normalisers add only those (in tile order, so C
+//    is deterministic), pass 2 walks only those, and the extraction's label
+//    sums and their reduction use the same bits: no partial matrix is
+//    cleared or read in full.
+// Phases (barrier between consecutive ones):
+//   A  predict (Eq. 5-6), measurement-space geometry, cell key, chunk
+//      histograms; measurement staging
+//   B  cell totals per (slice, cell)          C  cell starts per (slice, cell)
+//   D  stable scatter to the cell order       E  pass 1 (Eq. 7) per tile
+//   F  C_p, ginv_p and the dW keys (Eq. 12, 16) per measurement
+//   G  pass 2 (Eq. 8) per tile: updated weights, tile sums and maxima
+//   H  N^j, the resampling plan, LT_j per slice
+//   I  selection ranks (Step 3) per measurement; CDF chunk totals per chunk
+//   J  pass 3 (Eq. 18 sums) per tile; CDF chunk offsets per slice
+//   K  estimates per selected label; offspring ends per chunk
+//   L  children gathered (Sec. 2.2 step 3), counts and step counter advanced
+// The barrier is one release atomic per CTA on a 64-bit count that only grows
+// and acquire polls; the host passes the count the launch starts from.
+#include "phd_internal.cuh"
+
+namespace phd {
+
+constexpr int kPT = 256;      // threads per CTA
+constexpr int kPMB = 4;       // pass 1: measurements per thread
+constexpr int kPhases = 12;
+
+template <class R> struct PersistArgs {
+  const R* Z;                 // one filter: the scan (staged into the workspace in phase A); NULL for a batch
+  int M;
+  const R* noise;             // injected predict draws or NULL
+  const uint32_t* u;          // injected resampling uniforms or NULL
+  R* out_states;              // one filter: estimates in ascending label order
+  int* out_labels;
+  int cap;
+  int* d_count;               // one filter: true estimate count (may be NULL)
+  unsigned long long base;    // barrier count at launch
+  int direct;                 // 1: one filter (write the outputs)
+};
+
+// Barrier b (1-based) of the launch: every CTA arrives once; wait until all
+// have (count >= base + b G), polling at most `limit` times.  On expiry or an
+// error recorded by another CTA: false in every thread.
+__device__ __forceinline__ bool pbar_sync(const Dev& d, unsigned long long target, long long limit) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(d.pbar) : "memory");
+    long long it = 0;
+    for (;;) {
+      unsigned long long c;
+      int e;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(d.pbar) : "memory");
+      asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(d.err) : "memory");
+      if (c >= target) {
+        ok = 1;
+        break;
+      }
+      if (e & kErrTimeout) break;
+      if (++it > limit) {
+        atomicOr(d.err, kErrTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Warp-wide sum of one value per lane (every lane gets the total).
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R, int RB>
+__global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArgs<R> a) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  __shared__ int ipref[kMaxPE + 1];   // items (256-particle chunks / tiles) per slice, prefix
+  __shared__ int npred_s[kMaxPE];     // predicted particles per slice
+  __shared__ int wcnt[kPT / 32];
+  __shared__ R bsh[4 * (kPT / 32)];
+  __shared__ double dred[kPT / 32], dredm[kPT / 32];
+  __shared__ int nlive_s;
+  const int K = m.K, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = gridDim.x, bid = blockIdx.x;
+  const long gw = ((long)bid * kPT + tid) >> 5, nwarps = ((long)nb * kPT) >> 5;
+  const long long lim = m.spin_limit;
+  const unsigned long long G = nb;
+  unsigned long long tb = 0ull;   // barriers passed
+  unsigned long long t_prev = (bid == 0 && tid == 0) ? gtimer() : 0ull;
+  auto barrier = [&](int phase) -> bool {
+    ++tb;
+    const bool ok = pbar_sync(d, a.base + tb * G, lim);
+    if (ok && bid == 0 && tid == 0) {
+      const unsigned long long t = gtimer();
+      atomicAdd(d.ptimes + phase, t - t_prev);
+      t_prev = t;
+    }
+    return ok;
+  };
+  // slice sizes after prediction: survivors + births
+  for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
+  __syncthreads();
+  slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + 255) / 256; });
+  const int nitems = ipref[K];
+  const unsigned long long step = *d.step;
+  const Cst<R> cc = consts<R>(m);
+  const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
+  const int W = d.gwords;
+
+  // ---- A: prediction, geometry, cell keys, chunk histograms; Z staging
+  {
+    int* hist = reinterpret_cast<int*>(smem);
+    const St4<R>* __restrict__ x = static_cast<const St4<R>*>(d.x);
+    const R* __restrict__ w = static_cast<const R*>(d.w);
+    St4<R>* __restrict__ xp = static_cast<St4<R>*>(d.x_alt);
+    R* __restrict__ wp = static_cast<R*>(d.w_alt);
+    P4<R>* __restrict__ geo_s = static_cast<P4<R>*>(d.geo_s);
+    if (a.direct) {
+      V2<R>* zs = static_cast<V2<R>*>(d.Z);
+      for (int p = bid * kPT + tid; p < a.M; p += nb * kPT) {
+        const V2<R> z = reinterpret_cast<const V2<R>*>(a.Z)[p];
+        if (!isfinite(z.a) || !isfinite(z.b)) atomicOr(d.err, kErrNonFinite);
+        if (a.Z != static_cast<const R*>(d.Z)) zs[p] = z;
+      }
+    }
+    if (bid == 0) {
+      for (int j = tid; j < K; j += kPT) d.n_pred[j] = npred_s[j];
+      if (tid == 0 && a.direct) *d.M = a.M;
+    }
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int i = (it - ipref[j]) * 256 + tid;
+      hist[tid] = 0;
+      __syncthreads();
+      if (i < npred_s[j]) {
+        const long g = (long)j * m.pe_cap + i;
+        R n1, n2, u1, u2;
+        draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
+        const bool surv = i < d.n_cur[j];
+        St4<R> o;
+        R wo;
+        predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j), n1, n2,
+                        u1, u2, o, wo);
+        xp[g] = o;
+        wp[g] = wo;
+        const H3<R> h = meas_h<R>(m, o, tab);
+        geo_s[g] = P4<R>{h.h0, h.h1, h.h1lo, wo};
+        const int k = cell_key(m, (float)h.h0, (float)h.h1);
+        d.ckey[g] = (unsigned char)k;
+        atomicAdd(&hist[k], 1);
+      }
+      __syncthreads();
+      d.pchist[(long)it * 256 + tid] = hist[tid];
+      __syncthreads();
+    }
+  }
+  if (!barrier(0)) return;
+
+  // ---- B: per (slice, cell): total over the slice's chunks (a warp per
+  // unit; each lane sums a contiguous run of chunks, independent loads)
+  for (long u = gw; u < (long)K * 256; u += nwarps) {
+    const int j = (int)(u >> 8), b = (int)(u & 255);
+    const int c0 = ipref[j], nc = ipref[j + 1] - c0;
+    const int per = (nc + 31) / 32;
+    int tot = 0;
+    for (int k = 0; k < per; ++k) {
+      const int c = lane * per + k;
+      if (c < nc) tot += __ldcg(d.pchist + (long)(c0 + c) * 256 + b);
+    }
+    tot = warp_sum(tot);
+    if (lane == 0) d.bintot[u] = tot;
+  }
+  if (!barrier(1)) return;
+
+  // ---- C: per (slice, cell): the cell's start (cells before it), then each
+  // chunk's start within the cell (chunks before it): pchist in place
+  for (long u = gw; u < (long)K * 256; u += nwarps) {
+    const int j = (int)(u >> 8), b = (int)(u & 255);
+    int base = 0;
+    for (int q = lane; q < b; q += 32) base += __ldcg(d.bintot + (long)j * 256 + q);
+    base = warp_sum(base);
+    const int c0 = ipref[j], nc = ipref[j + 1] - c0;
+    const int per = (nc + 31) / 32;
+    int mine = 0;
+    for (int k = 0; k < per; ++k) {
+      const int c = lane * per + k;
+      if (c < nc) mine += __ldcg(d.pchist + (long)(c0 + c) * 256 + b);
+    }
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int run = base + incl - mine;
+    for (int k = 0; k < per; ++k) {
+      const int c = lane * per + k;
+      if (c < nc) {
+        int* e = d.pchist + (long)(c0 + c) * 256 + b;
+        const int v = __ldcg(e);
+        *e = run;
+        run += v;
+      }
+    }
+  }
+  if (!barrier(2)) return;
+
+  // ---- D: stable scatter: each particle's rank among its chunk's particles
+  // with its key gives its sorted position; the geometry record moves there
+  {
+    int* wc = reinterpret_cast<int*>(smem);   // [8][256]
+    const P4<R>* __restrict__ geo_s = static_cast<const P4<R>*>(d.geo_s);
+    P4<R>* __restrict__ geo = static_cast<P4<R>*>(d.geo);
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int i = (it - ipref[j]) * 256 + tid;
+      const bool live = i < npred_s[j];
+      const long g = (long)j * m.pe_cap + i;
+      const int key = live ? (int)d.ckey[g] : kCells;
+      for (int t = tid; t < 8 * kCells; t += kPT) wc[t] = 0;
+      __syncthreads();
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int rank_w = __popc(peers & ((1u << lane) - 1u));
+      if (live && rank_w == 0) wc[wid * kCells + key] = __popc(peers);
+      __syncthreads();
+      {
+        int run = 0;
+        for (int w8 = 0; w8 < 8; ++w8) {
+          const int v = wc[w8 * kCells + tid];
+          wc[w8 * kCells + tid] = run;
+          run += v;
+        }
+      }
+      __syncthreads();
+      if (live) {
+        const int dst = __ldcg(d.pchist + (long)it * 256 + key) + wc[wid * kCells + key] + rank_w;
+        d.perm[(long)j * m.pe_cap + dst] = i;
+        geo[(long)j * m.pe_cap + dst] = geo_s[g];
+      }
+      __syncthreads();
+    }
+  }
+  if (!barrier(3)) return;
+
+  const PairQ<R, RB> Q(m);
+  const Lik<R> LB = make_lik<R>(m);
+  const P4<R>* __restrict__ geo = static_cast<const P4<R>*>(d.geo);
+  // the tile's box (every thread loads its particle's record) and the
+  // measurements of slice j that can reach it: live list in smem (lidx, in
+  // measurement order) and, when `record`, the tile's gate bits
+  auto tile_gate = [&](int it, int j, int cnt, P4<R>& q, int* lidx, bool record) -> int {
+    const R inf = (R)INFINITY;
+    R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
+    q = P4<R>{0, 0, 0, 0};
+    if (tid < cnt) {
+      q = geo[(long)j * m.pe_cap + (long)(it - ipref[j]) * 256 + tid];
+      lo0 = q.h0;
+      hi0 = q.h0;
+      lo1 = q.h1;
+      hi1 = q.h1;
+    }
+    const Box<R> box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
+    const int M = slice_M(d, j);
+    const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+    int nl = 0;
+    for (int p0 = 0; p0 < M; p0 += kPT) {
+      const int p = p0 + tid;
+      bool keep = false;
+      if (p < M) {
+        const V2<R> z = Z[p];
+        keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_limit<R>(m);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) {
+        wcnt[wid] = __popc(bal);
+        if (record && p0 + wid * 32 < M) d.gbits[(long)it * W + (p0 >> 5) + wid] = bal;
+      }
+      __syncthreads();
+      int before = 0, all = 0;
+      for (int k = 0; k < kPT / 32; ++k) {
+        before += k < wid ? wcnt[k] : 0;
+        all += wcnt[k];
+      }
+      if (keep) lidx[nl + before + __popc(bal & ((1u << lane) - 1u))] = p;
+      nl += all;
+      __syncthreads();
+    }
+    return nl;
+  };
+  // the live list of a tile from its gate bits (measurement order)
+  auto tile_bits = [&](int it, int j, int* lidx) -> int {
+    const int M = slice_M(d, j);
+    const int nwd = (M + 31) / 32;
+    if (tid == 0) nlive_s = 0;
+    __syncthreads();
+    int nl = 0;
+    for (int w0 = 0; w0 < nwd; w0 += kPT) {
+      const int wd = w0 + tid;
+      const unsigned bits = wd < nwd ? __ldcg(d.gbits + (long)it * W + wd) : 0u;
+      const int c = __popc(bits);
+      int incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) wcnt[wid] = incl;
+      __syncthreads();
+      int before = 0, all = 0;
+      for (int k = 0; k < kPT / 32; ++k) {
+        before += k < wid ? wcnt[k] : 0;
+        all += wcnt[k];
+      }
+      int pos = nl + before + incl - c;
+      unsigned b = bits;
+      while (b) {
+        const int k = __ffs(b) - 1;
+        b &= b - 1u;
+        lidx[pos++] = wd * 32 + k;
+      }
+      nl += all;
+      __syncthreads();
+    }
+    return nl;
+  };
+
+  // ---- E: pass 1 (Eq. 7): tile partials of the live measurements, in FP32
+  // within the tile, written as FP64
+  {
+    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);        // [256]
+    R* red = reinterpret_cast<R*>(sp + 256);            // [kPT * kPMB]
+    int* lidx = reinterpret_cast<int*>(red + kPT * kPMB);   // [m_max]
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int cnt = min(256, npred_s[j] - (it - ipref[j]) * 256);
+      P4<R> q;
+      __syncthreads();
+      const int nl = tile_gate(it, j, cnt, q, lidx, true);
+      sp[tid] = q;
+      if (tid == 0 && nl > 0) atomicAdd(&d.stats[4], (unsigned long long)nl * (unsigned long long)cnt);
+      const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+      __syncthreads();
+      for (int r0 = 0; r0 < nl; r0 += 64 * kPMB) {
+        const int Ml = min(64 * kPMB, nl - r0);
+        const int Gm = (Ml + kPMB - 1) / kPMB;   // threads per split
+        const int S = kPT / Gm;                    // splits of the tile
+        const int GM = Gm * kPMB;
+        const int g = tid % Gm, sidx = tid / Gm;
+        R acc[kPMB];
+#pragma unroll
+        for (int k = 0; k < kPMB; ++k) acc[k] = 0;
+        if (sidx < S) {
+          R z0[kPMB], z1[kPMB];
+#pragma unroll
+          for (int k = 0; k < kPMB; ++k) {
+            const int qq = g + k * Gm;
+            const V2<R> z = qq < Ml ? Z[lidx[r0 + qq]] : V2<R>{0, 0};
+            z0[k] = z.a;
+            z1[k] = z.b;
+          }
+          int i = sidx;
+          for (; i + S < cnt; i += 2 * S) {
+            const P4<R> qa = sp[i], qb = sp[i + S];
+#pragma unroll
+            for (int k = 0; k < kPMB; ++k)
+              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+#pragma unroll
+            for (int k = 0; k < kPMB; ++k)
+              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
+          }
+          if (i < cnt) {
+            const P4<R> qa = sp[i];
+#pragma unroll
+            for (int k = 0; k < kPMB; ++k)
+              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < kPMB; ++k) red[sidx * GM + g + k * Gm] = acc[k];
+        }
+        __syncthreads();
+        for (int width = S; width > 1;) {   // fixed-shape pairwise tree over the splits
+          const int half = (width + 1) >> 1;
+          for (int t = tid; t < (width - half) * GM; t += kPT) red[t] += red[t + half * GM];
+          __syncthreads();
+          width = half;
+        }
+        for (int qq = tid; qq < Ml; qq += kPT) d.colpart[(long)it * m.m_max + lidx[r0 + qq]] = (double)red[qq];
+        __syncthreads();
+      }
+    }
+  }
+  if (!barrier(4)) return;
+
+  // ---- F: per (slice, measurement): C = p_D cnorm (sum of the live tile
+  // partials in tile order), the normaliser, ginv and the dW order key
+  {
+    const double cs = m.p_d * m.cnorm;
+    R* ginv = static_cast<R*>(d.ginv);
+    const long units = a.direct ? (long)a.M : (long)K * m.m_max;
+    for (long u = gw; u < units; u += nwarps) {
+      const int j = a.direct ? 0 : (int)(u / m.m_max);
+      const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+      if (p >= slice_M(d, j)) continue;   // uniform over the warp
+      double c = 0.0;
+#pragma unroll 4
+      for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
+        const unsigned bits = __ldcg(d.gbits + (long)it * W + (p >> 5));
+        if ((bits >> (p & 31)) & 1u) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+      }
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+      if (lane == 0) {
+        c *= cs;
+        d.C[j * m.m_max + p] = c;
+        d.Cused[j * m.m_max + p] = c;
+        const double den = d.kap[j] + c;
+        ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
+        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
+      }
+    }
+    if (bid == 0) {
+      // counters: pairs, particles, measurements, updates
+      unsigned long long n = 0, pairs = 0, meas = 0;
+      for (int j = tid; j < K; j += kPT) {
+        const unsigned long long Mj = (unsigned long long)slice_M(d, j);
+        n += (unsigned long long)npred_s[j];
+        pairs += (unsigned long long)npred_s[j] * Mj;
+        meas += Mj;
+      }
+      n = warp_sum(n);
+      pairs = warp_sum(pairs);
+      meas = warp_sum(meas);
+      __shared__ unsigned long long cst[3][kPT / 32];
+      if (lane == 0) {
+        cst[0][wid] = pairs;
+        cst[1][wid] = n;
+        cst[2][wid] = meas;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long s0 = 0, s1 = 0, s2 = 0;
+        for (int k = 0; k < kPT / 32; ++k) {
+          s0 += cst[0][k];
+          s1 += cst[1][k];
+          s2 += cst[2][k];
+        }
+        d.stats[0] += s0;
+        d.stats[1] += s1;
+        d.stats[2] += s2;
+        d.stats[3] += 1ull;
+      }
+    }
+  }
+  if (!barrier(5)) return;
+
+  // ---- G: pass 2 (Eq. 8) per tile: the live measurements from the gate
+  // bits, updated weights to their slots, tile sum and largest weight
+  {
+    int* lidx = reinterpret_cast<int*>(smem);                          // [m_max]
+    Z4<R>* zs = reinterpret_cast<Z4<R>*>(lidx + ((m.m_max + 7) & ~7));   // [m_max]
+    const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
+    R* __restrict__ wu = static_cast<R*>(d.wu);
+    const R miss = cc.miss;
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int t = it - ipref[j];
+      const int cnt = min(256, npred_s[j] - t * 256);
+      const long base = (long)j * m.pe_cap + (long)t * 256;
+      __syncthreads();
+      const int nl = tile_bits(it, j, lidx);
+      const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+      for (int e = tid; e < nl; e += kPT) {
+        const int p = lidx[e];
+        const V2<R> z = Z[p];
+        zs[e] = Z4<R>{z.a, z.b, ginv[j * m.m_max + p], (R)0};
+      }
+      __syncthreads();
+      R wv = 0;
+      if (tid < cnt) {
+        const P4<R> q = geo[base + tid];
+        R a0 = 0, a1 = 0;
+        for (int e = 0; e < nl; ++e) {
+          const Z4<R> za = zs[e];
+          const R v = exp2_neg(Q(za.z0, za.z1, q.h0, q.h1, q.h1lo)) * za.g;
+          if (lidx[e] & 1) a1 += v; else a0 += v;
+        }
+        wv = (miss + (a0 + a1)) * q.w;
+        wu[(long)j * m.pe_cap + d.perm[base + tid]] = wv;
+      }
+      // tile sum and largest weight: warps in the kernel's precision, warp
+      // totals in FP64 in warp order
+      R sv = wv, mv = wv;
+      for (int o = 16; o > 0; o >>= 1) {
+        sv += __shfl_down_sync(0xffffffffu, sv, o);
+        const R v2 = __shfl_down_sync(0xffffffffu, mv, o);
+        mv = v2 > mv ? v2 : mv;
+      }
+      if (lane == 0) {
+        dred[wid] = (double)sv;
+        dredm[wid] = (double)mv;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0, mx = 0.0;
+        for (int k = 0; k < kPT / 32; ++k) {
+          s += dred[k];
+          mx = fmax(mx, dredm[k]);
+        }
+        d.rowpart[it] = s;
+        d.rowmax[it] = mx;
+      }
+    }
+  }
+  if (!barrier(6)) return;
+
+  // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
+  // LT_j = min(round(N^j), labels with dW > 0)
+  for (int j = bid; j < K; j += nb) {
+    double s = 0.0, mx = 0.0;
+    for (int it = ipref[j] + tid; it < ipref[j + 1]; it += kPT) {
+      s += __ldcg(d.rowpart + it);
+      mx = fmax(mx, __ldcg(d.rowmax + it));
+    }
+    int npos = 0;
+    const int M = slice_M(d, j);
+    for (int p = tid; p < M; p += kPT) npos += __ldcg(d.dwkey + j * m.m_max + p) > 0ull ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    npos = warp_sum(npos);
+    __syncthreads();
+    if (lane == 0) {
+      dred[wid] = s;
+      dredm[wid] = mx;
+      wcnt[wid] = npos;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0, tm = 0.0;
+      int np = 0;
+      for (int k = 0; k < kPT / 32; ++k) {
+        t += dred[k];
+        tm = fmax(tm, dredm[k]);
+        np += wcnt[k];
+      }
+      d.mass[j] = t;
+      int L, sc;
+      resample_plan(d.rho[j], d.lmax[j], npred_s[j], t, tm, L, sc);
+      d.rs_mass[j] = t;
+      d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
+      d.rs_s[j] = sc;
+      d.rs_L[j] = L;
+      long long LT = llround(t);
+      if (LT > np) LT = np;
+      if (LT < 0) LT = 0;
+      d.nsel[j] = (int)LT;
+    }
+    __syncthreads();
+  }
+  if (!barrier(7)) return;
+
+  // ---- I: selection ranks (Step 3: the LT largest dW, ties to the lower
+  // label) per measurement; CDF chunk totals per slot chunk
+  {
+    const long units = a.direct ? (long)a.M : (long)K * m.m_max;
+    for (long u = gw; u < units; u += nwarps) {
+      const int j = a.direct ? 0 : (int)(u / m.m_max);
+      const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+      const int M = slice_M(d, j);
+      if (p >= M) continue;
+      const unsigned long long* key = d.dwkey + (long)j * m.m_max;
+      const unsigned long long v = __ldcg(key + p);
+      int c = 0;
+#pragma unroll 4
+      for (int q = lane; q < M; q += 32) {
+        const unsigned long long w2 = __ldcg(key + q);
+        c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
+      }
+      const int rank = warp_sum(c);
+      if (lane == 0) {
+        const bool take = v > 0ull && rank < __ldcg(d.nsel + j);
+        d.selrank[j * m.m_max + p] = take ? rank : -1;
+        if (take) d.sel[j * m.m_max + rank] = p;
+      }
+    }
+    unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
+    const R* wu = static_cast<const R*>(d.wu);
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int i = (it - ipref[j]) * 256 + tid;
+      const unsigned long long q = i < npred_s[j] ? scaled_floor(wu[(long)j * m.pe_cap + i], d.rs_s[j]) : 0ull;
+      unsigned long long tot = 0;
+      block_scan_u64<R>(q, wt, &tot);
+      if (tid == 0) d.pcsum[it] = tot;
+    }
+  }
+  if (!barrier(8)) return;
+
+  // ---- J: pass 3 per tile (Eq. 18 label sums of the selected labels that
+  // can reach the tile, offsets from the label's point); CDF chunk offsets
+  // per slice (the last CTAs)
+  {
+    for (int j = nb - 1 - bid; j >= 0 && j < K; j += nb) {
+      unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
+      unsigned long long carry = 0ull;
+      for (int c0 = ipref[j]; c0 < ipref[j + 1]; c0 += kPT) {
+        const int c = c0 + tid;
+        const unsigned long long v = c < ipref[j + 1] ? __ldcg(d.pcsum + c) : 0ull;
+        unsigned long long tot = 0;
+        const unsigned long long incl = block_scan_u64<R>(v, wt, &tot);
+        if (c < ipref[j + 1]) d.pcoff[c] = carry + incl - v;
+        carry += tot;
+      }
+      if (tid == 0) {
+        d.rs_Qn[j] = carry;
+        const Recip r = make_recip(carry);
+        d.rs_rcp[2 * j] = r.d;
+        d.rs_rcp[2 * j + 1] = r.v;
+      }
+      __syncthreads();
+    }
+    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);               // [256]
+    St4<R>* sx = reinterpret_cast<St4<R>*>(sp + 256);          // [256]
+    int* lidx = reinterpret_cast<int*>(sx + 256);              // [m_max] live measurements
+    int* lr = lidx + ((m.m_max + 7) & ~7);                      // [m_max] live selected ranks
+    const St4<R>* __restrict__ xs = static_cast<const St4<R>*>(d.x_alt);
+    constexpr int LB = 2;   // labels per thread group
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int ns = __ldcg(d.nsel + j);
+      if (ns <= 0) continue;   // uniform over the block
+      const int t = it - ipref[j];
+      const int cnt = min(256, npred_s[j] - t * 256);
+      const long base = (long)j * m.pe_cap + (long)t * 256;
+      __syncthreads();
+      const int nl = tile_bits(it, j, lidx);
+      if (tid < cnt) {
+        sp[tid] = geo[base + tid];
+        sx[tid] = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+      }
+      // the selected labels among the live measurements, in rank order
+      if (tid == 0) nlive_s = 0;
+      __syncthreads();
+      for (int e = tid; e < nl; e += kPT) {
+        const int r = __ldcg(d.selrank + j * m.m_max + lidx[e]);
+        if (r >= 0) lr[atomicAdd(&nlive_s, 1)] = r;
+      }
+      __syncthreads();
+      const int nr = nlive_s;
+      if (nr == 0) continue;   // uniform
+      // ranks in increasing order (insertion by one thread: nr is small)
+      if (tid == 0)
+        for (int x1 = 1; x1 < nr; ++x1) {
+          const int v = lr[x1];
+          int y = x1 - 1;
+          while (y >= 0 && lr[y] > v) {
+            lr[y + 1] = lr[y];
+            --y;
+          }
+          lr[y + 1] = v;
+        }
+      __syncthreads();
+      const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
+      const int ng = (nr + LB - 1) / LB;
+      int nsplit = 1;
+      while (nsplit * 2 <= 32 && nsplit * 2 * ng <= kPT) nsplit *= 2;
+      const int gpr = kPT / nsplit;
+      const int rl = tid / nsplit, split = tid % nsplit;
+      for (int g0 = 0; g0 < ng; g0 += gpr) {
+        const int g = g0 + rl;
+        R s[LB][5];
+        R z0[LB], z1[LB], px[LB], py[LB];
+#pragma unroll
+        for (int k = 0; k < LB; ++k) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) s[k][c] = 0;
+          const int qq = g * LB + k;
+          V2<R> z = {0, 0};
+          if (g < ng && qq < nr) z = Z[__ldcg(d.sel + j * m.m_max + lr[qq])];
+          z0[k] = z.a;
+          z1[k] = z.b;
+          meas_point<R>(m, z, px[k], py[k]);
+        }
+        if (g < ng) {
+          for (int i = split; i < cnt; i += nsplit) {
+            const P4<R> q = sp[i];
+            const St4<R> st = sx[i];
+#pragma unroll
+            for (int k = 0; k < LB; ++k) {
+              const R ew = exp2_neg(Q(z0[k], z1[k], q.h0, q.h1, q.h1lo)) * q.w;
+              s[k][0] += ew;
+              s[k][1] = fma(ew, st.x - px[k], s[k][1]);
+              s[k][2] = fma(ew, st.vx, s[k][2]);
+              s[k][3] = fma(ew, st.y - py[k], s[k][3]);
+              s[k][4] = fma(ew, st.vy, s[k][4]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < LB; ++k)
+#pragma unroll
+          for (int c = 0; c < 5; ++c)
+            for (int o = nsplit >> 1; o > 0; o >>= 1) s[k][c] += __shfl_down_sync(0xffffffffu, s[k][c], o, nsplit);
+        if (split == 0 && g < ng) {
+#pragma unroll
+          for (int k = 0; k < LB; ++k) {
+            const int qq = g * LB + k;
+            if (qq < nr) {
+              double* o = d.spart + ((long)it * m.m_max + lr[qq]) * 5;
+#pragma unroll
+              for (int c = 0; c < 5; ++c) o[c] = (double)s[k][c];
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!barrier(9)) return;
+
+  // ---- K: estimates (Eq. 18) per selected label: the live tile partials in
+  // tile order (FP64 shuffle tree); one filter: the output in ascending
+  // label order.  Offspring ends per slot chunk (exact integer CDF).
+  {
+    St4<R>* est = static_cast<St4<R>*>(d.est_local);
+    const long units = (long)K * m.m_max;
+    for (long u = gw; u < units; u += nwarps) {
+      const int j = (int)(u / m.m_max);
+      const int r = (int)(u - (long)j * m.m_max);
+      const int nsel = __ldcg(d.nsel + j);
+      if (a.direct && r == 0 && lane == 0) {
+        *d.out_count = nsel;
+        if (a.d_count) *a.d_count = nsel;
+      }
+      if (r >= nsel) continue;   // uniform over the warp
+      const int p = __ldcg(d.sel + j * m.m_max + r);
+      int below = 0;
+      if (a.direct) {
+        for (int t = lane; t < nsel; t += 32) below += __ldcg(d.sel + j * m.m_max + t) < p ? 1 : 0;
+        below = warp_sum(below);
+      }
+      const V2<R> z = slice_Z<R>(d, j)[p];
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
+        const unsigned bits = __ldcg(d.gbits + (long)it * W + (p >> 5));
+        if ((bits >> (p & 31)) & 1u) {
+          const double* q = d.spart + ((long)it * m.m_max + r) * 5;
+          a0 += __ldcg(q);
+          a1 += __ldcg(q + 1);
+          a2 += __ldcg(q + 2);
+          a3 += __ldcg(q + 3);
+          a4 += __ldcg(q + 4);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, o);
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        a2 += __shfl_down_sync(0xffffffffu, a2, o);
+        a3 += __shfl_down_sync(0xffffffffu, a3, o);
+        a4 += __shfl_down_sync(0xffffffffu, a4, o);
+      }
+      if (lane == 0) {
+        R px, py;
+        meas_point<R>(m, z, px, py);
+        St4<R> o;
+        if (a0 > 0.0) {
+          if constexpr (sizeof(R) == 4) {
+            const float inv = 1.0f / (float)a0;
+            o.x = px + (float)a1 * inv;
+            o.vx = (float)a2 * inv;
+            o.y = py + (float)a3 * inv;
+            o.vy = (float)a4 * inv;
+          } else {
+            o.x = (R)((double)px + a1 / a0);
+            o.vx = (R)(a2 / a0);
+            o.y = (R)((double)py + a3 / a0);
+            o.vy = (R)(a4 / a0);
+          }
+        } else {
+          o = St4<R>{px, (R)0, py, (R)0};
+        }
+        est[u] = o;
+        if (a.direct && below < a.cap) {
+          a.out_states[4 * below + 0] = o.x;
+          a.out_states[4 * below + 1] = o.vx;
+          a.out_states[4 * below + 2] = o.y;
+          a.out_states[4 * below + 3] = o.vy;
+          a.out_labels[below] = p;
+        }
+      }
+    }
+    unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
+    const R* wu = static_cast<const R*>(d.wu);
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int i = (it - ipref[j]) * 256 + tid;
+      const long g = (long)j * m.pe_cap + i;
+      const bool live = i < npred_s[j];
+      const unsigned long long q = live ? scaled_floor(wu[g], d.rs_s[j]) : 0ull;
+      const unsigned long long Qi = __ldcg(d.pcoff + it) + block_scan_u64<R>(q, wt, nullptr);
+      if (live) {
+        const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
+        const unsigned long long Qn = __ldcg(d.rs_Qn + j);
+        const Recip rq{__ldcg(d.rs_rcp + 2 * j), __ldcg(d.rs_rcp + 2 * j + 1), Qn ? __clzll((long long)Qn) : 0};
+        d.child_end[g] = offspring_end(Qi, Qn, (unsigned long long)d.rs_L[j], U, rq);
+      }
+    }
+  }
+  if (!barrier(10)) return;
+
+  // ---- L: children gathered from their parents (a warp per 32 consecutive
+  // parents, children written as one contiguous range), weight N^j / L_j;
+  // counts and the step counter for the next step
+  {
+    const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
+    St4<R>* x = static_cast<St4<R>*>(d.x);
+    R* w = static_cast<R*>(d.w);
+    if (bid == 0)
+      for (int j = tid; j < K; j += kPT) d.n_cur[j] = d.rs_L[j];
+    for (int it = bid; it < nitems; it += nb) {
+      const int j = item_pe(ipref, K, it);
+      const int n = npred_s[j];
+      const int L = d.rs_L[j];
+      if (L == 0) continue;   // uniform over the block
+      const int wb = (it - ipref[j]) * 256 + (tid & ~31);
+      if (wb >= n) continue;   // uniform over the warp
+      const long base = (long)j * m.pe_cap;
+      const int i = wb + lane;
+      const bool live = i < n;
+      const int ce = __ldcg(d.child_end + base + (live ? i : n - 1));
+      const int c0 = __shfl_sync(0xffffffffu, wb > 0 ? __ldcg(d.child_end + base + wb - 1) : 0, 0);
+      const int c1 = __shfl_sync(0xffffffffu, ce, 31);
+      const St4<R> s = live ? xp[base + i] : St4<R>{0, 0, 0, 0};
+      const R wn = (R)d.rs_wn[j];
+      for (int t0 = c0; t0 < c1; t0 += 32) {
+        const int t = t0 + lane;
+        int lo = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          const int e = __shfl_sync(0xffffffffu, ce, lo + st - 1);
+          if (e <= t) lo += st;
+        }
+        const R sx = __shfl_sync(0xffffffffu, s.x, lo), svx = __shfl_sync(0xffffffffu, s.vx, lo);
+        const R sy = __shfl_sync(0xffffffffu, s.y, lo), svy = __shfl_sync(0xffffffffu, s.vy, lo);
+        if (t < c1) {
+          x[base + t] = St4<R>{sx, svx, sy, svy};
+          w[base + t] = wn;
+          d.parent[base + t] = wb + lo;
+        }
+      }
+    }
+    // every reader of this step's counter finished before barrier 10
+    if (bid == 0 && tid == 0) {
+      *d.step += 1ull;
+      atomicAdd(d.ptimes + 11, gtimer() - t_prev);
+    }
+  }
+}
+
+// Dynamic shared memory of the kernel for a handle's m_max (the largest of
+// the phases' layouts).
+template <class R> size_t persist_smem(int m_max) {
+  const size_t mm = ((size_t)m_max + 7) & ~(size_t)7;
+  const size_t a = 8 * kCells * sizeof(int);                                         // D
+  const size_t e = 256 * sizeof(P4<R>) + kPT * kPMB * sizeof(R) + mm * sizeof(int);  // E
+  const size_t g = mm * sizeof(int) + mm * sizeof(Z4<R>);                            // G
+  const size_t j = 256 * sizeof(P4<R>) + 256 * sizeof(St4<R>) + 2 * mm * sizeof(int);  // J
+  size_t s = a;
+  if (e > s) s = e;
+  if (g > s) s = g;
+  if (j > s) s = j;
+  return (s + 127) & ~(size_t)127;
+}
+
+template <class R, int RB> static void* persist_fn() { return reinterpret_cast<void*>(&k_step_grid<R, RB>); }
+
+template <class R> static void* persist_kernel(int rb) {
+  switch (rb) {
+    case 1: return persist_fn<R, 1>();
+    case 2: return persist_fn<R, 2>();
+    case 3: return persist_fn<R, 3>();
+    default: return persist_fn<R, 0>();
+  }
+}
+
+// CTAs of the cooperative launch: co-resident blocks per SM x SMs (0 if the
+// kernel cannot be launched with this shared memory).
+template <class R> int persist_grid(const Model& m) {
+  void* fn = persist_kernel<R>(model_flag(m));
+  const size_t smem = persist_smem<R>(m.m_max);
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kPT, smem) != cudaSuccess) return 0;
+  if (per > 4) per = 4;
+  return per * sms;
+}
+
+template <class R>
+cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
+                           const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
+                           unsigned long long base, bool direct, cudaStream_t s) {
+  PersistArgs<R> a{Z, M, noise, u, out_states, out_labels, cap, d_count, base, direct ? 1 : 0};
+  Dev dd = d;
+  Model mm = m;
+  void* args[] = {&dd, &mm, &a};
+  return cudaLaunchCooperativeKernel(persist_kernel<R>(model_flag(m)), dim3(grid), dim3(kPT), args,
+                                     persist_smem<R>(m.m_max), s);
+}
+
+int persist_barriers() { return kPhases - 1; }
+
+template size_t persist_smem<float>(int);
+template size_t persist_smem<double>(int);
+template int persist_grid<float>(const Model&);
+template int persist_grid<double>(const Model&);
+template cudaError_t launch_persist<float>(const Dev&, const Model&, int, const float*, int, const float*,
+                                           const uint32_t*, float*, int*, int, int*, unsigned long long, bool,
+                                           cudaStream_t);
+template cudaError_t launch_persist<double>(const Dev&, const Model&, int, const double*, int, const double*,
+                                            const uint32_t*, double*, int*, int, int*, unsigned long long, bool,
+                                            cudaStream_t);
+
+}  // namespace phd

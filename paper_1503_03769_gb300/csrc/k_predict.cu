@@ -19,9 +19,6 @@
 
 namespace phd {
 
-template <class R> __device__ __forceinline__ R slice_bw(const Dev& d, int j);
-template <> __device__ __forceinline__ float slice_bw<float>(const Dev& d, int j) { return d.bwf[j]; }
-template <> __device__ __forceinline__ double slice_bw<double>(const Dev& d, int j) { return d.bwd[j]; }
 
 template <class R>
 __global__ void __launch_bounds__(256) k_predict(Dev d, Model m, const R* __restrict__ noise) {

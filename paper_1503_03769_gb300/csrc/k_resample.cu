@@ -32,32 +32,6 @@ namespace phd {
 // chunk totals of q_i = floor(w_i 2^s), an exclusive scan of the totals per
 // PE, then every chunk rescans its own q_i and turns Q_i into offspring ends.
 template <class R>
-__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long* wt,
-                                                             unsigned long long* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned long long incl = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wt[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    unsigned long long u = lane < nw ? wt[lane] : 0ull;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long t = __shfl_up_sync(0xffffffffu, u, o);
-      if (lane >= o) u += t;
-    }
-    if (lane < nw) wt[lane] = u;
-  }
-  __syncthreads();
-  const unsigned long long r = (wid > 0 ? wt[wid - 1] : 0ull) + incl;
-  if (total) *total = wt[nw - 1];
-  __syncthreads();
-  return r;
-}
-
-template <class R>
 __global__ void __launch_bounds__(kChunk) k_rs_q(Dev d, Model m) {
   pdl_enter();
   __shared__ int pref[kMaxPE + 1];

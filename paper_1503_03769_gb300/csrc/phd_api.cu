@@ -44,7 +44,9 @@ struct phd_handle {
   unsigned long long timer_calls = 0;
   unsigned long long launches = 0;
   bool fused_ok = false;   // the fused step kernel fits this configuration
-  int path = 0;            // PHD_PATH_AUTO / PHD_PATH_STAGED / PHD_PATH_FUSED
+  int pgrid = 0;           // CTAs of the grid path's step kernel (0: unavailable)
+  unsigned long long pbar_count = 0;  // its barrier count after the launches so far
+  int path = 0;            // PHD_PATH_AUTO / PHD_PATH_STAGED / PHD_PATH_FUSED / PHD_PATH_GRID
   bool have_update = false;
   int batch_runs = 0;      // > 0: a batch of independent one-PE filters
   std::vector<int> slice_J;  // births per step of each slice (host copy)
@@ -145,6 +147,14 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.hdone = cv.take<unsigned int>(K);
   t.geo_s = cv.take<char>(K * P, 4 * rs);
   t.geo = cv.take<char>(K * P, 4 * rs);
+  t.gwords = (int)((Mm + 31) / 32);
+  t.pchist = cv.take<int>(items * 256);
+  t.bintot = cv.take<int>(K * 256);
+  t.gbits = cv.take<unsigned int>(items * (size_t)t.gwords);
+  t.pcsum = cv.take<unsigned long long>(items);
+  t.pcoff = cv.take<unsigned long long>(items);
+  t.pbar = cv.take<unsigned long long>(1);
+  t.ptimes = cv.take<unsigned long long>(16);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -366,9 +376,11 @@ phd_status read_device_error(phd_handle* h) {
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err == 0) return PHD_OK;
   PHD_CUDA(h, cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
-  // a wait that gave up may have left the grid barrier mid-count (and an
+  // a wait that gave up may have left the grid barriers mid-count (and an
   // injected fault its flag)
   PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 4 * sizeof(unsigned int), h->stream));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.pbar, 0, sizeof(unsigned long long), h->stream));
+  h->pbar_count = 0;
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (err & phd::kErrNonFinite) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");
@@ -588,7 +600,48 @@ phd_status run_step_body(phd_handle* h) {
 }
 
 phd_status stage_z_only(phd_handle* h, const void* Z, int M);
-bool use_fused(const phd_handle* h) { return h->fused_ok && !h->m.learned && h->path != PHD_PATH_STAGED; }
+bool use_fused(const phd_handle* h) {
+  return h->fused_ok && !h->m.learned && (h->path == PHD_PATH_AUTO || h->path == PHD_PATH_FUSED);
+}
+bool use_grid(const phd_handle* h) {
+  return h->pgrid > 0 && !h->m.learned && (h->path == PHD_PATH_GRID || (h->path == PHD_PATH_AUTO && !use_fused(h)));
+}
+
+// One launch of the grid path's step kernel.  One filter (direct): the scan
+// at Z, the estimates to states / labels (cap) and the count to d_count;
+// a batch: the scans staged by k_stage_zb, the outputs by k_batch_out.
+phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u, void* states,
+                    int* labels, int cap, int* d_count) {
+  const bool timed = h->timer;
+  const bool direct = h->batch_runs == 0;
+  cudaError_t e = cudaSuccess;
+  if (timed) {
+    if (h->ev_used >= 4096) e = drain_timer(h);
+    if (e == cudaSuccess && h->ev_used == h->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+      e = cudaEventCreate(&p.first);
+      if (e == cudaSuccess) e = cudaEventCreate(&p.second);
+      if (e == cudaSuccess) h->ev.push_back(p);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].first, h->stream);
+  }
+  if (e == cudaSuccess)
+    e = is_fp64(h) ? phd::launch_persist<double>(h->d, h->m, h->pgrid, static_cast<const double*>(Z), M,
+                                                 static_cast<const double*>(noise), u, static_cast<double*>(states),
+                                                 labels, cap, d_count, h->pbar_count, direct, h->stream)
+                   : phd::launch_persist<float>(h->d, h->m, h->pgrid, static_cast<const float*>(Z), M,
+                                                static_cast<const float*>(noise), u, static_cast<float*>(states),
+                                                labels, cap, d_count, h->pbar_count, direct, h->stream);
+  if (e == cudaSuccess && timed) {
+    e = cudaEventRecord(h->ev[h->ev_used].second, h->stream);
+    if (e == cudaSuccess) ++h->ev_used;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "grid step");
+  h->pbar_count += (unsigned long long)phd::persist_barriers() * (unsigned long long)h->pgrid;
+  h->launches += 1;
+  h->have_update = true;
+  return PHD_OK;
+}
 
 // One fused launch of S steps.  With zoff == NULL: one step of M rows at Z.
 phd_status run_fused(phd_handle* h, const void* Z, const int* zoff, int M, int S, const void* noise,
@@ -638,12 +691,17 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
                        const uint32_t* xu, void* d_states, int* d_labels, int cap, int* d_count) {
   phd_status st;
   const bool fused = use_fused(h);
+  const bool grid = !fused && use_grid(h);
   if (fused) {
     // the kernel writes the count to the caller's buffer and the workspace
     const bool direct = cap > 0 && d_states && d_labels;
     st = run_fused(h, Z, nullptr, M, 1, noise, u, xu, direct ? d_states : h->out_states,
                    direct ? d_labels : h->out_labels, d_count ? d_count : h->d.out_count,
                    direct ? cap : h->cfg.m_max);
+  } else if (grid) {
+    const bool direct = cap > 0 && d_states && d_labels;
+    st = run_grid(h, Z, M, noise, u, direct ? d_states : h->out_states, direct ? d_labels : h->out_labels,
+                  direct ? cap : h->cfg.m_max, d_count);
   } else if (noise || u || xu) {
     if (h->m.learned) {
       st = stage_z_only(h, Z, M);
@@ -674,7 +732,7 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
   }
   if (st != PHD_OK) return st;
   h->have_update = true;
-  if (d_count && !fused)
+  if (d_count && !fused && !grid)
     PHD_CUDA(h, cudaMemcpyAsync(d_count, h->d.out_count, sizeof(int), cudaMemcpyDefault, h->stream));
   return PHD_OK;
 }
@@ -751,6 +809,8 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
   if (e == cudaSuccess && h->m.K > 1 && h->m.exchange_frac > 0) e = phd::prepare_exchange(h->m);
   if (e == cudaSuccess)
     h->fused_ok = is_fp64(h) ? phd::fused_eligible<double>(h->m, h->device) : phd::fused_eligible<float>(h->m, h->device);
+  if (e == cudaSuccess && h->m.K == 1)
+    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m) : phd::persist_grid<float>(h->m);
   (void)cudaGetLastError();   // an ineligible attribute query leaves no sticky error
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
   phd::Anchor tab[phd::kAnchors];
@@ -970,17 +1030,19 @@ phd_status phd_run(phd_handle* h, const void* d_Z, const int32_t* d_offsets, int
 
 phd_status phd_set_path(phd_handle* h, int32_t path) {
   if (!h) return PHD_ERR_INVALID_ARG;
-  if (path != PHD_PATH_AUTO && path != PHD_PATH_STAGED && path != PHD_PATH_FUSED)
+  if (path != PHD_PATH_AUTO && path != PHD_PATH_STAGED && path != PHD_PATH_FUSED && path != PHD_PATH_GRID)
     return fail(h, PHD_ERR_INVALID_ARG, "unknown path");
   if (path == PHD_PATH_FUSED && !h->fused_ok)
     return fail(h, PHD_ERR_INVALID_ARG, "the fused step kernel does not fit this configuration");
+  if (path == PHD_PATH_GRID && h->pgrid <= 0)
+    return fail(h, PHD_ERR_INVALID_ARG, "the grid step kernel needs a one-PE filter or a batch");
   h->path = path;
   return PHD_OK;
 }
 
 phd_status phd_get_path(phd_handle* h, int32_t* path) {
   if (!h || !path) return PHD_ERR_INVALID_ARG;
-  *path = use_fused(h) ? PHD_PATH_FUSED : PHD_PATH_STAGED;
+  *path = use_fused(h) ? PHD_PATH_FUSED : use_grid(h) ? PHD_PATH_GRID : PHD_PATH_STAGED;
   return PHD_OK;
 }
 
@@ -1131,10 +1193,20 @@ phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
   return read_device_error(h);
 }
 
+phd_status phd_get_phase_times(phd_handle* h, double* h_ms, int32_t n) {
+  if (!h || !h_ms || n < 0 || n > 12) return PHD_ERR_INVALID_ARG;
+  unsigned long long v[16] = {};
+  PHD_CUDA(h, cudaMemcpyAsync(v, h->d.ptimes, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  PHD_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < n; ++k) h_ms[k] = 1e-6 * (double)v[k];
+  return PHD_OK;
+}
+
 phd_status phd_reset_stats(phd_handle* h) {
   if (!h) return PHD_ERR_INVALID_ARG;
   PHD_CUDA(h, drain_timer(h));
   PHD_CUDA(h, cudaMemsetAsync(h->d.stats, 0, 5 * sizeof(unsigned long long), h->stream));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.ptimes, 0, 16 * sizeof(unsigned long long), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->launches = 0;
   h->timer_ms = 0.0;
@@ -1338,6 +1410,9 @@ phd_status phd_batch_init(phd_handle** out, const phd_config* cfgs, int32_t runs
   carve(e, static_cast<char*>(ws), &h->d, &h->out_states, &h->out_labels, runs);
   cudaError_t err = cudaGetDevice(&h->device);
   if (err == cudaSuccess) err = is_fp64(h) ? phd::prepare_kernels<double>(h->m) : phd::prepare_kernels<float>(h->m);
+  if (err == cudaSuccess)
+    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m) : phd::persist_grid<float>(h->m);
+  (void)cudaGetLastError();
   if (err == cudaSuccess) err = cudaMemsetAsync(ws, 0, need, h->stream);
   phd::Anchor tab[phd::kAnchors];
   phd::fill_anchor_table(tab);
@@ -1374,7 +1449,10 @@ phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* 
   if (e != cudaSuccess) return cuda_fail(h, e, "stage_zb");
   h->launches += 1;
   phd_status st = PHD_OK;
-  if (d_noise || d_u) {
+  if (use_grid(h)) {
+    st = run_grid(h, nullptr, 0, d_noise, d_u, nullptr, nullptr, 0, nullptr);
+    if (st != PHD_OK) return st;
+  } else if (d_noise || d_u) {
     // caller random numbers: the stages one by one (no graph)
     st = do_predict(h, d_noise);
     if (st == PHD_OK) {

@@ -176,6 +176,15 @@ struct Dev {
   unsigned int* hdone;   // [K] cell-histogram chunks finished per slice (the last scans the slice)
   void* geo_s;           // P4<R> [K*pe_cap] sensor-space geometry and predicted weight, slot order
   void* geo;             // P4<R> [K*pe_cap] the same at each sorted position (read by passes 1-3)
+  // persistent step kernel (k_step_grid): items of 256 particles of every slice
+  int* pchist;           // [max_items][256] cell counts per slot chunk, then their sorted starts
+  int* bintot;           // [K][256] cell totals per slice
+  unsigned int* gbits;   // [max_items][gwords] measurements that reach each sorted tile (gate survivors)
+  unsigned long long* pcsum;  // [max_items] CDF totals per slot chunk
+  unsigned long long* pcoff;  // [max_items] their exclusive offsets within the slice
+  unsigned long long* pbar;   // [1] arrival count of the kernel's grid barriers (only grows)
+  unsigned long long* ptimes; // [16] phase durations summed over launches, ns
+  int gwords;            // words of gbits per tile: ceil(m_max / 32)
 };
 
 enum : int { kErrNonFinite = 1, kErrCapacity = 2, kErrTimeout = 4 };
@@ -905,6 +914,116 @@ __device__ __forceinline__ uint32_t philox_u32(const Model& m, uint32_t a, unsig
 }
 
 // ---------------------------------------------------------------------------
+// Helpers shared by the staged kernels and the persistent step kernel.
+// ---------------------------------------------------------------------------
+constexpr int kCells = 256;   // 16 x 16 cells over measurement space, Morton order
+
+__device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
+  int cx = (int)floorf((h0 - m.f_cell_o0) * m.f_cell_s0);
+  int cy = (int)floorf((h1 - m.f_cell_o1) * m.f_cell_s1);
+  cx = min(max(cx, 0), 15);
+  cy = min(max(cy, 0), 15);
+  int k = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) k |= (((cx >> b) & 1) << (2 * b)) | (((cy >> b) & 1) << (2 * b + 1));
+  return k;
+}
+
+// Exact CDF in three passes over chunks of particles (any PE size):
+// chunk totals of q_i = floor(w_i 2^s), an exclusive scan of the totals per
+// PE, then every chunk rescans its own q_i and turns Q_i into offspring ends.
+template <class R>
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long* wt,
+                                                             unsigned long long* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wt[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long u = lane < nw ? wt[lane] : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += t;
+    }
+    if (lane < nw) wt[lane] = u;
+  }
+  __syncthreads();
+  const unsigned long long r = (wid > 0 ? wt[wid - 1] : 0ull) + incl;
+  if (total) *total = wt[nw - 1];
+  __syncthreads();
+  return r;
+}
+
+// Cartesian point of a measurement, the offset origin of the labelled sums.
+template <class R>
+__device__ __forceinline__ void meas_point(const Model& m, V2<R> z, R& rx, R& ry) {
+  if (m.meas_model == 0) {
+    rx = z.a;
+    ry = z.b;
+  } else {
+    R sn, cs;
+    sincos(z.b, &sn, &cs);
+    rx = (R)m.sx + z.a * cs;
+    ry = (R)m.sy + z.a * sn;
+  }
+}
+
+// Birth weight nu_b / J_j of slice j in the kernel's precision.
+template <class R> __device__ __forceinline__ R slice_bw(const Dev& d, int j);
+template <> __device__ __forceinline__ float slice_bw<float>(const Dev& d, int j) { return d.bwf[j]; }
+template <> __device__ __forceinline__ double slice_bw<double>(const Dev& d, int j) { return d.bwd[j]; }
+
+// Grid-wide barrier over gridDim.x CTAs with a bounded wait (`limit`
+// polls).  Every CTA adds one to a 64-bit arrival count that only grows, so
+// barrier b of a launch completes when the count reaches b * gridDim.x: one
+// release atomic and the acquire polls are the whole cost (no reset, no
+// generation word).  The count is a multiple of gridDim.x between launches; a
+// launch that gave up leaves an error word behind and the host clears both
+// before the next.  Returns false (in every thread of the CTA) when the wait
+// gave up or an error was recorded; the caller then returns from the kernel.
+// `lost` (read by thread 0) makes the CTA leave without arriving, as a PE that
+// died would: the host's failure injection.
+__device__ __forceinline__ bool grid_sync(const Dev& d, long long limit, bool lost) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    if (!lost) {
+      unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.bar);
+      const unsigned long long G = gridDim.x;
+      unsigned long long old;
+      asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(cnt) : "memory");
+      const unsigned long long target = (old / G + 1ull) * G;
+      long long it = 0;
+      for (;;) {
+        unsigned long long c;
+        int e;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
+        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(d.err) : "memory");
+        if (e != 0) break;
+        if (c >= target) {
+          ok = 1;
+          break;
+        }
+        if (++it > limit) {
+          atomicOr(d.err, kErrTimeout);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+
+// ---------------------------------------------------------------------------
 // Launchers (one per stage), instantiated for float and double.
 // ---------------------------------------------------------------------------
 template <class R> cudaError_t launch_predict(const Dev& d, const Model& m, const R* noise, cudaStream_t s);
@@ -940,6 +1059,13 @@ template <class R> cudaError_t prepare_kernels(const Model& m);
 template <class R> cudaError_t prepare_extract();
 cudaError_t prepare_exchange(const Model& m);
 template <class R> bool fused_eligible(const Model& m, int device);
+// persistent step kernel (k_persist.cu): grid size (0: cannot launch), launch
+template <class R> int persist_grid(const Model& m);
+template <class R>
+cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
+                           const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
+                           unsigned long long base, bool direct, cudaStream_t s);
+int persist_barriers();   // grid barriers one launch passes
 void fill_anchor_table(Anchor* tab);
 Model model_from_config(const phd_config& c);
 const char* config_problem(const phd_config& c);

@@ -22,10 +22,10 @@ PHD_OK, PHD_ERR_INVALID_ARG, PHD_ERR_CAPACITY, PHD_ERR_CUDA, PHD_ERR_TIMEOUT, PH
 PHD_MEAS_LINEAR, PHD_MEAS_RANGE_BEARING = 0, 1
 PHD_FP32, PHD_FP64 = 0, 1
 PHD_CK_LOCAL, PHD_CK_GLOBAL = 0, 1
-PHD_PATH_AUTO, PHD_PATH_STAGED, PHD_PATH_FUSED = 0, 1, 2
+PHD_PATH_AUTO, PHD_PATH_STAGED, PHD_PATH_FUSED, PHD_PATH_GRID = 0, 1, 2, 3
 PHD_BIRTH_UNIFORM, PHD_BIRTH_GAUSSIAN = 0, 1
 PHD_XCHG_RING, PHD_XCHG_ALL = 0, 1
-_PATHS = {"auto": PHD_PATH_AUTO, "staged": PHD_PATH_STAGED, "fused": PHD_PATH_FUSED}
+_PATHS = {"auto": PHD_PATH_AUTO, "staged": PHD_PATH_STAGED, "fused": PHD_PATH_FUSED, "grid": PHD_PATH_GRID}
 
 
 class PhdError(RuntimeError):
@@ -125,6 +125,7 @@ ABI = {
     "phd_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),
     "phd_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, _P]),
+    "phd_get_phase_times": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "phd_measure_ex2_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), _P]),
 }
@@ -497,7 +498,7 @@ class ParticlePHD:
     def get_path(self) -> str:
         v = ctypes.c_int32(0)
         self._check(self.L.phd_get_path(self.h, ctypes.byref(v)), "phd_get_path")
-        return {PHD_PATH_STAGED: "staged", PHD_PATH_FUSED: "fused"}[v.value]
+        return {PHD_PATH_STAGED: "staged", PHD_PATH_FUSED: "fused", PHD_PATH_GRID: "grid"}[v.value]
 
     def get_predicted(self):
         X = torch.empty((self.K, self.pe_cap, 4), dtype=self.dtype, device=self.device)
@@ -586,6 +587,15 @@ class ParticlePHD:
 
     def reset_stats(self):
         self._check(self.L.phd_reset_stats(self.h), "phd_reset_stats")
+
+    PHASES = ("predict_keys", "cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2",
+              "mass_plan", "ranks_cdf", "label_sums_offsets", "estimates_offspring", "gather")
+
+    def phase_times(self) -> dict:
+        """Grid path: summed time per phase of the step kernel, ms (phd_get_phase_times)."""
+        v = (ctypes.c_double * 12)()
+        self._check(self.L.phd_get_phase_times(self.h, v, 12), "phd_get_phase_times")
+        return dict(zip(self.PHASES, list(v)))
 
     def set_stage_timer(self, on: bool):
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")

@@ -70,8 +70,9 @@ def gpu_stages(f, w, Z, noise, u, xu, path):
     """Run one step on the GPU and collect its intermediates.
 
     path "staged": phd_predict / phd_update / phd_extract / phd_resample with
-    the intermediates read between the calls; path "fused": one
-    phd_step_inject on the fused kernel, intermediates read afterwards."""
+    the intermediates read between the calls; path "fused" or "grid": one
+    phd_step_inject on that path's step kernel, intermediates read
+    afterwards."""
     dt = npdtype(w)
     g = {}
     g["xs0"], g["ws0"] = f.get_state()
@@ -85,7 +86,7 @@ def gpu_stages(f, w, Z, noise, u, xu, path):
         g["loc_s"], g["loc_l"] = f.get_local_estimates()
         f.resample(u, xu)
     else:
-        assert f.get_path() == "fused"
+        assert f.get_path() == path
         g["states"], g["labels"] = f.step_inject(np.asarray(Z, dt), noise, u, xu)
         g["xp"], g["wp"], g["wu"] = f.get_predicted()
         g["C"], g["mass"] = f.get_update()

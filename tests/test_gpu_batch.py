@@ -29,8 +29,9 @@ def _runs():
     return [w.with_(pe_cap=cap) for w in ws]
 
 
+@pytest.mark.parametrize("path", ["grid", "staged"])
 @pytest.mark.parametrize("autotune", [False, True])
-def test_batch_runs_match_their_oracles(autotune):
+def test_batch_runs_match_their_oracles(autotune, path):
     """Three batched steps, each from generator slices (every run's own size;
     the second shaped like a resampling output); with autotune, the pair
     passes' launch shape is re-chosen after the first step (timed on the
@@ -39,6 +40,7 @@ def test_batch_runs_match_their_oracles(autotune):
     ws = _runs()
     R = len(ws)
     b = ParticlePHDBatch(ws, seed=2)
+    b.set_path(path)
     scs = [scenario.simulate(w, 40 + j, steps=3) for j, w in enumerate(ws)]
     rep = StageReport()
     for k in range(3):

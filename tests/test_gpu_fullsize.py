@@ -46,13 +46,18 @@ def _dense_inputs():
     return w, sc.meas[60], x, wt, noise, scenario.resample_u32(3, 60, 1)
 
 
-@pytest.mark.parametrize("shape", ["autotuned", "fixed"])
+@pytest.mark.parametrize("shape", ["autotuned", "fixed", "grid"])
 def test_dense_full_size_step(shape):
+    """shape: the staged kernels in the autotuner's launch shape or a fixed
+    one, or the grid path's step kernel (what the benchmark times)."""
     from paper_1503_03769_gb300 import ParticlePHD
     w, Z, x, wt, noise, u = _dense_inputs()
     assert len(Z) > 450 and len(x) > 1.5e5
     f = ParticlePHD(w, seed=3, device="cuda:0")
-    assert f.get_path() == "staged"
+    assert f.get_path() == "grid"       # the default path of a one-PE filter this size
+    path = "grid" if shape == "grid" else "staged"
+    if shape != "grid":
+        f.set_path("staged")
     if shape == "autotuned":
         # as the benchmark does: a step on the workload, then the autotuner
         f.set_state([x], [wt])
@@ -61,26 +66,29 @@ def test_dense_full_size_step(shape):
         tuned = f.autotune(3)
         f.extract()
         f.resample(u)
-    else:
+    elif shape == "fixed":
         f.set_tuning(**FIXED)
     f.set_state([x], [wt])
-    g = gpu_stages(f, w, Z, noise, u, None, "staged")
+    g = gpu_stages(f, w, Z, noise, u, None, path)
     rep = StageReport()
     check_step_from_inputs(w, oracle.model(w), [x], [wt], Z, noise, u, None, g, rep)
     st = f.stats()
     f.close()
     assert rep.compared_labels >= 50, rep
     assert st["pairs"] >= 1e8
-    print(f"dense full size ({shape}{'' if shape == 'fixed' else ' ' + str(tuned)}): C {rep.max_c_rel:.2e}, "
+    print(f"dense full size ({shape}{' ' + str(tuned) if shape == 'autotuned' else ''}): C {rep.max_c_rel:.2e}, "
           f"weights {rep.max_w_rel:.2e}, mass {rep.max_mass_rel:.2e}, states {rep.max_state_err:.2e} m, "
           f"{rep.compared_labels} labels")
 
 
-def test_batch_of_32_runs_against_their_oracles():
+@pytest.mark.parametrize("path", ["grid", "staged"])
+def test_batch_of_32_runs_against_their_oracles(path):
     from paper_1503_03769_gb300 import ParticlePHDBatch
     ws = scenario.batch_workloads(seed=1000, runs=32)
     R = len(ws)
     b = ParticlePHDBatch(ws, seed=7)
+    assert b.get_path() == "grid"
+    b.set_path(path)
     rng = np.random.default_rng(7)
     xs, wts, Zs = [], [], []
     for j, w in enumerate(ws):

@@ -77,7 +77,7 @@ def _log_errors(w, path, rep):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_global_linear_stages(precision, path):
     """Global filter, linear sensor: a ragged 2600-particle set, 3 steps."""
     w = scenario.workload("linear4_fp64", precision=precision, n_targets=4,
@@ -198,12 +198,13 @@ def test_range_bearing_stages_many_measurements(path):
     assert rep.compared_labels > 0
 
 
-def test_bearing_branch_cut():
+@pytest.mark.parametrize("path", ["staged", "grid"])
+def test_bearing_branch_cut(path):
     """Particles and measurements on both sides of bearing +-pi: the wrapped
     likelihood must match the oracle's (a missing wrap drops their weights)."""
     w = scenario.workload("dense_rb_100t", n_targets=1, clutter_rate=5.0,
                           particles_per_target=300, birth_count=64)
-    f = _filter(w, 1)
+    f = _filter(w, 1, path)
     m = oracle.model(w)
     rng = np.random.default_rng(1)
     n = 700
@@ -215,7 +216,7 @@ def test_bearing_branch_cut():
     noise = np.zeros((w.pe_cap, 4), np.float32)
     noise[:, 2:] = 0.5
     rep = StageReport()
-    stage_step(f, w, m, [x], [wt], Z, noise, np.array([12345], np.uint32), None, rep)
+    stage_step(f, w, m, [x], [wt], Z, noise, np.array([12345], np.uint32), None, rep, path=path)
     assert rep.compared_labels >= 1
 
 
@@ -518,14 +519,18 @@ def test_fused_run_matches_fused_steps():
         np.testing.assert_array_equal(wa[j], wb[j])
 
 
-def test_fused_and_staged_track_each_other():
-    """Free-running with the same seed: the fused kernel and the staged
-    kernels draw the same Philox numbers and agree on the estimates over a
-    40-scan run of the 16-PE workload, up to near-tie selections (and the
-    divergence a resampling tie-flip starts)."""
+@pytest.mark.parametrize("pair", ["fused-staged", "grid-staged"])
+def test_paths_track_each_other(pair):
+    """Free-running with the same seed: the fused (or grid) step kernel and
+    the staged kernels draw the same Philox numbers and agree on the
+    estimates over a 40-scan run (the 16-PE workload; its one-PE form for the
+    grid path), up to near-tie selections (and the divergence a resampling
+    tie-flip starts)."""
     w = scenario.workload("dist16_10t", steps=40)
+    if pair.startswith("grid"):
+        w = w.with_(num_pe=1, exchange_frac=0.0, pe_cap=16 * w.pe_cap)
     sc = scenario.simulate(w, 31)
-    a, b = _filter(w, 31, "fused"), _filter(w, 31, "staged")
+    a, b = _filter(w, 31, pair.split("-")[0]), _filter(w, 31, "staged")
     same = 0
     for Z in sc.meas:
         sa, la = a.step(Z)
