@@ -103,6 +103,7 @@ template <class R, int RB>
 __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArgs<R> a) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ int ipref[kMaxPE + 1];   // items (256-particle chunks / tiles) per slice, prefix
+  __shared__ int hpref[kMaxPE + 1];   // chunk-histogram rows per slice: 256 x (items rounded up to 4), prefix
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
   __shared__ int wcnt[kPT / 32];
   __shared__ R bsh[4 * (kPT / 32)];
@@ -129,11 +130,14 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
   __syncthreads();
   slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + 255) / 256; });
+  slice_prefix(K, hpref, [&](int j) { return 256 * ((((npred_s[j] + 255) / 256) + 3) & ~3); });
   const int nitems = ipref[K];
+  const long T = d.max_items;   // row stride of the gate bits [word][tile]
+  // chunk histograms: slice j, cell b, chunk c at pchist[hpref[j] + b * hstride(j) + c]
+  auto hstride = [&](int j) { return ((ipref[j + 1] - ipref[j]) + 3) & ~3; };
   const unsigned long long step = *d.step;
   const Cst<R> cc = consts<R>(m);
   const Anchor* __restrict__ tab = static_cast<const Anchor*>(d.anchors);
-  const int W = d.gwords;
 
   // ---- A: prediction, geometry, cell keys, chunk histograms; Z staging
   {
@@ -178,22 +182,24 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         atomicAdd(&hist[k], 1);
       }
       __syncthreads();
-      d.pchist[(long)it * 256 + tid] = hist[tid];
+      d.pchist[hpref[j] + (long)tid * hstride(j) + (it - ipref[j])] = hist[tid];
       __syncthreads();
     }
   }
   if (!barrier(0)) return;
 
   // ---- B: per (slice, cell): total over the slice's chunks (a warp per
-  // unit; each lane sums a contiguous run of chunks, independent loads)
+  // unit; the cell's row of chunk counts is contiguous, read 4 at a time)
   for (long u = gw; u < (long)K * 256; u += nwarps) {
     const int j = (int)(u >> 8), b = (int)(u & 255);
-    const int c0 = ipref[j], nc = ipref[j + 1] - c0;
-    const int per = (nc + 31) / 32;
+    const int4* row = reinterpret_cast<const int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
+    const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
     int tot = 0;
-    for (int k = 0; k < per; ++k) {
-      const int c = lane * per + k;
-      if (c < nc) tot += __ldcg(d.pchist + (long)(c0 + c) * 256 + b);
+#pragma unroll 4
+    for (int q = lane; q < n4; q += 32) {
+      const int4 v = __ldcg(row + q);
+      const int c = 4 * q;
+      tot += (c < nc ? v.x : 0) + (c + 1 < nc ? v.y : 0) + (c + 2 < nc ? v.z : 0) + (c + 3 < nc ? v.w : 0);
     }
     tot = warp_sum(tot);
     if (lane == 0) d.bintot[u] = tot;
@@ -201,33 +207,32 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   if (!barrier(1)) return;
 
   // ---- C: per (slice, cell): the cell's start (cells before it), then each
-  // chunk's start within the cell (chunks before it): pchist in place
+  // chunk's start within the cell (chunks before it), in place: rounds of
+  // 128 chunks, four per lane, a warp scan of the lane totals
   for (long u = gw; u < (long)K * 256; u += nwarps) {
     const int j = (int)(u >> 8), b = (int)(u & 255);
     int base = 0;
     for (int q = lane; q < b; q += 32) base += __ldcg(d.bintot + (long)j * 256 + q);
     base = warp_sum(base);
-    const int c0 = ipref[j], nc = ipref[j + 1] - c0;
-    const int per = (nc + 31) / 32;
-    int mine = 0;
-    for (int k = 0; k < per; ++k) {
-      const int c = lane * per + k;
-      if (c < nc) mine += __ldcg(d.pchist + (long)(c0 + c) * 256 + b);
-    }
-    int incl = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    int run = base + incl - mine;
-    for (int k = 0; k < per; ++k) {
-      const int c = lane * per + k;
-      if (c < nc) {
-        int* e = d.pchist + (long)(c0 + c) * 256 + b;
-        const int v = __ldcg(e);
-        *e = run;
-        run += v;
+    int4* row = reinterpret_cast<int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
+    const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
+    for (int q0 = 0; q0 < n4; q0 += 32) {
+      const int q = q0 + lane;
+      int4 v = q < n4 ? __ldcg(row + q) : int4{0, 0, 0, 0};
+      const int c = 4 * q;
+      if (c >= nc) v.x = 0;
+      if (c + 1 >= nc) v.y = 0;
+      if (c + 2 >= nc) v.z = 0;
+      if (c + 3 >= nc) v.w = 0;
+      const int tot = v.x + v.y + v.z + v.w;
+      int incl = tot;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
       }
+      const int s0 = base + incl - tot;
+      if (q < n4) row[q] = int4{s0, s0 + v.x, s0 + v.x + v.y, s0 + v.x + v.y + v.z};
+      base += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
   if (!barrier(2)) return;
@@ -260,7 +265,8 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       __syncthreads();
       if (live) {
-        const int dst = __ldcg(d.pchist + (long)it * 256 + key) + wc[wid * kCells + key] + rank_w;
+        const int dst = __ldcg(d.pchist + hpref[j] + (long)key * hstride(j) + (it - ipref[j])) +
+                        wc[wid * kCells + key] + rank_w;
         d.perm[(long)j * m.pe_cap + dst] = i;
         geo[(long)j * m.pe_cap + dst] = geo_s[g];
       }
@@ -300,7 +306,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) {
         wcnt[wid] = __popc(bal);
-        if (record && p0 + wid * 32 < M) d.gbits[(long)it * W + (p0 >> 5) + wid] = bal;
+        if (record && p0 + wid * 32 < M) d.gbits[(long)((p0 >> 5) + wid) * T + it] = bal;
       }
       __syncthreads();
       int before = 0, all = 0;
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     int nl = 0;
     for (int w0 = 0; w0 < nwd; w0 += kPT) {
       const int wd = w0 + tid;
-      const unsigned bits = wd < nwd ? __ldcg(d.gbits + (long)it * W + wd) : 0u;
+      const unsigned bits = wd < nwd ? __ldcg(d.gbits + (long)wd * T + it) : 0u;
       const int c = __popc(bits);
       int incl = c;
       for (int o = 1; o < 32; o <<= 1) {
@@ -354,8 +360,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // within the tile, written as FP64
   {
     P4<R>* sp = reinterpret_cast<P4<R>*>(smem);        // [256]
-    R* red = reinterpret_cast<R*>(sp + 256);            // [kPT * kPMB]
-    int* lidx = reinterpret_cast<int*>(red + kPT * kPMB);   // [m_max]
+    int* lidx = reinterpret_cast<int*>(sp + 256);       // [m_max]
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
       const int cnt = min(256, npred_s[j] - (it - ipref[j]) * 256);
@@ -366,52 +371,36 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       if (tid == 0 && nl > 0) atomicAdd(&d.stats[4], (unsigned long long)nl * (unsigned long long)cnt);
       const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
       __syncthreads();
-      for (int r0 = 0; r0 < nl; r0 += 64 * kPMB) {
-        const int Ml = min(64 * kPMB, nl - r0);
-        const int Gm = (Ml + kPMB - 1) / kPMB;   // threads per split
-        const int S = kPT / Gm;                    // splits of the tile
-        const int GM = Gm * kPMB;
-        const int g = tid % Gm, sidx = tid / Gm;
-        R acc[kPMB];
+      // a warp per group of kPMB live measurements, its lanes over the tile's
+      // particles (lane l: particles l, l + 32, ... in order), FP32 sums per
+      // lane, a fixed shuffle tree over the lanes
+      const int ngr = (nl + kPMB - 1) / kPMB;
+      for (int gi = wid; gi < ngr; gi += kPT / 32) {
+        R z0[kPMB], z1[kPMB], acc[kPMB];
 #pragma unroll
-        for (int k = 0; k < kPMB; ++k) acc[k] = 0;
-        if (sidx < S) {
-          R z0[kPMB], z1[kPMB];
-#pragma unroll
-          for (int k = 0; k < kPMB; ++k) {
-            const int qq = g + k * Gm;
-            const V2<R> z = qq < Ml ? Z[lidx[r0 + qq]] : V2<R>{0, 0};
-            z0[k] = z.a;
-            z1[k] = z.b;
-          }
-          int i = sidx;
-          for (; i + S < cnt; i += 2 * S) {
-            const P4<R> qa = sp[i], qb = sp[i + S];
-#pragma unroll
-            for (int k = 0; k < kPMB; ++k)
-              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
-#pragma unroll
-            for (int k = 0; k < kPMB; ++k)
-              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qb.h0, qb.h1, qb.h1lo)), qb.w, acc[k]);
-          }
-          if (i < cnt) {
-            const P4<R> qa = sp[i];
-#pragma unroll
-            for (int k = 0; k < kPMB; ++k)
-              acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
-          }
-#pragma unroll
-          for (int k = 0; k < kPMB; ++k) red[sidx * GM + g + k * Gm] = acc[k];
+        for (int k = 0; k < kPMB; ++k) {
+          const int qq = gi * kPMB + k;
+          const V2<R> z = qq < nl ? Z[lidx[qq]] : V2<R>{0, 0};
+          z0[k] = z.a;
+          z1[k] = z.b;
+          acc[k] = 0;
         }
-        __syncthreads();
-        for (int width = S; width > 1;) {   // fixed-shape pairwise tree over the splits
-          const int half = (width + 1) >> 1;
-          for (int t = tid; t < (width - half) * GM; t += kPT) red[t] += red[t + half * GM];
-          __syncthreads();
-          width = half;
+        for (int i = lane; i < cnt; i += 32) {
+          const P4<R> qa = sp[i];
+#pragma unroll
+          for (int k = 0; k < kPMB; ++k)
+            acc[k] = fma(exp2_neg(Q(z0[k], z1[k], qa.h0, qa.h1, qa.h1lo)), qa.w, acc[k]);
         }
-        for (int qq = tid; qq < Ml; qq += kPT) d.colpart[(long)it * m.m_max + lidx[r0 + qq]] = (double)red[qq];
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPMB; ++k)
+          for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        if (lane < kPMB) {
+          R v = acc[0];
+#pragma unroll
+          for (int k = 1; k < kPMB; ++k) v = lane == k ? acc[k] : v;
+          const int qq = gi * kPMB + lane;
+          if (qq < nl) d.colpart[(long)it * m.m_max + lidx[qq]] = (double)v;
+        }
       }
     }
   }
@@ -427,11 +416,15 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const int j = a.direct ? 0 : (int)(u / m.m_max);
       const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
       if (p >= slice_M(d, j)) continue;   // uniform over the warp
+      // lane l takes tiles l, l + 32, ... of the slice in order; the bit row
+      // of word p / 32 is contiguous over tiles (one load per 32 tiles)
       double c = 0.0;
+      const unsigned* brow = d.gbits + (long)(p >> 5) * T;
 #pragma unroll 4
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const unsigned bits = __ldcg(d.gbits + (long)it * W + (p >> 5));
-        if ((bits >> (p & 31)) & 1u) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+        const unsigned bits = __ldcg(brow + it);
+        const double v = ((bits >> (p & 31)) & 1u) ? __ldcg(d.colpart + (long)it * m.m_max + p) : 0.0;
+        c += v;
       }
       for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
       if (lane == 0) {
@@ -766,8 +759,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       const V2<R> z = slice_Z<R>(d, j)[p];
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+#pragma unroll 2
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const unsigned bits = __ldcg(d.gbits + (long)it * W + (p >> 5));
+        const unsigned bits = __ldcg(brow + it);
         if ((bits >> (p & 31)) & 1u) {
           const double* q = d.spart + ((long)it * m.m_max + r) * 5;
           a0 += __ldcg(q);
@@ -887,7 +882,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
 template <class R> size_t persist_smem(int m_max) {
   const size_t mm = ((size_t)m_max + 7) & ~(size_t)7;
   const size_t a = 8 * kCells * sizeof(int);                                         // D
-  const size_t e = 256 * sizeof(P4<R>) + kPT * kPMB * sizeof(R) + mm * sizeof(int);  // E
+  const size_t e = 256 * sizeof(P4<R>) + mm * sizeof(int);                            // E
   const size_t g = mm * sizeof(int) + mm * sizeof(Z4<R>);                            // G
   const size_t j = 256 * sizeof(P4<R>) + 256 * sizeof(St4<R>) + 2 * mm * sizeof(int);  // J
   size_t s = a;

@@ -148,7 +148,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.geo_s = cv.take<char>(K * P, 4 * rs);
   t.geo = cv.take<char>(K * P, 4 * rs);
   t.gwords = (int)((Mm + 31) / 32);
-  t.pchist = cv.take<int>(items * 256);
+  t.pchist = cv.take<int>(items * 256 + K * 1024);   // rows of each slice rounded up to 4 chunks
   t.bintot = cv.take<int>(K * 256);
   t.gbits = cv.take<unsigned int>(items * (size_t)t.gwords);
   t.pcsum = cv.take<unsigned long long>(items);
