@@ -394,12 +394,12 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
 #pragma unroll
         for (int k = 0; k < kPMB; ++k)
           for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        if (lane < kPMB) {
-          R v = acc[0];
+        if (lane == 0) {   // the tree's totals are in lane 0
 #pragma unroll
-          for (int k = 1; k < kPMB; ++k) v = lane == k ? acc[k] : v;
-          const int qq = gi * kPMB + lane;
-          if (qq < nl) d.colpart[(long)it * m.m_max + lidx[qq]] = (double)v;
+          for (int k = 0; k < kPMB; ++k) {
+            const int qq = gi * kPMB + k;
+            if (qq < nl) d.colpart[(long)it * m.m_max + lidx[qq]] = (double)acc[k];
+          }
         }
       }
     }
