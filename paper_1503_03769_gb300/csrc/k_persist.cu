@@ -296,11 +296,18 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     const int M = slice_M(d, j);
     const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
     int nl = 0;
+    constexpr int kPre = 4;   // rounds whose measurements are fetched up front
+    V2<R> zpre[kPre];
+#pragma unroll
+    for (int r = 0; r < kPre; ++r) zpre[r] = r * kPT + tid < M ? Z[r * kPT + tid] : V2<R>{0, 0};
     for (int p0 = 0; p0 < M; p0 += kPT) {
       const int p = p0 + tid;
       bool keep = false;
       if (p < M) {
-        const V2<R> z = Z[p];
+        V2<R> z = zpre[0];
+#pragma unroll
+        for (int r = 1; r < kPre; ++r) z = p0 == r * kPT ? zpre[r] : z;
+        if (p0 >= kPre * kPT) z = Z[p];
         keep = !m.tune.gate || box_qmin<R, RB>(box, LB.b0, LB.b1, z.a, z.b) < gate_limit<R>(m);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       // of word p / 32 is contiguous over tiles (one load per 32 tiles)
       double c = 0.0;
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-#pragma unroll 4
+#pragma unroll 8
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
         const unsigned bits = __ldcg(brow + it);
         const double v = ((bits >> (p & 31)) & 1u) ? __ldcg(d.colpart + (long)it * m.m_max + p) : 0.0;
@@ -582,7 +589,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // label) per measurement; CDF chunk totals per slot chunk
   {
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    for (long u = gw; u < units; u += nwarps) {
+    for (long u = nwarps - 1 - gw; u < units; u += nwarps) {
       const int j = a.direct ? 0 : (int)(u / m.m_max);
       const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
       const int M = slice_M(d, j);
@@ -590,7 +597,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const unsigned long long* key = d.dwkey + (long)j * m.m_max;
       const unsigned long long v = __ldcg(key + p);
       int c = 0;
-#pragma unroll 4
+#pragma unroll 8
       for (int q = lane; q < M; q += 32) {
         const unsigned long long w2 = __ldcg(key + q);
         c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
@@ -742,7 +749,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   {
     St4<R>* est = static_cast<St4<R>*>(d.est_local);
     const long units = (long)K * m.m_max;
-    for (long u = gw; u < units; u += nwarps) {
+    // warps counted from the end of the grid: the first CTAs also take the
+    // second round of chunk items below
+    for (long u = nwarps - 1 - gw; u < units; u += nwarps) {
       const int j = (int)(u / m.m_max);
       const int r = (int)(u - (long)j * m.m_max);
       const int nsel = __ldcg(d.nsel + j);
@@ -760,7 +769,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const V2<R> z = slice_Z<R>(d, j)[p];
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-#pragma unroll 2
+#pragma unroll 4
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
         const unsigned bits = __ldcg(brow + it);
         if ((bits >> (p & 31)) & 1u) {
