@@ -54,35 +54,21 @@ template <class R> struct PersistArgs {
   int direct;                 // 1: one filter (write the outputs)
 };
 
-// Barrier b (1-based) of the launch, in two levels: CTAs arrive in groups of
-// kGroup on their group's count (own cache line); the last arriver of a group
-// (the count reaches a multiple of the group's size) adds one to the top
-// count.  Every CTA then waits until the top count reaches base + b groups,
-// polling at most `limit` times.  Counts only grow (the host tracks the top
-// count a launch starts from; a group's count is a multiple of its size
-// between barriers).  On expiry or an error recorded by another CTA: false in
-// every thread.
-constexpr int kGroup = 32;
-constexpr int kBarStride = 16;   // u64 words between counts (a 128-byte line each)
-
+// Barrier b (1-based) of the launch: every CTA arrives once; wait until all
+// have (count >= base + b G), polling at most `limit` times.  On expiry or an
+// error recorded by another CTA: false in every thread.
 __device__ __forceinline__ bool pbar_sync(const Dev& d, unsigned long long target, long long limit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 0;
-    const int grp = blockIdx.x / kGroup;
-    const unsigned gsz = min((unsigned)kGroup, gridDim.x - (unsigned)grp * kGroup);
-    unsigned long long* top = d.pbar;
-    unsigned long long* gc = d.pbar + (long)(1 + grp) * kBarStride;
     unsigned long long old;
-    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(gc) : "memory");
-    if ((old + 1ull) % gsz == 0ull)
-      asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(top) : "memory");
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(d.pbar) : "memory");
     long long it = 0;
     for (;;) {
       unsigned long long c;
       int e;
-      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(top) : "memory");
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(d.pbar) : "memory");
       asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(d.err) : "memory");
       if (c >= target) {
         ok = 1;
@@ -127,7 +113,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   const int nb = gridDim.x, bid = blockIdx.x;
   const long gw = ((long)bid * kPT + tid) >> 5, nwarps = ((long)nb * kPT) >> 5;
   const long long lim = m.spin_limit;
-  const unsigned long long G = (nb + kGroup - 1) / kGroup;   // arrivals on the top count per barrier
+  const unsigned long long G = nb;
   unsigned long long tb = 0ull;   // barriers passed
   unsigned long long t_prev = (bid == 0 && tid == 0) ? gtimer() : 0ull;
   auto barrier = [&](int phase) -> bool {
@@ -955,8 +941,6 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
 }
 
 int persist_barriers() { return kPhases - 1; }
-unsigned long long persist_top_arrivals(int grid) { return (unsigned long long)((grid + kGroup - 1) / kGroup); }
-size_t persist_bar_words() { return (size_t)(1 + (152 * 8 + kGroup - 1) / kGroup) * kBarStride; }
 
 template size_t persist_smem<float>(int);
 template size_t persist_smem<double>(int);

@@ -153,7 +153,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.gbits = cv.take<unsigned int>(items * (size_t)t.gwords);
   t.pcsum = cv.take<unsigned long long>(items);
   t.pcoff = cv.take<unsigned long long>(items);
-  t.pbar = cv.take<unsigned long long>(phd::persist_bar_words());
+  t.pbar = cv.take<unsigned long long>(1);
   t.ptimes = cv.take<unsigned long long>(16);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
@@ -379,7 +379,7 @@ phd_status read_device_error(phd_handle* h) {
   // a wait that gave up may have left the grid barriers mid-count (and an
   // injected fault its flag)
   PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 4 * sizeof(unsigned int), h->stream));
-  PHD_CUDA(h, cudaMemsetAsync(h->d.pbar, 0, phd::persist_bar_words() * sizeof(unsigned long long), h->stream));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.pbar, 0, sizeof(unsigned long long), h->stream));
   h->pbar_count = 0;
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
@@ -637,7 +637,7 @@ phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, cons
     if (e == cudaSuccess) ++h->ev_used;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "grid step");
-  h->pbar_count += (unsigned long long)phd::persist_barriers() * phd::persist_top_arrivals(h->pgrid);
+  h->pbar_count += (unsigned long long)phd::persist_barriers() * (unsigned long long)h->pgrid;
   h->launches += 1;
   h->have_update = true;
   return PHD_OK;

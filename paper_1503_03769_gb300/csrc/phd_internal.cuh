@@ -182,7 +182,7 @@ struct Dev {
   unsigned int* gbits;   // [max_items][gwords] measurements that reach each sorted tile (gate survivors)
   unsigned long long* pcsum;  // [max_items] CDF totals per slot chunk
   unsigned long long* pcoff;  // [max_items] their exclusive offsets within the slice
-  unsigned long long* pbar;   // arrival counts of the kernel's grid barriers (only grow): top, groups
+  unsigned long long* pbar;   // [1] arrival count of the kernel's grid barriers (only grows)
   unsigned long long* ptimes; // [16] phase durations summed over launches, ns
   int gwords;            // words of gbits per tile: ceil(m_max / 32)
 };
@@ -1066,8 +1066,6 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
                            const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
                            unsigned long long base, bool direct, cudaStream_t s);
 int persist_barriers();   // grid barriers one launch passes
-unsigned long long persist_top_arrivals(int grid);   // arrivals on the top count per barrier
-size_t persist_bar_words();   // u64 words of the barrier counts
 void fill_anchor_table(Anchor* tab);
 Model model_from_config(const phd_config& c);
 const char* config_problem(const phd_config& c);
