@@ -112,6 +112,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   const int K = m.K, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = gridDim.x, bid = blockIdx.x;
   const long gw = ((long)bid * kPT + tid) >> 5, nwarps = ((long)nb * kPT) >> 5;
+  // warp-per-unit phases spread consecutive units over CTAs first (unit u on
+  // CTA u mod nb), so a few hundred units use every SM's FP64 pipe
+  const long sw = (long)wid * nb + bid;
   const long long lim = m.spin_limit;
   const unsigned long long G = nb;
   unsigned long long tb = 0ull;   // barriers passed
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
 
   // ---- B: per (slice, cell): total over the slice's chunks (a warp per
   // unit; the cell's row of chunk counts is contiguous, read 4 at a time)
-  for (long u = gw; u < (long)K * 256; u += nwarps) {
+  for (long u = sw; u < (long)K * 256; u += nwarps) {
     const int j = (int)(u >> 8), b = (int)(u & 255);
     const int4* row = reinterpret_cast<const int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
     const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ---- C: per (slice, cell): the cell's start (cells before it), then each
   // chunk's start within the cell (chunks before it), in place: rounds of
   // 128 chunks, four per lane, a warp scan of the lane totals
-  for (long u = gw; u < (long)K * 256; u += nwarps) {
+  for (long u = sw; u < (long)K * 256; u += nwarps) {
     const int j = (int)(u >> 8), b = (int)(u & 255);
     int base = 0;
     for (int q = lane; q < b; q += 32) base += __ldcg(d.bintot + (long)j * 256 + q);
@@ -419,19 +422,19 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     const double cs = m.p_d * m.cnorm;
     R* ginv = static_cast<R*>(d.ginv);
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    for (long u = gw; u < units; u += nwarps) {
+    for (long u = sw; u < units; u += nwarps) {
       const int j = a.direct ? 0 : (int)(u / m.m_max);
       const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
       if (p >= slice_M(d, j)) continue;   // uniform over the warp
       // lane l takes tiles l, l + 32, ... of the slice in order; the bit row
-      // of word p / 32 is contiguous over tiles (one load per 32 tiles)
+      // of word p / 32 is contiguous over tiles (one load per 32 tiles); only
+      // the tiles the measurement reaches are loaded and added
       double c = 0.0;
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
 #pragma unroll 8
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const unsigned bits = __ldcg(brow + it);
-        const double v = ((bits >> (p & 31)) & 1u) ? __ldcg(d.colpart + (long)it * m.m_max + p) : 0.0;
-        c += v;
+        const bool live = (__ldcg(brow + it) >> (p & 31)) & 1u;
+        if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
       }
       for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
       if (lane == 0) {
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // label) per measurement; CDF chunk totals per slot chunk
   {
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    for (long u = nwarps - 1 - gw; u < units; u += nwarps) {
+    for (long u = sw; u < units; u += nwarps) {
       const int j = a.direct ? 0 : (int)(u / m.m_max);
       const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
       const int M = slice_M(d, j);
@@ -749,9 +752,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   {
     St4<R>* est = static_cast<St4<R>*>(d.est_local);
     const long units = (long)K * m.m_max;
-    // warps counted from the end of the grid: the first CTAs also take the
-    // second round of chunk items below
-    for (long u = nwarps - 1 - gw; u < units; u += nwarps) {
+    for (long u = sw; u < units; u += nwarps) {
       const int j = (int)(u / m.m_max);
       const int r = (int)(u - (long)j * m.m_max);
       const int nsel = __ldcg(d.nsel + j);
@@ -771,8 +772,8 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
 #pragma unroll 4
       for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const unsigned bits = __ldcg(brow + it);
-        if ((bits >> (p & 31)) & 1u) {
+        const bool live = (__ldcg(brow + it) >> (p & 31)) & 1u;
+        if (__any_sync(0xffffffffu, live) && live) {
           const double* q = d.spart + ((long)it * m.m_max + r) * 5;
           a0 += __ldcg(q);
           a1 += __ldcg(q + 1);
