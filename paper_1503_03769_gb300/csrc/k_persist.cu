@@ -431,9 +431,11 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       // the tiles the measurement reaches are loaded and added
       double c = 0.0;
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+      const int t1 = ipref[j + 1];
 #pragma unroll 8
-      for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const bool live = (__ldcg(brow + it) >> (p & 31)) & 1u;
+      for (int t0 = ipref[j]; t0 < t1; t0 += 32) {   // warp-uniform rounds: every lane runs every round
+        const int it = t0 + lane;
+        const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
         if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
       }
       for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -770,9 +772,11 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const V2<R> z = slice_Z<R>(d, j)[p];
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+      const int t1 = ipref[j + 1];
 #pragma unroll 4
-      for (int it = ipref[j] + lane; it < ipref[j + 1]; it += 32) {
-        const bool live = (__ldcg(brow + it) >> (p & 31)) & 1u;
+      for (int t0 = ipref[j]; t0 < t1; t0 += 32) {   // warp-uniform rounds
+        const int it = t0 + lane;
+        const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
         if (__any_sync(0xffffffffu, live) && live) {
           const double* q = d.spart + ((long)it * m.m_max + r) * 5;
           a0 += __ldcg(q);
