@@ -598,6 +598,8 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
         nt = max(st["timed_updates"], 1)
         roofline["step_kernel_ms_per_step"] = step_ms / nt
         roofline["phase_ms_per_step"] = {k: v / nt for k, v in phases.items()}
+        _, pmax, _ = f.phase_times(detail=True)
+        roofline["phase_longest_cta_ms"] = pmax
 
     # whole runs in one launch each (phd_run): S scans per call, L2 flushed
     # between runs (outside the events)

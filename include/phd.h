@@ -429,15 +429,20 @@ typedef struct phd_stats {
 phd_status phd_get_stats(phd_handle *h, phd_stats *out);
 phd_status phd_reset_stats(phd_handle *h);
 
-/* Time spent in each phase of the grid path's step kernel, summed over its
- * launches since phd_init / phd_reset_stats (device clock at the phases'
- * barriers, read by one thread): h_ms[0..n-1] (n <= 12) in milliseconds for
- * the phases prediction + spatial keys, cell totals, cell starts, scatter,
- * pass 1 (Eq. 7), normalisers (Eq. 12), pass 2 (Eq. 8), mass and plan,
- * selection ranks + CDF chunk sums, label sums (Eq. 18) + CDF offsets,
- * estimates + offspring ends, gather.  Each figure runs from the previous
- * barrier to the phase's own (it includes the wait for the slowest CTA).
- * Zeros on the other paths.  Synchronises. */
+/* Time spent in each phase of the grid path's step kernel since phd_init /
+ * phd_reset_stats (device clock, read by one thread per CTA at the phases'
+ * barriers), in milliseconds, for the 12 phases prediction + spatial keys,
+ * cell totals, cell starts, scatter, pass 1 (Eq. 7), normalisers (Eq. 12),
+ * pass 2 (Eq. 8), mass and plan, selection ranks + CDF chunk sums, label
+ * sums (Eq. 18) + CDF offsets, estimates + offspring ends, gather:
+ *   h_ms[0..11]   summed over launches, from the previous barrier's release
+ *                 to the phase's own (the phase's wall time);
+ *   h_ms[12..23]  the longest time one CTA worked in the phase (from leaving
+ *                 the previous barrier to arriving at the next), the largest
+ *                 over launches;
+ *   h_ms[24..35]  the time a CTA worked in the phase, summed over launches and
+ *                 averaged over CTAs.
+ * n <= 36 values are written.  Zeros on the other paths.  Synchronises. */
 phd_status phd_get_phase_times(phd_handle *h, double *h_ms, int32_t n);
 
 /* on != 0: phd_step / phd_step_host bracket the update stage (Eq. 7-8 pair

@@ -115,17 +115,49 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // warp-per-unit phases spread consecutive units over CTAs first (unit u on
   // CTA u mod nb), so a few hundred units use every SM's FP64 pipe
   const long sw = (long)wid * nb + bid;
+  // when a phase has few units (one filter's measurements or labels), a group
+  // of G warps of one CTA shares a unit, its lanes over the unit's loop, and
+  // the warps' totals are added in warp order; with G > 1 the loop over units
+  // runs in rounds that every warp of the CTA takes (a block barrier between
+  // the warps' partials and their sum); groups spread over CTAs first
+  struct Grp {
+    int G, slot, gl;
+    long gid, ng;
+  };
+  auto groups = [&](long units) {
+    Grp g;
+    g.G = 1;
+    while (g.G < kPT / 32 && units * g.G * 2 <= nwarps) g.G *= 2;
+    g.slot = wid / g.G;
+    g.gl = (wid % g.G) * 32 + lane;
+    g.gid = (long)g.slot * nb + bid;
+    g.ng = (long)(kPT / 32 / g.G) * nb;
+    return g;
+  };
+  __shared__ double gred[2][kPT / 32][5];   // group partials, two buffers used in turn
+  __shared__ int gcnt[2][kPT / 32][2];
   const long long lim = m.spin_limit;
   const unsigned long long G = nb;
   unsigned long long tb = 0ull;   // barriers passed
-  unsigned long long t_prev = (bid == 0 && tid == 0) ? gtimer() : 0ull;
+  unsigned long long t_prev = tid == 0 ? gtimer() : 0ull;   // CTA 0: the last barrier's release
+  unsigned long long t_go = t_prev;                          // every CTA: when it left the last barrier
+  // phase clock: ptimes[phase] sums CTA 0's time from barrier to barrier;
+  // ptimes[16 + phase] keeps the longest time any CTA spent working in the
+  // phase (leaving one barrier to arriving at the next) and ptimes[32 + phase]
+  // sums those times over CTAs
   auto barrier = [&](int phase) -> bool {
     ++tb;
+    if (tid == 0) {
+      const unsigned long long busy = gtimer() - t_go;
+      atomicMax(d.ptimes + 16 + phase, busy);
+      atomicAdd(d.ptimes + 32 + phase, busy);
+    }
     const bool ok = pbar_sync(d, a.base + tb * G, lim);
-    if (ok && bid == 0 && tid == 0) {
+    if (ok && tid == 0) {
       const unsigned long long t = gtimer();
-      atomicAdd(d.ptimes + phase, t - t_prev);
+      if (bid == 0) atomicAdd(d.ptimes + phase, t - t_prev);
       t_prev = t;
+      t_go = t;
     }
     return ok;
   };
@@ -422,24 +454,43 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     const double cs = m.p_d * m.cnorm;
     R* ginv = static_cast<R*>(d.ginv);
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    for (long u = sw; u < units; u += nwarps) {
-      const int j = a.direct ? 0 : (int)(u / m.m_max);
-      const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
-      if (p >= slice_M(d, j)) continue;   // uniform over the warp
-      // lane l takes tiles l, l + 32, ... of the slice in order; the bit row
-      // of word p / 32 is contiguous over tiles (one load per 32 tiles); only
-      // the tiles the measurement reaches are loaded and added
+    const Grp g = groups(units);
+    int par = 0;
+    for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
+      const long u = r0 + g.gid;
+      int j = 0, p = 0;
+      bool act = u < units;
+      if (act) {
+        j = a.direct ? 0 : (int)(u / m.m_max);
+        p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+        act = p < slice_M(d, j);
+      }
+      if (g.G == 1 && !act) continue;
+      // group lane l takes tiles l, l + 32 G, ... of the slice in order; the
+      // bit row of word p / 32 is contiguous over tiles; only the tiles the
+      // measurement reaches are loaded and added
       double c = 0.0;
-      const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-      const int t1 = ipref[j + 1];
-#pragma unroll 8
-      for (int t0 = ipref[j]; t0 < t1; t0 += 32) {   // warp-uniform rounds: every lane runs every round
-        const int it = t0 + lane;
-        const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
-        if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+      if (act) {   // uniform over the group
+        const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+        const int t1 = ipref[j + 1];
+#pragma unroll 4
+        for (int t0 = ipref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds: every lane runs every round
+          const int it = t0 + g.gl;
+          const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
+          if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+        }
       }
       for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      if (lane == 0) {
+      if (g.G > 1) {
+        if (lane == 0) gred[par][wid][0] = c;
+        __syncthreads();
+        if (g.gl == 0) {
+          c = 0.0;
+          for (int k = 0; k < g.G; ++k) c += gred[par][g.slot * g.G + k][0];
+        }
+        par ^= 1;
+      }
+      if (act && g.gl == 0) {
         c *= cs;
         d.C[j * m.m_max + p] = c;
         d.Cused[j * m.m_max + p] = c;
@@ -496,6 +547,13 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const int t = it - ipref[j];
       const int cnt = min(256, npred_s[j] - t * 256);
       const long base = (long)j * m.pe_cap + (long)t * 256;
+      // the particle's record and slot are fetched before the gate bits are read
+      P4<R> q{0, 0, 0, 0};
+      int slot = 0;
+      if (tid < cnt) {
+        q = geo[base + tid];
+        slot = d.perm[base + tid];
+      }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
       const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
@@ -507,7 +565,6 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       __syncthreads();
       R wv = 0;
       if (tid < cnt) {
-        const P4<R> q = geo[base + tid];
         R a0 = 0, a1 = 0;
         for (int e = 0; e < nl; ++e) {
           const Z4<R> za = zs[e];
@@ -515,7 +572,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           if (lidx[e] & 1) a1 += v; else a0 += v;
         }
         wv = (miss + (a0 + a1)) * q.w;
-        wu[(long)j * m.pe_cap + d.perm[base + tid]] = wv;
+        wu[(long)j * m.pe_cap + slot] = wv;
       }
       // tile sum and largest weight: warps in the kernel's precision, warp
       // totals in FP64 in warp order
@@ -544,8 +601,11 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   if (!barrier(6)) return;
 
   // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
-  // LT_j = min(round(N^j), labels with dW > 0)
-  for (int j = bid; j < K; j += nb) {
+  // LT_j = min(round(N^j), labels with dW > 0).  One filter: every CTA forms
+  // them itself at the start of I (the same loads in the same order, so the
+  // same values in every CTA) and the barrier between H and I goes.
+  __shared__ int nsel_s, rss_s;
+  auto slice_plan = [&](int j, bool store) {
     double s = 0.0, mx = 0.0;
     for (int it = ipref[j] + tid; it < ipref[j + 1]; it += kPT) {
       s += __ldcg(d.rowpart + it);
@@ -574,42 +634,65 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         tm = fmax(tm, dredm[k]);
         np += wcnt[k];
       }
-      d.mass[j] = t;
       int L, sc;
       resample_plan(d.rho[j], d.lmax[j], npred_s[j], t, tm, L, sc);
-      d.rs_mass[j] = t;
-      d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
-      d.rs_s[j] = sc;
-      d.rs_L[j] = L;
       long long LT = llround(t);
       if (LT > np) LT = np;
       if (LT < 0) LT = 0;
-      d.nsel[j] = (int)LT;
+      nsel_s = (int)LT;
+      rss_s = sc;
+      if (store) {
+        d.mass[j] = t;
+        d.rs_mass[j] = t;
+        d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
+        d.rs_s[j] = sc;
+        d.rs_L[j] = L;
+        d.nsel[j] = (int)LT;
+      }
     }
     __syncthreads();
+  };
+  if (!a.direct) {
+    for (int j = bid; j < K; j += nb) slice_plan(j, true);
+    if (!barrier(7)) return;
   }
-  if (!barrier(7)) return;
 
   // ---- I: selection ranks (Step 3: the LT largest dW, ties to the lower
   // label) per measurement; CDF chunk totals per slot chunk
   {
+    if (a.direct) slice_plan(0, bid == 0);
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    for (long u = sw; u < units; u += nwarps) {
-      const int j = a.direct ? 0 : (int)(u / m.m_max);
-      const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
-      const int M = slice_M(d, j);
-      if (p >= M) continue;
+    const Grp g = groups(units);
+    int par = 0;
+    for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
+      const long u = r0 + g.gid;
+      int j = 0, p = 0, M = 0;
+      bool act = u < units;
+      if (act) {
+        j = a.direct ? 0 : (int)(u / m.m_max);
+        p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+        M = slice_M(d, j);
+        act = p < M;
+      }
+      if (g.G == 1 && !act) continue;
       const unsigned long long* key = d.dwkey + (long)j * m.m_max;
-      const unsigned long long v = __ldcg(key + p);
+      const unsigned long long v = act ? __ldcg(key + p) : 0ull;
       int c = 0;
-#pragma unroll 8
-      for (int q = lane; q < M; q += 32) {
+#pragma unroll 4
+      for (int q = g.gl; q < M; q += 32 * g.G) {
         const unsigned long long w2 = __ldcg(key + q);
         c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
       }
-      const int rank = warp_sum(c);
-      if (lane == 0) {
-        const bool take = v > 0ull && rank < __ldcg(d.nsel + j);
+      int rank = warp_sum(c);
+      if (g.G > 1) {
+        if (lane == 0) gcnt[par][wid][0] = rank;
+        __syncthreads();
+        rank = 0;
+        for (int k = 0; k < g.G; ++k) rank += gcnt[par][g.slot * g.G + k][0];
+        par ^= 1;
+      }
+      if (act && g.gl == 0) {
+        const bool take = v > 0ull && rank < (a.direct ? nsel_s : __ldcg(d.nsel + j));
         d.selrank[j * m.m_max + p] = take ? rank : -1;
         if (take) d.sel[j * m.m_max + rank] = p;
       }
@@ -619,7 +702,8 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
       const int i = (it - ipref[j]) * 256 + tid;
-      const unsigned long long q = i < npred_s[j] ? scaled_floor(wu[(long)j * m.pe_cap + i], d.rs_s[j]) : 0ull;
+      const int sj = a.direct ? rss_s : d.rs_s[j];
+      const unsigned long long q = i < npred_s[j] ? scaled_floor(wu[(long)j * m.pe_cap + i], sj) : 0ull;
       unsigned long long tot = 0;
       block_scan_u64<R>(q, wt, &tot);
       if (tid == 0) d.pcsum[it] = tot;
@@ -652,45 +736,42 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     }
     P4<R>* sp = reinterpret_cast<P4<R>*>(smem);               // [256]
     St4<R>* sx = reinterpret_cast<St4<R>*>(sp + 256);          // [256]
-    int* lidx = reinterpret_cast<int*>(sx + 256);              // [m_max] live measurements
-    int* lr = lidx + ((m.m_max + 7) & ~7);                      // [m_max] live selected ranks
+    int2* lr = reinterpret_cast<int2*>(sx + 256);               // [m_max] live selected (rank, measurement)
+    int* lidx = reinterpret_cast<int*>(lr + m.m_max);            // [m_max] live measurements
     const St4<R>* __restrict__ xs = static_cast<const St4<R>*>(d.x_alt);
     constexpr int LB = 2;   // labels per thread group
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
-      const int ns = __ldcg(d.nsel + j);
+      const int ns = a.direct ? nsel_s : __ldcg(d.nsel + j);
       if (ns <= 0) continue;   // uniform over the block
       const int t = it - ipref[j];
       const int cnt = min(256, npred_s[j] - t * 256);
       const long base = (long)j * m.pe_cap + (long)t * 256;
+      // the tile's records are fetched before its gate bits are read
+      P4<R> qg{0, 0, 0, 0};
+      St4<R> xg{0, 0, 0, 0};
+      if (tid < cnt) {
+        qg = geo[base + tid];
+        xg = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+      }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
       if (tid < cnt) {
-        sp[tid] = geo[base + tid];
-        sx[tid] = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+        sp[tid] = qg;
+        sx[tid] = xg;
       }
-      // the selected labels among the live measurements, in rank order
+      // the selected labels among the live measurements (any order: a
+      // label's sums do not depend on its place in the list)
       if (tid == 0) nlive_s = 0;
       __syncthreads();
       for (int e = tid; e < nl; e += kPT) {
-        const int r = __ldcg(d.selrank + j * m.m_max + lidx[e]);
-        if (r >= 0) lr[atomicAdd(&nlive_s, 1)] = r;
+        const int p = lidx[e];
+        const int r = __ldcg(d.selrank + j * m.m_max + p);
+        if (r >= 0) lr[atomicAdd(&nlive_s, 1)] = make_int2(r, p);
       }
       __syncthreads();
       const int nr = nlive_s;
       if (nr == 0) continue;   // uniform
-      // ranks in increasing order (insertion by one thread: nr is small)
-      if (tid == 0)
-        for (int x1 = 1; x1 < nr; ++x1) {
-          const int v = lr[x1];
-          int y = x1 - 1;
-          while (y >= 0 && lr[y] > v) {
-            lr[y + 1] = lr[y];
-            --y;
-          }
-          lr[y + 1] = v;
-        }
-      __syncthreads();
       const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
       const int ng = (nr + LB - 1) / LB;
       int nsplit = 1;
@@ -707,7 +788,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           for (int c = 0; c < 5; ++c) s[k][c] = 0;
           const int qq = g * LB + k;
           V2<R> z = {0, 0};
-          if (g < ng && qq < nr) z = Z[__ldcg(d.sel + j * m.m_max + lr[qq])];
+          if (g < ng && qq < nr) z = Z[lr[qq].y];
           z0[k] = z.a;
           z1[k] = z.b;
           meas_point<R>(m, z, px[k], py[k]);
@@ -737,7 +818,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           for (int k = 0; k < LB; ++k) {
             const int qq = g * LB + k;
             if (qq < nr) {
-              double* o = d.spart + ((long)it * m.m_max + lr[qq]) * 5;
+              double* o = d.spart + ((long)it * m.m_max + lr[qq].x) * 5;
 #pragma unroll
               for (int c = 0; c < 5; ++c) o[c] = (double)s[k][c];
             }
@@ -753,37 +834,49 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // label order.  Offspring ends per slot chunk (exact integer CDF).
   {
     St4<R>* est = static_cast<St4<R>*>(d.est_local);
-    const long units = (long)K * m.m_max;
-    for (long u = sw; u < units; u += nwarps) {
-      const int j = (int)(u / m.m_max);
-      const int r = (int)(u - (long)j * m.m_max);
-      const int nsel = __ldcg(d.nsel + j);
-      if (a.direct && r == 0 && lane == 0) {
-        *d.out_count = nsel;
-        if (a.d_count) *a.d_count = nsel;
+    // one filter: units are the selected labels, their groups taken from the
+    // end of the grid (the CTAs with the fewest offspring chunks below)
+    const long units = a.direct ? (long)nsel_s : (long)K * m.m_max;
+    const Grp g = groups(units);
+    const long gid0 = a.direct ? (long)g.slot * nb + (nb - 1 - bid) : g.gid;
+    if (a.direct && bid == 0 && tid == 0) {
+      *d.out_count = nsel_s;
+      if (a.d_count) *a.d_count = nsel_s;
+    }
+    int par = 0;
+    for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
+      const long u = r0 + gid0;
+      int j = 0, r = 0, nsel = 0;
+      bool act = u < units;
+      if (act) {
+        j = a.direct ? 0 : (int)(u / m.m_max);
+        r = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+        nsel = a.direct ? nsel_s : __ldcg(d.nsel + j);
+        act = r < nsel;
       }
-      if (r >= nsel) continue;   // uniform over the warp
-      const int p = __ldcg(d.sel + j * m.m_max + r);
-      int below = 0;
-      if (a.direct) {
-        for (int t = lane; t < nsel; t += 32) below += __ldcg(d.sel + j * m.m_max + t) < p ? 1 : 0;
-        below = warp_sum(below);
-      }
-      const V2<R> z = slice_Z<R>(d, j)[p];
+      if (g.G == 1 && !act) continue;
+      int p = 0, below = 0;
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-      const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-      const int t1 = ipref[j + 1];
+      if (act) {   // uniform over the group
+        p = __ldcg(d.sel + j * m.m_max + r);
+        if (a.direct) {
+          for (int t = g.gl; t < nsel; t += 32 * g.G) below += __ldcg(d.sel + j * m.m_max + t) < p ? 1 : 0;
+          below = warp_sum(below);
+        }
+        const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+        const int t1 = ipref[j + 1];
 #pragma unroll 4
-      for (int t0 = ipref[j]; t0 < t1; t0 += 32) {   // warp-uniform rounds
-        const int it = t0 + lane;
-        const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
-        if (__any_sync(0xffffffffu, live) && live) {
-          const double* q = d.spart + ((long)it * m.m_max + r) * 5;
-          a0 += __ldcg(q);
-          a1 += __ldcg(q + 1);
-          a2 += __ldcg(q + 2);
-          a3 += __ldcg(q + 3);
-          a4 += __ldcg(q + 4);
+        for (int t0 = ipref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds
+          const int it = t0 + g.gl;
+          const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
+          if (__any_sync(0xffffffffu, live) && live) {
+            const double* q = d.spart + ((long)it * m.m_max + r) * 5;
+            a0 += __ldcg(q);
+            a1 += __ldcg(q + 1);
+            a2 += __ldcg(q + 2);
+            a3 += __ldcg(q + 3);
+            a4 += __ldcg(q + 4);
+          }
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -793,7 +886,33 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         a3 += __shfl_down_sync(0xffffffffu, a3, o);
         a4 += __shfl_down_sync(0xffffffffu, a4, o);
       }
-      if (lane == 0) {
+      if (g.G > 1) {
+        if (lane == 0) {
+          gred[par][wid][0] = a0;
+          gred[par][wid][1] = a1;
+          gred[par][wid][2] = a2;
+          gred[par][wid][3] = a3;
+          gred[par][wid][4] = a4;
+          gcnt[par][wid][1] = below;
+        }
+        __syncthreads();
+        if (g.gl == 0) {
+          a0 = a1 = a2 = a3 = a4 = 0.0;
+          below = 0;
+          for (int k = 0; k < g.G; ++k) {
+            const int w2 = g.slot * g.G + k;
+            a0 += gred[par][w2][0];
+            a1 += gred[par][w2][1];
+            a2 += gred[par][w2][2];
+            a3 += gred[par][w2][3];
+            a4 += gred[par][w2][4];
+            below += gcnt[par][w2][1];
+          }
+        }
+        par ^= 1;
+      }
+      if (act && g.gl == 0) {
+        const V2<R> z = slice_Z<R>(d, j)[p];
         R px, py;
         meas_point<R>(m, z, px, py);
         St4<R> o;
@@ -813,7 +932,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         } else {
           o = St4<R>{px, (R)0, py, (R)0};
         }
-        est[u] = o;
+        est[(long)j * m.m_max + r] = o;
         if (a.direct && below < a.cap) {
           a.out_states[4 * below + 0] = o.x;
           a.out_states[4 * below + 1] = o.vx;
@@ -884,9 +1003,14 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
     // every reader of this step's counter finished before barrier 10
-    if (bid == 0 && tid == 0) {
-      *d.step += 1ull;
-      atomicAdd(d.ptimes + 11, gtimer() - t_prev);
+    if (tid == 0) {
+      const unsigned long long t = gtimer();
+      if (bid == 0) {
+        *d.step += 1ull;
+        atomicAdd(d.ptimes + 11, t - t_prev);
+      }
+      atomicMax(d.ptimes + 16 + 11, t - t_go);
+      atomicAdd(d.ptimes + 32 + 11, t - t_go);
     }
   }
 }
@@ -898,7 +1022,7 @@ template <class R> size_t persist_smem(int m_max) {
   const size_t a = 8 * kCells * sizeof(int);                                         // D
   const size_t e = 256 * sizeof(P4<R>) + mm * sizeof(int);                            // E
   const size_t g = mm * sizeof(int) + mm * sizeof(Z4<R>);                            // G
-  const size_t j = 256 * sizeof(P4<R>) + 256 * sizeof(St4<R>) + 2 * mm * sizeof(int);  // J
+  const size_t j = 256 * sizeof(P4<R>) + 256 * sizeof(St4<R>) + mm * sizeof(int2) + mm * sizeof(int);  // J
   size_t s = a;
   if (e > s) s = e;
   if (g > s) s = g;
@@ -945,7 +1069,7 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
                                      persist_smem<R>(m.m_max), s);
 }
 
-int persist_barriers() { return kPhases - 1; }
+int persist_barriers(bool direct) { return direct ? kPhases - 2 : kPhases - 1; }
 
 template size_t persist_smem<float>(int);
 template size_t persist_smem<double>(int);

@@ -154,7 +154,7 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.pcsum = cv.take<unsigned long long>(items);
   t.pcoff = cv.take<unsigned long long>(items);
   t.pbar = cv.take<unsigned long long>(1);
-  t.ptimes = cv.take<unsigned long long>(16);
+  t.ptimes = cv.take<unsigned long long>(48);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);
   t.max_items = (int)items;
@@ -637,7 +637,7 @@ phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, cons
     if (e == cudaSuccess) ++h->ev_used;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "grid step");
-  h->pbar_count += (unsigned long long)phd::persist_barriers() * (unsigned long long)h->pgrid;
+  h->pbar_count += (unsigned long long)phd::persist_barriers(direct) * (unsigned long long)h->pgrid;
   h->launches += 1;
   h->have_update = true;
   return PHD_OK;
@@ -1194,11 +1194,16 @@ phd_status phd_get_stats(phd_handle* h, phd_stats* out) {
 }
 
 phd_status phd_get_phase_times(phd_handle* h, double* h_ms, int32_t n) {
-  if (!h || !h_ms || n < 0 || n > 12) return PHD_ERR_INVALID_ARG;
-  unsigned long long v[16] = {};
+  if (!h || !h_ms || n < 0 || n > 36) return PHD_ERR_INVALID_ARG;
+  unsigned long long v[48] = {};
   PHD_CUDA(h, cudaMemcpyAsync(v, h->d.ptimes, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
-  for (int k = 0; k < n; ++k) h_ms[k] = 1e-6 * (double)v[k];
+  for (int k = 0; k < n; ++k) {
+    const int blk = k / 12, ph = k % 12;
+    double ms = 1e-6 * (double)v[16 * blk + ph];
+    if (blk == 2) ms /= (h->pgrid > 0 ? (double)h->pgrid : 1.0);   // sum over CTAs -> per CTA
+    h_ms[k] = ms;
+  }
   return PHD_OK;
 }
 
@@ -1206,7 +1211,7 @@ phd_status phd_reset_stats(phd_handle* h) {
   if (!h) return PHD_ERR_INVALID_ARG;
   PHD_CUDA(h, drain_timer(h));
   PHD_CUDA(h, cudaMemsetAsync(h->d.stats, 0, 5 * sizeof(unsigned long long), h->stream));
-  PHD_CUDA(h, cudaMemsetAsync(h->d.ptimes, 0, 16 * sizeof(unsigned long long), h->stream));
+  PHD_CUDA(h, cudaMemsetAsync(h->d.ptimes, 0, 48 * sizeof(unsigned long long), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   h->launches = 0;
   h->timer_ms = 0.0;

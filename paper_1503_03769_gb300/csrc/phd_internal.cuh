@@ -1065,7 +1065,7 @@ template <class R>
 cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
                            const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
                            unsigned long long base, bool direct, cudaStream_t s);
-int persist_barriers();   // grid barriers one launch passes
+int persist_barriers(bool direct);   // grid barriers one launch passes (one filter / a batch)
 void fill_anchor_table(Anchor* tab);
 Model model_from_config(const phd_config& c);
 const char* config_problem(const phd_config& c);

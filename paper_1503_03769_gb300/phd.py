@@ -591,11 +591,16 @@ class ParticlePHD:
     PHASES = ("predict_keys", "cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2",
               "mass_plan", "ranks_cdf", "label_sums_offsets", "estimates_offspring", "gather")
 
-    def phase_times(self) -> dict:
-        """Grid path: summed time per phase of the step kernel, ms (phd_get_phase_times)."""
-        v = (ctypes.c_double * 12)()
-        self._check(self.L.phd_get_phase_times(self.h, v, 12), "phd_get_phase_times")
-        return dict(zip(self.PHASES, list(v)))
+    def phase_times(self, detail: bool = False):
+        """Grid path: summed wall time per phase of the step kernel, ms
+        (phd_get_phase_times); with detail, also the longest and the mean
+        per-CTA working time of each phase."""
+        v = (ctypes.c_double * 36)()
+        self._check(self.L.phd_get_phase_times(self.h, v, 36), "phd_get_phase_times")
+        wall = dict(zip(self.PHASES, list(v)[:12]))
+        if not detail:
+            return wall
+        return wall, dict(zip(self.PHASES, list(v)[12:24])), dict(zip(self.PHASES, list(v)[24:36]))
 
     def set_stage_timer(self, on: bool):
         self._check(self.L.phd_set_stage_timer(self.h, 1 if on else 0), "phd_set_stage_timer")
