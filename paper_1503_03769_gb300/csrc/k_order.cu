@@ -5,7 +5,7 @@
 // particles are close to one another, which slot order does not give (births
 // are spread over the region and resampling keeps parents in slot order).
 // Before pass 1, every slice's predicted particles are put in the order of a
-// 16 x 16 grid over measurement space (Morton order of the cells), by a
+// 16 x 16 grid over measurement space (Hilbert order of the cells), by a
 // stable counting sort: the permutation perm[sorted position] = slot is read
 // by passes 1 and 2 (the particles themselves stay where they are, and every
 // per-particle result goes to its own slot), so the only effect on results is

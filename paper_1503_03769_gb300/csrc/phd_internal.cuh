@@ -916,8 +916,15 @@ __device__ __forceinline__ uint32_t philox_u32(const Model& m, uint32_t a, unsig
 // ---------------------------------------------------------------------------
 // Helpers shared by the staged kernels and the persistent step kernel.
 // ---------------------------------------------------------------------------
-constexpr int kCells = 256;   // 16 x 16 cells over measurement space, Morton order
+constexpr int kCells = 256;   // 16 x 16 cells over measurement space, Hilbert order
 
+// Position of the particle's cell on the Hilbert curve through the 16 x 16
+// grid (Hilbert 1891; the usual quadrant recursion: at each level the
+// quadrant's place on the curve, then the sub-square turned into the
+// quadrant's frame).  Consecutive keys are edge neighbours, so a run of
+// particles in key order stays in a compact patch of cells; the Morton
+// (Z) order jumps across the grid at its quadrant boundaries, and a
+// 256-particle tile spanning such a jump reaches most measurements.
 __device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
   int cx = (int)floorf((h0 - m.f_cell_o0) * m.f_cell_s0);
   int cy = (int)floorf((h1 - m.f_cell_o1) * m.f_cell_s1);
@@ -925,7 +932,19 @@ __device__ __forceinline__ int cell_key(const Model& m, float h0, float h1) {
   cy = min(max(cy, 0), 15);
   int k = 0;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) k |= (((cx >> b) & 1) << (2 * b)) | (((cy >> b) & 1) << (2 * b + 1));
+  for (int s = 8; s > 0; s >>= 1) {
+    const int rx = (cx & s) ? 1 : 0, ry = (cy & s) ? 1 : 0;
+    k += s * s * ((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        cx = 15 - cx;
+        cy = 15 - cy;
+      }
+      const int t = cx;
+      cx = cy;
+      cy = t;
+    }
+  }
   return k;
 }
 
