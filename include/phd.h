@@ -434,7 +434,7 @@ phd_status phd_reset_stats(phd_handle *h);
  * barriers), in milliseconds, for the 12 phases prediction + spatial keys,
  * cell totals, cell starts, scatter, pass 1 (Eq. 7), normalisers (Eq. 12),
  * pass 2 (Eq. 8), mass and plan, selection ranks + CDF chunk sums, label
- * sums (Eq. 18) + CDF offsets, estimates + offspring ends, gather:
+ * sums (Eq. 18) + CDF offsets, estimates, offspring ends + gather:
  *   h_ms[0..11]   summed over launches, from the previous barrier's release
  *                 to the phase's own (the phase's wall time);
  *   h_ms[12..23]  the longest time one CTA worked in the phase (from leaving

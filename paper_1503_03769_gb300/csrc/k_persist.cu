@@ -22,15 +22,17 @@
 // Phases (barrier between consecutive ones):
 //   A  predict (Eq. 5-6), measurement-space geometry, cell key, chunk
 //      histograms; measurement staging
-//   B  cell totals per (slice, cell)          C  cell starts per (slice, cell)
+//   B  (folded into A: cell totals per (slice, cell) by integer atomics)
+//   C  cell starts per (slice, cell)
 //   D  stable scatter to the cell order       E  pass 1 (Eq. 7) per tile
 //   F  C_p, ginv_p and the dW keys (Eq. 12, 16) per measurement
 //   G  pass 2 (Eq. 8) per tile: updated weights, tile sums and maxima
 //   H  N^j, the resampling plan, LT_j per slice
 //   I  selection ranks (Step 3) per measurement; CDF chunk totals per chunk
 //   J  pass 3 (Eq. 18 sums) per tile; CDF chunk offsets per slice
-//   K  estimates per selected label; offspring ends per chunk
-//   L  children gathered (Sec. 2.2 step 3), counts and step counter advanced
+//   K  estimates per selected label
+//   L  offspring ends per chunk and the children gathered (Sec. 2.2 step 3),
+//      counts and step counter advanced
 // The barrier is one release atomic per CTA on a 64-bit count that only grows
 // and acquire polls; the host passes the count the launch starts from.
 #include "phd_internal.cuh"
@@ -102,12 +104,15 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
 template <class R, int RB>
 __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArgs<R> a) {
   extern __shared__ __align__(32) unsigned char smem[];
+  unsigned smem_bytes;   // dynamic shared memory of the launch
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(smem_bytes));
   __shared__ int ipref[kMaxPE + 1];   // items (256-particle chunks / tiles) per slice, prefix
   __shared__ int hpref[kMaxPE + 1];   // chunk-histogram rows per slice: 256 x (items rounded up to 4), prefix
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
   __shared__ int wcnt[kPT / 32];
   __shared__ R bsh[4 * (kPT / 32)];
   __shared__ double dred[kPT / 32], dredm[kPT / 32];
+  __shared__ unsigned long long dredb[kPT / 32];
   __shared__ int nlive_s;
   const int K = m.K, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = gridDim.x, bid = blockIdx.x;
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   };
   __shared__ double gred[2][kPT / 32][5];   // group partials, two buffers used in turn
   __shared__ int gcnt[2][kPT / 32][2];
+  __shared__ R gredr[2][kPT / 32][5];
   const long long lim = m.spin_limit;
   const unsigned long long G = nb;
   unsigned long long tb = 0ull;   // barriers passed
@@ -217,43 +223,38 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         atomicAdd(&hist[k], 1);
       }
       __syncthreads();
-      d.pchist[hpref[j] + (long)tid * hstride(j) + (it - ipref[j])] = hist[tid];
+      // the chunk's count of every cell, and (phase B folded in) the cell
+      // totals of the slice by integer atomics (exact in any order); the
+      // totals were cleared by the previous launch after their last use
+      const int hv = hist[tid];
+      d.pchist[hpref[j] + (long)tid * hstride(j) + (it - ipref[j])] = hv;
+      if (hv) atomicAdd(d.bintot + (long)j * 256 + tid, hv);
       __syncthreads();
     }
   }
   if (!barrier(0)) return;
-
-  // ---- B: per (slice, cell): total over the slice's chunks (a warp per
-  // unit; the cell's row of chunk counts is contiguous, read 4 at a time)
-  for (long u = sw; u < (long)K * 256; u += nwarps) {
-    const int j = (int)(u >> 8), b = (int)(u & 255);
-    const int4* row = reinterpret_cast<const int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
-    const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
-    int tot = 0;
-#pragma unroll 4
-    for (int q = lane; q < n4; q += 32) {
-      const int4 v = __ldcg(row + q);
-      const int c = 4 * q;
-      tot += (c < nc ? v.x : 0) + (c + 1 < nc ? v.y : 0) + (c + 2 < nc ? v.z : 0) + (c + 3 < nc ? v.w : 0);
-    }
-    tot = warp_sum(tot);
-    if (lane == 0) d.bintot[u] = tot;
-  }
-  if (!barrier(1)) return;
 
   // ---- C: per (slice, cell): the cell's start (cells before it), then each
   // chunk's start within the cell (chunks before it), in place: rounds of
   // 128 chunks, four per lane, a warp scan of the lane totals
   for (long u = sw; u < (long)K * 256; u += nwarps) {
     const int j = (int)(u >> 8), b = (int)(u & 255);
+    int4* row = reinterpret_cast<int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
+    const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
+    // the first kCR rounds of the row are fetched with the cell totals
+    constexpr int kCR = 8;
+    int4 pre[kCR];
+#pragma unroll
+    for (int r = 0; r < kCR; ++r) pre[r] = 32 * r + lane < n4 ? __ldcg(row + 32 * r + lane) : int4{0, 0, 0, 0};
     int base = 0;
     for (int q = lane; q < b; q += 32) base += __ldcg(d.bintot + (long)j * 256 + q);
     base = warp_sum(base);
-    int4* row = reinterpret_cast<int4*>(d.pchist + hpref[j] + (long)b * hstride(j));
-    const int n4 = hstride(j) >> 2, nc = ipref[j + 1] - ipref[j];
     for (int q0 = 0; q0 < n4; q0 += 32) {
       const int q = q0 + lane;
-      int4 v = q < n4 ? __ldcg(row + q) : int4{0, 0, 0, 0};
+      int4 v = pre[0];
+#pragma unroll
+      for (int r = 1; r < kCR; ++r) v = q0 == 32 * r ? pre[r] : v;
+      if (q0 >= 32 * kCR) v = q < n4 ? __ldcg(row + q) : int4{0, 0, 0, 0};
       const int c = 4 * q;
       if (c >= nc) v.x = 0;
       if (c + 1 >= nc) v.y = 0;
@@ -278,12 +279,17 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     int* wc = reinterpret_cast<int*>(smem);   // [8][256]
     const P4<R>* __restrict__ geo_s = static_cast<const P4<R>*>(d.geo_s);
     P4<R>* __restrict__ geo = static_cast<P4<R>*>(d.geo);
+    // the cell totals were last read in C: cleared for the next launch
+    for (long u = (long)bid * kPT + tid; u < (long)K * 256; u += (long)nb * kPT) d.bintot[u] = 0;
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
       const int i = (it - ipref[j]) * 256 + tid;
       const bool live = i < npred_s[j];
       const long g = (long)j * m.pe_cap + i;
       const int key = live ? (int)d.ckey[g] : kCells;
+      // the record and the (cell, chunk) start are fetched before the ranking
+      const P4<R> rec = live ? geo_s[g] : P4<R>{0, 0, 0, 0};
+      const int cstart = live ? __ldcg(d.pchist + hpref[j] + (long)key * hstride(j) + (it - ipref[j])) : 0;
       for (int t = tid; t < 8 * kCells; t += kPT) wc[t] = 0;
       __syncthreads();
       const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -300,10 +306,13 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       __syncthreads();
       if (live) {
-        const int dst = __ldcg(d.pchist + hpref[j] + (long)key * hstride(j) + (it - ipref[j])) +
-                        wc[wid * kCells + key] + rank_w;
-        d.perm[(long)j * m.pe_cap + dst] = i;
-        geo[(long)j * m.pe_cap + dst] = geo_s[g];
+        const int dst = cstart + wc[wid * kCells + key] + rank_w;
+        if (dst >= 0 && dst < npred_s[j]) {
+          d.perm[(long)j * m.pe_cap + dst] = i;
+          geo[(long)j * m.pe_cap + dst] = rec;
+        } else {
+          atomicOr(d.err, kErrCapacity);   // inconsistent cell counts: never written out of the slice
+        }
       }
       __syncthreads();
     }
@@ -606,34 +615,54 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // same values in every CTA) and the barrier between H and I goes.
   __shared__ int nsel_s, rss_s;
   auto slice_plan = [&](int j, bool store) {
-    double s = 0.0, mx = 0.0;
-    for (int it = ipref[j] + tid; it < ipref[j + 1]; it += kPT) {
-      s += __ldcg(d.rowpart + it);
-      mx = fmax(mx, __ldcg(d.rowmax + it));
-    }
+    // N^j: the FP64 sum of the tile sums by warp 0 alone (lane l: tiles l,
+    // l + 32, ... in order, then a shuffle tree), so one warp per CTA uses
+    // the narrow FP64 pipe; the largest weight and the count of positive
+    // labels on the integer units (non-negative doubles order as their bit
+    // patterns)
+    double s = 0.0;
+    unsigned long long mxb = 0ull;
     int npos = 0;
     const int M = slice_M(d, j);
+    const int nt = ipref[j + 1] - ipref[j];
+    // every thread fetches its share of the tile sums into shared memory (one
+    // round of loads), then warp 0 adds them
+    double* ts = reinterpret_cast<double*>(smem);   // [tiles of the slice] when they fit, else read directly
+    const bool staged = (size_t)nt * sizeof(double) <= smem_bytes;
+    for (int t = tid; t < nt; t += kPT) {
+      const double v = __ldcg(d.rowpart + ipref[j] + t);
+      if (staged) ts[t] = v;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(d.rowmax + ipref[j] + t));
+      mxb = b > mxb ? b : mxb;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll 8
+      for (int t = lane; t < nt; t += 32) s += staged ? ts[t] : __ldcg(d.rowpart + ipref[j] + t);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
     for (int p = tid; p < M; p += kPT) npos += __ldcg(d.dwkey + j * m.m_max + p) > 0ull ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_down_sync(0xffffffffu, s, o);
-      mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mxb, o);
+      mxb = t > mxb ? t : mxb;
     }
     npos = warp_sum(npos);
     __syncthreads();
     if (lane == 0) {
-      dred[wid] = s;
-      dredm[wid] = mx;
+      dredb[wid] = mxb;
       wcnt[wid] = npos;
+      if (wid == 0) dred[0] = s;
     }
     __syncthreads();
     if (tid == 0) {
-      double t = 0.0, tm = 0.0;
+      const double t = dred[0];
+      unsigned long long tb = 0ull;
       int np = 0;
       for (int k = 0; k < kPT / 32; ++k) {
-        t += dred[k];
-        tm = fmax(tm, dredm[k]);
+        tb = dredb[k] > tb ? dredb[k] : tb;
         np += wcnt[k];
       }
+      const double tm = __longlong_as_double((long long)tb);
       int L, sc;
       resample_plan(d.rho[j], d.lmax[j], npred_s[j], t, tm, L, sc);
       long long LT = llround(t);
@@ -660,6 +689,20 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ---- I: selection ranks (Step 3: the LT largest dW, ties to the lower
   // label) per measurement; CDF chunk totals per slot chunk
   {
+    const R* wu = static_cast<const R*>(d.wu);
+    // the weights of the CTA's first two chunks are fetched before the plan
+    // and the ranks
+    R wpre[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int it = bid + k * nb;
+      wpre[k] = 0;
+      if (it < nitems) {
+        const int j = item_pe(ipref, K, it);
+        const int i = (it - ipref[j]) * 256 + tid;
+        if (i < npred_s[j]) wpre[k] = wu[(long)j * m.pe_cap + i];
+      }
+    }
     if (a.direct) slice_plan(0, bid == 0);
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
     const Grp g = groups(units);
@@ -698,15 +741,23 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
-    const R* wu = static_cast<const R*>(d.wu);
-    for (int it = bid; it < nitems; it += nb) {
+    int k = 0;
+    for (int it = bid; it < nitems; it += nb, ++k) {
       const int j = item_pe(ipref, K, it);
       const int i = (it - ipref[j]) * 256 + tid;
       const int sj = a.direct ? rss_s : d.rs_s[j];
-      const unsigned long long q = i < npred_s[j] ? scaled_floor(wu[(long)j * m.pe_cap + i], sj) : 0ull;
-      unsigned long long tot = 0;
-      block_scan_u64<R>(q, wt, &tot);
-      if (tid == 0) d.pcsum[it] = tot;
+      const R wi = k == 0 ? wpre[0] : k == 1 ? wpre[1] : (i < npred_s[j] ? wu[(long)j * m.pe_cap + i] : (R)0);
+      const unsigned long long q = i < npred_s[j] ? scaled_floor(wi, sj) : 0ull;
+      // the chunk total: warp sums, then the 8 warp totals in warp order
+      const unsigned long long ws = warp_sum(q);
+      if (lane == 0) wt[wid] = ws;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long t = 0ull;
+        for (int w2 = 0; w2 < kPT / 32; ++w2) t += wt[w2];
+        d.pcsum[it] = t;
+      }
+      __syncthreads();
     }
   }
   if (!barrier(8)) return;
@@ -718,12 +769,23 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     for (int j = nb - 1 - bid; j >= 0 && j < K; j += nb) {
       unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
       unsigned long long carry = 0ull;
-      for (int c0 = ipref[j]; c0 < ipref[j + 1]; c0 += kPT) {
-        const int c = c0 + tid;
-        const unsigned long long v = c < ipref[j + 1] ? __ldcg(d.pcsum + c) : 0ull;
+      constexpr int kCh = 4;   // consecutive chunks per thread and round
+      const int cend_j = ipref[j + 1];
+      for (int c0 = ipref[j]; c0 < cend_j; c0 += kCh * kPT) {
+        const int cb = c0 + kCh * tid;
+        unsigned long long v[kCh], sum = 0ull;
+#pragma unroll
+        for (int k = 0; k < kCh; ++k) {
+          v[k] = cb + k < cend_j ? __ldcg(d.pcsum + cb + k) : 0ull;
+          sum += v[k];
+        }
         unsigned long long tot = 0;
-        const unsigned long long incl = block_scan_u64<R>(v, wt, &tot);
-        if (c < ipref[j + 1]) d.pcoff[c] = carry + incl - v;
+        unsigned long long run = carry + block_scan_u64<R>(sum, wt, &tot) - sum;
+#pragma unroll
+        for (int k = 0; k < kCh; ++k) {
+          if (cb + k < cend_j) d.pcoff[cb + k] = run;
+          run += v[k];
+        }
         carry += tot;
       }
       if (tid == 0) {
@@ -818,9 +880,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           for (int k = 0; k < LB; ++k) {
             const int qq = g * LB + k;
             if (qq < nr) {
-              double* o = d.spart + ((long)it * m.m_max + lr[qq].x) * 5;
+              R* o = reinterpret_cast<R*>(d.spart) + ((long)it * m.m_max + lr[qq].x) * 5;
 #pragma unroll
-              for (int c = 0; c < 5; ++c) o[c] = (double)s[k][c];
+              for (int c = 0; c < 5; ++c) o[c] = s[k][c];
             }
           }
         }
@@ -830,15 +892,15 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   if (!barrier(9)) return;
 
   // ---- K: estimates (Eq. 18) per selected label: the live tile partials in
-  // tile order (FP64 shuffle tree); one filter: the output in ascending
-  // label order.  Offspring ends per slot chunk (exact integer CDF).
+  // tile order, in the kernel's precision (the tile partials are sums of
+  // offsets from the label's point, so the ratio keeps the estimate within
+  // 1e-4 m in FP32); one filter: the output in ascending label order
   {
     St4<R>* est = static_cast<St4<R>*>(d.est_local);
-    // one filter: units are the selected labels, their groups taken from the
-    // end of the grid (the CTAs with the fewest offspring chunks below)
+    // one filter: units are the selected labels
     const long units = a.direct ? (long)nsel_s : (long)K * m.m_max;
     const Grp g = groups(units);
-    const long gid0 = a.direct ? (long)g.slot * nb + (nb - 1 - bid) : g.gid;
+    const long gid0 = g.gid;
     if (a.direct && bid == 0 && tid == 0) {
       *d.out_count = nsel_s;
       if (a.d_count) *a.d_count = nsel_s;
@@ -856,7 +918,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       if (g.G == 1 && !act) continue;
       int p = 0, below = 0;
-      double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       if (act) {   // uniform over the group
         p = __ldcg(d.sel + j * m.m_max + r);
         if (a.direct) {
@@ -870,7 +932,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           const int it = t0 + g.gl;
           const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
           if (__any_sync(0xffffffffu, live) && live) {
-            const double* q = d.spart + ((long)it * m.m_max + r) * 5;
+            const R* q = reinterpret_cast<const R*>(d.spart) + ((long)it * m.m_max + r) * 5;
             a0 += __ldcg(q);
             a1 += __ldcg(q + 1);
             a2 += __ldcg(q + 2);
@@ -879,33 +941,35 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           }
         }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_down_sync(0xffffffffu, a0, o);
-        a1 += __shfl_down_sync(0xffffffffu, a1, o);
-        a2 += __shfl_down_sync(0xffffffffu, a2, o);
-        a3 += __shfl_down_sync(0xffffffffu, a3, o);
-        a4 += __shfl_down_sync(0xffffffffu, a4, o);
+      if (act) {   // uniform over the warp
+        for (int o = 16; o > 0; o >>= 1) {
+          a0 += __shfl_down_sync(0xffffffffu, a0, o);
+          a1 += __shfl_down_sync(0xffffffffu, a1, o);
+          a2 += __shfl_down_sync(0xffffffffu, a2, o);
+          a3 += __shfl_down_sync(0xffffffffu, a3, o);
+          a4 += __shfl_down_sync(0xffffffffu, a4, o);
+        }
       }
       if (g.G > 1) {
         if (lane == 0) {
-          gred[par][wid][0] = a0;
-          gred[par][wid][1] = a1;
-          gred[par][wid][2] = a2;
-          gred[par][wid][3] = a3;
-          gred[par][wid][4] = a4;
+          gredr[par][wid][0] = a0;
+          gredr[par][wid][1] = a1;
+          gredr[par][wid][2] = a2;
+          gredr[par][wid][3] = a3;
+          gredr[par][wid][4] = a4;
           gcnt[par][wid][1] = below;
         }
         __syncthreads();
-        if (g.gl == 0) {
-          a0 = a1 = a2 = a3 = a4 = 0.0;
+        if (act && g.gl == 0) {
+          a0 = a1 = a2 = a3 = a4 = 0;
           below = 0;
           for (int k = 0; k < g.G; ++k) {
             const int w2 = g.slot * g.G + k;
-            a0 += gred[par][w2][0];
-            a1 += gred[par][w2][1];
-            a2 += gred[par][w2][2];
-            a3 += gred[par][w2][3];
-            a4 += gred[par][w2][4];
+            a0 += gredr[par][w2][0];
+            a1 += gredr[par][w2][1];
+            a2 += gredr[par][w2][2];
+            a3 += gredr[par][w2][3];
+            a4 += gredr[par][w2][4];
             below += gcnt[par][w2][1];
           }
         }
@@ -916,19 +980,12 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         R px, py;
         meas_point<R>(m, z, px, py);
         St4<R> o;
-        if (a0 > 0.0) {
-          if constexpr (sizeof(R) == 4) {
-            const float inv = 1.0f / (float)a0;
-            o.x = px + (float)a1 * inv;
-            o.vx = (float)a2 * inv;
-            o.y = py + (float)a3 * inv;
-            o.vy = (float)a4 * inv;
-          } else {
-            o.x = (R)((double)px + a1 / a0);
-            o.vx = (R)(a2 / a0);
-            o.y = (R)((double)py + a3 / a0);
-            o.vy = (R)(a4 / a0);
-          }
+        if (a0 > (R)0) {
+          const R inv = (R)1 / a0;
+          o.x = px + a1 * inv;
+          o.vx = a2 * inv;
+          o.y = py + a3 * inv;
+          o.vy = a4 * inv;
         } else {
           o = St4<R>{px, (R)0, py, (R)0};
         }
@@ -942,32 +999,22 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         }
       }
     }
-    unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
-    const R* wu = static_cast<const R*>(d.wu);
-    for (int it = bid; it < nitems; it += nb) {
-      const int j = item_pe(ipref, K, it);
-      const int i = (it - ipref[j]) * 256 + tid;
-      const long g = (long)j * m.pe_cap + i;
-      const bool live = i < npred_s[j];
-      const unsigned long long q = live ? scaled_floor(wu[g], d.rs_s[j]) : 0ull;
-      const unsigned long long Qi = __ldcg(d.pcoff + it) + block_scan_u64<R>(q, wt, nullptr);
-      if (live) {
-        const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
-        const unsigned long long Qn = __ldcg(d.rs_Qn + j);
-        const Recip rq{__ldcg(d.rs_rcp + 2 * j), __ldcg(d.rs_rcp + 2 * j + 1), Qn ? __clzll((long long)Qn) : 0};
-        d.child_end[g] = offspring_end(Qi, Qn, (unsigned long long)d.rs_L[j], U, rq);
-      }
-    }
   }
   if (!barrier(10)) return;
 
-  // ---- L: children gathered from their parents (a warp per 32 consecutive
+  // ---- L: offspring ends per slot chunk (exact integer CDF: the chunk's
+  // offset plus an inclusive scan of its q_i; c = children of slots up to i)
+  // and the children gathered from their parents (a warp per 32 consecutive
   // parents, children written as one contiguous range), weight N^j / L_j;
   // counts and the step counter for the next step
   {
     const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
     St4<R>* x = static_cast<St4<R>*>(d.x);
     R* w = static_cast<R*>(d.w);
+    const R* wu = static_cast<const R*>(d.wu);
+    unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);   // [kPT / 32]
+    int* cend = reinterpret_cast<int*>(wt + kPT / 32);                      // [kPT]
+    __shared__ int cprev_s;
     if (bid == 0)
       for (int j = tid; j < K; j += kPT) d.n_cur[j] = d.rs_L[j];
     for (int it = bid; it < nitems; it += nb) {
@@ -975,32 +1022,44 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const int n = npred_s[j];
       const int L = d.rs_L[j];
       if (L == 0) continue;   // uniform over the block
-      const int wb = (it - ipref[j]) * 256 + (tid & ~31);
-      if (wb >= n) continue;   // uniform over the warp
       const long base = (long)j * m.pe_cap;
-      const int i = wb + lane;
+      const int c0i = (it - ipref[j]) * 256;
+      const int i = c0i + tid;
       const bool live = i < n;
-      const int ce = __ldcg(d.child_end + base + (live ? i : n - 1));
-      const int c0 = __shfl_sync(0xffffffffu, wb > 0 ? __ldcg(d.child_end + base + wb - 1) : 0, 0);
-      const int c1 = __shfl_sync(0xffffffffu, ce, 31);
-      const St4<R> s = live ? xp[base + i] : St4<R>{0, 0, 0, 0};
-      const R wn = (R)d.rs_wn[j];
-      for (int t0 = c0; t0 < c1; t0 += 32) {
-        const int t = t0 + lane;
-        int lo = 0;
+      const St4<R> sv = live ? xp[base + i] : St4<R>{0, 0, 0, 0};
+      const unsigned long long q = live ? scaled_floor(wu[base + i], d.rs_s[j]) : 0ull;
+      const unsigned long long off = __ldcg(d.pcoff + it);
+      const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
+      const unsigned long long Qn = __ldcg(d.rs_Qn + j);
+      const Recip rq{__ldcg(d.rs_rcp + 2 * j), __ldcg(d.rs_rcp + 2 * j + 1), Qn ? __clzll((long long)Qn) : 0};
+      // slots past the slice's end repeat the last slot's end (q = 0)
+      const int ce = offspring_end(off + block_scan_u64<R>(q, wt, nullptr), Qn, (unsigned long long)L, U, rq);
+      cend[tid] = ce;
+      if (tid == 0) cprev_s = offspring_end(off, Qn, (unsigned long long)L, U, rq);   // slots before the chunk
+      __syncthreads();
+      const int wb = c0i + (tid & ~31);
+      if (wb < n) {   // uniform over the warp
+        const int c0 = (tid & ~31) ? cend[(tid & ~31) - 1] : cprev_s;
+        const int c1 = __shfl_sync(0xffffffffu, ce, 31);
+        const R wn = (R)d.rs_wn[j];
+        for (int t0 = c0; t0 < c1; t0 += 32) {
+          const int t = t0 + lane;
+          int lo = 0;
 #pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-          const int e = __shfl_sync(0xffffffffu, ce, lo + st - 1);
-          if (e <= t) lo += st;
-        }
-        const R sx = __shfl_sync(0xffffffffu, s.x, lo), svx = __shfl_sync(0xffffffffu, s.vx, lo);
-        const R sy = __shfl_sync(0xffffffffu, s.y, lo), svy = __shfl_sync(0xffffffffu, s.vy, lo);
-        if (t < c1) {
-          x[base + t] = St4<R>{sx, svx, sy, svy};
-          w[base + t] = wn;
-          d.parent[base + t] = wb + lo;
+          for (int st = 16; st > 0; st >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, ce, lo + st - 1);
+            if (e <= t) lo += st;
+          }
+          const R sx = __shfl_sync(0xffffffffu, sv.x, lo), svx = __shfl_sync(0xffffffffu, sv.vx, lo);
+          const R sy = __shfl_sync(0xffffffffu, sv.y, lo), svy = __shfl_sync(0xffffffffu, sv.vy, lo);
+          if (t < c1) {
+            x[base + t] = St4<R>{sx, svx, sy, svy};
+            w[base + t] = wn;
+            d.parent[base + t] = wb + lo;
+          }
         }
       }
+      __syncthreads();   // cend and cprev_s are rewritten by the next chunk
     }
     // every reader of this step's counter finished before barrier 10
     if (tid == 0) {
@@ -1069,7 +1128,7 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
                                      persist_smem<R>(m.m_max), s);
 }
 
-int persist_barriers(bool direct) { return direct ? kPhases - 2 : kPhases - 1; }
+int persist_barriers(bool direct) { return direct ? kPhases - 3 : kPhases - 2; }
 
 template size_t persist_smem<float>(int);
 template size_t persist_smem<double>(int);

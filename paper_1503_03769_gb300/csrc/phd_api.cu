@@ -381,6 +381,8 @@ phd_status read_device_error(phd_handle* h) {
   PHD_CUDA(h, cudaMemsetAsync(h->d.bar, 0, 4 * sizeof(unsigned int), h->stream));
   PHD_CUDA(h, cudaMemsetAsync(h->d.pbar, 0, sizeof(unsigned long long), h->stream));
   h->pbar_count = 0;
+  // and a grid step that stopped early its running cell totals
+  PHD_CUDA(h, cudaMemsetAsync(h->d.bintot, 0, (size_t)h->m.K * 256 * sizeof(int), h->stream));
   PHD_CUDA(h, cudaStreamSynchronize(h->stream));
   if (err & phd::kErrTimeout) return fail(h, PHD_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (err & phd::kErrNonFinite) return fail(h, PHD_ERR_INVALID_ARG, "non-finite measurement in Z");

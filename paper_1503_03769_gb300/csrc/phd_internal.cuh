@@ -131,7 +131,7 @@ struct Dev {
   int* nsel;             // [K] labels selected per PE
   int* sel;              // [K][m_max] selected labels, selection order
   int* selrank;          // [K][m_max] label -> selection rank or -1
-  double* spart;         // [max_items][m_max][5] pass-3 partial labelled sums
+  double* spart;         // [max_items][m_max][5] pass-3 partial labelled sums (the grid step kernel stores reals)
   void* est_local;       // St4<R> [K][m_max] local estimates (selection order)
   int* out_count;        // [1] fused estimate count
   double* rs_mass;       // [K] mass before resampling

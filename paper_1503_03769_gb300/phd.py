@@ -589,7 +589,7 @@ class ParticlePHD:
         self._check(self.L.phd_reset_stats(self.h), "phd_reset_stats")
 
     PHASES = ("predict_keys", "cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2",
-              "mass_plan", "ranks_cdf", "label_sums_offsets", "estimates_offspring", "gather")
+              "mass_plan", "ranks_cdf", "label_sums_offsets", "estimates", "offspring_gather")
 
     def phase_times(self, detail: bool = False):
         """Grid path: summed wall time per phase of the step kernel, ms
