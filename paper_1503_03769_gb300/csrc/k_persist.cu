@@ -7,8 +7,10 @@
 // one filter (one PE) or a batch of independent runs.  What changes is the
 // organisation of the work, which on the gated dense workloads is what the
 // staged step's time goes to (a dozen launches of latency-bound kernels):
-//  - every phase is one sweep of the grid over work items of 256 particles
-//    (or over measurements / labels), with no launch between phases;
+//  - every phase is one sweep of the grid over work items: chunks of 256
+//    particles (prediction, spatial order, CDF, gather), tiles of 512 for the
+//    pair passes (two particles per thread, so most CTAs hold one tile of a
+//    large slice), or measurements / labels; no launch between phases;
 //  - the spatial order of the pair passes (a stable counting sort on a 16 x 16
 //    grid over measurement space) is built in three phases (chunk histograms
 //    with the prediction, per-bin totals, per-bin starts) and its records
@@ -40,7 +42,8 @@
 namespace phd {
 
 constexpr int kPT = 256;      // threads per CTA
-constexpr int kPMB = 4;       // pass 1: measurements per thread
+constexpr int kPMB = 4;       // pass 1: measurements per warp group
+constexpr int kGT = 512;      // particles of a pair-pass tile (two per thread)
 constexpr int kPhases = 12;
 
 template <class R> struct PersistArgs {
@@ -106,7 +109,8 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   extern __shared__ __align__(32) unsigned char smem[];
   unsigned smem_bytes;   // dynamic shared memory of the launch
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(smem_bytes));
-  __shared__ int ipref[kMaxPE + 1];   // items (256-particle chunks / tiles) per slice, prefix
+  __shared__ int ipref[kMaxPE + 1];   // 256-particle chunks per slice, prefix
+  __shared__ int tpref[kMaxPE + 1];   // pair-pass tiles (kGT particles) per slice, prefix
   __shared__ int hpref[kMaxPE + 1];   // chunk-histogram rows per slice: 256 x (items rounded up to 4), prefix
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
   __shared__ int wcnt[kPT / 32];
@@ -171,8 +175,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
   __syncthreads();
   slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + 255) / 256; });
+  slice_prefix(K, tpref, [&](int j) { return (npred_s[j] + kGT - 1) / kGT; });
   slice_prefix(K, hpref, [&](int j) { return 256 * ((((npred_s[j] + 255) / 256) + 3) & ~3); });
   const int nitems = ipref[K];
+  const int ntiles = tpref[K];
   const long T = d.max_items;   // row stride of the gate bits [word][tile]
   // chunk histograms: slice j, cell b, chunk c at pchist[hpref[j] + b * hstride(j) + c]
   auto hstride = [&](int j) { return ((ipref[j + 1] - ipref[j]) + 3) & ~3; };
@@ -322,19 +328,28 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
   const P4<R>* __restrict__ geo = static_cast<const P4<R>*>(d.geo);
-  // the tile's box (every thread loads its particle's record) and the
+  // the tile's box (every thread loads its two particles' records) and the
   // measurements of slice j that can reach it: live list in smem (lidx, in
   // measurement order) and, when `record`, the tile's gate bits
-  auto tile_gate = [&](int it, int j, int cnt, P4<R>& q, int* lidx, bool record) -> int {
+  auto tile_gate = [&](int it, int j, int cnt, P4<R>& q0, P4<R>& q1, int* lidx, bool record) -> int {
     const R inf = (R)INFINITY;
     R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
-    q = P4<R>{0, 0, 0, 0};
+    q0 = P4<R>{0, 0, 0, 0};
+    q1 = q0;
+    const long base = (long)j * m.pe_cap + (long)(it - tpref[j]) * kGT;
     if (tid < cnt) {
-      q = geo[(long)j * m.pe_cap + (long)(it - ipref[j]) * 256 + tid];
-      lo0 = q.h0;
-      hi0 = q.h0;
-      lo1 = q.h1;
-      hi1 = q.h1;
+      q0 = geo[base + tid];
+      lo0 = q0.h0;
+      hi0 = q0.h0;
+      lo1 = q0.h1;
+      hi1 = q0.h1;
+    }
+    if (tid + kPT < cnt) {
+      q1 = geo[base + kPT + tid];
+      lo0 = fmin(lo0, q1.h0);
+      hi0 = fmax(hi0, q1.h0);
+      lo1 = fmin(lo1, q1.h1);
+      hi1 = fmax(hi1, q1.h1);
     }
     const Box<R> box = block_box<R>(lo0, hi0, lo1, hi1, bsh);
     const int M = slice_M(d, j);
@@ -410,15 +425,16 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ---- E: pass 1 (Eq. 7): tile partials of the live measurements, in FP32
   // within the tile, written as FP64
   {
-    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);        // [256]
-    int* lidx = reinterpret_cast<int*>(sp + 256);       // [m_max]
-    for (int it = bid; it < nitems; it += nb) {
-      const int j = item_pe(ipref, K, it);
-      const int cnt = min(256, npred_s[j] - (it - ipref[j]) * 256);
-      P4<R> q;
+    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);        // [kGT]
+    int* lidx = reinterpret_cast<int*>(sp + kGT);     // [m_max]
+    for (int it = bid; it < ntiles; it += nb) {
+      const int j = item_pe(tpref, K, it);
+      const int cnt = min(kGT, npred_s[j] - (it - tpref[j]) * kGT);
+      P4<R> q0, q1;
       __syncthreads();
-      const int nl = tile_gate(it, j, cnt, q, lidx, true);
-      sp[tid] = q;
+      const int nl = tile_gate(it, j, cnt, q0, q1, lidx, true);
+      sp[tid] = q0;
+      sp[tid + kPT] = q1;
       if (tid == 0 && nl > 0) atomicAdd(&d.stats[4], (unsigned long long)nl * (unsigned long long)cnt);
       const V2<R>* __restrict__ Z = slice_Z<R>(d, j);
       __syncthreads();
@@ -481,9 +497,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       double c = 0.0;
       if (act) {   // uniform over the group
         const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-        const int t1 = ipref[j + 1];
+        const int t1 = tpref[j + 1];
 #pragma unroll 4
-        for (int t0 = ipref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds: every lane runs every round
+        for (int t0 = tpref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds: every lane runs every round
           const int it = t0 + g.gl;
           const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
           if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
@@ -551,17 +567,23 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
     R* __restrict__ wu = static_cast<R*>(d.wu);
     const R miss = cc.miss;
-    for (int it = bid; it < nitems; it += nb) {
-      const int j = item_pe(ipref, K, it);
-      const int t = it - ipref[j];
-      const int cnt = min(256, npred_s[j] - t * 256);
-      const long base = (long)j * m.pe_cap + (long)t * 256;
-      // the particle's record and slot are fetched before the gate bits are read
-      P4<R> q{0, 0, 0, 0};
-      int slot = 0;
-      if (tid < cnt) {
-        q = geo[base + tid];
-        slot = d.perm[base + tid];
+    for (int it = bid; it < ntiles; it += nb) {
+      const int j = item_pe(tpref, K, it);
+      const int t = it - tpref[j];
+      const int cnt = min(kGT, npred_s[j] - t * kGT);
+      const long base = (long)j * m.pe_cap + (long)t * kGT;
+      // the two particles' records and slots are fetched before the gate bits
+      // are read
+      P4<R> q0{0, 0, 0, 0}, q1{0, 0, 0, 0};
+      int slot0 = 0, slot1 = 0;
+      const bool has0 = tid < cnt, has1 = tid + kPT < cnt;
+      if (has0) {
+        q0 = geo[base + tid];
+        slot0 = d.perm[base + tid];
+      }
+      if (has1) {
+        q1 = geo[base + kPT + tid];
+        slot1 = d.perm[base + kPT + tid];
       }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
@@ -572,20 +594,31 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         zs[e] = Z4<R>{z.a, z.b, ginv[j * m.m_max + p], (R)0};
       }
       __syncthreads();
-      R wv = 0;
-      if (tid < cnt) {
-        R a0 = 0, a1 = 0;
+      R wv0 = 0, wv1 = 0;
+      if (has0) {   // both particles in one walk of the live list
+        R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
         for (int e = 0; e < nl; ++e) {
           const Z4<R> za = zs[e];
-          const R v = exp2_neg(Q(za.z0, za.z1, q.h0, q.h1, q.h1lo)) * za.g;
-          if (lidx[e] & 1) a1 += v; else a0 += v;
+          const R v = exp2_neg(Q(za.z0, za.z1, q0.h0, q0.h1, q0.h1lo)) * za.g;
+          const R u = exp2_neg(Q(za.z0, za.z1, q1.h0, q1.h1, q1.h1lo)) * za.g;
+          if (lidx[e] & 1) {
+            a1 += v;
+            b1 += u;
+          } else {
+            a0 += v;
+            b0 += u;
+          }
         }
-        wv = (miss + (a0 + a1)) * q.w;
-        wu[(long)j * m.pe_cap + slot] = wv;
+        wv0 = (miss + (a0 + a1)) * q0.w;
+        wu[(long)j * m.pe_cap + slot0] = wv0;
+        if (has1) {
+          wv1 = (miss + (b0 + b1)) * q1.w;
+          wu[(long)j * m.pe_cap + slot1] = wv1;
+        }
       }
       // tile sum and largest weight: warps in the kernel's precision, warp
       // totals in FP64 in warp order
-      R sv = wv, mv = wv;
+      R sv = wv0 + wv1, mv = wv1 > wv0 ? wv1 : wv0;
       for (int o = 16; o > 0; o >>= 1) {
         sv += __shfl_down_sync(0xffffffffu, sv, o);
         const R v2 = __shfl_down_sync(0xffffffffu, mv, o);
@@ -593,17 +626,18 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       if (lane == 0) {
         dred[wid] = (double)sv;
-        dredm[wid] = (double)mv;
+        bsh[wid] = mv;
       }
       __syncthreads();
       if (tid == 0) {
-        double s = 0.0, mx = 0.0;
+        double s = 0.0;
+        R mx = 0;
         for (int k = 0; k < kPT / 32; ++k) {
           s += dred[k];
-          mx = fmax(mx, dredm[k]);
+          mx = bsh[k] > mx ? bsh[k] : mx;
         }
         d.rowpart[it] = s;
-        d.rowmax[it] = mx;
+        d.rowmax[it] = (double)mx;
       }
     }
   }
@@ -624,21 +658,21 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     unsigned long long mxb = 0ull;
     int npos = 0;
     const int M = slice_M(d, j);
-    const int nt = ipref[j + 1] - ipref[j];
+    const int nt = tpref[j + 1] - tpref[j];
     // every thread fetches its share of the tile sums into shared memory (one
     // round of loads), then warp 0 adds them
     double* ts = reinterpret_cast<double*>(smem);   // [tiles of the slice] when they fit, else read directly
     const bool staged = (size_t)nt * sizeof(double) <= smem_bytes;
     for (int t = tid; t < nt; t += kPT) {
-      const double v = __ldcg(d.rowpart + ipref[j] + t);
+      const double v = __ldcg(d.rowpart + tpref[j] + t);
       if (staged) ts[t] = v;
-      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(d.rowmax + ipref[j] + t));
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(d.rowmax + tpref[j] + t));
       mxb = b > mxb ? b : mxb;
     }
     __syncthreads();
     if (wid == 0) {
 #pragma unroll 8
-      for (int t = lane; t < nt; t += 32) s += staged ? ts[t] : __ldcg(d.rowpart + ipref[j] + t);
+      for (int t = lane; t < nt; t += 32) s += staged ? ts[t] : __ldcg(d.rowpart + tpref[j] + t);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
     for (int p = tid; p < M; p += kPT) npos += __ldcg(d.dwkey + j * m.m_max + p) > 0ull ? 1 : 0;
@@ -796,31 +830,39 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       __syncthreads();
     }
-    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);               // [256]
-    St4<R>* sx = reinterpret_cast<St4<R>*>(sp + 256);          // [256]
-    int2* lr = reinterpret_cast<int2*>(sx + 256);               // [m_max] live selected (rank, measurement)
+    P4<R>* sp = reinterpret_cast<P4<R>*>(smem);               // [kGT]
+    St4<R>* sx = reinterpret_cast<St4<R>*>(sp + kGT);        // [kGT]
+    int2* lr = reinterpret_cast<int2*>(sx + kGT);             // [m_max] live selected (rank, measurement)
     int* lidx = reinterpret_cast<int*>(lr + m.m_max);            // [m_max] live measurements
     const St4<R>* __restrict__ xs = static_cast<const St4<R>*>(d.x_alt);
     constexpr int LB = 2;   // labels per thread group
-    for (int it = bid; it < nitems; it += nb) {
-      const int j = item_pe(ipref, K, it);
+    for (int it = bid; it < ntiles; it += nb) {
+      const int j = item_pe(tpref, K, it);
       const int ns = a.direct ? nsel_s : __ldcg(d.nsel + j);
       if (ns <= 0) continue;   // uniform over the block
-      const int t = it - ipref[j];
-      const int cnt = min(256, npred_s[j] - t * 256);
-      const long base = (long)j * m.pe_cap + (long)t * 256;
+      const int t = it - tpref[j];
+      const int cnt = min(kGT, npred_s[j] - t * kGT);
+      const long base = (long)j * m.pe_cap + (long)t * kGT;
       // the tile's records are fetched before its gate bits are read
-      P4<R> qg{0, 0, 0, 0};
-      St4<R> xg{0, 0, 0, 0};
+      P4<R> qg0{0, 0, 0, 0}, qg1{0, 0, 0, 0};
+      St4<R> xg0{0, 0, 0, 0}, xg1{0, 0, 0, 0};
       if (tid < cnt) {
-        qg = geo[base + tid];
-        xg = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+        qg0 = geo[base + tid];
+        xg0 = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+      }
+      if (tid + kPT < cnt) {
+        qg1 = geo[base + kPT + tid];
+        xg1 = xs[(long)j * m.pe_cap + d.perm[base + kPT + tid]];
       }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
       if (tid < cnt) {
-        sp[tid] = qg;
-        sx[tid] = xg;
+        sp[tid] = qg0;
+        sx[tid] = xg0;
+      }
+      if (tid + kPT < cnt) {
+        sp[tid + kPT] = qg1;
+        sx[tid + kPT] = xg1;
       }
       // the selected labels among the live measurements (any order: a
       // label's sums do not depend on its place in the list)
@@ -926,9 +968,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
           below = warp_sum(below);
         }
         const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-        const int t1 = ipref[j + 1];
+        const int t1 = tpref[j + 1];
 #pragma unroll 4
-        for (int t0 = ipref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds
+        for (int t0 = tpref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds
           const int it = t0 + g.gl;
           const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
           if (__any_sync(0xffffffffu, live) && live) {
@@ -1079,9 +1121,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
 template <class R> size_t persist_smem(int m_max) {
   const size_t mm = ((size_t)m_max + 7) & ~(size_t)7;
   const size_t a = 8 * kCells * sizeof(int);                                         // D
-  const size_t e = 256 * sizeof(P4<R>) + mm * sizeof(int);                            // E
+  const size_t e = kGT * sizeof(P4<R>) + mm * sizeof(int);                          // E
   const size_t g = mm * sizeof(int) + mm * sizeof(Z4<R>);                            // G
-  const size_t j = 256 * sizeof(P4<R>) + 256 * sizeof(St4<R>) + mm * sizeof(int2) + mm * sizeof(int);  // J
+  const size_t j = kGT * sizeof(P4<R>) + kGT * sizeof(St4<R>) + mm * sizeof(int2) + mm * sizeof(int);  // J
   size_t s = a;
   if (e > s) s = e;
   if (g > s) s = g;

@@ -605,8 +605,24 @@ phd_status stage_z_only(phd_handle* h, const void* Z, int M);
 bool use_fused(const phd_handle* h) {
   return h->fused_ok && !h->m.learned && (h->path == PHD_PATH_AUTO || h->path == PHD_PATH_FUSED);
 }
+// AUTO takes the grid path while the handle's capacity is at most kGridAutoItems
+// 256-particle chunks per CTA of the step kernel (capacities run a few times
+// the particles a step holds: the dense 100-target filter has 5.4 chunks of
+// capacity per CTA and ~2 in use): there each phase is a few latency-bound
+// rounds per CTA and the launches and barriers of the staged graph are what
+// the step's time goes to.  Past that (batches of tens to hundreds of runs,
+// 50-200 chunks per CTA) the phases become long serial chains at 3 CTAs per
+// SM, and the staged kernels (more resident threads, autotuned pair-pass
+// shapes) are faster (256 runs, ~1e7 particles: 1.27 ms per batched step
+// staged, 2.02 ms grid).
+constexpr double kGridAutoItems = 16.0;
+bool grid_auto(const phd_handle* h) {
+  const double items = (double)h->m.K * (double)((h->cfg.pe_cap + 255) / 256);
+  return h->pgrid > 0 && items <= kGridAutoItems * (double)h->pgrid;
+}
 bool use_grid(const phd_handle* h) {
-  return h->pgrid > 0 && !h->m.learned && (h->path == PHD_PATH_GRID || (h->path == PHD_PATH_AUTO && !use_fused(h)));
+  return h->pgrid > 0 && !h->m.learned &&
+         (h->path == PHD_PATH_GRID || (h->path == PHD_PATH_AUTO && !use_fused(h) && grid_auto(h)));
 }
 
 // One launch of the grid path's step kernel.  One filter (direct): the scan
