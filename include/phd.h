@@ -311,7 +311,8 @@ phd_status phd_run(phd_handle *h, const void *d_Z, const int32_t *d_offsets, int
  * whole GPU, its phases (prediction, spatial order, the two pair passes,
  * selection, label sums, resampling) separated by grid-wide barriers with
  * bounded waits (available for one-PE filters and batches of independent
- * runs, without a birth network; the pair passes always walk the spatial
+ * runs; with a birth network the scan is staged and the network's head,
+ * mixture table and draws run as kernels before it; the pair passes always walk the spatial
  * order, the gate setting of phd_set_tuning applies); PHD_PATH_STAGED: the
  * stage kernels of phd_predict .. phd_resample as a CUDA graph;
  * PHD_PATH_AUTO (default): fused when available, else grid when available

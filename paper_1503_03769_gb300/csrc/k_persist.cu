@@ -213,15 +213,22 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       __syncthreads();
       if (i < npred_s[j]) {
         const long g = (long)j * m.pe_cap + i;
-        R n1, n2, u1, u2;
-        draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
         const bool surv = i < d.n_cur[j];
         St4<R> o;
         R wo;
-        predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j), n1, n2,
-                        u1, u2, o, wo);
-        xp[g] = o;
-        wp[g] = wo;
+        if (!surv && m.learned) {
+          // a birth of the measurement-driven proposal, drawn into its slot
+          // before the launch
+          o = xp[g];
+          wo = wp[g];
+        } else {
+          R n1, n2, u1, u2;
+          draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
+          predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j), n1,
+                          n2, u1, u2, o, wo);
+          xp[g] = o;
+          wp[g] = wo;
+        }
         const H3<R> h = meas_h<R>(m, o, tab);
         geo_s[g] = P4<R>{h.h0, h.h1, h.h1lo, wo};
         const int k = cell_key(m, (float)h.h0, (float)h.h1);

@@ -621,7 +621,7 @@ bool grid_auto(const phd_handle* h) {
   return h->pgrid > 0 && items <= kGridAutoItems * (double)h->pgrid;
 }
 bool use_grid(const phd_handle* h) {
-  return h->pgrid > 0 && !h->m.learned &&
+  return h->pgrid > 0 &&
          (h->path == PHD_PATH_GRID || (h->path == PHD_PATH_AUTO && !use_fused(h) && grid_auto(h)));
 }
 
@@ -718,8 +718,24 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
                    direct ? cap : h->cfg.m_max);
   } else if (grid) {
     const bool direct = cap > 0 && d_states && d_labels;
-    st = run_grid(h, Z, M, noise, u, direct ? d_states : h->out_states, direct ? d_labels : h->out_labels,
-                  direct ? cap : h->cfg.m_max, d_count);
+    const void* Zk = Z;
+    st = PHD_OK;
+    if (h->m.learned) {
+      // measurement-driven births before the step kernel: the scan staged,
+      // the network head and mixture table, the draws into the birth slots
+      // (the step kernel's prediction leaves those slots as drawn)
+      st = stage_z_only(h, Z, M);
+      if (st == PHD_OK) {
+        cudaError_t e = phd::launch_birth_head(h->d, h->m, h->stream);
+        if (e == cudaSuccess) e = phd::launch_birth_draw(h->d, h->m, static_cast<const float*>(noise), h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "learned birth");
+        h->launches += kNBirth;
+      }
+      Zk = h->d.Z;
+    }
+    if (st == PHD_OK)
+      st = run_grid(h, Zk, M, noise, u, direct ? d_states : h->out_states, direct ? d_labels : h->out_labels,
+                    direct ? cap : h->cfg.m_max, d_count);
   } else if (noise || u || xu) {
     if (h->m.learned) {
       st = stage_z_only(h, Z, M);

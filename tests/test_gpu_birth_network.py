@@ -219,6 +219,53 @@ def test_learned_births_match_oracle(model_name, alpha):
     f.close()
 
 
+def test_learned_grid_step_matches_staged():
+    """The grid path draws the measurement-driven births with the staged
+    path's own kernels (network head, mixture table, draws) before its step
+    kernel, whose prediction leaves the birth slots as drawn.  On the same
+    state, scan and injected random numbers the two paths' predicted sets are
+    equal bit for bit, births included (the births themselves are held to
+    the oracle by test_learned_births_match_oracle), and the update,
+    extraction and resampling agree within the FP32 grouping tolerance (the
+    grid path sums in other tiles)."""
+    from paper_1503_03769_gb300 import ParticlePHD
+    from gpu_harness import exact_particles
+    w = scenario.workload("dense_rb_100t", precision="fp32", n_targets=10, clutter_rate=50.0,
+                          particles_per_target=300, birth_count=2000, birth_steps=(1,) * 10)
+    P = scenario.mlp_params(4)
+    sc = scenario.simulate(w, 21, steps=4)
+    Z = np.asarray(sc.meas[3], np.float32)
+    cen = sc.truth[3][:, [0, 2]]
+    x, wt = exact_particles(np.random.default_rng(5), w, 3000, centres=cen, spread=20.0, mass=float(len(cen)))
+    plain = scenario.step_noise(17, 3, 1, w.pe_cap, np.float32)
+    extra = scenario.birth_extra_noise(17, 3, 1, w.birth_count, np.float32)
+    noise = np.concatenate([plain, extra])
+    u = scenario.resample_u32(17, 3, 1)
+    out = {}
+    for path in ["staged", "grid"]:
+        f = ParticlePHD(w, seed=3, device="cuda:0")
+        f.set_birth_proposal(torch.tensor(P, dtype=torch.float32, device="cuda"), 0.2)
+        f.set_path(path)
+        assert f.get_path() == path
+        f.set_state([x], [wt])
+        s_, l_ = f.step_inject(Z, noise=noise, u=u)
+        xp, wp, wu = f.get_predicted()
+        C, mass = f.get_update()
+        xr, wr = f.get_state()
+        out[path] = (xp[0], wp[0], wu[0], C[0, :len(Z)], mass[0], s_.cpu().numpy(), l_.cpu().numpy(), len(xr[0]))
+        f.close()
+    a, b = out["staged"], out["grid"]
+    assert len(a[0]) == len(x) + w.birth_count
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    kap = oracle.kappa(oracle.model(w))
+    np.testing.assert_allclose(b[3], a[3], rtol=1e-4, atol=1e-7 * kap)
+    np.testing.assert_allclose(b[2], a[2], rtol=1e-4, atol=1e-9 * float(np.mean(a[2])))
+    assert abs(b[4] - a[4]) <= 1e-5 * a[4]
+    assert np.array_equal(a[6], b[6])
+    np.testing.assert_allclose(b[5], a[5], atol=1e-3)
+    assert abs(b[7] - a[7]) <= 1
+
+
 def test_learned_step_graph_and_unload():
     """Free-running steps with the network (graph path), the plain path back
     after unloading, and the refusals."""
