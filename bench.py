@@ -577,11 +577,11 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
         # normaliser and pass-2 phases (Eq. 7-8 with the order the passes walk)
         phases = {k: v - head_phases.get(k, 0.0) for k, v in f.phase_times().items()}
         step_ms = upd_ms
-        upd_ms = sum(phases[k] for k in ("cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2"))
+        upd_ms = sum(phases[k] for k in ("cell_starts", "scatter", "pass1", "normalisers", "pass2_ranks"))
     achieved = (pairs / (upd_ms * 1e-3)) / 1e12 if upd_ms > 0 else 0.0
     ev_frac = st["pairs_evaluated"] / pairs if pairs else None
     kname = {"fused": "k_step_fused (whole step, one CTA per PE)",
-             "grid": "k_step_grid update phases (cell totals, cell starts, scatter, pass 1, normalisers, pass 2)"
+             "grid": "k_step_grid update phases (cell starts, scatter, pass 1, normalisers, pass 2 with the ranks)"
              }.get(path, UPDATE_KERNELS)
     roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": peak["Texp_per_s"], "unit": "Texp/s",

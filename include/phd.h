@@ -434,10 +434,12 @@ phd_status phd_reset_stats(phd_handle *h);
 
 /* Time spent in each phase of the grid path's step kernel since phd_init /
  * phd_reset_stats (device clock, read by one thread per CTA at the phases'
- * barriers), in milliseconds, for the 12 phases prediction + spatial keys,
- * cell totals, cell starts, scatter, pass 1 (Eq. 7), normalisers (Eq. 12),
- * pass 2 (Eq. 8), mass and plan, selection ranks + CDF chunk sums, label
- * sums (Eq. 18) + CDF offsets, estimates, offspring ends + gather:
+ * barriers), in milliseconds, in 12 slots per figure of which 10 are used,
+ * for the phases: prediction + spatial keys + cell totals, cell starts,
+ * scatter, pass 1 (Eq. 7), normalisers (Eq. 12), pass 2 (Eq. 8) + selection
+ * ranks, mass and plan (batches), plan + CDF chunk sums + label sums
+ * (Eq. 18), estimates + CDF offsets, offspring ends + gather (slots 10, 11:
+ * zero):
  *   h_ms[0..11]   summed over launches, from the previous barrier's release
  *                 to the phase's own (the phase's wall time);
  *   h_ms[12..23]  the longest time one CTA worked in the phase (from leaving

@@ -23,16 +23,17 @@
 //    cleared or read in full.
 // Phases (barrier between consecutive ones):
 //   A  predict (Eq. 5-6), measurement-space geometry, cell key, chunk
-//      histograms; measurement staging
-//   B  (folded into A: cell totals per (slice, cell) by integer atomics)
+//      histograms and the cell totals per (slice, cell) by integer atomics;
+//      measurement staging
 //   C  cell starts per (slice, cell)
 //   D  stable scatter to the cell order       E  pass 1 (Eq. 7) per tile
 //   F  C_p, ginv_p and the dW keys (Eq. 12, 16) per measurement
-//   G  pass 2 (Eq. 8) per tile: updated weights, tile sums and maxima
-//   H  N^j, the resampling plan, LT_j per slice
-//   I  selection ranks (Step 3) per measurement; CDF chunk totals per chunk
-//   J  pass 3 (Eq. 18 sums) per tile; CDF chunk offsets per slice
-//   K  estimates per selected label
+//   G  pass 2 (Eq. 8) per tile: updated weights, tile sums and maxima;
+//      selection ranks (Step 3) per measurement beside it
+//   H  (batches) N^j, the resampling plan, LT_j per slice
+//   J  (one filter: N^j, the plan and LT_j in every CTA) CDF chunk totals per
+//      chunk; pass 3 (Eq. 18 sums) per tile
+//   K  estimates per selected label; CDF chunk offsets per slice
 //   L  offspring ends per chunk and the children gathered (Sec. 2.2 step 3),
 //      counts and step counter advanced
 // The barrier is one release atomic per CTA on a 64-bit count that only grows
@@ -44,7 +45,8 @@ namespace phd {
 constexpr int kPT = 256;      // threads per CTA
 constexpr int kPMB = 4;       // pass 1: measurements per warp group
 constexpr int kGT = 512;      // particles of a pair-pass tile (two per thread)
-constexpr int kPhases = 12;
+// phase clock slots (phd_get_phase_times order)
+enum : int { kPhA = 0, kPhC, kPhD, kPhE, kPhF, kPhG, kPhH, kPhJ, kPhK, kPhL };
 
 template <class R> struct PersistArgs {
   const R* Z;                 // one filter: the scan (staged into the workspace in phase A); NULL for a batch
@@ -115,12 +117,12 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
   __shared__ int wcnt[kPT / 32];
   __shared__ R bsh[4 * (kPT / 32)];
-  __shared__ double dred[kPT / 32], dredm[kPT / 32];
+  __shared__ double dred[kPT / 32];
   __shared__ unsigned long long dredb[kPT / 32];
   __shared__ int nlive_s;
   const int K = m.K, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = gridDim.x, bid = blockIdx.x;
-  const long gw = ((long)bid * kPT + tid) >> 5, nwarps = ((long)nb * kPT) >> 5;
+  const long nwarps = ((long)nb * kPT) >> 5;
   // warp-per-unit phases spread consecutive units over CTAs first (unit u on
   // CTA u mod nb), so a few hundred units use every SM's FP64 pipe
   const long sw = (long)wid * nb + bid;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       __syncthreads();
     }
   }
-  if (!barrier(0)) return;
+  if (!barrier(kPhA)) return;
 
   // ---- C: per (slice, cell): the cell's start (cells before it), then each
   // chunk's start within the cell (chunks before it), in place: rounds of
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
-  if (!barrier(2)) return;
+  if (!barrier(kPhC)) return;
 
   // ---- D: stable scatter: each particle's rank among its chunk's particles
   // with its key gives its sorted position; the geometry record moves there
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       __syncthreads();
     }
   }
-  if (!barrier(3)) return;
+  if (!barrier(kPhD)) return;
 
   const PairQ<R, RB> Q(m);
   const Lik<R> LB = make_lik<R>(m);
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(4)) return;
+  if (!barrier(kPhE)) return;
 
   // ---- F: per (slice, measurement): C = p_D cnorm (sum of the live tile
   // partials in tile order), the normaliser, ginv and the dW order key
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(5)) return;
+  if (!barrier(kPhF)) return;
 
   // ---- G: pass 2 (Eq. 8) per tile: the live measurements from the gate
   // bits, updated weights to their slots, tile sum and largest weight
@@ -648,7 +650,35 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(6)) return;
+  // selection ranks (Step 3) beside pass 2: a warp per measurement, on the
+  // CTAs from the end of the grid (those past the last pass-2 tile have no
+  // other work here); the rank of its dW among the slice's (larger first,
+  // ties to the lower label) goes to selrank, the measurement to sel[rank]
+  // (the ranks are a permutation); the selection itself, rank < LT, is
+  // applied where LT is known (J, K)
+  {
+    const long units = a.direct ? (long)a.M : (long)K * m.m_max;
+    for (long u = (long)(nb - 1 - bid) * (kPT / 32) + wid; u < units; u += nwarps) {
+      const int j = a.direct ? 0 : (int)(u / m.m_max);
+      const int p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+      const int M = slice_M(d, j);
+      if (p >= M) continue;   // uniform over the warp
+      const unsigned long long* key = d.dwkey + (long)j * m.m_max;
+      const unsigned long long v = __ldcg(key + p);
+      int c = 0;
+#pragma unroll 8
+      for (int q = lane; q < M; q += 32) {
+        const unsigned long long w2 = __ldcg(key + q);
+        c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
+      }
+      const int rank = warp_sum(c);
+      if (lane == 0) {
+        d.selrank[j * m.m_max + p] = rank;
+        d.sel[j * m.m_max + rank] = p;
+      }
+    }
+  }
+  if (!barrier(kPhG)) return;
 
   // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
   // LT_j = min(round(N^j), labels with dW > 0).  One filter: every CTA forms
@@ -724,15 +754,17 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   };
   if (!a.direct) {
     for (int j = bid; j < K; j += nb) slice_plan(j, true);
-    if (!barrier(7)) return;
+    if (!barrier(kPhH)) return;
   }
 
-  // ---- I: selection ranks (Step 3: the LT largest dW, ties to the lower
-  // label) per measurement; CDF chunk totals per slot chunk
+  // ---- J: one filter: N^j, the resampling plan and LT_j formed by every
+  // CTA itself (the same loads in the same order, so the same values in
+  // every CTA); the CDF chunk totals per slot chunk; pass 3 per tile (Eq. 18
+  // label sums of the selected labels that can reach the tile, offsets from
+  // the label's point)
   {
     const R* wu = static_cast<const R*>(d.wu);
     // the weights of the CTA's first two chunks are fetched before the plan
-    // and the ranks
     R wpre[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -745,42 +777,6 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
     if (a.direct) slice_plan(0, bid == 0);
-    const long units = a.direct ? (long)a.M : (long)K * m.m_max;
-    const Grp g = groups(units);
-    int par = 0;
-    for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
-      const long u = r0 + g.gid;
-      int j = 0, p = 0, M = 0;
-      bool act = u < units;
-      if (act) {
-        j = a.direct ? 0 : (int)(u / m.m_max);
-        p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
-        M = slice_M(d, j);
-        act = p < M;
-      }
-      if (g.G == 1 && !act) continue;
-      const unsigned long long* key = d.dwkey + (long)j * m.m_max;
-      const unsigned long long v = act ? __ldcg(key + p) : 0ull;
-      int c = 0;
-#pragma unroll 4
-      for (int q = g.gl; q < M; q += 32 * g.G) {
-        const unsigned long long w2 = __ldcg(key + q);
-        c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
-      }
-      int rank = warp_sum(c);
-      if (g.G > 1) {
-        if (lane == 0) gcnt[par][wid][0] = rank;
-        __syncthreads();
-        rank = 0;
-        for (int k = 0; k < g.G; ++k) rank += gcnt[par][g.slot * g.G + k][0];
-        par ^= 1;
-      }
-      if (act && g.gl == 0) {
-        const bool take = v > 0ull && rank < (a.direct ? nsel_s : __ldcg(d.nsel + j));
-        d.selrank[j * m.m_max + p] = take ? rank : -1;
-        if (take) d.sel[j * m.m_max + rank] = p;
-      }
-    }
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
     int k = 0;
     for (int it = bid; it < nitems; it += nb, ++k) {
@@ -800,43 +796,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
       __syncthreads();
     }
-  }
-  if (!barrier(8)) return;
-
-  // ---- J: pass 3 per tile (Eq. 18 label sums of the selected labels that
-  // can reach the tile, offsets from the label's point); CDF chunk offsets
-  // per slice (the last CTAs)
-  {
-    for (int j = nb - 1 - bid; j >= 0 && j < K; j += nb) {
-      unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
-      unsigned long long carry = 0ull;
-      constexpr int kCh = 4;   // consecutive chunks per thread and round
-      const int cend_j = ipref[j + 1];
-      for (int c0 = ipref[j]; c0 < cend_j; c0 += kCh * kPT) {
-        const int cb = c0 + kCh * tid;
-        unsigned long long v[kCh], sum = 0ull;
-#pragma unroll
-        for (int k = 0; k < kCh; ++k) {
-          v[k] = cb + k < cend_j ? __ldcg(d.pcsum + cb + k) : 0ull;
-          sum += v[k];
-        }
-        unsigned long long tot = 0;
-        unsigned long long run = carry + block_scan_u64<R>(sum, wt, &tot) - sum;
-#pragma unroll
-        for (int k = 0; k < kCh; ++k) {
-          if (cb + k < cend_j) d.pcoff[cb + k] = run;
-          run += v[k];
-        }
-        carry += tot;
-      }
-      if (tid == 0) {
-        d.rs_Qn[j] = carry;
-        const Recip r = make_recip(carry);
-        d.rs_rcp[2 * j] = r.d;
-        d.rs_rcp[2 * j + 1] = r.v;
-      }
-      __syncthreads();
-    }
+    __syncthreads();
     P4<R>* sp = reinterpret_cast<P4<R>*>(smem);               // [kGT]
     St4<R>* sx = reinterpret_cast<St4<R>*>(sp + kGT);        // [kGT]
     int2* lr = reinterpret_cast<int2*>(sx + kGT);             // [m_max] live selected (rank, measurement)
@@ -878,7 +838,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       for (int e = tid; e < nl; e += kPT) {
         const int p = lidx[e];
         const int r = __ldcg(d.selrank + j * m.m_max + p);
-        if (r >= 0) lr[atomicAdd(&nlive_s, 1)] = make_int2(r, p);
+        if (r >= 0 && r < ns) lr[atomicAdd(&nlive_s, 1)] = make_int2(r, p);
       }
       __syncthreads();
       const int nr = nlive_s;
@@ -938,12 +898,14 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(9)) return;
+  if (!barrier(kPhJ)) return;
 
   // ---- K: estimates (Eq. 18) per selected label: the live tile partials in
   // tile order, in the kernel's precision (the tile partials are sums of
   // offsets from the label's point, so the ratio keeps the estimate within
-  // 1e-4 m in FP32); one filter: the output in ascending label order
+  // 1e-4 m in FP32); one filter: the output in ascending label order.  CDF
+  // chunk offsets per slice (the last CTAs); selrank of the labels not
+  // selected set to -1
   {
     St4<R>* est = static_cast<St4<R>*>(d.est_local);
     // one filter: units are the selected labels
@@ -1048,14 +1010,54 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         }
       }
     }
+    for (int j = nb - 1 - bid; j >= 0 && j < K; j += nb) {
+      unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
+      unsigned long long carry = 0ull;
+      constexpr int kCh = 4;   // consecutive chunks per thread and round
+      const int cend_j = ipref[j + 1];
+      for (int c0 = ipref[j]; c0 < cend_j; c0 += kCh * kPT) {
+        const int cb = c0 + kCh * tid;
+        unsigned long long v[kCh], sum = 0ull;
+#pragma unroll
+        for (int k = 0; k < kCh; ++k) {
+          v[k] = cb + k < cend_j ? __ldcg(d.pcsum + cb + k) : 0ull;
+          sum += v[k];
+        }
+        unsigned long long tot = 0;
+        unsigned long long run = carry + block_scan_u64<R>(sum, wt, &tot) - sum;
+#pragma unroll
+        for (int k = 0; k < kCh; ++k) {
+          if (cb + k < cend_j) d.pcoff[cb + k] = run;
+          run += v[k];
+        }
+        carry += tot;
+      }
+      if (tid == 0) {
+        d.rs_Qn[j] = carry;
+        const Recip r = make_recip(carry);
+        d.rs_rcp[2 * j] = r.d;
+        d.rs_rcp[2 * j + 1] = r.v;
+      }
+      __syncthreads();
+    }
+    {
+      const long units = a.direct ? (long)a.M : (long)K * m.m_max;
+      for (long x = (long)bid * kPT + tid; x < units; x += (long)nb * kPT) {
+        const int j = a.direct ? 0 : (int)(x / m.m_max);
+        const int p = a.direct ? (int)x : (int)(x - (long)j * m.m_max);
+        if (p >= slice_M(d, j)) continue;
+        const int ns = a.direct ? nsel_s : __ldcg(d.nsel + j);
+        if (__ldcg(d.selrank + j * m.m_max + p) >= ns) d.selrank[j * m.m_max + p] = -1;
+      }
+    }
   }
-  if (!barrier(10)) return;
+  if (!barrier(kPhK)) return;
 
   // ---- L: offspring ends per slot chunk (exact integer CDF: the chunk's
   // offset plus an inclusive scan of its q_i; c = children of slots up to i)
-  // and the children gathered from their parents (a warp per 32 consecutive
-  // parents, children written as one contiguous range), weight N^j / L_j;
-  // counts and the step counter for the next step
+  // and the children gathered from their parents (the chunk's children as
+  // one contiguous range, shared by its threads), weight N^j / L_j; counts
+  // and the step counter for the next step
   {
     const St4<R>* xp = static_cast<const St4<R>*>(d.x_alt);
     St4<R>* x = static_cast<St4<R>*>(d.x);
@@ -1075,7 +1077,6 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const int c0i = (it - ipref[j]) * 256;
       const int i = c0i + tid;
       const bool live = i < n;
-      const St4<R> sv = live ? xp[base + i] : St4<R>{0, 0, 0, 0};
       const unsigned long long q = live ? scaled_floor(wu[base + i], d.rs_s[j]) : 0ull;
       const unsigned long long off = __ldcg(d.pcoff + it);
       const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
@@ -1086,39 +1087,32 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       cend[tid] = ce;
       if (tid == 0) cprev_s = offspring_end(off, Qn, (unsigned long long)L, U, rq);   // slots before the chunk
       __syncthreads();
-      const int wb = c0i + (tid & ~31);
-      if (wb < n) {   // uniform over the warp
-        const int c0 = (tid & ~31) ? cend[(tid & ~31) - 1] : cprev_s;
-        const int c1 = __shfl_sync(0xffffffffu, ce, 31);
-        const R wn = (R)d.rs_wn[j];
-        for (int t0 = c0; t0 < c1; t0 += 32) {
-          const int t = t0 + lane;
-          int lo = 0;
+      // the chunk's children [cprev_s, cend[255]) are shared by all its
+      // threads in turn (a parent with many children does not hold back one
+      // warp); child t's parent is the first slot i with cend[i] > t
+      const int cA = cprev_s, cB = cend[kPT - 1];
+      const R wn = (R)d.rs_wn[j];
+      for (int t = cA + tid; t < cB; t += kPT) {
+        int lo = 0;
 #pragma unroll
-          for (int st = 16; st > 0; st >>= 1) {
-            const int e = __shfl_sync(0xffffffffu, ce, lo + st - 1);
-            if (e <= t) lo += st;
-          }
-          const R sx = __shfl_sync(0xffffffffu, sv.x, lo), svx = __shfl_sync(0xffffffffu, sv.vx, lo);
-          const R sy = __shfl_sync(0xffffffffu, sv.y, lo), svy = __shfl_sync(0xffffffffu, sv.vy, lo);
-          if (t < c1) {
-            x[base + t] = St4<R>{sx, svx, sy, svy};
-            w[base + t] = wn;
-            d.parent[base + t] = wb + lo;
-          }
-        }
+        for (int st = kPT / 2; st > 0; st >>= 1)
+          if (cend[lo + st - 1] <= t) lo += st;
+        const int par = c0i + lo;
+        x[base + t] = xp[base + par];
+        w[base + t] = wn;
+        d.parent[base + t] = par;
       }
       __syncthreads();   // cend and cprev_s are rewritten by the next chunk
     }
-    // every reader of this step's counter finished before barrier 10
+    // every reader of this step's counter finished before the last barrier
     if (tid == 0) {
       const unsigned long long t = gtimer();
       if (bid == 0) {
         *d.step += 1ull;
-        atomicAdd(d.ptimes + 11, t - t_prev);
+        atomicAdd(d.ptimes + kPhL, t - t_prev);
       }
-      atomicMax(d.ptimes + 16 + 11, t - t_go);
-      atomicAdd(d.ptimes + 32 + 11, t - t_go);
+      atomicMax(d.ptimes + 16 + kPhL, t - t_go);
+      atomicAdd(d.ptimes + 32 + kPhL, t - t_go);
     }
   }
 }
@@ -1177,7 +1171,8 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
                                      persist_smem<R>(m.m_max), s);
 }
 
-int persist_barriers(bool direct) { return direct ? kPhases - 3 : kPhases - 2; }
+// barriers after A, C, D, E, F, G, (H: batches), J, K
+int persist_barriers(bool direct) { return direct ? 8 : 9; }
 
 template size_t persist_smem<float>(int);
 template size_t persist_smem<double>(int);

@@ -588,8 +588,8 @@ class ParticlePHD:
     def reset_stats(self):
         self._check(self.L.phd_reset_stats(self.h), "phd_reset_stats")
 
-    PHASES = ("predict_keys", "cell_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2",
-              "mass_plan", "ranks_cdf", "label_sums_offsets", "estimates", "offspring_gather")
+    PHASES = ("predict_keys_totals", "cell_starts", "scatter", "pass1", "normalisers", "pass2_ranks",
+              "mass_plan", "plan_cdf_pass3", "estimates_offsets", "offspring_gather")
 
     def phase_times(self, detail: bool = False):
         """Grid path: summed wall time per phase of the step kernel, ms
