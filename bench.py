@@ -456,6 +456,8 @@ def run_gpu(args, w, rank, world, local_rank, sub=False):
     Zdev = {(r, k): torch.as_tensor(scen[r].meas[k], dtype=dtype, device=dev) for r, k in seq}
 
     f = ParticlePHD(w, seed=base_seed, device=f"cuda:{local_rank}")
+    if args.path:
+        f.set_path(args.path)
     empty_x = [np.zeros((0, 4))] * w.num_pe
     empty_w = [np.zeros(0)] * w.num_pe
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -713,6 +715,9 @@ def run_gpu_batch(args, rank, world, local_rank):
     total = args.warmup + args.steps
     scen = [scenario.simulate(w, 1000 + r + 7919 * rank, steps=steps_per_run) for r, w in enumerate(ws)]
     b = ParticlePHDBatch(ws, seed=1000 + rank, device=f"cuda:{local_rank}")
+    if args.path:
+        b.set_path(args.path)
+    batch_path = b.get_path()
     packed = [b.pack([scen[r].meas[k] for r in range(R)]) for k in range(steps_per_run)]
     empty_x = [np.zeros((0, 4))] * R
     empty_w = [np.zeros(0)] * R
@@ -847,7 +852,7 @@ def run_gpu_batch(args, rank, world, local_rank):
                      "kernel_ms_per_step": upd_ms / max(st["timed_updates"], 1),
                      "pairs_per_update": st["pairs"] / max(st["updates"], 1),
                      "pairs_evaluated_frac": st["pairs_evaluated"] / st["pairs"] if st["pairs"] else None},
-        "gpu_launches": int(st["launches"]), "clocks": clocks,
+        "gpu_launches": int(st["launches"]), "clocks": clocks, "path": batch_path,
         "tuning": {**{k: tuning[k] for k in ("c_tile", "c_mb", "r_pb", "r_g", "grid1", "grid2", "gate", "order")},
                    "pass1_us": round(float(tuning["pass1_us"]), 2), "pass2_us": round(float(tuning["pass2_us"]), 2),
                    "autotuned": not (args.no_autotune or args.tuning), "setup_s": round(t_tune, 3)},
@@ -1066,12 +1071,21 @@ def run_gpu_compare(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     wd = scenario.workload("dist16_10t")
+    K16 = wd.num_pe
     runs = max(1, -(-args.steps // wd.steps))
     seeds = [args.seed + r + 7919 * rank for r in range(runs)]
     # exchange variants (Step 6): all-to-all, and the ring only when a PE has
     # degenerated (its mass below half the PE mean)
     extra = [("DCPFPHD_all_to_all", wd.with_(exchange_mode="all")),
-             ("DCPFPHD_adaptive_0.5", wd.with_(exchange_threshold=0.5))]
+             ("DCPFPHD_adaptive_0.5", wd.with_(exchange_threshold=0.5)),
+             # where the gap to the global filter comes from (Steps 2 and 6):
+             # the normaliser (the PE mean of C^j instead of the local C^j),
+             # the exchange, and the particles and births a PE holds
+             ("DCPFPHD_ck_global", wd.with_(ck_mode="global")),
+             ("DCPFPHD_no_exchange", wd.with_(exchange_frac=0.0)),
+             ("DCPFPHD_4x_particles", wd.with_(particles_per_target=4 * wd.particles_per_target,
+                                               birth_count=4 * wd.birth_count, pe_cap=4 * wd.pe_cap)),
+             ("DCPFPHD_J_births_per_pe", wd.with_(birth_count=K16 * wd.birth_count))]
     res = _three_way(args, wd, seeds, dev, rank, local_rank, 2.0, extra)
     job_pairs, job_ms = job_totals(res["DCPFPHD"]["pairs"], res["DCPFPHD"]["ms"], world, dev)
     if rank != 0:
@@ -1181,7 +1195,7 @@ def compact_one(line):
 
 def compact_batch(line):
     out = _compact(line, ("value", "unit", "steps", "ms_per_step", "run_steps_per_s", "per_run_latency_ms",
-                          "vs_one_filter_at_a_time", "gpu_launches"))
+                          "vs_one_filter_at_a_time", "gpu_launches", "path"))
     out["workload"] = line["config"]["workload"]
     out["roofline"] = _compact(line["roofline"], ("frac", "achieved", "peak", "unit", "kernel_ms_per_step",
                                                   "pairs_evaluated_frac"))
@@ -1216,6 +1230,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--runs", type=int, default=256, help="filters in the batched workload (batch256)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of the pair passes")
+    ap.add_argument("--path", default=None, choices=["staged", "fused", "grid"],
+                    help="run the one-filter or batched workload on this path instead of the library's default")
     ap.add_argument("--steady-from", type=int, default=None,
                     help="time scans from this index of every run (earlier ones replayed untimed); "
                          "default 50 for dense_rb_100t, else 0")

@@ -44,7 +44,7 @@ namespace phd {
 
 constexpr int kPT = 256;      // threads per CTA
 constexpr int kPMB = 4;       // pass 1: measurements per warp group
-constexpr int kGT = 512;      // particles of a pair-pass tile (two per thread)
+constexpr int kGT = 512;      // particles of a chunk and of a pair-pass tile (two per thread)
 // phase clock slots (phd_get_phase_times order)
 enum : int { kPhA = 0, kPhC, kPhD, kPhE, kPhF, kPhG, kPhH, kPhJ, kPhK, kPhL };
 
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   extern __shared__ __align__(32) unsigned char smem[];
   unsigned smem_bytes;   // dynamic shared memory of the launch
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(smem_bytes));
-  __shared__ int ipref[kMaxPE + 1];   // 256-particle chunks per slice, prefix
+  __shared__ int ipref[kMaxPE + 1];   // chunks (kGT particles) per slice, prefix
   __shared__ int tpref[kMaxPE + 1];   // pair-pass tiles (kGT particles) per slice, prefix
   __shared__ int hpref[kMaxPE + 1];   // chunk-histogram rows per slice: 256 x (items rounded up to 4), prefix
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // slice sizes after prediction: survivors + births
   for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
   __syncthreads();
-  slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + 255) / 256; });
+  slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + kGT - 1) / kGT; });
   slice_prefix(K, tpref, [&](int j) { return (npred_s[j] + kGT - 1) / kGT; });
-  slice_prefix(K, hpref, [&](int j) { return 256 * ((((npred_s[j] + 255) / 256) + 3) & ~3); });
+  slice_prefix(K, hpref, [&](int j) { return 256 * ((((npred_s[j] + kGT - 1) / kGT) + 3) & ~3); });
   const int nitems = ipref[K];
   const int ntiles = tpref[K];
   const long T = d.max_items;   // row stride of the gate bits [word][tile]
@@ -210,37 +210,44 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     }
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
-      const int i = (it - ipref[j]) * 256 + tid;
       hist[tid] = 0;
       __syncthreads();
-      if (i < npred_s[j]) {
-        const long g = (long)j * m.pe_cap + i;
-        const bool surv = i < d.n_cur[j];
-        St4<R> o;
-        R wo;
-        if (!surv && m.learned) {
-          // a birth of the measurement-driven proposal, drawn into its slot
-          // before the launch
-          o = xp[g];
-          wo = wp[g];
-        } else {
-          R n1, n2, u1, u2;
-          draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
-          predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j), n1,
-                          n2, u1, u2, o, wo);
-          xp[g] = o;
-          wp[g] = wo;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {   // the thread's two slots of the chunk
+        const int i = (it - ipref[j]) * kGT + hh * kPT + tid;
+        int key = kCells;   // none
+        if (i < npred_s[j]) {
+          const long g = (long)j * m.pe_cap + i;
+          const bool surv = i < d.n_cur[j];
+          St4<R> o;
+          R wo;
+          if (!surv && m.learned) {
+            // a birth of the measurement-driven proposal, drawn into its slot
+            // before the launch
+            o = xp[g];
+            wo = wp[g];
+          } else {
+            R n1, n2, u1, u2;
+            draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
+            predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j),
+                            n1, n2, u1, u2, o, wo);
+            xp[g] = o;
+            wp[g] = wo;
+          }
+          const H3<R> h = meas_h<R>(m, o, tab);
+          geo_s[g] = P4<R>{h.h0, h.h1, h.h1lo, wo};
+          key = cell_key(m, (float)h.h0, (float)h.h1);
+          d.ckey[g] = (unsigned char)key;
         }
-        const H3<R> h = meas_h<R>(m, o, tab);
-        geo_s[g] = P4<R>{h.h0, h.h1, h.h1lo, wo};
-        const int k = cell_key(m, (float)h.h0, (float)h.h1);
-        d.ckey[g] = (unsigned char)k;
-        atomicAdd(&hist[k], 1);
+        // one shared-memory add per distinct cell of the warp (a chunk's slots
+        // hold siblings of a few parents, mostly in one cell)
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key < kCells && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&hist[key], __popc(peers));
       }
       __syncthreads();
-      // the chunk's count of every cell, and (phase B folded in) the cell
-      // totals of the slice by integer atomics (exact in any order); the
-      // totals were cleared by the previous launch after their last use
+      // the chunk's count of every cell, and the cell totals of the slice by
+      // integer atomics (exact in any order); the totals were cleared by the
+      // previous launch after their last use
       const int hv = hist[tid];
       d.pchist[hpref[j] + (long)tid * hstride(j) + (it - ipref[j])] = hv;
       if (hv) atomicAdd(d.bintot + (long)j * 256 + tid, hv);
@@ -291,40 +298,54 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ---- D: stable scatter: each particle's rank among its chunk's particles
   // with its key gives its sorted position; the geometry record moves there
   {
-    int* wc = reinterpret_cast<int*>(smem);   // [8][256]
+    int* wc = reinterpret_cast<int*>(smem);   // [16][256]: per (warp of 32 consecutive slots, cell)
     const P4<R>* __restrict__ geo_s = static_cast<const P4<R>*>(d.geo_s);
     P4<R>* __restrict__ geo = static_cast<P4<R>*>(d.geo);
     // the cell totals were last read in C: cleared for the next launch
     for (long u = (long)bid * kPT + tid; u < (long)K * 256; u += (long)nb * kPT) d.bintot[u] = 0;
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
-      const int i = (it - ipref[j]) * 256 + tid;
-      const bool live = i < npred_s[j];
-      const long g = (long)j * m.pe_cap + i;
-      const int key = live ? (int)d.ckey[g] : kCells;
-      // the record and the (cell, chunk) start are fetched before the ranking
-      const P4<R> rec = live ? geo_s[g] : P4<R>{0, 0, 0, 0};
-      const int cstart = live ? __ldcg(d.pchist + hpref[j] + (long)key * hstride(j) + (it - ipref[j])) : 0;
-      for (int t = tid; t < 8 * kCells; t += kPT) wc[t] = 0;
+      // the thread's two slots: i[hh] = chunk start + hh 256 + tid, so the
+      // 16 groups of 32 consecutive slots are (hh, warp) in slot order
+      int key[2], cstart[2], slot[2];
+      bool live[2];
+      P4<R> rec[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        slot[hh] = (it - ipref[j]) * kGT + hh * kPT + tid;
+        live[hh] = slot[hh] < npred_s[j];
+        const long g = (long)j * m.pe_cap + slot[hh];
+        key[hh] = live[hh] ? (int)d.ckey[g] : kCells;
+        // the record and the (cell, chunk) start are fetched before the ranking
+        rec[hh] = live[hh] ? geo_s[g] : P4<R>{0, 0, 0, 0};
+        cstart[hh] = live[hh] ? __ldcg(d.pchist + hpref[j] + (long)key[hh] * hstride(j) + (it - ipref[j])) : 0;
+      }
+      for (int t = tid; t < 16 * kCells; t += kPT) wc[t] = 0;
       __syncthreads();
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int rank_w = __popc(peers & ((1u << lane) - 1u));
-      if (live && rank_w == 0) wc[wid * kCells + key] = __popc(peers);
+      int rank_w[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key[hh]);
+        rank_w[hh] = __popc(peers & ((1u << lane) - 1u));
+        if (live[hh] && rank_w[hh] == 0) wc[(hh * (kPT / 32) + wid) * kCells + key[hh]] = __popc(peers);
+      }
       __syncthreads();
       {
         int run = 0;
-        for (int w8 = 0; w8 < 8; ++w8) {
-          const int v = wc[w8 * kCells + tid];
-          wc[w8 * kCells + tid] = run;
+        for (int w16 = 0; w16 < 16; ++w16) {
+          const int v = wc[w16 * kCells + tid];
+          wc[w16 * kCells + tid] = run;
           run += v;
         }
       }
       __syncthreads();
-      if (live) {
-        const int dst = cstart + wc[wid * kCells + key] + rank_w;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        if (!live[hh]) continue;
+        const int dst = cstart[hh] + wc[(hh * (kPT / 32) + wid) * kCells + key[hh]] + rank_w[hh];
         if (dst >= 0 && dst < npred_s[j]) {
-          d.perm[(long)j * m.pe_cap + dst] = i;
-          geo[(long)j * m.pe_cap + dst] = rec;
+          d.perm[(long)j * m.pe_cap + dst] = slot[hh];
+          geo[(long)j * m.pe_cap + dst] = rec[hh];
         } else {
           atomicOr(d.err, kErrCapacity);   // inconsistent cell counts: never written out of the slice
         }
@@ -429,6 +450,53 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       __syncthreads();
     }
     return nl;
+  };
+
+  // the box of a warp's 64 particles (its lanes' two slots; slots past the
+  // tile's end take no part); false if the warp holds none
+  auto warp_box = [&](const P4<R>& q0, const P4<R>& q1, bool has0, bool has1, Box<R>& b) -> bool {
+    const R inf = (R)INFINITY;
+    R lo0 = inf, hi0 = -inf, lo1 = inf, hi1 = -inf;
+    if (has0) {
+      lo0 = q0.h0;
+      hi0 = q0.h0;
+      lo1 = q0.h1;
+      hi1 = q0.h1;
+    }
+    if (has1) {
+      lo0 = fmin(lo0, q1.h0);
+      hi0 = fmax(hi0, q1.h0);
+      lo1 = fmin(lo1, q1.h1);
+      hi1 = fmax(hi1, q1.h1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo0 = fmin(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+      hi0 = fmax(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+      lo1 = fmin(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+      hi1 = fmax(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+    }
+    b = Box<R>{lo0, hi0, lo1, hi1};
+    return __any_sync(0xffffffffu, has0 || has1);
+  };
+  // the entries e of the tile's live list (measurement points zt2(e)) that
+  // can reach the warp's box, in list order, into wl; returns their count.
+  // A skipped pair's term is an exact zero, so the sums do not change.
+  auto warp_list = [&](const Box<R>& b, bool any, int nl, unsigned short* wl, auto zt2) -> int {
+    int nw = 0;
+    if (!any) return 0;
+    for (int e0 = 0; e0 < nl; e0 += 32) {
+      const int e = e0 + lane;
+      bool keep = false;
+      if (e < nl) {
+        const V2<R> z = zt2(e);
+        keep = !m.tune.gate || box_qmin<R, RB>(b, LB.b0, LB.b1, z.a, z.b) < gate_limit<R>(m);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) wl[nw + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)e;
+      nw += __popc(bal);
+    }
+    __syncwarp();
+    return nw;
   };
 
   // ---- E: pass 1 (Eq. 7): tile partials of the live measurements, in FP32
@@ -571,8 +639,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ---- G: pass 2 (Eq. 8) per tile: the live measurements from the gate
   // bits, updated weights to their slots, tile sum and largest weight
   {
-    int* lidx = reinterpret_cast<int*>(smem);                          // [m_max]
-    Z4<R>* zs = reinterpret_cast<Z4<R>*>(lidx + ((m.m_max + 7) & ~7));   // [m_max]
+    const int mm = (m.m_max + 7) & ~7;
+    int* lidx = reinterpret_cast<int*>(smem);                                // [mm]
+    Z4<R>* zs = reinterpret_cast<Z4<R>*>(lidx + mm);                         // [mm]
+    unsigned short* wl = reinterpret_cast<unsigned short*>(zs + mm);         // [8][mm] warp lists
     const R* __restrict__ ginv = static_cast<const R*>(d.ginv);
     R* __restrict__ wu = static_cast<R*>(d.wu);
     const R miss = cc.miss;
@@ -602,11 +672,17 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         const V2<R> z = Z[p];
         zs[e] = Z4<R>{z.a, z.b, ginv[j * m.m_max + p], (R)0};
       }
+      Box<R> wb;
+      const bool any = warp_box(q0, q1, has0, has1, wb);
       __syncthreads();
+      // the live measurements that can reach the warp's 64 particles, walked
+      // by each thread for its two particles
+      const int nw = warp_list(wb, any, nl, wl + wid * mm, [&](int e) { return V2<R>{zs[e].z0, zs[e].z1}; });
       R wv0 = 0, wv1 = 0;
-      if (has0) {   // both particles in one walk of the live list
+      if (has0) {
         R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-        for (int e = 0; e < nl; ++e) {
+        for (int k = 0; k < nw; ++k) {
+          const int e = wl[wid * mm + k];
           const Z4<R> za = zs[e];
           const R v = exp2_neg(Q(za.z0, za.z1, q0.h0, q0.h1, q0.h1lo)) * za.g;
           const R u = exp2_neg(Q(za.z0, za.z1, q1.h0, q1.h1, q1.h1lo)) * za.g;
@@ -764,27 +840,33 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // the label's point)
   {
     const R* wu = static_cast<const R*>(d.wu);
-    // the weights of the CTA's first two chunks are fetched before the plan
+    // the weights of the CTA's first chunk (two slots per thread) are
+    // fetched before the plan
     R wpre[2];
+    {
+      const int it = bid;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int it = bid + k * nb;
-      wpre[k] = 0;
-      if (it < nitems) {
-        const int j = item_pe(ipref, K, it);
-        const int i = (it - ipref[j]) * 256 + tid;
-        if (i < npred_s[j]) wpre[k] = wu[(long)j * m.pe_cap + i];
+      for (int hh = 0; hh < 2; ++hh) {
+        wpre[hh] = 0;
+        if (it < nitems) {
+          const int j = item_pe(ipref, K, it);
+          const int i = (it - ipref[j]) * kGT + hh * kPT + tid;
+          if (i < npred_s[j]) wpre[hh] = wu[(long)j * m.pe_cap + i];
+        }
       }
     }
     if (a.direct) slice_plan(0, bid == 0);
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
-    int k = 0;
-    for (int it = bid; it < nitems; it += nb, ++k) {
+    for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
-      const int i = (it - ipref[j]) * 256 + tid;
       const int sj = a.direct ? rss_s : d.rs_s[j];
-      const R wi = k == 0 ? wpre[0] : k == 1 ? wpre[1] : (i < npred_s[j] ? wu[(long)j * m.pe_cap + i] : (R)0);
-      const unsigned long long q = i < npred_s[j] ? scaled_floor(wi, sj) : 0ull;
+      unsigned long long q = 0ull;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int i = (it - ipref[j]) * kGT + hh * kPT + tid;
+        const R wi = it == bid ? wpre[hh] : (i < npred_s[j] ? wu[(long)j * m.pe_cap + i] : (R)0);
+        q += i < npred_s[j] ? scaled_floor(wi, sj) : 0ull;
+      }
       // the chunk total: warp sums, then the 8 warp totals in warp order
       const unsigned long long ws = warp_sum(q);
       if (lane == 0) wt[wid] = ws;
@@ -1064,7 +1146,7 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
     R* w = static_cast<R*>(d.w);
     const R* wu = static_cast<const R*>(d.wu);
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);   // [kPT / 32]
-    int* cend = reinterpret_cast<int*>(wt + kPT / 32);                      // [kPT]
+    int* cend = reinterpret_cast<int*>(wt + kPT / 32);                      // [kGT]
     __shared__ int cprev_s;
     if (bid == 0)
       for (int j = tid; j < K; j += kPT) d.n_cur[j] = d.rs_L[j];
@@ -1074,28 +1156,33 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const int L = d.rs_L[j];
       if (L == 0) continue;   // uniform over the block
       const long base = (long)j * m.pe_cap;
-      const int c0i = (it - ipref[j]) * 256;
-      const int i = c0i + tid;
-      const bool live = i < n;
-      const unsigned long long q = live ? scaled_floor(wu[base + i], d.rs_s[j]) : 0ull;
+      const int c0i = (it - ipref[j]) * kGT;
+      const int i0 = c0i + tid, i1 = c0i + kPT + tid;   // the thread's two slots
+      const unsigned long long q0 = i0 < n ? scaled_floor(wu[base + i0], d.rs_s[j]) : 0ull;
+      const unsigned long long q1 = i1 < n ? scaled_floor(wu[base + i1], d.rs_s[j]) : 0ull;
       const unsigned long long off = __ldcg(d.pcoff + it);
       const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
       const unsigned long long Qn = __ldcg(d.rs_Qn + j);
       const Recip rq{__ldcg(d.rs_rcp + 2 * j), __ldcg(d.rs_rcp + 2 * j + 1), Qn ? __clzll((long long)Qn) : 0};
-      // slots past the slice's end repeat the last slot's end (q = 0)
-      const int ce = offspring_end(off + block_scan_u64<R>(q, wt, nullptr), Qn, (unsigned long long)L, U, rq);
-      cend[tid] = ce;
+      // inclusive scans in slot order: the first half, then the second after
+      // the first's total; slots past the slice's end repeat the last slot's
+      // end (q = 0)
+      unsigned long long t0 = 0;
+      const unsigned long long s0 = block_scan_u64<R>(q0, wt, &t0);
+      const unsigned long long s1 = block_scan_u64<R>(q1, wt, nullptr);
+      cend[tid] = offspring_end(off + s0, Qn, (unsigned long long)L, U, rq);
+      cend[kPT + tid] = offspring_end(off + t0 + s1, Qn, (unsigned long long)L, U, rq);
       if (tid == 0) cprev_s = offspring_end(off, Qn, (unsigned long long)L, U, rq);   // slots before the chunk
       __syncthreads();
-      // the chunk's children [cprev_s, cend[255]) are shared by all its
+      // the chunk's children [cprev_s, cend[kGT - 1]) are shared by all its
       // threads in turn (a parent with many children does not hold back one
       // warp); child t's parent is the first slot i with cend[i] > t
-      const int cA = cprev_s, cB = cend[kPT - 1];
+      const int cA = cprev_s, cB = cend[kGT - 1];
       const R wn = (R)d.rs_wn[j];
       for (int t = cA + tid; t < cB; t += kPT) {
         int lo = 0;
 #pragma unroll
-        for (int st = kPT / 2; st > 0; st >>= 1)
+        for (int st = kGT / 2; st > 0; st >>= 1)
           if (cend[lo + st - 1] <= t) lo += st;
         const int par = c0i + lo;
         x[base + t] = xp[base + par];
@@ -1121,9 +1208,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
 // the phases' layouts).
 template <class R> size_t persist_smem(int m_max) {
   const size_t mm = ((size_t)m_max + 7) & ~(size_t)7;
-  const size_t a = 8 * kCells * sizeof(int);                                         // D
+  const size_t a = 16 * kCells * sizeof(int);                                        // D
   const size_t e = kGT * sizeof(P4<R>) + mm * sizeof(int);                          // E
-  const size_t g = mm * sizeof(int) + mm * sizeof(Z4<R>);                            // G
+  const size_t g = mm * (sizeof(int) + sizeof(Z4<R>)) + (kPT / 32) * mm * sizeof(unsigned short);   // G
   const size_t j = kGT * sizeof(P4<R>) + kGT * sizeof(St4<R>) + mm * sizeof(int2) + mm * sizeof(int);  // J
   size_t s = a;
   if (e > s) s = e;

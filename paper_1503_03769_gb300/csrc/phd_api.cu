@@ -613,8 +613,8 @@ bool use_fused(const phd_handle* h) {
 // the step's time goes to.  Past that (batches of tens to hundreds of runs,
 // 50-200 chunks per CTA) the phases become long serial chains at 3 CTAs per
 // SM, and the staged kernels (more resident threads, autotuned pair-pass
-// shapes) are faster (256 runs, ~1e7 particles: 1.27 ms per batched step
-// staged, 2.02 ms grid).
+// shapes) are faster (256 runs, ~1e7 particles: 1.05 ms per batched step
+// staged, 1.17 ms grid).
 constexpr double kGridAutoItems = 16.0;
 bool grid_auto(const phd_handle* h) {
   const double items = (double)h->m.K * (double)((h->cfg.pe_cap + 255) / 256);

@@ -1,0 +1,47 @@
+"""DCPFPHD against the global filter on the GPU (Algorithm 1 vs Sec. 2.2).
+
+The paper's claim (Sec. 4, Table 1) is that the distributed scheme tracks as
+well as the global filter on its scenario.  The FP64 oracle's recursion is
+held to that claim by tests/test_oracle_recursion.py
+(test_distributed_ospa_close_to_global: mean OSPA, c = 100 m, p = 2, after a
+5-scan burn-in over seeds 0-19, within 5 % at clutter 0 and 20 and 20 % at
+clutter 10).  Here the GPU filters run the same runs with the same injected
+random numbers and are held to the same margins."""
+import numpy as np
+import pytest
+
+import oracle
+import scenario
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_ospa(w_sc, w_f, seeds, burn_in=5):
+    from paper_1503_03769_gb300 import ParticlePHD
+    osp = []
+    for seed in seeds:
+        sc = scenario.simulate(w_sc, seed)
+        f = ParticlePHD(w_f, seed=seed, device="cuda:0")
+        K = w_f.num_pe
+        for k, Z in enumerate(sc.meas):
+            noise = scenario.step_noise(seed, k, K, w_f.pe_cap, np.float32)
+            u = scenario.resample_u32(seed, k, K)
+            xu = scenario.exchange_u32(seed, k, K, w_f.pe_cap) if K > 1 else None
+            s_, _ = f.step_inject(np.asarray(Z, np.float32), noise=noise, u=u, xu=xu)
+            if k < burn_in:
+                continue
+            X = s_.double().cpu().numpy()[:, [0, 2]] if len(s_) else np.zeros((0, 2))
+            Y = sc.truth[k][:, [0, 2]] if len(sc.truth[k]) else np.zeros((0, 2))
+            osp.append(oracle.ospa(X, Y, 100.0, 2.0))
+        f.close()
+    return float(np.mean(osp))
+
+
+@pytest.mark.parametrize("clutter,margin", [(0.0, 0.05), (20.0, 0.05), (10.0, 0.20)])
+def test_gpu_distributed_ospa_close_to_global(clutter, margin):
+    wd = scenario.workload("paper_bot", clutter_rate=clutter, precision="fp32")
+    wg = wd.with_(num_pe=1, exchange_frac=0.0, pe_cap=wd.num_pe * wd.pe_cap)
+    og = _gpu_ospa(wd, wg, range(20))
+    od = _gpu_ospa(wd, wd, range(20))
+    print(f"clutter {clutter}: global {og:.2f}, DCPFPHD {od:.2f}")
+    assert abs(od - og) <= margin * og, (clutter, od, og)
