@@ -470,7 +470,8 @@ phd_status phd_set_wait_limit(phd_handle *h, int64_t iterations);
  * flag that makes PE 0 leave the next fused step of a K > 1 filter at its
  * first grid barrier without arriving, as a PE that died would; the other PEs
  * wait out their limit there and the step reports PHD_ERR_TIMEOUT (which
- * clears the flag).  Synchronises. */
+ * clears the flag).  On the grid path CTA 0 of the step kernel leaves the
+ * same way and the other CTAs time out.  Synchronises. */
 phd_status phd_inject_barrier_fault(phd_handle *h);
 
 /* ---- launch shapes of the update's pair passes, and their autotuner -------- */

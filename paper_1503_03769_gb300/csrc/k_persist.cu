@@ -61,16 +61,22 @@ template <class R> struct PersistArgs {
   int direct;                 // 1: one filter (write the outputs)
 };
 
-// Barrier b (1-based) of the launch: every CTA arrives once; wait until all
-// have (count >= base + b G), polling at most `limit` times.  On expiry or an
-// error recorded by another CTA: false in every thread.
-__device__ __forceinline__ bool pbar_sync(const Dev& d, unsigned long long target, long long limit) {
-  __shared__ int ok_s;
+// Barrier b (1-based) of the launch, in two halves: every CTA arrives once
+// (a release add on the count after a block barrier), may then issue loads
+// that do not depend on the phase just finished, and waits until all have
+// arrived (count >= base + b G), polling at most `limit` times.  On expiry or
+// an error recorded by another CTA the wait returns false in every thread.
+__device__ __forceinline__ void pbar_arrive(const Dev& d) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = 0;
     unsigned long long old;
     asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(d.pbar) : "memory");
+  }
+}
+__device__ __forceinline__ bool pbar_wait(const Dev& d, unsigned long long target, long long limit) {
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 0;
     long long it = 0;
     for (;;) {
       unsigned long long c;
@@ -157,14 +163,25 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ptimes[16 + phase] keeps the longest time any CTA spent working in the
   // phase (leaving one barrier to arriving at the next) and ptimes[32 + phase]
   // sums those times over CTAs
-  auto barrier = [&](int phase) -> bool {
+  // host-injected failure: CTA 0 leaves at its first grid barrier without
+  // arriving, as a lost part of the grid would; the others' bounded waits
+  // report the timeout
+  __shared__ int lost_s;
+  if (tid == 0) lost_s = bid == 0 && reinterpret_cast<volatile unsigned int*>(d.bar)[2] != 0u;
+  __syncthreads();
+  auto arrive = [&](int phase) {
     ++tb;
+    if (lost_s) return;   // uniform over the block
     if (tid == 0) {
       const unsigned long long busy = gtimer() - t_go;
       atomicMax(d.ptimes + 16 + phase, busy);
       atomicAdd(d.ptimes + 32 + phase, busy);
     }
-    const bool ok = pbar_sync(d, a.base + tb * G, lim);
+    pbar_arrive(d);
+  };
+  auto wait = [&](int phase) -> bool {
+    if (lost_s) return false;
+    const bool ok = pbar_wait(d, a.base + tb * G, lim);
     if (ok && tid == 0) {
       const unsigned long long t = gtimer();
       if (bid == 0) atomicAdd(d.ptimes + phase, t - t_prev);
@@ -172,6 +189,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       t_go = t;
     }
     return ok;
+  };
+  auto barrier = [&](int phase) -> bool {
+    arrive(phase);
+    return wait(phase);
   };
   // slice sizes after prediction: survivors + births
   for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
@@ -293,7 +314,24 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
-  if (!barrier(kPhC)) return;
+  arrive(kPhC);
+  // the first chunk's keys and records (phase A's) are fetched while the
+  // other CTAs finish the cell starts
+  int dkey[2] = {kCells, kCells};
+  P4<R> drec[2] = {P4<R>{0, 0, 0, 0}, P4<R>{0, 0, 0, 0}};
+  if (bid < nitems) {
+    const int j = item_pe(ipref, K, bid);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int i = (bid - ipref[j]) * kGT + hh * kPT + tid;
+      if (i < npred_s[j]) {
+        const long g = (long)j * m.pe_cap + i;
+        dkey[hh] = (int)d.ckey[g];
+        drec[hh] = static_cast<const P4<R>*>(d.geo_s)[g];
+      }
+    }
+  }
+  if (!wait(kPhC)) return;
 
   // ---- D: stable scatter: each particle's rank among its chunk's particles
   // with its key gives its sorted position; the geometry record moves there
@@ -315,9 +353,14 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         slot[hh] = (it - ipref[j]) * kGT + hh * kPT + tid;
         live[hh] = slot[hh] < npred_s[j];
         const long g = (long)j * m.pe_cap + slot[hh];
-        key[hh] = live[hh] ? (int)d.ckey[g] : kCells;
-        // the record and the (cell, chunk) start are fetched before the ranking
-        rec[hh] = live[hh] ? geo_s[g] : P4<R>{0, 0, 0, 0};
+        if (it == bid) {
+          key[hh] = dkey[hh];
+          rec[hh] = drec[hh];
+        } else {
+          key[hh] = live[hh] ? (int)d.ckey[g] : kCells;
+          rec[hh] = live[hh] ? geo_s[g] : P4<R>{0, 0, 0, 0};
+        }
+        // the (cell, chunk) start is fetched before the ranking
         cstart[hh] = live[hh] ? __ldcg(d.pchist + hpref[j] + (long)key[hh] * hstride(j) + (it - ipref[j])) : 0;
       }
       for (int t = tid; t < 16 * kCells; t += kPT) wc[t] = 0;
@@ -634,7 +677,26 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(kPhF)) return;
+  arrive(kPhF);
+  // the first tile's records and slots (phase D's) are fetched while the
+  // other CTAs finish the normalisers
+  P4<R> gq0{0, 0, 0, 0}, gq1{0, 0, 0, 0};
+  int gs0 = 0, gs1 = 0;
+  if (bid < ntiles) {
+    const int j = item_pe(tpref, K, bid);
+    const int t = bid - tpref[j];
+    const int cnt = min(kGT, npred_s[j] - t * kGT);
+    const long base = (long)j * m.pe_cap + (long)t * kGT;
+    if (tid < cnt) {
+      gq0 = geo[base + tid];
+      gs0 = d.perm[base + tid];
+    }
+    if (tid + kPT < cnt) {
+      gq1 = geo[base + kPT + tid];
+      gs1 = d.perm[base + kPT + tid];
+    }
+  }
+  if (!wait(kPhF)) return;
 
   // ---- G: pass 2 (Eq. 8) per tile: the live measurements from the gate
   // bits, updated weights to their slots, tile sum and largest weight
@@ -656,13 +718,20 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       P4<R> q0{0, 0, 0, 0}, q1{0, 0, 0, 0};
       int slot0 = 0, slot1 = 0;
       const bool has0 = tid < cnt, has1 = tid + kPT < cnt;
-      if (has0) {
-        q0 = geo[base + tid];
-        slot0 = d.perm[base + tid];
-      }
-      if (has1) {
-        q1 = geo[base + kPT + tid];
-        slot1 = d.perm[base + kPT + tid];
+      if (it == bid) {
+        q0 = gq0;
+        q1 = gq1;
+        slot0 = gs0;
+        slot1 = gs1;
+      } else {
+        if (has0) {
+          q0 = geo[base + tid];
+          slot0 = d.perm[base + tid];
+        }
+        if (has1) {
+          q1 = geo[base + kPT + tid];
+          slot1 = d.perm[base + kPT + tid];
+        }
       }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
@@ -754,12 +823,32 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(kPhG)) return;
+  arrive(kPhG);
+  // pass 3's first tile: records and predicted states (phases D and A) are
+  // fetched while the other CTAs finish pass 2
+  P4<R> jq0{0, 0, 0, 0}, jq1{0, 0, 0, 0};
+  St4<R> jx0{0, 0, 0, 0}, jx1{0, 0, 0, 0};
+  if (bid < ntiles) {
+    const St4<R>* __restrict__ xs = static_cast<const St4<R>*>(d.x_alt);
+    const int j = item_pe(tpref, K, bid);
+    const int t = bid - tpref[j];
+    const int cnt = min(kGT, npred_s[j] - t * kGT);
+    const long base = (long)j * m.pe_cap + (long)t * kGT;
+    if (tid < cnt) {
+      jq0 = geo[base + tid];
+      jx0 = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+    }
+    if (tid + kPT < cnt) {
+      jq1 = geo[base + kPT + tid];
+      jx1 = xs[(long)j * m.pe_cap + d.perm[base + kPT + tid]];
+    }
+  }
+  if (!wait(kPhG)) return;
 
   // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
   // LT_j = min(round(N^j), labels with dW > 0).  One filter: every CTA forms
-  // them itself at the start of I (the same loads in the same order, so the
-  // same values in every CTA) and the barrier between H and I goes.
+  // them itself at the start of J (the same loads in the same order, so the
+  // same values in every CTA) and the barrier between H and J goes.
   __shared__ int nsel_s, rss_s;
   auto slice_plan = [&](int j, bool store) {
     // N^j: the FP64 sum of the tile sums by warp 0 alone (lane l: tiles l,
@@ -895,13 +984,20 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       // the tile's records are fetched before its gate bits are read
       P4<R> qg0{0, 0, 0, 0}, qg1{0, 0, 0, 0};
       St4<R> xg0{0, 0, 0, 0}, xg1{0, 0, 0, 0};
-      if (tid < cnt) {
-        qg0 = geo[base + tid];
-        xg0 = xs[(long)j * m.pe_cap + d.perm[base + tid]];
-      }
-      if (tid + kPT < cnt) {
-        qg1 = geo[base + kPT + tid];
-        xg1 = xs[(long)j * m.pe_cap + d.perm[base + kPT + tid]];
+      if (it == bid) {
+        qg0 = jq0;
+        qg1 = jq1;
+        xg0 = jx0;
+        xg1 = jx1;
+      } else {
+        if (tid < cnt) {
+          qg0 = geo[base + tid];
+          xg0 = xs[(long)j * m.pe_cap + d.perm[base + tid]];
+        }
+        if (tid + kPT < cnt) {
+          qg1 = geo[base + kPT + tid];
+          xg1 = xs[(long)j * m.pe_cap + d.perm[base + kPT + tid]];
+        }
       }
       __syncthreads();
       const int nl = tile_bits(it, j, lidx);
@@ -1133,7 +1229,19 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
-  if (!barrier(kPhK)) return;
+  arrive(kPhK);
+  // the first chunk's updated weights (phase G's) are fetched while the other
+  // CTAs finish the estimates and the CDF offsets
+  R lw0 = 0, lw1 = 0;
+  if (bid < nitems) {
+    const int j = item_pe(ipref, K, bid);
+    const long base = (long)j * m.pe_cap;
+    const int i0 = (bid - ipref[j]) * kGT + tid, i1 = i0 + kPT;
+    const R* wu = static_cast<const R*>(d.wu);
+    if (i0 < npred_s[j]) lw0 = wu[base + i0];
+    if (i1 < npred_s[j]) lw1 = wu[base + i1];
+  }
+  if (!wait(kPhK)) return;
 
   // ---- L: offspring ends per slot chunk (exact integer CDF: the chunk's
   // offset plus an inclusive scan of its q_i; c = children of slots up to i)
@@ -1158,8 +1266,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       const long base = (long)j * m.pe_cap;
       const int c0i = (it - ipref[j]) * kGT;
       const int i0 = c0i + tid, i1 = c0i + kPT + tid;   // the thread's two slots
-      const unsigned long long q0 = i0 < n ? scaled_floor(wu[base + i0], d.rs_s[j]) : 0ull;
-      const unsigned long long q1 = i1 < n ? scaled_floor(wu[base + i1], d.rs_s[j]) : 0ull;
+      const R w0 = it == bid ? lw0 : (i0 < n ? wu[base + i0] : (R)0);
+      const R w1 = it == bid ? lw1 : (i1 < n ? wu[base + i1] : (R)0);
+      const unsigned long long q0 = i0 < n ? scaled_floor(w0, d.rs_s[j]) : 0ull;
+      const unsigned long long q1 = i1 < n ? scaled_floor(w1, d.rs_s[j]) : 0ull;
       const unsigned long long off = __ldcg(d.pcoff + it);
       const uint32_t U = a.u ? a.u[j] : philox_u32(m, (uint32_t)j, step, kTagResample);
       const unsigned long long Qn = __ldcg(d.rs_Qn + j);

@@ -328,18 +328,20 @@ def test_dense_workload_64_pes_full_size(path):
     assert rep.compared_labels > 100
 
 
-def test_barrier_timeout_is_reported_and_recoverable():
-    """Failure detection without a GPU fault: the host flags PE 0 as lost, so
-    it leaves the fused step at the first grid barrier without arriving; the
-    other PEs' bounded waits (limit lowered to 2e4 polls) give up, the step
-    reports PHD_ERR_TIMEOUT, and the same handle then steps normally again
-    (barrier words, flag and error word reset)."""
+@pytest.mark.parametrize("path", ["fused", "grid"])
+def test_barrier_timeout_is_reported_and_recoverable(path):
+    """Failure detection without a GPU fault: the host flags PE 0 (on the grid
+    path, CTA 0 of the step kernel) as lost, so it leaves the step at the
+    first grid barrier without arriving; the others' bounded waits (limit
+    lowered to 2e4 polls) give up, the step reports PHD_ERR_TIMEOUT, and the
+    same handle then steps normally again (barrier words, flag, error word
+    and the grid path's running cell totals reset)."""
     from paper_1503_03769_gb300 import PhdError, phd
-    w = scenario.workload("dist16_10t", num_pe=4, n_targets=3, clutter_rate=10.0, particles_per_target=200,
-                          birth_count=200)
+    w = scenario.workload("dist16_10t", num_pe=4 if path == "fused" else 1, n_targets=3, clutter_rate=10.0,
+                          particles_per_target=200, birth_count=200, exchange_frac=0.1 if path == "fused" else 0.0)
     sc = scenario.simulate(w, 2, steps=6)
-    f = _filter(w, 2, "fused")
-    ref = _filter(w, 2, "fused")
+    f = _filter(w, 2, path)
+    ref = _filter(w, 2, path)
     for k in range(2):
         f.step(sc.meas[k])
         ref.step(sc.meas[k])
@@ -410,6 +412,42 @@ def test_edge_cases_and_errors():
         f.extract(cap=1)
     assert e.value.status == P.PHD_ERR_CAPACITY and e.value.count > 1
     f.resample()
+    f.close()
+
+
+@pytest.mark.parametrize("path", ["grid", "staged"])
+def test_whole_step_edge_cases(path):
+    """Whole steps (phd_step) at the edges, on the grid path and the staged
+    graph: an empty filter with no measurements (births only: the mass is
+    (1 - p_D) nu_b, nothing is extracted, rho max(1, N) particles are kept);
+    exactly m_max measurements with an estimate count above cap (reported as
+    PHD_ERR_CAPACITY with the true count, and the filter steps on); a
+    non-finite measurement (reported as PHD_ERR_INVALID_ARG)."""
+    from paper_1503_03769_gb300 import PhdError
+    from paper_1503_03769_gb300 import phd as P
+    w = scenario.workload("linear4_fp64", precision="fp32", birth_count=50, particles_per_target=20)
+    f = _filter(w, 0, path)
+    assert f.get_path() == path
+    s, l = f.step(np.zeros((0, 2), np.float32))
+    C, mass = f.get_update()
+    assert mass[0] == pytest.approx((1 - w.p_d) * w.birth_mass, rel=1e-6)
+    assert len(l) == 0
+    xs, ws = f.get_state()
+    assert len(xs[0]) == 20          # rho * max(1, N) with N < 1
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-900, 900, (w.pe_cap - 50, 4)).astype(np.float32)
+    x[:, [1, 3]] = 0
+    f.set_state([x], [np.full(len(x), 0.05, np.float32)])
+    Zf = np.asarray(x[:w.m_max][:, [0, 2]], np.float32)
+    with pytest.raises(PhdError) as e:
+        f.step(Zf, cap=1)
+    assert e.value.status == P.PHD_ERR_CAPACITY and e.value.count > 1
+    s, l = f.step(Zf[:10])
+    assert np.isfinite(s.cpu().numpy()).all()
+    Z = np.array([[1.0, 2.0], [np.nan, 0.0]], np.float32)
+    with pytest.raises(PhdError) as e:
+        f.step(Z)
+    assert e.value.status == P.PHD_ERR_INVALID_ARG
     f.close()
 
 
