@@ -31,8 +31,8 @@
 //   G  pass 2 (Eq. 8) per tile: updated weights, tile sums and maxima;
 //      selection ranks (Step 3) per measurement beside it
 //   H  (batches) N^j, the resampling plan, LT_j per slice
-//   J  (one filter: N^j, the plan and LT_j in every CTA) CDF chunk totals per
-//      chunk; pass 3 (Eq. 18 sums) per tile
+//   J  CDF chunk totals per chunk; pass 3 (Eq. 18 sums) per tile (one
+//      filter: N^j, the plan and LT_j from integer sums kept by F and G)
 //   K  estimates per selected label; CDF chunk offsets per slice
 //   L  offspring ends per chunk and the children gathered (Sec. 2.2 step 3),
 //      counts and step counter advanced
@@ -226,7 +226,14 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
     if (bid == 0) {
-      for (int j = tid; j < K; j += kPT) d.n_pred[j] = npred_s[j];
+      for (int j = tid; j < K; j += kPT) {
+        d.n_pred[j] = npred_s[j];
+        // the slice plan's inputs, filled by F and G
+        d.pmassq[2 * j] = 0ull;
+        d.pmassq[2 * j + 1] = 0ull;
+        d.pwmaxb[j] = 0ull;
+        d.pnpos[j] = 0;
+      }
       if (tid == 0 && a.direct) *d.M = a.M;
     }
     for (int it = bid; it < nitems; it += nb) {
@@ -641,7 +648,9 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         d.Cused[j * m.m_max + p] = c;
         const double den = d.kap[j] + c;
         ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
-        d.dwkey[j * m.m_max + p] = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
+        const unsigned long long key = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
+        d.dwkey[j * m.m_max + p] = key;
+        if (key > 0ull) atomicAdd(d.pnpos + j, 1);
       }
     }
     if (bid == 0) {
@@ -677,6 +686,79 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
       }
     }
   }
+  // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
+  // LT_j = min(round(N^j), labels with dW > 0).  One filter: every CTA forms
+  // them at the start of J from the integer sums F and G kept (N^j as exact
+  // fixed-point sums of the tile sums, the largest weight and the count of
+  // positive labels), and the barrier between H and J goes.
+  __shared__ int nsel_s, rss_s;
+  auto slice_plan = [&](int j, bool store) {
+    // N^j: the FP64 sum of the tile sums by warp 0 alone (lane l: tiles l,
+    // l + 32, ... in order, then a shuffle tree), so one warp per CTA uses
+    // the narrow FP64 pipe; the largest weight and the count of positive
+    // labels on the integer units (non-negative doubles order as their bit
+    // patterns)
+    double s = 0.0;
+    unsigned long long mxb = 0ull;
+    int npos = 0;
+    const int M = slice_M(d, j);
+    const int nt = tpref[j + 1] - tpref[j];
+    // every thread fetches its share of the tile sums into shared memory (one
+    // round of loads), then warp 0 adds them
+    double* ts = reinterpret_cast<double*>(smem);   // [tiles of the slice] when they fit, else read directly
+    const bool staged = (size_t)nt * sizeof(double) <= smem_bytes;
+    for (int t = tid; t < nt; t += kPT) {
+      const double v = __ldcg(d.rowpart + tpref[j] + t);
+      if (staged) ts[t] = v;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(d.rowmax + tpref[j] + t));
+      mxb = b > mxb ? b : mxb;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll 8
+      for (int t = lane; t < nt; t += 32) s += staged ? ts[t] : __ldcg(d.rowpart + tpref[j] + t);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    for (int p = tid; p < M; p += kPT) npos += __ldcg(d.dwkey + j * m.m_max + p) > 0ull ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mxb, o);
+      mxb = t > mxb ? t : mxb;
+    }
+    npos = warp_sum(npos);
+    __syncthreads();
+    if (lane == 0) {
+      dredb[wid] = mxb;
+      wcnt[wid] = npos;
+      if (wid == 0) dred[0] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double t = dred[0];
+      unsigned long long tb = 0ull;
+      int np = 0;
+      for (int k = 0; k < kPT / 32; ++k) {
+        tb = dredb[k] > tb ? dredb[k] : tb;
+        np += wcnt[k];
+      }
+      const double tm = __longlong_as_double((long long)tb);
+      int L, sc;
+      resample_plan(d.rho[j], d.lmax[j], npred_s[j], t, tm, L, sc);
+      long long LT = llround(t);
+      if (LT > np) LT = np;
+      if (LT < 0) LT = 0;
+      nsel_s = (int)LT;
+      rss_s = sc;
+      if (store) {
+        d.mass[j] = t;
+        d.rs_mass[j] = t;
+        d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
+        d.rs_s[j] = sc;
+        d.rs_L[j] = L;
+        d.nsel[j] = (int)LT;
+      }
+    }
+    __syncthreads();
+  };
   arrive(kPhF);
   // the first tile's records and slots (phase D's) are fetched while the
   // other CTAs finish the normalisers
@@ -792,6 +874,15 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         }
         d.rowpart[it] = s;
         d.rowmax[it] = (double)mx;
+        // the slice's mass as exact integer sums (any order gives the same
+        // bits): s 2^30 = hi + f with f in [0, 1), lo = floor(f 2^32); the
+        // largest weight as an integer max of the bit patterns
+        const double s30 = s * 1073741824.0;
+        const unsigned long long hi = __double2ull_rz(s30);
+        const unsigned long long lo = __double2ull_rz((s30 - (double)hi) * 4294967296.0);
+        atomicAdd(d.pmassq + 2 * j, hi);
+        atomicAdd(d.pmassq + 2 * j + 1, lo);
+        atomicMax(d.pwmaxb + j, (unsigned long long)__double_as_longlong((double)mx));
       }
     }
   }
@@ -845,86 +936,12 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   }
   if (!wait(kPhG)) return;
 
-  // ---- H: per slice: N^j (tile sums in a fixed order), the resampling plan,
-  // LT_j = min(round(N^j), labels with dW > 0).  One filter: every CTA forms
-  // them itself at the start of J (the same loads in the same order, so the
-  // same values in every CTA) and the barrier between H and J goes.
-  __shared__ int nsel_s, rss_s;
-  auto slice_plan = [&](int j, bool store) {
-    // N^j: the FP64 sum of the tile sums by warp 0 alone (lane l: tiles l,
-    // l + 32, ... in order, then a shuffle tree), so one warp per CTA uses
-    // the narrow FP64 pipe; the largest weight and the count of positive
-    // labels on the integer units (non-negative doubles order as their bit
-    // patterns)
-    double s = 0.0;
-    unsigned long long mxb = 0ull;
-    int npos = 0;
-    const int M = slice_M(d, j);
-    const int nt = tpref[j + 1] - tpref[j];
-    // every thread fetches its share of the tile sums into shared memory (one
-    // round of loads), then warp 0 adds them
-    double* ts = reinterpret_cast<double*>(smem);   // [tiles of the slice] when they fit, else read directly
-    const bool staged = (size_t)nt * sizeof(double) <= smem_bytes;
-    for (int t = tid; t < nt; t += kPT) {
-      const double v = __ldcg(d.rowpart + tpref[j] + t);
-      if (staged) ts[t] = v;
-      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(d.rowmax + tpref[j] + t));
-      mxb = b > mxb ? b : mxb;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll 8
-      for (int t = lane; t < nt; t += 32) s += staged ? ts[t] : __ldcg(d.rowpart + tpref[j] + t);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    }
-    for (int p = tid; p < M; p += kPT) npos += __ldcg(d.dwkey + j * m.m_max + p) > 0ull ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mxb, o);
-      mxb = t > mxb ? t : mxb;
-    }
-    npos = warp_sum(npos);
-    __syncthreads();
-    if (lane == 0) {
-      dredb[wid] = mxb;
-      wcnt[wid] = npos;
-      if (wid == 0) dred[0] = s;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const double t = dred[0];
-      unsigned long long tb = 0ull;
-      int np = 0;
-      for (int k = 0; k < kPT / 32; ++k) {
-        tb = dredb[k] > tb ? dredb[k] : tb;
-        np += wcnt[k];
-      }
-      const double tm = __longlong_as_double((long long)tb);
-      int L, sc;
-      resample_plan(d.rho[j], d.lmax[j], npred_s[j], t, tm, L, sc);
-      long long LT = llround(t);
-      if (LT > np) LT = np;
-      if (LT < 0) LT = 0;
-      nsel_s = (int)LT;
-      rss_s = sc;
-      if (store) {
-        d.mass[j] = t;
-        d.rs_mass[j] = t;
-        d.rs_wn[j] = L > 0 ? t / (double)L : 0.0;
-        d.rs_s[j] = sc;
-        d.rs_L[j] = L;
-        d.nsel[j] = (int)LT;
-      }
-    }
-    __syncthreads();
-  };
   if (!a.direct) {
     for (int j = bid; j < K; j += nb) slice_plan(j, true);
     if (!barrier(kPhH)) return;
   }
 
-  // ---- J: one filter: N^j, the resampling plan and LT_j formed by every
-  // CTA itself (the same loads in the same order, so the same values in
-  // every CTA); the CDF chunk totals per slot chunk; pass 3 per tile (Eq. 18
+  // ---- J: the CDF chunk totals per slot chunk; pass 3 per tile (Eq. 18
   // label sums of the selected labels that can reach the tile, offsets from
   // the label's point)
   {
@@ -944,7 +961,31 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         }
       }
     }
-    if (a.direct) slice_plan(0, bid == 0);
+    if (a.direct) {
+      // one filter: N^j, the resampling plan and LT_j from F's and G's
+      // integer sums (every CTA the same; CTA 0 stores them; N^j / L_j in K)
+      if (tid == 0) {
+        const double t = (double)__ldcg(d.pmassq) * 9.313225746154785e-10 +        // 2^-30
+                         (double)__ldcg(d.pmassq + 1) * 2.168404344971009e-19;    // 2^-62
+        const double tm = __longlong_as_double((long long)__ldcg(d.pwmaxb));
+        const int np = __ldcg(d.pnpos);
+        int L, sc;
+        resample_plan(d.rho[0], d.lmax[0], npred_s[0], t, tm, L, sc);
+        long long LT = llround(t);
+        if (LT > np) LT = np;
+        if (LT < 0) LT = 0;
+        nsel_s = (int)LT;
+        rss_s = sc;
+        if (bid == 0) {
+          d.mass[0] = t;
+          d.rs_mass[0] = t;
+          d.rs_s[0] = sc;
+          d.rs_L[0] = L;
+          d.nsel[0] = (int)LT;
+        }
+      }
+      __syncthreads();
+    }
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);
     for (int it = bid; it < nitems; it += nb) {
       const int j = item_pe(ipref, K, it);
@@ -1215,6 +1256,10 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
         const Recip r = make_recip(carry);
         d.rs_rcp[2 * j] = r.d;
         d.rs_rcp[2 * j + 1] = r.v;
+        if (a.direct) {   // the new weight N^j / L_j (batches: formed in H)
+          const int L = d.rs_L[j];
+          d.rs_wn[j] = L > 0 ? d.rs_mass[j] / (double)L : 0.0;
+        }
       }
       __syncthreads();
     }

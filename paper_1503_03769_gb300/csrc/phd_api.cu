@@ -154,6 +154,9 @@ size_t carve(const phd_config& c, char* base, Dev* d, void** out_states, int** o
   t.pcsum = cv.take<unsigned long long>(items);
   t.pcoff = cv.take<unsigned long long>(items);
   t.pbar = cv.take<unsigned long long>(1);
+  t.pmassq = cv.take<unsigned long long>(2 * K);
+  t.pwmaxb = cv.take<unsigned long long>(K);
+  t.pnpos = cv.take<int>(K);
   t.ptimes = cv.take<unsigned long long>(48);
   void* os = cv.take<char>(Mm, 4 * rs);
   int* ol = cv.take<int>(Mm);

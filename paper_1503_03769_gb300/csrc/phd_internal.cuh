@@ -183,6 +183,9 @@ struct Dev {
   unsigned long long* pcsum;  // [max_items] CDF totals per slot chunk
   unsigned long long* pcoff;  // [max_items] their exclusive offsets within the slice
   unsigned long long* pbar;   // [1] arrival count of the kernel's grid barriers (only grows)
+  unsigned long long* pmassq; // [2K] grid path: slice mass as two fixed-point integers (2^-30 and 2^-62 units), integer adds of the tile sums
+  unsigned long long* pwmaxb; // [K] grid path: largest updated weight (bit pattern, integer max)
+  int* pnpos;                 // [K] grid path: labels with dW > 0
   unsigned long long* ptimes; // [16] phase durations summed over launches, ns
   int gwords;            // words of gbits per tile: ceil(m_max / 32)
 };
