@@ -892,7 +892,32 @@ __global__ void __launch_bounds__(kPT, 3) k_step_grid(Dev d, Model m, PersistArg
   // ties to the lower label) goes to selrank, the measurement to sel[rank]
   // (the ranks are a permutation); the selection itself, rank < LT, is
   // applied where LT is known (J, K)
-  {
+  if (a.direct && ntiles < nb) {
+    // one filter with CTAs to spare: only those rank, each from a copy of the
+    // slice's dW keys in shared memory (one load round per CTA)
+    if (bid >= ntiles) {
+      const int M = a.M;
+      unsigned long long* ks = reinterpret_cast<unsigned long long*>(smem);   // [M]
+      for (int p = tid; p < M; p += kPT) ks[p] = __ldcg(d.dwkey + p);
+      __syncthreads();
+      const long nw = (long)(nb - ntiles) * (kPT / 32);
+      for (long u = (long)(bid - ntiles) * (kPT / 32) + wid; u < M; u += nw) {
+        const int p = (int)u;
+        const unsigned long long v = ks[p];
+        int c = 0;
+#pragma unroll 8
+        for (int q = lane; q < M; q += 32) {
+          const unsigned long long w2 = ks[q];
+          c += (w2 > v || (w2 == v && q < p)) ? 1 : 0;
+        }
+        const int rank = warp_sum(c);
+        if (lane == 0) {
+          d.selrank[p] = rank;
+          d.sel[rank] = p;
+        }
+      }
+    }
+  } else {
     const long units = a.direct ? (long)a.M : (long)K * m.m_max;
     for (long u = (long)(nb - 1 - bid) * (kPT / 32) + wid; u < units; u += nwarps) {
       const int j = a.direct ? 0 : (int)(u / m.m_max);
