@@ -614,10 +614,10 @@ bool use_fused(const phd_handle* h) {
 // capacity per CTA and ~2 in use): there each phase is a few latency-bound
 // rounds per CTA and the launches and barriers of the staged graph are what
 // the step's time goes to.  Past that (batches of tens to hundreds of runs,
-// 50-200 chunks per CTA) the phases become long serial chains at 3 CTAs per
-// SM, and the staged kernels (more resident threads, autotuned pair-pass
-// shapes) are faster (256 runs, ~1e7 particles: 1.05 ms per batched step
-// staged, 1.17 ms grid).
+// 50-200 chunks per CTA) the phases become long serial chains, and the
+// staged graph with the autotuner's launch shapes runs level with the grid
+// kernel at its batch register budget (256 runs, ~1e7 particles: 1.05 ms
+// per batched step staged, 1.04 ms grid); AUTO keeps the autotuned graph.
 constexpr double kGridAutoItems = 16.0;
 bool grid_auto(const phd_handle* h) {
   const double items = (double)h->m.K * (double)((h->cfg.pe_cap + 255) / 256);
@@ -847,7 +847,7 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
   if (e == cudaSuccess)
     h->fused_ok = is_fp64(h) ? phd::fused_eligible<double>(h->m, h->device) : phd::fused_eligible<float>(h->m, h->device);
   if (e == cudaSuccess && h->m.K == 1)
-    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m) : phd::persist_grid<float>(h->m);
+    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m, false) : phd::persist_grid<float>(h->m, false);
   (void)cudaGetLastError();   // an ineligible attribute query leaves no sticky error
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
   phd::Anchor tab[phd::kAnchors];
@@ -1453,7 +1453,7 @@ phd_status phd_batch_init(phd_handle** out, const phd_config* cfgs, int32_t runs
   cudaError_t err = cudaGetDevice(&h->device);
   if (err == cudaSuccess) err = is_fp64(h) ? phd::prepare_kernels<double>(h->m) : phd::prepare_kernels<float>(h->m);
   if (err == cudaSuccess)
-    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m) : phd::persist_grid<float>(h->m);
+    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m, true) : phd::persist_grid<float>(h->m, true);
   (void)cudaGetLastError();
   if (err == cudaSuccess) err = cudaMemsetAsync(ws, 0, need, h->stream);
   phd::Anchor tab[phd::kAnchors];

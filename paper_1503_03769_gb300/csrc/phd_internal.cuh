@@ -1082,7 +1082,7 @@ template <class R> cudaError_t prepare_extract();
 cudaError_t prepare_exchange(const Model& m);
 template <class R> bool fused_eligible(const Model& m, int device);
 // persistent step kernel (k_persist.cu): grid size (0: cannot launch), launch
-template <class R> int persist_grid(const Model& m);
+template <class R> int persist_grid(const Model& m, bool wide);   // wide: the batch kernel
 template <class R>
 cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
                            const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
