@@ -307,7 +307,7 @@ def run_reference(args, w, rank, world):
 # the kernel sources the counters were taken on).  The traffic is reported
 # only while those sources are unchanged.
 _TRAFFIC_PROFILES = {
-    ("grid", "dense_rb_100t"): ("k_step_grid_dense_rb_100t_ncu.md", ("k_persist.cu", "phd_internal.cuh")),
+    ("grid", "dense_rb_100t"): ("k_step_grid_dense_rb_100t_ncu.md", ("k_persist.cuh", "phd_internal.cuh")),
     ("fused", "dist16_10t"): ("k_step_fused_dist16_ncu.md", ("k_fused.cu", "phd_internal.cuh")),
     ("staged", "dense_rb_100t"): ("update_dense_rb_100t_ncu.md",
                                   ("k_update.cu", "k_order.cu", "k_extract.cu", "phd_internal.cuh")),
