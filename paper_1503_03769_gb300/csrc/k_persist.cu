@@ -12,6 +12,7 @@ void* persist_kernel_wide_f32(int rb);   // k_persist_wide.cu
 template <class R> size_t persist_smem(int m_max) {
   const size_t mm = ((size_t)m_max + 7) & ~(size_t)7;
   const size_t a = 16 * kCells * sizeof(int);                                        // D
+  const size_t l = (kPT / 32) * sizeof(unsigned long long) + kGT * (sizeof(int) + sizeof(St4<R>));  // L
   const size_t e = kGT * sizeof(P4<R>) + mm * sizeof(int);                          // E
   const size_t g = mm * (sizeof(int) + sizeof(Z4<R>)) + (kPT / 32) * mm * sizeof(unsigned short);   // G
   const size_t j = kGT * sizeof(P4<R>) + kGT * sizeof(St4<R>) + mm * sizeof(int2) + mm * sizeof(int);  // J
@@ -19,6 +20,7 @@ template <class R> size_t persist_smem(int m_max) {
   if (e > s) s = e;
   if (g > s) s = g;
   if (j > s) s = j;
+  if (l > s) s = l;
   return (s + 127) & ~(size_t)127;
 }
 

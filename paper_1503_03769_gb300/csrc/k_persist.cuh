@@ -1331,6 +1331,7 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
     const R* wu = static_cast<const R*>(d.wu);
     unsigned long long* wt = reinterpret_cast<unsigned long long*>(smem);   // [kPT / 32]
     int* cend = reinterpret_cast<int*>(wt + kPT / 32);                      // [kGT]
+    St4<R>* sxs = reinterpret_cast<St4<R>*>(cend + kGT);                    // [kGT] the chunk's parents
     __shared__ int cprev_s;
     if (bid == 0)
       for (int j = tid; j < K; j += kPT) d.n_cur[j] = d.rs_L[j];
@@ -1344,6 +1345,9 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
       const int i0 = c0i + tid, i1 = c0i + kPT + tid;   // the thread's two slots
       const R w0 = it == bid ? lw0 : (i0 < n ? wu[base + i0] : (R)0);
       const R w1 = it == bid ? lw1 : (i1 < n ? wu[base + i1] : (R)0);
+      // the chunk's predicted states, staged once for its children
+      sxs[tid] = i0 < n ? xp[base + i0] : St4<R>{0, 0, 0, 0};
+      sxs[kPT + tid] = i1 < n ? xp[base + i1] : St4<R>{0, 0, 0, 0};
       const unsigned long long q0 = i0 < n ? scaled_floor(w0, d.rs_s[j]) : 0ull;
       const unsigned long long q1 = i1 < n ? scaled_floor(w1, d.rs_s[j]) : 0ull;
       const unsigned long long off = __ldcg(d.pcoff + it);
@@ -1371,11 +1375,11 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
         for (int st = kGT / 2; st > 0; st >>= 1)
           if (cend[lo + st - 1] <= t) lo += st;
         const int par = c0i + lo;
-        x[base + t] = xp[base + par];
+        x[base + t] = sxs[lo];
         w[base + t] = wn;
         d.parent[base + t] = par;
       }
-      __syncthreads();   // cend and cprev_s are rewritten by the next chunk
+      __syncthreads();   // cend, sxs and cprev_s are rewritten by the next chunk
     }
     // every reader of this step's counter finished before the last barrier
     if (tid == 0) {
