@@ -1148,7 +1148,23 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
       }
     }
   }
-  if (!barrier(kPhJ)) return;
+  arrive(kPhJ);
+  // one filter, a label per CTA (the group mapping K uses when labels are
+  // few): the label's measurement, its point and its output position (all
+  // from G) are fetched while the other CTAs finish pass 3
+  const bool kpre = a.direct && (long)nsel_s * 16 <= nwarps && bid < nsel_s;
+  int kp_p = 0, kp_below = 0;
+  V2<R> kp_z{0, 0};
+  if (kpre) {
+    kp_p = __ldcg(d.sel + bid);
+    if (wid == 0) {
+      int b = 0;
+      for (int t = lane; t < nsel_s; t += 32) b += __ldcg(d.sel + t) < kp_p ? 1 : 0;
+      kp_below = warp_sum(b);
+    }
+    kp_z = slice_Z<R>(d, 0)[kp_p];
+  }
+  if (!wait(kPhJ)) return;
 
   // ---- K: estimates (Eq. 18) per selected label: the live tile partials in
   // tile order, in the kernel's precision (the tile partials are sums of
@@ -1180,11 +1196,17 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
       if (g.G == 1 && !act) continue;
       int p = 0, below = 0;
       R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      const bool pre = kpre && g.G == kPT / 32 && r0 == 0;   // fetched before the wait
       if (act) {   // uniform over the group
-        p = __ldcg(d.sel + j * m.m_max + r);
-        if (a.direct) {
-          for (int t = g.gl; t < nsel; t += 32 * g.G) below += __ldcg(d.sel + j * m.m_max + t) < p ? 1 : 0;
-          below = warp_sum(below);
+        if (pre) {
+          p = kp_p;
+          below = wid == 0 ? kp_below : 0;   // the group's sum below adds the warps' shares
+        } else {
+          p = __ldcg(d.sel + j * m.m_max + r);
+          if (a.direct) {
+            for (int t = g.gl; t < nsel; t += 32 * g.G) below += __ldcg(d.sel + j * m.m_max + t) < p ? 1 : 0;
+            below = warp_sum(below);
+          }
         }
         const unsigned* brow = d.gbits + (long)(p >> 5) * T;
         const int t1 = tpref[j + 1];
@@ -1237,7 +1259,7 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
         par ^= 1;
       }
       if (act && g.gl == 0) {
-        const V2<R> z = slice_Z<R>(d, j)[p];
+        const V2<R> z = pre ? kp_z : slice_Z<R>(d, j)[p];
         R px, py;
         meas_point<R>(m, z, px, py);
         St4<R> o;
