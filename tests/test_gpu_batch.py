@@ -92,3 +92,51 @@ def test_batch_free_running_and_capacity_errors():
         b.batch_step(Zs)
     assert e.value.status == P.PHD_ERR_CAPACITY
     b.close()
+
+
+@pytest.mark.parametrize("path", ["grid", "staged"])
+def test_batch_edge_runs_match_their_oracles(path):
+    """Runs at the edges in one batched step, each against its own oracle
+    step from generator slices: no particles and no measurements (births
+    only), particles and no measurements, no particles and a scan, and an
+    ordinary run."""
+    from paper_1503_03769_gb300 import ParticlePHDBatch
+    ws = _runs()[:4]
+    R = len(ws)
+    b = ParticlePHDBatch(ws, seed=5)
+    b.set_path(path)
+    assert b.get_path() == path
+    scs = [scenario.simulate(w, 80 + j, steps=2) for j, w in enumerate(ws)]
+    n_seed = [0, 600, 0, 900]
+    xs, wts = [], []
+    for j, w in enumerate(ws):
+        if n_seed[j]:
+            cen = np.concatenate([t[:, [0, 2]] for t in scs[j].truth if len(t)])
+            x, wt = exact_state(w, 300 + j, [n_seed[j]], centres=cen, mass=2.0)
+            xs.append(x[0])
+            wts.append(wt[0])
+        else:
+            xs.append(np.zeros((0, 4), np.float32))
+            wts.append(np.zeros(0, np.float32))
+    b.set_state(xs, wts)
+    empty = np.zeros((0, 2), np.float32)
+    Zs = [empty, empty, np.asarray(scs[2].meas[1], np.float32), np.asarray(scs[3].meas[1], np.float32)]
+    noise = exact_noise(9, 1, R, b.pe_cap, np.float32)
+    u = scenario.resample_u32(9, 1, R)
+    outs = b.batch_step(Zs, noise=noise, u=u)
+    xp, wp, wu = b.get_predicted()
+    C, mass = b.get_update()
+    loc_s, loc_l = b.get_local_estimates()
+    par, _ = b.get_resample()
+    xr, wr = b.get_state()
+    nz = np.asarray(noise).reshape(R, b.pe_cap, 4)
+    rep = StageReport()
+    for j, w in enumerate(ws):
+        g = dict(xp=[xp[j]], wp=[wp[j]], wu=[wu[j]], C=C[j:j + 1], mass=mass[j:j + 1], loc_s=[loc_s[j]],
+                 loc_l=[loc_l[j]], states=outs[j][0], labels=outs[j][1], par=par[j:j + 1], lx=0,
+                 xr=[xr[j]], wr=[wr[j]])
+        check_step_from_inputs(w, oracle.model(w), [xs[j]], [wts[j]], Zs[j], nz[j], u[j:j + 1], None, g, rep)
+    # births only where nothing was measured: the mass is (1 - p_D) nu_b
+    assert mass[0] == pytest.approx((1 - ws[0].p_d) * ws[0].birth_mass, rel=1e-6)
+    assert len(outs[0][1]) == 0 and len(outs[1][1]) == 0
+    b.close()
