@@ -70,10 +70,7 @@ template <class R> struct PersistArgs {
 // an error recorded by another CTA the wait returns false in every thread.
 __device__ __forceinline__ void pbar_arrive(const Dev& d) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long old;
-    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(d.pbar) : "memory");
-  }
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(d.pbar) : "memory");
 }
 __device__ __forceinline__ bool pbar_wait(const Dev& d, unsigned long long target, long long limit) {
   __shared__ int ok_s;
@@ -127,6 +124,8 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
   __shared__ int tpref[kMaxPE + 1];   // pair-pass tiles (kGT particles) per slice, prefix
   __shared__ int hpref[kMaxPE + 1];   // chunk-histogram rows per slice: 256 x (items rounded up to 4), prefix
   __shared__ int npred_s[kMaxPE];     // predicted particles per slice
+  __shared__ int ncur_s[kMaxPE];      // survivors per slice (the current set)
+  __shared__ R bw_s[kMaxPE];          // birth weight per slice
   __shared__ int wcnt[kPT / 32];
   __shared__ R bsh[4 * (kPT / 32)];
   __shared__ double dred[kPT / 32];
@@ -201,7 +200,11 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
     return wait(phase);
   };
   // slice sizes after prediction: survivors + births
-  for (int j = tid; j < K; j += kPT) npred_s[j] = d.n_cur[j] + d.Jb[j];
+  for (int j = tid; j < K; j += kPT) {
+    ncur_s[j] = d.n_cur[j];
+    npred_s[j] = ncur_s[j] + d.Jb[j];
+    bw_s[j] = slice_bw<R>(d, j);
+  }
   __syncthreads();
   slice_prefix(K, ipref, [&](int j) { return (npred_s[j] + kGT - 1) / kGT; });
   slice_prefix(K, tpref, [&](int j) { return (npred_s[j] + kGT - 1) / kGT; });
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
         int key = kCells;   // none
         if (i < npred_s[j]) {
           const long g = (long)j * m.pe_cap + i;
-          const bool surv = i < d.n_cur[j];
+          const bool surv = i < ncur_s[j];
           St4<R> o;
           R wo;
           if (!surv && m.learned) {
@@ -263,8 +266,8 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
           } else {
             R n1, n2, u1, u2;
             draw_noise<R>(m, a.noise, g, step, n1, n2, u1, u2);
-            predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, slice_bw<R>(d, j),
-                            n1, n2, u1, u2, o, wo);
+            predict_slot<R>(cc, surv, surv ? x[g] : St4<R>{0, 0, 0, 0}, surv ? w[g] : (R)0, bw_s[j], n1, n2, u1,
+                            u2, o, wo);
             xp[g] = o;
             wp[g] = wo;
           }
@@ -476,7 +479,6 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
   auto tile_bits = [&](int it, int j, int* lidx) -> int {
     const int M = slice_M(d, j);
     const int nwd = (M + 31) / 32;
-    if (tid == 0) nlive_s = 0;
     __syncthreads();
     int nl = 0;
     for (int w0 = 0; w0 < nwd; w0 += kPT) {
