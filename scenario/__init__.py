@@ -383,7 +383,8 @@ def random_particles(rng: np.random.Generator, w: Workload, n: int,
     vel = 20.0 * rng.standard_normal((n, 2))
     x = np.stack([pos[:, 0], vel[:, 0], pos[:, 1], vel[:, 1]], axis=1)
     wgt = rng.random(n) + 0.05
-    wgt *= mass / wgt.sum()
+    if n > 0:
+        wgt *= mass / wgt.sum()
     return x, wgt
 
 

@@ -139,7 +139,7 @@ int main(void) {
     int32_t L[M_MAX];
 
     double truth[2][4] = {{-300.0, 10.0, 200.0, -5.0}, {400.0, -8.0, -100.0, 12.0}};
-    int hits[2] = {0, 0}, judged = 0;
+    int hits[2] = {0, 0}, scored = 0;
     for (int k = 0; k < SCANS + HOST_SCANS; ++k) {
         move(truth);
         const int M = make_scan(truth, Z);
@@ -152,7 +152,7 @@ int main(void) {
             CHECK(phd_step_host(h, Z, M, S, L, M_MAX, &n));
         }
         if (k >= 15) {
-            ++judged;
+            ++scored;
             for (int t = 0; t < 2; ++t) hits[t] += near(truth, S, n, t);
         }
         if (k % 10 == 9) printf("scan %d: %d measurements, %d estimates\n", k + 1, M, (int)n);
@@ -171,7 +171,7 @@ int main(void) {
     CUDA(cudaFree(dL));
     CUDA(cudaFree(dN));
     CUDA(cudaFree(ws));
-    const int ok = hits[0] * 10 >= judged * 8 && hits[1] * 10 >= judged * 8;
-    printf("tracked %d/%d and %d/%d scans: %s\n", hits[0], judged, hits[1], judged, ok ? "ok" : "FAIL");
+    const int ok = hits[0] * 10 >= scored * 8 && hits[1] * 10 >= scored * 8;
+    printf("tracked %d/%d and %d/%d scans: %s\n", hits[0], scored, hits[1], scored, ok ? "ok" : "FAIL");
     return ok ? 0 : 2;
 }
