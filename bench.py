@@ -1011,8 +1011,8 @@ def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p, extra=()):
     """The paper's three filters on the same scenarios of workload wd: the
     global filter (PHD, all particles), the distributed scheme (DCPFPHD, wd's
     PEs, ring exchange, CU fusion) and the global filter on 1/K of the
-    particles (partPHD), plus any `extra` (name, workload) variants; steps/s
-    and OSPA (c = 100 m, order ospa_p) each."""
+    particles (partPHD), plus any `extra` (name, workload[, path]) variants;
+    steps/s and OSPA (c = 100 m, order ospa_p) each."""
     import torch
     from paper_1503_03769_gb300 import ParticlePHD
 
@@ -1026,8 +1026,11 @@ def _three_way(args, wd, seeds, dev, rank, local_rank, ospa_p, extra=()):
     scen = {s_: scenario.simulate(wd, s_) for s_ in seeds}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     res = {}
-    for name, w in variants:
+    for v in variants:
+        name, w = v[0], v[1]
         f = ParticlePHD(w, seed=5 + rank, device=f"cuda:{local_rank}")
+        if len(v) > 2:
+            f.set_path(v[2])
         Zd = {(s_, k): torch.as_tensor(scen[s_].meas[k], dtype=torch.float32, device=dev)
               for s_ in seeds for k in range(w.steps)}
         for k in range(min(args.warmup, w.steps)):
@@ -1076,7 +1079,8 @@ def run_gpu_compare(args, rank, world, local_rank):
     seeds = [args.seed + r + 7919 * rank for r in range(runs)]
     # exchange variants (Step 6): all-to-all, and the ring only when a PE has
     # degenerated (its mass below half the PE mean)
-    extra = [("DCPFPHD_all_to_all", wd.with_(exchange_mode="all")),
+    extra = [("DCPFPHD_grid", wd, "grid"),   # the PEs spread over the grid step kernel's CTAs
+             ("DCPFPHD_all_to_all", wd.with_(exchange_mode="all")),
              ("DCPFPHD_adaptive_0.5", wd.with_(exchange_threshold=0.5)),
              # where the gap to the global filter comes from (Steps 2 and 6):
              # the normaliser (the PE mean of C^j instead of the local C^j),

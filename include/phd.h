@@ -310,16 +310,19 @@ phd_status phd_run(phd_handle *h, const void *d_Z, const int32_t *d_offsets, int
  * co-resident); PHD_PATH_GRID: one cooperative kernel per step over the
  * whole GPU, its phases (prediction, spatial order, the two pair passes,
  * selection, label sums, resampling) separated by grid-wide barriers with
- * bounded waits (available for one-PE filters and batches of independent
- * runs whose m_max fits its shared memory; with a birth network the scan is
- * staged and the network's head, mixture table and draws run as kernels
- * before it; the pair passes always walk the spatial order, the gate
- * setting of phd_set_tuning applies, its launch shapes do not);
+ * bounded waits, every PE's slice spread over the kernel's CTAs (available
+ * when m_max fits its shared memory, for one-PE filters, for K PEs on one
+ * scan without a birth network, whose scan is staged before the launch and
+ * whose CU fusion (Step 4) and exchange (Step 6) run as kernels after it,
+ * and for batches of independent runs; a one-PE filter with a birth network
+ * has the scan staged and the network's head, mixture table and draws run
+ * as kernels before it; the pair passes always walk the spatial order, the
+ * gate setting of phd_set_tuning applies, its launch shapes do not);
  * PHD_PATH_STAGED: the stage kernels of phd_predict .. phd_resample as a
  * CUDA graph; PHD_PATH_AUTO (default): fused when available, else grid when
  * available and the handle holds at most 16 chunks of 256 particle slots
  * per CTA of the step kernel (K x ceil(pe_cap / 256) <= 16 x its CTAs: one
- * filter, small batches), else staged.  phd_set_path returns
+ * filter, PEs whose slices outgrow an SM, small batches), else staged.  phd_set_path returns
  * PHD_ERR_INVALID_ARG for an unavailable path; phd_get_path reports the
  * path in use.  The stage calls (phd_predict, phd_update, phd_extract,
  * phd_resample) always run the staged kernels. */

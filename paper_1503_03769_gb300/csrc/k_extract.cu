@@ -470,6 +470,15 @@ cudaError_t launch_select(const Dev& d, const Model& m, cudaStream_t s) {
 template cudaError_t launch_select<float>(const Dev&, const Model&, cudaStream_t);
 template cudaError_t launch_select<double>(const Dev&, const Model&, cudaStream_t);
 
+template <class R>
+cudaError_t launch_fuse(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap, int* d_count,
+                        cudaStream_t s) {
+  launch_k(k_fuse<R>, dim3(1), dim3(1024), 0, s, d, m, out_states, out_labels, cap, d_count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fuse<float>(const Dev&, const Model&, float*, int*, int, int*, cudaStream_t);
+template cudaError_t launch_fuse<double>(const Dev&, const Model&, double*, int*, int, int*, cudaStream_t);
+
 template cudaError_t launch_extract<float>(const Dev&, const Model&, float*, int*, int, int*, cudaStream_t);
 template cudaError_t launch_extract<double>(const Dev&, const Model&, double*, int*, int, int*, cudaStream_t);
 

@@ -56,8 +56,8 @@ template <class R> int persist_grid(const Model& m, bool wide) {
 template <class R>
 cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
                            const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
-                           unsigned long long base, bool direct, cudaStream_t s) {
-  PersistArgs<R> a{Z, M, noise, u, out_states, out_labels, cap, d_count, base, direct ? 1 : 0};
+                           unsigned long long base, bool direct, bool advance, cudaStream_t s) {
+  PersistArgs<R> a{Z, M, noise, u, out_states, out_labels, cap, d_count, base, direct ? 1 : 0, advance ? 1 : 0};
   Dev dd = d;
   Model mm = m;
   void* args[] = {&dd, &mm, &a};
@@ -65,7 +65,7 @@ cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, i
                                      persist_smem<R>(m.m_max), s);
 }
 
-// barriers after A, C, D, E, F, G, (H: batches), J, K
+// barriers after A, C, D, E, F, G, (H: batches and PEs), J, K
 int persist_barriers(bool direct) { return direct ? 8 : 9; }
 
 template size_t persist_smem<float>(int);
@@ -74,9 +74,9 @@ template int persist_grid<float>(const Model&, bool);
 template int persist_grid<double>(const Model&, bool);
 template cudaError_t launch_persist<float>(const Dev&, const Model&, int, const float*, int, const float*,
                                            const uint32_t*, float*, int*, int, int*, unsigned long long, bool,
-                                           cudaStream_t);
+                                           bool, cudaStream_t);
 template cudaError_t launch_persist<double>(const Dev&, const Model&, int, const double*, int, const double*,
                                             const uint32_t*, double*, int*, int, int*, unsigned long long, bool,
-                                            cudaStream_t);
+                                            bool, cudaStream_t);
 
 }  // namespace phd

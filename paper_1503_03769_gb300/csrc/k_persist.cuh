@@ -61,6 +61,7 @@ template <class R> struct PersistArgs {
   int* d_count;               // one filter: true estimate count (may be NULL)
   unsigned long long base;    // barrier count at launch
   int direct;                 // 1: one filter (write the outputs)
+  int advance;                // 1: advance the step counter (0: the exchange kernels after the launch do)
 };
 
 // Barrier b (1-based) of the launch, in two halves: every CTA arrives once
@@ -609,56 +610,111 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
   if (!barrier(kPhE)) return;
 
   // ---- F: per (slice, measurement): C = p_D cnorm (sum of the live tile
-  // partials in tile order), the normaliser, ginv and the dW order key
+  // partials in tile order), the normaliser, ginv and the dW order key.
+  // PEs on one scan with the global normaliser (Alg. 1 Step 2 with the PE
+  // mean): a unit per measurement forms every PE's C^j in PE order, then
+  // C_used = their mean, the same for all PEs (not in the FP32 instance at
+  // 3 CTAs per SM, which runs one filter only)
   {
     const double cs = m.p_d * m.cnorm;
     R* ginv = static_cast<R*>(d.ginv);
-    const long units = a.direct ? (long)a.M : (long)K * m.m_max;
+    constexpr bool kMulti = !(sizeof(R) == 4 && MB == 3);
+    const bool cglob = kMulti && !a.direct && m.ck_global && K > 1;
+    const long units = a.direct ? (long)a.M : cglob ? (long)slice_M(d, 0) : (long)K * m.m_max;
     const Grp g = groups(units);
     int par = 0;
-    for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
-      const long u = r0 + g.gid;
-      int j = 0, p = 0;
-      bool act = u < units;
-      if (act) {
-        j = a.direct ? 0 : (int)(u / m.m_max);
-        p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
-        act = p < slice_M(d, j);
-      }
-      if (g.G == 1 && !act) continue;
-      // group lane l takes tiles l, l + 32 G, ... of the slice in order; the
-      // bit row of word p / 32 is contiguous over tiles; only the tiles the
-      // measurement reaches are loaded and added
-      double c = 0.0;
-      if (act) {   // uniform over the group
-        const unsigned* brow = d.gbits + (long)(p >> 5) * T;
-        const int t1 = tpref[j + 1];
-#pragma unroll 4
-        for (int t0 = tpref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds: every lane runs every round
-          const int it = t0 + g.gl;
-          const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
-          if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+    if (cglob) {
+      for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
+        const long u = r0 + g.gid;
+        const int p = (int)u;
+        const bool act = u < units;
+        if (g.G == 1 && !act) continue;
+        double mean = 0.0;
+        for (int j = 0; j < K; ++j) {   // C^j as below, the PEs in order
+          double c = 0.0;
+          if (act) {   // uniform over the group
+            const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+            const int t1 = tpref[j + 1];
+            for (int t0 = tpref[j]; t0 < t1; t0 += 32 * g.G) {
+              const int it = t0 + g.gl;
+              const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
+              if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+          if (g.G > 1) {
+            if (lane == 0) gred[par][wid][0] = c;
+            __syncthreads();
+            if (g.gl == 0) {
+              c = 0.0;
+              for (int k = 0; k < g.G; ++k) c += gred[par][g.slot * g.G + k][0];
+            }
+            par ^= 1;
+          }
+          if (act && g.gl == 0) {
+            c *= cs;
+            d.C[j * m.m_max + p] = c;
+            mean += c;
+          }
+        }
+        if (act && g.gl == 0) {
+          const double cu = mean / (double)K;
+          for (int j = 0; j < K; ++j) {
+            const double c = d.C[j * m.m_max + p];
+            d.Cused[j * m.m_max + p] = cu;
+            const double den = d.kap[j] + cu;
+            ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
+            const unsigned long long key = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
+            d.dwkey[j * m.m_max + p] = key;
+            if (key > 0ull) atomicAdd(d.pnpos + j, 1);
+          }
         }
       }
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      if (g.G > 1) {
-        if (lane == 0) gred[par][wid][0] = c;
-        __syncthreads();
-        if (g.gl == 0) {
-          c = 0.0;
-          for (int k = 0; k < g.G; ++k) c += gred[par][g.slot * g.G + k][0];
+    } else {
+      for (long r0 = 0; r0 < units; r0 += g.ng) {   // CTA-uniform rounds
+        const long u = r0 + g.gid;
+        int j = 0, p = 0;
+        bool act = u < units;
+        if (act) {
+          j = a.direct ? 0 : (int)(u / m.m_max);
+          p = a.direct ? (int)u : (int)(u - (long)j * m.m_max);
+          act = p < slice_M(d, j);
         }
-        par ^= 1;
-      }
-      if (act && g.gl == 0) {
-        c *= cs;
-        d.C[j * m.m_max + p] = c;
-        d.Cused[j * m.m_max + p] = c;
-        const double den = d.kap[j] + c;
-        ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
-        const unsigned long long key = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
-        d.dwkey[j * m.m_max + p] = key;
-        if (key > 0ull) atomicAdd(d.pnpos + j, 1);
+        if (g.G == 1 && !act) continue;
+        // group lane l takes tiles l, l + 32 G, ... of the slice in order; the
+        // bit row of word p / 32 is contiguous over tiles; only the tiles the
+        // measurement reaches are loaded and added
+        double c = 0.0;
+        if (act) {   // uniform over the group
+          const unsigned* brow = d.gbits + (long)(p >> 5) * T;
+          const int t1 = tpref[j + 1];
+  #pragma unroll 4
+          for (int t0 = tpref[j]; t0 < t1; t0 += 32 * g.G) {   // group-uniform rounds: every lane runs every round
+            const int it = t0 + g.gl;
+            const bool live = it < t1 && ((__ldcg(brow + it) >> (p & 31)) & 1u);
+            if (__any_sync(0xffffffffu, live) && live) c += __ldcg(d.colpart + (long)it * m.m_max + p);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (g.G > 1) {
+          if (lane == 0) gred[par][wid][0] = c;
+          __syncthreads();
+          if (g.gl == 0) {
+            c = 0.0;
+            for (int k = 0; k < g.G; ++k) c += gred[par][g.slot * g.G + k][0];
+          }
+          par ^= 1;
+        }
+        if (act && g.gl == 0) {
+          c *= cs;
+          d.C[j * m.m_max + p] = c;
+          d.Cused[j * m.m_max + p] = c;
+          const double den = d.kap[j] + c;
+          ginv[j * m.m_max + p] = den > 0.0 ? quot<R>(cs, den) : (R)0;
+          const unsigned long long key = order_key(den > 0.0 ? (double)quot<R>(c, den) : 0.0);
+          d.dwkey[j * m.m_max + p] = key;
+          if (key > 0ull) atomicAdd(d.pnpos + j, 1);
+        }
       }
     }
     if (bid == 0) {
@@ -1409,7 +1465,7 @@ __global__ void __launch_bounds__(kPT, MB) k_step_grid(Dev d, Model m, PersistAr
     if (tid == 0) {
       const unsigned long long t = gtimer();
       if (bid == 0) {
-        *d.step += 1ull;
+        if (a.advance) *d.step += 1ull;
         atomicAdd(d.ptimes + kPhL, t - t_prev);
       }
       atomicMax(d.ptimes + 16 + kPhL, t - t_go);

@@ -243,16 +243,24 @@ cudaError_t launch_resample(const Dev& d, const Model& m, const uint32_t* u, con
   const bool xchg = m.K > 1 && m.exchange_frac > 0.0;
   launch_k(k_rs_gather<R>, dim3((int)(gitems < 152 * 16 ? (gitems > 0 ? gitems : 1) : 152 * 16)), dim3(256), 0, s, d, m,
            !xchg);
-  if (xchg) {
-    int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
-    if (bx < 1) bx = 1;
-    if (bx > 152 * 8) bx = 152 * 8;
-    launch_k(k_xplan, dim3(m.K), dim3(256), sizeof(int) * 2 * (size_t)m.pe_cap, s, d, m, xu);
-    launch_k(k_xout<R>, dim3(bx), dim3(256), 0, s, d, m);
-    launch_k(k_xin<R>, dim3(bx), dim3(256), 0, s, d, m);
-  }
+  if (xchg) return launch_exchange<R>(d, m, xu, s);
   return cudaGetLastError();
 }
+
+// Step 6 on the resampled slices: plan, outboxes, receivers; the last kernel
+// advances the step counter.
+template <class R>
+cudaError_t launch_exchange(const Dev& d, const Model& m, const uint32_t* xu, cudaStream_t s) {
+  int bx = (int)(((long)m.K * (long)(m.exchange_frac * m.pe_cap) + 255) / 256);
+  if (bx < 1) bx = 1;
+  if (bx > 152 * 8) bx = 152 * 8;
+  launch_k(k_xplan, dim3(m.K), dim3(256), sizeof(int) * 2 * (size_t)m.pe_cap, s, d, m, xu);
+  launch_k(k_xout<R>, dim3(bx), dim3(256), 0, s, d, m);
+  launch_k(k_xin<R>, dim3(bx), dim3(256), 0, s, d, m);
+  return cudaGetLastError();
+}
+template cudaError_t launch_exchange<float>(const Dev&, const Model&, const uint32_t*, cudaStream_t);
+template cudaError_t launch_exchange<double>(const Dev&, const Model&, const uint32_t*, cudaStream_t);
 
 cudaError_t prepare_exchange(const Model& m) {
   return cudaFuncSetAttribute(k_xplan, cudaFuncAttributeMaxDynamicSharedMemorySize,

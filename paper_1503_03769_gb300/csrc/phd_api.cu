@@ -630,11 +630,15 @@ bool use_grid(const phd_handle* h) {
 
 // One launch of the grid path's step kernel.  One filter (direct): the scan
 // at Z, the estimates to states / labels (cap) and the count to d_count;
-// a batch: the scans staged by k_stage_zb, the outputs by k_batch_out.
-phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u, void* states,
-                    int* labels, int cap, int* d_count) {
+// PEs on one scan: the scan staged before the launch, the CU fusion into
+// states / labels / d_count and the exchange (draws xu) after it; a batch:
+// the scans staged by k_stage_zb, the outputs by k_batch_out.
+phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, const uint32_t* u,
+                    const uint32_t* xu, void* states, int* labels, int cap, int* d_count) {
   const bool timed = h->timer;
-  const bool direct = h->batch_runs == 0;
+  const bool direct = h->batch_runs == 0 && h->m.K == 1;
+  const bool pes = h->batch_runs == 0 && h->m.K > 1;
+  const bool xchg = pes && h->m.exchange_frac > 0.0;
   cudaError_t e = cudaSuccess;
   if (timed) {
     if (h->ev_used >= 4096) e = drain_timer(h);
@@ -646,20 +650,37 @@ phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, cons
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
+  if (e == cudaSuccess && pes && Z != h->d.Z) {
+    e = is_fp64(h) ? phd::launch_stage_z<double>(h->d, h->m, static_cast<const double*>(Z), M, h->stream)
+                   : phd::launch_stage_z<float>(h->d, h->m, static_cast<const float*>(Z), M, h->stream);
+    h->launches += kNStageZ;
+  }
   if (e == cudaSuccess)
     e = is_fp64(h) ? phd::launch_persist<double>(h->d, h->m, h->pgrid, static_cast<const double*>(Z), M,
                                                  static_cast<const double*>(noise), u, static_cast<double*>(states),
-                                                 labels, cap, d_count, h->pbar_count, direct, h->stream)
+                                                 labels, cap, d_count, h->pbar_count, direct, !xchg, h->stream)
                    : phd::launch_persist<float>(h->d, h->m, h->pgrid, static_cast<const float*>(Z), M,
                                                 static_cast<const float*>(noise), u, static_cast<float*>(states),
-                                                labels, cap, d_count, h->pbar_count, direct, h->stream);
+                                                labels, cap, d_count, h->pbar_count, direct, !xchg, h->stream);
+  if (e == cudaSuccess) {
+    h->pbar_count += (unsigned long long)phd::persist_barriers(direct) * (unsigned long long)h->pgrid;
+    h->launches += 1;
+  }
+  if (e == cudaSuccess && pes) {
+    e = is_fp64(h) ? phd::launch_fuse<double>(h->d, h->m, static_cast<double*>(states), labels, cap, d_count, h->stream)
+                   : phd::launch_fuse<float>(h->d, h->m, static_cast<float*>(states), labels, cap, d_count, h->stream);
+    h->launches += 1;
+    if (e == cudaSuccess && xchg) {
+      e = is_fp64(h) ? phd::launch_exchange<double>(h->d, h->m, xu, h->stream)
+                     : phd::launch_exchange<float>(h->d, h->m, xu, h->stream);
+      h->launches += 3;
+    }
+  }
   if (e == cudaSuccess && timed) {
     e = cudaEventRecord(h->ev[h->ev_used].second, h->stream);
     if (e == cudaSuccess) ++h->ev_used;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "grid step");
-  h->pbar_count += (unsigned long long)phd::persist_barriers(direct) * (unsigned long long)h->pgrid;
-  h->launches += 1;
   h->have_update = true;
   return PHD_OK;
 }
@@ -737,7 +758,7 @@ phd_status step_common(phd_handle* h, const void* Z, int M, const void* noise, c
       Zk = h->d.Z;
     }
     if (st == PHD_OK)
-      st = run_grid(h, Zk, M, noise, u, direct ? d_states : h->out_states, direct ? d_labels : h->out_labels,
+      st = run_grid(h, Zk, M, noise, u, xu, direct ? d_states : h->out_states, direct ? d_labels : h->out_labels,
                     direct ? cap : h->cfg.m_max, d_count);
   } else if (noise || u || xu) {
     if (h->m.learned) {
@@ -846,8 +867,12 @@ phd_status phd_init(phd_handle** out, const phd_config* cfg, void* ws, size_t by
   if (e == cudaSuccess && h->m.K > 1 && h->m.exchange_frac > 0) e = phd::prepare_exchange(h->m);
   if (e == cudaSuccess)
     h->fused_ok = is_fp64(h) ? phd::fused_eligible<double>(h->m, h->device) : phd::fused_eligible<float>(h->m, h->device);
-  if (e == cudaSuccess && h->m.K == 1)
-    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m, false) : phd::persist_grid<float>(h->m, false);
+  // the grid step kernel: one filter, or PEs on one scan (its batch budget,
+  // the PEs' fusion and exchange as kernels after it); a birth network runs
+  // on one PE only
+  if (e == cudaSuccess && (h->m.K == 1 || !h->m.learned))
+    h->pgrid = is_fp64(h) ? phd::persist_grid<double>(h->m, h->m.K > 1)
+                          : phd::persist_grid<float>(h->m, h->m.K > 1);
   (void)cudaGetLastError();   // an ineligible attribute query leaves no sticky error
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, need, h->stream);
   phd::Anchor tab[phd::kAnchors];
@@ -1072,7 +1097,7 @@ phd_status phd_set_path(phd_handle* h, int32_t path) {
   if (path == PHD_PATH_FUSED && !h->fused_ok)
     return fail(h, PHD_ERR_INVALID_ARG, "the fused step kernel does not fit this configuration");
   if (path == PHD_PATH_GRID && h->pgrid <= 0)
-    return fail(h, PHD_ERR_INVALID_ARG, "the grid step kernel needs a one-PE filter or a batch");
+    return fail(h, PHD_ERR_INVALID_ARG, "the grid step kernel does not fit this configuration");
   h->path = path;
   return PHD_OK;
 }
@@ -1492,7 +1517,7 @@ phd_status phd_batch_step_inject(phd_handle* h, const void* d_Z, const int32_t* 
   h->launches += 1;
   phd_status st = PHD_OK;
   if (use_grid(h)) {
-    st = run_grid(h, nullptr, 0, d_noise, d_u, nullptr, nullptr, 0, nullptr);
+    st = run_grid(h, nullptr, 0, d_noise, d_u, nullptr, nullptr, nullptr, 0, nullptr);
     if (st != PHD_OK) return st;
   } else if (d_noise || d_u) {
     // caller random numbers: the stages one by one (no graph)

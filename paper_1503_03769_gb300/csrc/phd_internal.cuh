@@ -1082,12 +1082,21 @@ template <class R> cudaError_t prepare_extract();
 cudaError_t prepare_exchange(const Model& m);
 template <class R> bool fused_eligible(const Model& m, int device);
 // persistent step kernel (k_persist.cu): grid size (0: cannot launch), launch
-template <class R> int persist_grid(const Model& m, bool wide);   // wide: the batch kernel
+template <class R> int persist_grid(const Model& m, bool wide);   // wide: batches and PEs
+// direct: one filter (the kernel stages the scan and writes the estimates);
+// advance: the kernel advances the step counter (PEs with an exchange leave
+// it to the exchange kernels launched after it)
 template <class R>
 cudaError_t launch_persist(const Dev& d, const Model& m, int grid, const R* Z, int M, const R* noise,
                            const uint32_t* u, R* out_states, int* out_labels, int cap, int* d_count,
-                           unsigned long long base, bool direct, cudaStream_t s);
-int persist_barriers(bool direct);   // grid barriers one launch passes (one filter / a batch)
+                           unsigned long long base, bool direct, bool advance, cudaStream_t s);
+int persist_barriers(bool direct);   // grid barriers one launch passes (one filter / batches and PEs)
+// after the grid step kernel on PEs: the CU fusion of their local estimates
+// (Step 4) and the particle exchange (Step 6), as in the staged step
+template <class R>
+cudaError_t launch_fuse(const Dev& d, const Model& m, R* out_states, int* out_labels, int cap, int* d_count,
+                        cudaStream_t s);
+template <class R> cudaError_t launch_exchange(const Dev& d, const Model& m, const uint32_t* xu, cudaStream_t s);
 void fill_anchor_table(Anchor* tab);
 Model model_from_config(const phd_config& c);
 const char* config_problem(const phd_config& c);

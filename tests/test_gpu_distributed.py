@@ -16,12 +16,14 @@ import scenario
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_ospa(w_sc, w_f, seeds, burn_in=5):
+def _gpu_ospa(w_sc, w_f, seeds, burn_in=5, path=None):
     from paper_1503_03769_gb300 import ParticlePHD
     osp = []
     for seed in seeds:
         sc = scenario.simulate(w_sc, seed)
         f = ParticlePHD(w_f, seed=seed, device="cuda:0")
+        if path:
+            f.set_path(path)
         K = w_f.num_pe
         for k, Z in enumerate(sc.meas):
             noise = scenario.step_noise(seed, k, K, w_f.pe_cap, np.float32)
@@ -37,11 +39,14 @@ def _gpu_ospa(w_sc, w_f, seeds, burn_in=5):
     return float(np.mean(osp))
 
 
+@pytest.mark.parametrize("path", ["auto", "grid"])
 @pytest.mark.parametrize("clutter,margin", [(0.0, 0.05), (20.0, 0.05), (10.0, 0.20)])
-def test_gpu_distributed_ospa_close_to_global(clutter, margin):
+def test_gpu_distributed_ospa_close_to_global(clutter, margin, path):
+    """The default paths (the fused step kernel for the 4 PEs), and the 4 PEs
+    on the grid step kernel."""
     wd = scenario.workload("paper_bot", clutter_rate=clutter, precision="fp32")
     wg = wd.with_(num_pe=1, exchange_frac=0.0, pe_cap=wd.num_pe * wd.pe_cap)
     og = _gpu_ospa(wd, wg, range(20))
-    od = _gpu_ospa(wd, wd, range(20))
-    print(f"clutter {clutter}: global {og:.2f}, DCPFPHD {od:.2f}")
+    od = _gpu_ospa(wd, wd, range(20), path=None if path == "auto" else path)
+    print(f"clutter {clutter}: global {og:.2f}, DCPFPHD ({path}) {od:.2f}")
     assert abs(od - og) <= margin * og, (clutter, od, og)

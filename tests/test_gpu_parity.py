@@ -93,9 +93,10 @@ def test_global_linear_stages(precision, path):
 
 
 @pytest.mark.parametrize("ck_mode", ["local", "global"])
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_distributed_linear_stages(ck_mode, path):
-    """16 PEs (the paper's DCPFPHD form) with exchange, uneven slice sizes."""
+    """16 PEs (the paper's DCPFPHD form) with exchange, uneven slice sizes;
+    on the grid path every PE's slice spreads over the kernel's CTAs."""
     w = scenario.workload("dist16_10t", ck_mode=ck_mode, n_targets=6, clutter_rate=30.0,
                           particles_per_target=800, birth_count=1000, birth_steps=(1,) * 6)
     truth = scenario.simulate(w, 9, steps=3)
@@ -106,7 +107,7 @@ def test_distributed_linear_stages(ck_mode, path):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_paper_scenario_stages(precision, path):
     """The paper's own simulation shape (Sec. 4): Gaussian birth N(x_bar, Q),
     per-axis process noise, a bearing field of view (kappa over [0, r_max] x
@@ -148,11 +149,13 @@ def test_fused_many_pes_small_slices(pe_cap):
     assert rep.compared_labels > 0
 
 
-def test_maximum_pe_count_staged():
+@pytest.mark.parametrize("path", ["staged", "grid"])
+def test_maximum_pe_count(path):
     """K = 256 PEs, the most a handle takes: more PEs than SMs, so the fused
-    kernel (one co-resident CTA per PE) cannot hold them; AUTO runs the staged
-    path, a forced fused path is refused, and every stage (ring exchange and
-    CU fusion over 256 voters included) matches the oracle."""
+    kernel (one co-resident CTA per PE) cannot hold them; AUTO runs the grid
+    step kernel (its CTAs take the PEs' tiles), a forced fused path is
+    refused, and every stage (ring exchange and CU fusion over 256 voters
+    included) matches the oracle on the staged and grid paths."""
     from paper_1503_03769_gb300 import PhdError
     w = scenario.workload("dist16_10t", num_pe=256, n_targets=3, clutter_rate=20.0,
                           particles_per_target=2560, birth_count=2560, birth_steps=(1, 1, 1),
@@ -160,16 +163,16 @@ def test_maximum_pe_count_staged():
     truth = scenario.simulate(w, 17, steps=2)
     centres = np.concatenate([t[:, [0, 2]] for t in truth.truth if len(t)])
     f = _filter(w, 17, "auto")
-    assert f.get_path() == "staged"
+    assert f.get_path() == "grid"
     with pytest.raises(PhdError):
         f.set_path("fused")
     f.close()
-    rep = _run_stages(w, 17, 2, sc=truth, n_seed=[20 + (j % 9) for j in range(256)], centres=centres)
+    rep = _run_stages(w, 17, 2, sc=truth, n_seed=[20 + (j % 9) for j in range(256)], centres=centres, path=path)
     assert rep.compared_labels > 0
 
 
 @pytest.mark.parametrize("mode,threshold", [("all", 0.0), ("ring", 1e-9), ("all", 1e9), ("all", 0.97)])
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_exchange_variants_stages(mode, threshold, path):
     """Step 6 variants on 16 PEs: all-to-all every step; the adaptive trigger
     never firing (threshold 1e-9), always firing (1e9) and deciding from the
@@ -184,7 +187,7 @@ def test_exchange_variants_stages(mode, threshold, path):
     assert rep.compared_labels > 0
 
 
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_range_bearing_stages_many_measurements(path):
     """Range-bearing sensor, M ~ 330 (> one 256-thread round), 4 PEs, FP32."""
     w = scenario.workload("dense_rb_100t", n_targets=30, clutter_rate=300.0,
@@ -280,7 +283,7 @@ def test_free_running_fp64_matches_oracle_over_many_steps():
     assert worst < 1e-6
 
 
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_published_distributed_workload_sizes(path):
     """The 16-PE workload at its published sizes (10 targets, lambda = 50,
     1000 particles per target, 1000 births) in the launch configuration the
@@ -291,14 +294,15 @@ def test_published_distributed_workload_sizes(path):
     assert rep.max_mass_rel <= 1e-5
 
 
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_dense_workload_64_pes_full_size(path):
     """The dense workload's 64-PE distributed form (config 3) at full size:
     64 generator slices of rho / 64 particles per live target (~3.1e3 each,
     ~2.2e5 in all) against ~600 measurements, one step in the launch
     configuration the benchmark times (staged path autotuned on these
-    slices; fused path one CTA per PE), every stage of every PE against the
-    oracle (which runs on all host cores)."""
+    slices; fused path one CTA per PE; grid path the PEs over the whole
+    GPU), every stage of every PE against the oracle (which runs on all host
+    cores)."""
     w = scenario.workload("dense_rb_100t_pe64")
     sc = scenario.simulate(w, 6, steps=61)
     tr = sc.truth[60]
@@ -478,7 +482,7 @@ def test_free_running_philox_moments():
     f.close()
 
 
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_checkpoint_resume_is_bit_identical(path):
     w = scenario.workload("dist16_10t", num_pe=4, n_targets=4, clutter_rate=20.0,
                           particles_per_target=300, birth_count=400)
@@ -503,7 +507,7 @@ def test_checkpoint_resume_is_bit_identical(path):
 
 
 @pytest.mark.parametrize("pinned", [False, True])
-@pytest.mark.parametrize("path", ["staged", "fused"])
+@pytest.mark.parametrize("path", ["staged", "fused", "grid"])
 def test_step_host_matches_device_step(path, pinned):
     """Host-memory steps equal device steps: pageable buffers (copies through
     the workspace) and pinned ones (the kernels read Z and write the
@@ -557,18 +561,18 @@ def test_fused_run_matches_fused_steps():
         np.testing.assert_array_equal(wa[j], wb[j])
 
 
-@pytest.mark.parametrize("pair", ["fused-staged", "grid-staged"])
+@pytest.mark.parametrize("pair", ["fused-staged", "grid-staged", "grid16-staged"])
 def test_paths_track_each_other(pair):
     """Free-running with the same seed: the fused (or grid) step kernel and
     the staged kernels draw the same Philox numbers and agree on the
-    estimates over a 40-scan run (the 16-PE workload; its one-PE form for the
-    grid path), up to near-tie selections (and the divergence a resampling
-    tie-flip starts)."""
+    estimates over a 40-scan run (the 16-PE workload; on the grid path its
+    one-PE form and the 16 PEs), up to near-tie selections (and the
+    divergence a resampling tie-flip starts)."""
     w = scenario.workload("dist16_10t", steps=40)
-    if pair.startswith("grid"):
+    if pair.startswith("grid-"):
         w = w.with_(num_pe=1, exchange_frac=0.0, pe_cap=16 * w.pe_cap)
     sc = scenario.simulate(w, 31)
-    a, b = _filter(w, 31, pair.split("-")[0]), _filter(w, 31, "staged")
+    a, b = _filter(w, 31, pair.split("-")[0].rstrip("0123456789")), _filter(w, 31, "staged")
     same, diffs, oa, ob = 0, [], [], []
     for k, Z in enumerate(sc.meas):
         sa, la = a.step(Z)
