@@ -650,7 +650,7 @@ phd_status run_grid(phd_handle* h, const void* Z, int M, const void* noise, cons
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
-  if (e == cudaSuccess && pes && Z != h->d.Z) {
+  if (e == cudaSuccess && pes) {   // also in place (Z already in the workspace): it publishes M
     e = is_fp64(h) ? phd::launch_stage_z<double>(h->d, h->m, static_cast<const double*>(Z), M, h->stream)
                    : phd::launch_stage_z<float>(h->d, h->m, static_cast<const float*>(Z), M, h->stream);
     h->launches += kNStageZ;

@@ -515,16 +515,22 @@ def test_step_host_matches_device_step(path, pinned):
     from paper_1503_03769_gb300 import PhdError
     w = scenario.workload("dist16_10t", num_pe=4, n_targets=4, clutter_rate=20.0,
                           particles_per_target=300, birth_count=400)
-    sc = scenario.simulate(w, 8, steps=6)
+    sc = scenario.simulate(w, 8, steps=8)
     a, b = _filter(w, 8, path), _filter(w, 8, path)
 
     def host(shape, dt):
         t = torch.zeros(shape, dtype=dt)
         return (t.pin_memory() if pinned else t).numpy()
 
+    # both start from the same generator slices around the targets of scan 2
+    # (the first with a live target), so the compared steps have estimates
+    x0, w0 = exact_state(w, 81, 300, centres=sc.truth[2][:, [0, 2]], mass=float(len(sc.truth[2])))
+    a.set_state(x0, w0)
+    b.set_state(x0, w0)
     out_s = host((w.m_max, 4), torch.float32)
     out_l = host(w.m_max, torch.int32)
-    for Z in sc.meas[:5]:
+    compared = 0
+    for Z in sc.meas[2:7]:
         Zh = host(Z.shape, torch.float32)
         Zh[:] = Z
         sa, la = a.step(Z)
@@ -532,7 +538,9 @@ def test_step_host_matches_device_step(path, pinned):
         assert n == len(la)
         np.testing.assert_array_equal(out_l[:n], la.cpu().numpy())
         np.testing.assert_array_equal(out_s[:n], sa.cpu().numpy())
-    Z = sc.meas[5]
+        compared += n
+    assert compared > 0
+    Z = sc.meas[7]
     Zh = host(Z.shape, torch.float32)
     Zh[:] = Z
     sa, la = a.step(Z)
