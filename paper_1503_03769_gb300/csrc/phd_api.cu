@@ -618,6 +618,9 @@ bool use_fused(const phd_handle* h) {
 // staged graph with the autotuner's launch shapes runs level with the grid
 // kernel at its batch register budget (256 runs, ~1e7 particles: 1.05 ms
 // per batched step staged, 1.04 ms grid); AUTO keeps the autotuned graph.
+// PEs the fused kernel cannot hold (slices past an SM's shared memory, more
+// PEs than co-resident CTAs) follow the same rule (16 PEs at 4x the
+// particles of the 16-PE workload: 99.8 us per step grid, 102 us staged).
 constexpr double kGridAutoItems = 16.0;
 bool grid_auto(const phd_handle* h) {
   const double items = (double)h->m.K * (double)((h->cfg.pe_cap + 255) / 256);
